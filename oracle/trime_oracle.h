@@ -1,0 +1,128 @@
+/*
+ * trime_oracle.h -- plain FP64 CPU oracle for one TriMe++ meshing iteration.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference arm of bench.py may load this code.  The product
+ * path (the CUDA library under paper_2309_13824_gb300/) shares no code with it.
+ *
+ * What it computes, with the paper section each part follows
+ * (TriMe++, Lu & Rycroft, arXiv 2309.13824):
+ *   - geometry grid classes, h_i, geps_i                      Sec. 3.2, 3.4, 3.7
+ *   - bounded Voronoi cells by half-plane clipping            Sec. 2.1 Fig. 3, Sec. 4.1
+ *   - Delaunay triangles read off the cells, Tests 1-3        Sec. 4.1, Procedure I
+ *   - DistMesh spring forces + forward Euler                  Sec. 2.2 Eqs. 2-5
+ *   - CVD density-weighted centroid, adaptive quadrature      Sec. 2.3 Eq. 6, Sec. 4.2
+ *   - point treatment: clamp, classify, sphere trace, Newton  Sec. 4.3 Eqs. 8-10
+ *   - aspect/edge ratio quality, 1/2-means, hybrid switch     Sec. 3.6 Eqs. 11-12, Sec. 4
+ *
+ * Every sign decision of the triangulation (incircle / orientation) is exact:
+ * big-integer arithmetic behind a deliberately loose double-precision filter,
+ * with symbolic perturbation of the lifted coordinate for exact ties.
+ */
+#ifndef TRIME_ORACLE_H
+#define TRIME_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t nx, ny;            /* nodes, >= 2 each                      */
+    double x0, y0, x1, y1;     /* node (0,0) at (x0,y0), (nx-1,ny-1) at (x1,y1) */
+    const float* v;            /* row-major v[j*nx+i], borrowed          */
+} om_grid;
+
+typedef struct {
+    int32_t method;            /* 0 DistMesh, 1 CVD, 2 hybrid            */
+    int32_t bounded;           /* 1: octagon bound of span S (Sec. 4.1); 0: domain box only */
+    int32_t validity;          /* 1: Tests 1-3 (Sec. 4.1); 0: keep every emitted triangle */
+    int32_t newton_max;        /* T_ct^newton = 10                       */
+    int32_t trace_max;         /* sphere-trace step cap (paper silent)   */
+    int32_t quad_max_level;    /* quadrature level cap (paper silent)    */
+    double fac_F, k_spring, dt;
+    double fac_pt, fac_geps, fac_voro_bound, fac_end;
+    double T_circ, T_switch, T_end_q, T_end_amax;
+    double N_opt, eta, damping;
+} om_params;
+
+typedef struct {
+    int64_t n_tri;             /* valid triangles                        */
+    int64_t n_edges;           /* unique valid edges                     */
+    double half_mean_alpha;    /* M_1/2(alpha), Eq. 12                   */
+    double half_mean_beta;     /* M_1/2(beta)                            */
+    double max_alpha, max_beta, min_angle_deg;
+    double mean_size_dev;      /* mean |l/(fac_mu mu(m)) - 1| over valid edges */
+    double fac_mu;             /* Eq. 3                                  */
+    int64_t newton_fail, trace_cap, quad_cap, clip_errors;
+    int32_t method_used;       /* 0 DM / 1 CVD for the move just made    */
+    int32_t terminated;        /* termination test held (Sec. 4)         */
+    int32_t switched;          /* hybrid has switched to CVD             */
+    int32_t small_moves;       /* all inner moves < fac_end h_i          */
+} om_stats;
+
+typedef struct om_mesh om_mesh;
+
+void om_default_params(om_params* p);
+
+/* Create from positions xy[2n] (x,y interleaved).  Grids are deep-copied.
+ * Returns NULL on invalid input (message via om_last_error). */
+om_mesh* om_create(const om_grid* sdf, const om_grid* sizing, const double* xy,
+                   int64_t n, const om_params* p);
+void om_destroy(om_mesh* m);
+const char* om_last_error(void);
+
+/* Procedure I at the current positions: cells, triangles, validity, quality. */
+int om_rebuild(om_mesh* m);
+/* One meshing iteration: rebuild, quality, hybrid/termination logic, move. */
+int om_step(om_mesh* m);
+/* Same as om_step but only for the cells listed (timing sample; no move). */
+int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid);
+
+int64_t om_num_points(const om_mesh* m);
+int64_t om_num_triangles(const om_mesh* m);
+void om_get_triangles(const om_mesh* m, int32_t* tri);          /* 3*n_tri, sorted */
+int64_t om_num_edges(const om_mesh* m);
+void om_get_edges(const om_mesh* m, int32_t* e);                /* 2*n_edges, sorted */
+void om_get_points(const om_mesh* m, double* xy);
+void om_set_points(om_mesh* m, const double* xy);
+void om_get_class(const om_mesh* m, uint8_t* cls);
+void om_set_class(om_mesh* m, const uint8_t* cls);
+void om_get_dprev(const om_mesh* m, double* d);
+void om_set_dprev(om_mesh* m, const double* d);
+void om_set_method_state(om_mesh* m, int32_t switched, double prev_a, double prev_b, double prev_amax);
+/* Results of the last om_step: raw move p_new before treatment, force F (DM)
+ * or centroid c (CVD), and the quadrature level used per point. */
+void om_get_pnew(const om_mesh* m, double* xy);
+void om_get_force(const om_mesh* m, double* f);
+void om_get_fsum(const om_mesh* m, double* s);   /* sum_e |f_e| per point (force scale) */
+void om_get_centroid(const om_mesh* m, double* c);
+void om_get_cell_area(const om_mesh* m, double* a);
+void om_get_quad_level(const om_mesh* m, int32_t* lv);
+void om_get_stats(const om_mesh* m, om_stats* s);
+
+/* Per-cell views for pins. */
+int om_get_ring(const om_mesh* m, int64_t i, int32_t* labels, int cap);
+int om_get_cell_polygon(const om_mesh* m, int64_t i, double* xy, int cap);
+void om_get_geometry(const om_mesh* m, uint8_t* cls, double* h, double* geps, double* havg);
+int om_point_cell(const om_mesh* m, double x, double y, int32_t* gi, int32_t* gj);
+
+/* Exact predicates (sign in {-1,0,1}); incircle is det of rows
+ * [x, y, x^2+y^2, 1] of (a,b,c,d): > 0 iff d is inside circle(a,b,c) for
+ * counter-clockwise a,b,c.  The _sos form never returns 0. */
+int om_orient2d(const double* a, const double* b, const double* c);
+int om_incircle(const double* a, const double* b, const double* c, const double* d);
+int om_incircle_sos(const double* a, int64_t ia, const double* b, int64_t ib,
+                    const double* c, int64_t ic, const double* d, int64_t id);
+double om_bilinear(const om_grid* g, double x, double y);
+
+/* Standalone pieces for pins. */
+int om_polygon_centroid(const om_grid* sizing, const double* gen, const double* poly, int nv,
+                        double eps_c, int max_level, double* c, int32_t* level);
+int om_project_point(om_mesh* m, const double* p_old, int old_class, const double* p_new,
+                     double* p_final, int32_t* new_class);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
