@@ -1,0 +1,174 @@
+/*
+ * trime.h -- C ABI of the GB300 meshing-iteration library.
+ *
+ * One meshing iteration of TriMe++ (Lu & Rycroft, arXiv 2309.13824) on one
+ * GPU: bucket the points into a uniform grid, build every point's bounded
+ * Voronoi cell by half-plane clipping, read the Delaunay triangles off the
+ * cells and keep the valid ones, then move the points (DistMesh springs, CVD
+ * centroids or the hybrid of the two) and project escaped points back through
+ * the bilinear signed-distance grid.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: 0 on success, a negative TRIME_E* code on failure; the
+ *    message of the last failure on the calling thread is mesh_last_error().
+ *  - Ownership: the library deep-copies every input at mesh_init and owns all
+ *    device memory it allocates; output functions copy into caller buffers.
+ *  - Streams: every call is ordered on the stream given at mesh_init.  Calls
+ *    that return data to the host synchronise that stream.
+ *  - No torch types cross this boundary: plain pointers and sizes only.
+ */
+#ifndef TRIME_H
+#define TRIME_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRIME_OK 0
+#define TRIME_EINVAL (-1)     /* bad argument (null pointer, size, non-finite value) */
+#define TRIME_ENOMEM (-2)     /* device or host allocation failed                   */
+#define TRIME_ECUDA (-3)      /* a CUDA runtime call failed                          */
+#define TRIME_ECAPACITY (-4)  /* output buffer too small; *n_out holds the size needed */
+#define TRIME_ETIMEOUT (-5)   /* a bounded device wait ran out                       */
+#define TRIME_EDEVICE (-6)    /* the device reported an error (see mesh_stats counters) */
+
+/* A node-centred grid sampled bilinearly: node (i,j) sits at
+ * (x0 + i*(x1-x0)/(nx-1), y0 + j*(y1-y0)/(ny-1)); values are row-major
+ * v[j*nx + i] in HOST memory (float32).  nx, ny >= 2.  Used for the signed
+ * distance field (Sec. 3.1: negative inside, positive outside) and for the
+ * element sizing field mu (Sec. 3.3, Eq. 7; density rho = 1/mu^2, Eq. 8). */
+typedef struct {
+    int32_t nx, ny;
+    double x0, y0, x1, y1;
+    const float* v;
+} mesh_grid2d;
+
+/* Control parameters; mesh_default_params fills the paper's App. B defaults.
+ * Fields the paper leaves open carry the readings stated beside them. */
+typedef struct {
+    int32_t precision;       /* 0: FP64 positions; 1: FP32 positions, FP64 predicates   */
+    int32_t method;          /* 0 DistMesh (Sec. 2.2), 1 CVD (Sec. 2.3), 2 hybrid (Sec. 2.4) */
+    int32_t bounded;         /* 1: octagon cell bound of span S = fac_voro_bound*h (Sec. 4.1) */
+    int32_t validity;        /* 1: keep only triangles passing Tests 1-3 (Sec. 4.1)     */
+    int32_t newton_max;      /* Newton steps of the point projection, T_ct^newton = 10  */
+    int32_t trace_max;       /* sphere-trace steps (paper silent): 64                   */
+    int32_t quad_max_level;  /* centroid quadrature level cap (paper silent): 8         */
+    int32_t debug;           /* 1: mesh_step records per-point moves for mesh_get_debug */
+    double fac_F;            /* 1.2   desired-length factor (Eq. 3)                       */
+    double k_spring;         /* 1.0   spring stiffness k (paper lists none)               */
+    double dt;               /* 0.2   forward-Euler step (paper lists none)               */
+    double fac_pt;           /* 0.4   movement clamp T_pt = fac_pt*h_i (Sec. 3.7)          */
+    double fac_geps;         /* 0.01  geps_i = fac_geps*min(h_i, h_avg)                    */
+    double fac_voro_bound;   /* 5     octagon span factor                                  */
+    double fac_end;          /* 0.001 small-movement factor                                */
+    double T_circ;           /* 0.4   circumcentre test threshold (Test 3)                 */
+    double T_switch;         /* 0.0015 hybrid switch threshold                             */
+    double T_end_q;          /* 0.001 quality termination threshold                        */
+    double T_end_amax;       /* 0.005 max-aspect-ratio termination threshold               */
+    double N_opt;            /* 3.3   points per bucket of the neighbour grid (Sec. 3.2)   */
+    double eta;              /* 0.5   selected-boundary band factor (Sec. 3.5)             */
+    double damping;          /* 1.0   Newton damping alpha-hat                             */
+} mesh_params;
+
+/* Statistics of the last iteration run by mesh_step (or of mesh_rebuild). */
+typedef struct {
+    int32_t iterations;        /* iterations executed by the call                         */
+    int32_t terminated;        /* a termination criterion of Sec. 4 holds                 */
+    int32_t method;            /* move of the last executed iteration: 0 DM, 1 CVD, -1 none */
+    int32_t switched;          /* hybrid has switched to CVD                              */
+    int64_t n_tri;             /* valid triangles of the last rebuild                     */
+    int64_t n_edges;           /* unique valid edges                                      */
+    double half_mean_alpha;    /* 1/2-mean of the aspect ratio alpha (Eqs. 11-12)         */
+    double half_mean_beta;     /* 1/2-mean of the edge ratio beta                         */
+    double max_alpha, max_beta;
+    double min_angle_deg;
+    double mean_size_dev;      /* mean |l / (fac_mu mu(m)) - 1| over valid edges          */
+    double fac_mu;             /* Eq. 3 scaling factor                                    */
+    int64_t exact_calls;       /* predicate evaluations that needed exact arithmetic      */
+    int64_t clip_inconsistent; /* clips whose cut set was not one run (0 expected)        */
+    int64_t ring_overflow;     /* cells with more than 32 edges (results dropped)         */
+    int64_t exact_overflow;    /* exact-arithmetic capacity or underflow guard tripped    */
+    int64_t newton_fail;       /* projections that kept p_old (Sec. 4.3)                  */
+    int64_t trace_cap;         /* sphere traces that hit trace_max                        */
+    int64_t quad_cap;          /* centroids that hit quad_max_level                       */
+    int64_t dup_points;        /* points whose cell is empty (exact duplicate, SoS)       */
+    int32_t small_moves;       /* every inner point moved less than fac_end*h_i           */
+    int32_t reserved1;
+} mesh_stats;
+
+typedef struct mesh_s mesh_t;
+
+/* Fill *p with the defaults listed above.  Never fails. */
+void mesh_default_params(mesh_params* p);
+
+/* Create a mesh on the current CUDA device.
+ *  sdf, sizing: host grids, deep-copied (sizing values must be > 0).
+ *  xy: HOST array of n (x, y) pairs, float64 if p->precision == 0 else
+ *      float32, every point finite and inside the SDF grid's box.
+ *  n >= 0.  p may be NULL for the defaults.  cuda_stream: a cudaStream_t
+ *  (NULL = legacy default stream) on which all later work is ordered.
+ * Precomputes the geometry grid on the SDF grid's cells (Sec. 3.2 classes,
+ * Sec. 3.7 h_i and geps_i), allocates all device buffers and captures one
+ * iteration into a CUDA graph.  Errors: TRIME_EINVAL, TRIME_ENOMEM, TRIME_ECUDA. */
+int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, const void* xy, int64_t n,
+              const mesh_params* p, void* cuda_stream);
+
+/* Procedure I (Sec. 2.1, 4.1) at the current positions: cells, triangles,
+ * Tests 1-3 and quality, without moving.  Synchronises; fills *stats if given. */
+int mesh_rebuild(mesh_t* m, mesh_stats* stats);
+
+/* Run up to n_iters meshing iterations (Algorithms 1-2; hybrid Sec. 4.2),
+ * each one graph launch: rebuild, quality, hybrid/termination decision, move,
+ * point treatment (Sec. 4.3).  Stops early once a termination criterion of
+ * Sec. 4 holds.  Synchronises at the end; fills *stats if given.  Returns
+ * TRIME_EDEVICE if a capacity guard tripped (counters in *stats). */
+int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats);
+
+/* Valid triangles of the last rebuild as int32 (a, b, c) point indices, a the
+ * smallest index, counter-clockwise; order unspecified.  tri may be host or
+ * device memory (detected); cap in triangles.  If cap is too small returns
+ * TRIME_ECAPACITY with *n_out = the number needed. */
+int mesh_get_triangles(mesh_t* m, int32_t* tri, int64_t cap, int64_t* n_out);
+
+/* Current positions in input order, float64 or float32 as the precision;
+ * host or device buffer of cap points. */
+int mesh_get_points(mesh_t* m, void* xy, int64_t cap, int64_t* n_out);
+
+/* Replace the per-point state (positions in the mesh's precision, point
+ * classes 0 inner / 1 boundary, previous move distances as float64); host
+ * pointers, any may be NULL to keep the current value.  Used to resume a
+ * mesh or to start two implementations from identical states. */
+int mesh_set_state(mesh_t* m, const void* xy, const uint8_t* cls, const double* dprev);
+
+/* Hybrid state: switched flag and the previous iteration's quality. */
+int mesh_set_method_state(mesh_t* m, int32_t switched, double prev_half_alpha, double prev_half_beta,
+                          double prev_max_alpha);
+
+/* Per-point results of the last mesh_step iteration, in input order, float64:
+ * what = 0 raw new position before treatment (2 per point), 1 DistMesh force F_i
+ * (2), 2 CVD centroid (2), 3 sum of spring magnitudes |f| at the point (1),
+ * 4 point class after treatment (1, as 0.0/1.0), 5 previous-move distance (1),
+ * 6 quadrature level used (1).  Host buffer of cap doubles. */
+int mesh_get_debug(mesh_t* m, int32_t what, double* out, int64_t cap);
+
+/* Release all memory of m (NULL is ignored). */
+void mesh_destroy(mesh_t* m);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* mesh_last_error(void);
+
+/* a1 on its own (Sec. 3.2 grid, App. B N_opt): counting sort of n points into
+ * an nbx*nby bucket grid over [x0,x1]x[y0,y1].  All pointers are DEVICE
+ * memory: x, y (n float64), out: bucket_start (nbx*nby+1 int32), sorted_idx
+ * (n int32, input indices grouped by bucket, order within a bucket
+ * unspecified).  scratch: device int32 array of at least 2*n + nbx*nby + 1024
+ * entries, overwritten.  Asynchronous on the stream (cudaStream_t). */
+int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, double y0, double x1,
+                       double y1, int32_t nbx, int32_t nby, int32_t* bucket_start, int32_t* sorted_idx,
+                       int32_t* scratch, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,239 @@
+"""GB300 meshing iteration of TriMe++ (arXiv 2309.13824) behind a C ABI.
+
+This module only marshals arguments to the shared library built from csrc/
+(see include/trime.h); every step of the iteration runs in the CUDA kernels.
+There is no CPU fallback: importing works without a GPU, but any call needs
+the built library and a CUDA device and raises otherwise.
+
+Function names mirror the C ABI.  ``Mesh`` is a small convenience wrapper
+that accepts numpy arrays and torch tensors and returns numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_build" / "libtrime_gb300.so"
+
+TRIME_OK = 0
+TRIME_EINVAL = -1
+TRIME_ENOMEM = -2
+TRIME_ECUDA = -3
+TRIME_ECAPACITY = -4
+TRIME_ETIMEOUT = -5
+TRIME_EDEVICE = -6
+
+
+class MeshError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"trime error {code}: {msg}")
+        self.code = code
+
+
+class mesh_grid2d(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("x0", C.c_double), ("y0", C.c_double),
+                ("x1", C.c_double), ("y1", C.c_double), ("v", C.POINTER(C.c_float))]
+
+
+class mesh_params(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("method", C.c_int32), ("bounded", C.c_int32),
+                ("validity", C.c_int32), ("newton_max", C.c_int32), ("trace_max", C.c_int32),
+                ("quad_max_level", C.c_int32), ("debug", C.c_int32), ("fac_F", C.c_double),
+                ("k_spring", C.c_double), ("dt", C.c_double), ("fac_pt", C.c_double), ("fac_geps", C.c_double),
+                ("fac_voro_bound", C.c_double), ("fac_end", C.c_double), ("T_circ", C.c_double),
+                ("T_switch", C.c_double), ("T_end_q", C.c_double), ("T_end_amax", C.c_double),
+                ("N_opt", C.c_double), ("eta", C.c_double), ("damping", C.c_double)]
+
+
+class mesh_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("terminated", C.c_int32), ("method", C.c_int32),
+                ("switched", C.c_int32), ("n_tri", C.c_int64), ("n_edges", C.c_int64),
+                ("half_mean_alpha", C.c_double), ("half_mean_beta", C.c_double), ("max_alpha", C.c_double),
+                ("max_beta", C.c_double), ("min_angle_deg", C.c_double), ("mean_size_dev", C.c_double),
+                ("fac_mu", C.c_double), ("exact_calls", C.c_int64), ("clip_inconsistent", C.c_int64),
+                ("ring_overflow", C.c_int64), ("exact_overflow", C.c_int64), ("newton_fail", C.c_int64),
+                ("trace_cap", C.c_int64), ("quad_cap", C.c_int64), ("dup_points", C.c_int64),
+                ("small_moves", C.c_int32), ("reserved1", C.c_int32)]
+
+
+# every symbol include/trime.h declares
+EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles",
+           "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
+           "mesh_last_error", "mesh_bucket_points"]
+
+_lib = None
+
+
+def build(**kw) -> Path:
+    from . import buildlib as _b
+
+    return _b.build(**kw)
+
+
+def lib():
+    """Load the CUDA library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run paper_2309_13824_gb300.build())")
+    L = C.CDLL(str(LIB_PATH))
+    P = C.POINTER
+    vp = C.c_void_p
+    L.mesh_default_params.argtypes = [P(mesh_params)]
+    L.mesh_default_params.restype = None
+    L.mesh_init.argtypes = [P(vp), P(mesh_grid2d), P(mesh_grid2d), vp, C.c_int64, P(mesh_params), vp]
+    L.mesh_rebuild.argtypes = [vp, P(mesh_stats)]
+    L.mesh_step.argtypes = [vp, C.c_int32, P(mesh_stats)]
+    L.mesh_get_triangles.argtypes = [vp, vp, C.c_int64, P(C.c_int64)]
+    L.mesh_get_points.argtypes = [vp, vp, C.c_int64, P(C.c_int64)]
+    L.mesh_set_state.argtypes = [vp, vp, vp, vp]
+    L.mesh_set_method_state.argtypes = [vp, C.c_int32, C.c_double, C.c_double, C.c_double]
+    L.mesh_get_debug.argtypes = [vp, C.c_int32, vp, C.c_int64]
+    L.mesh_destroy.argtypes = [vp]
+    L.mesh_destroy.restype = None
+    L.mesh_last_error.restype = C.c_char_p
+    L.mesh_bucket_points.argtypes = [vp, vp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                     C.c_int32, C.c_int32, vp, vp, vp, vp]
+    for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles", "mesh_get_points",
+                 "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != TRIME_OK:
+        raise MeshError(rc, lib().mesh_last_error().decode())
+    return rc
+
+
+def mesh_default_params() -> mesh_params:
+    p = mesh_params()
+    lib().mesh_default_params(C.byref(p))
+    return p
+
+
+def mesh_last_error() -> str:
+    return lib().mesh_last_error().decode()
+
+
+def _grid(g):
+    v = np.ascontiguousarray(g.values, dtype=np.float32)
+    return mesh_grid2d(v.shape[1], v.shape[0], g.x0, g.y0, g.x1, g.y1, v.ctypes.data_as(C.POINTER(C.c_float))), v
+
+
+def _ptr(t):
+    """Raw pointer of a numpy array or torch tensor (device or host)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(t.ctypes.data)
+
+
+def mesh_bucket_points(x, y, n, box, nbx, nby, bucket_start, sorted_idx, scratch, stream=0):
+    """a1 on device arrays (torch CUDA tensors); asynchronous on `stream`."""
+    rc = lib().mesh_bucket_points(_ptr(x), _ptr(y), n, box[0], box[1], box[2], box[3], nbx, nby,
+                                  _ptr(bucket_start), _ptr(sorted_idx), _ptr(scratch), C.c_void_p(stream))
+    return _check(rc)
+
+
+def _stats_dict(s: mesh_stats) -> dict:
+    return {name: getattr(s, name) for name, _ in mesh_stats._fields_}
+
+
+class Mesh:
+    """One mesh on the current CUDA device (a handle to mesh_t)."""
+
+    def __init__(self, sdf, sizing, xy, stream=None, **params):
+        L = lib()
+        p = mesh_default_params()
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        self.params = p
+        self.precision = p.precision
+        self.dtype = np.float64 if p.precision == 0 else np.float32
+        xy = np.ascontiguousarray(np.asarray(xy, dtype=self.dtype).reshape(-1, 2))
+        self.n = len(xy)
+        gs, ks = _grid(sdf)
+        gz, kz = _grid(sizing)
+        h = C.c_void_p()
+        st = C.c_void_p(0 if stream is None else int(stream))
+        rc = L.mesh_init(C.byref(h), C.byref(gs), C.byref(gz), xy.ctypes.data_as(C.c_void_p), self.n,
+                         C.byref(p), st)
+        _check(rc)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rebuild(self) -> dict:
+        s = mesh_stats()
+        _check(lib().mesh_rebuild(self._h, C.byref(s)))
+        return _stats_dict(s)
+
+    def step(self, n_iters: int = 1, check=True) -> dict:
+        s = mesh_stats()
+        rc = lib().mesh_step(self._h, n_iters, C.byref(s))
+        if check:
+            _check(rc)
+        d = _stats_dict(s)
+        d["rc"] = rc
+        return d
+
+    def triangles(self, out=None):
+        """Valid triangles (int32, smallest id first, CCW), order unspecified.
+        With `out` (host array or device tensor of shape (cap, 3)) fills it
+        and returns the count; otherwise returns a numpy array."""
+        L = lib()
+        n = C.c_int64()
+        if out is not None:
+            _check(L.mesh_get_triangles(self._h, _ptr(out), out.shape[0], C.byref(n)))
+            return n.value
+        rc = L.mesh_get_triangles(self._h, None, 0, C.byref(n))
+        if rc not in (TRIME_OK, TRIME_ECAPACITY):
+            _check(rc)
+        t = np.zeros((n.value, 3), dtype=np.int32)
+        if n.value:
+            _check(L.mesh_get_triangles(self._h, t.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
+        return t
+
+    def points(self, out=None):
+        n = C.c_int64()
+        if out is not None:
+            _check(lib().mesh_get_points(self._h, _ptr(out), out.shape[0], C.byref(n)))
+            return out
+        p = np.zeros((self.n, 2), dtype=self.dtype)
+        _check(lib().mesh_get_points(self._h, p.ctypes.data_as(C.c_void_p), self.n, C.byref(n)))
+        return p
+
+    def set_state(self, xy=None, cls=None, dprev=None):
+        a = None if xy is None else np.ascontiguousarray(np.asarray(xy, dtype=self.dtype).reshape(-1, 2))
+        b = None if cls is None else np.ascontiguousarray(cls, dtype=np.uint8)
+        c = None if dprev is None else np.ascontiguousarray(dprev, dtype=np.float64)
+        _check(lib().mesh_set_state(self._h, None if a is None else a.ctypes.data_as(C.c_void_p),
+                                    None if b is None else b.ctypes.data_as(C.c_void_p),
+                                    None if c is None else c.ctypes.data_as(C.c_void_p)))
+
+    def set_method_state(self, switched, prev_a=0.0, prev_b=0.0, prev_amax=0.0):
+        _check(lib().mesh_set_method_state(self._h, switched, prev_a, prev_b, prev_amax))
+
+    def debug(self, what: int):
+        width = [2, 2, 2, 1, 1, 1, 1][what]
+        out = np.zeros(width * self.n)
+        _check(lib().mesh_get_debug(self._h, what, out.ctypes.data_as(C.c_void_p), len(out)))
+        return out.reshape(self.n, 2) if width == 2 else out

@@ -1,0 +1,260 @@
+// bucket.cu -- a1: counting sort of the points into the neighbour-bucket grid
+// (the paper's Voro++ container of N/N_opt blocks, Sec. 3.2 and Listing 1),
+// plus the per-slot precomputation the later kernels read: the geometry cell
+// by the fixed formula and the exact-duplicate (SoS) flag.
+//
+// count: one atomic per point gives its bucket and rank; scan: exclusive
+// prefix over the bucket counts (three passes); scatter: each point moves its
+// whole state to bucket_start[key] + rank.  All passes are HBM-streaming.
+#include "kernels.cuh"
+
+namespace trime {
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_count(IterArgs<T> a) {
+    if (!a.force && a.ctrl->terminated) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int bx, by;
+    bucket_of(a.P, a.cur.x[i], a.cur.y[i], bx, by);
+    int k = by * a.P.nbx + bx;
+    a.key[i] = k;
+    a.rank[i] = atomicAdd(&a.bcount[k], 1);
+}
+
+// ------------------------------------------------------------------ scan
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;  // per thread
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__device__ __forceinline__ int block_excl_scan(int v, int* sh, int& total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < (blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    int base = w > 0 ? sh[w - 1] : 0;
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_reduce(const int32_t* in, int32_t n, int32_t* tile_sums) {
+    __shared__ int sh[32];
+    int base = blockIdx.x * kScanTile;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int i = base + k * kScanBlock + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    int total;
+    block_excl_scan(s, sh, total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_tiles(int32_t* tile_sums, int32_t ntiles) {
+    __shared__ int sh[32];
+    int carry = 0;
+    for (int b = 0; b < ntiles; b += kScanBlock) {
+        int i = b + threadIdx.x;
+        int v = i < ntiles ? tile_sums[i] : 0;
+        int total;
+        int e = block_excl_scan(v, sh, total);
+        if (i < ntiles) tile_sums[i] = carry + e;
+        carry += total;
+    }
+}
+
+// out[i] = sum in[0..i), out[n] = total; items of a tile are blocked per thread
+__global__ void __launch_bounds__(kScanBlock) k_scan_down(const int32_t* in, int32_t* out, int32_t n,
+                                                           const int32_t* tile_off) {
+    __shared__ int sh[32];
+    int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int i = base + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    int total;
+    int e = block_excl_scan(s, sh, total) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        int i = base + k;
+        if (i < n) out[i] = e;
+        if (i == n - 1) out[n] = e + v[k];
+        e += v[k];
+    }
+}
+
+void launch_scan(const int32_t* in, int32_t* out, int32_t n, int32_t* tmp, cudaStream_t st) {
+    int ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles < 1) ntiles = 1;
+    k_scan_reduce<<<ntiles, kScanBlock, 0, st>>>(in, n, tmp);
+    k_scan_tiles<<<1, kScanBlock, 0, st>>>(tmp, ntiles);
+    k_scan_down<<<ntiles, kScanBlock, 0, st>>>(in, out, n, tmp);
+}
+
+// ------------------------------------------------------------------ scatter
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_scatter(IterArgs<T> a) {
+    if (!a.force && a.ctrl->terminated) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int k = a.key[i];
+    int d = a.bstart[k] + a.rank[i];
+    T x = a.cur.x[i], y = a.cur.y[i];
+    a.srt.x[d] = x;
+    a.srt.y[d] = y;
+    a.srt.id[d] = a.cur.id[i];
+    a.srt.cls[d] = a.cur.cls[i];
+    a.srt.dprev[d] = a.cur.dprev[i];
+    a.skey[d] = k;
+    // geometry cell by the fixed formula floor((x - x0) / dx); the cheaper
+    // product with 1/dx decides unless it lands within 1e-9 of a cell edge
+    double xd = (double)x, yd = (double)y;
+    double tx = (xd - a.sdf.x0) * (1.0 / a.sdf.dx), ty = (yd - a.sdf.y0) * (1.0 / a.sdf.dy);
+    double ftx = tx - floor(tx), fty = ty - floor(ty);
+    int gi, gj;
+    int ncx = a.sdf.nx - 1, ncy = a.sdf.ny - 1;
+    if (ftx > 1e-9 && ftx < 1.0 - 1e-9 && fty > 1e-9 && fty < 1.0 - 1e-9 && tx >= 0.0 && ty >= 0.0 &&
+        tx < (double)ncx && ty < (double)ncy) {
+        gi = (int)tx;
+        gj = (int)ty;
+    } else {
+        point_cell_fixed(a.sdf, xd, yd, gi, gj);
+    }
+    a.cell[d] = gj * ncx + gi;
+}
+
+// SoS duplicate rule: of several points at exactly the same position the one
+// with the largest id owns the cell; the others are flagged (empty cells)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dups(IterArgs<T> a) {
+    if (!a.force && a.ctrl->terminated) return;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned dup = 0;
+    if (s < a.n) {
+        int k = a.skey[s];
+        T x = a.srt.x[s], y = a.srt.y[s];
+        int id = a.srt.id[s];
+        int e = a.bstart[k + 1];
+        for (int q = a.bstart[k]; q < e; q++)
+            if (q != s && a.srt.x[q] == x && a.srt.y[q] == y && a.srt.id[q] > id) dup = 1;
+        a.dom[s] = (uint8_t)dup;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, dup);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctrl->cnt.dup_points, (unsigned long long)__popc(m));
+}
+
+template <typename T>
+void launch_bucket(const IterArgs<T>& a, cudaStream_t st) {
+    int nb = a.P.nbx * a.P.nby;
+    int g = (a.n + kThreads - 1) / kThreads;
+    if (g < 1) g = 1;
+    cudaMemsetAsync(a.bcount, 0, sizeof(int32_t) * (size_t)nb, st);
+    k_count<T><<<g, kThreads, 0, st>>>(a);
+    launch_scan(a.bcount, a.bstart, nb, a.scan_tmp, st);
+    k_scatter<T><<<g, kThreads, 0, st>>>(a);
+    k_dups<T><<<g, kThreads, 0, st>>>(a);
+}
+
+template void launch_bucket<double>(const IterArgs<double>&, cudaStream_t);
+template void launch_bucket<float>(const IterArgs<float>&, cudaStream_t);
+
+// ------------------------------------------------------------------ permutations
+template <typename T>
+__global__ void k_unpermute(IterArgs<T> a, T* out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    int id = a.cur.id[s];
+    out[2 * (size_t)id] = a.cur.x[s];
+    out[2 * (size_t)id + 1] = a.cur.y[s];
+}
+
+template <typename T>
+void launch_unpermute(const IterArgs<T>& a, T* out, cudaStream_t st) {
+    int g = (a.n + kThreads - 1) / kThreads;
+    if (g > 0) k_unpermute<T><<<g, kThreads, 0, st>>>(a, out);
+}
+template void launch_unpermute<double>(const IterArgs<double>&, double*, cudaStream_t);
+template void launch_unpermute<float>(const IterArgs<float>&, float*, cudaStream_t);
+
+template <typename T>
+__global__ void k_set_state(IterArgs<T> a, const T* xy, const uint8_t* cls, const double* dprev) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    int id = a.cur.id[s];
+    if (xy) {
+        a.cur.x[s] = xy[2 * (size_t)id];
+        a.cur.y[s] = xy[2 * (size_t)id + 1];
+    }
+    if (cls) a.cur.cls[s] = cls[id];
+    if (dprev) a.cur.dprev[s] = (T)dprev[id];
+}
+
+template <typename T>
+void launch_set_state(const IterArgs<T>& a, const T* xy, const uint8_t* cls, const double* dprev, cudaStream_t st) {
+    int g = (a.n + kThreads - 1) / kThreads;
+    if (g > 0) k_set_state<T><<<g, kThreads, 0, st>>>(a, xy, cls, dprev);
+}
+template void launch_set_state<double>(const IterArgs<double>&, const double*, const uint8_t*, const double*,
+                                       cudaStream_t);
+template void launch_set_state<float>(const IterArgs<float>&, const float*, const uint8_t*, const double*,
+                                      cudaStream_t);
+
+// ------------------------------------------------------------------ standalone a1
+__global__ void k_count_raw(const double* x, const double* y, int32_t n, double x0, double y0, double ibsx,
+                            double ibsy, int32_t nbx, int32_t nby, int32_t* key, int32_t* rank, int32_t* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int bx = (int)floor((x[i] - x0) * ibsx), by = (int)floor((y[i] - y0) * ibsy);
+    bx = bx < 0 ? 0 : (bx >= nbx ? nbx - 1 : bx);
+    by = by < 0 ? 0 : (by >= nby ? nby - 1 : by);
+    int k = by * nbx + bx;
+    key[i] = k;
+    rank[i] = atomicAdd(&cnt[k], 1);
+}
+
+__global__ void k_scatter_raw(int32_t n, const int32_t* key, const int32_t* rank, const int32_t* bstart,
+                              int32_t* sorted_idx) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sorted_idx[bstart[key[i]] + rank[i]] = i;
+}
+
+// scratch layout: key[n] | rank[n] | counts[nb] | scan tiles (<= 1024)
+void launch_bucket_raw(const double* x, const double* y, int32_t n, double x0, double y0, double bsx, double bsy,
+                       int32_t nbx, int32_t nby, int32_t* bstart, int32_t* sorted_idx, int32_t* scratch,
+                       cudaStream_t st) {
+    int nb = nbx * nby;
+    int32_t* key = scratch;
+    int32_t* rank = scratch + n;
+    int32_t* cnt = scratch + 2 * (size_t)n;
+    int32_t* tiles = cnt + nb;
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)nb, st);
+    int g = (n + kThreads - 1) / kThreads;
+    if (g > 0)
+        k_count_raw<<<g, kThreads, 0, st>>>(x, y, n, x0, y0, 1.0 / bsx, 1.0 / bsy, nbx, nby, key, rank, cnt);
+    launch_scan(cnt, bstart, nb, tiles, st);
+    if (g > 0) k_scatter_raw<<<g, kThreads, 0, st>>>(n, key, rank, bstart, sorted_idx);
+}
+
+}  // namespace trime

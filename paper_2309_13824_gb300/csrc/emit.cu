@@ -1,0 +1,335 @@
+// emit.cu -- a3/a4: Delaunay triangles read off the cells and the valid ones
+// kept (TriMe++ Sec. 4.1, Procedure I; duality Sec. 1.1), plus the per-block
+// quality sums of a8 (Sec. 3.6 Eqs. 11-12) and the DistMesh sums of Eq. 3.
+//
+// One thread per cell.  Consecutive bisector edges (j, k) of cell i's ring
+// meet at the circumcentre c of the CCW triangle (i, j, k).  The triangle is
+// emitted iff c lies in Reg_i, Reg_j and Reg_k (octagon of span S = fac*h
+// intersected with the domain box) and is valid iff Tests 1-3 pass; both are
+// decided by fixed FP64 formulas evaluated on the canonical order (smallest
+// id first, CCW), so the three cells of a triangle always agree.  A float
+// evaluation with a proven error bound decides first when it is far from the
+// threshold.  Cell i records the result as bit t of vmask[i]; the triangle
+// is counted once, by its smallest-id vertex.
+#include "kernels.cuh"
+
+namespace trime {
+
+constexpr float kEpsF = 5.9604645e-8f;  // 2^-24
+
+__device__ __forceinline__ void circumcentre_fixed(double ax, double ay, double bx, double by, double cx, double cy,
+                                                   double& ox, double& oy, double& R) {
+    double bx_ = fsub(bx, ax), by_ = fsub(by, ay), cx_ = fsub(cx, ax), cy_ = fsub(cy, ay);
+    double B = fadd(fmul(bx_, bx_), fmul(by_, by_));
+    double C = fadd(fmul(cx_, cx_), fmul(cy_, cy_));
+    double D = fmul(2.0, fsub(fmul(bx_, cy_), fmul(by_, cx_)));
+    double ux = fdiv(fsub(fmul(cy_, B), fmul(by_, C)), D);
+    double uy = fdiv(fsub(fmul(bx_, C), fmul(cx_, B)), D);
+    ox = fadd(ax, ux);
+    oy = fadd(ay, uy);
+    R = __dsqrt_rn(fadd(fmul(ux, ux), fmul(uy, uy)));
+}
+
+// c in Reg_v = Oct_v (span S_v) cap domain box, fixed formula
+__device__ __forceinline__ bool reg_contains_fixed(const DevParams& P, double px, double py, double h, double cx,
+                                                   double cy) {
+    if (!(cx >= P.bx0 && cx <= P.bx1 && cy >= P.by0 && cy <= P.by1)) return false;
+    if (!P.bounded) return true;
+    double S = fmul(P.fac_voro_bound, h);
+    double dx = fsub(cx, px), dy = fsub(cy, py);
+    return fabs(dx) <= S && fabs(dy) <= S && fabs(fmul(kRT, fadd(dx, dy))) <= S &&
+           fabs(fmul(kRT, fsub(dy, dx))) <= S;
+}
+
+struct Tri {
+    double x[3], y[3];
+    double h[3];
+};
+
+// Tests 1-3 on the canonical order (a = smallest id, CCW)
+template <typename T>
+__device__ bool valid_fixed(const IterArgs<T>& a, const Tri& t) {
+    const DevGrid& s = a.sdf;
+    int ncx = s.nx - 1;
+    double gx = fdiv(fadd(fadd(t.x[0], t.x[1]), t.x[2]), 3.0);
+    double gy = fdiv(fadd(fadd(t.y[0], t.y[1]), t.y[2]), 3.0);
+    int gi, gj;
+    if (!point_cell_fixed(s, gx, gy, gi, gj)) return false;
+    int c = gj * ncx + gi;
+    uint8_t k = a.gcls[c];
+    if (k == CELL_INNER) return true;
+    if (k == CELL_OUTER) return false;
+    if (bilin_fixed(s, gx, gy) > a.ggeps[c]) return false;
+    int count = 0;
+    for (int e = 0; e < 3; e++) {
+        int f = e == 2 ? 0 : e + 1;
+        double mx = fmul(fadd(t.x[e], t.x[f]), 0.5), my = fmul(fadd(t.y[e], t.y[f]), 0.5);
+        if (!point_cell_fixed(s, mx, my, gi, gj)) continue;
+        int q = gj * ncx + gi;
+        if (a.gcls[q] == CELL_INNER) count++;
+        else if (a.gcls[q] == CELL_BOUNDARY && bilin_fixed(s, mx, my) <= a.ggeps[q]) count++;
+    }
+    if (count >= 2) return true;
+    double ox, oy, R;
+    circumcentre_fixed(t.x[0], t.y[0], t.x[1], t.y[1], t.x[2], t.y[2], ox, oy, R);
+    return fdiv(fabs(bilin_fixed(s, ox, oy)), R) <= a.P.T_circ;
+}
+
+struct Nbr {
+    int slot, id, cell;
+    float dx, dy;  // relative to the cell's generator
+};
+
+template <typename T>
+__device__ __forceinline__ Nbr load_nbr(const IterArgs<T>& a, int lab, T xi, T yi) {
+    Nbr n;
+    n.slot = lab;
+    if (lab >= 0) {
+        T x = a.srt.x[lab], y = a.srt.y[lab];
+        n.id = a.srt.id[lab];
+        n.cell = a.cell[lab];
+        n.dx = (float)(x - xi);
+        n.dy = (float)(y - yi);
+    } else {
+        n.id = 0;
+        n.cell = 0;
+        n.dx = n.dy = 0.f;
+    }
+    return n;
+}
+
+// emission decision for (i, j, k), CCW as seen from cell i
+template <typename T>
+__device__ bool emitted(const IterArgs<T>& a, int si, int idi, int ci, T xi, T yi, const Nbr& j, const Nbr& k) {
+    const DevParams& P = a.P;
+    float ax = j.dx, ay = j.dy, bx = k.dx, by = k.dy;
+    float M = ax * by - ay * bx;
+    float PM = fabsf(ax * by) + fabsf(ay * bx);
+    if (M > 64.0f * kEpsF * PM && PM > 1e-30f) {
+        float al = ax * ax + ay * ay, bl = bx * bx + by * by;
+        float ux = (al * by - bl * ay) / (2.0f * M), uy = (bl * ax - al * bx) / (2.0f * M);
+        float un = fabsf(ux) + fabsf(uy);
+        float eu = 64.0f * kEpsF * ((al * fabsf(by) + bl * fabsf(ay)) + (bl * fabsf(ax) + al * fabsf(bx)) + 2.0f * un * PM) /
+                   (2.0f * M);
+        int state = 1;  // 1 inside, 0 outside, 2 undecided
+        // domain box, relative to p_i
+        float lx = (float)(P.bx0 - (double)xi), hx = (float)(P.bx1 - (double)xi);
+        float ly = (float)(P.by0 - (double)yi), hy = (float)(P.by1 - (double)yi);
+        float mgb = eu + 4.0f * kEpsF * (un + fabsf(lx) + fabsf(hx) + fabsf(ly) + fabsf(hy)) + 1e-7f;
+        float bo = fmaxf(fmaxf(lx - ux, ux - hx), fmaxf(ly - uy, uy - hy));  // > 0 outside
+        if (bo > mgb) state = 0;
+        else if (bo > -mgb) state = 2;
+        if (state != 0 && P.bounded) {
+            const Nbr* V[2] = {&j, &k};
+            for (int v = 0; v < 3 && state != 0; v++) {
+                float dvx = v == 0 ? 0.f : V[v - 1]->dx, dvy = v == 0 ? 0.f : V[v - 1]->dy;
+                int cv = v == 0 ? ci : V[v - 1]->cell;
+                float S = (float)(P.fac_voro_bound * a.gh[cv]);
+                float wx = ux - dvx, wy = uy - dvy;
+                float f = fmaxf(fmaxf(fabsf(wx), fabsf(wy)), 0.70710678f * fmaxf(fabsf(wx + wy), fabsf(wy - wx)));
+                float mg = eu + 4.0f * kEpsF * (un + fabsf(dvx) + fabsf(dvy)) + 1e-6f * S;
+                if (f > S + mg) state = 0;
+                else if (f > S - mg) state = 2;
+            }
+        }
+        if (state != 2) return state == 1;
+    }
+    // fixed FP64 formula on the canonical order
+    double xs[3] = {(double)xi, (double)a.srt.x[j.slot], (double)a.srt.x[k.slot]};
+    double ys[3] = {(double)yi, (double)a.srt.y[j.slot], (double)a.srt.y[k.slot]};
+    int ids[3] = {idi, j.id, k.id};
+    int cells[3] = {ci, j.cell, k.cell};
+    int r = 0;
+    if (ids[1] < ids[r]) r = 1;
+    if (ids[2] < ids[r]) r = 2;
+    int o1 = r == 2 ? 0 : r + 1, o2 = o1 == 2 ? 0 : o1 + 1;
+    double ox, oy, R;
+    circumcentre_fixed(xs[r], ys[r], xs[o1], ys[o1], xs[o2], ys[o2], ox, oy, R);
+    for (int v = 0; v < 3; v++)
+        if (!reg_contains_fixed(P, xs[v], ys[v], a.gh[cells[v]], ox, oy)) return false;
+    return true;
+}
+
+template <typename T>
+__device__ bool valid_tri(const IterArgs<T>& a, int idi, int ci, T xi, T yi, const Nbr& j, const Nbr& k) {
+    if (!a.P.validity) return true;
+    // Test 1 shortcut: the centroid's cell is within a few cells of p_i's cell,
+    // and every cell closer than gidist is inner
+    float gx = (j.dx + k.dx) * (1.0f / 3.0f), gy = (j.dy + k.dy) * (1.0f / 3.0f);
+    float off = fmaxf(fabsf(gx) * (float)(1.0 / a.sdf.dx), fabsf(gy) * (float)(1.0 / a.sdf.dy));
+    if (off + 2.01f < (float)a.gidist[ci]) return true;
+    int ids[3] = {idi, j.id, k.id};
+    double xs[3] = {(double)xi, (double)a.srt.x[j.slot], (double)a.srt.x[k.slot]};
+    double ys[3] = {(double)yi, (double)a.srt.y[j.slot], (double)a.srt.y[k.slot]};
+    int r = 0;
+    if (ids[1] < ids[r]) r = 1;
+    if (ids[2] < ids[r]) r = 2;
+    int o1 = r == 2 ? 0 : r + 1, o2 = o1 == 2 ? 0 : o1 + 1;
+    Tri t;
+    t.x[0] = xs[r]; t.y[0] = ys[r];
+    t.x[1] = xs[o1]; t.y[1] = ys[o1];
+    t.x[2] = xs[o2]; t.y[2] = ys[o2];
+    return valid_fixed(a, t);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
+    if (!a.force && a.ctrl->terminated) return;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[9] = {0, 0, 0, 0, 0, 180.0, 0, 0, 0};
+    if (s < a.n) {
+        int ne = a.ring_n[s];
+        int lab[kRingCap];
+        const int4* row = reinterpret_cast<const int4*>(a.ring + (size_t)s * kRingCap);
+        for (int q = 0; q < (ne + 3) / 4; q++) {
+            int4 v = row[q];
+            lab[4 * q] = v.x;
+            lab[4 * q + 1] = v.y;
+            lab[4 * q + 2] = v.z;
+            lab[4 * q + 3] = v.w;
+        }
+        T xi = a.srt.x[s], yi = a.srt.y[s];
+        int idi = a.srt.id[s];
+        int ci = a.cell[s];
+        uint32_t vm = 0;
+        if (ne >= 2) {
+            Nbr first = load_nbr(a, lab[0], xi, yi);
+            Nbr cur = first;
+            for (int t = 0; t < ne; t++) {
+                Nbr nxt = t + 1 < ne ? load_nbr(a, lab[t + 1], xi, yi) : first;
+                if (cur.slot >= 0 && nxt.slot >= 0 && emitted(a, s, idi, ci, xi, yi, cur, nxt) &&
+                    valid_tri(a, idi, ci, xi, yi, cur, nxt)) {
+                    vm |= 1u << t;
+                    if (idi < cur.id && idi < nxt.id) {
+                        // quality of the triangle (Eq. 11), float from the relative coordinates
+                        float bx = cur.dx, by = cur.dy, cx = nxt.dx, cy = nxt.dy;
+                        float la = hypotf(bx - cx, by - cy), lb = hypotf(cx, cy), lc = hypotf(bx, by);
+                        float A2 = fabsf(bx * cy - by * cx);
+                        float alpha = (la * lb * lc * (la + lb + lc)) / (4.0f * A2 * A2);
+                        float lmax = fmaxf(la, fmaxf(lb, lc)), lmin = fminf(la, fminf(lb, lc));
+                        float p = lmin == la ? lb : la, q = lmin == lc ? lb : lc;
+                        if (lmin == lb) { p = la; q = lc; }
+                        float cs = (p * p + q * q - lmin * lmin) / (2.0f * p * q);
+                        cs = fminf(1.0f, fmaxf(-1.0f, cs));
+                        acc[0] += 1.0;
+                        acc[1] += sqrt((double)alpha);
+                        acc[2] += sqrt((double)(lmax / lmin));
+                        acc[3] = fmax(acc[3], (double)alpha);
+                        acc[4] = fmax(acc[4], (double)(lmax / lmin));
+                        acc[5] = fmin(acc[5], (double)acosf(cs) * (180.0 / 3.14159265358979323846));
+                    }
+                }
+                cur = nxt;
+            }
+            // valid edges (Eq. 3 sums), counted by the smaller id
+            for (int t = 0; t < ne; t++) {
+                int j = lab[t];
+                if (j < 0) continue;
+                int tp = t == 0 ? ne - 1 : t - 1;
+                if (!((vm >> t) & 1u) && !((vm >> tp) & 1u)) continue;
+                if (!(idi < a.srt.id[j])) continue;
+                T xj = a.srt.x[j], yj = a.srt.y[j];
+                T dx = xj - xi, dy = yj - yi;
+                T mu = bilin<T>(a.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
+                acc[6] += 1.0;
+                acc[7] += (double)(dx * dx + dy * dy);
+                acc[8] += (double)(mu * mu);
+            }
+        }
+        a.vmask[s] = vm;
+    }
+    // block reduction into one partial
+    __shared__ double sh[kThreads / 32][9];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = 0; q < 9; q++) {
+        double v = (q == 3 || q == 4) ? warp_max_d(acc[q]) : (q == 5 ? warp_min_d(acc[q]) : warp_sum_d(acc[q]));
+        if (lane == 0) sh[w][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        int q = threadIdx.x;
+        double v = sh[0][q];
+        for (int k = 1; k < kThreads / 32; k++)
+            v = (q == 3 || q == 4) ? fmax(v, sh[k][q]) : (q == 5 ? fmin(v, sh[k][q]) : v + sh[k][q]);
+        double* out = reinterpret_cast<double*>(&a.ep[blockIdx.x]);
+        out[q] = v;
+    }
+}
+
+template <typename T>
+void launch_emit(const IterArgs<T>& a, int nblocks, cudaStream_t st) {
+    k_emit<T><<<nblocks, kThreads, 0, st>>>(a);
+}
+template void launch_emit<double>(const IterArgs<double>&, int, cudaStream_t);
+template void launch_emit<float>(const IterArgs<float>&, int, cudaStream_t);
+
+// ------------------------------------------------------------------ triangle output
+template <typename T>
+__global__ void k_tri_count(IterArgs<T> a, int32_t* cnt) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    int ne = a.ring_n[s];
+    uint32_t vm = a.vmask[s];
+    int idi = a.srt.id[s];
+    int c = 0;
+    for (int t = 0; t < ne; t++) {
+        if (!((vm >> t) & 1u)) continue;
+        int j = a.ring[(size_t)s * kRingCap + t], k = a.ring[(size_t)s * kRingCap + (t + 1 == ne ? 0 : t + 1)];
+        if (idi < a.srt.id[j] && idi < a.srt.id[k]) c++;
+    }
+    cnt[s] = c;
+}
+
+template <typename T>
+__global__ void k_tri_write(IterArgs<T> a, const int32_t* off, int32_t* tri) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    int ne = a.ring_n[s];
+    uint32_t vm = a.vmask[s];
+    int idi = a.srt.id[s];
+    int o = off[s];
+    for (int t = 0; t < ne; t++) {
+        if (!((vm >> t) & 1u)) continue;
+        int j = a.ring[(size_t)s * kRingCap + t], k = a.ring[(size_t)s * kRingCap + (t + 1 == ne ? 0 : t + 1)];
+        int idj = a.srt.id[j], idk = a.srt.id[k];
+        if (idi < idj && idi < idk) {
+            tri[3 * (size_t)o] = idi;
+            tri[3 * (size_t)o + 1] = idj;
+            tri[3 * (size_t)o + 2] = idk;
+            o++;
+        }
+    }
+}
+
+template <typename T>
+void launch_tri_count(const IterArgs<T>& a, int32_t* cnt, cudaStream_t st) {
+    int g = (a.n + kThreads - 1) / kThreads;
+    if (g > 0) k_tri_count<T><<<g, kThreads, 0, st>>>(a, cnt);
+}
+template <typename T>
+void launch_tri_write(const IterArgs<T>& a, const int32_t* off, int32_t* tri, cudaStream_t st) {
+    int g = (a.n + kThreads - 1) / kThreads;
+    if (g > 0) k_tri_write<T><<<g, kThreads, 0, st>>>(a, off, tri);
+}
+template void launch_tri_count<double>(const IterArgs<double>&, int32_t*, cudaStream_t);
+template void launch_tri_count<float>(const IterArgs<float>&, int32_t*, cudaStream_t);
+template void launch_tri_write<double>(const IterArgs<double>&, const int32_t*, int32_t*, cudaStream_t);
+template void launch_tri_write<float>(const IterArgs<float>&, const int32_t*, int32_t*, cudaStream_t);
+
+}  // namespace trime

@@ -1,0 +1,712 @@
+// mesh.cu -- host runtime behind the C ABI of include/trime.h.
+//
+// Owns every device buffer, precomputes the geometry grid once (TriMe++
+// Sec. 3.2 cell classes, Sec. 3.4-3.5 density, Sec. 3.7 h_i and geps_i) with
+// serial row-major sums, and captures one meshing iteration (a1..a8) into a
+// CUDA graph that mesh_step replays.  Work runs on a private stream that is
+// ordered after / before the caller's stream with events, so graph capture
+// works whatever stream the caller passes.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "trime.h"
+
+using namespace trime;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(x)                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = (x);                                                                  \
+        if (e_ != cudaSuccess) return fail(TRIME_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct mesh_s {
+    int prec = 0;
+    int64_t n = 0;
+    mesh_params P{};
+    DevParams dp{};
+    cudaStream_t user = nullptr, st = nullptr;
+    cudaEvent_t ev = nullptr;
+    DevGrid sdf{}, siz{};
+    uint8_t* gcls = nullptr;
+    double* gh = nullptr;
+    double* ggeps = nullptr;
+    uint8_t* gidist = nullptr;
+    void *cx = nullptr, *cy = nullptr, *cdp = nullptr, *sx = nullptr, *sy = nullptr, *sdp = nullptr;
+    int32_t *cid = nullptr, *sid = nullptr;
+    uint8_t *ccls = nullptr, *scls = nullptr;
+    int32_t *cell = nullptr, *key = nullptr, *rank = nullptr, *skey = nullptr;
+    uint8_t* dom = nullptr;
+    int32_t *bcount = nullptr, *bstart = nullptr, *scan_tmp = nullptr;
+    int32_t* ring = nullptr;
+    uint8_t* ring_n = nullptr;
+    float* cellR = nullptr;
+    uint32_t* vmask = nullptr;
+    EmitPartial* ep = nullptr;
+    UpdatePartial* up = nullptr;
+    int nblk = 1;
+    DevCtrl* ctrl = nullptr;
+    DevCtrl* hctrl = nullptr;  // pinned host copy
+    double* dbg = nullptr;
+    int32_t *tcnt = nullptr, *toff = nullptr, *tbuf = nullptr;
+    void* xybuf = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<void*> allocs;
+};
+
+template <typename T>
+static T* dalloc(mesh_s* m, size_t count, int& rc) {
+    if (rc) return nullptr;
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        rc = fail(TRIME_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return nullptr;
+    }
+    m->allocs.push_back(p);
+    return static_cast<T*>(p);
+}
+
+// ------------------------------------------------------------------ host geometry
+static double host_bilin(const mesh_grid2d& g, double dx, double dy, double x, double y) {
+    double tx = (x - g.x0) / dx, ty = (y - g.y0) / dy;
+    double fi = std::floor(tx), fj = std::floor(ty);
+    int i = !(fi >= 0.0) ? 0 : (fi > (double)(g.nx - 2) ? g.nx - 2 : (int)fi);
+    int j = !(fj >= 0.0) ? 0 : (fj > (double)(g.ny - 2) ? g.ny - 2 : (int)fj);
+    double fx = tx - (double)i, fy = ty - (double)j;
+    fx = fx < 0.0 ? 0.0 : (fx > 1.0 ? 1.0 : fx);
+    fy = fy < 0.0 ? 0.0 : (fy > 1.0 ? 1.0 : fy);
+    const float* r0 = g.v + (size_t)j * g.nx + i;
+    const float* r1 = r0 + g.nx;
+    double v00 = r0[0], v10 = r0[1], v01 = r1[0], v11 = r1[1];
+    double a = v00 + fx * (v10 - v00);
+    double b = v01 + fx * (v11 - v01);
+    return a + fy * (b - a);
+}
+
+static bool grid_ok(const mesh_grid2d* g) {
+    if (!g || !g->v || g->nx < 2 || g->ny < 2 || !(g->x1 > g->x0) || !(g->y1 > g->y0)) return false;
+    if (!std::isfinite(g->x0) || !std::isfinite(g->x1) || !std::isfinite(g->y0) || !std::isfinite(g->y1)) return false;
+    size_t n = (size_t)g->nx * (size_t)g->ny;
+    for (size_t k = 0; k < n; k++)
+        if (!std::isfinite(g->v[k])) return false;
+    return true;
+}
+
+struct HostGeometry {
+    std::vector<uint8_t> cls, idist;
+    std::vector<double> h, geps;
+    double havg = 0;
+};
+
+// Sec. 3.2 classes from the SDF at cell midpoints; Sec. 3.5 normalised
+// density over inner and selected-boundary cells; Sec. 3.7 h_i, geps_i
+static int host_geometry(const mesh_grid2d& sdf, const mesh_grid2d& siz, int64_t N, const mesh_params& P,
+                         HostGeometry& G) {
+    int ncx = sdf.nx - 1, ncy = sdf.ny - 1;
+    size_t nc = (size_t)ncx * (size_t)ncy;
+    double dx = (sdf.x1 - sdf.x0) / (double)(sdf.nx - 1), dy = (sdf.y1 - sdf.y0) / (double)(sdf.ny - 1);
+    double hdx = (siz.x1 - siz.x0) / (double)(siz.nx - 1), hdy = (siz.y1 - siz.y0) / (double)(siz.ny - 1);
+    double ldiag = std::sqrt(dx * dx + dy * dy);
+    double band = P.eta * std::min(dx, dy);
+    G.cls.resize(nc);
+    G.h.resize(nc);
+    G.geps.resize(nc);
+    std::vector<double> rho(nc);
+    std::vector<uint8_t> sel(nc);
+    double sum_rho = 0.0;
+    int64_t nsel = 0;
+    for (int gj = 0; gj < ncy; gj++)
+        for (int gi = 0; gi < ncx; gi++) {
+            size_t c = (size_t)gj * ncx + gi;
+            const float* r0 = sdf.v + (size_t)gj * sdf.nx + gi;
+            const float* r1 = r0 + sdf.nx;
+            double sm = 0.25 * ((((double)r0[0] + (double)r0[1]) + (double)r1[0]) + (double)r1[1]);
+            uint8_t k = std::fabs(sm) <= ldiag ? CELL_BOUNDARY : (sm < 0.0 ? CELL_INNER : CELL_OUTER);
+            G.cls[c] = k;
+            double mx = sdf.x0 + ((double)gi + 0.5) * dx, my = sdf.y0 + ((double)gj + 0.5) * dy;
+            double mu = host_bilin(siz, hdx, hdy, mx, my);
+            rho[c] = 1.0 / (mu * mu);
+            sel[c] = (k == CELL_INNER) || (k == CELL_BOUNDARY && sm <= band);
+            if (sel[c]) {
+                sum_rho += rho[c];
+                nsel++;
+            }
+        }
+    if (nsel == 0) return fail(TRIME_EINVAL, "the SDF grid has no inner or selected boundary cells");
+    double sum_h = 0.0;
+    for (int gj = 0; gj < ncy; gj++)
+        for (int gi = 0; gi < ncx; gi++) {
+            size_t c = (size_t)gj * ncx + gi;
+            double nE = (rho[c] / sum_rho) * (double)N;
+            G.h[c] = std::sqrt((dx * dy) / nE);
+            if (sel[c]) sum_h += G.h[c];
+        }
+    G.havg = sum_h / (double)nsel;
+    for (size_t c = 0; c < nc; c++) G.geps[c] = P.fac_geps * std::min(G.h[c], G.havg);
+    // Chebyshev distance to the nearest non-inner cell (outside the grid counts)
+    std::vector<int> d(nc);
+    for (int gj = 0; gj < ncy; gj++)
+        for (int gi = 0; gi < ncx; gi++) {
+            size_t c = (size_t)gj * ncx + gi;
+            int e = std::min(std::min(gi + 1, gj + 1), std::min(ncx - gi, ncy - gj));
+            d[c] = G.cls[c] == CELL_INNER ? e : 0;
+        }
+    for (int gj = 0; gj < ncy; gj++)
+        for (int gi = 0; gi < ncx; gi++) {
+            size_t c = (size_t)gj * ncx + gi;
+            for (int oj = -1; oj <= 0; oj++)
+                for (int oi = -1; oi <= 1; oi++) {
+                    if (oj == 0 && oi >= 0) continue;
+                    int a = gi + oi, b = gj + oj;
+                    if (a < 0 || a >= ncx || b < 0) continue;
+                    d[c] = std::min(d[c], d[(size_t)b * ncx + a] + 1);
+                }
+        }
+    for (int gj = ncy - 1; gj >= 0; gj--)
+        for (int gi = ncx - 1; gi >= 0; gi--) {
+            size_t c = (size_t)gj * ncx + gi;
+            for (int oj = 0; oj <= 1; oj++)
+                for (int oi = -1; oi <= 1; oi++) {
+                    if (oj == 0 && oi <= 0) continue;
+                    int a = gi + oi, b = gj + oj;
+                    if (a < 0 || a >= ncx || b >= ncy) continue;
+                    d[c] = std::min(d[c], d[(size_t)b * ncx + a] + 1);
+                }
+        }
+    G.idist.resize(nc);
+    for (size_t c = 0; c < nc; c++) G.idist[c] = (uint8_t)std::min(d[c], 255);
+    return 0;
+}
+
+// ------------------------------------------------------------------ enqueue helpers
+template <typename T>
+static IterArgs<T> make_args(mesh_s* m, int force) {
+    IterArgs<T> a;
+    a.n = (int32_t)m->n;
+    a.force = force;
+    a.P = m->dp;
+    a.sdf = m->sdf;
+    a.siz = m->siz;
+    a.gcls = m->gcls;
+    a.gh = m->gh;
+    a.ggeps = m->ggeps;
+    a.gidist = m->gidist;
+    a.cur = {(T*)m->cx, (T*)m->cy, m->cid, m->ccls, (T*)m->cdp};
+    a.srt = {(T*)m->sx, (T*)m->sy, m->sid, m->scls, (T*)m->sdp};
+    a.cell = m->cell;
+    a.key = m->key;
+    a.rank = m->rank;
+    a.skey = m->skey;
+    a.dom = m->dom;
+    a.bcount = m->bcount;
+    a.bstart = m->bstart;
+    a.scan_tmp = m->scan_tmp;
+    a.ring = m->ring;
+    a.ring_n = m->ring_n;
+    a.cellR = m->cellR;
+    a.vmask = m->vmask;
+    a.ep = m->ep;
+    a.up = m->up;
+    a.ctrl = m->ctrl;
+    a.dbg = m->dbg;
+    return a;
+}
+
+template <typename T>
+static void enqueue_rebuild(mesh_s* m, int force, int decide) {
+    IterArgs<T> a = make_args<T>(m, force);
+    launch_bucket<T>(a, m->st);
+    launch_voronoi<T>(a, m->st);
+    launch_emit<T>(a, m->nblk, m->st);
+    launch_stats_pre(m->ctrl, m->ep, m->nblk, decide, force, m->dp, m->st);
+}
+
+template <typename T>
+static void enqueue_iteration(mesh_s* m) {
+    enqueue_rebuild<T>(m, 0, 1);
+    IterArgs<T> a = make_args<T>(m, 0);
+    launch_update<T>(a, m->nblk, m->st);
+    launch_stats_post(m->ctrl, m->up, m->nblk, m->st);
+}
+
+static void enqueue(mesh_s* m, bool iteration, int force) {
+    if (m->prec == 0) {
+        if (iteration) enqueue_iteration<double>(m);
+        else enqueue_rebuild<double>(m, force, 0);
+    } else {
+        if (iteration) enqueue_iteration<float>(m);
+        else enqueue_rebuild<float>(m, force, 0);
+    }
+}
+
+static int sync_in(mesh_s* m) {
+    CUDA_TRY(cudaEventRecord(m->ev, m->user));
+    CUDA_TRY(cudaStreamWaitEvent(m->st, m->ev, 0));
+    return 0;
+}
+
+static int sync_out(mesh_s* m) {
+    CUDA_TRY(cudaEventRecord(m->ev, m->st));
+    CUDA_TRY(cudaStreamWaitEvent(m->user, m->ev, 0));
+    return 0;
+}
+
+static int read_ctrl(mesh_s* m) {
+    CUDA_TRY(cudaMemcpyAsync(m->hctrl, m->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return 0;
+}
+
+static void fill_stats(const mesh_s* m, int iters, mesh_stats* s) {
+    const DevCtrl& c = *m->hctrl;
+    std::memset(s, 0, sizeof *s);
+    s->iterations = iters;
+    s->terminated = c.terminated;
+    s->method = c.last_method;
+    s->switched = c.switched;
+    s->n_tri = (int64_t)c.n_tri;
+    s->n_edges = (int64_t)c.n_edges;
+    s->half_mean_alpha = c.half_a;
+    s->half_mean_beta = c.half_b;
+    s->max_alpha = c.max_a;
+    s->max_beta = c.max_b;
+    s->min_angle_deg = c.min_ang;
+    s->mean_size_dev = c.size_dev;
+    s->fac_mu = c.fac_mu;
+    s->exact_calls = (int64_t)c.cnt.exact_calls;
+    s->clip_inconsistent = (int64_t)c.cnt.clip_inconsistent;
+    s->ring_overflow = (int64_t)c.cnt.ring_overflow;
+    s->exact_overflow = (int64_t)c.cnt.exact_overflow;
+    s->newton_fail = (int64_t)c.cnt.newton_fail;
+    s->trace_cap = (int64_t)c.cnt.trace_cap;
+    s->quad_cap = (int64_t)c.cnt.quad_cap;
+    s->dup_points = (int64_t)c.cnt.dup_points;
+    s->small_moves = c.small_moves;
+}
+
+static int reset_counters(mesh_s* m) {
+    CUDA_TRY(cudaMemsetAsync(&m->ctrl->cnt, 0, sizeof(DevCounters), m->st));
+    return 0;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void mesh_default_params(mesh_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->precision = 0;
+    p->method = 2;
+    p->bounded = 1;
+    p->validity = 1;
+    p->newton_max = 10;
+    p->trace_max = 64;
+    p->quad_max_level = 8;
+    p->fac_F = 1.2;
+    p->k_spring = 1.0;
+    p->dt = 0.2;
+    p->fac_pt = 0.4;
+    p->fac_geps = 0.01;
+    p->fac_voro_bound = 5.0;
+    p->fac_end = 0.001;
+    p->T_circ = 0.4;
+    p->T_switch = 0.0015;
+    p->T_end_q = 0.001;
+    p->T_end_amax = 0.005;
+    p->N_opt = 3.3;
+    p->eta = 0.5;
+    p->damping = 1.0;
+}
+
+const char* mesh_last_error(void) { return g_err.c_str(); }
+
+void mesh_destroy(mesh_t* m) {
+    if (!m) return;
+    if (m->st) cudaStreamSynchronize(m->st);
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    for (void* p : m->allocs) cudaFree(p);
+    if (m->hctrl) cudaFreeHost(m->hctrl);
+    if (m->ev) cudaEventDestroy(m->ev);
+    if (m->st) cudaStreamDestroy(m->st);
+    delete m;
+}
+
+int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, const void* xy, int64_t n,
+              const mesh_params* p, void* cuda_stream) {
+    g_err.clear();
+    if (!out) return fail(TRIME_EINVAL, "out is NULL");
+    *out = nullptr;
+    mesh_params P;
+    if (p) P = *p; else mesh_default_params(&P);
+    if (P.precision != 0 && P.precision != 1) return fail(TRIME_EINVAL, "precision must be 0 or 1");
+    if (P.method < 0 || P.method > 2) return fail(TRIME_EINVAL, "method must be 0, 1 or 2");
+    if (P.quad_max_level < 1 || P.quad_max_level > 9) return fail(TRIME_EINVAL, "quad_max_level must be 1..9");
+    if (P.newton_max < 0 || P.trace_max < 1) return fail(TRIME_EINVAL, "bad newton_max / trace_max");
+    if (!(P.N_opt > 0) || !(P.fac_voro_bound > 0) || !(P.dt >= 0)) return fail(TRIME_EINVAL, "bad parameter value");
+    if (n < 0 || n > (int64_t)(1 << 30)) return fail(TRIME_EINVAL, "n out of range");
+    if (n > 0 && !xy) return fail(TRIME_EINVAL, "xy is NULL");
+    if (!grid_ok(sdf)) return fail(TRIME_EINVAL, "invalid SDF grid");
+    if (!grid_ok(sizing)) return fail(TRIME_EINVAL, "invalid sizing grid");
+    for (size_t k = 0; k < (size_t)sizing->nx * sizing->ny; k++)
+        if (!(sizing->v[k] > 0.0f)) return fail(TRIME_EINVAL, "sizing values must be positive");
+    for (int64_t i = 0; i < n; i++) {
+        double x = P.precision == 0 ? ((const double*)xy)[2 * i] : (double)((const float*)xy)[2 * i];
+        double y = P.precision == 0 ? ((const double*)xy)[2 * i + 1] : (double)((const float*)xy)[2 * i + 1];
+        if (!std::isfinite(x) || !std::isfinite(y) || x < sdf->x0 || x > sdf->x1 || y < sdf->y0 || y > sdf->y1)
+            return fail(TRIME_EINVAL, "point " + std::to_string(i) + " is not finite or outside the SDF grid box");
+    }
+    HostGeometry G;
+    int rc = host_geometry(*sdf, *sizing, n, P, G);
+    if (rc) return rc;
+
+    mesh_s* m = new mesh_s();
+    m->prec = P.precision;
+    m->n = n;
+    m->P = P;
+    m->user = (cudaStream_t)cuda_stream;
+    auto bail = [&](int code) {
+        mesh_destroy(m);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(TRIME_ECUDA, "stream/event creation failed"));
+    if (cudaMallocHost(&m->hctrl, sizeof(DevCtrl)) != cudaSuccess) return bail(fail(TRIME_ENOMEM, "pinned alloc"));
+
+    // device parameters
+    DevParams& d = m->dp;
+    d.bounded = P.bounded;
+    d.validity = P.validity;
+    d.newton_max = P.newton_max;
+    d.trace_max = P.trace_max;
+    d.quad_max_level = P.quad_max_level;
+    d.debug = P.debug != 0;
+    d.fac_F = P.fac_F;
+    d.k_spring = P.k_spring;
+    d.dt = P.dt;
+    d.fac_pt = P.fac_pt;
+    d.fac_geps = P.fac_geps;
+    d.fac_voro_bound = P.fac_voro_bound;
+    d.fac_end = P.fac_end;
+    d.T_circ = P.T_circ;
+    d.T_switch = P.T_switch;
+    d.T_end_q = P.T_end_q;
+    d.T_end_amax = P.T_end_amax;
+    d.damping = P.damping;
+    d.havg = G.havg;
+    d.bx0 = sdf->x0;
+    d.by0 = sdf->y0;
+    d.bx1 = sdf->x1;
+    d.by1 = sdf->y1;
+    double W = sdf->x1 - sdf->x0, H = sdf->y1 - sdf->y0;
+    double lam = std::sqrt((double)std::max<int64_t>(n, 1) / (P.N_opt * W * H));
+    d.nbx = std::max(1, (int)std::ceil(lam * W));
+    d.nby = std::max(1, (int)std::ceil(lam * H));
+    d.bsx = W / d.nbx;
+    d.bsy = H / d.nby;
+    int nb = d.nbx * d.nby;
+
+    size_t ns = (size_t)sdf->nx * sdf->ny, nz = (size_t)sizing->nx * sizing->ny;
+    size_t nc = (size_t)(sdf->nx - 1) * (sdf->ny - 1);
+    size_t N = (size_t)n;
+    size_t T = P.precision == 0 ? sizeof(double) : sizeof(float);
+    m->nblk = (int)std::max<size_t>(1, (N + kThreads - 1) / kThreads);
+    rc = 0;
+    float* dsdf = dalloc<float>(m, ns, rc);
+    float* dsiz = dalloc<float>(m, nz, rc);
+    m->gcls = dalloc<uint8_t>(m, nc, rc);
+    m->gh = dalloc<double>(m, nc, rc);
+    m->ggeps = dalloc<double>(m, nc, rc);
+    m->gidist = dalloc<uint8_t>(m, nc, rc);
+    m->cx = dalloc<char>(m, N * T, rc);
+    m->cy = dalloc<char>(m, N * T, rc);
+    m->cdp = dalloc<char>(m, N * T, rc);
+    m->sx = dalloc<char>(m, N * T, rc);
+    m->sy = dalloc<char>(m, N * T, rc);
+    m->sdp = dalloc<char>(m, N * T, rc);
+    m->cid = dalloc<int32_t>(m, N, rc);
+    m->sid = dalloc<int32_t>(m, N, rc);
+    m->ccls = dalloc<uint8_t>(m, N, rc);
+    m->scls = dalloc<uint8_t>(m, N, rc);
+    m->cell = dalloc<int32_t>(m, N, rc);
+    m->key = dalloc<int32_t>(m, N, rc);
+    m->rank = dalloc<int32_t>(m, N, rc);
+    m->skey = dalloc<int32_t>(m, N, rc);
+    m->dom = dalloc<uint8_t>(m, N, rc);
+    m->bcount = dalloc<int32_t>(m, nb, rc);
+    m->bstart = dalloc<int32_t>(m, (size_t)nb + 1, rc);
+    size_t scan_n = std::max<size_t>((size_t)nb + 1, N + 1);
+    m->scan_tmp = dalloc<int32_t>(m, scan_n / 4096 + 2, rc);
+    m->ring = dalloc<int32_t>(m, N * kRingCap, rc);
+    m->ring_n = dalloc<uint8_t>(m, N, rc);
+    m->cellR = dalloc<float>(m, N, rc);
+    m->vmask = dalloc<uint32_t>(m, N, rc);
+    m->ep = dalloc<EmitPartial>(m, (size_t)m->nblk, rc);
+    m->up = dalloc<UpdatePartial>(m, (size_t)m->nblk, rc);
+    m->ctrl = dalloc<DevCtrl>(m, 1, rc);
+    m->dbg = d.debug ? dalloc<double>(m, 10 * N, rc) : nullptr;
+    m->tcnt = dalloc<int32_t>(m, N + 1, rc);
+    m->toff = dalloc<int32_t>(m, N + 1, rc);
+    m->tbuf = dalloc<int32_t>(m, 3 * (2 * N + 16), rc);
+    m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
+    if (rc) return bail(rc);
+
+    m->sdf = {sdf->nx, sdf->ny, sdf->x0, sdf->y0, sdf->x1, sdf->y1, (sdf->x1 - sdf->x0) / (double)(sdf->nx - 1),
+              (sdf->y1 - sdf->y0) / (double)(sdf->ny - 1), dsdf};
+    m->siz = {sizing->nx, sizing->ny, sizing->x0, sizing->y0, sizing->x1, sizing->y1,
+              (sizing->x1 - sizing->x0) / (double)(sizing->nx - 1),
+              (sizing->y1 - sizing->y0) / (double)(sizing->ny - 1), dsiz};
+    auto H2D = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, m->st) == cudaSuccess;
+    };
+    bool ok = H2D(dsdf, sdf->v, ns * sizeof(float)) && H2D(dsiz, sizing->v, nz * sizeof(float)) &&
+              H2D(m->gcls, G.cls.data(), nc) && H2D(m->gh, G.h.data(), nc * sizeof(double)) &&
+              H2D(m->ggeps, G.geps.data(), nc * sizeof(double)) && H2D(m->gidist, G.idist.data(), nc);
+    // state in input order: ids 0..n-1, classes by Sec. 4.3 on the host
+    std::vector<int32_t> ids(N);
+    std::vector<uint8_t> cls(N);
+    std::vector<char> dp(N * T);
+    std::vector<char> xs(N * T), ys(N * T);
+    double sdx = m->sdf.dx, sdy = m->sdf.dy;
+    int ncx = sdf->nx - 1, ncy = sdf->ny - 1;
+    for (size_t i = 0; i < N; i++) {
+        ids[i] = (int32_t)i;
+        double x = P.precision == 0 ? ((const double*)xy)[2 * i] : (double)((const float*)xy)[2 * i];
+        double y = P.precision == 0 ? ((const double*)xy)[2 * i + 1] : (double)((const float*)xy)[2 * i + 1];
+        double fi = std::floor((x - sdf->x0) / sdx), fj = std::floor((y - sdf->y0) / sdy);
+        bool inside = fi >= 0 && fi <= ncx - 1 && fj >= 0 && fj <= ncy - 1;
+        int gi = !(fi >= 0) ? 0 : (fi > ncx - 1 ? ncx - 1 : (int)fi);
+        int gj = !(fj >= 0) ? 0 : (fj > ncy - 1 ? ncy - 1 : (int)fj);
+        size_t c = (size_t)gj * ncx + gi;
+        uint8_t pc = PT_BOUNDARY;
+        if (inside && G.cls[c] == CELL_INNER) pc = PT_INNER;
+        else if (inside && G.cls[c] == CELL_BOUNDARY) {
+            double s = host_bilin(*sdf, sdx, sdy, x, y);
+            if (s < -G.geps[c]) pc = PT_INNER;
+        }
+        cls[i] = pc;  // reading: a point outside at init counts as boundary
+        double h = G.h[c];
+        if (P.precision == 0) {
+            ((double*)xs.data())[i] = x;
+            ((double*)ys.data())[i] = y;
+            ((double*)dp.data())[i] = h;  // reading: eps_c = 1 at the first iteration
+        } else {
+            ((float*)xs.data())[i] = (float)x;
+            ((float*)ys.data())[i] = (float)y;
+            ((float*)dp.data())[i] = (float)h;
+        }
+    }
+    ok = ok && H2D(m->cx, xs.data(), N * T) && H2D(m->cy, ys.data(), N * T) && H2D(m->cdp, dp.data(), N * T) &&
+         H2D(m->cid, ids.data(), N * sizeof(int32_t)) && H2D(m->ccls, cls.data(), N);
+    DevCtrl c0;
+    std::memset(&c0, 0, sizeof c0);
+    c0.method_param = P.method;
+    c0.last_method = -1;
+    ok = ok && H2D(m->ctrl, &c0, sizeof c0);
+    if (!ok || cudaStreamSynchronize(m->st) != cudaSuccess) return bail(fail(TRIME_ECUDA, "initial upload failed"));
+
+    // one iteration as a CUDA graph
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bail(fail(TRIME_ECUDA, "cudaStreamBeginCapture failed"));
+    enqueue(m, true, 0);
+    cudaError_t e = cudaStreamEndCapture(m->st, &graph);
+    if (e != cudaSuccess) return bail(fail(TRIME_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e)));
+    e = cudaGraphInstantiate(&m->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bail(fail(TRIME_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)));
+    *out = m;
+    return TRIME_OK;
+}
+
+int mesh_rebuild(mesh_t* m, mesh_stats* stats) {
+    if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if ((rc = reset_counters(m))) return rc;
+    enqueue(m, false, 1);
+    CUDA_TRY(cudaGetLastError());
+    if ((rc = read_ctrl(m))) return rc;
+    if ((rc = sync_out(m))) return rc;
+    if (stats) fill_stats(m, 0, stats);
+    const DevCounters& c = m->hctrl->cnt;
+    if (c.ring_overflow || c.exact_overflow)
+        return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
+    return TRIME_OK;
+}
+
+int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats) {
+    if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
+    if (n_iters < 0) return fail(TRIME_EINVAL, "n_iters < 0");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if ((rc = reset_counters(m))) return rc;
+    if ((rc = read_ctrl(m))) return rc;
+    int start = m->hctrl->iterations;
+    for (int32_t k = 0; k < n_iters; k++) {
+        CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+        if ((k & 31) == 31 || k == n_iters - 1) {
+            if ((rc = read_ctrl(m))) return rc;
+            if (m->hctrl->terminated) break;
+        }
+    }
+    if (n_iters == 0 && (rc = read_ctrl(m))) return rc;
+    if ((rc = sync_out(m))) return rc;
+    if (stats) fill_stats(m, m->hctrl->iterations - start, stats);
+    const DevCounters& c = m->hctrl->cnt;
+    if (c.ring_overflow || c.exact_overflow)
+        return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
+    return TRIME_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int mesh_get_triangles(mesh_t* m, int32_t* tri, int64_t cap, int64_t* n_out) {
+    if (!m || !n_out) return fail(TRIME_EINVAL, "NULL argument");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    int32_t total = 0;
+    if (m->n > 0) {
+        if (m->prec == 0) launch_tri_count<double>(make_args<double>(m, 1), m->tcnt, m->st);
+        else launch_tri_count<float>(make_args<float>(m, 1), m->tcnt, m->st);
+        launch_scan(m->tcnt, m->toff, (int32_t)m->n, m->scan_tmp, m->st);
+        CUDA_TRY(cudaMemcpyAsync(&total, m->toff + m->n, sizeof(int32_t), cudaMemcpyDeviceToHost, m->st));
+        CUDA_TRY(cudaStreamSynchronize(m->st));
+    }
+    *n_out = total;
+    if (cap < total) return fail(TRIME_ECAPACITY, "triangle buffer too small");
+    if (total == 0) return sync_out(m);
+    if (!tri) return fail(TRIME_EINVAL, "tri is NULL");
+    bool dev = is_device_ptr(tri);
+    int32_t* dst = dev ? tri : m->tbuf;
+    if (!dev && (size_t)total > 2 * (size_t)m->n + 16) return fail(TRIME_EDEVICE, "triangle count exceeds 2n+16");
+    if (m->prec == 0) launch_tri_write<double>(make_args<double>(m, 1), m->toff, dst, m->st);
+    else launch_tri_write<float>(make_args<float>(m, 1), m->toff, dst, m->st);
+    if (!dev) {
+        CUDA_TRY(cudaMemcpyAsync(tri, dst, sizeof(int32_t) * 3 * (size_t)total, cudaMemcpyDeviceToHost, m->st));
+        CUDA_TRY(cudaStreamSynchronize(m->st));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return sync_out(m);
+}
+
+int mesh_get_points(mesh_t* m, void* xy, int64_t cap, int64_t* n_out) {
+    if (!m || !n_out) return fail(TRIME_EINVAL, "NULL argument");
+    *n_out = m->n;
+    if (cap < m->n) return fail(TRIME_ECAPACITY, "point buffer too small");
+    if (m->n == 0) return TRIME_OK;
+    if (!xy) return fail(TRIME_EINVAL, "xy is NULL");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    size_t T = m->prec == 0 ? sizeof(double) : sizeof(float);
+    bool dev = is_device_ptr(xy);
+    void* dst = dev ? xy : m->xybuf;
+    if (m->prec == 0) launch_unpermute<double>(make_args<double>(m, 1), (double*)dst, m->st);
+    else launch_unpermute<float>(make_args<float>(m, 1), (float*)dst, m->st);
+    if (!dev) {
+        CUDA_TRY(cudaMemcpyAsync(xy, dst, 2 * T * (size_t)m->n, cudaMemcpyDeviceToHost, m->st));
+        CUDA_TRY(cudaStreamSynchronize(m->st));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return sync_out(m);
+}
+
+int mesh_set_state(mesh_t* m, const void* xy, const uint8_t* cls, const double* dprev) {
+    if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
+    if (m->n == 0) return TRIME_OK;
+    size_t N = (size_t)m->n, T = m->prec == 0 ? sizeof(double) : sizeof(float);
+    if (xy)
+        for (size_t i = 0; i < 2 * N; i++) {
+            double v = m->prec == 0 ? ((const double*)xy)[i] : (double)((const float*)xy)[i];
+            double lo = (i & 1) ? m->dp.by0 : m->dp.bx0, hi = (i & 1) ? m->dp.by1 : m->dp.bx1;
+            if (!std::isfinite(v) || v < lo || v > hi) return fail(TRIME_EINVAL, "point outside the SDF grid box");
+        }
+    int rc = sync_in(m);
+    if (rc) return rc;
+    // staging: xy in xybuf, cls in tcnt, dprev in tbuf (all large enough)
+    char* sxy = (char*)m->xybuf;
+    uint8_t* scls = (uint8_t*)m->tcnt;
+    double* sdp = (double*)m->tbuf;
+    if (xy) CUDA_TRY(cudaMemcpyAsync(sxy, xy, 2 * N * T, cudaMemcpyHostToDevice, m->st));
+    if (cls) CUDA_TRY(cudaMemcpyAsync(scls, cls, N, cudaMemcpyHostToDevice, m->st));
+    if (dprev) CUDA_TRY(cudaMemcpyAsync(sdp, dprev, N * sizeof(double), cudaMemcpyHostToDevice, m->st));
+    if (m->prec == 0)
+        launch_set_state<double>(make_args<double>(m, 1), xy ? (const double*)sxy : nullptr, cls ? scls : nullptr,
+                                 dprev ? sdp : nullptr, m->st);
+    else
+        launch_set_state<float>(make_args<float>(m, 1), xy ? (const float*)sxy : nullptr, cls ? scls : nullptr,
+                                dprev ? sdp : nullptr, m->st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
+int mesh_set_method_state(mesh_t* m, int32_t switched, double pa, double pb, double pm) {
+    if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if ((rc = read_ctrl(m))) return rc;
+    DevCtrl c = *m->hctrl;
+    c.switched = switched;
+    c.have_prev = pa > 0;
+    c.prev_a = pa;
+    c.prev_b = pb;
+    c.prev_amax = pm;
+    c.terminated = 0;
+    c.small_moves = 0;
+    *m->hctrl = c;
+    CUDA_TRY(cudaMemcpyAsync(m->ctrl, m->hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
+int mesh_get_debug(mesh_t* m, int32_t what, double* out, int64_t cap) {
+    if (!m || !out) return fail(TRIME_EINVAL, "NULL argument");
+    if (!m->dbg) return fail(TRIME_EINVAL, "debug recording is off (mesh_params.debug = 1 enables it)");
+    static const int off[7] = {0, 2, 4, 6, 7, 8, 9};
+    static const int width[7] = {2, 2, 2, 1, 1, 1, 1};
+    if (what < 0 || what > 6) return fail(TRIME_EINVAL, "what must be 0..6");
+    size_t cnt = (size_t)width[what] * (size_t)m->n;
+    if ((size_t)cap < cnt) return fail(TRIME_ECAPACITY, "debug buffer too small");
+    if (cnt == 0) return TRIME_OK;
+    int rc = sync_in(m);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(out, m->dbg + (size_t)off[what] * m->n, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                             m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
+int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, double y0, double x1, double y1,
+                       int32_t nbx, int32_t nby, int32_t* bucket_start, int32_t* sorted_idx, int32_t* scratch,
+                       void* cuda_stream) {
+    if (n < 0 || n > (int64_t)(1 << 30)) return fail(TRIME_EINVAL, "n out of range");
+    if (nbx < 1 || nby < 1 || (int64_t)nbx * nby > (int64_t)4096 * 1024) return fail(TRIME_EINVAL, "bad bucket grid");
+    if (!(x1 > x0) || !(y1 > y0)) return fail(TRIME_EINVAL, "empty box");
+    if (!bucket_start || !scratch || (n > 0 && (!x || !y || !sorted_idx))) return fail(TRIME_EINVAL, "NULL pointer");
+    launch_bucket_raw(x, y, (int32_t)n, x0, y0, (x1 - x0) / nbx, (y1 - y0) / nby, nbx, nby, bucket_start, sorted_idx,
+                      scratch, (cudaStream_t)cuda_stream);
+    CUDA_TRY(cudaGetLastError());
+    return TRIME_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,509 @@
+// update.cu -- a5/a6/a7 and the a8 finalisation (TriMe++ Sec. 2.2-2.4, 4.2-4.3).
+//
+// One thread per cell computes the raw new position -- DistMesh: forward
+// Euler with the spring forces of its valid edges (Eqs. 2-5), gathered from
+// its own ring so no atomics are needed; CVD: the density-weighted centroid
+// of its bounded cell by adaptive longest-edge-bisection quadrature (Eq. 6,
+// Sec. 4.2) -- then clamps the move, classifies the point on the geometry
+// grid and projects it back by sphere tracing or damped Newton (Sec. 4.3).
+// The statistics kernels finalise the quality 1/2-means (Eq. 12), fac_mu
+// (Eq. 3), the hybrid switch (Sec. 4.2) and the termination tests (Sec. 4).
+#include "kernels.cuh"
+
+namespace trime {
+
+constexpr int kPolyCap = 48;
+
+// ------------------------------------------------------------------ point treatment
+template <typename T>
+__device__ __forceinline__ T geps_at(const IterArgs<T>& a, T x, T y) {
+    int gi, gj;
+    point_cell_t<T>(a.sdf, x, y, gi, gj);
+    return (T)a.ggeps[gj * (a.sdf.nx - 1) + gi];
+}
+
+template <typename T>
+__device__ int classify(const IterArgs<T>& a, T x, T y) {
+    int gi, gj;
+    if (!point_cell_t<T>(a.sdf, x, y, gi, gj)) return PT_OUTSIDE;
+    int c = gj * (a.sdf.nx - 1) + gi;
+    uint8_t k = a.gcls[c];
+    if (k == CELL_OUTER) return PT_OUTSIDE;
+    if (k == CELL_INNER) return PT_INNER;
+    T s = bilin<T>(a.sdf, x, y), g = (T)a.ggeps[c];
+    if (fabs(s) <= g) return PT_BOUNDARY;
+    if (s < -g) return PT_INNER;
+    return PT_OUTSIDE;
+}
+
+// sphere tracing from an inner p_old toward an outside p_new (Fig. 21a)
+template <typename T>
+__device__ bool sphere_trace(const IterArgs<T>& a, T ax, T ay, T bx, T by, T& ox, T& oy) {
+    T Lx = bx - ax, Ly = by - ay;
+    T L = sqrt(Lx * Lx + Ly * Ly);
+    T ux = Lx / L, uy = Ly / L;
+    T x = ax, y = ay, lox = ax, loy = ay, hix = bx, hiy = by, t = 0;
+    int it = 0;
+    bool bisect = false;
+    for (; it < a.P.trace_max; it++) {
+        T s = bilin<T>(a.sdf, x, y), g = geps_at(a, x, y);
+        if (fabs(s) <= g) { ox = x; oy = y; return false; }
+        if (s > g) { hix = x; hiy = y; bisect = true; break; }
+        lox = x; loy = y;
+        t += fabs(s);
+        if (t >= L) { bisect = true; break; }
+        x = ax + t * ux;
+        y = ay + t * uy;
+    }
+    if (bisect)
+        for (it++; it < a.P.trace_max; it++) {
+            T mx = (lox + hix) * (T)0.5, my = (loy + hiy) * (T)0.5;
+            T s = bilin<T>(a.sdf, mx, my), g = geps_at(a, mx, my);
+            if (fabs(s) <= g) { ox = mx; oy = my; return false; }
+            if (s < 0) { lox = mx; loy = my; } else { hix = mx; hiy = my; }
+        }
+    ox = lox;
+    oy = loy;
+    return true;
+}
+
+// damped Newton projection (Eqs. 8-10), gradient at the iterate, exact
+// derivatives of the bilinear interpolant
+template <typename T>
+__device__ void newton_project(const IterArgs<T>& a, T pnx, T pny, T& ox, T& oy) {
+    T x = pnx, y = pny;
+    for (int k = 0; k < a.P.newton_max; k++) {
+        T f, fx, fy, fxy;
+        bilin_grad<T>(a.sdf, x, y, f, fx, fy, fxy);
+        T L1 = f;
+        T L2 = (x - pnx) * fy - (y - pny) * fx;
+        T J00 = fx, J01 = fy;
+        T J10 = fy + (x - pnx) * fxy, J11 = -fx - (y - pny) * fxy;
+        T det = J00 * J11 - J01 * J10;
+        if (det == (T)0 || !isfinite(det)) break;
+        T dx = (J11 * L1 - J01 * L2) / det;
+        T dy = (-J10 * L1 + J00 * L2) / det;
+        x -= (T)a.P.damping * dx;
+        y -= (T)a.P.damping * dy;
+        if (fabs(bilin<T>(a.sdf, x, y)) <= geps_at(a, x, y)) break;
+    }
+    ox = x;
+    oy = y;
+}
+
+// ------------------------------------------------------------------ CVD centroid
+template <typename T>
+struct Poly {
+    T nx[kPolyCap], ny[kPolyCap], s[kPolyCap];
+    int m;
+};
+
+template <typename T>
+__device__ __forceinline__ void isect(const Poly<T>& P, int a, int b, T& ux, T& uy) {
+    T D = P.nx[a] * P.ny[b] - P.ny[a] * P.nx[b];
+    ux = (P.s[a] * P.ny[b] - P.s[b] * P.ny[a]) / D;
+    uy = (P.s[b] * P.nx[a] - P.s[a] * P.nx[b]) / D;
+}
+
+// clip by n.u <= s keeping one run (Sutherland-Hodgman on labelled edges)
+template <typename T>
+__device__ void clip_poly(Poly<T>& P, T nx, T ny, T s) {
+    int m = P.m;
+    if (m == 0) return;
+    unsigned long long cut = 0;
+    for (int t = 0; t < m; t++) {
+        T ux, uy;
+        isect(P, t, t + 1 == m ? 0 : t + 1, ux, uy);
+        if (nx * ux + ny * uy > s) cut |= 1ull << t;
+    }
+    if (!cut) return;
+    unsigned long long full = m >= 64 ? ~0ull : ((1ull << m) - 1);
+    if ((cut & full) == full) { P.m = 0; return; }
+    int st = -1;
+    for (int t = 0; t < m && st < 0; t++)
+        if (((cut >> t) & 1) && !((cut >> (t == 0 ? m - 1 : t - 1)) & 1)) st = t;
+    int e = st;
+    while ((cut >> e) & 1) e = e + 1 == m ? 0 : e + 1;
+    T tnx[kPolyCap], tny[kPolyCap], ts[kPolyCap];
+    int k = 0;
+    for (int t = e;; t = t + 1 == m ? 0 : t + 1) {
+        tnx[k] = P.nx[t]; tny[k] = P.ny[t]; ts[k] = P.s[t];
+        k++;
+        if (t == st) break;
+    }
+    if (k + 1 > kPolyCap) { P.m = 0; return; }
+    tnx[k] = nx; tny[k] = ny; ts[k] = s;
+    k++;
+    for (int t = 0; t < k; t++) { P.nx[t] = tnx[t]; P.ny[t] = tny[t]; P.s[t] = ts[t]; }
+    P.m = k;
+}
+
+// one-point rule on the leaves of the longest-edge bisection tree of given
+// depth under the triangle (0, v1, v2) (relative to the generator)
+template <typename T>
+__device__ void level_sum(const IterArgs<T>& a, T gx, T gy, T v1x, T v1y, T v2x, T v2y, int depth, T& W, T& WX,
+                          T& WY) {
+    T st[9][6];
+    int sd[9];
+    int sp = 0;
+    st[0][0] = 0; st[0][1] = 0; st[0][2] = v1x; st[0][3] = v1y; st[0][4] = v2x; st[0][5] = v2y;
+    sd[0] = depth;
+    sp = 1;
+    while (sp > 0) {
+        sp--;
+        T q0x = st[sp][0], q0y = st[sp][1], q1x = st[sp][2], q1y = st[sp][3], q2x = st[sp][4], q2y = st[sp][5];
+        int d = sd[sp];
+        if (d == 0) {
+            T A = (T)0.5 * ((q1x - q0x) * (q2y - q0y) - (q1y - q0y) * (q2x - q0x));
+            T cx = (q0x + q1x + q2x) / (T)3, cy = (q0y + q1y + q2y) / (T)3;
+            T mu = bilin<T>(a.siz, gx + cx, gy + cy);
+            T w = A / (mu * mu);
+            W += w;
+            WX += w * cx;
+            WY += w * cy;
+            continue;
+        }
+        T L01 = (q1x - q0x) * (q1x - q0x) + (q1y - q0y) * (q1y - q0y);
+        T L12 = (q2x - q1x) * (q2x - q1x) + (q2y - q1y) * (q2y - q1y);
+        T L20 = (q0x - q2x) * (q0x - q2x) + (q0y - q2y) * (q0y - q2y);
+        T ax = q0x, ay = q0y, bx = q1x, by = q1y, cx = q2x, cy = q2y, Lm = L01;
+        if (L12 > Lm) { ax = q1x; ay = q1y; bx = q2x; by = q2y; cx = q0x; cy = q0y; Lm = L12; }
+        if (L20 > Lm) { ax = q2x; ay = q2y; bx = q0x; by = q0y; cx = q1x; cy = q1y; }
+        T mx = (ax + bx) * (T)0.5, my = (ay + by) * (T)0.5;
+        // children (a, m, c) and (m, b, c); push the second first
+        st[sp][0] = mx; st[sp][1] = my; st[sp][2] = bx; st[sp][3] = by; st[sp][4] = cx; st[sp][5] = cy;
+        sd[sp] = d - 1;
+        sp++;
+        st[sp][0] = ax; st[sp][1] = ay; st[sp][2] = mx; st[sp][3] = my; st[sp][4] = cx; st[sp][5] = cy;
+        sd[sp] = d - 1;
+        sp++;
+    }
+}
+
+template <typename T>
+__device__ void cvd_centroid(const IterArgs<T>& a, int s, int ne, const int* lab, T xi, T yi, T h, T dprev, T& cx,
+                             T& cy, int& level, bool& capped) {
+    const DevParams& P = a.P;
+    cx = xi;
+    cy = yi;
+    level = 0;
+    capped = false;
+    if (ne < 3) return;
+    Poly<T> poly;
+    T W_ = (T)(P.bx1 - P.bx0), H_ = (T)(P.by1 - P.by0);
+    T S = (T)P.fac_voro_bound * h;
+    T SB = S * (T)(17.0 / 16.0);
+    T mb = P.bounded ? S * (T)(1.0 / 16.0) : (T)0.125 * (W_ > H_ ? W_ : H_);
+    T bl = xi - ((T)P.bx0 - mb), br = ((T)P.bx1 + mb) - xi, bb = yi - ((T)P.by0 - mb), bt = ((T)P.by1 + mb) - yi;
+    for (int t = 0; t < ne; t++) {
+        int l = lab[t];
+        if (l >= 0) {
+            T dx = a.srt.x[l] - xi, dy = a.srt.y[l] - yi;
+            poly.nx[t] = dx; poly.ny[t] = dy; poly.s[t] = (T)0.5 * (dx * dx + dy * dy);
+        } else if (l >= -8) {
+            int k = -1 - l;
+            const T c8[8] = {(T)1, (T)kRT, (T)0, -(T)kRT, (T)-1, -(T)kRT, (T)0, (T)kRT};
+            poly.nx[t] = c8[k]; poly.ny[t] = c8[(k + 6) & 7]; poly.s[t] = SB;
+        } else {
+            int b = -9 - l;
+            poly.nx[t] = b == 0 ? (T)-1 : (b == 1 ? (T)1 : (T)0);
+            poly.ny[t] = b == 2 ? (T)-1 : (b == 3 ? (T)1 : (T)0);
+            poly.s[t] = b == 0 ? bl : (b == 1 ? br : (b == 2 ? bb : bt));
+        }
+    }
+    poly.m = ne;
+    T R = (T)a.cellR[s];
+    T dl = xi - (T)P.bx0, dr = (T)P.bx1 - xi, db = yi - (T)P.by0, dt_ = (T)P.by1 - yi;
+    T dbox = fmin(fmin(dl, dr), fmin(db, dt_));
+    bool inside = R * (T)1.0001 < dbox && (!P.bounded || R * (T)1.0001 < S);
+    if (!inside) {
+        if (P.bounded) {
+            const T c8[8] = {(T)1, (T)kRT, (T)0, -(T)kRT, (T)-1, -(T)kRT, (T)0, (T)kRT};
+            for (int k = 0; k < 8; k++) clip_poly(poly, c8[k], c8[(k + 6) & 7], S);
+        }
+        clip_poly(poly, (T)-1, (T)0, dl);
+        clip_poly(poly, (T)1, (T)0, dr);
+        clip_poly(poly, (T)0, (T)-1, db);
+        clip_poly(poly, (T)0, (T)1, dt_);
+    }
+    int m = poly.m;
+    if (m < 3) return;
+    T vx[kPolyCap], vy[kPolyCap];
+    T A = 0;
+    for (int t = 0; t < m; t++) isect(poly, t, t + 1 == m ? 0 : t + 1, vx[t], vy[t]);
+    for (int t = 0; t < m; t++) {
+        int u = t + 1 == m ? 0 : t + 1;
+        A += (T)0.5 * (vx[t] * vy[u] - vy[t] * vx[u]);
+    }
+    if (!(A > 0)) return;
+    T E = sqrt(A) * fmax(dprev / h, (T)P.fac_end);
+    T px = 0, py = 0;
+    int Lmax = P.quad_max_level;
+    for (int k = 1; k <= Lmax; k++) {
+        T W = 0, WX = 0, WY = 0;
+        for (int t = 0; t < m; t++) {
+            int u = t + 1 == m ? 0 : t + 1;
+            level_sum<T>(a, xi, yi, vx[t], vy[t], vx[u], vy[u], k - 1, W, WX, WY);
+        }
+        if (!(W > 0)) return;
+        T ccx = WX / W, ccy = WY / W;
+        T dx = ccx - px, dy = ccy - py;
+        bool conv = sqrt(dx * dx + dy * dy) < E;
+        if (conv || k == Lmax) {
+            cx = xi + ccx;
+            cy = yi + ccy;
+            level = k;
+            capped = !conv;
+            return;
+        }
+        px = ccx;
+        py = ccy;
+    }
+}
+
+// ------------------------------------------------------------------ update
+__device__ __forceinline__ double blk_sum(double v, double* sh) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
+    return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
+    if (a.ctrl->terminated) return;
+    const DevParams& P = a.P;
+    int method = a.ctrl->method_now;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double dev = 0, nedge = 0, notsmall = 0;
+    unsigned long long nfail = 0, tcap = 0, qcap = 0;
+    if (s < a.n) {
+        T xi = a.srt.x[s], yi = a.srt.y[s];
+        int idi = a.srt.id[s];
+        int ocls = a.srt.cls[s];
+        T dprev = a.srt.dprev[s];
+        T h = (T)a.gh[a.cell[s]];
+        int ne = a.ring_n[s];
+        uint32_t vm = a.vmask[s];
+        int lab[kRingCap];
+        const int4* row = reinterpret_cast<const int4*>(a.ring + (size_t)s * kRingCap);
+        for (int q = 0; q < (ne + 3) / 4; q++) {
+            int4 v = row[q];
+            lab[4 * q] = v.x;
+            lab[4 * q + 1] = v.y;
+            lab[4 * q + 2] = v.z;
+            lab[4 * q + 3] = v.w;
+        }
+        T fac_mu = (T)a.ctrl->fac_mu;
+        T Fx = 0, Fy = 0, fs = 0;
+        // DistMesh forces on the valid edges (Eqs. 2-3); also the size deviation
+        for (int t = 0; t < ne; t++) {
+            int j = lab[t];
+            if (j < 0) continue;
+            int tp = t == 0 ? ne - 1 : t - 1;
+            if (!((vm >> t) & 1u) && !((vm >> tp) & 1u)) continue;
+            T xj = a.srt.x[j], yj = a.srt.y[j];
+            T dx = xi - xj, dy = yi - yj;
+            T l = sqrt(dx * dx + dy * dy);
+            T mu = bilin<T>(a.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
+            if (idi < a.srt.id[j]) {
+                dev += (double)fabs(l / (fac_mu * mu) - (T)1);
+                nedge += 1.0;
+            }
+            if (method != 0) continue;
+            T l0 = (T)P.fac_F * fac_mu * mu;
+            if (l < l0) {
+                T f = (T)P.k_spring * (l0 - l);
+                Fx += f * dx / l;
+                Fy += f * dy / l;
+                fs += f;
+            }
+        }
+        T pnx, pny, cx = xi, cy = yi;
+        int qlv = 0;
+        if (method == 0) {
+            pnx = xi + (T)P.dt * Fx;  // forward Euler (Eq. 5)
+            pny = yi + (T)P.dt * Fy;
+        } else {
+            bool capped;
+            cvd_centroid<T>(a, s, ne, lab, xi, yi, h, dprev, cx, cy, qlv, capped);
+            if (capped) qcap++;
+            pnx = cx;
+            pny = cy;
+        }
+        // Sec. 4.3: clamp, classify, project
+        T dx = pnx - xi, dy = pny - yi;
+        T d = sqrt(dx * dx + dy * dy);
+        T Tm = (T)P.fac_pt * h;
+        T qx = pnx, qy = pny;
+        if (d > Tm) {
+            qx = xi + dx * (Tm / d);
+            qy = yi + dy * (Tm / d);
+        }
+        int c = classify(a, qx, qy);
+        T fx = qx, fy = qy;
+        int ncls = c;
+        if (c == PT_OUTSIDE) {
+            T ox, oy;
+            if (ocls == PT_INNER) {
+                if (sphere_trace(a, xi, yi, qx, qy, ox, oy)) tcap++;
+                int cc = classify(a, ox, oy);
+                if (cc == PT_OUTSIDE) { fx = xi; fy = yi; ncls = ocls; }
+                else { fx = ox; fy = oy; ncls = cc; }
+            } else {
+                newton_project(a, qx, qy, ox, oy);
+                if (classify(a, ox, oy) == PT_BOUNDARY) { fx = ox; fy = oy; ncls = PT_BOUNDARY; }
+                else { nfail++; fx = xi; fy = yi; ncls = ocls; }
+            }
+        }
+        T mvx = fx - xi, mvy = fy - yi;
+        T mv = sqrt(mvx * mvx + mvy * mvy);
+        if (ocls == PT_INNER && !(mv < (T)P.fac_end * h)) notsmall = 1.0;
+        a.cur.x[s] = fx;
+        a.cur.y[s] = fy;
+        a.cur.id[s] = idi;
+        a.cur.cls[s] = (uint8_t)ncls;
+        a.cur.dprev[s] = mv;
+        if (P.debug) {
+            size_t n = (size_t)a.n, id = (size_t)idi;
+            a.dbg[2 * id] = (double)pnx;
+            a.dbg[2 * id + 1] = (double)pny;
+            a.dbg[2 * n + 2 * id] = (double)Fx;
+            a.dbg[2 * n + 2 * id + 1] = (double)Fy;
+            a.dbg[4 * n + 2 * id] = (double)cx;
+            a.dbg[4 * n + 2 * id + 1] = (double)cy;
+            a.dbg[6 * n + id] = (double)fs;
+            a.dbg[7 * n + id] = (double)ncls;
+            a.dbg[8 * n + id] = (double)mv;
+            a.dbg[9 * n + id] = (double)qlv;
+        }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, nfail != 0);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctrl->cnt.newton_fail, (unsigned long long)__popc(m));
+    m = __ballot_sync(0xffffffffu, tcap != 0);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctrl->cnt.trace_cap, (unsigned long long)__popc(m));
+    m = __ballot_sync(0xffffffffu, qcap != 0);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctrl->cnt.quad_cap, (unsigned long long)__popc(m));
+    __shared__ double sh[kThreads / 32];
+    double v0 = blk_sum(dev, sh);
+    double v1 = blk_sum(nedge, sh);
+    double v2 = blk_sum(notsmall, sh);
+    if (threadIdx.x == 0) {
+        a.up[blockIdx.x].size_dev = v0;
+        a.up[blockIdx.x].n_edge = v1;
+        a.up[blockIdx.x].not_small = v2;
+    }
+}
+
+template <typename T>
+void launch_update(const IterArgs<T>& a, int nblocks, cudaStream_t st) {
+    k_update<T><<<nblocks, kThreads, 0, st>>>(a);
+}
+template void launch_update<double>(const IterArgs<double>&, int, cudaStream_t);
+template void launch_update<float>(const IterArgs<float>&, int, cudaStream_t);
+
+// ------------------------------------------------------------------ statistics
+constexpr int kStatThreads = 512;
+
+__global__ void __launch_bounds__(kStatThreads) k_stats_pre(DevCtrl* ctrl, const EmitPartial* ep, int np, int decide,
+                                                            int force, DevParams P) {
+    if (!force && ctrl->terminated) return;
+    double acc[9] = {0, 0, 0, 0, 0, 180.0, 0, 0, 0};
+    for (int b = threadIdx.x; b < np; b += blockDim.x) {
+        const double* p = reinterpret_cast<const double*>(&ep[b]);
+        for (int q = 0; q < 9; q++)
+            acc[q] = (q == 3 || q == 4) ? fmax(acc[q], p[q]) : (q == 5 ? fmin(acc[q], p[q]) : acc[q] + p[q]);
+    }
+    __shared__ double sh[kStatThreads][9];
+    for (int q = 0; q < 9; q++) sh[threadIdx.x][q] = acc[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 9; q++) {
+                double o = sh[threadIdx.x + w][q];
+                sh[threadIdx.x][q] = (q == 3 || q == 4) ? fmax(sh[threadIdx.x][q], o)
+                                   : (q == 5 ? fmin(sh[threadIdx.x][q], o) : sh[threadIdx.x][q] + o);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double n = sh[0][0];
+    double qa = n > 0 ? (sh[0][1] / n) * (sh[0][1] / n) : 0.0;
+    double qb = n > 0 ? (sh[0][2] / n) * (sh[0][2] / n) : 0.0;
+    double qm = sh[0][3];
+    ctrl->n_tri = n;
+    ctrl->half_a = qa;
+    ctrl->half_b = qb;
+    ctrl->max_a = qm;
+    ctrl->max_b = sh[0][4];
+    ctrl->min_ang = n > 0 ? sh[0][5] : 0.0;
+    ctrl->n_edges = sh[0][6];
+    ctrl->fac_mu = sh[0][6] > 0 ? sqrt(sh[0][7] / sh[0][8]) : 1.0;
+    if (!decide) return;
+    double ra = 1, rb = 1, rm = 1;
+    if (ctrl->have_prev) {
+        ra = ctrl->prev_a > 0 ? fabs(qa - ctrl->prev_a) / ctrl->prev_a : 1.0;
+        rb = ctrl->prev_b > 0 ? fabs(qb - ctrl->prev_b) / ctrl->prev_b : 1.0;
+        rm = ctrl->prev_amax > 0 ? fabs(qm - ctrl->prev_amax) / ctrl->prev_amax : 1.0;
+    }
+    bool qend = ctrl->have_prev && ra < P.T_end_q && rb < P.T_end_q && rm < P.T_end_amax;
+    int method, term = 0;
+    if (ctrl->method_param == 2) {
+        if (!ctrl->switched) {
+            if (ctrl->have_prev && ra < P.T_switch) ctrl->switched = 1;  // Sec. 4.2
+        } else if (qend) {
+            term = 1;
+        }
+        method = ctrl->switched ? 1 : 0;
+    } else {
+        method = ctrl->method_param;
+        term = qend;
+    }
+    ctrl->prev_a = qa;
+    ctrl->prev_b = qb;
+    ctrl->prev_amax = qm;
+    ctrl->have_prev = 1;
+    ctrl->method_now = method;
+    ctrl->iterations += 1;
+    if (term) ctrl->terminated = 1;
+    else ctrl->last_method = method;
+}
+
+__global__ void __launch_bounds__(kStatThreads) k_stats_post(DevCtrl* ctrl, const UpdatePartial* up, int np) {
+    if (ctrl->terminated) return;
+    double acc[3] = {0, 0, 0};
+    for (int b = threadIdx.x; b < np; b += blockDim.x) {
+        acc[0] += up[b].size_dev;
+        acc[1] += up[b].n_edge;
+        acc[2] += up[b].not_small;
+    }
+    __shared__ double sh[kStatThreads][3];
+    for (int q = 0; q < 3; q++) sh[threadIdx.x][q] = acc[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 3; q++) sh[threadIdx.x][q] += sh[threadIdx.x + w][q];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    ctrl->size_dev = sh[0][1] > 0 ? sh[0][0] / sh[0][1] : 0.0;
+    int small = sh[0][2] == 0.0;
+    ctrl->small_moves = small;
+    if (small) ctrl->terminated = 1;  // Sec. 4: every inner move below fac_end * h_i
+}
+
+void launch_stats_pre(DevCtrl* ctrl, const EmitPartial* ep, int nparts, int decide, int force, DevParams P,
+                      cudaStream_t st) {
+    k_stats_pre<<<1, kStatThreads, 0, st>>>(ctrl, ep, nparts, decide, force, P);
+}
+void launch_stats_post(DevCtrl* ctrl, const UpdatePartial* up, int nparts, cudaStream_t st) {
+    k_stats_post<<<1, kStatThreads, 0, st>>>(ctrl, up, nparts);
+}
+
+}  // namespace trime

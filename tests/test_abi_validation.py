@@ -1,0 +1,46 @@
+"""Argument validation of the C ABI happens on the host before any CUDA call,
+so these run without a GPU: bad inputs return TRIME_EINVAL with a message."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2309_13824_gb300 as g
+
+    g.build()
+    return g
+
+
+def _init(g, sdf, siz, pts, **kw):
+    p = g.mesh_default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    gs, a = g._grid(sdf)
+    gz, b = g._grid(siz)
+    h = C.c_void_p()
+    xy = np.ascontiguousarray(pts, dtype=np.float64)
+    return g.lib().mesh_init(C.byref(h), C.byref(gs), C.byref(gz), xy.ctypes.data_as(C.c_void_p), len(xy),
+                             C.byref(p), None)
+
+
+def test_invalid_arguments(g):
+    sdf = W.grid_from_fn(W.disk_sdf_fn, 32)
+    siz = W.constant_grid(1.0)
+    ok = np.array([[0.0, 0.0], [0.1, 0.0]])
+    assert _init(g, sdf, siz, np.array([[np.nan, 0.0]])) == g.TRIME_EINVAL
+    assert "not finite" in g.mesh_last_error()
+    assert _init(g, sdf, siz, np.array([[5.0, 0.0]])) == g.TRIME_EINVAL
+    assert _init(g, sdf, W.constant_grid(-1.0), ok) == g.TRIME_EINVAL
+    assert _init(g, sdf, siz, ok, method=7) == g.TRIME_EINVAL
+    assert _init(g, sdf, siz, ok, precision=3) == g.TRIME_EINVAL
+    bad = W.Grid(np.zeros((1, 5), dtype=np.float32), -1, -1, 1, 1)
+    assert _init(g, bad, siz, ok) == g.TRIME_EINVAL
+    outside = W.grid_from_fn(lambda x, y: np.ones_like(x), 16)  # no inner cell anywhere
+    assert _init(g, outside, siz, ok) == g.TRIME_EINVAL
+    assert g.lib().mesh_step(None, 1, None) == g.TRIME_EINVAL
+    assert g.lib().mesh_bucket_points(None, None, 10, 0, 0, 1, 1, 0, 4, None, None, None, None) == g.TRIME_EINVAL

@@ -1,0 +1,241 @@
+"""GPU path vs the CPU oracle through the C ABI, on seeded synthetic inputs.
+
+Triangle sets must be identical (the emission and validity decisions are
+fixed FP64 formulas and the predicates are exact).  Forces, centroids and
+positions of one iteration from identical states must agree within 1e-12
+(FP64 mode) or 2e-6 (FP32 mode) of their natural scale: positions by h_i
+(FP64) or the coordinate magnitude (FP32), forces by the sum of spring
+magnitudes at the point, centroids by sqrt(cell area) (FP64) or the
+coordinate magnitude (FP32).  Threshold branches (clamp, classification,
+projection) may flip only in FP32 mode; flips are counted and bounded.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import TOL_FP32, TOL_FP64, annulus_small, disk_small, h_of_points, make_pair, sorted_tris
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import oracle
+    import paper_2309_13824_gb300 as g
+
+    g.build()
+    oracle.build()
+
+
+def _tri_equal(gm, om):
+    st = gm.rebuild()
+    om.rebuild()
+    tg, to = sorted_tris(gm.triangles()), sorted_tris(om.triangles())
+    assert st["ring_overflow"] == 0 and st["exact_overflow"] == 0
+    assert len(tg) == len(to), (len(tg), len(to))
+    assert np.array_equal(tg, to)
+    return st, tg
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_triangles_disk(precision):
+    gm, om = make_pair(disk_small(), precision=precision)
+    st, tg = _tri_equal(gm, om)
+    assert st["n_tri"] == len(tg)
+    assert st["clip_inconsistent"] == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_triangles_annulus(precision):
+    gm, om = make_pair(annulus_small(), precision=precision, method=1)
+    _tri_equal(gm, om)
+
+
+def test_triangles_unbounded_and_no_validity():
+    sdf = W.grid_from_fn(lambda x, y: W.disk_sdf_fn(x, y, r=1.0), 64)
+    rng = np.random.default_rng(5)
+    pts = rng.uniform(-1.05, 1.05, (3001, 2))
+    gm, om = make_pair((sdf, W.constant_grid(1.0), pts), bounded=0, validity=0)
+    _tri_equal(gm, om)
+
+
+def test_triangles_degenerate_lattice():
+    # every lattice square is cocircular: ties broken by symbolic perturbation
+    sdf = W.grid_from_fn(lambda x, y: W.disk_sdf_fn(x, y, r=1.0), 128)
+    pts = W.lattice_points("square", 40, 2.0 ** -6)
+    gm, om = make_pair((sdf, W.constant_grid(1.0), pts), bounded=0)
+    st, tg = _tri_equal(gm, om)
+    assert st["exact_calls"] > 0
+    assert len(tg) == 2 * 39 * 39
+
+
+def test_tiny_and_empty_inputs():
+    sdf = W.grid_from_fn(lambda x, y: W.disk_sdf_fn(x, y, r=1.0), 64)
+    siz = W.constant_grid(1.0)
+    for n in (0, 1, 2, 3, 5, 33):
+        pts = W.uniform_in(W.disk_sdf_fn, n, 3) if n else np.zeros((0, 2))
+        gm, om = make_pair((sdf, siz, pts))
+        _tri_equal(gm, om)
+        gm.step(2)
+
+
+def test_duplicate_points():
+    sdf = W.grid_from_fn(lambda x, y: W.disk_sdf_fn(x, y, r=1.0), 64)
+    pts = W.uniform_in(W.disk_sdf_fn, 500, 8)
+    pts[10] = pts[20]
+    pts[30] = pts[31] = pts[32]
+    gm, om = make_pair((sdf, W.constant_grid(1.0), pts))
+    st, tg = _tri_equal(gm, om)
+    assert st["dup_points"] == 3
+
+
+def _compare_step(gm, om, precision, method):
+    gm.step(1)
+    om.step()
+    p0 = None
+    tol = TOL_FP64 if precision == 0 else TOL_FP32
+    if method == 0:
+        Fg, Fo = gm.debug(1), om.force()
+        fs = om.fsum()
+        err = np.linalg.norm(Fg - Fo, axis=1)
+        scale = np.where(fs > 0, fs, 1.0)
+        assert np.all(err[fs == 0] == 0)
+        assert (err / scale).max() < tol, (err / scale).max()
+    else:
+        cg, co = gm.debug(2), om.centroid()
+        if precision == 0:
+            scale = np.sqrt(np.maximum(om.cell_area(), 1e-300))
+        else:
+            scale = np.maximum(np.abs(co).max(1), 1e-3)
+        err = np.linalg.norm(cg - co, axis=1) / scale
+        lv_g, lv_o = gm.debug(6).astype(int), om.quad_level()
+        flips = lv_g != lv_o
+        if precision == 0:
+            assert flips.sum() == 0
+        assert flips.mean() < 1e-3
+        assert err[~flips].max() < tol, err[~flips].max()
+    pg, po = gm.points(), om.points()
+    if precision == 0:
+        scale = h_of_points(om, po)
+    else:
+        scale = np.maximum(np.abs(po).max(1), 1e-3)
+    err = np.linalg.norm(pg.astype(np.float64) - po, axis=1) / scale
+    bad = err > tol
+    if precision == 0:
+        assert bad.sum() == 0, (bad.sum(), err.max())
+    else:
+        assert bad.mean() < 1e-3, (bad.sum(), err.max())
+    cg_cls, co_cls = gm.debug(4).astype(int), om.classes()
+    mism = cg_cls != co_cls
+    if precision == 0:
+        assert mism.sum() == 0
+    return err
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_distmesh_step(precision):
+    gm, om = make_pair(disk_small(), precision=precision, method=0)
+    _compare_step(gm, om, precision, 0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cvd_step_annulus(precision):
+    gm, om = make_pair(annulus_small(), precision=precision, method=1)
+    _compare_step(gm, om, precision, 1)
+
+
+def test_cvd_and_dm_after_several_steps():
+    # advance both from identical states several times, re-syncing the state
+    # each time so every comparison starts from identical inputs
+    gm, om = make_pair(annulus_small(n=8009, seed=4), precision=0, method=1)
+    for k in range(4):
+        _compare_step(gm, om, 0, 1)
+        gm.set_state(om.points(), om.classes(), om.dprev())
+    gm2, om2 = make_pair(disk_small(n=5003, seed=9), precision=0, method=0)
+    for k in range(4):
+        _compare_step(gm2, om2, 0, 0)
+        gm2.set_state(om2.points(), om2.classes(), om2.dprev())
+
+
+def test_hybrid_switch_and_quality_trajectory():
+    gm, om = make_pair(disk_small(n=4001, seed=2), precision=0, method=2)
+    for k in range(12):
+        sg = gm.step(1)
+        so = om.step()
+        assert sg["switched"] == so["switched"], k
+        assert sg["half_mean_alpha"] == pytest.approx(so["half_mean_alpha"], rel=1e-6)
+        assert sg["n_tri"] == so["n_tri"]
+        gm.set_state(om.points(), om.classes(), om.dprev())
+
+
+def test_multi_iteration_quality_statistics():
+    # trajectories diverge after topology flips; compare statistics only
+    gm, om = make_pair(disk_small(n=6007, seed=7), precision=0, method=2)
+    sg = gm.step(25)
+    so = None
+    for _ in range(25):
+        so = om.step()
+        if so["terminated"]:
+            break
+    assert sg["half_mean_alpha"] == pytest.approx(so["half_mean_alpha"], rel=2e-2)
+    assert sg["min_angle_deg"] > 0.5 * so["min_angle_deg"]
+
+
+def test_bucket_points_raw():
+    import torch
+
+    import paper_2309_13824_gb300 as g
+
+    rng = np.random.default_rng(1)
+    n, nbx, nby = 100_003, 97, 61
+    box = (-1.1, -1.1, 1.1, 1.1)
+    pts = rng.uniform(-1.1, 1.1, (n, 2))
+    x = torch.tensor(pts[:, 0], device="cuda")
+    y = torch.tensor(pts[:, 1], device="cuda")
+    bs = torch.zeros(nbx * nby + 1, dtype=torch.int32, device="cuda")
+    si = torch.zeros(n, dtype=torch.int32, device="cuda")
+    scratch = torch.zeros(2 * n + nbx * nby + 1024, dtype=torch.int32, device="cuda")
+    g.mesh_bucket_points(x, y, n, box, nbx, nby, bs, si, scratch, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    bs, si = bs.cpu().numpy(), si.cpu().numpy()
+    bx = np.clip(np.floor((pts[:, 0] - box[0]) * (nbx / 2.2)).astype(int), 0, nbx - 1)
+    by = np.clip(np.floor((pts[:, 1] - box[1]) * (nby / 2.2)).astype(int), 0, nby - 1)
+    key = by * nbx + bx
+    assert np.array_equal(np.diff(bs), np.bincount(key, minlength=nbx * nby))
+    assert np.array_equal(np.sort(si), np.arange(n))
+    for b in rng.integers(0, nbx * nby, 200):
+        assert np.all(key[si[bs[b]:bs[b + 1]]] == b)
+
+
+def test_device_outputs_and_torch_stream():
+    import torch
+
+    import paper_2309_13824_gb300 as g
+
+    sdf, siz, pts = disk_small(n=3001, seed=5)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        gm = g.Mesh(sdf, siz, pts, method=0, stream=s.cuda_stream)
+        gm.rebuild()
+        host = gm.triangles()
+        dev = torch.zeros((len(host) + 5, 3), dtype=torch.int32, device="cuda")
+        n = gm.triangles(out=dev)
+        s.synchronize()
+        assert n == len(host)
+        assert np.array_equal(sorted_tris(dev[:n].cpu().numpy()), sorted_tris(host))
+        small = torch.zeros((2, 3), dtype=torch.int32, device="cuda")
+        with pytest.raises(g.MeshError) as e:
+            gm.triangles(out=small)
+        assert e.value.code == g.TRIME_ECAPACITY
+        pd = torch.zeros((3001, 2), dtype=torch.float64, device="cuda")
+        gm.points(out=pd)
+        s.synchronize()
+        assert np.array_equal(pd.cpu().numpy(), gm.points())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_annulus_triangles(precision):
+    # the million-point annulus of the benchmark, checked completely
+    wl = W.annulus_workload(n=1_000_000, method=2, precision=precision)
+    gm, om = make_pair((wl.sdf, wl.sizing, wl.points), precision=precision, method=2)
+    _tri_equal(gm, om)
