@@ -26,6 +26,7 @@ namespace trime {
 
 constexpr float kEps = 5.9604645e-8f;  // 2^-24
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kStageCap = 160;  // staged candidates per warp (16 bytes each)
 
 struct Lane {
     float nx, ny, s;      // edge half-plane n.u <= s
@@ -245,6 +246,45 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
     const float bsx = (float)P.bsx, bsy = (float)P.bsy;
     const float bmargin = (float)(1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy)) + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
     const float INF = __int_as_float(0x7f800000);
+    // per-warp staging buffer: candidates of the current ring, applied
+    // nearest first across the whole staged set
+    __shared__ float4 stage_all[kVoroThreads / 32][kStageCap];
+    float4* stage = stage_all[threadIdx.x >> 5];
+    int nst = 0;
+    auto flush = [&]() -> int {
+        while (true) {
+            float best = INF;
+            int bi = -1;
+            float lim = 4.0f * Rmax * Rmax * 1.0001f;
+            for (int q = lane; q < nst; q += 32) {
+                float d2 = stage[q].z;
+                if (d2 < lim && d2 < best) {
+                    best = d2;
+                    bi = q;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                float ob = __shfl_xor_sync(kFull, best, o);
+                int oi = __shfl_xor_sync(kFull, bi, o);
+                if (ob < best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (bi < 0) break;
+            float4 c = stage[bi];
+            __syncwarp();
+            if (lane == 0) stage[bi].z = INF;
+            __syncwarp();
+            int st = clip_by<T>(L, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, RB, lane, ctx);
+            if (st) return st;
+            Rmax = warp_max(lane < ne ? L.vR : 0.0f);
+        }
+        nst = 0;
+        __syncwarp();
+        return 0;
+    };
     for (int r = 1;; r++) {
         int nr = r == 1 ? 3 : 4 * r;
         for (int kb = 0; kb < nr; kb += 32) {
@@ -253,7 +293,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
             if (k < nr) {
                 int row, c0, c1;
                 if (r == 1) {
-                    row = byi - 1 + k;
+                    row = byi + (k == 0 ? 0 : (k == 1 ? -1 : 1));  // own row first
                     c0 = bxi - 1;
                     c1 = bxi + 1;
                 } else if (k < 2) {
@@ -303,24 +343,9 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
                     d2 = dx * dx + dy * dy;
                 }
                 bool keep = valid && d2 < 4.0f * Rmax * Rmax * 1.0001f;
-                while (true) {
-                    unsigned km = __ballot_sync(kFull, keep);
-                    if (!km) break;
-                    float key = keep ? d2 : INF;
-                    int who = lane;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        float ok = __shfl_xor_sync(kFull, key, o);
-                        int ow2 = __shfl_xor_sync(kFull, who, o);
-                        if (ok < key || (ok == key && ow2 < who)) {
-                            key = ok;
-                            who = ow2;
-                        }
-                    }
-                    float cx = __shfl_sync(kFull, dx, who), cy = __shfl_sync(kFull, dy, who);
-                    float cl = __shfl_sync(kFull, d2, who);
-                    int cs = __shfl_sync(kFull, slot, who);
-                    int st = clip_by<T>(L, ne, cx, cy, 0.5f * cl, cs, true, RB, lane, ctx);
+                unsigned km = __ballot_sync(kFull, keep);
+                if (nst + __popc(km) > kStageCap) {
+                    int st = flush();
                     if (st) {
                         if (st == 2 && lane == 0) atomicAdd(&a.ctrl->cnt.ring_overflow, 1ull);
                         if (lane == 0) {
@@ -329,10 +354,22 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
                         }
                         return;
                     }
-                    Rmax = warp_max(lane < ne ? L.vR : 0.0f);
-                    keep = keep && lane != who && d2 < 4.0f * Rmax * Rmax * 1.0001f;
+                    keep = keep && d2 < 4.0f * Rmax * Rmax * 1.0001f;
+                    km = __ballot_sync(kFull, keep);
                 }
+                if (keep) stage[nst + __popc(km & ((1u << lane) - 1u))] = make_float4(dx, dy, d2, __int_as_float(slot));
+                nst += __popc(km);
+                __syncwarp();
             }
+        }
+        int st = flush();
+        if (st) {
+            if (st == 2 && lane == 0) atomicAdd(&a.ctrl->cnt.ring_overflow, 1ull);
+            if (lane == 0) {
+                a.ring_n[s] = 0;
+                a.cellR[s] = 0.0f;
+            }
+            return;
         }
         // nothing outside the (2r+1)^2 block can cut once it is beyond 2 Rmax
         float dmin = INF;
