@@ -168,6 +168,18 @@ int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, d
                        double y1, int32_t nbx, int32_t nby, int32_t* bucket_start, int32_t* sorted_idx,
                        int32_t* scratch, void* cuda_stream);
 
+/* Verification hook for the exact predicates the Voronoi kernel uses
+ * (Sec. 2.1 cell cutting decisions): for each of nq queries of four points
+ * a, b, c, d (HOST array pts of nq*8 doubles, x/y interleaved) and their ids
+ * (HOST nq*4 int32), evaluates on the device out_orient[q] = sign of
+ * orient2d(a, b, c) and out_incircle[q] = sign of the symbolically perturbed
+ * det of rows [x, y, x^2+y^2, 1] (> 0 iff d is inside circle(a, b, c) for
+ * counter-clockwise a, b, c; ties broken by perturbing the lift of point r by
+ * eps^(id_r + 1)).  A value of 2 reports the capacity/underflow guard.
+ * Synchronous; host output arrays of nq int32 each. */
+int mesh_exact_predicates(const double* pts, const int32_t* ids, int64_t nq, int32_t* out_orient,
+                          int32_t* out_incircle);
+
 #ifdef __cplusplus
 }
 #endif

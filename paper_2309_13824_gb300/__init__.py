@@ -62,7 +62,7 @@ class mesh_stats(C.Structure):
 # every symbol include/trime.h declares
 EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
-           "mesh_last_error", "mesh_bucket_points"]
+           "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates"]
 
 _lib = None
 
@@ -98,8 +98,10 @@ def lib():
     L.mesh_last_error.restype = C.c_char_p
     L.mesh_bucket_points.argtypes = [vp, vp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                      C.c_int32, C.c_int32, vp, vp, vp, vp]
+    L.mesh_exact_predicates.argtypes = [vp, vp, C.c_int64, vp, vp]
     for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles", "mesh_get_points",
-                 "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points"):
+                 "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
+                 "mesh_exact_predicates"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -140,6 +142,18 @@ def mesh_bucket_points(x, y, n, box, nbx, nby, bucket_start, sorted_idx, scratch
     rc = lib().mesh_bucket_points(_ptr(x), _ptr(y), n, box[0], box[1], box[2], box[3], nbx, nby,
                                   _ptr(bucket_start), _ptr(sorted_idx), _ptr(scratch), C.c_void_p(stream))
     return _check(rc)
+
+
+def mesh_exact_predicates(pts, ids):
+    """Device exact predicates on (nq, 4, 2) points and (nq, 4) ids."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 8)
+    ids = np.ascontiguousarray(ids, dtype=np.int32).reshape(-1, 4)
+    nq = len(pts)
+    o = np.zeros(nq, dtype=np.int32)
+    c = np.zeros(nq, dtype=np.int32)
+    _check(lib().mesh_exact_predicates(pts.ctypes.data_as(C.c_void_p), ids.ctypes.data_as(C.c_void_p), nq,
+                                       o.ctypes.data_as(C.c_void_p), c.ctypes.data_as(C.c_void_p)))
+    return o, c
 
 
 def _stats_dict(s: mesh_stats) -> dict:

@@ -10,7 +10,7 @@
 //
 // Guard: the arithmetic is exact while every non-zero coordinate difference
 // lies in [1e-50, 1e50] (no underflow of product error terms) and expansions
-// fit kExpCap components; otherwise *ovf is set and a fixed sign returned.
+// fit kExpCap components; otherwise the predicates return kExactFail.
 #pragma once
 #include "common.cuh"
 
@@ -48,7 +48,7 @@ __device__ __forceinline__ void two_prod(double a, double b, double& x, double& 
 }
 
 // h = e + b (zero-eliminating); returns length or -1 on overflow
-__device__ int grow_expansion(int elen, const double* e, double b, double* h, int cap) {
+__device__ __forceinline__ int grow_expansion(int elen, const double* e, double b, double* h, int cap) {
     double Q = b;
     int hl = 0;
     for (int i = 0; i < elen; i++) {
@@ -68,7 +68,7 @@ __device__ int grow_expansion(int elen, const double* e, double b, double* h, in
 }
 
 // h = e + f by repeated growth (each step keeps the expansion non-overlapping)
-__device__ int expansion_sum(int elen, const double* e, int flen, const double* f, double* h, int cap) {
+__device__ __forceinline__ int expansion_sum(int elen, const double* e, int flen, const double* f, double* h, int cap) {
     double t[kExpCap];
     if (elen > kExpCap) return -1;
     for (int i = 0; i < elen; i++) t[i] = e[i];
@@ -84,7 +84,7 @@ __device__ int expansion_sum(int elen, const double* e, int flen, const double* 
 }
 
 // h = e * b (zero-eliminating)
-__device__ int scale_expansion(int elen, const double* e, double b, double* h, int cap) {
+__device__ __forceinline__ int scale_expansion(int elen, const double* e, double b, double* h, int cap) {
     double Q, hh;
     int hl = 0;
     two_prod(e[0], b, Q, hh);
@@ -112,7 +112,7 @@ __device__ int scale_expansion(int elen, const double* e, double b, double* h, i
 
 // rewrite e (non-overlapping, increasing magnitude) with as few components as
 // the two sweeps leave; in place
-__device__ int compress(int elen, double* e) {
+__device__ __forceinline__ int compress(int elen, double* e) {
     if (elen <= 1) return elen;
     double g[kExpCap];
     int bottom = elen - 1;
@@ -140,7 +140,7 @@ __device__ int compress(int elen, double* e) {
 }
 
 // h = e * f, compressed
-__device__ int expansion_mul(int elen, const double* e, int flen, const double* f, double* h, int cap) {
+__device__ __forceinline__ int expansion_mul(int elen, const double* e, int flen, const double* f, double* h, int cap) {
     double acc[kExpCap], t[kExpCap], s[kExpCap];
     int al = 1;
     acc[0] = 0.0;
@@ -168,99 +168,125 @@ __device__ __forceinline__ bool diff_ok(double a, double b) {
     return d == 0.0 || (d >= 1e-50 && d <= 1e50);
 }
 
-// sign of (b-a) x (c-a), exact
-__device__ __noinline__ int orient_exact(const double* a, const double* b, const double* c, int* ovf) {
-    if (!diff_ok(b[0], a[0]) || !diff_ok(b[1], a[1]) || !diff_ok(c[0], a[0]) || !diff_ok(c[1], a[1])) {
-        *ovf = 1;
-        return 1;
+// Status codes of the exact predicates: -1 / 0 / +1 are signs, kExactFail
+// means the capacity or underflow guard tripped.
+constexpr int kExactFail = 2;
+
+// sign of (b-a) x (c-a), exact: the determinant with a column of ones is
+// the sum of the six products ax by - ay bx + bx cy - by cx + cx ay - cy ax,
+// each split exactly into two doubles and accumulated by growth
+__device__ __noinline__ int orient_exact(const double* a, const double* b, const double* c) {
+    const double* P[3] = {a, b, c};
+    bool ok = true;
+    for (int k = 0; k < 3; k++)
+        for (int q = 0; q < 2; q++) {
+            double v = fabs(P[k][q]);
+            ok = ok && (v == 0.0 || (v >= 1e-100 && v <= 1e100));
+        }
+    double acc[kExpCap], tmp[kExpCap];
+    int al = 1;
+    acc[0] = 0.0;
+    for (int k = 0; k < 3 && ok; k++) {
+        const double* u = P[k];
+        const double* v = P[k == 2 ? 0 : k + 1];
+        double t[4];
+        two_prod(u[0], v[1], t[1], t[0]);
+        two_prod(u[1], v[0], t[3], t[2]);
+        t[2] = -t[2];
+        t[3] = -t[3];
+        for (int q = 0; q < 4 && ok; q++) {
+            al = grow_expansion(al, acc, t[q], tmp, kExpCap);
+            ok = al > 0;
+            for (int i = 0; i < al; i++) acc[i] = tmp[i];
+        }
     }
-    double bx[2], by[2], cx[2], cy[2];
-    two_diff(b[0], a[0], bx[1], bx[0]);
-    two_diff(b[1], a[1], by[1], by[0]);
-    two_diff(c[0], a[0], cx[1], cx[0]);
-    two_diff(c[1], a[1], cy[1], cy[0]);
-    double p[kExpCap], q[kExpCap], r[kExpCap];
-    int pl = expansion_mul(2, bx, 2, cy, p, kExpCap);
-    int ql = expansion_mul(2, by, 2, cx, q, kExpCap);
-    if (pl < 0 || ql < 0) { *ovf = 1; return 1; }
-    for (int i = 0; i < ql; i++) q[i] = -q[i];
-    int rl = expansion_sum(pl, p, ql, q, r, kExpCap);
-    if (rl < 0) { *ovf = 1; return 1; }
-    return exp_sign(rl, r);
+    return ok ? exp_sign(al, acc) : kExactFail;
 }
 
 // sign of det of rows [x, y, x^2 + y^2, 1] of (a, b, c, d), exact
-__device__ __noinline__ int incircle_exact(const double* a, const double* b, const double* c, const double* d,
-                                           int* ovf) {
+__device__ __noinline__ int incircle_exact(const double* a, const double* b, const double* c, const double* d) {
     const double* P[3] = {a, b, c};
     double dx[3][2], dy[3][2];
+    bool ok = true;
     for (int r = 0; r < 3; r++) {
-        if (!diff_ok(P[r][0], d[0]) || !diff_ok(P[r][1], d[1])) { *ovf = 1; return 1; }
+        ok = ok && diff_ok(P[r][0], d[0]) && diff_ok(P[r][1], d[1]);
         two_diff(P[r][0], d[0], dx[r][1], dx[r][0]);
         two_diff(P[r][1], d[1], dy[r][1], dy[r][0]);
     }
     double lift[3][kExpCap];
-    int ll[3];
+    int ll[3] = {0, 0, 0};
     double t1[kExpCap], t2[kExpCap];
-    for (int r = 0; r < 3; r++) {
+    for (int r = 0; r < 3 && ok; r++) {
         int l1 = expansion_mul(2, dx[r], 2, dx[r], t1, kExpCap);
         int l2 = expansion_mul(2, dy[r], 2, dy[r], t2, kExpCap);
-        if (l1 < 0 || l2 < 0) { *ovf = 1; return 1; }
-        ll[r] = expansion_sum(l1, t1, l2, t2, lift[r], kExpCap);
-        if (ll[r] < 0) { *ovf = 1; return 1; }
-        ll[r] = compress(ll[r], lift[r]);
+        ok = l1 > 0 && l2 > 0;
+        if (ok) {
+            ll[r] = expansion_sum(l1, t1, l2, t2, lift[r], kExpCap);
+            ok = ll[r] > 0;
+            if (ok) ll[r] = compress(ll[r], lift[r]);
+        }
     }
     // det = lift_a (bx cy - by cx) + lift_b (cx ay - cy ax) + lift_c (ax by - ay bx)
     double acc[kExpCap];
     int al = 1;
     acc[0] = 0.0;
-    for (int r = 0; r < 3; r++) {
+    for (int r = 0; r < 3 && ok; r++) {
         int u = (r + 1) % 3, v = (r + 2) % 3;
         double m[kExpCap], term[kExpCap], s[kExpCap];
         int l1 = expansion_mul(2, dx[u], 2, dy[v], t1, kExpCap);
         int l2 = expansion_mul(2, dy[u], 2, dx[v], t2, kExpCap);
-        if (l1 < 0 || l2 < 0) { *ovf = 1; return 1; }
+        ok = l1 > 0 && l2 > 0;
+        if (!ok) break;
         for (int i = 0; i < l2; i++) t2[i] = -t2[i];
         int ml = expansion_sum(l1, t1, l2, t2, m, kExpCap);
-        if (ml < 0) { *ovf = 1; return 1; }
+        ok = ml > 0;
+        if (!ok) break;
         ml = compress(ml, m);
         int tl = expansion_mul(ll[r], lift[r], ml, m, term, kExpCap);
-        if (tl < 0) { *ovf = 1; return 1; }
+        ok = tl > 0;
+        if (!ok) break;
         al = expansion_sum(al, acc, tl, term, s, kExpCap);
-        if (al < 0) { *ovf = 1; return 1; }
+        ok = al > 0;
+        if (!ok) break;
         al = compress(al, s);
         for (int i = 0; i < al; i++) acc[i] = s[i];
     }
-    return exp_sign(al, acc);
+    return ok ? exp_sign(al, acc) : kExactFail;
 }
 
 // Perturbed det4(a,b,c,d) sign (never 0 for the configurations used here):
 // exact value first, then the coefficient of the largest perturbation with a
 // non-zero cofactor: C_a = orient(b,c,d), C_b = -orient(a,c,d),
-// C_c = orient(a,b,d), C_d = -orient(a,b,c).
+// C_c = orient(a,b,d), C_d = -orient(a,b,c).  Returns kExactFail on a guard.
 __device__ __noinline__ int incircle_sos(const double* a, int ia, const double* b, int ib, const double* c, int ic,
-                                         const double* d, int id, int* ovf) {
-    int s = incircle_exact(a, b, c, d, ovf);
-    if (s != 0) return s;
-    const double* P[4] = {a, b, c, d};
-    int I[4] = {ia, ib, ic, id};
-    int ord[4] = {0, 1, 2, 3};
-    for (int x = 1; x < 4; x++)
-        for (int y = x; y > 0 && I[ord[y]] < I[ord[y - 1]]; y--) {
-            int t = ord[y];
-            ord[y] = ord[y - 1];
-            ord[y - 1] = t;
+                                         const double* d, int id) {
+    int s = incircle_exact(a, b, c, d);
+    if (s == 0) {
+        const double* P[4] = {a, b, c, d};
+        int I[4] = {ia, ib, ic, id};
+        int ord[4] = {0, 1, 2, 3};
+        for (int x = 1; x < 4; x++)
+            for (int y = x; y > 0 && I[ord[y]] < I[ord[y - 1]]; y--) {
+                int t = ord[y];
+                ord[y] = ord[y - 1];
+                ord[y - 1] = t;
+            }
+        s = kExactFail;
+        for (int q = 0; q < 4; q++) {
+            int r = ord[q], cs;
+            if (r == 0) cs = orient_exact(P[1], P[2], P[3]);
+            else if (r == 1) cs = orient_exact(P[0], P[2], P[3]);
+            else if (r == 2) cs = orient_exact(P[0], P[1], P[3]);
+            else cs = orient_exact(P[0], P[1], P[2]);
+            if (cs == kExactFail) break;
+            if (r == 1 || r == 3) cs = -cs;
+            if (cs != 0) {
+                s = cs;
+                break;
+            }
         }
-    for (int q = 0; q < 4; q++) {
-        int r = ord[q], cs;
-        if (r == 0) cs = orient_exact(P[1], P[2], P[3], ovf);
-        else if (r == 1) cs = -orient_exact(P[0], P[2], P[3], ovf);
-        else if (r == 2) cs = orient_exact(P[0], P[1], P[3], ovf);
-        else cs = -orient_exact(P[0], P[1], P[2], ovf);
-        if (cs != 0) return cs;
     }
-    *ovf = 1;
-    return 1;
+    return s;
 }
 
 }  // namespace trime

@@ -73,6 +73,8 @@ template <typename T> void launch_tri_write(const IterArgs<T>& a, const int32_t*
 template <typename T> void launch_unpermute(const IterArgs<T>& a, T* out_xy, cudaStream_t st);
 template <typename T> void launch_set_state(const IterArgs<T>& a, const T* xy, const uint8_t* cls,
                                             const double* dprev, cudaStream_t st);
+void launch_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out,
+                       cudaStream_t st);
 // standalone a1 on raw arrays (mesh_bucket_points)
 void launch_bucket_raw(const double* x, const double* y, int32_t n, double x0, double y0, double bsx, double bsy,
                        int32_t nbx, int32_t nby, int32_t* bstart, int32_t* sorted_idx, int32_t* scratch,

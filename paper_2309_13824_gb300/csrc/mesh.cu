@@ -709,4 +709,34 @@ int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, d
     return TRIME_OK;
 }
 
+int mesh_exact_predicates(const double* pts, const int32_t* ids, int64_t nq, int32_t* out_orient,
+                          int32_t* out_incircle) {
+    if (nq < 0 || nq > (int64_t)(1 << 26)) return fail(TRIME_EINVAL, "nq out of range");
+    if (nq == 0) return TRIME_OK;
+    if (!pts || !ids || !out_orient || !out_incircle) return fail(TRIME_EINVAL, "NULL pointer");
+    double* dp = nullptr;
+    int32_t *di = nullptr, *dout = nullptr;
+    size_t n = (size_t)nq;
+    if (cudaMalloc(&dp, 8 * n * sizeof(double)) != cudaSuccess || cudaMalloc(&di, 4 * n * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&dout, 2 * n * sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(dp);
+        cudaFree(di);
+        cudaFree(dout);
+        return fail(TRIME_ENOMEM, "cudaMalloc failed");
+    }
+    cudaError_t e = cudaMemcpy(dp, pts, 8 * n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(di, ids, 4 * n * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_predicates(dp, di, (int32_t)nq, dout, dout + n, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out_orient, dout, n * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out_incircle, dout + n, n * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(dp);
+    cudaFree(di);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(TRIME_ECUDA, std::string("predicates: ") + cudaGetErrorString(e));
+    return TRIME_OK;
+}
+
 }  // extern "C"

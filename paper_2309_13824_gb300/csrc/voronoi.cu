@@ -100,10 +100,12 @@ __device__ __noinline__ bool exact_cut(const CellCtx<T>& c, int sj, int sk, int 
                cl * (fabs(ax * by) + fabs(ay * bx));
     if (P > 1e-280 && fabs(lam) > 64.0 * 1.1102230246251565e-16 * P) return lam < 0.0;  // lam = -det4
     atomicAdd(&c.ctrl->cnt.exact_calls, 1ull);
-    int ovf = 0;
-    int o = orient_exact(pi, pj, pk, &ovf);
-    int d = incircle_sos(pi, c.idi, pj, c.id[sj], pk, c.id[sk], pl, c.id[sl], &ovf);
-    if (ovf) atomicAdd(&c.ctrl->cnt.exact_overflow, 1ull);
+    int o = orient_exact(pi, pj, pk);
+    int d = incircle_sos(pi, c.idi, pj, c.id[sj], pk, c.id[sk], pl, c.id[sl]);
+    if (o == kExactFail || d == kExactFail) {
+        atomicAdd(&c.ctrl->cnt.exact_overflow, 1ull);
+        return false;
+    }
     return d * o > 0;
 }
 
@@ -400,6 +402,20 @@ void launch_voronoi(const IterArgs<T>& a, cudaStream_t st) {
 }
 
 template void launch_voronoi<double>(const IterArgs<double>&, cudaStream_t);
+// device exact predicates on explicit queries (verification hook)
+__global__ void k_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const double* p = pts + 8 * (size_t)q;
+    const int32_t* id = ids + 4 * (size_t)q;
+    o_out[q] = orient_exact(p, p + 2, p + 4);
+    c_out[q] = incircle_sos(p, id[0], p + 2, id[1], p + 4, id[2], p + 6, id[3]);
+}
+
+void launch_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out,
+                       cudaStream_t st) {
+    if (nq > 0) k_predicates<<<(nq + 127) / 128, 128, 0, st>>>(pts, ids, nq, o_out, c_out);
+}
 template void launch_voronoi<float>(const IterArgs<float>&, cudaStream_t);
 
 }  // namespace trime
