@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Meshing-iteration throughput of the GB300 path on the million-point annulus.
+
+Workload: annulus 0.3 <= r <= 1 on a 1024^2 FP32 SDF grid, adaptive sizing
+h = 0.002 + 0.05|sdf| on a 512^2 grid, 10^6 points drawn by rejection
+sampling with density proportional to 1/h^2 (seed 1), hybrid method
+(DistMesh then CVD), FP64 positions.  One step = one meshing iteration
+(bucketing, Voronoi cells, triangle emission and validity, quality, move,
+point treatment) over all points.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas, one per
+GPU (the meshes do not exchange data), and reports their aggregate.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s per meshing iteration at 1e6 pts; wall time to quality at 1e6 pts"
+WORKLOAD = ("annulus r in [0.3,1], 1024^2 FP32 SDF, sizing 0.002+0.05|sdf| on 512^2, "
+            "1e6 points ~ 1/h^2 (seed 1), hybrid DistMesh->CVD")
+VORONOI_FLOP_PER_CELL = 2500.0  # algorithmic flops of one cell's clipping
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--points", type=int, default=1_000_000)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--method", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true", help="skip time-to-quality / FP32 / CPU legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def committed_traffic(kernel_src):
+    """DRAM bytes per launch of the Voronoi kernel from the committed ncu
+    summary, or None if the kernel source changed since it was captured."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "voronoi_annulus_1e6.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    tr, hs = None, None
+    for line in txt.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            tr = float(line.split(":")[1])
+        if line.startswith("voronoi_cu_sha256_16:"):
+            hs = line.split(":")[1].strip()
+    return tr if hs == digest else None
+
+
+def flush_l2(buf):
+    buf.fill_(1)
+
+
+def oracle_sample_rate(wl, target_s, max_cells=None):
+    """Oracle (single thread) per-cell iteration work on a random sample."""
+    import oracle
+
+    oracle.build()
+    om = oracle.OracleMesh(wl.sdf, wl.sizing, wl.points, method=wl.method)
+    n = len(wl.points)
+    rng = np.random.default_rng(123)
+    probe = rng.choice(n, min(n, 4000), replace=False)
+    t = time.perf_counter()
+    om.rebuild_sample(probe)
+    per = (time.perf_counter() - t) / len(probe)
+    cnt = int(min(n if max_cells is None else max_cells, max(len(probe), target_s / per)))
+    cells = rng.choice(n, cnt, replace=False)
+    t = time.perf_counter()
+    om.rebuild_sample(cells)
+    dt = time.perf_counter() - t
+    return cnt, dt
+
+
+def run_reference(args, wl):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    cells_per_step = 30000
+    for _ in range(args.warmup):
+        oracle_sample_rate(wl, 0.0, max_cells=2000)
+    times = []
+    cnt_total = 0
+    for _ in range(args.steps):
+        cnt, dt = oracle_sample_rate(wl, 1e9, max_cells=cells_per_step)
+        times.append(dt)
+        cnt_total += cnt
+    v = cnt_total / sum(times) / 1e6
+    sample = (f"{cells_per_step} random cells of the 1e6-point workload per step: cell clipping, owned triangles "
+              f"with Tests 1-3 and CVD centroid (single thread, FP64 oracle)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "points": len(wl.points)},
+            "cpu_baseline": {"value": v, "unit": "Mpts/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    import workloads as W
+
+    wl = W.annulus_workload(n=args.points, method=args.method, precision=args.precision)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2309_13824_gb300 as g
+
+    if not g.LIB_PATH.exists():
+        g.build()
+    g.lib()
+    n = len(wl.points)
+    pts = wl.points if args.precision == 0 else W.to_fp32_positions(wl.points)
+    stream = torch.cuda.current_stream()
+    mesh = g.Mesh(wl.sdf, wl.sizing, pts, method=args.method, precision=args.precision,
+                  stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(max(3, args.warmup)):
+        mesh.step_async(1)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K iterations, L2 flushed before each, device events
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush_l2(flush)
+        ev[k][0].record(stream)
+        mesh.step_async(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    st = mesh.step(0)
+    if dist:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = n * world * args.steps / total_s / 1e6
+
+    # ---- per-stage device times (roofline of the dominant kernel)
+    pm = g.Mesh(wl.sdf, wl.sizing, pts, method=args.method, precision=args.precision, stream=stream.cuda_stream)
+    pm.profile(2)
+    prof = pm.profile(args.steps)
+    stage_ms = {k: v / args.steps for k, v in prof.items()}
+    pm.close()
+    t_vor = stage_ms["voronoi"] / 1e3
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA issue, TFLOP/s
+    achieved = VORONOI_FLOP_PER_CELL * n / t_vor / 1e12
+    src = os.path.join(ROOT, "paper_2309_13824_gb300", "csrc", "voronoi.cu")
+    roofline = {"bound": "alu", "kernel": "k_voronoi", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": committed_traffic(src),
+                "peak_note": f"{sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and clocks)",
+                "stage_ms": stage_ms}
+
+    # ---- end to end through the C ABI: H2D of the step's positions from
+    # pinned host memory, one iteration, D2H of the moved positions
+    e2e = None
+    if rank == 0 or world > 1:
+        em = g.Mesh(wl.sdf, wl.sizing, pts, method=args.method, precision=args.precision,
+                    stream=stream.cuda_stream)
+        dt_np = np.float64 if args.precision == 0 else np.float32
+        host_in = torch.from_numpy(np.ascontiguousarray(pts, dtype=dt_np)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        for _ in range(2):
+            em.set_state(host_in.numpy())
+            em.step(1)
+            em.points(out=host_out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            em.set_state(host_in.numpy())
+            em.step(1)
+            em.points(out=host_out)
+        torch.cuda.synchronize()
+        e_s = time.perf_counter() - t0
+        nbytes = n * 2 * host_in.element_size()
+        e2e = {"value": n * args.steps / e_s / 1e6, "unit": "Mpts/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+        em.close()
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # wall time to quality: hybrid from the seeds until termination
+        tq = g.Mesh(wl.sdf, wl.sizing, pts, method=2, precision=args.precision, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = tq.step(2000)
+        torch.cuda.synchronize()
+        extras["time_to_quality"] = {"seconds": time.perf_counter() - t0, "iterations": s["iterations"],
+                                     "terminated": bool(s["terminated"]), "min_angle_deg": s["min_angle_deg"],
+                                     "half_mean_alpha": s["half_mean_alpha"], "max_alpha": s["max_alpha"],
+                                     "mean_size_dev": s["mean_size_dev"], "n_tri": s["n_tri"]}
+        tq.close()
+        # FP32-position mode on the same workload
+        if args.precision == 0:
+            p32 = W.to_fp32_positions(wl.points)
+            fm = g.Mesh(wl.sdf, wl.sizing, p32, method=args.method, precision=1, stream=stream.cuda_stream)
+            for _ in range(3):
+                fm.step_async(1)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for k in range(args.steps):
+                flush_l2(flush)
+                evs[k][0].record(stream)
+                fm.step_async(1)
+                evs[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms32 = sum(a.elapsed_time(b) for a, b in evs)
+            extras["fp32_positions"] = {"value": n * args.steps / (ms32 / 1e3) / 1e6, "unit": "Mpts/s",
+                                        "ms_per_step": ms32 / args.steps}
+            fm.close()
+        cnt, dt = oracle_sample_rate(wl, 10.0)
+        extras["cpu_baseline"] = {"value": cnt / dt / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"{cnt} random cells of the workload: cell clipping, owned triangles "
+                                            f"with Tests 1-3, CVD centroid; single-thread FP64 oracle "
+                                            f"({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "points": n, "method": ["dm", "cvd", "hybrid"][args.method],
+                           "precision": ["fp64", "fp32"][args.precision],
+                           "l2": "flushed before every timed step (256 MB write)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "e2e": e2e, "clocks": clk,
+                "gpu_launches": 11 * args.steps,
+                "last_step": {"method": st["method"], "switched": st["switched"], "n_tri": st["n_tri"],
+                              "half_mean_alpha": st["half_mean_alpha"]}}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    mesh.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

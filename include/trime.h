@@ -121,8 +121,10 @@ int mesh_rebuild(mesh_t* m, mesh_stats* stats);
 /* Run up to n_iters meshing iterations (Algorithms 1-2; hybrid Sec. 4.2),
  * each one graph launch: rebuild, quality, hybrid/termination decision, move,
  * point treatment (Sec. 4.3).  Stops early once a termination criterion of
- * Sec. 4 holds.  Synchronises at the end; fills *stats if given.  Returns
- * TRIME_EDEVICE if a capacity guard tripped (counters in *stats). */
+ * Sec. 4 holds (checked on the host every 32 iterations; later iterations are
+ * device-side no-ops).  With stats != NULL synchronises at the end, fills
+ * *stats and returns TRIME_EDEVICE if a capacity guard tripped; with
+ * stats == NULL the call is asynchronous on the caller's stream. */
 int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats);
 
 /* Valid triangles of the last rebuild as int32 (a, b, c) point indices, a the
@@ -167,6 +169,15 @@ const char* mesh_last_error(void);
 int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, double y0, double x1,
                        double y1, int32_t nbx, int32_t nby, int32_t* bucket_start, int32_t* sorted_idx,
                        int32_t* scratch, void* cuda_stream);
+
+/* Per-stage device timing (tracing): run n_iters iterations as separate
+ * kernel launches (not the graph) with CUDA events between the stages on the
+ * library's stream and ADD the elapsed milliseconds to stage_ms[0..6]:
+ * 0 bucketing (a1), 1 Voronoi cells (a2), 2 triangle emission, validity and
+ * quality sums (a3/a4/a8), 3 statistics and hybrid/termination decision,
+ * 4 move and point treatment (a5-a7), 5 movement statistics, 6 whole
+ * iteration.  Semantics otherwise as mesh_step.  Synchronises. */
+int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms);
 
 /* Verification hook for the exact predicates the Voronoi kernel uses
  * (Sec. 2.1 cell cutting decisions): for each of nq queries of four points

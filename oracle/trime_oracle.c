@@ -1082,8 +1082,14 @@ static int centroid_adaptive(const grid_t* siz, const double* gen, const double*
 }
 
 /* V_i = cell of i clipped to Reg_i, vertices relative to p_i */
+static int cell_polygon_labels(const om_mesh* m, int64_t i, const int32_t* ring, int64_t ne, double* out, int cap);
+
 static int cell_polygon(const om_mesh* m, int64_t i, double* out, int cap) {
     int64_t o = m->ring_off[i], ne = m->ring_off[i + 1] - o;
+    return cell_polygon_labels(m, i, m->ring + o, ne, out, cap);
+}
+
+static int cell_polygon_labels(const om_mesh* m, int64_t i, const int32_t* ring, int64_t ne, double* out, int cap) {
     if (ne == 0) return 0;
     hp_t E[CELL_CAP];
     double px = m->x[i], py = m->y[i];
@@ -1091,7 +1097,7 @@ static int cell_polygon(const om_mesh* m, int64_t i, double* out, int cap) {
     double W = m->sdf.x1 - m->sdf.x0, H = m->sdf.y1 - m->sdf.y0;
     double mb = m->P.bounded ? S * 0.125 : 0.125 * (W > H ? W : H);
     for (int64_t t = 0; t < ne; t++) {
-        int32_t lab = m->ring[o + t];
+        int32_t lab = ring[t];
         hp_t* e = &E[t];
         e->lab = lab;
         if (lab >= 0) {
@@ -1328,18 +1334,42 @@ int om_step(om_mesh* m) {
     return 0;
 }
 
+/* Per-cell work of one iteration on a subset of cells, for timing: the
+ * cell (Sec. 2.1), its owned triangles with Tests 1-3 (Sec. 4.1) and, with
+ * with_centroid, its CVD centroid (Sec. 4.2).  Returns the triangles kept. */
 int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid) {
     ogrid_t G;
     ogrid_build(m, &G);
     hp_t E[CELL_CAP];
+    int32_t lab[CELL_CAP];
+    double poly[2 * CELL_CAP];
     int64_t errs = 0;
+    int kept = 0;
     for (int64_t q = 0; q < ncells; q++) {
-        int ne = cell_compute(m, &G, cells[q], E, &errs);
-        (void)ne;
+        int64_t i = cells[q];
+        int ne = cell_compute(m, &G, i, E, &errs);
+        for (int t = 0; t < ne; t++) lab[t] = E[t].lab;
+        for (int t = 0; t < ne; t++) {
+            int32_t j = lab[t], k = lab[(t + 1) % ne];
+            if (j < 0 || k < 0 || !(i < j && i < k)) continue;
+            double ox, oy, R;
+            circumcenter_fixed(m->x[i], m->y[i], m->x[j], m->y[j], m->x[k], m->y[k], &ox, &oy, &R);
+            if (!(reg_contains(m, i, ox, oy) && reg_contains(m, j, ox, oy) && reg_contains(m, k, ox, oy))) continue;
+            if (m->P.validity && !triangle_valid(m, i, j, k)) continue;
+            kept++;
+        }
+        if (with_centroid) {
+            int n = cell_polygon_labels(m, i, lab, ne, poly, CELL_CAP);
+            double gen[2] = {m->x[i], m->y[i]}, c[2];
+            double h = h_at(m, m->x[i], m->y[i]);
+            int32_t lv;
+            if (n >= 3)
+                centroid_adaptive(&m->siz, gen, poly, n, fmax(m->dprev[i] / h, m->P.fac_end), m->P.quad_max_level,
+                                  c, &lv, NULL);
+        }
     }
     ogrid_free(&G);
-    (void)with_centroid;
-    return 0;
+    return kept;
 }
 
 /* ------------------------------------------------------------------------ */

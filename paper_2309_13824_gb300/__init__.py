@@ -62,7 +62,7 @@ class mesh_stats(C.Structure):
 # every symbol include/trime.h declares
 EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
-           "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates"]
+           "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step"]
 
 _lib = None
 
@@ -99,9 +99,10 @@ def lib():
     L.mesh_bucket_points.argtypes = [vp, vp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                      C.c_int32, C.c_int32, vp, vp, vp, vp]
     L.mesh_exact_predicates.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.mesh_profile_step.argtypes = [vp, C.c_int32, vp]
     for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles", "mesh_get_points",
                  "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
-                 "mesh_exact_predicates"):
+                 "mesh_exact_predicates", "mesh_profile_step"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -208,6 +209,16 @@ class Mesh:
         d = _stats_dict(s)
         d["rc"] = rc
         return d
+
+    def step_async(self, n_iters: int = 1):
+        """Enqueue iterations on the mesh's stream without reading back."""
+        _check(lib().mesh_step(self._h, n_iters, None))
+
+    def profile(self, n_iters: int = 1):
+        """Per-stage device milliseconds summed over n_iters iterations."""
+        ms = np.zeros(7)
+        _check(lib().mesh_profile_step(self._h, n_iters, ms.ctypes.data_as(C.c_void_p)))
+        return dict(zip(["bucket", "voronoi", "emit", "stats", "update", "post", "total"], ms))
 
     def triangles(self, out=None):
         """Valid triangles (int32, smallest id first, CCW), order unspecified.

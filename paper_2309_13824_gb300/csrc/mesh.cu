@@ -554,14 +554,20 @@ int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats) {
     if (rc) return rc;
     if ((rc = reset_counters(m))) return rc;
     if ((rc = read_ctrl(m))) return rc;
+    if (m->hctrl->terminated) {
+        if ((rc = sync_out(m))) return rc;
+        if (stats) fill_stats(m, 0, stats);
+        return TRIME_OK;
+    }
     int start = m->hctrl->iterations;
     for (int32_t k = 0; k < n_iters; k++) {
         CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
-        if ((k & 31) == 31 || k == n_iters - 1) {
+        if ((k & 31) == 31 || (stats && k == n_iters - 1)) {
             if ((rc = read_ctrl(m))) return rc;
             if (m->hctrl->terminated) break;
         }
     }
+    if (!stats) return sync_out(m);  // asynchronous: no read-back
     if (n_iters == 0 && (rc = read_ctrl(m))) return rc;
     if ((rc = sync_out(m))) return rc;
     if (stats) fill_stats(m, m->hctrl->iterations - start, stats);
@@ -707,6 +713,59 @@ int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, d
                       scratch, (cudaStream_t)cuda_stream);
     CUDA_TRY(cudaGetLastError());
     return TRIME_OK;
+}
+
+int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms) {
+    if (!m || !stage_ms || n_iters < 0) return fail(TRIME_EINVAL, "bad argument");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    cudaEvent_t ev[7];
+    for (int k = 0; k < 7; k++) CUDA_TRY(cudaEventCreate(&ev[k]));
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int32_t it = 0; it < n_iters; it++) {
+        CUDA_TRY(cudaEventRecord(ev[0], m->st));
+        if (m->prec == 0) {
+            IterArgs<double> a = make_args<double>(m, 0);
+            launch_bucket<double>(a, m->st);
+            CUDA_TRY(cudaEventRecord(ev[1], m->st));
+            launch_voronoi<double>(a, m->st);
+            CUDA_TRY(cudaEventRecord(ev[2], m->st));
+            launch_emit<double>(a, m->nblk, m->st);
+            CUDA_TRY(cudaEventRecord(ev[3], m->st));
+            launch_stats_pre(m->ctrl, m->ep, m->nblk, 1, 0, m->dp, m->st);
+            CUDA_TRY(cudaEventRecord(ev[4], m->st));
+            launch_update<double>(a, m->nblk, m->st);
+        } else {
+            IterArgs<float> a = make_args<float>(m, 0);
+            launch_bucket<float>(a, m->st);
+            CUDA_TRY(cudaEventRecord(ev[1], m->st));
+            launch_voronoi<float>(a, m->st);
+            CUDA_TRY(cudaEventRecord(ev[2], m->st));
+            launch_emit<float>(a, m->nblk, m->st);
+            CUDA_TRY(cudaEventRecord(ev[3], m->st));
+            launch_stats_pre(m->ctrl, m->ep, m->nblk, 1, 0, m->dp, m->st);
+            CUDA_TRY(cudaEventRecord(ev[4], m->st));
+            launch_update<float>(a, m->nblk, m->st);
+        }
+        CUDA_TRY(cudaEventRecord(ev[5], m->st));
+        launch_stats_post(m->ctrl, m->up, m->nblk, m->st);
+        CUDA_TRY(cudaEventRecord(ev[6], m->st));
+        CUDA_TRY(cudaEventSynchronize(ev[6]));
+        for (int k = 0; k < 6; k++) {
+            float ms = 0;
+            CUDA_TRY(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            acc[k] += ms;
+        }
+        float tot = 0;
+        CUDA_TRY(cudaEventElapsedTime(&tot, ev[0], ev[6]));
+        acc[6] += tot;
+    }
+    for (int k = 0; k < 7; k++) {
+        stage_ms[k] += acc[k];
+        cudaEventDestroy(ev[k]);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return sync_out(m);
 }
 
 int mesh_exact_predicates(const double* pts, const int32_t* ids, int64_t nq, int32_t* out_orient,
