@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--method", type=int, default=2)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-quality / FP32 / CPU legs")
+    ap.add_argument("--n-opt", type=float, default=None, help="points per neighbour bucket (default 3.3)")
     return ap.parse_args()
 
 
@@ -207,8 +208,9 @@ def main():
     n = len(wl.points)
     pts = wl.points if args.precision == 0 else W.to_fp32_positions(wl.points)
     stream = torch.cuda.current_stream()
+    kw = {} if args.n_opt is None else {"N_opt": args.n_opt}
     mesh = g.Mesh(wl.sdf, wl.sizing, pts, method=args.method, precision=args.precision,
-                  stream=stream.cuda_stream)
+                  stream=stream.cuda_stream, **kw)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(max(3, args.warmup)):
@@ -241,7 +243,8 @@ def main():
     value = n * world * args.steps / total_s / 1e6
 
     # ---- per-stage device times (roofline of the dominant kernel)
-    pm = g.Mesh(wl.sdf, wl.sizing, pts, method=args.method, precision=args.precision, stream=stream.cuda_stream)
+    pm = g.Mesh(wl.sdf, wl.sizing, pts, method=args.method, precision=args.precision, stream=stream.cuda_stream,
+                **kw)
     pm.profile(2)
     prof = pm.profile(args.steps)
     stage_ms = {k: v / args.steps for k, v in prof.items()}
@@ -263,18 +266,22 @@ def main():
     e2e = None
     if rank == 0 or world > 1:
         em = g.Mesh(wl.sdf, wl.sizing, pts, method=args.method, precision=args.precision,
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, **kw)
         dt_np = np.float64 if args.precision == 0 else np.float32
         host_in = torch.from_numpy(np.ascontiguousarray(pts, dtype=dt_np)).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
+        # every step restarts from the host positions, so the hybrid state is
+        # reset too (otherwise the repeated identical quality terminates it)
         for _ in range(2):
             em.set_state(host_in.numpy())
+            em.set_method_state(0)
             em.step(1)
             em.points(out=host_out)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             em.set_state(host_in.numpy())
+            em.set_method_state(0)
             em.step(1)
             em.points(out=host_out)
         torch.cuda.synchronize()
@@ -287,7 +294,7 @@ def main():
     extras = {}
     if not args.no_extras and rank == 0:
         # wall time to quality: hybrid from the seeds until termination
-        tq = g.Mesh(wl.sdf, wl.sizing, pts, method=2, precision=args.precision, stream=stream.cuda_stream)
+        tq = g.Mesh(wl.sdf, wl.sizing, pts, method=2, precision=args.precision, stream=stream.cuda_stream, **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = tq.step(2000)
@@ -300,7 +307,7 @@ def main():
         # FP32-position mode on the same workload
         if args.precision == 0:
             p32 = W.to_fp32_positions(wl.points)
-            fm = g.Mesh(wl.sdf, wl.sizing, p32, method=args.method, precision=1, stream=stream.cuda_stream)
+            fm = g.Mesh(wl.sdf, wl.sizing, p32, method=args.method, precision=1, stream=stream.cuda_stream, **kw)
             for _ in range(3):
                 fm.step_async(1)
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

@@ -108,6 +108,7 @@ struct HostGeometry {
     std::vector<uint8_t> cls, idist;
     std::vector<double> h, geps;
     double havg = 0;
+    double rho_eff = 0;  // point-weighted mean point density (points per unit area)
 };
 
 // Sec. 3.2 classes from the SDF at cell midpoints; Sec. 3.5 normalised
@@ -155,6 +156,16 @@ static int host_geometry(const mesh_grid2d& sdf, const mesh_grid2d& siz, int64_t
         }
     G.havg = sum_h / (double)nsel;
     for (size_t c = 0; c < nc; c++) G.geps[c] = P.fac_geps * std::min(G.h[c], G.havg);
+    // expected point density of cell c is nE_c / (dx dy) = 1 / h_c^2; weighted
+    // by the points it holds: sum h^-4 / sum h^-2 over the selected cells
+    double s2 = 0.0, s4 = 0.0;
+    for (size_t c = 0; c < nc; c++)
+        if (sel[c] && std::isfinite(G.h[c]) && G.h[c] > 0) {
+            double r = 1.0 / (G.h[c] * G.h[c]);
+            s2 += r;
+            s4 += r * r;
+        }
+    G.rho_eff = s2 > 0 ? s4 / s2 : 0.0;
     // Chebyshev distance to the nearest non-inner cell (outside the grid counts)
     std::vector<int> d(nc);
     for (int gj = 0; gj < ncy; gj++)
@@ -411,7 +422,13 @@ int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, c
     d.bx1 = sdf->x1;
     d.by1 = sdf->y1;
     double W = sdf->x1 - sdf->x0, H = sdf->y1 - sdf->y0;
+    // neighbour buckets: the paper sizes the block grid for N_opt points per
+    // block under uniform density (Sec. 3.2); with adaptive density we size it
+    // so that the bucket holding a typical point expects N_opt points
     double lam = std::sqrt((double)std::max<int64_t>(n, 1) / (P.N_opt * W * H));
+    if (G.rho_eff > 0 && n > 0) lam = std::max(lam, std::sqrt(G.rho_eff / P.N_opt));
+    double cap = std::sqrt((4.0 * (double)n + 1024.0) / (W * H));
+    lam = std::min(lam, cap);
     d.nbx = std::max(1, (int)std::ceil(lam * W));
     d.nby = std::max(1, (int)std::ceil(lam * H));
     d.bsx = W / d.nbx;

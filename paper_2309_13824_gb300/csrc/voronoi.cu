@@ -288,16 +288,19 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
         return 0;
     };
     for (int r = 1;; r++) {
-        int nr = r == 1 ? 3 : 4 * r;
+        int nr = r == 1 ? 5 : 4 * r;
         for (int kb = 0; kb < nr; kb += 32) {
             int k = kb + lane;
             int lo = 0, hi = 0;
             if (k < nr) {
                 int row, c0, c1;
                 if (r == 1) {
-                    row = byi + (k == 0 ? 0 : (k == 1 ? -1 : 1));  // own row first
-                    c0 = bxi - 1;
-                    c1 = bxi + 1;
+                    // own bucket first, then its row neighbours, then the rows below / above
+                    row = k < 3 ? byi : (k == 3 ? byi - 1 : byi + 1);
+                    c0 = k == 0 ? bxi : (k == 1 ? bxi - 1 : (k == 2 ? bxi + 1 : bxi - 1));
+                    c1 = k == 0 ? bxi : (k == 1 ? bxi - 1 : (k == 2 ? bxi + 1 : bxi + 1));
+                    if (k == 1 && c0 < 0) c0 = 1, c1 = 0;            // no bucket left of the grid
+                    if (k == 2 && c1 >= P.nbx) c0 = 1, c1 = 0;       // no bucket right of the grid
                 } else if (k < 2) {
                     row = k == 0 ? byi - r : byi + r;
                     c0 = bxi - r;
