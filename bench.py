@@ -137,6 +137,21 @@ def flush_l2(buf):
     buf.fill_(1)
 
 
+def replica_value(points_per_rank, steps, local_seconds, dist=None, device="cpu"):
+    """Aggregate throughput of independent replicas: all ranks' points x steps
+    over the slowest rank's time (max over ranks).  Returns (Mpts/s, max s)."""
+    import torch
+
+    world = 1
+    t = local_seconds
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        x = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return points_per_rank * world * steps / t / 1e6, t
+
+
 def oracle_sample_rate(wl, target_s, max_cells=None):
     """Oracle (single thread) per-cell iteration work on a random sample."""
     import oracle
@@ -236,11 +251,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
     st = mesh.step(0)
-    if dist:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = n * world * args.steps / total_s / 1e6
+    value, total_s = replica_value(n, args.steps, total_s, dist, device="cuda")
 
     # ---- per-stage device times (roofline of the dominant kernel)
     pm = g.Mesh(wl.sdf, wl.sizing, pts, method=args.method, precision=args.precision, stream=stream.cuda_stream,
