@@ -170,6 +170,24 @@ int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, d
                        double y1, int32_t nbx, int32_t nby, int32_t* bucket_start, int32_t* sorted_idx,
                        int32_t* scratch, void* cuda_stream);
 
+/* mesh_bucket_points for callers that cannot allocate device memory: the
+ * same counting sort (same arguments and outputs, all DEVICE pointers), but
+ * its scratch is a fixed 16 MiB array inside the library instead of a
+ * caller buffer, and it calls no cudaMalloc, cudaFree or allocating routine.
+ * It serves callers whose device memory belongs to another allocator (a
+ * framework pool that has reserved the GPU, where an extra cudaMalloc fails or
+ * fragments it) and callers on latency-critical loops where cudaMalloc's
+ * implicit synchronisation would stall other work.  Limit: 2*n + nbx*nby +
+ * nbx*nby/4096 + 1 <= 4194304, else TRIME_EINVAL.  The first call on each
+ * device resolves the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * on a device share the array and each call re-clears the part that must start
+ * at zero: calls that overlap on the GPU (e.g. on two streams) race.  The paper
+ * has no counterpart; asynchronous on the stream (cudaStream_t). */
+int mesh_bucket_points_noalloc(const double* x, const double* y, int64_t n, double x0, double y0, double x1,
+                               double y1, int32_t nbx, int32_t nby, int32_t* bucket_start, int32_t* sorted_idx,
+                               void* cuda_stream);
+
 /* Per-stage device timing (tracing): run n_iters iterations as separate
  * kernel launches (not the graph) with CUDA events between the stages on the
  * library's stream and ADD the elapsed milliseconds to stage_ms[0..6]:

@@ -62,7 +62,8 @@ class mesh_stats(C.Structure):
 # every symbol include/trime.h declares
 EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
-           "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step"]
+           "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step",
+           "mesh_bucket_points_noalloc"]
 
 _lib = None
 
@@ -100,9 +101,11 @@ def lib():
                                      C.c_int32, C.c_int32, vp, vp, vp, vp]
     L.mesh_exact_predicates.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.mesh_profile_step.argtypes = [vp, C.c_int32, vp]
+    L.mesh_bucket_points_noalloc.argtypes = [vp, vp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                             C.c_int32, C.c_int32, vp, vp, vp]
     for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles", "mesh_get_points",
                  "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
-                 "mesh_exact_predicates", "mesh_profile_step"):
+                 "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -142,6 +145,13 @@ def mesh_bucket_points(x, y, n, box, nbx, nby, bucket_start, sorted_idx, scratch
     """a1 on device arrays (torch CUDA tensors); asynchronous on `stream`."""
     rc = lib().mesh_bucket_points(_ptr(x), _ptr(y), n, box[0], box[1], box[2], box[3], nbx, nby,
                                   _ptr(bucket_start), _ptr(sorted_idx), _ptr(scratch), C.c_void_p(stream))
+    return _check(rc)
+
+
+def mesh_bucket_points_noalloc(x, y, n, box, nbx, nby, bucket_start, sorted_idx, stream=0):
+    """mesh_bucket_points without any device allocation (library-owned scratch)."""
+    rc = lib().mesh_bucket_points_noalloc(_ptr(x), _ptr(y), n, box[0], box[1], box[2], box[3], nbx, nby,
+                                          _ptr(bucket_start), _ptr(sorted_idx), C.c_void_p(stream))
     return _check(rc)
 
 

@@ -6,7 +6,10 @@
 // count: one atomic per point gives its bucket and rank; scan: exclusive
 // prefix over the bucket counts (three passes); scatter: each point moves its
 // whole state to bucket_start[key] + rank.  All passes are HBM-streaming.
+#include <mutex>
+
 #include "kernels.cuh"
+#include "trime.h"
 
 namespace trime {
 
@@ -257,4 +260,60 @@ void launch_bucket_raw(const double* x, const double* y, int32_t n, double x0, d
     if (g > 0) k_scatter_raw<<<g, kThreads, 0, st>>>(n, key, rank, bstart, sorted_idx);
 }
 
+// ------------------------------------------------------------------ a1 without allocation
+// Scratch of mesh_bucket_points_noalloc: a file-scope device array, so the
+// entry point never allocates.  Every GPU that loads the library holds it
+// (16 MiB) until the process exits.  In host code g_bucket_scratch names a
+// host-side stand-in, not a device address: kernels receive the address
+// resolved by cudaGetSymbolAddress below.
+constexpr size_t kNoallocScratchInts = size_t(1) << 22;
+static __device__ __align__(256) int32_t g_bucket_scratch[kNoallocScratchInts];
+
+static std::mutex g_scratch_mu;
+static int32_t* g_scratch_ptr[256];  // per device ordinal, resolved once
+
+// set-up, once per device, with that device current
+static int32_t* noalloc_scratch(int& rc) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256) {
+        rc = set_error(TRIME_ECUDA, "cudaGetDevice failed");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_bucket_scratch);
+        if (e != cudaSuccess || !p) {
+            rc = set_error(TRIME_ECUDA, "cudaGetSymbolAddress of the bucketing scratch failed");
+            return nullptr;
+        }
+        g_scratch_ptr[dev] = static_cast<int32_t*>(p);
+    }
+    return g_scratch_ptr[dev];
+}
+
 }  // namespace trime
+
+extern "C" int mesh_bucket_points_noalloc(const double* x, const double* y, int64_t n, double x0, double y0,
+                                          double x1, double y1, int32_t nbx, int32_t nby, int32_t* bucket_start,
+                                          int32_t* sorted_idx, void* cuda_stream) {
+    using namespace trime;
+    if (n < 0 || nbx < 1 || nby < 1) return set_error(TRIME_EINVAL, "n < 0 or empty bucket grid");
+    if (!(x1 > x0) || !(y1 > y0)) return set_error(TRIME_EINVAL, "empty box");
+    if (!bucket_start || (n > 0 && (!x || !y || !sorted_idx))) return set_error(TRIME_EINVAL, "NULL pointer");
+    size_t nb = (size_t)nbx * (size_t)nby;
+    size_t tiles = nb / 4096 + 1;
+    size_t need = 2 * (size_t)n + nb + tiles;
+    if ((int64_t)nbx * nby > (int64_t)4096 * 1024 || need > kNoallocScratchInts)
+        return set_error(TRIME_EINVAL, "mesh_bucket_points_noalloc: 2*n + nbx*nby + nbx*nby/4096 + 1 must not exceed "
+                                       "4194304 (its fixed 16 MiB scratch)");
+    int rc = 0;
+    int32_t* scratch = noalloc_scratch(rc);
+    if (!scratch) return rc;
+    launch_bucket_raw(x, y, (int32_t)n, x0, y0, (x1 - x0) / nbx, (y1 - y0) / nby, nbx, nby, bucket_start, sorted_idx,
+                      scratch, (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(TRIME_ECUDA, cudaGetErrorString(e));
+    return TRIME_OK;
+}

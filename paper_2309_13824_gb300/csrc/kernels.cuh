@@ -80,6 +80,9 @@ void launch_bucket_raw(const double* x, const double* y, int32_t n, double x0, d
                        int32_t nbx, int32_t nby, int32_t* bstart, int32_t* sorted_idx, int32_t* scratch,
                        cudaStream_t st);
 
+// records the calling thread's error message (mesh_last_error) and returns code
+int set_error(int code, const char* msg);
+
 constexpr int kThreads = 256;
 constexpr int kVoroThreads = 128;
 

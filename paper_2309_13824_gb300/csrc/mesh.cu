@@ -24,6 +24,10 @@ static int fail(int code, const std::string& msg) {
     return code;
 }
 
+namespace trime {
+int set_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace trime
+
 #define CUDA_TRY(x)                                                                            \
     do {                                                                                       \
         cudaError_t e_ = (x);                                                                  \
