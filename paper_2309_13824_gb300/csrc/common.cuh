@@ -26,6 +26,7 @@ struct DevGrid {
     int32_t nx, ny;
     double x0, y0, x1, y1, dx, dy;
     const float* v;
+    double idx, idy;  // 1/dx, 1/dy for the non-decision lookups of the moves
 };
 
 // Counters the device accumulates (mesh_stats fields).
@@ -110,7 +111,7 @@ __device__ __forceinline__ double bilin_fixed(const DevGrid& g, double x, double
 // bilinear value and its exact derivatives (f_xx = f_yy = 0), FMAs allowed
 template <typename T>
 __device__ __forceinline__ void bilin_grad(const DevGrid& g, T x, T y, T& f, T& fx_, T& fy_, T& fxy) {
-    T tx = (x - (T)g.x0) / (T)g.dx, ty = (y - (T)g.y0) / (T)g.dy;
+    T tx = (x - (T)g.x0) * (T)g.idx, ty = (y - (T)g.y0) * (T)g.idy;
     T fi = floor(tx), fj = floor(ty);
     int i = !(fi >= (T)0) ? 0 : (fi > (T)(g.nx - 2) ? g.nx - 2 : (int)fi);
     int j = !(fj >= (T)0) ? 0 : (fj > (T)(g.ny - 2) ? g.ny - 2 : (int)fj);
@@ -124,15 +125,15 @@ __device__ __forceinline__ void bilin_grad(const DevGrid& g, T x, T y, T& f, T& 
     T b = v01 + fx * (v11 - v01);
     f = a + fy * (b - a);
     T d0 = v10 - v00, d1 = v11 - v01;
-    fx_ = (d0 + fy * (d1 - d0)) / (T)g.dx;
-    fy_ = (b - a) / (T)g.dy;
-    fxy = (d1 - d0) / ((T)g.dx * (T)g.dy);
+    fx_ = (d0 + fy * (d1 - d0)) * (T)g.idx;
+    fy_ = (b - a) * (T)g.idy;
+    fxy = (d1 - d0) * ((T)g.idx * (T)g.idy);
 }
 
 // bilinear value in precision T (FMAs allowed): used for the moves
 template <typename T>
 __device__ __forceinline__ T bilin(const DevGrid& g, T x, T y) {
-    T tx = (x - (T)g.x0) / (T)g.dx, ty = (y - (T)g.y0) / (T)g.dy;
+    T tx = (x - (T)g.x0) * (T)g.idx, ty = (y - (T)g.y0) * (T)g.idy;
     T fi = floor(tx), fj = floor(ty);
     int i = !(fi >= (T)0) ? 0 : (fi > (T)(g.nx - 2) ? g.nx - 2 : (int)fi);
     int j = !(fj >= (T)0) ? 0 : (fj > (T)(g.ny - 2) ? g.ny - 2 : (int)fj);
@@ -162,7 +163,7 @@ __device__ __forceinline__ bool point_cell_fixed(const DevGrid& s, double x, dou
 // same lookup in precision T (approximate near cell edges): used by the moves
 template <typename T>
 __device__ __forceinline__ bool point_cell_t(const DevGrid& s, T x, T y, int& gi, int& gj) {
-    T tx = (x - (T)s.x0) / (T)s.dx, ty = (y - (T)s.y0) / (T)s.dy;
+    T tx = (x - (T)s.x0) * (T)s.idx, ty = (y - (T)s.y0) * (T)s.idy;
     T fi = floor(tx), fj = floor(ty);
     int ncx = s.nx - 1, ncy = s.ny - 1;
     bool inside = fi >= (T)0 && fi <= (T)(ncx - 1) && fj >= (T)0 && fj <= (T)(ncy - 1);

@@ -78,6 +78,15 @@ __device__ bool valid_fixed(const IterArgs<T>& a, const Tri& t) {
 struct Nbr {
     int slot, id, cell;
     float dx, dy;  // relative to the cell's generator
+    float S;       // octagon span at the neighbour's geometry cell
+};
+
+// per-cell constants shared by all the cell's triangles
+struct CellC {
+    float S;               // octagon span of the generator
+    float lx, hx, ly, hy;  // domain box relative to the generator
+    float tx, ty;          // generator's grid coordinates (x - x0) / dx
+    float idx, idy;        // 1 / dx, 1 / dy
 };
 
 template <typename T>
@@ -90,41 +99,40 @@ __device__ __forceinline__ Nbr load_nbr(const IterArgs<T>& a, int lab, T xi, T y
         n.cell = a.cell[lab];
         n.dx = (float)(x - xi);
         n.dy = (float)(y - yi);
+        n.S = (float)(a.P.fac_voro_bound * a.gh[n.cell]);
     } else {
         n.id = 0;
         n.cell = 0;
         n.dx = n.dy = 0.f;
+        n.S = 0.f;
     }
     return n;
 }
 
 // emission decision for (i, j, k), CCW as seen from cell i
 template <typename T>
-__device__ bool emitted(const IterArgs<T>& a, int si, int idi, int ci, T xi, T yi, const Nbr& j, const Nbr& k) {
+__device__ bool emitted(const IterArgs<T>& a, const CellC& cc, int idi, int ci, T xi, T yi, const Nbr& j,
+                        const Nbr& k) {
     const DevParams& P = a.P;
     float ax = j.dx, ay = j.dy, bx = k.dx, by = k.dy;
     float M = ax * by - ay * bx;
     float PM = fabsf(ax * by) + fabsf(ay * bx);
     if (M > 64.0f * kEpsF * PM && PM > 1e-30f) {
         float al = ax * ax + ay * ay, bl = bx * bx + by * by;
-        float ux = (al * by - bl * ay) / (2.0f * M), uy = (bl * ax - al * bx) / (2.0f * M);
+        float i2M = 0.5f / M;
+        float ux = (al * by - bl * ay) * i2M, uy = (bl * ax - al * bx) * i2M;
         float un = fabsf(ux) + fabsf(uy);
-        float eu = 64.0f * kEpsF * ((al * fabsf(by) + bl * fabsf(ay)) + (bl * fabsf(ax) + al * fabsf(bx)) + 2.0f * un * PM) /
-                   (2.0f * M);
+        float eu = 64.0f * kEpsF * ((al * fabsf(by) + bl * fabsf(ay)) + (bl * fabsf(ax) + al * fabsf(bx)) + 2.0f * un * PM) *
+                   i2M;
         int state = 1;  // 1 inside, 0 outside, 2 undecided
-        // domain box, relative to p_i
-        float lx = (float)(P.bx0 - (double)xi), hx = (float)(P.bx1 - (double)xi);
-        float ly = (float)(P.by0 - (double)yi), hy = (float)(P.by1 - (double)yi);
-        float mgb = eu + 4.0f * kEpsF * (un + fabsf(lx) + fabsf(hx) + fabsf(ly) + fabsf(hy)) + 1e-7f;
-        float bo = fmaxf(fmaxf(lx - ux, ux - hx), fmaxf(ly - uy, uy - hy));  // > 0 outside
+        float mgb = eu + 4.0f * kEpsF * (un + fabsf(cc.lx) + fabsf(cc.hx) + fabsf(cc.ly) + fabsf(cc.hy)) + 1e-7f;
+        float bo = fmaxf(fmaxf(cc.lx - ux, ux - cc.hx), fmaxf(cc.ly - uy, uy - cc.hy));  // > 0 outside
         if (bo > mgb) state = 0;
         else if (bo > -mgb) state = 2;
         if (state != 0 && P.bounded) {
-            const Nbr* V[2] = {&j, &k};
             for (int v = 0; v < 3 && state != 0; v++) {
-                float dvx = v == 0 ? 0.f : V[v - 1]->dx, dvy = v == 0 ? 0.f : V[v - 1]->dy;
-                int cv = v == 0 ? ci : V[v - 1]->cell;
-                float S = (float)(P.fac_voro_bound * a.gh[cv]);
+                float dvx = v == 0 ? 0.f : (v == 1 ? j.dx : k.dx), dvy = v == 0 ? 0.f : (v == 1 ? j.dy : k.dy);
+                float S = v == 0 ? cc.S : (v == 1 ? j.S : k.S);
                 float wx = ux - dvx, wy = uy - dvy;
                 float f = fmaxf(fmaxf(fabsf(wx), fabsf(wy)), 0.70710678f * fmaxf(fabsf(wx + wy), fabsf(wy - wx)));
                 float mg = eu + 4.0f * kEpsF * (un + fabsf(dvx) + fabsf(dvy)) + 1e-6f * S;
@@ -151,13 +159,29 @@ __device__ bool emitted(const IterArgs<T>& a, int si, int idi, int ci, T xi, T y
 }
 
 template <typename T>
-__device__ bool valid_tri(const IterArgs<T>& a, int idi, int ci, T xi, T yi, const Nbr& j, const Nbr& k) {
+__device__ bool valid_tri(const IterArgs<T>& a, const CellC& cc, int idi, int ci, T xi, T yi, const Nbr& j,
+                          const Nbr& k) {
     if (!a.P.validity) return true;
-    // Test 1 shortcut: the centroid's cell is within a few cells of p_i's cell,
-    // and every cell closer than gidist is inner
+    // Test 1 shortcuts: (a) every cell within gidist of p_i's cell is inner
     float gx = (j.dx + k.dx) * (1.0f / 3.0f), gy = (j.dy + k.dy) * (1.0f / 3.0f);
-    float off = fmaxf(fabsf(gx) * (float)(1.0 / a.sdf.dx), fabsf(gy) * (float)(1.0 / a.sdf.dy));
+    float offx = gx * cc.idx, offy = gy * cc.idy;
+    float off = fmaxf(fabsf(offx), fabsf(offy));
     if (off + 2.01f < (float)a.gidist[ci]) return true;
+    // (b) the centroid's cell is certain and not a boundary cell: the float
+    // grid coordinate errs by at most two roundings (2^-23 |t|) plus the
+    // offset's error, far below em, so a coordinate more than em away from an
+    // integer has the same floor as the fixed FP64 formula
+    float tx = cc.tx + offx, ty = cc.ty + offy;
+    float fx = tx - floorf(tx), fy = ty - floorf(ty);
+    float emx = 2.5e-7f * fabsf(tx) + 1e-4f, emy = 2.5e-7f * fabsf(ty) + 1e-4f;
+    int ncx = a.sdf.nx - 1, ncy = a.sdf.ny - 1;
+    if (fx > emx && fx < 1.0f - emx && fy > emy && fy < 1.0f - emy) {
+        int gi = (int)floorf(tx), gj = (int)floorf(ty);
+        if (gi < 0 || gj < 0 || gi >= ncx || gj >= ncy) return false;
+        uint8_t c = a.gcls[gj * ncx + gi];
+        if (c == CELL_INNER) return true;
+        if (c == CELL_OUTER) return false;
+    }
     int ids[3] = {idi, j.id, k.id};
     double xs[3] = {(double)xi, (double)a.srt.x[j.slot], (double)a.srt.x[k.slot]};
     double ys[3] = {(double)yi, (double)a.srt.y[j.slot], (double)a.srt.y[k.slot]};
@@ -209,34 +233,56 @@ __global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
         int ci = a.cell[s];
         uint32_t vm = 0;
         if (ne >= 2) {
+            CellC cc;
+            cc.S = (float)(a.P.fac_voro_bound * a.gh[ci]);
+            double xd = (double)xi, yd = (double)yi;
+            cc.lx = (float)(a.P.bx0 - xd);
+            cc.hx = (float)(a.P.bx1 - xd);
+            cc.ly = (float)(a.P.by0 - yd);
+            cc.hy = (float)(a.P.by1 - yd);
+            cc.tx = (float)((xd - a.sdf.x0) * a.sdf.idx);
+            cc.ty = (float)((yd - a.sdf.y0) * a.sdf.idy);
+            cc.idx = (float)a.sdf.idx;
+            cc.idy = (float)a.sdf.idy;
+            float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f, q5 = 180.f;
             Nbr first = load_nbr(a, lab[0], xi, yi);
             Nbr cur = first;
             for (int t = 0; t < ne; t++) {
                 Nbr nxt = t + 1 < ne ? load_nbr(a, lab[t + 1], xi, yi) : first;
-                if (cur.slot >= 0 && nxt.slot >= 0 && emitted(a, s, idi, ci, xi, yi, cur, nxt) &&
-                    valid_tri(a, idi, ci, xi, yi, cur, nxt)) {
+                if (cur.slot >= 0 && nxt.slot >= 0 && emitted(a, cc, idi, ci, xi, yi, cur, nxt) &&
+                    valid_tri(a, cc, idi, ci, xi, yi, cur, nxt)) {
                     vm |= 1u << t;
                     if (idi < cur.id && idi < nxt.id) {
                         // quality of the triangle (Eq. 11), float from the relative coordinates
                         float bx = cur.dx, by = cur.dy, cx = nxt.dx, cy = nxt.dy;
-                        float la = hypotf(bx - cx, by - cy), lb = hypotf(cx, cy), lc = hypotf(bx, by);
+                        float la = sqrtf((bx - cx) * (bx - cx) + (by - cy) * (by - cy));
+                        float lb = sqrtf(cx * cx + cy * cy), lc = sqrtf(bx * bx + by * by);
                         float A2 = fabsf(bx * cy - by * cx);
                         float alpha = (la * lb * lc * (la + lb + lc)) / (4.0f * A2 * A2);
                         float lmax = fmaxf(la, fmaxf(lb, lc)), lmin = fminf(la, fminf(lb, lc));
-                        float p = lmin == la ? lb : la, q = lmin == lc ? lb : lc;
-                        if (lmin == lb) { p = la; q = lc; }
+                        // the smallest angle is opposite the shortest side
+                        float p = la, q = lb;
+                        if (lmin == la) { p = lb; q = lc; }
+                        else if (lmin == lb) { p = la; q = lc; }
                         float cs = (p * p + q * q - lmin * lmin) / (2.0f * p * q);
                         cs = fminf(1.0f, fmaxf(-1.0f, cs));
-                        acc[0] += 1.0;
-                        acc[1] += sqrt((double)alpha);
-                        acc[2] += sqrt((double)(lmax / lmin));
-                        acc[3] = fmax(acc[3], (double)alpha);
-                        acc[4] = fmax(acc[4], (double)(lmax / lmin));
-                        acc[5] = fmin(acc[5], (double)acosf(cs) * (180.0 / 3.14159265358979323846));
+                        float beta = lmax / lmin;
+                        q0 += 1.0f;
+                        q1 += sqrtf(alpha);
+                        q2 += sqrtf(beta);
+                        q3 = fmaxf(q3, alpha);
+                        q4 = fmaxf(q4, beta);
+                        q5 = fminf(q5, acosf(cs) * (180.0f / 3.14159265f));
                     }
                 }
                 cur = nxt;
             }
+            acc[0] = q0;
+            acc[1] = q1;
+            acc[2] = q2;
+            acc[3] = q3;
+            acc[4] = q4;
+            acc[5] = q5;
             // valid edges (Eq. 3 sums), counted by the smaller id
             for (int t = 0; t < ne; t++) {
                 int j = lab[t];
@@ -249,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
                 T mu = bilin<T>(a.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
                 acc[6] += 1.0;
                 acc[7] += (double)(dx * dx + dy * dy);
-                acc[8] += (double)(mu * mu);
+                acc[8] += (double)(mu * mu);  // Eq. 3 sums stay in T precision
             }
         }
         a.vmask[s] = vm;

@@ -485,10 +485,14 @@ int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, c
     if (rc) return bail(rc);
 
     m->sdf = {sdf->nx, sdf->ny, sdf->x0, sdf->y0, sdf->x1, sdf->y1, (sdf->x1 - sdf->x0) / (double)(sdf->nx - 1),
-              (sdf->y1 - sdf->y0) / (double)(sdf->ny - 1), dsdf};
+              (sdf->y1 - sdf->y0) / (double)(sdf->ny - 1), dsdf, 0.0, 0.0};
     m->siz = {sizing->nx, sizing->ny, sizing->x0, sizing->y0, sizing->x1, sizing->y1,
               (sizing->x1 - sizing->x0) / (double)(sizing->nx - 1),
-              (sizing->y1 - sizing->y0) / (double)(sizing->ny - 1), dsiz};
+              (sizing->y1 - sizing->y0) / (double)(sizing->ny - 1), dsiz, 0.0, 0.0};
+    m->sdf.idx = 1.0 / m->sdf.dx;
+    m->sdf.idy = 1.0 / m->sdf.dy;
+    m->siz.idx = 1.0 / m->siz.dx;
+    m->siz.idy = 1.0 / m->siz.dy;
     auto H2D = [&](void* dst, const void* src, size_t bytes) {
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, m->st) == cudaSuccess;
     };

@@ -155,7 +155,7 @@ __device__ void level_sum(const IterArgs<T>& a, T gx, T gy, T v1x, T v1y, T v2x,
         int d = sd[sp];
         if (d == 0) {
             T A = (T)0.5 * ((q1x - q0x) * (q2y - q0y) - (q1y - q0y) * (q2x - q0x));
-            T cx = (q0x + q1x + q2x) / (T)3, cy = (q0y + q1y + q2y) / (T)3;
+            T cx = (q0x + q1x + q2x) * (T)(1.0 / 3.0), cy = (q0y + q1y + q2y) * (T)(1.0 / 3.0);
             T mu = bilin<T>(a.siz, gx + cx, gy + cy);
             T w = A / (mu * mu);
             W += w;
@@ -246,9 +246,10 @@ __device__ void cvd_centroid(const IterArgs<T>& a, int s, int ne, const int* lab
             level_sum<T>(a, xi, yi, vx[t], vy[t], vx[u], vy[u], k - 1, W, WX, WY);
         }
         if (!(W > 0)) return;
-        T ccx = WX / W, ccy = WY / W;
+        T iW = (T)1 / W;
+        T ccx = WX * iW, ccy = WY * iW;
         T dx = ccx - px, dy = ccy - py;
-        bool conv = sqrt(dx * dx + dy * dy) < E;
+        bool conv = dx * dx + dy * dy < E * E;
         if (conv || k == Lmax) {
             cx = xi + ccx;
             cy = yi + ccy;
@@ -313,15 +314,16 @@ __global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
             T l = sqrt(dx * dx + dy * dy);
             T mu = bilin<T>(a.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
             if (idi < a.srt.id[j]) {
-                dev += (double)fabs(l / (fac_mu * mu) - (T)1);
+                dev += (double)fabsf((float)l / ((float)fac_mu * (float)mu) - 1.0f);
                 nedge += 1.0;
             }
             if (method != 0) continue;
             T l0 = (T)P.fac_F * fac_mu * mu;
             if (l < l0) {
                 T f = (T)P.k_spring * (l0 - l);
-                Fx += f * dx / l;
-                Fy += f * dy / l;
+                T fl = f / l;
+                Fx += fl * dx;
+                Fy += fl * dy;
                 fs += f;
             }
         }
