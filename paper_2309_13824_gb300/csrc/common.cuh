@@ -58,6 +58,8 @@ struct DevCtrl {
     int32_t have_prev;
     int32_t small_moves;
     int32_t last_method;
+    int32_t ovf_n;          // cells queued for the 32-lane Voronoi pass
+    int32_t pad0;
     double prev_a, prev_b, prev_amax;
     double fac_mu;
     double n_tri, n_edges, half_a, half_b, max_a, max_b, min_ang, size_dev;

@@ -52,6 +52,7 @@ struct IterArgs {
     UpdatePartial* up;
     DevCtrl* ctrl;
     double* dbg;       // [8][n] by original id, written when P.debug
+    int32_t* ovf_list; // [n] cells whose 16-lane clipping ran out of lanes
 };
 
 // a1: counting sort

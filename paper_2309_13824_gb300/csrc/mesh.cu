@@ -63,6 +63,7 @@ struct mesh_s {
     DevCtrl* hctrl = nullptr;  // pinned host copy
     double* dbg = nullptr;
     int32_t *tcnt = nullptr, *toff = nullptr, *tbuf = nullptr;
+    int32_t* ovf_list = nullptr;
     void* xybuf = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<void*> allocs;
@@ -236,6 +237,7 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.up = m->up;
     a.ctrl = m->ctrl;
     a.dbg = m->dbg;
+    a.ovf_list = m->ovf_list;
     return a;
 }
 
@@ -482,6 +484,7 @@ int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, c
     m->toff = dalloc<int32_t>(m, N + 1, rc);
     m->tbuf = dalloc<int32_t>(m, 3 * (2 * N + 16), rc);
     m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
+    m->ovf_list = dalloc<int32_t>(m, N, rc);
     if (rc) return bail(rc);
 
     m->sdf = {sdf->nx, sdf->ny, sdf->x0, sdf->y0, sdf->x1, sdf->y1, (sdf->x1 - sdf->x0) / (double)(sdf->nx - 1),

@@ -2,14 +2,18 @@
 // clipping (TriMe++ Sec. 2.1 Fig. 3, cell-based approach; Sec. 4.1 octagon
 // bound of span S = fac_voro_bound * h_i).
 //
-// One warp per cell.  The convex polygon lives in the warp, one edge per lane
-// (<= 32 edges): lane t holds edge E_t as a half-plane n.u <= s (u relative to
-// the generator) and the vertex V_t = E_t cap E_{t+1}.  Candidates come from
-// the bucket grid ring by ring, are loaded one per lane, filtered by the
-// security radius (a point farther than twice the largest vertex distance
-// cannot cut) and applied nearest first.  A clip classifies every vertex in
-// parallel, finds the single run of cut vertices with two ballots and
-// rotates the edge list with shuffles.
+// A group of G lanes clips one cell: the convex polygon lives in the group,
+// one edge per lane: lane t holds edge E_t as a half-plane n.u <= s (u
+// relative to the generator) and the vertex V_t = E_t cap E_{t+1}.  The main
+// pass uses G = 16 (two cells per warp; final cells have 6-8 edges); a cell
+// that would need more than 16 edges is queued and redone with G = 32 by the
+// same code.  Candidates come from the bucket grid ring by ring, one per lane,
+// are filtered by the security radius (a point farther than twice the largest
+// vertex distance cannot cut), staged in shared memory and applied nearest
+// first across the staged set.  A clip classifies every vertex in parallel,
+// finds the single run of cut vertices with two ballots and rotates the edge
+// list with shuffles.  Every collective operation is executed by the whole
+// warp; a group with nothing to do runs it as a no-op.
 //
 // Exactness: a vertex where two bisectors meet is the circumcentre of
 // (i, j, k); the candidate l cuts it iff det4(i,j,k,l) > 0 (l inside that
@@ -26,7 +30,28 @@ namespace trime {
 
 constexpr float kEps = 5.9604645e-8f;  // 2^-24
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kStageCap = 160;  // staged candidates per warp (16 bytes each)
+constexpr int kStageCap = 96;  // staged candidates per group (16 bytes each)
+
+template <int G>
+struct Grp {
+    int gl;    // lane inside the group
+    int goff;  // first warp lane of the group
+    __device__ unsigned ballot(bool p) const {
+        unsigned b = __ballot_sync(kFull, p);
+        return G == 32 ? b : (b >> goff) & ((1u << G) - 1u);
+    }
+    template <typename V>
+    __device__ V shfl(V v, int src) const {
+        return __shfl_sync(kFull, v, src, G);
+    }
+    __device__ float max(float v) const {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+        return v;
+    }
+};
+
+__device__ __forceinline__ bool warp_any(bool p) { return __any_sync(kFull, p); }
 
 struct Lane {
     float nx, ny, s;      // edge half-plane n.u <= s
@@ -41,11 +66,12 @@ struct Lane {
 __device__ __forceinline__ void make_vertex(Lane& L, float nx2, float ny2, float s2, int lab2, float RB) {
     float D = L.nx * ny2 - L.ny * nx2;
     float px = L.s * ny2 - s2 * L.ny, py = s2 * L.nx - L.s * nx2;
-    float ux = px / D, uy = py / D;
+    float iD = 1.0f / D;
+    float ux = px * iD, uy = py * iD;
     float r = sqrtf(ux * ux + uy * uy);
     float perm = fabsf(L.s * ny2) + fabsf(s2 * L.ny) + fabsf(s2 * L.nx) + fabsf(L.s * nx2) +
                  r * (fabsf(L.nx * ny2) + fabsf(L.ny * nx2));
-    float err = 64.0f * kEps * perm / fabsf(D);
+    float err = 64.0f * kEps * perm * fabsf(iD);
     bool ok = (D != 0.0f) && (r + err < RB);  // false for NaN as well
     L.vR = ok ? r + err : RB;
     L.vx = ok ? ux : 0.0f;
@@ -65,12 +91,13 @@ __device__ __forceinline__ void make_vertex(Lane& L, float nx2, float ny2, float
 }
 
 // vertex of this lane with the next lane's edge (all lanes participate)
-__device__ __forceinline__ void lane_vertex(Lane& L, int ne, int lane, float RB, bool active) {
-    int nxt = lane + 1 >= ne ? 0 : lane + 1;
-    float nx2 = __shfl_sync(kFull, L.nx, nxt), ny2 = __shfl_sync(kFull, L.ny, nxt);
-    float s2 = __shfl_sync(kFull, L.s, nxt);
-    int lab2 = __shfl_sync(kFull, L.lab, nxt);
-    if (active && lane < ne) make_vertex(L, nx2, ny2, s2, lab2, RB);
+template <int G>
+__device__ __forceinline__ void lane_vertex(Lane& L, int ne, const Grp<G>& g, float RB, bool active) {
+    int nxt = g.gl + 1 >= ne ? 0 : g.gl + 1;
+    float nx2 = g.shfl(L.nx, nxt), ny2 = g.shfl(L.ny, nxt);
+    float s2 = g.shfl(L.s, nxt);
+    int lab2 = g.shfl(L.lab, nxt);
+    if (active && g.gl < ne) make_vertex(L, nx2, ny2, s2, lab2, RB);
 }
 
 template <typename T>
@@ -109,13 +136,14 @@ __device__ __noinline__ bool exact_cut(const CellCtx<T>& c, int sj, int sk, int 
     return d * o > 0;
 }
 
-// Clip the warp's polygon by n.u <= s (label lab).  bisector: a neighbour's
-// bisector (n = d, s = |d|^2/2).  Returns 0 ok, 1 empty, 2 overflow.
-template <typename T>
-__device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, bool bisector, float RB, int lane,
-                       const CellCtx<T>& ctx) {
+// Clip the group's polygon by n.u <= s (label lab) when `active`; bisector:
+// a neighbour's bisector (n = d, s = |d|^2/2).  Executed by every lane of the
+// warp.  Returns 0 ok / no-op, 1 empty cell, 2 more than G edges.
+template <typename T, int G>
+__device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, bool bisector, bool active, float RB,
+                       const Grp<G>& g, const CellCtx<T>& ctx) {
     bool cut = false;
-    if (lane < ne) {
+    if (active && g.gl < ne) {
         if (bisector && L.bb) {
             float cl = 2.0f * s;
             float lam = fmaf(nx, L.Qx, fmaf(ny, L.Qy, cl * L.M));
@@ -128,68 +156,71 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
             cut = nx * L.vx + ny * L.vy > s;
         }
     }
-    unsigned m = __ballot_sync(kFull, cut);
-    if (m == 0) return 0;
+    unsigned m = g.ballot(cut);
     unsigned full = ne >= 32 ? kFull : ((1u << ne) - 1u);
-    if ((m & full) == full) return 1;
-    int prevl = lane == 0 ? ne - 1 : lane - 1;
+    int status = 0;
+    bool doit = active && m != 0;
+    if (doit && (m & full) == full) {
+        status = 1;
+        doit = false;
+    }
+    int prevl = g.gl == 0 ? ne - 1 : g.gl - 1;
     bool pcut = (m >> (prevl & 31)) & 1u;
-    unsigned starts = __ballot_sync(kFull, lane < ne && cut && !pcut);
-    unsigned ends = __ballot_sync(kFull, lane < ne && !cut && pcut);
-    if (__popc(starts) != 1 && lane == 0) atomicAdd(&ctx.ctrl->cnt.clip_inconsistent, 1ull);
-    int sidx = __ffs(starts) - 1;
+    unsigned starts = g.ballot(g.gl < ne && cut && !pcut);
+    unsigned ends = g.ballot(g.gl < ne && !cut && pcut);
+    if (doit && __popc(starts) != 1 && g.gl == 0) atomicAdd(&ctx.ctrl->cnt.clip_inconsistent, 1ull);
+    int sidx = starts ? __ffs(starts) - 1 : 0;
     unsigned after = sidx >= 31 ? 0u : (ends >> (sidx + 1)) << (sidx + 1);
-    int eidx = after ? __ffs(after) - 1 : __ffs(ends) - 1;
-    int k = (sidx - eidx + ne) % ne + 1;  // kept edges E_e .. E_s
+    int eidx = after ? __ffs(after) - 1 : (ends ? __ffs(ends) - 1 : 0);
+    int k = ne > 0 ? (sidx - eidx + ne) % ne + 1 : 1;  // kept edges E_e .. E_s
     int nn = k + 1;
-    if (nn > kRingCap) return 2;
-    int src = (eidx + lane) % ne;
+    if (doit && nn > G) {
+        status = 2;
+        doit = false;
+    }
+    int src = doit ? (eidx + g.gl) % ne : g.gl;
     Lane R;
-    R.nx = __shfl_sync(kFull, L.nx, src);
-    R.ny = __shfl_sync(kFull, L.ny, src);
-    R.s = __shfl_sync(kFull, L.s, src);
-    R.lab = __shfl_sync(kFull, L.lab, src);
-    R.vx = __shfl_sync(kFull, L.vx, src);
-    R.vy = __shfl_sync(kFull, L.vy, src);
-    R.vR = __shfl_sync(kFull, L.vR, src);
-    R.nlab = __shfl_sync(kFull, L.nlab, src);
-    R.bb = __shfl_sync(kFull, (int)L.bb, src) != 0;
-    R.Qx = __shfl_sync(kFull, L.Qx, src);
-    R.Qy = __shfl_sync(kFull, L.Qy, src);
-    R.M = __shfl_sync(kFull, L.M, src);
-    R.PQx = __shfl_sync(kFull, L.PQx, src);
-    R.PQy = __shfl_sync(kFull, L.PQy, src);
-    R.PM = __shfl_sync(kFull, L.PM, src);
-    if (lane < k) L = R;
-    if (lane == k) {
+    R.nx = g.shfl(L.nx, src);
+    R.ny = g.shfl(L.ny, src);
+    R.s = g.shfl(L.s, src);
+    R.lab = g.shfl(L.lab, src);
+    R.vx = g.shfl(L.vx, src);
+    R.vy = g.shfl(L.vy, src);
+    R.vR = g.shfl(L.vR, src);
+    R.nlab = g.shfl(L.nlab, src);
+    R.bb = g.shfl((int)L.bb, src) != 0;
+    R.Qx = g.shfl(L.Qx, src);
+    R.Qy = g.shfl(L.Qy, src);
+    R.M = g.shfl(L.M, src);
+    R.PQx = g.shfl(L.PQx, src);
+    R.PQy = g.shfl(L.PQy, src);
+    R.PM = g.shfl(L.PM, src);
+    if (doit && g.gl < k) L = R;
+    if (doit && g.gl == k) {
         L.nx = nx;
         L.ny = ny;
         L.s = s;
         L.lab = lab;
     }
-    ne = nn;
-    lane_vertex(L, ne, lane, RB, lane == k - 1 || lane == k);
-    return 0;
+    if (doit) ne = nn;
+    lane_vertex<G>(L, ne, g, RB, doit && (g.gl == k - 1 || g.gl == k));
+    return status;
 }
 
-template <typename T>
-__device__ __forceinline__ void finish_cell(const IterArgs<T>& a, int s, int lane, const Lane& L, int ne, float R) {
-    if (lane < ne) a.ring[(size_t)s * kRingCap + lane] = L.lab;
-    if (lane == 0) {
-        a.ring_n[s] = (uint8_t)ne;
-        a.cellR[s] = R;
-    }
-}
-
-template <typename T>
-__device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
+// one cell per group; slot < 0 marks an idle group (it still takes part in
+// every collective operation of its warp)
+template <typename T, int G>
+__device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, float4* stage) {
     const DevParams& P = a.P;
-    if (a.dom[s]) {
-        if (lane == 0) {
+    const float INF = __int_as_float(0x7f800000);
+    bool live = slot >= 0;
+    int s = live ? slot : 0;
+    if (live && a.dom[s]) {
+        if (g.gl == 0) {
             a.ring_n[s] = 0;
             a.cellR[s] = 0.0f;
         }
-        return;
+        live = false;
     }
     T xi = a.srt.x[s], yi = a.srt.y[s];
     CellCtx<T> ctx;
@@ -205,6 +236,9 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
     Lane L;
     L.bb = false;
     L.vR = 0.0f;
+    L.vx = L.vy = 0.0f;
+    L.nlab = -1;
+    L.M = L.Qx = L.Qy = L.PM = L.PQx = L.PQy = 0.0f;
     int ne;
     if (P.bounded) {
         float S = (float)(P.fac_voro_bound * a.gh[a.cell[s]]);
@@ -212,7 +246,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
         RB = SB * 1.0824459f * 1.0001f;  // octagon circumradius SB / cos(pi/8)
         mb = S * (1.0f / 16.0f);
         const float c8[8] = {1.f, 0.70710678f, 0.f, -0.70710678f, -1.f, -0.70710678f, 0.f, 0.70710678f};
-        int t = lane & 7;
+        int t = g.gl & 7;
         L.nx = c8[t];
         L.ny = c8[(t + 6) & 7];
         L.s = SB;
@@ -222,43 +256,41 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
         mb = (float)(0.125 * (W > H ? W : H));
         RB = (float)((sqrt(W * W + H * H) + 4.0 * mb) * 1.0001);
         ne = 4;  // enlarged box, CCW: bottom, right, top, left
-        int b = lane & 3;
-        const int bside[4] = {2, 1, 3, 0};
-        int bs = bside[b];
+        int b = g.gl & 3;
+        int bs = b == 0 ? 2 : (b == 1 ? 1 : (b == 2 ? 3 : 0));
         L.nx = bs == 0 ? -1.f : (bs == 1 ? 1.f : 0.f);
         L.ny = bs == 2 ? -1.f : (bs == 3 ? 1.f : 0.f);
         L.s = bs == 0 ? (float)(ctx.pix - (P.bx0 - mb)) : bs == 1 ? (float)((P.bx1 + mb) - ctx.pix)
             : bs == 2 ? (float)(ctx.piy - (P.by0 - mb)) : (float)((P.by1 + mb) - ctx.piy);
         L.lab = box_label(bs);
     }
-    lane_vertex(L, ne, lane, RB, true);
+    lane_vertex<G>(L, ne, g, RB, true);
+    int status = 0;
     if (P.bounded) {
         for (int b = 0; b < 4; b++) {
             float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
             float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
             float sb = b == 0 ? (float)(ctx.pix - (P.bx0 - mb)) : b == 1 ? (float)((P.bx1 + mb) - ctx.pix)
                      : b == 2 ? (float)(ctx.piy - (P.by0 - mb)) : (float)((P.by1 + mb) - ctx.piy);
-            clip_by<T>(L, ne, nx, ny, sb, box_label(b), false, RB, lane, ctx);
+            int st = clip_by<T, G>(L, ne, nx, ny, sb, box_label(b), false, live && status == 0, RB, g, ctx);
+            if (st) status = st;
         }
     }
-    float Rmax = warp_max(lane < ne ? L.vR : 0.0f);
+    float Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
     int bxi, byi;
     bucket_of(P, xi, yi, bxi, byi);
     const float xf = (float)(ctx.pix - P.bx0), yf = (float)(ctx.piy - P.by0);
     const float bsx = (float)P.bsx, bsy = (float)P.bsy;
     const float bmargin = (float)(1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy)) + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
-    const float INF = __int_as_float(0x7f800000);
-    // per-warp staging buffer: candidates of the current ring, applied
-    // nearest first across the whole staged set
-    __shared__ float4 stage_all[kVoroThreads / 32][kStageCap];
-    float4* stage = stage_all[threadIdx.x >> 5];
+    bool done = !live || status != 0;
     int nst = 0;
-    auto flush = [&]() -> int {
+    // apply the staged candidates nearest first (warp-uniform loop)
+    auto flush = [&]() {
         while (true) {
             float best = INF;
             int bi = -1;
             float lim = 4.0f * Rmax * Rmax * 1.0001f;
-            for (int q = lane; q < nst; q += 32) {
+            for (int q = g.gl; q < nst; q += G) {
                 float d2 = stage[q].z;
                 if (d2 < lim && d2 < best) {
                     best = d2;
@@ -266,7 +298,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
                 }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = G / 2; o > 0; o >>= 1) {
                 float ob = __shfl_xor_sync(kFull, best, o);
                 int oi = __shfl_xor_sync(kFull, bi, o);
                 if (ob < best || (ob == best && oi < bi)) {
@@ -274,33 +306,37 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
                     bi = oi;
                 }
             }
-            if (bi < 0) break;
-            float4 c = stage[bi];
+            bool has = !done && bi >= 0;
+            if (!warp_any(has)) break;
+            float4 c = has ? stage[bi] : make_float4(0.f, 0.f, 1.f, 0.f);
             __syncwarp();
-            if (lane == 0) stage[bi].z = INF;
+            if (has && g.gl == 0) stage[bi].z = INF;
             __syncwarp();
-            int st = clip_by<T>(L, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, RB, lane, ctx);
-            if (st) return st;
-            Rmax = warp_max(lane < ne ? L.vR : 0.0f);
+            int st = clip_by<T, G>(L, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, has, RB, g, ctx);
+            if (st) {
+                status = st;
+                done = true;
+                nst = 0;
+            }
+            Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
         }
         nst = 0;
         __syncwarp();
-        return 0;
     };
-    for (int r = 1;; r++) {
+    for (int r = 1; warp_any(!done); r++) {
         int nr = r == 1 ? 5 : 4 * r;
-        for (int kb = 0; kb < nr; kb += 32) {
-            int k = kb + lane;
+        for (int kb = 0; kb < nr; kb += G) {
+            int k = kb + g.gl;
             int lo = 0, hi = 0;
-            if (k < nr) {
+            if (!done && k < nr) {
                 int row, c0, c1;
                 if (r == 1) {
                     // own bucket first, then its row neighbours, then the rows below / above
                     row = k < 3 ? byi : (k == 3 ? byi - 1 : byi + 1);
                     c0 = k == 0 ? bxi : (k == 1 ? bxi - 1 : (k == 2 ? bxi + 1 : bxi - 1));
                     c1 = k == 0 ? bxi : (k == 1 ? bxi - 1 : (k == 2 ? bxi + 1 : bxi + 1));
-                    if (k == 1 && c0 < 0) c0 = 1, c1 = 0;            // no bucket left of the grid
-                    if (k == 2 && c1 >= P.nbx) c0 = 1, c1 = 0;       // no bucket right of the grid
+                    if (k == 1 && c0 < 0) c0 = 1, c1 = 0;       // no bucket left of the grid
+                    if (k == 2 && c1 >= P.nbx) c0 = 1, c1 = 0;  // no bucket right of the grid
                 } else if (k < 2) {
                     row = k == 0 ? byi - r : byi + r;
                     c0 = bxi - r;
@@ -320,91 +356,129 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int s, int lane) {
             int cnt = hi - lo;
             int incl = cnt;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += y;
+            for (int o = 1; o < G; o <<= 1) {
+                int y = __shfl_up_sync(kFull, incl, o, G);
+                if (g.gl >= o) incl += y;
             }
-            int total = __shfl_sync(kFull, incl, 31);
+            int total = g.shfl(incl, G - 1);
             int excl = incl - cnt;
-            for (int q0 = 0; q0 < total; q0 += 32) {
-                int q = q0 + lane;
+            for (int q0 = 0; warp_any(q0 < total); q0 += G) {
+                int q = q0 + g.gl;
                 int ow = 0;
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
+                for (int step = G / 2; step > 0; step >>= 1) {
                     int pr = ow + step;
-                    int ex = __shfl_sync(kFull, excl, pr);
+                    int ex = g.shfl(excl, pr);
                     if (ex <= q) ow = pr;
                 }
-                int olo = __shfl_sync(kFull, lo, ow);
-                int oex = __shfl_sync(kFull, excl, ow);
-                int slot = olo + (q - oex);
-                bool valid = q < total && slot != s;
+                int olo = g.shfl(lo, ow);
+                int oex = g.shfl(excl, ow);
+                int cs = olo + (q - oex);
+                bool valid = !done && q < total && cs != s;
                 float dx = 0.f, dy = 0.f, d2 = INF;
-                if (valid) valid = !a.dom[slot];
+                if (valid) valid = !a.dom[cs];
                 if (valid) {
-                    T xj = a.srt.x[slot], yj = a.srt.y[slot];
+                    T xj = a.srt.x[cs], yj = a.srt.y[cs];
                     dx = (float)(xj - xi);
                     dy = (float)(yj - yi);
                     d2 = dx * dx + dy * dy;
                 }
                 bool keep = valid && d2 < 4.0f * Rmax * Rmax * 1.0001f;
-                unsigned km = __ballot_sync(kFull, keep);
-                if (nst + __popc(km) > kStageCap) {
-                    int st = flush();
-                    if (st) {
-                        if (st == 2 && lane == 0) atomicAdd(&a.ctrl->cnt.ring_overflow, 1ull);
-                        if (lane == 0) {
-                            a.ring_n[s] = 0;
-                            a.cellR[s] = 0.0f;
-                        }
-                        return;
-                    }
-                    keep = keep && d2 < 4.0f * Rmax * Rmax * 1.0001f;
-                    km = __ballot_sync(kFull, keep);
+                unsigned km = g.ballot(keep);
+                if (warp_any(nst + __popc(km) > kStageCap)) {
+                    flush();
+                    keep = keep && !done && d2 < 4.0f * Rmax * Rmax * 1.0001f;
+                    km = g.ballot(keep);
                 }
-                if (keep) stage[nst + __popc(km & ((1u << lane) - 1u))] = make_float4(dx, dy, d2, __int_as_float(slot));
+                if (keep) stage[nst + __popc(km & ((1u << g.gl) - 1u))] = make_float4(dx, dy, d2, __int_as_float(cs));
                 nst += __popc(km);
                 __syncwarp();
             }
         }
-        int st = flush();
-        if (st) {
-            if (st == 2 && lane == 0) atomicAdd(&a.ctrl->cnt.ring_overflow, 1ull);
-            if (lane == 0) {
-                a.ring_n[s] = 0;
-                a.cellR[s] = 0.0f;
-            }
-            return;
-        }
+        flush();
         // nothing outside the (2r+1)^2 block can cut once it is beyond 2 Rmax
-        float dmin = INF;
-        if (bxi - r > 0) dmin = fminf(dmin, xf - (float)(bxi - r) * bsx);
-        if (bxi + r < P.nbx - 1) dmin = fminf(dmin, (float)(bxi + r + 1) * bsx - xf);
-        if (byi - r > 0) dmin = fminf(dmin, yf - (float)(byi - r) * bsy);
-        if (byi + r < P.nby - 1) dmin = fminf(dmin, (float)(byi + r + 1) * bsy - yf);
-        bool all = bxi - r <= 0 && bxi + r >= P.nbx - 1 && byi - r <= 0 && byi + r >= P.nby - 1;
-        if (all || 2.0f * Rmax * 1.0001f < dmin - bmargin) break;
+        if (!done) {
+            float dmin = INF;
+            if (bxi - r > 0) dmin = fminf(dmin, xf - (float)(bxi - r) * bsx);
+            if (bxi + r < P.nbx - 1) dmin = fminf(dmin, (float)(bxi + r + 1) * bsx - xf);
+            if (byi - r > 0) dmin = fminf(dmin, yf - (float)(byi - r) * bsy);
+            if (byi + r < P.nby - 1) dmin = fminf(dmin, (float)(byi + r + 1) * bsy - yf);
+            bool all = bxi - r <= 0 && bxi + r >= P.nbx - 1 && byi - r <= 0 && byi + r >= P.nby - 1;
+            if (all || 2.0f * Rmax * 1.0001f < dmin - bmargin) done = true;
+        }
     }
-    finish_cell(a, s, lane, L, ne, Rmax);
+    if (!live) return;
+    if (status == 2 && G < 32) {
+        // out of lanes: queue the cell for the 32-lane pass
+        if (g.gl == 0) {
+            int q = atomicAdd(&a.ctrl->ovf_n, 1);
+            a.ovf_list[q] = s;
+        }
+        return;
+    }
+    if (status != 0) {
+        if (status == 2 && g.gl == 0) atomicAdd(&a.ctrl->cnt.ring_overflow, 1ull);
+        if (g.gl == 0) {
+            a.ring_n[s] = 0;
+            a.cellR[s] = 0.0f;
+        }
+        return;
+    }
+    if (g.gl < ne) a.ring[(size_t)s * kRingCap + g.gl] = L.lab;
+    if (g.gl == 0) {
+        a.ring_n[s] = (uint8_t)ne;
+        a.cellR[s] = Rmax;
+    }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kVoroThreads) k_voronoi(IterArgs<T> a) {
+// main pass: G = 16 lanes per cell, 32 / G cells per warp
+template <typename T, int G>
+__global__ void __launch_bounds__(kVoroThreads, 6) k_voronoi(IterArgs<T> a) {
     if (!a.force && a.ctrl->terminated) return;
+    __shared__ float4 stage_all[kVoroThreads / G][kStageCap];
+    Grp<G> g;
     int lane = threadIdx.x & 31;
-    int wpb = blockDim.x >> 5;
-    for (int s = blockIdx.x * wpb + (threadIdx.x >> 5); s < a.n; s += gridDim.x * wpb) voronoi_cell<T>(a, s, lane);
+    g.gl = lane & (G - 1);
+    g.goff = lane & ~(G - 1);
+    constexpr int cpw = 32 / G;  // cells per warp
+    int wib = threadIdx.x >> 5;
+    int nwarps = gridDim.x * (kVoroThreads / 32);
+    float4* stage = stage_all[threadIdx.x / G];
+    for (int w = blockIdx.x * (kVoroThreads / 32) + wib; w * cpw < a.n; w += nwarps) {
+        int s = w * cpw + lane / G;
+        voronoi_cell<T, G>(a, s < a.n ? s : -1, g, stage);
+    }
+}
+
+// 32-lane pass over the cells the 16-lane pass could not hold
+template <typename T>
+__global__ void __launch_bounds__(kVoroThreads) k_voronoi_wide(IterArgs<T> a) {
+    if (!a.force && a.ctrl->terminated) return;
+    __shared__ float4 stage_all[kVoroThreads / 32][kStageCap];
+    Grp<32> g;
+    g.gl = threadIdx.x & 31;
+    g.goff = 0;
+    int wib = threadIdx.x >> 5;
+    int nw = gridDim.x * (kVoroThreads / 32);
+    int n = a.ctrl->ovf_n;
+    for (int i = blockIdx.x * (kVoroThreads / 32) + wib; i < n; i += nw)
+        voronoi_cell<T, 32>(a, a.ovf_list[i], g, stage_all[wib]);
 }
 
 template <typename T>
 void launch_voronoi(const IterArgs<T>& a, cudaStream_t st) {
-    int wpb = kVoroThreads / 32;
-    int g = (a.n + wpb - 1) / wpb;
+    cudaMemsetAsync(&a.ctrl->ovf_n, 0, sizeof(int32_t), st);
+    constexpr int G = 16;
+    int cpb = kVoroThreads / G;  // cells per block
+    int g = (a.n + cpb - 1) / cpb;
     if (g < 1) g = 1;
-    k_voronoi<T><<<g, kVoroThreads, 0, st>>>(a);
+    k_voronoi<T, G><<<g, kVoroThreads, 0, st>>>(a);
+    k_voronoi_wide<T><<<152 * 2, kVoroThreads, 0, st>>>(a);
 }
 
 template void launch_voronoi<double>(const IterArgs<double>&, cudaStream_t);
+template void launch_voronoi<float>(const IterArgs<float>&, cudaStream_t);
+
 // device exact predicates on explicit queries (verification hook)
 __global__ void k_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -419,6 +493,5 @@ void launch_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_
                        cudaStream_t st) {
     if (nq > 0) k_predicates<<<(nq + 127) / 128, 128, 0, st>>>(pts, ids, nq, o_out, c_out);
 }
-template void launch_voronoi<float>(const IterArgs<float>&, cudaStream_t);
 
 }  // namespace trime
