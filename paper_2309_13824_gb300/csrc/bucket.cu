@@ -145,6 +145,11 @@ __global__ void __launch_bounds__(kThreads) k_scatter(IterArgs<T> a) {
         point_cell_fixed(a.sdf, xd, yd, gi, gj);
     }
     a.cell[d] = gj * ncx + gi;
+    // per-slot float data read by the cell kernels (computed once per point)
+    float xh = (float)x, yh = (float)y;
+    float xl = (float)(xd - (double)xh), yl = (float)(yd - (double)yh);
+    a.pf[d] = make_float4(xh, xl, yh, yl);
+    a.pS[d] = (float)(a.P.fac_voro_bound * a.gh[gj * ncx + gi]);
 }
 
 // SoS duplicate rule: of several points at exactly the same position the one

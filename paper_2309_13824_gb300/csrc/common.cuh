@@ -76,7 +76,13 @@ struct DevParams {
     // neighbour-bucket grid
     int32_t nbx, nby;
     double bsx, bsy;  // bucket sizes
+    // float copies used by the bucket assignment (both kernels use these)
+    float bx0f, by0f, ibsxf, ibsyf;
 };
+
+// a - b for positions stored as float pairs (hi, lo) with hi + lo = x to 2^-48 |x|;
+// relative error below 2^-22 once |a - b| >= 2^-20 (callers fall back to double below)
+__device__ __forceinline__ float ff_diff(float ah, float al, float bh, float bl) { return (ah - bh) + (al - bl); }
 
 // ---------------------------------------------------------------- fixed FP64 ops
 __device__ __forceinline__ double fadd(double a, double b) { return __dadd_rn(a, b); }

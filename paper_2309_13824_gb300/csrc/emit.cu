@@ -90,16 +90,20 @@ struct CellC {
 };
 
 template <typename T>
-__device__ __forceinline__ Nbr load_nbr(const IterArgs<T>& a, int lab, T xi, T yi) {
+__device__ __forceinline__ Nbr load_nbr(const IterArgs<T>& a, int lab, float4 pi4, T xi, T yi) {
     Nbr n;
     n.slot = lab;
     if (lab >= 0) {
-        T x = a.srt.x[lab], y = a.srt.y[lab];
+        float4 pj4 = a.pf[lab];
         n.id = a.srt.id[lab];
         n.cell = a.cell[lab];
-        n.dx = (float)(x - xi);
-        n.dy = (float)(y - yi);
-        n.S = (float)(a.P.fac_voro_bound * a.gh[n.cell]);
+        n.dx = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y);
+        n.dy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
+        if (sizeof(T) == 8 && n.dx * n.dx + n.dy * n.dy < 9.094947e-13f) {  // |d| < 2^-20
+            n.dx = (float)(a.srt.x[lab] - xi);
+            n.dy = (float)(a.srt.y[lab] - yi);
+        }
+        n.S = a.pS[lab];
     } else {
         n.id = 0;
         n.cell = 0;
@@ -158,30 +162,92 @@ __device__ bool emitted(const IterArgs<T>& a, const CellC& cc, int idi, int ci, 
     return true;
 }
 
+// A grid point located in float: its cell is certain when the grid
+// coordinate is more than em (its error bound) away from a cell edge.
+struct FLoc {
+    int gi, gj;
+    float fx, fy, emx, emy;
+    bool ok, off;
+};
+
+__device__ __forceinline__ FLoc locate_f(float tx, float ty, int ncx, int ncy) {
+    FLoc L;
+    float fi = floorf(tx), fj = floorf(ty);
+    L.fx = tx - fi;
+    L.fy = ty - fj;
+    L.emx = 2.5e-7f * fabsf(tx) + 1e-4f;
+    L.emy = 2.5e-7f * fabsf(ty) + 1e-4f;
+    L.ok = L.fx > L.emx && L.fx < 1.0f - L.emx && L.fy > L.emy && L.fy < 1.0f - L.emy;
+    L.gi = (int)fi;
+    L.gj = (int)fj;
+    L.off = L.gi < 0 || L.gj < 0 || L.gi >= ncx || L.gj >= ncy;
+    return L;
+}
+
+// SDF at a located point vs threshold thr: +1 value certainly above, -1
+// certainly at or below, 0 undecided.  The bound covers the coordinate error
+// (em times the cell's value differences) and float rounding.
+__device__ __forceinline__ int sdf_cmp_f(const DevGrid& g, const FLoc& L, float thr) {
+    const float* r0 = g.v + (size_t)L.gj * g.nx + L.gi;
+    const float* r1 = r0 + g.nx;
+    float v00 = __ldg(r0), v10 = __ldg(r0 + 1), v01 = __ldg(r1), v11 = __ldg(r1 + 1);
+    float a = v00 + L.fx * (v10 - v00), b = v01 + L.fx * (v11 - v01);
+    float val = a + L.fy * (b - a);
+    float err = L.emx * (fabsf(v10 - v00) + fabsf(v11 - v01)) + L.emy * fabsf(b - a) +
+                1e-6f * (fabsf(v00) + fabsf(v10) + fabsf(v01) + fabsf(v11)) + 2.4e-7f * fabsf(thr);
+    if (val > thr + err) return 1;
+    if (val < thr - err) return -1;
+    return 0;
+}
+
+// Tests 1-2 in float on positions relative to p_i: 1 valid, 0 invalid,
+// -1 undecided (the fixed FP64 formulas decide; Test 3 always goes there)
+template <typename T>
+__device__ int valid_float(const IterArgs<T>& a, const CellC& cc, const Nbr& j, const Nbr& k) {
+    int ncx = a.sdf.nx - 1, ncy = a.sdf.ny - 1;
+    float gx = (j.dx + k.dx) * (1.0f / 3.0f), gy = (j.dy + k.dy) * (1.0f / 3.0f);
+    FLoc L = locate_f(cc.tx + gx * cc.idx, cc.ty + gy * cc.idy, ncx, ncy);
+    if (!L.ok) return -1;
+    if (L.off) return 0;
+    int c = L.gj * ncx + L.gi;
+    uint8_t cls = a.gcls[c];
+    if (cls == CELL_INNER) return 1;
+    if (cls == CELL_OUTER) return 0;
+    int r = sdf_cmp_f(a.sdf, L, (float)a.ggeps[c]);
+    if (r == 1) return 0;
+    if (r == 0) return -1;
+    // Test 2: edge midpoints (0, j)/2, (j + k)/2, (k, 0)/2 relative to p_i
+    int count = 0;
+    for (int e = 0; e < 3; e++) {
+        float mx = e == 0 ? 0.5f * j.dx : (e == 1 ? 0.5f * (j.dx + k.dx) : 0.5f * k.dx);
+        float my = e == 0 ? 0.5f * j.dy : (e == 1 ? 0.5f * (j.dy + k.dy) : 0.5f * k.dy);
+        FLoc M = locate_f(cc.tx + mx * cc.idx, cc.ty + my * cc.idy, ncx, ncy);
+        if (!M.ok) return -1;
+        if (M.off) continue;
+        int q = M.gj * ncx + M.gi;
+        uint8_t qc = a.gcls[q];
+        if (qc == CELL_INNER) {
+            count++;
+        } else if (qc == CELL_BOUNDARY) {
+            int rr = sdf_cmp_f(a.sdf, M, (float)a.ggeps[q]);
+            if (rr == 0) return -1;
+            if (rr == -1) count++;
+        }
+    }
+    if (count >= 2) return 1;
+    return -1;
+}
+
 template <typename T>
 __device__ bool valid_tri(const IterArgs<T>& a, const CellC& cc, int idi, int ci, T xi, T yi, const Nbr& j,
                           const Nbr& k) {
     if (!a.P.validity) return true;
-    // Test 1 shortcuts: (a) every cell within gidist of p_i's cell is inner
+    // Test 1 shortcut: every cell within gidist of p_i's cell is inner
     float gx = (j.dx + k.dx) * (1.0f / 3.0f), gy = (j.dy + k.dy) * (1.0f / 3.0f);
-    float offx = gx * cc.idx, offy = gy * cc.idy;
-    float off = fmaxf(fabsf(offx), fabsf(offy));
+    float off = fmaxf(fabsf(gx * cc.idx), fabsf(gy * cc.idy));
     if (off + 2.01f < (float)a.gidist[ci]) return true;
-    // (b) the centroid's cell is certain and not a boundary cell: the float
-    // grid coordinate errs by at most two roundings (2^-23 |t|) plus the
-    // offset's error, far below em, so a coordinate more than em away from an
-    // integer has the same floor as the fixed FP64 formula
-    float tx = cc.tx + offx, ty = cc.ty + offy;
-    float fx = tx - floorf(tx), fy = ty - floorf(ty);
-    float emx = 2.5e-7f * fabsf(tx) + 1e-4f, emy = 2.5e-7f * fabsf(ty) + 1e-4f;
-    int ncx = a.sdf.nx - 1, ncy = a.sdf.ny - 1;
-    if (fx > emx && fx < 1.0f - emx && fy > emy && fy < 1.0f - emy) {
-        int gi = (int)floorf(tx), gj = (int)floorf(ty);
-        if (gi < 0 || gj < 0 || gi >= ncx || gj >= ncy) return false;
-        uint8_t c = a.gcls[gj * ncx + gi];
-        if (c == CELL_INNER) return true;
-        if (c == CELL_OUTER) return false;
-    }
+    int f = valid_float(a, cc, j, k);
+    if (f >= 0) return f == 1;
     int ids[3] = {idi, j.id, k.id};
     double xs[3] = {(double)xi, (double)a.srt.x[j.slot], (double)a.srt.x[k.slot]};
     double ys[3] = {(double)yi, (double)a.srt.y[j.slot], (double)a.srt.y[k.slot]};
@@ -234,7 +300,8 @@ __global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
         uint32_t vm = 0;
         if (ne >= 2) {
             CellC cc;
-            cc.S = (float)(a.P.fac_voro_bound * a.gh[ci]);
+            const float4 pi4 = a.pf[s];
+            cc.S = a.pS[s];
             double xd = (double)xi, yd = (double)yi;
             cc.lx = (float)(a.P.bx0 - xd);
             cc.hx = (float)(a.P.bx1 - xd);
@@ -245,10 +312,10 @@ __global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
             cc.idx = (float)a.sdf.idx;
             cc.idy = (float)a.sdf.idy;
             float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f, q5 = 180.f;
-            Nbr first = load_nbr(a, lab[0], xi, yi);
+            Nbr first = load_nbr(a, lab[0], pi4, xi, yi);
             Nbr cur = first;
             for (int t = 0; t < ne; t++) {
-                Nbr nxt = t + 1 < ne ? load_nbr(a, lab[t + 1], xi, yi) : first;
+                Nbr nxt = t + 1 < ne ? load_nbr(a, lab[t + 1], pi4, xi, yi) : first;
                 if (cur.slot >= 0 && nxt.slot >= 0 && emitted(a, cc, idi, ci, xi, yi, cur, nxt) &&
                     valid_tri(a, cc, idi, ci, xi, yi, cur, nxt)) {
                     vm |= 1u << t;

@@ -53,6 +53,8 @@ struct IterArgs {
     DevCtrl* ctrl;
     double* dbg;       // [8][n] by original id, written when P.debug
     int32_t* ovf_list; // [n] cells whose 16-lane clipping ran out of lanes
+    float4* pf;        // [n] sorted positions as float pairs (xhi, xlo, yhi, ylo)
+    float* pS;         // [n] octagon span S = fac_voro_bound * h of each sorted slot
 };
 
 // a1: counting sort
@@ -91,8 +93,8 @@ constexpr int kVoroThreads = 128;
 // Voronoi kernel call this same function so assignments agree
 template <typename T>
 __device__ __forceinline__ void bucket_of(const DevParams& P, T x, T y, int& bx, int& by) {
-    float fx = ((float)x - (float)P.bx0) * (float)(1.0 / P.bsx);
-    float fy = ((float)y - (float)P.by0) * (float)(1.0 / P.bsy);
+    float fx = ((float)x - P.bx0f) * P.ibsxf;
+    float fy = ((float)y - P.by0f) * P.ibsyf;
     bx = (int)floorf(fx);
     by = (int)floorf(fy);
     bx = bx < 0 ? 0 : (bx >= P.nbx ? P.nbx - 1 : bx);

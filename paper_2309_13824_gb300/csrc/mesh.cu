@@ -64,6 +64,8 @@ struct mesh_s {
     double* dbg = nullptr;
     int32_t *tcnt = nullptr, *toff = nullptr, *tbuf = nullptr;
     int32_t* ovf_list = nullptr;
+    float4* pf = nullptr;
+    float* pS = nullptr;
     void* xybuf = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<void*> allocs;
@@ -238,6 +240,8 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.ctrl = m->ctrl;
     a.dbg = m->dbg;
     a.ovf_list = m->ovf_list;
+    a.pf = m->pf;
+    a.pS = m->pS;
     return a;
 }
 
@@ -439,6 +443,10 @@ int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, c
     d.nby = std::max(1, (int)std::ceil(lam * H));
     d.bsx = W / d.nbx;
     d.bsy = H / d.nby;
+    d.bx0f = (float)d.bx0;
+    d.by0f = (float)d.by0;
+    d.ibsxf = (float)(1.0 / d.bsx);
+    d.ibsyf = (float)(1.0 / d.bsy);
     int nb = d.nbx * d.nby;
 
     size_t ns = (size_t)sdf->nx * sdf->ny, nz = (size_t)sizing->nx * sizing->ny;
@@ -485,6 +493,8 @@ int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, c
     m->tbuf = dalloc<int32_t>(m, 3 * (2 * N + 16), rc);
     m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
     m->ovf_list = dalloc<int32_t>(m, N, rc);
+    m->pf = dalloc<float4>(m, N, rc);
+    m->pS = dalloc<float>(m, N, rc);
     if (rc) return bail(rc);
 
     m->sdf = {sdf->nx, sdf->ny, sdf->x0, sdf->y0, sdf->x1, sdf->y1, (sdf->x1 - sdf->x0) / (double)(sdf->nx - 1),

@@ -222,16 +222,19 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
         }
         live = false;
     }
-    T xi = a.srt.x[s], yi = a.srt.y[s];
+    const float4 pi4 = a.pf[s];
     CellCtx<T> ctx;
     ctx.x = a.srt.x;
     ctx.y = a.srt.y;
     ctx.id = a.srt.id;
     ctx.ctrl = a.ctrl;
-    ctx.pix = (double)xi;
-    ctx.piy = (double)yi;
+    ctx.pix = (double)a.srt.x[s];
+    ctx.piy = (double)a.srt.y[s];
     ctx.idi = a.srt.id[s];
-    double W = P.bx1 - P.bx0, H = P.by1 - P.by0;
+    // generator relative to the box corner, and the box size (float; the box
+    // planes only need to bound Reg_i with the S/16 margin)
+    const float xf = (pi4.x - P.bx0f) + pi4.y, yf = (pi4.z - P.by0f) + pi4.w;
+    const float Wf = (float)(P.bx1 - P.bx0), Hf = (float)(P.by1 - P.by0);
     float RB, mb;
     Lane L;
     L.bb = false;
@@ -241,7 +244,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
     L.M = L.Qx = L.Qy = L.PM = L.PQx = L.PQy = 0.0f;
     int ne;
     if (P.bounded) {
-        float S = (float)(P.fac_voro_bound * a.gh[a.cell[s]]);
+        float S = a.pS[s];
         float SB = S * (17.0f / 16.0f);
         RB = SB * 1.0824459f * 1.0001f;  // octagon circumradius SB / cos(pi/8)
         mb = S * (1.0f / 16.0f);
@@ -253,15 +256,14 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
         L.lab = oct_label(t);
         ne = 8;
     } else {
-        mb = (float)(0.125 * (W > H ? W : H));
-        RB = (float)((sqrt(W * W + H * H) + 4.0 * mb) * 1.0001);
+        mb = 0.125f * (Wf > Hf ? Wf : Hf);
+        RB = (sqrtf(Wf * Wf + Hf * Hf) + 4.0f * mb) * 1.0001f;
         ne = 4;  // enlarged box, CCW: bottom, right, top, left
         int b = g.gl & 3;
         int bs = b == 0 ? 2 : (b == 1 ? 1 : (b == 2 ? 3 : 0));
         L.nx = bs == 0 ? -1.f : (bs == 1 ? 1.f : 0.f);
         L.ny = bs == 2 ? -1.f : (bs == 3 ? 1.f : 0.f);
-        L.s = bs == 0 ? (float)(ctx.pix - (P.bx0 - mb)) : bs == 1 ? (float)((P.bx1 + mb) - ctx.pix)
-            : bs == 2 ? (float)(ctx.piy - (P.by0 - mb)) : (float)((P.by1 + mb) - ctx.piy);
+        L.s = bs == 0 ? xf + mb : bs == 1 ? (Wf - xf) + mb : bs == 2 ? yf + mb : (Hf - yf) + mb;
         L.lab = box_label(bs);
     }
     lane_vertex<G>(L, ne, g, RB, true);
@@ -270,16 +272,14 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
         for (int b = 0; b < 4; b++) {
             float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
             float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
-            float sb = b == 0 ? (float)(ctx.pix - (P.bx0 - mb)) : b == 1 ? (float)((P.bx1 + mb) - ctx.pix)
-                     : b == 2 ? (float)(ctx.piy - (P.by0 - mb)) : (float)((P.by1 + mb) - ctx.piy);
+            float sb = b == 0 ? xf + mb : b == 1 ? (Wf - xf) + mb : b == 2 ? yf + mb : (Hf - yf) + mb;
             int st = clip_by<T, G>(L, ne, nx, ny, sb, box_label(b), false, live && status == 0, RB, g, ctx);
             if (st) status = st;
         }
     }
     float Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
     int bxi, byi;
-    bucket_of(P, xi, yi, bxi, byi);
-    const float xf = (float)(ctx.pix - P.bx0), yf = (float)(ctx.piy - P.by0);
+    bucket_of(P, pi4.x, pi4.z, bxi, byi);
     const float bsx = (float)P.bsx, bsy = (float)P.bsy;
     const float bmargin = (float)(1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy)) + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
     bool done = !live || status != 0;
@@ -378,10 +378,15 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
                 float dx = 0.f, dy = 0.f, d2 = INF;
                 if (valid) valid = !a.dom[cs];
                 if (valid) {
-                    T xj = a.srt.x[cs], yj = a.srt.y[cs];
-                    dx = (float)(xj - xi);
-                    dy = (float)(yj - yi);
+                    float4 pj4 = a.pf[cs];
+                    dx = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y);
+                    dy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
                     d2 = dx * dx + dy * dy;
+                    if (sizeof(T) == 8 && d2 < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
+                        dx = (float)((double)a.srt.x[cs] - ctx.pix);
+                        dy = (float)((double)a.srt.y[cs] - ctx.piy);
+                        d2 = dx * dx + dy * dy;
+                    }
                 }
                 bool keep = valid && d2 < 4.0f * Rmax * Rmax * 1.0001f;
                 unsigned km = g.ballot(keep);
