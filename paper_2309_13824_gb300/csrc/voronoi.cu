@@ -164,6 +164,7 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
         status = 1;
         doit = false;
     }
+    if (!warp_any(doit)) return status;  // nothing to cut anywhere in the warp
     int prevl = g.gl == 0 ? ne - 1 : g.gl - 1;
     bool pcut = (m >> (prevl & 31)) & 1u;
     unsigned starts = g.ballot(g.gl < ne && cut && !pcut);
@@ -178,32 +179,26 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
         status = 2;
         doit = false;
     }
+    // rotate the edges so E_e lands in lane 0, append the new edge in lane k,
+    // then every lane recomputes its vertex (SIMT: as cheap as two lanes)
     int src = doit ? (eidx + g.gl) % ne : g.gl;
-    Lane R;
-    R.nx = g.shfl(L.nx, src);
-    R.ny = g.shfl(L.ny, src);
-    R.s = g.shfl(L.s, src);
-    R.lab = g.shfl(L.lab, src);
-    R.vx = g.shfl(L.vx, src);
-    R.vy = g.shfl(L.vy, src);
-    R.vR = g.shfl(L.vR, src);
-    R.nlab = g.shfl(L.nlab, src);
-    R.bb = g.shfl((int)L.bb, src) != 0;
-    R.Qx = g.shfl(L.Qx, src);
-    R.Qy = g.shfl(L.Qy, src);
-    R.M = g.shfl(L.M, src);
-    R.PQx = g.shfl(L.PQx, src);
-    R.PQy = g.shfl(L.PQy, src);
-    R.PM = g.shfl(L.PM, src);
-    if (doit && g.gl < k) L = R;
-    if (doit && g.gl == k) {
-        L.nx = nx;
-        L.ny = ny;
-        L.s = s;
-        L.lab = lab;
+    float rnx = g.shfl(L.nx, src), rny = g.shfl(L.ny, src), rs = g.shfl(L.s, src);
+    int rlab = g.shfl(L.lab, src);
+    if (doit) {
+        if (g.gl < k) {
+            L.nx = rnx;
+            L.ny = rny;
+            L.s = rs;
+            L.lab = rlab;
+        } else if (g.gl == k) {
+            L.nx = nx;
+            L.ny = ny;
+            L.s = s;
+            L.lab = lab;
+        }
+        ne = nn;
     }
-    if (doit) ne = nn;
-    lane_vertex<G>(L, ne, g, RB, doit && (g.gl == k - 1 || g.gl == k));
+    lane_vertex<G>(L, ne, g, RB, doit);
     return status;
 }
 
