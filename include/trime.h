@@ -95,6 +95,12 @@ typedef struct {
     int64_t dup_points;        /* points whose cell is empty (exact duplicate, SoS)       */
     int32_t small_moves;       /* every inner point moved less than fac_end*h_i           */
     int32_t reserved1;
+    /* Voronoi work of the last call, counted only with mesh_params.debug = 1: */
+    int64_t vor_candidates;    /* candidate points loaded within the security radius      */
+    int64_t vor_picks;         /* candidates applied to a cell                            */
+    int64_t vor_cuts;          /* applications that changed a cell                        */
+    int64_t vor_rings;         /* bucket rings scanned (summed over cells)                */
+    int64_t vor_wide;          /* cells redone with 32 lanes                              */
 } mesh_stats;
 
 typedef struct mesh_s mesh_t;

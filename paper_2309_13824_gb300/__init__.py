@@ -56,7 +56,8 @@ class mesh_stats(C.Structure):
                 ("fac_mu", C.c_double), ("exact_calls", C.c_int64), ("clip_inconsistent", C.c_int64),
                 ("ring_overflow", C.c_int64), ("exact_overflow", C.c_int64), ("newton_fail", C.c_int64),
                 ("trace_cap", C.c_int64), ("quad_cap", C.c_int64), ("dup_points", C.c_int64),
-                ("small_moves", C.c_int32), ("reserved1", C.c_int32)]
+                ("small_moves", C.c_int32), ("reserved1", C.c_int32), ("vor_candidates", C.c_int64),
+                ("vor_picks", C.c_int64), ("vor_cuts", C.c_int64), ("vor_rings", C.c_int64), ("vor_wide", C.c_int64)]
 
 
 # every symbol include/trime.h declares

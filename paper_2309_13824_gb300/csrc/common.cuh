@@ -33,6 +33,8 @@ struct DevGrid {
 struct DevCounters {
     unsigned long long exact_calls, clip_inconsistent, ring_overflow, exact_overflow;
     unsigned long long newton_fail, trace_cap, quad_cap, dup_points;
+    // Voronoi work, counted only with debug recording on
+    unsigned long long vor_candidates, vor_picks, vor_cuts, vor_rings, vor_wide;
 };
 
 // Per-block partial sums written by the emit kernel (a3/a4/a8 and Eq. 3 sums).

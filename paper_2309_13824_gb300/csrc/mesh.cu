@@ -315,6 +315,11 @@ static void fill_stats(const mesh_s* m, int iters, mesh_stats* s) {
     s->quad_cap = (int64_t)c.cnt.quad_cap;
     s->dup_points = (int64_t)c.cnt.dup_points;
     s->small_moves = c.small_moves;
+    s->vor_candidates = (int64_t)c.cnt.vor_candidates;
+    s->vor_picks = (int64_t)c.cnt.vor_picks;
+    s->vor_cuts = (int64_t)c.cnt.vor_cuts;
+    s->vor_rings = (int64_t)c.cnt.vor_rings;
+    s->vor_wide = (int64_t)c.cnt.vor_wide;
 }
 
 static int reset_counters(mesh_s* m) {

@@ -307,7 +307,12 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
             __syncwarp();
             if (has && g.gl == 0) stage[bi].z = INF;
             __syncwarp();
+            int ne0 = ne;
             int st = clip_by<T, G>(L, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, has, RB, g, ctx);
+            if (P.debug && has && g.gl == 0) {
+                atomicAdd(&a.ctrl->cnt.vor_picks, 1ull);
+                if (ne != ne0 || st) atomicAdd(&a.ctrl->cnt.vor_cuts, 1ull);
+            }
             if (st) {
                 status = st;
                 done = true;
@@ -319,6 +324,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
         __syncwarp();
     };
     for (int r = 1; warp_any(!done); r++) {
+        if (P.debug && !done && g.gl == 0) atomicAdd(&a.ctrl->cnt.vor_rings, 1ull);
         int nr = r == 1 ? 5 : 4 * r;
         for (int kb = 0; kb < nr; kb += G) {
             int k = kb + g.gl;
@@ -391,6 +397,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
                     km = g.ballot(keep);
                 }
                 if (keep) stage[nst + __popc(km & ((1u << g.gl) - 1u))] = make_float4(dx, dy, d2, __int_as_float(cs));
+                if (P.debug && g.gl == 0 && km) atomicAdd(&a.ctrl->cnt.vor_candidates, (unsigned long long)__popc(km));
                 nst += __popc(km);
                 __syncwarp();
             }
@@ -413,6 +420,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
         if (g.gl == 0) {
             int q = atomicAdd(&a.ctrl->ovf_n, 1);
             a.ovf_list[q] = s;
+            if (P.debug) atomicAdd(&a.ctrl->cnt.vor_wide, 1ull);
         }
         return;
     }
