@@ -128,7 +128,7 @@ def committed_traffic(kernel_src):
     for line in txt.splitlines():
         if line.startswith("traffic_bytes_per_launch:"):
             tr = float(line.split(":")[1])
-        if line.startswith("voronoi_cu_sha256_16:"):
+        if line.startswith("voronoi_cuh_sha256_16:"):
             hs = line.split(":")[1].strip()
     return tr if hs == digest else None
 
@@ -266,7 +266,7 @@ def main():
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA issue, TFLOP/s
     achieved = VORONOI_FLOP_PER_CELL * n / t_vor / 1e12
-    src = os.path.join(ROOT, "paper_2309_13824_gb300", "csrc", "voronoi.cu")
+    src = os.path.join(ROOT, "paper_2309_13824_gb300", "csrc", "voronoi.cuh")
     roofline = {"bound": "alu", "kernel": "k_voronoi", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": committed_traffic(src),
                 "peak_note": f"{sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and clocks)",

@@ -203,6 +203,14 @@ int mesh_bucket_points_noalloc(const double* x, const double* y, int64_t n, doub
  * iteration.  Semantics otherwise as mesh_step.  Synchronises. */
 int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms);
 
+/* Tiling of the iteration: size the bucket grid for n_opt points per bucket
+ * (> 0; the default is mesh_params.N_opt) and clip each Voronoi cell with
+ * `lanes` = 16 (two cells per warp, cells needing more than 16 edges redone
+ * with 32) or 32 lanes (one cell per warp).  The results do not depend on
+ * either choice, only the speed does.  Re-captures the iteration graph;
+ * synchronises.  Errors: TRIME_EINVAL, TRIME_ENOMEM, TRIME_ECUDA. */
+int mesh_set_tuning(mesh_t* m, double n_opt, int32_t lanes);
+
 /* Verification hook for the exact predicates the Voronoi kernel uses
  * (Sec. 2.1 cell cutting decisions): for each of nq queries of four points
  * a, b, c, d (HOST array pts of nq*8 doubles, x/y interleaved) and their ids
@@ -214,6 +222,78 @@ int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms);
  * Synchronous; host output arrays of nq int32 each. */
 int mesh_exact_predicates(const double* pts, const int32_t* ids, int64_t nq, int32_t* out_orient,
                           int32_t* out_incircle);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent meshes of uneven sizes stepped together: every stage of
+ * an iteration is one kernel launch over all meshes (their points are
+ * concatenated on the device, each mesh padded to a multiple of 256 slots so
+ * a thread block or warp never mixes meshes), and one CUDA graph replays the
+ * whole batch's iteration.  Each mesh keeps its own grids, geometry grid,
+ * bucket grid, fac_mu, quality statistics, hybrid switch and termination
+ * (Sec. 2.4, 4.2, 4); a mesh that has terminated is skipped by every kernel
+ * while the others continue.  Per mesh, the results are those of a mesh_t
+ * created with the same inputs (triangles identical, moves equal up to the
+ * order of floating-point sums).  The paper treats one mesh at a time; the
+ * batch is this library's production form for many small meshes. */
+typedef struct mesh_batch_s mesh_batch_t;
+
+/* What mesh_batch_init's autotuner chose and what it measured. */
+typedef struct {
+    double n_opt;             /* points per bucket the bucket grids are sized for     */
+    int32_t lanes;            /* Voronoi lanes per cell: 16 (two cells per warp) or 32 */
+    int32_t n_candidates;     /* candidates timed (0 without autotuning)              */
+    int64_t n_slots;          /* device slots: the meshes' points plus padding        */
+    int64_t n_buckets;        /* buckets of all meshes, one pad bucket per mesh added */
+    double cand_n_opt[8];
+    int32_t cand_lanes[8];
+    double cand_ms[8];        /* device time of one rebuild (a1..a4) per candidate    */
+} mesh_tuning;
+
+/* Create a batch of n_meshes (1 .. 2^20) meshes on the current device.
+ *  sdfs, sizings: n_meshes host grids each (as mesh_init); xys: n_meshes
+ *  HOST point arrays (precision as p->precision); ns: n_meshes point counts
+ *  (>= 0; total padded size <= 2^30).  One parameter set p (NULL: defaults)
+ *  serves every mesh.  autotune != 0: time one rebuild per candidate of
+ *  (points per bucket in {2/3, 1, 3/2} x p->N_opt) x (16 or 32 Voronoi lanes
+ *  per cell) on these inputs and keep the fastest (the triangles do not
+ *  depend on the choice); autotune == 0 uses p->N_opt and 16 lanes.  Errors as
+ *  mesh_init; a message names the offending mesh. */
+int mesh_batch_init(mesh_batch_t** out, int32_t n_meshes, const mesh_grid2d* sdfs, const mesh_grid2d* sizings,
+                    const void* const* xys, const int64_t* ns, const mesh_params* p, int32_t autotune,
+                    void* cuda_stream);
+
+/* Number of meshes (0 for NULL). */
+int mesh_batch_size(const mesh_batch_t* b);
+
+/* mesh_rebuild for every mesh; stats: NULL or n_meshes entries. */
+int mesh_batch_rebuild(mesh_batch_t* b, mesh_stats* stats);
+
+/* Up to n_iters iterations of every mesh that has not terminated (one graph
+ * launch each); stops early once every mesh has terminated.  stats: NULL
+ * (asynchronous) or n_meshes entries, each with that mesh's iteration count. */
+int mesh_batch_step(mesh_batch_t* b, int32_t n_iters, mesh_stats* stats);
+
+/* mesh_get_triangles / mesh_get_points / mesh_set_state /
+ * mesh_set_method_state for mesh index `mesh` of the batch (0-based, point
+ * indices local to that mesh). */
+int mesh_batch_get_triangles(mesh_batch_t* b, int32_t mesh, int32_t* tri, int64_t cap, int64_t* n_out);
+int mesh_batch_get_points(mesh_batch_t* b, int32_t mesh, void* xy, int64_t cap, int64_t* n_out);
+int mesh_batch_set_state(mesh_batch_t* b, int32_t mesh, const void* xy, const uint8_t* cls, const double* dprev);
+int mesh_batch_set_method_state(mesh_batch_t* b, int32_t mesh, int32_t switched, double prev_half_alpha,
+                                double prev_half_beta, double prev_max_alpha);
+
+/* mesh_profile_step for the whole batch. */
+int mesh_batch_profile_step(mesh_batch_t* b, int32_t n_iters, double* stage_ms);
+
+/* mesh_set_tuning for the whole batch (e.g. to reuse an earlier autotuning
+ * result without timing again). */
+int mesh_batch_set_tuning(mesh_batch_t* b, double n_opt, int32_t lanes);
+
+/* The autotuner's choice and timings. */
+int mesh_batch_get_tuning(const mesh_batch_t* b, mesh_tuning* out);
+
+/* Release all memory of b (NULL is ignored). */
+void mesh_batch_destroy(mesh_batch_t* b);
 
 #ifdef __cplusplus
 }

@@ -5,8 +5,9 @@ This module only marshals arguments to the shared library built from csrc/
 There is no CPU fallback: importing works without a GPU, but any call needs
 the built library and a CUDA device and raises otherwise.
 
-Function names mirror the C ABI.  ``Mesh`` is a small convenience wrapper
-that accepts numpy arrays and torch tensors and returns numpy arrays.
+Function names mirror the C ABI.  ``Mesh`` (one mesh) and ``MeshBatch``
+(many meshes stepped by the same launches) are small convenience wrappers
+that accept numpy arrays and torch tensors and return numpy arrays.
 """
 from __future__ import annotations
 
@@ -60,11 +61,20 @@ class mesh_stats(C.Structure):
                 ("vor_picks", C.c_int64), ("vor_cuts", C.c_int64), ("vor_rings", C.c_int64), ("vor_wide", C.c_int64)]
 
 
+class mesh_tuning(C.Structure):
+    _fields_ = [("n_opt", C.c_double), ("lanes", C.c_int32), ("n_candidates", C.c_int32),
+                ("n_slots", C.c_int64), ("n_buckets", C.c_int64), ("cand_n_opt", C.c_double * 8),
+                ("cand_lanes", C.c_int32 * 8), ("cand_ms", C.c_double * 8)]
+
+
 # every symbol include/trime.h declares
 EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
            "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step",
-           "mesh_bucket_points_noalloc"]
+           "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
+           "mesh_batch_step", "mesh_batch_get_triangles", "mesh_batch_get_points", "mesh_batch_set_state",
+           "mesh_batch_set_method_state", "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_batch_destroy",
+           "mesh_set_tuning", "mesh_batch_set_tuning"]
 
 _lib = None
 
@@ -104,9 +114,27 @@ def lib():
     L.mesh_profile_step.argtypes = [vp, C.c_int32, vp]
     L.mesh_bucket_points_noalloc.argtypes = [vp, vp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                              C.c_int32, C.c_int32, vp, vp, vp]
+    L.mesh_batch_init.argtypes = [P(vp), C.c_int32, P(mesh_grid2d), P(mesh_grid2d), P(vp), P(C.c_int64),
+                                  P(mesh_params), C.c_int32, vp]
+    L.mesh_batch_size.argtypes = [vp]
+    L.mesh_batch_rebuild.argtypes = [vp, vp]
+    L.mesh_batch_step.argtypes = [vp, C.c_int32, vp]
+    L.mesh_batch_get_triangles.argtypes = [vp, C.c_int32, vp, C.c_int64, P(C.c_int64)]
+    L.mesh_batch_get_points.argtypes = [vp, C.c_int32, vp, C.c_int64, P(C.c_int64)]
+    L.mesh_batch_set_state.argtypes = [vp, C.c_int32, vp, vp, vp]
+    L.mesh_batch_set_method_state.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double]
+    L.mesh_batch_profile_step.argtypes = [vp, C.c_int32, vp]
+    L.mesh_batch_get_tuning.argtypes = [vp, P(mesh_tuning)]
+    L.mesh_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
+    L.mesh_batch_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
+    L.mesh_batch_destroy.argtypes = [vp]
+    L.mesh_batch_destroy.restype = None
     for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles", "mesh_get_points",
                  "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
-                 "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc"):
+                 "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc", "mesh_batch_init",
+                 "mesh_batch_size", "mesh_batch_rebuild", "mesh_batch_step", "mesh_batch_get_triangles",
+                 "mesh_batch_get_points", "mesh_batch_set_state", "mesh_batch_set_method_state",
+                 "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_set_tuning", "mesh_batch_set_tuning"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -177,11 +205,7 @@ class Mesh:
 
     def __init__(self, sdf, sizing, xy, stream=None, **params):
         L = lib()
-        p = mesh_default_params()
-        for k, v in params.items():
-            if not hasattr(p, k):
-                raise KeyError(k)
-            setattr(p, k, v)
+        p = _params(params)
         self.params = p
         self.precision = p.precision
         self.dtype = np.float64 if p.precision == 0 else np.float32
@@ -268,8 +292,128 @@ class Mesh:
     def set_method_state(self, switched, prev_a=0.0, prev_b=0.0, prev_amax=0.0):
         _check(lib().mesh_set_method_state(self._h, switched, prev_a, prev_b, prev_amax))
 
+    def set_tuning(self, n_opt: float, lanes: int = 16):
+        _check(lib().mesh_set_tuning(self._h, n_opt, lanes))
+
     def debug(self, what: int):
         width = [2, 2, 2, 1, 1, 1, 1][what]
         out = np.zeros(width * self.n)
         _check(lib().mesh_get_debug(self._h, what, out.ctypes.data_as(C.c_void_p), len(out)))
         return out.reshape(self.n, 2) if width == 2 else out
+
+
+def _params(params) -> mesh_params:
+    p = mesh_default_params()
+    for k, v in params.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class MeshBatch:
+    """Several independent meshes stepped by the same launches (a handle to
+    mesh_batch_t).  `meshes` is a sequence of (sdf, sizing, xy) triples."""
+
+    def __init__(self, meshes, stream=None, autotune=True, **params):
+        L = lib()
+        p = _params(params)
+        self.params = p
+        self.dtype = np.float64 if p.precision == 0 else np.float32
+        nm = len(meshes)
+        self.size = nm
+        G = (mesh_grid2d * nm)()
+        Z = (mesh_grid2d * nm)()
+        X = (C.c_void_p * nm)()
+        N = (C.c_int64 * nm)()
+        self._keep = []
+        self.ns = []
+        for k, (sdf, siz, xy) in enumerate(meshes):
+            gs, ks = _grid(sdf)
+            gz, kz = _grid(siz)
+            xy = np.ascontiguousarray(np.asarray(xy, dtype=self.dtype).reshape(-1, 2))
+            G[k] = gs
+            Z[k] = gz
+            X[k] = xy.ctypes.data_as(C.c_void_p)
+            N[k] = len(xy)
+            self.ns.append(len(xy))
+            self._keep += [ks, kz, xy]
+        h = C.c_void_p()
+        st = C.c_void_p(0 if stream is None else int(stream))
+        rc = L.mesh_batch_init(C.byref(h), nm, G, Z, X, N, C.byref(p), 1 if autotune else 0, st)
+        self._keep = None
+        _check(rc)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mesh_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rebuild(self):
+        s = (mesh_stats * self.size)()
+        _check(lib().mesh_batch_rebuild(self._h, s))
+        return [_stats_dict(x) for x in s]
+
+    def step(self, n_iters: int = 1, check=True):
+        s = (mesh_stats * self.size)()
+        rc = lib().mesh_batch_step(self._h, n_iters, s)
+        if check:
+            _check(rc)
+        return [_stats_dict(x) for x in s]
+
+    def step_async(self, n_iters: int = 1):
+        _check(lib().mesh_batch_step(self._h, n_iters, None))
+
+    def profile(self, n_iters: int = 1):
+        ms = np.zeros(7)
+        _check(lib().mesh_batch_profile_step(self._h, n_iters, ms.ctypes.data_as(C.c_void_p)))
+        return dict(zip(["bucket", "voronoi", "emit", "stats", "update", "post", "total"], ms))
+
+    def set_tuning(self, n_opt: float, lanes: int = 16):
+        _check(lib().mesh_batch_set_tuning(self._h, n_opt, lanes))
+
+    def tuning(self) -> dict:
+        t = mesh_tuning()
+        _check(lib().mesh_batch_get_tuning(self._h, C.byref(t)))
+        nc = t.n_candidates
+        return {"n_opt": t.n_opt, "lanes": t.lanes, "n_slots": t.n_slots, "n_buckets": t.n_buckets,
+                "candidates": [(t.cand_n_opt[k], t.cand_lanes[k], t.cand_ms[k]) for k in range(nc)]}
+
+    def triangles(self, mesh: int):
+        L = lib()
+        n = C.c_int64()
+        rc = L.mesh_batch_get_triangles(self._h, mesh, None, 0, C.byref(n))
+        if rc not in (TRIME_OK, TRIME_ECAPACITY):
+            _check(rc)
+        t = np.zeros((n.value, 3), dtype=np.int32)
+        if n.value:
+            _check(L.mesh_batch_get_triangles(self._h, mesh, t.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
+        return t
+
+    def points(self, mesh: int, out=None):
+        n = C.c_int64()
+        if out is not None:
+            _check(lib().mesh_batch_get_points(self._h, mesh, _ptr(out), out.shape[0], C.byref(n)))
+            return out
+        p = np.zeros((self.ns[mesh], 2), dtype=self.dtype)
+        _check(lib().mesh_batch_get_points(self._h, mesh, p.ctypes.data_as(C.c_void_p), self.ns[mesh],
+                                           C.byref(n)))
+        return p
+
+    def set_state(self, mesh: int, xy=None, cls=None, dprev=None):
+        a = None if xy is None else np.ascontiguousarray(np.asarray(xy, dtype=self.dtype).reshape(-1, 2))
+        b = None if cls is None else np.ascontiguousarray(cls, dtype=np.uint8)
+        c = None if dprev is None else np.ascontiguousarray(dprev, dtype=np.float64)
+        _check(lib().mesh_batch_set_state(self._h, mesh, None if a is None else a.ctypes.data_as(C.c_void_p),
+                                          None if b is None else b.ctypes.data_as(C.c_void_p),
+                                          None if c is None else c.ctypes.data_as(C.c_void_p)))
+
+    def set_method_state(self, mesh: int, switched, prev_a=0.0, prev_b=0.0, prev_amax=0.0):
+        _check(lib().mesh_batch_set_method_state(self._h, mesh, switched, prev_a, prev_b, prev_amax))

@@ -21,7 +21,8 @@ INCLUDE = PKG.parent / "include"
 OUT_DIR = PKG / "_build"
 LIB = OUT_DIR / "libtrime_gb300.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["bucket.cu", "voronoi.cu", "emit.cu", "update.cu", "mesh.cu"]
+UNITS = ["voronoi_f64.cu", "voronoi_f32.cu", "voronoi_f64b.cu", "voronoi_f32b.cu", "bucket.cu", "emit.cu",
+         "update.cu", "mesh.cu"]
 
 
 def _nvcc() -> str:

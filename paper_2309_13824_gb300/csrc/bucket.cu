@@ -13,14 +13,31 @@
 
 namespace trime {
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_count(IterArgs<T> a) {
-    if (!a.force && a.ctrl->terminated) return;
+// One thread per point.  In a batch, a mesh whose iterations have ended keeps
+// its sorted order: its slots all count into its pad bucket, so the offsets of
+// the meshes after it stay put; the padding slots of a live mesh count there too.
+template <typename T, bool B>
+__global__ void __launch_bounds__(kThreads) k_count(const __grid_constant__ IterArgs<T> a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    const MeshView& V = mesh_of<B>(a, i);
+    bool term = !a.force && V.ctrl->terminated;
+    if constexpr (B) {
+        int loc = i - V.soff;
+        if (term) {
+            if (loc == 0) a.bcount[V.boff + V.nb] = V.n + V.npad;
+            return;
+        }
+        if (loc >= V.n) {
+            if (loc == V.n) a.bcount[V.boff + V.nb] = V.npad;
+            return;
+        }
+    } else {
+        if (term) return;
+    }
     int bx, by;
-    bucket_of(a.P, a.cur.x[i], a.cur.y[i], bx, by);
-    int k = by * a.P.nbx + bx;
+    bucket_of(V.P, a.cur.x[i], a.cur.y[i], bx, by);
+    int k = V.boff + by * V.P.nbx + bx;
     a.key[i] = k;
     a.rank[i] = atomicAdd(&a.bcount[k], 1);
 }
@@ -116,11 +133,13 @@ void launch_scan(const int32_t* in, int32_t* out, int32_t n, int32_t* tmp, cudaS
 }
 
 // ------------------------------------------------------------------ scatter
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_scatter(IterArgs<T> a) {
-    if (!a.force && a.ctrl->terminated) return;
+template <typename T, bool B>
+__global__ void __launch_bounds__(kThreads) k_scatter(const __grid_constant__ IterArgs<T> a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    const MeshView& V = mesh_of<B>(a, i);
+    if (!a.force && V.ctrl->terminated) return;
+    if (B && i - V.soff >= V.n) return;
     int k = a.key[i];
     int d = a.bstart[k] + a.rank[i];
     T x = a.cur.x[i], y = a.cur.y[i];
@@ -132,34 +151,38 @@ __global__ void __launch_bounds__(kThreads) k_scatter(IterArgs<T> a) {
     a.skey[d] = k;
     // geometry cell by the fixed formula floor((x - x0) / dx); the cheaper
     // product with 1/dx decides unless it lands within 1e-9 of a cell edge
+    const DevGrid& sg = V.sdf;
     double xd = (double)x, yd = (double)y;
-    double tx = (xd - a.sdf.x0) * (1.0 / a.sdf.dx), ty = (yd - a.sdf.y0) * (1.0 / a.sdf.dy);
+    double tx = (xd - sg.x0) * (1.0 / sg.dx), ty = (yd - sg.y0) * (1.0 / sg.dy);
     double ftx = tx - floor(tx), fty = ty - floor(ty);
     int gi, gj;
-    int ncx = a.sdf.nx - 1, ncy = a.sdf.ny - 1;
+    int ncx = sg.nx - 1, ncy = sg.ny - 1;
     if (ftx > 1e-9 && ftx < 1.0 - 1e-9 && fty > 1e-9 && fty < 1.0 - 1e-9 && tx >= 0.0 && ty >= 0.0 &&
         tx < (double)ncx && ty < (double)ncy) {
         gi = (int)tx;
         gj = (int)ty;
     } else {
-        point_cell_fixed(a.sdf, xd, yd, gi, gj);
+        point_cell_fixed(sg, xd, yd, gi, gj);
     }
     a.cell[d] = gj * ncx + gi;
     // per-slot float data read by the cell kernels (computed once per point)
     float xh = (float)x, yh = (float)y;
     float xl = (float)(xd - (double)xh), yl = (float)(yd - (double)yh);
     a.pf[d] = make_float4(xh, xl, yh, yl);
-    a.pS[d] = (float)(a.P.fac_voro_bound * a.gh[gj * ncx + gi]);
+    a.pS[d] = (float)(V.P.fac_voro_bound * V.gh[gj * ncx + gi]);
 }
 
 // SoS duplicate rule: of several points at exactly the same position the one
-// with the largest id owns the cell; the others are flagged (empty cells)
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dups(IterArgs<T> a) {
-    if (!a.force && a.ctrl->terminated) return;
+// with the largest id owns the cell; the others are flagged (empty cells).
+// The 32 slots of a warp belong to one mesh.
+template <typename T, bool B>
+__global__ void __launch_bounds__(kThreads) k_dups(const __grid_constant__ IterArgs<T> a) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int sv = s < a.n ? s : a.n - 1;
+    const MeshView& V = mesh_of<B>(a, sv);
+    if (!a.force && V.ctrl->terminated) return;
     unsigned dup = 0;
-    if (s < a.n) {
+    if (s < a.n && (!B || s - V.soff < V.n)) {
         int k = a.skey[s];
         T x = a.srt.x[s], y = a.srt.y[s];
         int id = a.srt.id[s];
@@ -169,64 +192,75 @@ __global__ void __launch_bounds__(kThreads) k_dups(IterArgs<T> a) {
         a.dom[s] = (uint8_t)dup;
     }
     unsigned m = __ballot_sync(0xffffffffu, dup);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctrl->cnt.dup_points, (unsigned long long)__popc(m));
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&V.ctrl->cnt.dup_points, (unsigned long long)__popc(m));
 }
 
 template <typename T>
 void launch_bucket(const IterArgs<T>& a, cudaStream_t st) {
-    int nb = a.P.nbx * a.P.nby;
     int g = (a.n + kThreads - 1) / kThreads;
     if (g < 1) g = 1;
-    cudaMemsetAsync(a.bcount, 0, sizeof(int32_t) * (size_t)nb, st);
-    k_count<T><<<g, kThreads, 0, st>>>(a);
-    launch_scan(a.bcount, a.bstart, nb, a.scan_tmp, st);
-    k_scatter<T><<<g, kThreads, 0, st>>>(a);
-    k_dups<T><<<g, kThreads, 0, st>>>(a);
+    cudaMemsetAsync(a.bcount, 0, sizeof(int32_t) * (size_t)a.nbtot, st);
+    if (a.Vs) {
+        k_count<T, true><<<g, kThreads, 0, st>>>(a);
+        launch_scan(a.bcount, a.bstart, a.nbtot, a.scan_tmp, st);
+        k_scatter<T, true><<<g, kThreads, 0, st>>>(a);
+        k_dups<T, true><<<g, kThreads, 0, st>>>(a);
+    } else {
+        k_count<T, false><<<g, kThreads, 0, st>>>(a);
+        launch_scan(a.bcount, a.bstart, a.nbtot, a.scan_tmp, st);
+        k_scatter<T, false><<<g, kThreads, 0, st>>>(a);
+        k_dups<T, false><<<g, kThreads, 0, st>>>(a);
+    }
 }
 
 template void launch_bucket<double>(const IterArgs<double>&, cudaStream_t);
 template void launch_bucket<float>(const IterArgs<float>&, cudaStream_t);
 
 // ------------------------------------------------------------------ permutations
+// cur slots [s0, s0 + ns) hold one mesh whose ids start at s0
 template <typename T>
-__global__ void k_unpermute(IterArgs<T> a, T* out) {
+__global__ void k_unpermute(const __grid_constant__ IterArgs<T> a, int32_t s0, int32_t ns, T* out) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.n) return;
-    int id = a.cur.id[s];
-    out[2 * (size_t)id] = a.cur.x[s];
-    out[2 * (size_t)id + 1] = a.cur.y[s];
+    if (s >= ns) return;
+    s += s0;
+    size_t id = (size_t)(a.cur.id[s] - s0);
+    out[2 * id] = a.cur.x[s];
+    out[2 * id + 1] = a.cur.y[s];
 }
 
 template <typename T>
-void launch_unpermute(const IterArgs<T>& a, T* out, cudaStream_t st) {
-    int g = (a.n + kThreads - 1) / kThreads;
-    if (g > 0) k_unpermute<T><<<g, kThreads, 0, st>>>(a, out);
+void launch_unpermute(const IterArgs<T>& a, int32_t s0, int32_t ns, T* out, cudaStream_t st) {
+    int g = (ns + kThreads - 1) / kThreads;
+    if (g > 0) k_unpermute<T><<<g, kThreads, 0, st>>>(a, s0, ns, out);
 }
-template void launch_unpermute<double>(const IterArgs<double>&, double*, cudaStream_t);
-template void launch_unpermute<float>(const IterArgs<float>&, float*, cudaStream_t);
+template void launch_unpermute<double>(const IterArgs<double>&, int32_t, int32_t, double*, cudaStream_t);
+template void launch_unpermute<float>(const IterArgs<float>&, int32_t, int32_t, float*, cudaStream_t);
 
 template <typename T>
-__global__ void k_set_state(IterArgs<T> a, const T* xy, const uint8_t* cls, const double* dprev) {
+__global__ void k_set_state(const __grid_constant__ IterArgs<T> a, int32_t s0, int32_t ns, const T* xy,
+                            const uint8_t* cls, const double* dprev) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.n) return;
-    int id = a.cur.id[s];
+    if (s >= ns) return;
+    s += s0;
+    size_t id = (size_t)(a.cur.id[s] - s0);
     if (xy) {
-        a.cur.x[s] = xy[2 * (size_t)id];
-        a.cur.y[s] = xy[2 * (size_t)id + 1];
+        a.cur.x[s] = xy[2 * id];
+        a.cur.y[s] = xy[2 * id + 1];
     }
     if (cls) a.cur.cls[s] = cls[id];
     if (dprev) a.cur.dprev[s] = (T)dprev[id];
 }
 
 template <typename T>
-void launch_set_state(const IterArgs<T>& a, const T* xy, const uint8_t* cls, const double* dprev, cudaStream_t st) {
-    int g = (a.n + kThreads - 1) / kThreads;
-    if (g > 0) k_set_state<T><<<g, kThreads, 0, st>>>(a, xy, cls, dprev);
+void launch_set_state(const IterArgs<T>& a, int32_t s0, int32_t ns, const T* xy, const uint8_t* cls,
+                      const double* dprev, cudaStream_t st) {
+    int g = (ns + kThreads - 1) / kThreads;
+    if (g > 0) k_set_state<T><<<g, kThreads, 0, st>>>(a, s0, ns, xy, cls, dprev);
 }
-template void launch_set_state<double>(const IterArgs<double>&, const double*, const uint8_t*, const double*,
-                                       cudaStream_t);
-template void launch_set_state<float>(const IterArgs<float>&, const float*, const uint8_t*, const double*,
-                                      cudaStream_t);
+template void launch_set_state<double>(const IterArgs<double>&, int32_t, int32_t, const double*, const uint8_t*,
+                                       const double*, cudaStream_t);
+template void launch_set_state<float>(const IterArgs<float>&, int32_t, int32_t, const float*, const uint8_t*,
+                                      const double*, cudaStream_t);
 
 // ------------------------------------------------------------------ standalone a1
 __global__ void k_count_raw(const double* x, const double* y, int32_t n, double x0, double y0, double ibsx,

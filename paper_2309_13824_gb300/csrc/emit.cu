@@ -47,32 +47,31 @@ struct Tri {
 };
 
 // Tests 1-3 on the canonical order (a = smallest id, CCW)
-template <typename T>
-__device__ bool valid_fixed(const IterArgs<T>& a, const Tri& t) {
-    const DevGrid& s = a.sdf;
+__device__ bool valid_fixed(const MeshView& V, const Tri& t) {
+    const DevGrid& s = V.sdf;
     int ncx = s.nx - 1;
     double gx = fdiv(fadd(fadd(t.x[0], t.x[1]), t.x[2]), 3.0);
     double gy = fdiv(fadd(fadd(t.y[0], t.y[1]), t.y[2]), 3.0);
     int gi, gj;
     if (!point_cell_fixed(s, gx, gy, gi, gj)) return false;
     int c = gj * ncx + gi;
-    uint8_t k = a.gcls[c];
+    uint8_t k = V.gcls[c];
     if (k == CELL_INNER) return true;
     if (k == CELL_OUTER) return false;
-    if (bilin_fixed(s, gx, gy) > a.ggeps[c]) return false;
+    if (bilin_fixed(s, gx, gy) > V.ggeps[c]) return false;
     int count = 0;
     for (int e = 0; e < 3; e++) {
         int f = e == 2 ? 0 : e + 1;
         double mx = fmul(fadd(t.x[e], t.x[f]), 0.5), my = fmul(fadd(t.y[e], t.y[f]), 0.5);
         if (!point_cell_fixed(s, mx, my, gi, gj)) continue;
         int q = gj * ncx + gi;
-        if (a.gcls[q] == CELL_INNER) count++;
-        else if (a.gcls[q] == CELL_BOUNDARY && bilin_fixed(s, mx, my) <= a.ggeps[q]) count++;
+        if (V.gcls[q] == CELL_INNER) count++;
+        else if (V.gcls[q] == CELL_BOUNDARY && bilin_fixed(s, mx, my) <= V.ggeps[q]) count++;
     }
     if (count >= 2) return true;
     double ox, oy, R;
     circumcentre_fixed(t.x[0], t.y[0], t.x[1], t.y[1], t.x[2], t.y[2], ox, oy, R);
-    return fdiv(fabs(bilin_fixed(s, ox, oy)), R) <= a.P.T_circ;
+    return fdiv(fabs(bilin_fixed(s, ox, oy)), R) <= V.P.T_circ;
 }
 
 struct Nbr {
@@ -115,9 +114,9 @@ __device__ __forceinline__ Nbr load_nbr(const IterArgs<T>& a, int lab, float4 pi
 
 // emission decision for (i, j, k), CCW as seen from cell i
 template <typename T>
-__device__ bool emitted(const IterArgs<T>& a, const CellC& cc, int idi, int ci, T xi, T yi, const Nbr& j,
-                        const Nbr& k) {
-    const DevParams& P = a.P;
+__device__ bool emitted(const IterArgs<T>& a, const MeshView& V, const CellC& cc, int idi, int ci, T xi, T yi,
+                        const Nbr& j, const Nbr& k) {
+    const DevParams& P = V.P;
     float ax = j.dx, ay = j.dy, bx = k.dx, by = k.dy;
     float M = ax * by - ay * bx;
     float PM = fabsf(ax * by) + fabsf(ay * bx);
@@ -158,7 +157,7 @@ __device__ bool emitted(const IterArgs<T>& a, const CellC& cc, int idi, int ci, 
     double ox, oy, R;
     circumcentre_fixed(xs[r], ys[r], xs[o1], ys[o1], xs[o2], ys[o2], ox, oy, R);
     for (int v = 0; v < 3; v++)
-        if (!reg_contains_fixed(P, xs[v], ys[v], a.gh[cells[v]], ox, oy)) return false;
+        if (!reg_contains_fixed(P, xs[v], ys[v], V.gh[cells[v]], ox, oy)) return false;
     return true;
 }
 
@@ -202,18 +201,17 @@ __device__ __forceinline__ int sdf_cmp_f(const DevGrid& g, const FLoc& L, float 
 
 // Tests 1-2 in float on positions relative to p_i: 1 valid, 0 invalid,
 // -1 undecided (the fixed FP64 formulas decide; Test 3 always goes there)
-template <typename T>
-__device__ int valid_float(const IterArgs<T>& a, const CellC& cc, const Nbr& j, const Nbr& k) {
-    int ncx = a.sdf.nx - 1, ncy = a.sdf.ny - 1;
+__device__ int valid_float(const MeshView& V, const CellC& cc, const Nbr& j, const Nbr& k) {
+    int ncx = V.sdf.nx - 1, ncy = V.sdf.ny - 1;
     float gx = (j.dx + k.dx) * (1.0f / 3.0f), gy = (j.dy + k.dy) * (1.0f / 3.0f);
     FLoc L = locate_f(cc.tx + gx * cc.idx, cc.ty + gy * cc.idy, ncx, ncy);
     if (!L.ok) return -1;
     if (L.off) return 0;
     int c = L.gj * ncx + L.gi;
-    uint8_t cls = a.gcls[c];
+    uint8_t cls = V.gcls[c];
     if (cls == CELL_INNER) return 1;
     if (cls == CELL_OUTER) return 0;
-    int r = sdf_cmp_f(a.sdf, L, (float)a.ggeps[c]);
+    int r = sdf_cmp_f(V.sdf, L, (float)V.ggeps[c]);
     if (r == 1) return 0;
     if (r == 0) return -1;
     // Test 2: edge midpoints (0, j)/2, (j + k)/2, (k, 0)/2 relative to p_i
@@ -225,11 +223,11 @@ __device__ int valid_float(const IterArgs<T>& a, const CellC& cc, const Nbr& j, 
         if (!M.ok) return -1;
         if (M.off) continue;
         int q = M.gj * ncx + M.gi;
-        uint8_t qc = a.gcls[q];
+        uint8_t qc = V.gcls[q];
         if (qc == CELL_INNER) {
             count++;
         } else if (qc == CELL_BOUNDARY) {
-            int rr = sdf_cmp_f(a.sdf, M, (float)a.ggeps[q]);
+            int rr = sdf_cmp_f(V.sdf, M, (float)V.ggeps[q]);
             if (rr == 0) return -1;
             if (rr == -1) count++;
         }
@@ -239,14 +237,14 @@ __device__ int valid_float(const IterArgs<T>& a, const CellC& cc, const Nbr& j, 
 }
 
 template <typename T>
-__device__ bool valid_tri(const IterArgs<T>& a, const CellC& cc, int idi, int ci, T xi, T yi, const Nbr& j,
-                          const Nbr& k) {
-    if (!a.P.validity) return true;
+__device__ bool valid_tri(const IterArgs<T>& a, const MeshView& V, const CellC& cc, int idi, int ci, T xi, T yi,
+                          const Nbr& j, const Nbr& k) {
+    if (!V.P.validity) return true;
     // Test 1 shortcut: every cell within gidist of p_i's cell is inner
     float gx = (j.dx + k.dx) * (1.0f / 3.0f), gy = (j.dy + k.dy) * (1.0f / 3.0f);
     float off = fmaxf(fabsf(gx * cc.idx), fabsf(gy * cc.idy));
-    if (off + 2.01f < (float)a.gidist[ci]) return true;
-    int f = valid_float(a, cc, j, k);
+    if (off + 2.01f < (float)V.gidist[ci]) return true;
+    int f = valid_float(V, cc, j, k);
     if (f >= 0) return f == 1;
     int ids[3] = {idi, j.id, k.id};
     double xs[3] = {(double)xi, (double)a.srt.x[j.slot], (double)a.srt.x[k.slot]};
@@ -259,7 +257,7 @@ __device__ bool valid_tri(const IterArgs<T>& a, const CellC& cc, int idi, int ci
     t.x[0] = xs[r]; t.y[0] = ys[r];
     t.x[1] = xs[o1]; t.y[1] = ys[o1];
     t.x[2] = xs[o2]; t.y[2] = ys[o2];
-    return valid_fixed(a, t);
+    return valid_fixed(V, t);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -278,12 +276,14 @@ __device__ __forceinline__ double warp_min_d(double v) {
     return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
-    if (!a.force && a.ctrl->terminated) return;
+// one block per chunk of kThreads slots (one mesh in a batch)
+template <typename T, bool B>
+__global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterArgs<T> a) {
+    const MeshView& V = mesh_of<B>(a, blockIdx.x * kThreads);
+    if (!a.force && V.ctrl->terminated) return;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double acc[9] = {0, 0, 0, 0, 0, 180.0, 0, 0, 0};
-    if (s < a.n) {
+    if (s < a.n && (!B || s - V.soff < V.n)) {
         int ne = a.ring_n[s];
         int lab[kRingCap];
         const int4* row = reinterpret_cast<const int4*>(a.ring + (size_t)s * kRingCap);
@@ -303,21 +303,21 @@ __global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
             const float4 pi4 = a.pf[s];
             cc.S = a.pS[s];
             double xd = (double)xi, yd = (double)yi;
-            cc.lx = (float)(a.P.bx0 - xd);
-            cc.hx = (float)(a.P.bx1 - xd);
-            cc.ly = (float)(a.P.by0 - yd);
-            cc.hy = (float)(a.P.by1 - yd);
-            cc.tx = (float)((xd - a.sdf.x0) * a.sdf.idx);
-            cc.ty = (float)((yd - a.sdf.y0) * a.sdf.idy);
-            cc.idx = (float)a.sdf.idx;
-            cc.idy = (float)a.sdf.idy;
+            cc.lx = (float)(V.P.bx0 - xd);
+            cc.hx = (float)(V.P.bx1 - xd);
+            cc.ly = (float)(V.P.by0 - yd);
+            cc.hy = (float)(V.P.by1 - yd);
+            cc.tx = (float)((xd - V.sdf.x0) * V.sdf.idx);
+            cc.ty = (float)((yd - V.sdf.y0) * V.sdf.idy);
+            cc.idx = (float)V.sdf.idx;
+            cc.idy = (float)V.sdf.idy;
             float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f, q5 = 180.f;
             Nbr first = load_nbr(a, lab[0], pi4, xi, yi);
             Nbr cur = first;
             for (int t = 0; t < ne; t++) {
                 Nbr nxt = t + 1 < ne ? load_nbr(a, lab[t + 1], pi4, xi, yi) : first;
-                if (cur.slot >= 0 && nxt.slot >= 0 && emitted(a, cc, idi, ci, xi, yi, cur, nxt) &&
-                    valid_tri(a, cc, idi, ci, xi, yi, cur, nxt)) {
+                if (cur.slot >= 0 && nxt.slot >= 0 && emitted(a, V, cc, idi, ci, xi, yi, cur, nxt) &&
+                    valid_tri(a, V, cc, idi, ci, xi, yi, cur, nxt)) {
                     vm |= 1u << t;
                     if (idi < cur.id && idi < nxt.id) {
                         // quality of the triangle (Eq. 11), float from the relative coordinates
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
                 if (!(idi < a.srt.id[j])) continue;
                 T xj = a.srt.x[j], yj = a.srt.y[j];
                 T dx = xj - xi, dy = yj - yi;
-                T mu = bilin<T>(a.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
+                T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
                 acc[6] += 1.0;
                 acc[7] += (double)(dx * dx + dy * dy);
                 acc[8] += (double)(mu * mu);  // Eq. 3 sums stay in T precision
@@ -387,16 +387,19 @@ __global__ void __launch_bounds__(kThreads) k_emit(IterArgs<T> a) {
 
 template <typename T>
 void launch_emit(const IterArgs<T>& a, int nblocks, cudaStream_t st) {
-    k_emit<T><<<nblocks, kThreads, 0, st>>>(a);
+    if (a.Vs) k_emit<T, true><<<nblocks, kThreads, 0, st>>>(a);
+    else k_emit<T, false><<<nblocks, kThreads, 0, st>>>(a);
 }
 template void launch_emit<double>(const IterArgs<double>&, int, cudaStream_t);
 template void launch_emit<float>(const IterArgs<float>&, int, cudaStream_t);
 
 // ------------------------------------------------------------------ triangle output
+// on the slots [s0, s0 + ns) of one mesh; ids are written relative to s0
 template <typename T>
-__global__ void k_tri_count(IterArgs<T> a, int32_t* cnt) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.n) return;
+__global__ void k_tri_count(const __grid_constant__ IterArgs<T> a, int32_t s0, int32_t ns, int32_t* cnt) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ns) return;
+    int s = s0 + r;
     int ne = a.ring_n[s];
     uint32_t vm = a.vmask[s];
     int idi = a.srt.id[s];
@@ -406,43 +409,48 @@ __global__ void k_tri_count(IterArgs<T> a, int32_t* cnt) {
         int j = a.ring[(size_t)s * kRingCap + t], k = a.ring[(size_t)s * kRingCap + (t + 1 == ne ? 0 : t + 1)];
         if (idi < a.srt.id[j] && idi < a.srt.id[k]) c++;
     }
-    cnt[s] = c;
+    cnt[r] = c;
 }
 
 template <typename T>
-__global__ void k_tri_write(IterArgs<T> a, const int32_t* off, int32_t* tri) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.n) return;
+__global__ void k_tri_write(const __grid_constant__ IterArgs<T> a, int32_t s0, int32_t ns, const int32_t* off,
+                            int32_t* tri) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ns) return;
+    int s = s0 + r;
     int ne = a.ring_n[s];
     uint32_t vm = a.vmask[s];
     int idi = a.srt.id[s];
-    int o = off[s];
+    int o = off[r];
     for (int t = 0; t < ne; t++) {
         if (!((vm >> t) & 1u)) continue;
         int j = a.ring[(size_t)s * kRingCap + t], k = a.ring[(size_t)s * kRingCap + (t + 1 == ne ? 0 : t + 1)];
         int idj = a.srt.id[j], idk = a.srt.id[k];
         if (idi < idj && idi < idk) {
-            tri[3 * (size_t)o] = idi;
-            tri[3 * (size_t)o + 1] = idj;
-            tri[3 * (size_t)o + 2] = idk;
+            tri[3 * (size_t)o] = idi - s0;
+            tri[3 * (size_t)o + 1] = idj - s0;
+            tri[3 * (size_t)o + 2] = idk - s0;
             o++;
         }
     }
 }
 
 template <typename T>
-void launch_tri_count(const IterArgs<T>& a, int32_t* cnt, cudaStream_t st) {
-    int g = (a.n + kThreads - 1) / kThreads;
-    if (g > 0) k_tri_count<T><<<g, kThreads, 0, st>>>(a, cnt);
+void launch_tri_count(const IterArgs<T>& a, int32_t s0, int32_t ns, int32_t* cnt, cudaStream_t st) {
+    int g = (ns + kThreads - 1) / kThreads;
+    if (g > 0) k_tri_count<T><<<g, kThreads, 0, st>>>(a, s0, ns, cnt);
 }
 template <typename T>
-void launch_tri_write(const IterArgs<T>& a, const int32_t* off, int32_t* tri, cudaStream_t st) {
-    int g = (a.n + kThreads - 1) / kThreads;
-    if (g > 0) k_tri_write<T><<<g, kThreads, 0, st>>>(a, off, tri);
+void launch_tri_write(const IterArgs<T>& a, int32_t s0, int32_t ns, const int32_t* off, int32_t* tri,
+                      cudaStream_t st) {
+    int g = (ns + kThreads - 1) / kThreads;
+    if (g > 0) k_tri_write<T><<<g, kThreads, 0, st>>>(a, s0, ns, off, tri);
 }
-template void launch_tri_count<double>(const IterArgs<double>&, int32_t*, cudaStream_t);
-template void launch_tri_count<float>(const IterArgs<float>&, int32_t*, cudaStream_t);
-template void launch_tri_write<double>(const IterArgs<double>&, const int32_t*, int32_t*, cudaStream_t);
-template void launch_tri_write<float>(const IterArgs<float>&, const int32_t*, int32_t*, cudaStream_t);
+template void launch_tri_count<double>(const IterArgs<double>&, int32_t, int32_t, int32_t*, cudaStream_t);
+template void launch_tri_count<float>(const IterArgs<float>&, int32_t, int32_t, int32_t*, cudaStream_t);
+template void launch_tri_write<double>(const IterArgs<double>&, int32_t, int32_t, const int32_t*, int32_t*,
+                                       cudaStream_t);
+template void launch_tri_write<float>(const IterArgs<float>&, int32_t, int32_t, const int32_t*, int32_t*,
+                                      cudaStream_t);
 
 }  // namespace trime

@@ -175,7 +175,7 @@ constexpr int kExactFail = 2;
 // sign of (b-a) x (c-a), exact: the determinant with a column of ones is
 // the sum of the six products ax by - ay bx + bx cy - by cx + cx ay - cy ax,
 // each split exactly into two doubles and accumulated by growth
-__device__ __noinline__ int orient_exact(const double* a, const double* b, const double* c) {
+static __device__ __noinline__ int orient_exact(const double* a, const double* b, const double* c) {
     const double* P[3] = {a, b, c};
     bool ok = true;
     for (int k = 0; k < 3; k++)
@@ -204,7 +204,7 @@ __device__ __noinline__ int orient_exact(const double* a, const double* b, const
 }
 
 // sign of det of rows [x, y, x^2 + y^2, 1] of (a, b, c, d), exact
-__device__ __noinline__ int incircle_exact(const double* a, const double* b, const double* c, const double* d) {
+static __device__ __noinline__ int incircle_exact(const double* a, const double* b, const double* c, const double* d) {
     const double* P[3] = {a, b, c};
     double dx[3][2], dy[3][2];
     bool ok = true;
@@ -258,7 +258,7 @@ __device__ __noinline__ int incircle_exact(const double* a, const double* b, con
 // exact value first, then the coefficient of the largest perturbation with a
 // non-zero cofactor: C_a = orient(b,c,d), C_b = -orient(a,c,d),
 // C_c = orient(a,b,d), C_d = -orient(a,b,c).  Returns kExactFail on a guard.
-__device__ __noinline__ int incircle_sos(const double* a, int ia, const double* b, int ib, const double* c, int ic,
+static __device__ __noinline__ int incircle_sos(const double* a, int ia, const double* b, int ib, const double* c, int ic,
                                          const double* d, int id) {
     int s = incircle_exact(a, b, c, d);
     if (s == 0) {

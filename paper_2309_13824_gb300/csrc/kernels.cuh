@@ -24,10 +24,14 @@ struct State {
     T* dprev;
 };
 
-template <typename T>
-struct IterArgs {
-    int32_t n;
-    int32_t force;       // ignore the terminated flag (rebuild-only calls)
+// Everything a kernel reads that belongs to one mesh.  A batch concatenates
+// its meshes' slots, each mesh padded to whole chunks of kChunk slots, so a
+// block of the emit / update kernels and a warp of the Voronoi kernel always
+// work on one mesh.
+constexpr int kChunk = 256;
+constexpr int kChunkShift = 8;
+
+struct MeshView {
     DevParams P;
     DevGrid sdf, siz;
     // geometry grid on the SDF grid's cells
@@ -35,47 +39,79 @@ struct IterArgs {
     const double* gh;
     const double* ggeps;
     const uint8_t* gidist;  // Chebyshev distance to the nearest non-inner cell, capped
+    DevCtrl* ctrl;
+    int32_t soff, n;        // first slot, number of points
+    int32_t boff, nb;       // first bucket, buckets (a pad bucket follows them)
+    int32_t c0, c1;         // chunks [c0, c1): the emit / update partials of this mesh
+    int32_t npad;           // padding slots after the points
+    int32_t pad0;
+};
+
+template <typename T>
+struct IterArgs {
+    int32_t n;         // slots (single mesh: points; batch: padded total)
+    int32_t force;     // ignore the terminated flags (rebuild-only calls)
+    int32_t nmesh;     // meshes in Vs (batched launches)
+    int32_t nbtot;     // buckets in bcount / bstart, pad buckets included
+    MeshView V;        // the mesh of single-mesh launches
+    const MeshView* Vs;     // [nmesh] per-mesh views of batched launches
+    const int32_t* cmesh;   // [n / kChunk] mesh of each chunk
+    int32_t* ovf_n;    // cells queued for the 32-lane Voronoi pass
     State<T> cur, srt;
     int32_t* cell;     // [n] geometry cell of each sorted slot (fixed formula)
     int32_t* key;      // [n] bucket of each cur point
     int32_t* rank;     // [n] rank inside its bucket
     int32_t* skey;     // [n] bucket of each sorted slot
     uint8_t* dom;      // [n] sorted slot has an exact duplicate with a larger id
-    int32_t* bcount;   // [nb] bucket counts
-    int32_t* bstart;   // [nb + 1]
+    int32_t* bcount;   // [nbtot] bucket counts
+    int32_t* bstart;   // [nbtot + 1]
     int32_t* scan_tmp;
     int32_t* ring;
     uint8_t* ring_n;
     float* cellR;
     uint32_t* vmask;
-    EmitPartial* ep;
+    EmitPartial* ep;   // [n / kThreads] one per block of the emit kernel
     UpdatePartial* up;
-    DevCtrl* ctrl;
     double* dbg;       // [8][n] by original id, written when P.debug
     int32_t* ovf_list; // [n] cells whose 16-lane clipping ran out of lanes
     float4* pf;        // [n] sorted positions as float pairs (xhi, xlo, yhi, ylo)
     float* pS;         // [n] octagon span S = fac_voro_bound * h of each sorted slot
 };
 
+// the mesh owning a slot: the launch's own view, or the batch table entry of
+// the slot's chunk
+template <bool B, typename T>
+__device__ __forceinline__ const MeshView& mesh_of(const IterArgs<T>& a, int slot) {
+    if constexpr (B) return a.Vs[__ldg(a.cmesh + (slot >> kChunkShift))];
+    else return a.V;
+}
+
 // a1: counting sort
 template <typename T> void launch_bucket(const IterArgs<T>& a, cudaStream_t st);
 void launch_scan(const int32_t* in, int32_t* out, int32_t n, int32_t* tmp, cudaStream_t st);
 // a2
-template <typename T> void launch_voronoi(const IterArgs<T>& a, cudaStream_t st);
+template <typename T, bool B> void launch_voronoi_impl(const IterArgs<T>& a, int lanes, cudaStream_t st);
+template <typename T>
+inline void launch_voronoi(const IterArgs<T>& a, int lanes, cudaStream_t st) {
+    if (a.Vs) launch_voronoi_impl<T, true>(a, lanes, st);
+    else launch_voronoi_impl<T, false>(a, lanes, st);
+}
 // a3/a4 + quality partials (a8) + Eq. 3 sums
 template <typename T> void launch_emit(const IterArgs<T>& a, int nblocks, cudaStream_t st);
 // a8 finalisation + hybrid / termination logic
-void launch_stats_pre(DevCtrl* ctrl, const EmitPartial* ep, int nparts, int decide, int force, DevParams P,
-                      cudaStream_t st);
+template <typename T> void launch_stats_pre(const IterArgs<T>& a, int decide, cudaStream_t st);
 // a5/a6/a7
 template <typename T> void launch_update(const IterArgs<T>& a, int nblocks, cudaStream_t st);
-void launch_stats_post(DevCtrl* ctrl, const UpdatePartial* up, int nparts, cudaStream_t st);
-// output helpers
-template <typename T> void launch_tri_count(const IterArgs<T>& a, int32_t* cnt, cudaStream_t st);
-template <typename T> void launch_tri_write(const IterArgs<T>& a, const int32_t* off, int32_t* tri, cudaStream_t st);
-template <typename T> void launch_unpermute(const IterArgs<T>& a, T* out_xy, cudaStream_t st);
-template <typename T> void launch_set_state(const IterArgs<T>& a, const T* xy, const uint8_t* cls,
-                                            const double* dprev, cudaStream_t st);
+template <typename T> void launch_stats_post(const IterArgs<T>& a, cudaStream_t st);
+// output helpers on the slots [s0, s0 + ns) of one mesh whose ids start at s0
+template <typename T> void launch_tri_count(const IterArgs<T>& a, int32_t s0, int32_t ns, int32_t* cnt,
+                                            cudaStream_t st);
+template <typename T> void launch_tri_write(const IterArgs<T>& a, int32_t s0, int32_t ns, const int32_t* off,
+                                            int32_t* tri, cudaStream_t st);
+template <typename T> void launch_unpermute(const IterArgs<T>& a, int32_t s0, int32_t ns, T* out_xy,
+                                            cudaStream_t st);
+template <typename T> void launch_set_state(const IterArgs<T>& a, int32_t s0, int32_t ns, const T* xy,
+                                            const uint8_t* cls, const double* dprev, cudaStream_t st);
 void launch_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out,
                        cudaStream_t st);
 // standalone a1 on raw arrays (mesh_bucket_points)

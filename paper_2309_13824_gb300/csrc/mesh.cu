@@ -6,6 +6,13 @@
 // CUDA graph that mesh_step replays.  Work runs on a private stream that is
 // ordered after / before the caller's stream with events, so graph capture
 // works whatever stream the caller passes.
+//
+// A mesh_t holds one mesh; a mesh_batch_t holds several independent meshes
+// whose slots are concatenated (each padded to whole chunks of kChunk slots)
+// and stepped by the same launches: one launch per stage covers every mesh,
+// each block or warp reading its mesh's view from a device table.  The
+// batch's bucket size and Voronoi lane count can be picked by timing the
+// candidates on the batch itself (autotuning at mesh_batch_init).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -34,18 +41,40 @@ int set_error(int code, const char* msg) { return fail(code, msg); }
         if (e_ != cudaSuccess) return fail(TRIME_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-struct mesh_s {
-    int prec = 0;
+// one mesh of a mesh_s
+struct Part {
     int64_t n = 0;
-    mesh_params P{};
+    int32_t soff = 0, npad = 0;  // first slot, padding slots after the points
+    int32_t boff = 0, nb = 0;    // first bucket, buckets
+    int32_t c0 = 0, c1 = 0;      // chunks (blocks of the emit / update kernels)
     DevParams dp{};
-    cudaStream_t user = nullptr, st = nullptr;
-    cudaEvent_t ev = nullptr;
     DevGrid sdf{}, siz{};
     uint8_t* gcls = nullptr;
     double* gh = nullptr;
     double* ggeps = nullptr;
     uint8_t* gidist = nullptr;
+    double rho_eff = 0;          // point-weighted mean point density
+};
+
+struct TuneCand {
+    double nopt;
+    int lanes;
+    double ms;
+};
+
+struct mesh_s {
+    int prec = 0;
+    bool batched = false;
+    int64_t nslots = 0;          // slots of all parts
+    mesh_params P{};
+    std::vector<Part> parts;
+    int nbtot = 0;               // buckets in use (pad buckets included)
+    int nbcap = 0;               // buckets allocated
+    int lanes = 16;              // Voronoi lanes per cell
+    double nopt = 3.3;           // points per bucket the grids are sized for
+    std::vector<TuneCand> tune;  // autotuning record
+    cudaStream_t user = nullptr, st = nullptr;
+    cudaEvent_t ev = nullptr;
     void *cx = nullptr, *cy = nullptr, *cdp = nullptr, *sx = nullptr, *sy = nullptr, *sdp = nullptr;
     int32_t *cid = nullptr, *sid = nullptr;
     uint8_t *ccls = nullptr, *scls = nullptr;
@@ -59,8 +88,11 @@ struct mesh_s {
     EmitPartial* ep = nullptr;
     UpdatePartial* up = nullptr;
     int nblk = 1;
-    DevCtrl* ctrl = nullptr;
-    DevCtrl* hctrl = nullptr;  // pinned host copy
+    DevCtrl* ctrl = nullptr;     // [parts]
+    DevCtrl* hctrl = nullptr;    // pinned host copy [parts]
+    int32_t* ovf_n = nullptr;
+    MeshView* dviews = nullptr;  // [parts] (batch)
+    int32_t* cmesh = nullptr;    // [nslots / kChunk] (batch)
     double* dbg = nullptr;
     int32_t *tcnt = nullptr, *toff = nullptr, *tbuf = nullptr;
     int32_t* ovf_list = nullptr;
@@ -70,6 +102,8 @@ struct mesh_s {
     cudaGraphExec_t gexec = nullptr;
     std::vector<void*> allocs;
 };
+
+struct mesh_batch_s : mesh_s {};
 
 template <typename T>
 static T* dalloc(mesh_s* m, size_t count, int& rc) {
@@ -208,19 +242,88 @@ static int host_geometry(const mesh_grid2d& sdf, const mesh_grid2d& siz, int64_t
     return 0;
 }
 
+// ------------------------------------------------------------------ layout
+// neighbour buckets: the paper sizes the block grid for N_opt points per
+// block under uniform density (Sec. 3.2); with adaptive density we size it so
+// that the bucket holding a typical point expects nopt points
+static void size_buckets(Part& p, double nopt) {
+    DevParams& d = p.dp;
+    double W = d.bx1 - d.bx0, H = d.by1 - d.by0;
+    int64_t n = p.n;
+    double lam = std::sqrt((double)std::max<int64_t>(n, 1) / (nopt * W * H));
+    if (p.rho_eff > 0 && n > 0) lam = std::max(lam, std::sqrt(p.rho_eff / nopt));
+    double cap = std::sqrt((4.0 * (double)n + 1024.0) / (W * H));
+    lam = std::min(lam, cap);
+    d.nbx = std::max(1, (int)std::ceil(lam * W));
+    d.nby = std::max(1, (int)std::ceil(lam * H));
+    d.bsx = W / d.nbx;
+    d.bsy = H / d.nby;
+    d.bx0f = (float)d.bx0;
+    d.by0f = (float)d.by0;
+    d.ibsxf = (float)(1.0 / d.bsx);
+    d.ibsyf = (float)(1.0 / d.bsy);
+    p.nb = d.nbx * d.nby;
+}
+
+// bucket offsets of every part; a batch gives each part one pad bucket
+static int layout_buckets(mesh_s* m, double nopt) {
+    int64_t tot = 0;
+    for (Part& p : m->parts) {
+        size_buckets(p, nopt);
+        p.boff = (int32_t)tot;
+        tot += p.nb + (m->batched ? 1 : 0);
+    }
+    if (tot > (int64_t)1 << 30) return fail(TRIME_EINVAL, "too many buckets");
+    m->nbtot = (int)tot;
+    m->nopt = nopt;
+    return 0;
+}
+
+static MeshView view_of(const mesh_s* m, int k) {
+    const Part& p = m->parts[k];
+    MeshView V;
+    std::memset(&V, 0, sizeof V);
+    V.P = p.dp;
+    V.sdf = p.sdf;
+    V.siz = p.siz;
+    V.gcls = p.gcls;
+    V.gh = p.gh;
+    V.ggeps = p.ggeps;
+    V.gidist = p.gidist;
+    V.ctrl = m->ctrl + k;
+    V.soff = p.soff;
+    V.n = (int32_t)p.n;
+    V.boff = p.boff;
+    V.nb = p.nb;
+    V.c0 = p.c0;
+    V.c1 = p.c1;
+    V.npad = p.npad;
+    return V;
+}
+
+// device table of the views (batch only), after any change of the layout
+static int upload_views(mesh_s* m) {
+    if (!m->batched) return 0;
+    std::vector<MeshView> v(m->parts.size());
+    for (size_t k = 0; k < v.size(); k++) v[k] = view_of(m, (int)k);
+    CUDA_TRY(cudaMemcpyAsync(m->dviews, v.data(), v.size() * sizeof(MeshView), cudaMemcpyHostToDevice, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return 0;
+}
+
 // ------------------------------------------------------------------ enqueue helpers
 template <typename T>
 static IterArgs<T> make_args(mesh_s* m, int force) {
     IterArgs<T> a;
-    a.n = (int32_t)m->n;
+    std::memset(&a, 0, sizeof a);
+    a.n = (int32_t)m->nslots;
     a.force = force;
-    a.P = m->dp;
-    a.sdf = m->sdf;
-    a.siz = m->siz;
-    a.gcls = m->gcls;
-    a.gh = m->gh;
-    a.ggeps = m->ggeps;
-    a.gidist = m->gidist;
+    a.nmesh = (int32_t)m->parts.size();
+    a.nbtot = m->nbtot;
+    a.V = view_of(m, 0);
+    a.Vs = m->batched ? m->dviews : nullptr;
+    a.cmesh = m->batched ? m->cmesh : nullptr;
+    a.ovf_n = m->ovf_n;
     a.cur = {(T*)m->cx, (T*)m->cy, m->cid, m->ccls, (T*)m->cdp};
     a.srt = {(T*)m->sx, (T*)m->sy, m->sid, m->scls, (T*)m->sdp};
     a.cell = m->cell;
@@ -237,7 +340,6 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.vmask = m->vmask;
     a.ep = m->ep;
     a.up = m->up;
-    a.ctrl = m->ctrl;
     a.dbg = m->dbg;
     a.ovf_list = m->ovf_list;
     a.pf = m->pf;
@@ -249,9 +351,9 @@ template <typename T>
 static void enqueue_rebuild(mesh_s* m, int force, int decide) {
     IterArgs<T> a = make_args<T>(m, force);
     launch_bucket<T>(a, m->st);
-    launch_voronoi<T>(a, m->st);
+    launch_voronoi<T>(a, m->lanes, m->st);
     launch_emit<T>(a, m->nblk, m->st);
-    launch_stats_pre(m->ctrl, m->ep, m->nblk, decide, force, m->dp, m->st);
+    launch_stats_pre<T>(a, decide, m->st);
 }
 
 template <typename T>
@@ -259,7 +361,7 @@ static void enqueue_iteration(mesh_s* m) {
     enqueue_rebuild<T>(m, 0, 1);
     IterArgs<T> a = make_args<T>(m, 0);
     launch_update<T>(a, m->nblk, m->st);
-    launch_stats_post(m->ctrl, m->up, m->nblk, m->st);
+    launch_stats_post<T>(a, m->st);
 }
 
 static void enqueue(mesh_s* m, bool iteration, int force) {
@@ -285,13 +387,19 @@ static int sync_out(mesh_s* m) {
 }
 
 static int read_ctrl(mesh_s* m) {
-    CUDA_TRY(cudaMemcpyAsync(m->hctrl, m->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, m->st));
+    CUDA_TRY(cudaMemcpyAsync(m->hctrl, m->ctrl, sizeof(DevCtrl) * m->parts.size(), cudaMemcpyDeviceToHost, m->st));
     CUDA_TRY(cudaStreamSynchronize(m->st));
     return 0;
 }
 
-static void fill_stats(const mesh_s* m, int iters, mesh_stats* s) {
-    const DevCtrl& c = *m->hctrl;
+static bool all_terminated(const mesh_s* m) {
+    for (size_t k = 0; k < m->parts.size(); k++)
+        if (!m->hctrl[k].terminated) return false;
+    return true;
+}
+
+static void fill_stats(const mesh_s* m, int k, int iters, mesh_stats* s) {
+    const DevCtrl& c = m->hctrl[k];
     std::memset(s, 0, sizeof *s);
     s->iterations = iters;
     s->terminated = c.terminated;
@@ -322,9 +430,553 @@ static void fill_stats(const mesh_s* m, int iters, mesh_stats* s) {
     s->vor_wide = (int64_t)c.cnt.vor_wide;
 }
 
+static bool guard_tripped(const mesh_s* m) {
+    for (size_t k = 0; k < m->parts.size(); k++) {
+        const DevCounters& c = m->hctrl[k].cnt;
+        if (c.ring_overflow || c.exact_overflow) return true;
+    }
+    return false;
+}
+
+__global__ void k_reset_counters(DevCtrl* ctrl, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) ctrl[k].cnt = DevCounters{};
+}
+
 static int reset_counters(mesh_s* m) {
-    CUDA_TRY(cudaMemsetAsync(&m->ctrl->cnt, 0, sizeof(DevCounters), m->st));
+    int n = (int)m->parts.size();
+    k_reset_counters<<<(n + 127) / 128, 128, 0, m->st>>>(m->ctrl, n);
+    CUDA_TRY(cudaGetLastError());
     return 0;
+}
+
+// ------------------------------------------------------------------ creation
+static int check_params(const mesh_params& P) {
+    if (P.precision != 0 && P.precision != 1) return fail(TRIME_EINVAL, "precision must be 0 or 1");
+    if (P.method < 0 || P.method > 2) return fail(TRIME_EINVAL, "method must be 0, 1 or 2");
+    if (P.quad_max_level < 1 || P.quad_max_level > 9) return fail(TRIME_EINVAL, "quad_max_level must be 1..9");
+    if (P.newton_max < 0 || P.trace_max < 1) return fail(TRIME_EINVAL, "bad newton_max / trace_max");
+    if (!(P.N_opt > 0) || !(P.fac_voro_bound > 0) || !(P.dt >= 0)) return fail(TRIME_EINVAL, "bad parameter value");
+    return 0;
+}
+
+static int check_part(const mesh_grid2d* sdf, const mesh_grid2d* sizing, const void* xy, int64_t n, int prec,
+                      const std::string& who) {
+    if (n < 0 || n > (int64_t)(1 << 30)) return fail(TRIME_EINVAL, who + "n out of range");
+    if (n > 0 && !xy) return fail(TRIME_EINVAL, who + "xy is NULL");
+    if (!grid_ok(sdf)) return fail(TRIME_EINVAL, who + "invalid SDF grid");
+    if (!grid_ok(sizing)) return fail(TRIME_EINVAL, who + "invalid sizing grid");
+    for (size_t k = 0; k < (size_t)sizing->nx * sizing->ny; k++)
+        if (!(sizing->v[k] > 0.0f)) return fail(TRIME_EINVAL, who + "sizing values must be positive");
+    for (int64_t i = 0; i < n; i++) {
+        double x = prec == 0 ? ((const double*)xy)[2 * i] : (double)((const float*)xy)[2 * i];
+        double y = prec == 0 ? ((const double*)xy)[2 * i + 1] : (double)((const float*)xy)[2 * i + 1];
+        if (!std::isfinite(x) || !std::isfinite(y) || x < sdf->x0 || x > sdf->x1 || y < sdf->y0 || y > sdf->y1)
+            return fail(TRIME_EINVAL,
+                        who + "point " + std::to_string(i) + " is not finite or outside the SDF grid box");
+    }
+    return 0;
+}
+
+static DevGrid dev_grid(const mesh_grid2d* g, const float* dv) {
+    DevGrid d{g->nx, g->ny, g->x0, g->y0, g->x1, g->y1, (g->x1 - g->x0) / (double)(g->nx - 1),
+              (g->y1 - g->y0) / (double)(g->ny - 1), dv, 0.0, 0.0};
+    d.idx = 1.0 / d.dx;
+    d.idy = 1.0 / d.dy;
+    return d;
+}
+
+static void fill_devparams(DevParams& d, const mesh_params& P, const HostGeometry& G, const mesh_grid2d* sdf) {
+    std::memset(&d, 0, sizeof d);
+    d.bounded = P.bounded;
+    d.validity = P.validity;
+    d.newton_max = P.newton_max;
+    d.trace_max = P.trace_max;
+    d.quad_max_level = P.quad_max_level;
+    d.debug = P.debug != 0;
+    d.fac_F = P.fac_F;
+    d.k_spring = P.k_spring;
+    d.dt = P.dt;
+    d.fac_pt = P.fac_pt;
+    d.fac_geps = P.fac_geps;
+    d.fac_voro_bound = P.fac_voro_bound;
+    d.fac_end = P.fac_end;
+    d.T_circ = P.T_circ;
+    d.T_switch = P.T_switch;
+    d.T_end_q = P.T_end_q;
+    d.T_end_amax = P.T_end_amax;
+    d.damping = P.damping;
+    d.havg = G.havg;
+    d.bx0 = sdf->x0;
+    d.by0 = sdf->y0;
+    d.bx1 = sdf->x1;
+    d.by1 = sdf->y1;
+}
+
+// uploads part k's grids and initial state (ids soff + i in input order,
+// classes by Sec. 4.3 on the host)
+static int upload_part(mesh_s* m, int k, const mesh_grid2d* sdf, const mesh_grid2d* sizing, const void* xy,
+                       const HostGeometry& G) {
+    Part& p = m->parts[k];
+    size_t N = (size_t)p.n, T = m->prec == 0 ? sizeof(double) : sizeof(float);
+    size_t ns = (size_t)sdf->nx * sdf->ny, nz = (size_t)sizing->nx * sizing->ny;
+    size_t nc = (size_t)(sdf->nx - 1) * (sdf->ny - 1);
+    int rc = 0;
+    float* dsdf = dalloc<float>(m, ns, rc);
+    float* dsiz = dalloc<float>(m, nz, rc);
+    p.gcls = dalloc<uint8_t>(m, nc, rc);
+    p.gh = dalloc<double>(m, nc, rc);
+    p.ggeps = dalloc<double>(m, nc, rc);
+    p.gidist = dalloc<uint8_t>(m, nc, rc);
+    if (rc) return rc;
+    p.sdf = dev_grid(sdf, dsdf);
+    p.siz = dev_grid(sizing, dsiz);
+    auto H2D = [&](void* dst, const void* src, size_t bytes) {
+        return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, m->st) == cudaSuccess;
+    };
+    bool ok = H2D(dsdf, sdf->v, ns * sizeof(float)) && H2D(dsiz, sizing->v, nz * sizeof(float)) &&
+              H2D(p.gcls, G.cls.data(), nc) && H2D(p.gh, G.h.data(), nc * sizeof(double)) &&
+              H2D(p.ggeps, G.geps.data(), nc * sizeof(double)) && H2D(p.gidist, G.idist.data(), nc);
+    std::vector<int32_t> ids(N);
+    std::vector<uint8_t> cls(N);
+    std::vector<char> dp(N * T), xs(N * T), ys(N * T);
+    double sdx = p.sdf.dx, sdy = p.sdf.dy;
+    int ncx = sdf->nx - 1, ncy = sdf->ny - 1;
+    for (size_t i = 0; i < N; i++) {
+        ids[i] = p.soff + (int32_t)i;
+        double x = m->prec == 0 ? ((const double*)xy)[2 * i] : (double)((const float*)xy)[2 * i];
+        double y = m->prec == 0 ? ((const double*)xy)[2 * i + 1] : (double)((const float*)xy)[2 * i + 1];
+        double fi = std::floor((x - sdf->x0) / sdx), fj = std::floor((y - sdf->y0) / sdy);
+        bool inside = fi >= 0 && fi <= ncx - 1 && fj >= 0 && fj <= ncy - 1;
+        int gi = !(fi >= 0) ? 0 : (fi > ncx - 1 ? ncx - 1 : (int)fi);
+        int gj = !(fj >= 0) ? 0 : (fj > ncy - 1 ? ncy - 1 : (int)fj);
+        size_t c = (size_t)gj * ncx + gi;
+        uint8_t pc = PT_BOUNDARY;
+        if (inside && G.cls[c] == CELL_INNER) pc = PT_INNER;
+        else if (inside && G.cls[c] == CELL_BOUNDARY) {
+            double s = host_bilin(*sdf, sdx, sdy, x, y);
+            if (s < -G.geps[c]) pc = PT_INNER;
+        }
+        cls[i] = pc;  // reading: a point outside at init counts as boundary
+        double h = G.h[c];
+        if (m->prec == 0) {
+            ((double*)xs.data())[i] = x;
+            ((double*)ys.data())[i] = y;
+            ((double*)dp.data())[i] = h;  // reading: eps_c = 1 at the first iteration
+        } else {
+            ((float*)xs.data())[i] = (float)x;
+            ((float*)ys.data())[i] = (float)y;
+            ((float*)dp.data())[i] = (float)h;
+        }
+    }
+    size_t o = (size_t)p.soff;
+    ok = ok && H2D((char*)m->cx + o * T, xs.data(), N * T) && H2D((char*)m->cy + o * T, ys.data(), N * T) &&
+         H2D((char*)m->cdp + o * T, dp.data(), N * T) && H2D(m->cid + o, ids.data(), N * sizeof(int32_t)) &&
+         H2D(m->ccls + o, cls.data(), N);
+    DevCtrl c0;
+    std::memset(&c0, 0, sizeof c0);
+    c0.method_param = m->P.method;
+    c0.last_method = -1;
+    ok = ok && H2D(m->ctrl + k, &c0, sizeof c0);
+    // the host vectors above must outlive the copies
+    if (!ok || cudaStreamSynchronize(m->st) != cudaSuccess) return fail(TRIME_ECUDA, "initial upload failed");
+    return 0;
+}
+
+static int capture_graph(mesh_s* m) {
+    if (m->gexec) {
+        cudaGraphExecDestroy(m->gexec);
+        m->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return fail(TRIME_ECUDA, "cudaStreamBeginCapture failed");
+    enqueue(m, true, 0);
+    cudaError_t e = cudaStreamEndCapture(m->st, &graph);
+    if (e != cudaSuccess) return fail(TRIME_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&m->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(TRIME_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return 0;
+}
+
+// times rebuilds (a1..a4, no move) for each candidate bucket size and Voronoi
+// lane count and keeps the fastest; results do not depend on the choice
+static int autotune(mesh_s* m, const std::vector<double>& nopts) {
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int lanes_c[2] = {16, 32};
+    TuneCand best{m->nopt, m->lanes, 1e300};
+    m->tune.clear();
+    int rc = 0;
+    for (double no : nopts) {
+        for (int ln : lanes_c) {
+            if ((rc = layout_buckets(m, no)) || (rc = upload_views(m))) break;
+            m->lanes = ln;
+            enqueue(m, false, 1);  // warm-up
+            CUDA_TRY(cudaEventRecord(e0, m->st));
+            for (int r = 0; r < 2; r++) enqueue(m, false, 1);
+            CUDA_TRY(cudaEventRecord(e1, m->st));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            TuneCand c{no, ln, ms * 0.5};
+            m->tune.push_back(c);
+            if (c.ms < best.ms) best = c;
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    m->lanes = best.lanes;
+    if ((rc = layout_buckets(m, best.nopt)) || (rc = upload_views(m))) return rc;
+    return reset_counters(m);
+}
+
+// shared by mesh_init (one part, no padding) and mesh_batch_init
+static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_grid2d* sizings,
+                  const void* const* xys, const int64_t* ns, const mesh_params& P, void* cuda_stream,
+                  int tune) {
+    int rc = check_params(P);
+    if (rc) return rc;
+    m->prec = P.precision;
+    m->P = P;
+    m->user = (cudaStream_t)cuda_stream;
+    m->parts.resize(nparts);
+    std::vector<HostGeometry> G(nparts);
+    int64_t slots = 0;
+    for (int k = 0; k < nparts; k++) {
+        std::string who = m->batched ? "mesh " + std::to_string(k) + ": " : "";
+        if ((rc = check_part(&sdfs[k], &sizings[k], xys ? xys[k] : nullptr, ns[k], P.precision, who))) return rc;
+        if ((rc = host_geometry(sdfs[k], sizings[k], ns[k], P, G[k]))) return fail(rc, who + g_err);
+        Part& p = m->parts[k];
+        p.n = ns[k];
+        fill_devparams(p.dp, P, G[k], &sdfs[k]);
+        p.rho_eff = G[k].rho_eff;
+        p.soff = (int32_t)slots;
+        int64_t len = m->batched ? (p.n + kChunk - 1) / kChunk * kChunk : p.n;
+        p.npad = (int32_t)(len - p.n);
+        slots += len;
+        if (slots > (int64_t)1 << 30) return fail(TRIME_EINVAL, "too many points");
+        p.c0 = (int32_t)(p.soff / kChunk);
+        p.c1 = (int32_t)((p.soff + len) / kChunk);
+    }
+    m->nslots = slots;
+    m->nblk = m->batched ? (int)(slots / kChunk) : (int)std::max<int64_t>(1, (slots + kThreads - 1) / kThreads);
+    if (!m->batched) m->parts[0].c1 = m->nblk;
+    std::vector<double> nopts = {P.N_opt};
+    if (tune) nopts = {P.N_opt * (2.0 / 3.0), P.N_opt, P.N_opt * 1.5};
+    int nbmax = 0;
+    for (double no : nopts) {
+        if ((rc = layout_buckets(m, no))) return rc;
+        nbmax = std::max(nbmax, m->nbtot);
+    }
+
+    if (cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess)
+        return fail(TRIME_ECUDA, "stream/event creation failed");
+    if (cudaMallocHost(&m->hctrl, sizeof(DevCtrl) * nparts) != cudaSuccess) return fail(TRIME_ENOMEM, "pinned alloc");
+
+    size_t N = (size_t)slots;
+    size_t T = P.precision == 0 ? sizeof(double) : sizeof(float);
+    size_t nmax = 0;
+    for (const Part& p : m->parts) nmax = std::max(nmax, (size_t)p.n);
+    rc = 0;
+    m->cx = dalloc<char>(m, N * T, rc);
+    m->cy = dalloc<char>(m, N * T, rc);
+    m->cdp = dalloc<char>(m, N * T, rc);
+    m->sx = dalloc<char>(m, N * T, rc);
+    m->sy = dalloc<char>(m, N * T, rc);
+    m->sdp = dalloc<char>(m, N * T, rc);
+    m->cid = dalloc<int32_t>(m, N, rc);
+    m->sid = dalloc<int32_t>(m, N, rc);
+    m->ccls = dalloc<uint8_t>(m, N, rc);
+    m->scls = dalloc<uint8_t>(m, N, rc);
+    m->cell = dalloc<int32_t>(m, N, rc);
+    m->key = dalloc<int32_t>(m, N, rc);
+    m->rank = dalloc<int32_t>(m, N, rc);
+    m->skey = dalloc<int32_t>(m, N, rc);
+    m->dom = dalloc<uint8_t>(m, N, rc);
+    m->bcount = dalloc<int32_t>(m, (size_t)nbmax, rc);
+    m->bstart = dalloc<int32_t>(m, (size_t)nbmax + 1, rc);
+    size_t scan_n = std::max<size_t>((size_t)nbmax + 1, N + 1);
+    m->scan_tmp = dalloc<int32_t>(m, scan_n / 4096 + 2, rc);
+    m->nbcap = nbmax;
+    m->ring = dalloc<int32_t>(m, N * kRingCap, rc);
+    m->ring_n = dalloc<uint8_t>(m, N, rc);
+    m->cellR = dalloc<float>(m, N, rc);
+    m->vmask = dalloc<uint32_t>(m, N, rc);
+    m->ep = dalloc<EmitPartial>(m, (size_t)m->nblk, rc);
+    m->up = dalloc<UpdatePartial>(m, (size_t)m->nblk, rc);
+    m->ctrl = dalloc<DevCtrl>(m, (size_t)nparts, rc);
+    m->ovf_n = dalloc<int32_t>(m, 1, rc);
+    m->dbg = P.debug ? dalloc<double>(m, 10 * N, rc) : nullptr;
+    m->tcnt = dalloc<int32_t>(m, N + 1, rc);
+    m->toff = dalloc<int32_t>(m, N + 1, rc);
+    m->tbuf = dalloc<int32_t>(m, 3 * (2 * nmax + 16), rc);
+    m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
+    m->ovf_list = dalloc<int32_t>(m, N, rc);
+    m->pf = dalloc<float4>(m, N, rc);
+    m->pS = dalloc<float>(m, N, rc);
+    if (m->batched) {
+        m->dviews = dalloc<MeshView>(m, (size_t)nparts, rc);
+        m->cmesh = dalloc<int32_t>(m, N / kChunk, rc);
+    }
+    if (rc) return rc;
+    // padding slots hold zeros; no kernel reads them as points
+    CUDA_TRY(cudaMemsetAsync(m->cx, 0, N * T, m->st));
+    CUDA_TRY(cudaMemsetAsync(m->cy, 0, N * T, m->st));
+    CUDA_TRY(cudaMemsetAsync(m->cdp, 0, N * T, m->st));
+    CUDA_TRY(cudaMemsetAsync(m->cid, 0, N * sizeof(int32_t), m->st));
+    CUDA_TRY(cudaMemsetAsync(m->ccls, 0, N, m->st));
+    for (int k = 0; k < nparts; k++)
+        if ((rc = upload_part(m, k, &sdfs[k], &sizings[k], xys ? xys[k] : nullptr, G[k]))) return rc;
+    if (m->batched) {
+        std::vector<int32_t> cm(N / kChunk);
+        for (int k = 0; k < nparts; k++)
+            for (int32_t c = m->parts[k].c0; c < m->parts[k].c1; c++) cm[c] = k;
+        if (!cm.empty()) CUDA_TRY(cudaMemcpyAsync(m->cmesh, cm.data(), cm.size() * 4, cudaMemcpyHostToDevice, m->st));
+        CUDA_TRY(cudaStreamSynchronize(m->st));
+    }
+    if ((rc = layout_buckets(m, P.N_opt)) || (rc = upload_views(m))) return rc;
+    if (tune && (rc = autotune(m, nopts))) return rc;
+    return capture_graph(m);
+}
+
+// ------------------------------------------------------------------ operations shared by both handles
+static void destroy(mesh_s* m) {
+    if (m->st) cudaStreamSynchronize(m->st);
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    for (void* p : m->allocs) cudaFree(p);
+    if (m->hctrl) cudaFreeHost(m->hctrl);
+    if (m->ev) cudaEventDestroy(m->ev);
+    if (m->st) cudaStreamDestroy(m->st);
+}
+
+// stats: one entry per part, or NULL
+static int do_rebuild(mesh_s* m, mesh_stats* stats) {
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if ((rc = reset_counters(m))) return rc;
+    enqueue(m, false, 1);
+    CUDA_TRY(cudaGetLastError());
+    if ((rc = read_ctrl(m))) return rc;
+    if ((rc = sync_out(m))) return rc;
+    if (stats)
+        for (size_t k = 0; k < m->parts.size(); k++) fill_stats(m, (int)k, 0, &stats[k]);
+    if (guard_tripped(m)) return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
+    return TRIME_OK;
+}
+
+static int do_step(mesh_s* m, int32_t n_iters, mesh_stats* stats) {
+    if (n_iters < 0) return fail(TRIME_EINVAL, "n_iters < 0");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if ((rc = reset_counters(m))) return rc;
+    if ((rc = read_ctrl(m))) return rc;
+    size_t np = m->parts.size();
+    std::vector<int> start(np);
+    for (size_t k = 0; k < np; k++) start[k] = m->hctrl[k].iterations;
+    if (!all_terminated(m)) {
+        for (int32_t k = 0; k < n_iters; k++) {
+            CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+            if ((k & 31) == 31 || (stats && k == n_iters - 1)) {
+                if ((rc = read_ctrl(m))) return rc;
+                if (all_terminated(m)) break;
+            }
+        }
+    }
+    if (!stats) return sync_out(m);  // asynchronous: no read-back
+    if ((rc = read_ctrl(m))) return rc;
+    if ((rc = sync_out(m))) return rc;
+    for (size_t k = 0; k < np; k++) fill_stats(m, (int)k, m->hctrl[k].iterations - start[k], &stats[k]);
+    if (guard_tripped(m)) return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
+    return TRIME_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static int get_triangles(mesh_s* m, int k, int32_t* tri, int64_t cap, int64_t* n_out) {
+    const Part& p = m->parts[k];
+    int rc = sync_in(m);
+    if (rc) return rc;
+    int32_t total = 0;
+    if (p.n > 0) {
+        if (m->prec == 0) launch_tri_count<double>(make_args<double>(m, 1), p.soff, (int32_t)p.n, m->tcnt, m->st);
+        else launch_tri_count<float>(make_args<float>(m, 1), p.soff, (int32_t)p.n, m->tcnt, m->st);
+        launch_scan(m->tcnt, m->toff, (int32_t)p.n, m->scan_tmp, m->st);
+        CUDA_TRY(cudaMemcpyAsync(&total, m->toff + p.n, sizeof(int32_t), cudaMemcpyDeviceToHost, m->st));
+        CUDA_TRY(cudaStreamSynchronize(m->st));
+    }
+    *n_out = total;
+    if (cap < total) return fail(TRIME_ECAPACITY, "triangle buffer too small");
+    if (total == 0) return sync_out(m);
+    if (!tri) return fail(TRIME_EINVAL, "tri is NULL");
+    bool dev = is_device_ptr(tri);
+    int32_t* dst = dev ? tri : m->tbuf;
+    if (!dev && (size_t)total > 2 * (size_t)p.n + 16) return fail(TRIME_EDEVICE, "triangle count exceeds 2n+16");
+    if (m->prec == 0) launch_tri_write<double>(make_args<double>(m, 1), p.soff, (int32_t)p.n, m->toff, dst, m->st);
+    else launch_tri_write<float>(make_args<float>(m, 1), p.soff, (int32_t)p.n, m->toff, dst, m->st);
+    if (!dev) {
+        CUDA_TRY(cudaMemcpyAsync(tri, dst, sizeof(int32_t) * 3 * (size_t)total, cudaMemcpyDeviceToHost, m->st));
+        CUDA_TRY(cudaStreamSynchronize(m->st));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return sync_out(m);
+}
+
+static int get_points(mesh_s* m, int k, void* xy, int64_t cap, int64_t* n_out) {
+    const Part& p = m->parts[k];
+    *n_out = p.n;
+    if (cap < p.n) return fail(TRIME_ECAPACITY, "point buffer too small");
+    if (p.n == 0) return TRIME_OK;
+    if (!xy) return fail(TRIME_EINVAL, "xy is NULL");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    size_t T = m->prec == 0 ? sizeof(double) : sizeof(float);
+    bool dev = is_device_ptr(xy);
+    void* dst = dev ? xy : m->xybuf;
+    if (m->prec == 0) launch_unpermute<double>(make_args<double>(m, 1), p.soff, (int32_t)p.n, (double*)dst, m->st);
+    else launch_unpermute<float>(make_args<float>(m, 1), p.soff, (int32_t)p.n, (float*)dst, m->st);
+    if (!dev) {
+        CUDA_TRY(cudaMemcpyAsync(xy, dst, 2 * T * (size_t)p.n, cudaMemcpyDeviceToHost, m->st));
+        CUDA_TRY(cudaStreamSynchronize(m->st));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return sync_out(m);
+}
+
+static int set_state(mesh_s* m, int k, const void* xy, const uint8_t* cls, const double* dprev) {
+    const Part& p = m->parts[k];
+    if (p.n == 0) return TRIME_OK;
+    size_t N = (size_t)p.n, T = m->prec == 0 ? sizeof(double) : sizeof(float);
+    if (xy)
+        for (size_t i = 0; i < 2 * N; i++) {
+            double v = m->prec == 0 ? ((const double*)xy)[i] : (double)((const float*)xy)[i];
+            double lo = (i & 1) ? p.dp.by0 : p.dp.bx0, hi = (i & 1) ? p.dp.by1 : p.dp.bx1;
+            if (!std::isfinite(v) || v < lo || v > hi) return fail(TRIME_EINVAL, "point outside the SDF grid box");
+        }
+    int rc = sync_in(m);
+    if (rc) return rc;
+    // staging: xy in xybuf, cls in tcnt, dprev in tbuf (all large enough)
+    char* sxy = (char*)m->xybuf;
+    uint8_t* scls = (uint8_t*)m->tcnt;
+    double* sdp = (double*)m->tbuf;
+    if (xy) CUDA_TRY(cudaMemcpyAsync(sxy, xy, 2 * N * T, cudaMemcpyHostToDevice, m->st));
+    if (cls) CUDA_TRY(cudaMemcpyAsync(scls, cls, N, cudaMemcpyHostToDevice, m->st));
+    if (dprev) CUDA_TRY(cudaMemcpyAsync(sdp, dprev, N * sizeof(double), cudaMemcpyHostToDevice, m->st));
+    if (m->prec == 0)
+        launch_set_state<double>(make_args<double>(m, 1), p.soff, (int32_t)N, xy ? (const double*)sxy : nullptr,
+                                 cls ? scls : nullptr, dprev ? sdp : nullptr, m->st);
+    else
+        launch_set_state<float>(make_args<float>(m, 1), p.soff, (int32_t)N, xy ? (const float*)sxy : nullptr,
+                                cls ? scls : nullptr, dprev ? sdp : nullptr, m->st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
+static int set_method_state(mesh_s* m, int k, int32_t switched, double pa, double pb, double pm) {
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if ((rc = read_ctrl(m))) return rc;
+    DevCtrl& c = m->hctrl[k];
+    c.switched = switched;
+    c.have_prev = pa > 0;
+    c.prev_a = pa;
+    c.prev_b = pb;
+    c.prev_amax = pm;
+    c.terminated = 0;
+    c.small_moves = 0;
+    CUDA_TRY(cudaMemcpyAsync(m->ctrl + k, &c, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
+template <typename T>
+static int profile_stages(mesh_s* m, cudaEvent_t* ev) {
+    IterArgs<T> a = make_args<T>(m, 0);
+    CUDA_TRY(cudaEventRecord(ev[0], m->st));
+    launch_bucket<T>(a, m->st);
+    CUDA_TRY(cudaEventRecord(ev[1], m->st));
+    launch_voronoi<T>(a, m->lanes, m->st);
+    CUDA_TRY(cudaEventRecord(ev[2], m->st));
+    launch_emit<T>(a, m->nblk, m->st);
+    CUDA_TRY(cudaEventRecord(ev[3], m->st));
+    launch_stats_pre<T>(a, 1, m->st);
+    CUDA_TRY(cudaEventRecord(ev[4], m->st));
+    launch_update<T>(a, m->nblk, m->st);
+    CUDA_TRY(cudaEventRecord(ev[5], m->st));
+    launch_stats_post<T>(a, m->st);
+    CUDA_TRY(cudaEventRecord(ev[6], m->st));
+    return 0;
+}
+
+static int profile(mesh_s* m, int32_t n_iters, double* stage_ms) {
+    int rc = sync_in(m);
+    if (rc) return rc;
+    cudaEvent_t ev[7];
+    for (int k = 0; k < 7; k++) CUDA_TRY(cudaEventCreate(&ev[k]));
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int32_t it = 0; it < n_iters && !rc; it++) {
+        rc = m->prec == 0 ? profile_stages<double>(m, ev) : profile_stages<float>(m, ev);
+        if (rc) break;
+        CUDA_TRY(cudaEventSynchronize(ev[6]));
+        for (int k = 0; k < 6; k++) {
+            float ms = 0;
+            CUDA_TRY(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+            acc[k] += ms;
+        }
+        float tot = 0;
+        CUDA_TRY(cudaEventElapsedTime(&tot, ev[0], ev[6]));
+        acc[6] += tot;
+    }
+    for (int k = 0; k < 7; k++) {
+        stage_ms[k] += acc[k];
+        cudaEventDestroy(ev[k]);
+    }
+    if (rc) return rc;
+    CUDA_TRY(cudaGetLastError());
+    return sync_out(m);
+}
+
+// new bucket size and Voronoi lane count: re-layout (growing the bucket
+// arrays if needed) and capture the iteration again
+static void drop_alloc(mesh_s* m, void* p) {
+    auto it = std::find(m->allocs.begin(), m->allocs.end(), p);
+    if (it != m->allocs.end()) m->allocs.erase(it);
+    cudaFree(p);
+}
+
+static int set_tuning(mesh_s* m, double nopt, int32_t lanes) {
+    if (!(nopt > 0) || (lanes != 16 && lanes != 32)) return fail(TRIME_EINVAL, "n_opt must be > 0, lanes 16 or 32");
+    int rc = sync_in(m);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    if ((rc = layout_buckets(m, nopt))) return rc;
+    if (m->nbtot > m->nbcap) {
+        drop_alloc(m, m->bcount);
+        drop_alloc(m, m->bstart);
+        drop_alloc(m, m->scan_tmp);
+        size_t scan_n = std::max<size_t>((size_t)m->nbtot + 1, (size_t)m->nslots + 1);
+        m->bcount = dalloc<int32_t>(m, (size_t)m->nbtot, rc);
+        m->bstart = dalloc<int32_t>(m, (size_t)m->nbtot + 1, rc);
+        m->scan_tmp = dalloc<int32_t>(m, scan_n / 4096 + 2, rc);
+        if (rc) return rc;
+        m->nbcap = m->nbtot;
+    }
+    m->lanes = lanes;
+    if ((rc = upload_views(m)) || (rc = capture_graph(m))) return rc;
+    return sync_out(m);
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -360,12 +1012,7 @@ const char* mesh_last_error(void) { return g_err.c_str(); }
 
 void mesh_destroy(mesh_t* m) {
     if (!m) return;
-    if (m->st) cudaStreamSynchronize(m->st);
-    if (m->gexec) cudaGraphExecDestroy(m->gexec);
-    for (void* p : m->allocs) cudaFree(p);
-    if (m->hctrl) cudaFreeHost(m->hctrl);
-    if (m->ev) cudaEventDestroy(m->ev);
-    if (m->st) cudaStreamDestroy(m->st);
+    destroy(m);
     delete m;
 }
 
@@ -374,358 +1021,48 @@ int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, c
     g_err.clear();
     if (!out) return fail(TRIME_EINVAL, "out is NULL");
     *out = nullptr;
+    if (!sdf || !sizing) return fail(TRIME_EINVAL, "grid is NULL");
     mesh_params P;
-    if (p) P = *p; else mesh_default_params(&P);
-    if (P.precision != 0 && P.precision != 1) return fail(TRIME_EINVAL, "precision must be 0 or 1");
-    if (P.method < 0 || P.method > 2) return fail(TRIME_EINVAL, "method must be 0, 1 or 2");
-    if (P.quad_max_level < 1 || P.quad_max_level > 9) return fail(TRIME_EINVAL, "quad_max_level must be 1..9");
-    if (P.newton_max < 0 || P.trace_max < 1) return fail(TRIME_EINVAL, "bad newton_max / trace_max");
-    if (!(P.N_opt > 0) || !(P.fac_voro_bound > 0) || !(P.dt >= 0)) return fail(TRIME_EINVAL, "bad parameter value");
-    if (n < 0 || n > (int64_t)(1 << 30)) return fail(TRIME_EINVAL, "n out of range");
-    if (n > 0 && !xy) return fail(TRIME_EINVAL, "xy is NULL");
-    if (!grid_ok(sdf)) return fail(TRIME_EINVAL, "invalid SDF grid");
-    if (!grid_ok(sizing)) return fail(TRIME_EINVAL, "invalid sizing grid");
-    for (size_t k = 0; k < (size_t)sizing->nx * sizing->ny; k++)
-        if (!(sizing->v[k] > 0.0f)) return fail(TRIME_EINVAL, "sizing values must be positive");
-    for (int64_t i = 0; i < n; i++) {
-        double x = P.precision == 0 ? ((const double*)xy)[2 * i] : (double)((const float*)xy)[2 * i];
-        double y = P.precision == 0 ? ((const double*)xy)[2 * i + 1] : (double)((const float*)xy)[2 * i + 1];
-        if (!std::isfinite(x) || !std::isfinite(y) || x < sdf->x0 || x > sdf->x1 || y < sdf->y0 || y > sdf->y1)
-            return fail(TRIME_EINVAL, "point " + std::to_string(i) + " is not finite or outside the SDF grid box");
-    }
-    HostGeometry G;
-    int rc = host_geometry(*sdf, *sizing, n, P, G);
-    if (rc) return rc;
-
+    if (p) P = *p;
+    else mesh_default_params(&P);
     mesh_s* m = new mesh_s();
-    m->prec = P.precision;
-    m->n = n;
-    m->P = P;
-    m->user = (cudaStream_t)cuda_stream;
-    auto bail = [&](int code) {
+    int rc = create(m, 1, sdf, sizing, &xy, &n, P, cuda_stream, 0);
+    if (rc) {
         mesh_destroy(m);
-        return code;
-    };
-    if (cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess)
-        return bail(fail(TRIME_ECUDA, "stream/event creation failed"));
-    if (cudaMallocHost(&m->hctrl, sizeof(DevCtrl)) != cudaSuccess) return bail(fail(TRIME_ENOMEM, "pinned alloc"));
-
-    // device parameters
-    DevParams& d = m->dp;
-    d.bounded = P.bounded;
-    d.validity = P.validity;
-    d.newton_max = P.newton_max;
-    d.trace_max = P.trace_max;
-    d.quad_max_level = P.quad_max_level;
-    d.debug = P.debug != 0;
-    d.fac_F = P.fac_F;
-    d.k_spring = P.k_spring;
-    d.dt = P.dt;
-    d.fac_pt = P.fac_pt;
-    d.fac_geps = P.fac_geps;
-    d.fac_voro_bound = P.fac_voro_bound;
-    d.fac_end = P.fac_end;
-    d.T_circ = P.T_circ;
-    d.T_switch = P.T_switch;
-    d.T_end_q = P.T_end_q;
-    d.T_end_amax = P.T_end_amax;
-    d.damping = P.damping;
-    d.havg = G.havg;
-    d.bx0 = sdf->x0;
-    d.by0 = sdf->y0;
-    d.bx1 = sdf->x1;
-    d.by1 = sdf->y1;
-    double W = sdf->x1 - sdf->x0, H = sdf->y1 - sdf->y0;
-    // neighbour buckets: the paper sizes the block grid for N_opt points per
-    // block under uniform density (Sec. 3.2); with adaptive density we size it
-    // so that the bucket holding a typical point expects N_opt points
-    double lam = std::sqrt((double)std::max<int64_t>(n, 1) / (P.N_opt * W * H));
-    if (G.rho_eff > 0 && n > 0) lam = std::max(lam, std::sqrt(G.rho_eff / P.N_opt));
-    double cap = std::sqrt((4.0 * (double)n + 1024.0) / (W * H));
-    lam = std::min(lam, cap);
-    d.nbx = std::max(1, (int)std::ceil(lam * W));
-    d.nby = std::max(1, (int)std::ceil(lam * H));
-    d.bsx = W / d.nbx;
-    d.bsy = H / d.nby;
-    d.bx0f = (float)d.bx0;
-    d.by0f = (float)d.by0;
-    d.ibsxf = (float)(1.0 / d.bsx);
-    d.ibsyf = (float)(1.0 / d.bsy);
-    int nb = d.nbx * d.nby;
-
-    size_t ns = (size_t)sdf->nx * sdf->ny, nz = (size_t)sizing->nx * sizing->ny;
-    size_t nc = (size_t)(sdf->nx - 1) * (sdf->ny - 1);
-    size_t N = (size_t)n;
-    size_t T = P.precision == 0 ? sizeof(double) : sizeof(float);
-    m->nblk = (int)std::max<size_t>(1, (N + kThreads - 1) / kThreads);
-    rc = 0;
-    float* dsdf = dalloc<float>(m, ns, rc);
-    float* dsiz = dalloc<float>(m, nz, rc);
-    m->gcls = dalloc<uint8_t>(m, nc, rc);
-    m->gh = dalloc<double>(m, nc, rc);
-    m->ggeps = dalloc<double>(m, nc, rc);
-    m->gidist = dalloc<uint8_t>(m, nc, rc);
-    m->cx = dalloc<char>(m, N * T, rc);
-    m->cy = dalloc<char>(m, N * T, rc);
-    m->cdp = dalloc<char>(m, N * T, rc);
-    m->sx = dalloc<char>(m, N * T, rc);
-    m->sy = dalloc<char>(m, N * T, rc);
-    m->sdp = dalloc<char>(m, N * T, rc);
-    m->cid = dalloc<int32_t>(m, N, rc);
-    m->sid = dalloc<int32_t>(m, N, rc);
-    m->ccls = dalloc<uint8_t>(m, N, rc);
-    m->scls = dalloc<uint8_t>(m, N, rc);
-    m->cell = dalloc<int32_t>(m, N, rc);
-    m->key = dalloc<int32_t>(m, N, rc);
-    m->rank = dalloc<int32_t>(m, N, rc);
-    m->skey = dalloc<int32_t>(m, N, rc);
-    m->dom = dalloc<uint8_t>(m, N, rc);
-    m->bcount = dalloc<int32_t>(m, nb, rc);
-    m->bstart = dalloc<int32_t>(m, (size_t)nb + 1, rc);
-    size_t scan_n = std::max<size_t>((size_t)nb + 1, N + 1);
-    m->scan_tmp = dalloc<int32_t>(m, scan_n / 4096 + 2, rc);
-    m->ring = dalloc<int32_t>(m, N * kRingCap, rc);
-    m->ring_n = dalloc<uint8_t>(m, N, rc);
-    m->cellR = dalloc<float>(m, N, rc);
-    m->vmask = dalloc<uint32_t>(m, N, rc);
-    m->ep = dalloc<EmitPartial>(m, (size_t)m->nblk, rc);
-    m->up = dalloc<UpdatePartial>(m, (size_t)m->nblk, rc);
-    m->ctrl = dalloc<DevCtrl>(m, 1, rc);
-    m->dbg = d.debug ? dalloc<double>(m, 10 * N, rc) : nullptr;
-    m->tcnt = dalloc<int32_t>(m, N + 1, rc);
-    m->toff = dalloc<int32_t>(m, N + 1, rc);
-    m->tbuf = dalloc<int32_t>(m, 3 * (2 * N + 16), rc);
-    m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
-    m->ovf_list = dalloc<int32_t>(m, N, rc);
-    m->pf = dalloc<float4>(m, N, rc);
-    m->pS = dalloc<float>(m, N, rc);
-    if (rc) return bail(rc);
-
-    m->sdf = {sdf->nx, sdf->ny, sdf->x0, sdf->y0, sdf->x1, sdf->y1, (sdf->x1 - sdf->x0) / (double)(sdf->nx - 1),
-              (sdf->y1 - sdf->y0) / (double)(sdf->ny - 1), dsdf, 0.0, 0.0};
-    m->siz = {sizing->nx, sizing->ny, sizing->x0, sizing->y0, sizing->x1, sizing->y1,
-              (sizing->x1 - sizing->x0) / (double)(sizing->nx - 1),
-              (sizing->y1 - sizing->y0) / (double)(sizing->ny - 1), dsiz, 0.0, 0.0};
-    m->sdf.idx = 1.0 / m->sdf.dx;
-    m->sdf.idy = 1.0 / m->sdf.dy;
-    m->siz.idx = 1.0 / m->siz.dx;
-    m->siz.idy = 1.0 / m->siz.dy;
-    auto H2D = [&](void* dst, const void* src, size_t bytes) {
-        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, m->st) == cudaSuccess;
-    };
-    bool ok = H2D(dsdf, sdf->v, ns * sizeof(float)) && H2D(dsiz, sizing->v, nz * sizeof(float)) &&
-              H2D(m->gcls, G.cls.data(), nc) && H2D(m->gh, G.h.data(), nc * sizeof(double)) &&
-              H2D(m->ggeps, G.geps.data(), nc * sizeof(double)) && H2D(m->gidist, G.idist.data(), nc);
-    // state in input order: ids 0..n-1, classes by Sec. 4.3 on the host
-    std::vector<int32_t> ids(N);
-    std::vector<uint8_t> cls(N);
-    std::vector<char> dp(N * T);
-    std::vector<char> xs(N * T), ys(N * T);
-    double sdx = m->sdf.dx, sdy = m->sdf.dy;
-    int ncx = sdf->nx - 1, ncy = sdf->ny - 1;
-    for (size_t i = 0; i < N; i++) {
-        ids[i] = (int32_t)i;
-        double x = P.precision == 0 ? ((const double*)xy)[2 * i] : (double)((const float*)xy)[2 * i];
-        double y = P.precision == 0 ? ((const double*)xy)[2 * i + 1] : (double)((const float*)xy)[2 * i + 1];
-        double fi = std::floor((x - sdf->x0) / sdx), fj = std::floor((y - sdf->y0) / sdy);
-        bool inside = fi >= 0 && fi <= ncx - 1 && fj >= 0 && fj <= ncy - 1;
-        int gi = !(fi >= 0) ? 0 : (fi > ncx - 1 ? ncx - 1 : (int)fi);
-        int gj = !(fj >= 0) ? 0 : (fj > ncy - 1 ? ncy - 1 : (int)fj);
-        size_t c = (size_t)gj * ncx + gi;
-        uint8_t pc = PT_BOUNDARY;
-        if (inside && G.cls[c] == CELL_INNER) pc = PT_INNER;
-        else if (inside && G.cls[c] == CELL_BOUNDARY) {
-            double s = host_bilin(*sdf, sdx, sdy, x, y);
-            if (s < -G.geps[c]) pc = PT_INNER;
-        }
-        cls[i] = pc;  // reading: a point outside at init counts as boundary
-        double h = G.h[c];
-        if (P.precision == 0) {
-            ((double*)xs.data())[i] = x;
-            ((double*)ys.data())[i] = y;
-            ((double*)dp.data())[i] = h;  // reading: eps_c = 1 at the first iteration
-        } else {
-            ((float*)xs.data())[i] = (float)x;
-            ((float*)ys.data())[i] = (float)y;
-            ((float*)dp.data())[i] = (float)h;
-        }
+        return rc;
     }
-    ok = ok && H2D(m->cx, xs.data(), N * T) && H2D(m->cy, ys.data(), N * T) && H2D(m->cdp, dp.data(), N * T) &&
-         H2D(m->cid, ids.data(), N * sizeof(int32_t)) && H2D(m->ccls, cls.data(), N);
-    DevCtrl c0;
-    std::memset(&c0, 0, sizeof c0);
-    c0.method_param = P.method;
-    c0.last_method = -1;
-    ok = ok && H2D(m->ctrl, &c0, sizeof c0);
-    if (!ok || cudaStreamSynchronize(m->st) != cudaSuccess) return bail(fail(TRIME_ECUDA, "initial upload failed"));
-
-    // one iteration as a CUDA graph
-    cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return bail(fail(TRIME_ECUDA, "cudaStreamBeginCapture failed"));
-    enqueue(m, true, 0);
-    cudaError_t e = cudaStreamEndCapture(m->st, &graph);
-    if (e != cudaSuccess) return bail(fail(TRIME_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e)));
-    e = cudaGraphInstantiate(&m->gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return bail(fail(TRIME_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)));
     *out = m;
     return TRIME_OK;
 }
 
 int mesh_rebuild(mesh_t* m, mesh_stats* stats) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
-    int rc = sync_in(m);
-    if (rc) return rc;
-    if ((rc = reset_counters(m))) return rc;
-    enqueue(m, false, 1);
-    CUDA_TRY(cudaGetLastError());
-    if ((rc = read_ctrl(m))) return rc;
-    if ((rc = sync_out(m))) return rc;
-    if (stats) fill_stats(m, 0, stats);
-    const DevCounters& c = m->hctrl->cnt;
-    if (c.ring_overflow || c.exact_overflow)
-        return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
-    return TRIME_OK;
+    return do_rebuild(m, stats);
 }
 
 int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
-    if (n_iters < 0) return fail(TRIME_EINVAL, "n_iters < 0");
-    int rc = sync_in(m);
-    if (rc) return rc;
-    if ((rc = reset_counters(m))) return rc;
-    if ((rc = read_ctrl(m))) return rc;
-    if (m->hctrl->terminated) {
-        if ((rc = sync_out(m))) return rc;
-        if (stats) fill_stats(m, 0, stats);
-        return TRIME_OK;
-    }
-    int start = m->hctrl->iterations;
-    for (int32_t k = 0; k < n_iters; k++) {
-        CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
-        if ((k & 31) == 31 || (stats && k == n_iters - 1)) {
-            if ((rc = read_ctrl(m))) return rc;
-            if (m->hctrl->terminated) break;
-        }
-    }
-    if (!stats) return sync_out(m);  // asynchronous: no read-back
-    if (n_iters == 0 && (rc = read_ctrl(m))) return rc;
-    if ((rc = sync_out(m))) return rc;
-    if (stats) fill_stats(m, m->hctrl->iterations - start, stats);
-    const DevCounters& c = m->hctrl->cnt;
-    if (c.ring_overflow || c.exact_overflow)
-        return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
-    return TRIME_OK;
-}
-
-static bool is_device_ptr(const void* p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return do_step(m, n_iters, stats);
 }
 
 int mesh_get_triangles(mesh_t* m, int32_t* tri, int64_t cap, int64_t* n_out) {
     if (!m || !n_out) return fail(TRIME_EINVAL, "NULL argument");
-    int rc = sync_in(m);
-    if (rc) return rc;
-    int32_t total = 0;
-    if (m->n > 0) {
-        if (m->prec == 0) launch_tri_count<double>(make_args<double>(m, 1), m->tcnt, m->st);
-        else launch_tri_count<float>(make_args<float>(m, 1), m->tcnt, m->st);
-        launch_scan(m->tcnt, m->toff, (int32_t)m->n, m->scan_tmp, m->st);
-        CUDA_TRY(cudaMemcpyAsync(&total, m->toff + m->n, sizeof(int32_t), cudaMemcpyDeviceToHost, m->st));
-        CUDA_TRY(cudaStreamSynchronize(m->st));
-    }
-    *n_out = total;
-    if (cap < total) return fail(TRIME_ECAPACITY, "triangle buffer too small");
-    if (total == 0) return sync_out(m);
-    if (!tri) return fail(TRIME_EINVAL, "tri is NULL");
-    bool dev = is_device_ptr(tri);
-    int32_t* dst = dev ? tri : m->tbuf;
-    if (!dev && (size_t)total > 2 * (size_t)m->n + 16) return fail(TRIME_EDEVICE, "triangle count exceeds 2n+16");
-    if (m->prec == 0) launch_tri_write<double>(make_args<double>(m, 1), m->toff, dst, m->st);
-    else launch_tri_write<float>(make_args<float>(m, 1), m->toff, dst, m->st);
-    if (!dev) {
-        CUDA_TRY(cudaMemcpyAsync(tri, dst, sizeof(int32_t) * 3 * (size_t)total, cudaMemcpyDeviceToHost, m->st));
-        CUDA_TRY(cudaStreamSynchronize(m->st));
-    }
-    CUDA_TRY(cudaGetLastError());
-    return sync_out(m);
+    return get_triangles(m, 0, tri, cap, n_out);
 }
 
 int mesh_get_points(mesh_t* m, void* xy, int64_t cap, int64_t* n_out) {
     if (!m || !n_out) return fail(TRIME_EINVAL, "NULL argument");
-    *n_out = m->n;
-    if (cap < m->n) return fail(TRIME_ECAPACITY, "point buffer too small");
-    if (m->n == 0) return TRIME_OK;
-    if (!xy) return fail(TRIME_EINVAL, "xy is NULL");
-    int rc = sync_in(m);
-    if (rc) return rc;
-    size_t T = m->prec == 0 ? sizeof(double) : sizeof(float);
-    bool dev = is_device_ptr(xy);
-    void* dst = dev ? xy : m->xybuf;
-    if (m->prec == 0) launch_unpermute<double>(make_args<double>(m, 1), (double*)dst, m->st);
-    else launch_unpermute<float>(make_args<float>(m, 1), (float*)dst, m->st);
-    if (!dev) {
-        CUDA_TRY(cudaMemcpyAsync(xy, dst, 2 * T * (size_t)m->n, cudaMemcpyDeviceToHost, m->st));
-        CUDA_TRY(cudaStreamSynchronize(m->st));
-    }
-    CUDA_TRY(cudaGetLastError());
-    return sync_out(m);
+    return get_points(m, 0, xy, cap, n_out);
 }
 
 int mesh_set_state(mesh_t* m, const void* xy, const uint8_t* cls, const double* dprev) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
-    if (m->n == 0) return TRIME_OK;
-    size_t N = (size_t)m->n, T = m->prec == 0 ? sizeof(double) : sizeof(float);
-    if (xy)
-        for (size_t i = 0; i < 2 * N; i++) {
-            double v = m->prec == 0 ? ((const double*)xy)[i] : (double)((const float*)xy)[i];
-            double lo = (i & 1) ? m->dp.by0 : m->dp.bx0, hi = (i & 1) ? m->dp.by1 : m->dp.bx1;
-            if (!std::isfinite(v) || v < lo || v > hi) return fail(TRIME_EINVAL, "point outside the SDF grid box");
-        }
-    int rc = sync_in(m);
-    if (rc) return rc;
-    // staging: xy in xybuf, cls in tcnt, dprev in tbuf (all large enough)
-    char* sxy = (char*)m->xybuf;
-    uint8_t* scls = (uint8_t*)m->tcnt;
-    double* sdp = (double*)m->tbuf;
-    if (xy) CUDA_TRY(cudaMemcpyAsync(sxy, xy, 2 * N * T, cudaMemcpyHostToDevice, m->st));
-    if (cls) CUDA_TRY(cudaMemcpyAsync(scls, cls, N, cudaMemcpyHostToDevice, m->st));
-    if (dprev) CUDA_TRY(cudaMemcpyAsync(sdp, dprev, N * sizeof(double), cudaMemcpyHostToDevice, m->st));
-    if (m->prec == 0)
-        launch_set_state<double>(make_args<double>(m, 1), xy ? (const double*)sxy : nullptr, cls ? scls : nullptr,
-                                 dprev ? sdp : nullptr, m->st);
-    else
-        launch_set_state<float>(make_args<float>(m, 1), xy ? (const float*)sxy : nullptr, cls ? scls : nullptr,
-                                dprev ? sdp : nullptr, m->st);
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaStreamSynchronize(m->st));
-    return sync_out(m);
+    return set_state(m, 0, xy, cls, dprev);
 }
 
 int mesh_set_method_state(mesh_t* m, int32_t switched, double pa, double pb, double pm) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
-    int rc = sync_in(m);
-    if (rc) return rc;
-    if ((rc = read_ctrl(m))) return rc;
-    DevCtrl c = *m->hctrl;
-    c.switched = switched;
-    c.have_prev = pa > 0;
-    c.prev_a = pa;
-    c.prev_b = pb;
-    c.prev_amax = pm;
-    c.terminated = 0;
-    c.small_moves = 0;
-    *m->hctrl = c;
-    CUDA_TRY(cudaMemcpyAsync(m->ctrl, m->hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
-    CUDA_TRY(cudaStreamSynchronize(m->st));
-    return sync_out(m);
+    return set_method_state(m, 0, switched, pa, pb, pm);
 }
 
 int mesh_get_debug(mesh_t* m, int32_t what, double* out, int64_t cap) {
@@ -734,15 +1071,126 @@ int mesh_get_debug(mesh_t* m, int32_t what, double* out, int64_t cap) {
     static const int off[7] = {0, 2, 4, 6, 7, 8, 9};
     static const int width[7] = {2, 2, 2, 1, 1, 1, 1};
     if (what < 0 || what > 6) return fail(TRIME_EINVAL, "what must be 0..6");
-    size_t cnt = (size_t)width[what] * (size_t)m->n;
+    int64_t n = m->nslots;
+    size_t cnt = (size_t)width[what] * (size_t)n;
     if ((size_t)cap < cnt) return fail(TRIME_ECAPACITY, "debug buffer too small");
     if (cnt == 0) return TRIME_OK;
     int rc = sync_in(m);
     if (rc) return rc;
-    CUDA_TRY(cudaMemcpyAsync(out, m->dbg + (size_t)off[what] * m->n, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+    CUDA_TRY(cudaMemcpyAsync(out, m->dbg + (size_t)off[what] * n, cnt * sizeof(double), cudaMemcpyDeviceToHost,
                              m->st));
     CUDA_TRY(cudaStreamSynchronize(m->st));
     return sync_out(m);
+}
+
+int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms) {
+    if (!m || !stage_ms || n_iters < 0) return fail(TRIME_EINVAL, "bad argument");
+    return profile(m, n_iters, stage_ms);
+}
+
+int mesh_set_tuning(mesh_t* m, double n_opt, int32_t lanes) {
+    if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
+    return set_tuning(m, n_opt, lanes);
+}
+
+// ------------------------------------------------------------------ batches
+int mesh_batch_init(mesh_batch_t** out, int32_t n_meshes, const mesh_grid2d* sdfs, const mesh_grid2d* sizings,
+                    const void* const* xys, const int64_t* ns, const mesh_params* p, int32_t autotune,
+                    void* cuda_stream) {
+    g_err.clear();
+    if (!out) return fail(TRIME_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_meshes < 1 || n_meshes > (1 << 20)) return fail(TRIME_EINVAL, "n_meshes out of range");
+    if (!sdfs || !sizings || !xys || !ns) return fail(TRIME_EINVAL, "NULL array");
+    mesh_params P;
+    if (p) P = *p;
+    else mesh_default_params(&P);
+    mesh_batch_s* b = new mesh_batch_s();
+    b->batched = true;
+    int rc = create(b, n_meshes, sdfs, sizings, xys, ns, P, cuda_stream, autotune != 0);
+    if (rc) {
+        mesh_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return TRIME_OK;
+}
+
+void mesh_batch_destroy(mesh_batch_t* b) {
+    if (!b) return;
+    destroy(b);
+    delete b;
+}
+
+int mesh_batch_size(const mesh_batch_t* b) { return b ? (int)b->parts.size() : 0; }
+
+int mesh_batch_rebuild(mesh_batch_t* b, mesh_stats* stats) {
+    if (!b) return fail(TRIME_EINVAL, "batch is NULL");
+    return do_rebuild(b, stats);
+}
+
+int mesh_batch_step(mesh_batch_t* b, int32_t n_iters, mesh_stats* stats) {
+    if (!b) return fail(TRIME_EINVAL, "batch is NULL");
+    return do_step(b, n_iters, stats);
+}
+
+static int check_mesh(const mesh_batch_t* b, int32_t mesh) {
+    if (!b) return fail(TRIME_EINVAL, "batch is NULL");
+    if (mesh < 0 || mesh >= (int32_t)b->parts.size()) return fail(TRIME_EINVAL, "mesh index out of range");
+    return 0;
+}
+
+int mesh_batch_get_triangles(mesh_batch_t* b, int32_t mesh, int32_t* tri, int64_t cap, int64_t* n_out) {
+    int rc = check_mesh(b, mesh);
+    if (rc) return rc;
+    if (!n_out) return fail(TRIME_EINVAL, "n_out is NULL");
+    return get_triangles(b, mesh, tri, cap, n_out);
+}
+
+int mesh_batch_get_points(mesh_batch_t* b, int32_t mesh, void* xy, int64_t cap, int64_t* n_out) {
+    int rc = check_mesh(b, mesh);
+    if (rc) return rc;
+    if (!n_out) return fail(TRIME_EINVAL, "n_out is NULL");
+    return get_points(b, mesh, xy, cap, n_out);
+}
+
+int mesh_batch_set_state(mesh_batch_t* b, int32_t mesh, const void* xy, const uint8_t* cls, const double* dprev) {
+    int rc = check_mesh(b, mesh);
+    if (rc) return rc;
+    return set_state(b, mesh, xy, cls, dprev);
+}
+
+int mesh_batch_set_method_state(mesh_batch_t* b, int32_t mesh, int32_t switched, double pa, double pb, double pm) {
+    int rc = check_mesh(b, mesh);
+    if (rc) return rc;
+    return set_method_state(b, mesh, switched, pa, pb, pm);
+}
+
+int mesh_batch_profile_step(mesh_batch_t* b, int32_t n_iters, double* stage_ms) {
+    if (!b || !stage_ms || n_iters < 0) return fail(TRIME_EINVAL, "bad argument");
+    return profile(b, n_iters, stage_ms);
+}
+
+int mesh_batch_set_tuning(mesh_batch_t* b, double n_opt, int32_t lanes) {
+    if (!b) return fail(TRIME_EINVAL, "batch is NULL");
+    return set_tuning(b, n_opt, lanes);
+}
+
+int mesh_batch_get_tuning(const mesh_batch_t* b, mesh_tuning* out) {
+    if (!b || !out) return fail(TRIME_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof *out);
+    out->n_opt = b->nopt;
+    out->lanes = b->lanes;
+    out->n_slots = b->nslots;
+    out->n_buckets = b->nbtot;
+    int nc = (int)std::min<size_t>(b->tune.size(), 8);
+    out->n_candidates = nc;
+    for (int k = 0; k < nc; k++) {
+        out->cand_n_opt[k] = b->tune[k].nopt;
+        out->cand_lanes[k] = b->tune[k].lanes;
+        out->cand_ms[k] = b->tune[k].ms;
+    }
+    return TRIME_OK;
 }
 
 int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, double y0, double x1, double y1,
@@ -756,59 +1204,6 @@ int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, d
                       scratch, (cudaStream_t)cuda_stream);
     CUDA_TRY(cudaGetLastError());
     return TRIME_OK;
-}
-
-int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms) {
-    if (!m || !stage_ms || n_iters < 0) return fail(TRIME_EINVAL, "bad argument");
-    int rc = sync_in(m);
-    if (rc) return rc;
-    cudaEvent_t ev[7];
-    for (int k = 0; k < 7; k++) CUDA_TRY(cudaEventCreate(&ev[k]));
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int32_t it = 0; it < n_iters; it++) {
-        CUDA_TRY(cudaEventRecord(ev[0], m->st));
-        if (m->prec == 0) {
-            IterArgs<double> a = make_args<double>(m, 0);
-            launch_bucket<double>(a, m->st);
-            CUDA_TRY(cudaEventRecord(ev[1], m->st));
-            launch_voronoi<double>(a, m->st);
-            CUDA_TRY(cudaEventRecord(ev[2], m->st));
-            launch_emit<double>(a, m->nblk, m->st);
-            CUDA_TRY(cudaEventRecord(ev[3], m->st));
-            launch_stats_pre(m->ctrl, m->ep, m->nblk, 1, 0, m->dp, m->st);
-            CUDA_TRY(cudaEventRecord(ev[4], m->st));
-            launch_update<double>(a, m->nblk, m->st);
-        } else {
-            IterArgs<float> a = make_args<float>(m, 0);
-            launch_bucket<float>(a, m->st);
-            CUDA_TRY(cudaEventRecord(ev[1], m->st));
-            launch_voronoi<float>(a, m->st);
-            CUDA_TRY(cudaEventRecord(ev[2], m->st));
-            launch_emit<float>(a, m->nblk, m->st);
-            CUDA_TRY(cudaEventRecord(ev[3], m->st));
-            launch_stats_pre(m->ctrl, m->ep, m->nblk, 1, 0, m->dp, m->st);
-            CUDA_TRY(cudaEventRecord(ev[4], m->st));
-            launch_update<float>(a, m->nblk, m->st);
-        }
-        CUDA_TRY(cudaEventRecord(ev[5], m->st));
-        launch_stats_post(m->ctrl, m->up, m->nblk, m->st);
-        CUDA_TRY(cudaEventRecord(ev[6], m->st));
-        CUDA_TRY(cudaEventSynchronize(ev[6]));
-        for (int k = 0; k < 6; k++) {
-            float ms = 0;
-            CUDA_TRY(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
-            acc[k] += ms;
-        }
-        float tot = 0;
-        CUDA_TRY(cudaEventElapsedTime(&tot, ev[0], ev[6]));
-        acc[6] += tot;
-    }
-    for (int k = 0; k < 7; k++) {
-        stage_ms[k] += acc[k];
-        cudaEventDestroy(ev[k]);
-    }
-    CUDA_TRY(cudaGetLastError());
-    return sync_out(m);
 }
 
 int mesh_exact_predicates(const double* pts, const int32_t* ids, int64_t nq, int32_t* out_orient,

@@ -16,21 +16,21 @@ constexpr int kPolyCap = 48;
 
 // ------------------------------------------------------------------ point treatment
 template <typename T>
-__device__ __forceinline__ T geps_at(const IterArgs<T>& a, T x, T y) {
+__device__ __forceinline__ T geps_at(const MeshView& V, T x, T y) {
     int gi, gj;
-    point_cell_t<T>(a.sdf, x, y, gi, gj);
-    return (T)a.ggeps[gj * (a.sdf.nx - 1) + gi];
+    point_cell_t<T>(V.sdf, x, y, gi, gj);
+    return (T)V.ggeps[gj * (V.sdf.nx - 1) + gi];
 }
 
 template <typename T>
-__device__ int classify(const IterArgs<T>& a, T x, T y) {
+__device__ int classify(const MeshView& V, T x, T y) {
     int gi, gj;
-    if (!point_cell_t<T>(a.sdf, x, y, gi, gj)) return PT_OUTSIDE;
-    int c = gj * (a.sdf.nx - 1) + gi;
-    uint8_t k = a.gcls[c];
+    if (!point_cell_t<T>(V.sdf, x, y, gi, gj)) return PT_OUTSIDE;
+    int c = gj * (V.sdf.nx - 1) + gi;
+    uint8_t k = V.gcls[c];
     if (k == CELL_OUTER) return PT_OUTSIDE;
     if (k == CELL_INNER) return PT_INNER;
-    T s = bilin<T>(a.sdf, x, y), g = (T)a.ggeps[c];
+    T s = bilin<T>(V.sdf, x, y), g = (T)V.ggeps[c];
     if (fabs(s) <= g) return PT_BOUNDARY;
     if (s < -g) return PT_INNER;
     return PT_OUTSIDE;
@@ -38,15 +38,15 @@ __device__ int classify(const IterArgs<T>& a, T x, T y) {
 
 // sphere tracing from an inner p_old toward an outside p_new (Fig. 21a)
 template <typename T>
-__device__ bool sphere_trace(const IterArgs<T>& a, T ax, T ay, T bx, T by, T& ox, T& oy) {
+__device__ bool sphere_trace(const MeshView& V, T ax, T ay, T bx, T by, T& ox, T& oy) {
     T Lx = bx - ax, Ly = by - ay;
     T L = sqrt(Lx * Lx + Ly * Ly);
     T ux = Lx / L, uy = Ly / L;
     T x = ax, y = ay, lox = ax, loy = ay, hix = bx, hiy = by, t = 0;
     int it = 0;
     bool bisect = false;
-    for (; it < a.P.trace_max; it++) {
-        T s = bilin<T>(a.sdf, x, y), g = geps_at(a, x, y);
+    for (; it < V.P.trace_max; it++) {
+        T s = bilin<T>(V.sdf, x, y), g = geps_at(V, x, y);
         if (fabs(s) <= g) { ox = x; oy = y; return false; }
         if (s > g) { hix = x; hiy = y; bisect = true; break; }
         lox = x; loy = y;
@@ -56,9 +56,9 @@ __device__ bool sphere_trace(const IterArgs<T>& a, T ax, T ay, T bx, T by, T& ox
         y = ay + t * uy;
     }
     if (bisect)
-        for (it++; it < a.P.trace_max; it++) {
+        for (it++; it < V.P.trace_max; it++) {
             T mx = (lox + hix) * (T)0.5, my = (loy + hiy) * (T)0.5;
-            T s = bilin<T>(a.sdf, mx, my), g = geps_at(a, mx, my);
+            T s = bilin<T>(V.sdf, mx, my), g = geps_at(V, mx, my);
             if (fabs(s) <= g) { ox = mx; oy = my; return false; }
             if (s < 0) { lox = mx; loy = my; } else { hix = mx; hiy = my; }
         }
@@ -70,11 +70,11 @@ __device__ bool sphere_trace(const IterArgs<T>& a, T ax, T ay, T bx, T by, T& ox
 // damped Newton projection (Eqs. 8-10), gradient at the iterate, exact
 // derivatives of the bilinear interpolant
 template <typename T>
-__device__ void newton_project(const IterArgs<T>& a, T pnx, T pny, T& ox, T& oy) {
+__device__ void newton_project(const MeshView& V, T pnx, T pny, T& ox, T& oy) {
     T x = pnx, y = pny;
-    for (int k = 0; k < a.P.newton_max; k++) {
+    for (int k = 0; k < V.P.newton_max; k++) {
         T f, fx, fy, fxy;
-        bilin_grad<T>(a.sdf, x, y, f, fx, fy, fxy);
+        bilin_grad<T>(V.sdf, x, y, f, fx, fy, fxy);
         T L1 = f;
         T L2 = (x - pnx) * fy - (y - pny) * fx;
         T J00 = fx, J01 = fy;
@@ -83,9 +83,9 @@ __device__ void newton_project(const IterArgs<T>& a, T pnx, T pny, T& ox, T& oy)
         if (det == (T)0 || !isfinite(det)) break;
         T dx = (J11 * L1 - J01 * L2) / det;
         T dy = (-J10 * L1 + J00 * L2) / det;
-        x -= (T)a.P.damping * dx;
-        y -= (T)a.P.damping * dy;
-        if (fabs(bilin<T>(a.sdf, x, y)) <= geps_at(a, x, y)) break;
+        x -= (T)V.P.damping * dx;
+        y -= (T)V.P.damping * dy;
+        if (fabs(bilin<T>(V.sdf, x, y)) <= geps_at(V, x, y)) break;
     }
     ox = x;
     oy = y;
@@ -141,7 +141,7 @@ __device__ void clip_poly(Poly<T>& P, T nx, T ny, T s) {
 // one-point rule on the leaves of the longest-edge bisection tree of given
 // depth under the triangle (0, v1, v2) (relative to the generator)
 template <typename T>
-__device__ void level_sum(const IterArgs<T>& a, T gx, T gy, T v1x, T v1y, T v2x, T v2y, int depth, T& W, T& WX,
+__device__ void level_sum(const MeshView& V, T gx, T gy, T v1x, T v1y, T v2x, T v2y, int depth, T& W, T& WX,
                           T& WY) {
     T st[9][6];
     int sd[9];
@@ -156,7 +156,7 @@ __device__ void level_sum(const IterArgs<T>& a, T gx, T gy, T v1x, T v1y, T v2x,
         if (d == 0) {
             T A = (T)0.5 * ((q1x - q0x) * (q2y - q0y) - (q1y - q0y) * (q2x - q0x));
             T cx = (q0x + q1x + q2x) * (T)(1.0 / 3.0), cy = (q0y + q1y + q2y) * (T)(1.0 / 3.0);
-            T mu = bilin<T>(a.siz, gx + cx, gy + cy);
+            T mu = bilin<T>(V.siz, gx + cx, gy + cy);
             T w = A / (mu * mu);
             W += w;
             WX += w * cx;
@@ -181,9 +181,9 @@ __device__ void level_sum(const IterArgs<T>& a, T gx, T gy, T v1x, T v1y, T v2x,
 }
 
 template <typename T>
-__device__ void cvd_centroid(const IterArgs<T>& a, int s, int ne, const int* lab, T xi, T yi, T h, T dprev, T& cx,
-                             T& cy, int& level, bool& capped) {
-    const DevParams& P = a.P;
+__device__ void cvd_centroid(const IterArgs<T>& a, const MeshView& V, int s, int ne, const int* lab, T xi, T yi, T h,
+                             T dprev, T& cx, T& cy, int& level, bool& capped) {
+    const DevParams& P = V.P;
     cx = xi;
     cy = yi;
     level = 0;
@@ -243,7 +243,7 @@ __device__ void cvd_centroid(const IterArgs<T>& a, int s, int ne, const int* lab
         T W = 0, WX = 0, WY = 0;
         for (int t = 0; t < m; t++) {
             int u = t + 1 == m ? 0 : t + 1;
-            level_sum<T>(a, xi, yi, vx[t], vy[t], vx[u], vy[u], k - 1, W, WX, WY);
+            level_sum<T>(V, xi, yi, vx[t], vy[t], vx[u], vy[u], k - 1, W, WX, WY);
         }
         if (!(W > 0)) return;
         T iW = (T)1 / W;
@@ -276,20 +276,22 @@ __device__ __forceinline__ double blk_sum(double v, double* sh) {
     return t;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
-    if (a.ctrl->terminated) return;
-    const DevParams& P = a.P;
-    int method = a.ctrl->method_now;
+// one block per chunk of kThreads slots (one mesh in a batch)
+template <typename T, bool B>
+__global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ IterArgs<T> a) {
+    const MeshView& V = mesh_of<B>(a, blockIdx.x * kThreads);
+    if (V.ctrl->terminated) return;
+    const DevParams& P = V.P;
+    int method = V.ctrl->method_now;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double dev = 0, nedge = 0, notsmall = 0;
     unsigned long long nfail = 0, tcap = 0, qcap = 0;
-    if (s < a.n) {
+    if (s < a.n && (!B || s - V.soff < V.n)) {
         T xi = a.srt.x[s], yi = a.srt.y[s];
         int idi = a.srt.id[s];
         int ocls = a.srt.cls[s];
         T dprev = a.srt.dprev[s];
-        T h = (T)a.gh[a.cell[s]];
+        T h = (T)V.gh[a.cell[s]];
         int ne = a.ring_n[s];
         uint32_t vm = a.vmask[s];
         int lab[kRingCap];
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
             lab[4 * q + 2] = v.z;
             lab[4 * q + 3] = v.w;
         }
-        T fac_mu = (T)a.ctrl->fac_mu;
+        T fac_mu = (T)V.ctrl->fac_mu;
         T Fx = 0, Fy = 0, fs = 0;
         // DistMesh forces on the valid edges (Eqs. 2-3); also the size deviation
         for (int t = 0; t < ne; t++) {
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
             T xj = a.srt.x[j], yj = a.srt.y[j];
             T dx = xi - xj, dy = yi - yj;
             T l = sqrt(dx * dx + dy * dy);
-            T mu = bilin<T>(a.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
+            T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
             if (idi < a.srt.id[j]) {
                 dev += (double)fabsf((float)l / ((float)fac_mu * (float)mu) - 1.0f);
                 nedge += 1.0;
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
             pny = yi + (T)P.dt * Fy;
         } else {
             bool capped;
-            cvd_centroid<T>(a, s, ne, lab, xi, yi, h, dprev, cx, cy, qlv, capped);
+            cvd_centroid<T>(a, V, s, ne, lab, xi, yi, h, dprev, cx, cy, qlv, capped);
             if (capped) qcap++;
             pnx = cx;
             pny = cy;
@@ -348,19 +350,19 @@ __global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
             qx = xi + dx * (Tm / d);
             qy = yi + dy * (Tm / d);
         }
-        int c = classify(a, qx, qy);
+        int c = classify(V, qx, qy);
         T fx = qx, fy = qy;
         int ncls = c;
         if (c == PT_OUTSIDE) {
             T ox, oy;
             if (ocls == PT_INNER) {
-                if (sphere_trace(a, xi, yi, qx, qy, ox, oy)) tcap++;
-                int cc = classify(a, ox, oy);
+                if (sphere_trace(V, xi, yi, qx, qy, ox, oy)) tcap++;
+                int cc = classify(V, ox, oy);
                 if (cc == PT_OUTSIDE) { fx = xi; fy = yi; ncls = ocls; }
                 else { fx = ox; fy = oy; ncls = cc; }
             } else {
-                newton_project(a, qx, qy, ox, oy);
-                if (classify(a, ox, oy) == PT_BOUNDARY) { fx = ox; fy = oy; ncls = PT_BOUNDARY; }
+                newton_project(V, qx, qy, ox, oy);
+                if (classify(V, ox, oy) == PT_BOUNDARY) { fx = ox; fy = oy; ncls = PT_BOUNDARY; }
                 else { nfail++; fx = xi; fy = yi; ncls = ocls; }
             }
         }
@@ -387,11 +389,11 @@ __global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
         }
     }
     unsigned m = __ballot_sync(0xffffffffu, nfail != 0);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctrl->cnt.newton_fail, (unsigned long long)__popc(m));
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&V.ctrl->cnt.newton_fail, (unsigned long long)__popc(m));
     m = __ballot_sync(0xffffffffu, tcap != 0);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctrl->cnt.trace_cap, (unsigned long long)__popc(m));
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&V.ctrl->cnt.trace_cap, (unsigned long long)__popc(m));
     m = __ballot_sync(0xffffffffu, qcap != 0);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&a.ctrl->cnt.quad_cap, (unsigned long long)__popc(m));
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&V.ctrl->cnt.quad_cap, (unsigned long long)__popc(m));
     __shared__ double sh[kThreads / 32];
     double v0 = blk_sum(dev, sh);
     double v1 = blk_sum(nedge, sh);
@@ -405,7 +407,8 @@ __global__ void __launch_bounds__(kThreads) k_update(IterArgs<T> a) {
 
 template <typename T>
 void launch_update(const IterArgs<T>& a, int nblocks, cudaStream_t st) {
-    k_update<T><<<nblocks, kThreads, 0, st>>>(a);
+    if (a.Vs) k_update<T, true><<<nblocks, kThreads, 0, st>>>(a);
+    else k_update<T, false><<<nblocks, kThreads, 0, st>>>(a);
 }
 template void launch_update<double>(const IterArgs<double>&, int, cudaStream_t);
 template void launch_update<float>(const IterArgs<float>&, int, cudaStream_t);
@@ -413,11 +416,16 @@ template void launch_update<float>(const IterArgs<float>&, int, cudaStream_t);
 // ------------------------------------------------------------------ statistics
 constexpr int kStatThreads = 512;
 
-__global__ void __launch_bounds__(kStatThreads) k_stats_pre(DevCtrl* ctrl, const EmitPartial* ep, int np, int decide,
-                                                            int force, DevParams P) {
-    if (!force && ctrl->terminated) return;
+// one block per mesh: reduces the mesh's emit partials [c0, c1)
+template <typename T, bool B>
+__global__ void __launch_bounds__(kStatThreads) k_stats_pre(const __grid_constant__ IterArgs<T> a, int decide) {
+    const MeshView& V = B ? a.Vs[blockIdx.x] : a.V;
+    DevCtrl* ctrl = V.ctrl;
+    const DevParams& P = V.P;
+    const EmitPartial* ep = a.ep;
+    if (!a.force && ctrl->terminated) return;
     double acc[9] = {0, 0, 0, 0, 0, 180.0, 0, 0, 0};
-    for (int b = threadIdx.x; b < np; b += blockDim.x) {
+    for (int b = V.c0 + threadIdx.x; b < V.c1; b += blockDim.x) {
         const double* p = reinterpret_cast<const double*>(&ep[b]);
         for (int q = 0; q < 9; q++)
             acc[q] = (q == 3 || q == 4) ? fmax(acc[q], p[q]) : (q == 5 ? fmin(acc[q], p[q]) : acc[q] + p[q]);
@@ -477,10 +485,14 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_pre(DevCtrl* ctrl, const
     else ctrl->last_method = method;
 }
 
-__global__ void __launch_bounds__(kStatThreads) k_stats_post(DevCtrl* ctrl, const UpdatePartial* up, int np) {
+template <typename T, bool B>
+__global__ void __launch_bounds__(kStatThreads) k_stats_post(const __grid_constant__ IterArgs<T> a) {
+    const MeshView& V = B ? a.Vs[blockIdx.x] : a.V;
+    DevCtrl* ctrl = V.ctrl;
+    const UpdatePartial* up = a.up;
     if (ctrl->terminated) return;
     double acc[3] = {0, 0, 0};
-    for (int b = threadIdx.x; b < np; b += blockDim.x) {
+    for (int b = V.c0 + threadIdx.x; b < V.c1; b += blockDim.x) {
         acc[0] += up[b].size_dev;
         acc[1] += up[b].n_edge;
         acc[2] += up[b].not_small;
@@ -500,12 +512,19 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_post(DevCtrl* ctrl, cons
     if (small) ctrl->terminated = 1;  // Sec. 4: every inner move below fac_end * h_i
 }
 
-void launch_stats_pre(DevCtrl* ctrl, const EmitPartial* ep, int nparts, int decide, int force, DevParams P,
-                      cudaStream_t st) {
-    k_stats_pre<<<1, kStatThreads, 0, st>>>(ctrl, ep, nparts, decide, force, P);
+template <typename T>
+void launch_stats_pre(const IterArgs<T>& a, int decide, cudaStream_t st) {
+    if (a.Vs) k_stats_pre<T, true><<<a.nmesh, kStatThreads, 0, st>>>(a, decide);
+    else k_stats_pre<T, false><<<1, kStatThreads, 0, st>>>(a, decide);
 }
-void launch_stats_post(DevCtrl* ctrl, const UpdatePartial* up, int nparts, cudaStream_t st) {
-    k_stats_post<<<1, kStatThreads, 0, st>>>(ctrl, up, nparts);
+template <typename T>
+void launch_stats_post(const IterArgs<T>& a, cudaStream_t st) {
+    if (a.Vs) k_stats_post<T, true><<<a.nmesh, kStatThreads, 0, st>>>(a);
+    else k_stats_post<T, false><<<1, kStatThreads, 0, st>>>(a);
 }
+template void launch_stats_pre<double>(const IterArgs<double>&, int, cudaStream_t);
+template void launch_stats_pre<float>(const IterArgs<float>&, int, cudaStream_t);
+template void launch_stats_post<double>(const IterArgs<double>&, cudaStream_t);
+template void launch_stats_post<float>(const IterArgs<float>&, cudaStream_t);
 
 }  // namespace trime

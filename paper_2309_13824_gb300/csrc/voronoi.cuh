@@ -1,4 +1,4 @@
-// voronoi.cu -- a2: bounded Voronoi cell of every point by half-plane
+// voronoi.cuh -- a2: bounded Voronoi cell of every point by half-plane
 // clipping (TriMe++ Sec. 2.1 Fig. 3, cell-based approach; Sec. 4.1 octagon
 // bound of span S = fac_voro_bound * h_i).
 //
@@ -23,6 +23,7 @@
 // octagon and box used here are enlarged by 1/16 of S over the region Reg_i
 // that the emission test reads, so those float decisions cannot change which
 // Delaunay triangles have their circumcentre inside Reg_i.
+#pragma once
 #include "exact.cuh"
 #include "kernels.cuh"
 
@@ -205,8 +206,8 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
 // one cell per group; slot < 0 marks an idle group (it still takes part in
 // every collective operation of its warp)
 template <typename T, int G>
-__device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, float4* stage) {
-    const DevParams& P = a.P;
+__device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, const Grp<G>& g, float4* stage) {
+    const DevParams& P = V.P;
     const float INF = __int_as_float(0x7f800000);
     bool live = slot >= 0;
     int s = live ? slot : 0;
@@ -222,7 +223,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
     ctx.x = a.srt.x;
     ctx.y = a.srt.y;
     ctx.id = a.srt.id;
-    ctx.ctrl = a.ctrl;
+    ctx.ctrl = V.ctrl;
     ctx.pix = (double)a.srt.x[s];
     ctx.piy = (double)a.srt.y[s];
     ctx.idi = a.srt.id[s];
@@ -310,8 +311,8 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
             int ne0 = ne;
             int st = clip_by<T, G>(L, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, has, RB, g, ctx);
             if (P.debug && has && g.gl == 0) {
-                atomicAdd(&a.ctrl->cnt.vor_picks, 1ull);
-                if (ne != ne0 || st) atomicAdd(&a.ctrl->cnt.vor_cuts, 1ull);
+                atomicAdd(&V.ctrl->cnt.vor_picks, 1ull);
+                if (ne != ne0 || st) atomicAdd(&V.ctrl->cnt.vor_cuts, 1ull);
             }
             if (st) {
                 status = st;
@@ -324,7 +325,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
         __syncwarp();
     };
     for (int r = 1; warp_any(!done); r++) {
-        if (P.debug && !done && g.gl == 0) atomicAdd(&a.ctrl->cnt.vor_rings, 1ull);
+        if (P.debug && !done && g.gl == 0) atomicAdd(&V.ctrl->cnt.vor_rings, 1ull);
         int nr = r == 1 ? 5 : 4 * r;
         for (int kb = 0; kb < nr; kb += G) {
             int k = kb + g.gl;
@@ -350,8 +351,8 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
                 c0 = c0 < 0 ? 0 : c0;
                 c1 = c1 >= P.nbx ? P.nbx - 1 : c1;
                 if (row >= 0 && row < P.nby && c0 <= c1) {
-                    lo = a.bstart[row * P.nbx + c0];
-                    hi = a.bstart[row * P.nbx + c1 + 1];
+                    lo = a.bstart[V.boff + row * P.nbx + c0];
+                    hi = a.bstart[V.boff + row * P.nbx + c1 + 1];
                 }
             }
             int cnt = hi - lo;
@@ -397,7 +398,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
                     km = g.ballot(keep);
                 }
                 if (keep) stage[nst + __popc(km & ((1u << g.gl) - 1u))] = make_float4(dx, dy, d2, __int_as_float(cs));
-                if (P.debug && g.gl == 0 && km) atomicAdd(&a.ctrl->cnt.vor_candidates, (unsigned long long)__popc(km));
+                if (P.debug && g.gl == 0 && km) atomicAdd(&V.ctrl->cnt.vor_candidates, (unsigned long long)__popc(km));
                 nst += __popc(km);
                 __syncwarp();
             }
@@ -418,14 +419,14 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
     if (status == 2 && G < 32) {
         // out of lanes: queue the cell for the 32-lane pass
         if (g.gl == 0) {
-            int q = atomicAdd(&a.ctrl->ovf_n, 1);
+            int q = atomicAdd(a.ovf_n, 1);
             a.ovf_list[q] = s;
-            if (P.debug) atomicAdd(&a.ctrl->cnt.vor_wide, 1ull);
+            if (P.debug) atomicAdd(&V.ctrl->cnt.vor_wide, 1ull);
         }
         return;
     }
     if (status != 0) {
-        if (status == 2 && g.gl == 0) atomicAdd(&a.ctrl->cnt.ring_overflow, 1ull);
+        if (status == 2 && g.gl == 0) atomicAdd(&V.ctrl->cnt.ring_overflow, 1ull);
         if (g.gl == 0) {
             a.ring_n[s] = 0;
             a.cellR[s] = 0.0f;
@@ -439,10 +440,11 @@ __device__ void voronoi_cell(const IterArgs<T>& a, int slot, const Grp<G>& g, fl
     }
 }
 
-// main pass: G = 16 lanes per cell, 32 / G cells per warp
-template <typename T, int G>
-__global__ void __launch_bounds__(kVoroThreads, 6) k_voronoi(IterArgs<T> a) {
-    if (!a.force && a.ctrl->terminated) return;
+// main pass: G lanes per cell, 32 / G cells per warp.  In a batch the cells
+// of a warp lie in one chunk, hence in one mesh.
+template <typename T, int G, bool B>
+__global__ void __launch_bounds__(kVoroThreads, 6) k_voronoi(const __grid_constant__ IterArgs<T> a) {
+    if (!B && !a.force && a.V.ctrl->terminated) return;
     __shared__ float4 stage_all[kVoroThreads / G][kStageCap];
     Grp<G> g;
     int lane = threadIdx.x & 31;
@@ -453,53 +455,46 @@ __global__ void __launch_bounds__(kVoroThreads, 6) k_voronoi(IterArgs<T> a) {
     int nwarps = gridDim.x * (kVoroThreads / 32);
     float4* stage = stage_all[threadIdx.x / G];
     for (int w = blockIdx.x * (kVoroThreads / 32) + wib; w * cpw < a.n; w += nwarps) {
+        const MeshView& V = mesh_of<B>(a, w * cpw);
+        if (B && !a.force && V.ctrl->terminated) continue;
         int s = w * cpw + lane / G;
-        voronoi_cell<T, G>(a, s < a.n ? s : -1, g, stage);
+        bool ok = s < a.n && (!B || s - V.soff < V.n);
+        voronoi_cell<T, G>(a, V, ok ? s : -1, g, stage);
     }
 }
 
 // 32-lane pass over the cells the 16-lane pass could not hold
-template <typename T>
-__global__ void __launch_bounds__(kVoroThreads) k_voronoi_wide(IterArgs<T> a) {
-    if (!a.force && a.ctrl->terminated) return;
+template <typename T, bool B>
+__global__ void __launch_bounds__(kVoroThreads) k_voronoi_wide(const __grid_constant__ IterArgs<T> a) {
+    if (!B && !a.force && a.V.ctrl->terminated) return;
     __shared__ float4 stage_all[kVoroThreads / 32][kStageCap];
     Grp<32> g;
     g.gl = threadIdx.x & 31;
     g.goff = 0;
     int wib = threadIdx.x >> 5;
     int nw = gridDim.x * (kVoroThreads / 32);
-    int n = a.ctrl->ovf_n;
-    for (int i = blockIdx.x * (kVoroThreads / 32) + wib; i < n; i += nw)
-        voronoi_cell<T, 32>(a, a.ovf_list[i], g, stage_all[wib]);
+    int n = *a.ovf_n;
+    for (int i = blockIdx.x * (kVoroThreads / 32) + wib; i < n; i += nw) {
+        int s = a.ovf_list[i];
+        voronoi_cell<T, 32>(a, mesh_of<B>(a, s), s, g, stage_all[wib]);
+    }
 }
 
-template <typename T>
-void launch_voronoi(const IterArgs<T>& a, cudaStream_t st) {
-    cudaMemsetAsync(&a.ctrl->ovf_n, 0, sizeof(int32_t), st);
-    constexpr int G = 16;
-    int cpb = kVoroThreads / G;  // cells per block
+// lanes = 16: two cells per warp plus the 32-lane pass; lanes = 32: one cell
+// per warp
+template <typename T, bool B>
+void launch_voronoi_impl(const IterArgs<T>& a, int lanes, cudaStream_t st) {
+    cudaMemsetAsync(a.ovf_n, 0, sizeof(int32_t), st);
+    if (lanes == 32) {
+        int cpb = kVoroThreads / 32;
+        int g = (a.n + cpb - 1) / cpb;
+        k_voronoi<T, 32, B><<<g < 1 ? 1 : g, kVoroThreads, 0, st>>>(a);
+        return;
+    }
+    int cpb = kVoroThreads / 16;  // cells per block
     int g = (a.n + cpb - 1) / cpb;
-    if (g < 1) g = 1;
-    k_voronoi<T, G><<<g, kVoroThreads, 0, st>>>(a);
-    k_voronoi_wide<T><<<152 * 2, kVoroThreads, 0, st>>>(a);
-}
-
-template void launch_voronoi<double>(const IterArgs<double>&, cudaStream_t);
-template void launch_voronoi<float>(const IterArgs<float>&, cudaStream_t);
-
-// device exact predicates on explicit queries (verification hook)
-__global__ void k_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    const double* p = pts + 8 * (size_t)q;
-    const int32_t* id = ids + 4 * (size_t)q;
-    o_out[q] = orient_exact(p, p + 2, p + 4);
-    c_out[q] = incircle_sos(p, id[0], p + 2, id[1], p + 4, id[2], p + 6, id[3]);
-}
-
-void launch_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out,
-                       cudaStream_t st) {
-    if (nq > 0) k_predicates<<<(nq + 127) / 128, 128, 0, st>>>(pts, ids, nq, o_out, c_out);
+    k_voronoi<T, 16, B><<<g < 1 ? 1 : g, kVoroThreads, 0, st>>>(a);
+    k_voronoi_wide<T, B><<<152 * 2, kVoroThreads, 0, st>>>(a);
 }
 
 }  // namespace trime

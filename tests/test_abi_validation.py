@@ -44,3 +44,39 @@ def test_invalid_arguments(g):
     assert _init(g, outside, siz, ok) == g.TRIME_EINVAL
     assert g.lib().mesh_step(None, 1, None) == g.TRIME_EINVAL
     assert g.lib().mesh_bucket_points(None, None, 10, 0, 0, 1, 1, 0, 4, None, None, None, None) == g.TRIME_EINVAL
+
+
+def _batch_init(g, meshes, n_meshes=None, **kw):
+    p = g.mesh_default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    nm = len(meshes)
+    G = (g.mesh_grid2d * max(nm, 1))()
+    Z = (g.mesh_grid2d * max(nm, 1))()
+    X = (C.c_void_p * max(nm, 1))()
+    N = (C.c_int64 * max(nm, 1))()
+    keep = []
+    for k, (sdf, siz, pts) in enumerate(meshes):
+        gs, a = g._grid(sdf)
+        gz, b = g._grid(siz)
+        xy = np.ascontiguousarray(pts, dtype=np.float64)
+        G[k], Z[k], X[k], N[k] = gs, gz, xy.ctypes.data_as(C.c_void_p), len(xy)
+        keep += [a, b, xy]
+    h = C.c_void_p()
+    return g.lib().mesh_batch_init(C.byref(h), nm if n_meshes is None else n_meshes, G, Z, X, N, C.byref(p), 0,
+                                   None)
+
+
+def test_invalid_batch_arguments(g):
+    sdf = W.grid_from_fn(W.disk_sdf_fn, 32)
+    siz = W.constant_grid(1.0)
+    ok = np.array([[0.0, 0.0], [0.1, 0.0]])
+    assert _batch_init(g, [], n_meshes=0) == g.TRIME_EINVAL
+    assert _batch_init(g, [(sdf, siz, ok), (sdf, siz, np.array([[7.0, 0.0]]))]) == g.TRIME_EINVAL
+    assert "mesh 1" in g.mesh_last_error()
+    assert _batch_init(g, [(sdf, W.constant_grid(0.0), ok)]) == g.TRIME_EINVAL
+    assert "mesh 0" in g.mesh_last_error()
+    assert _batch_init(g, [(sdf, siz, ok)], method=9) == g.TRIME_EINVAL
+    assert g.lib().mesh_batch_step(None, 1, None) == g.TRIME_EINVAL
+    assert g.lib().mesh_batch_get_triangles(None, 0, None, 0, None) == g.TRIME_EINVAL
+    assert g.lib().mesh_batch_size(None) == 0

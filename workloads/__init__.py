@@ -247,6 +247,56 @@ def star_workload(n: int, nv: int = 500, seed: int = 2, sdf_n: int = 1024, siz_n
     return Workload(f"star{nv}-hybrid-n{n}", sdf, siz, pts, 2, precision, 100)
 
 
+@dataclass
+class BatchWorkload:
+    name: str
+    meshes: list  # (sdf Grid, sizing Grid, points (N, 2) float64) per mesh
+    method: int
+    precision: int
+    iters: int
+
+    @property
+    def total_points(self) -> int:
+        return int(sum(len(m[2]) for m in self.meshes))
+
+
+def _star_batch_member(args):
+    nv, n, vseed, pseed, sdf_n = args
+    verts = star_polygon(nv, 0.4, 1.0, vseed)
+    sdf = polygon_sdf_grid(verts, sdf_n)
+    siz = Grid(np.ascontiguousarray(0.002 + 0.05 * np.abs(sdf.values), dtype=np.float32),
+               sdf.x0, sdf.y0, sdf.x1, sdf.y1)
+
+    def sdf_fn(x, y):
+        return _bilinear_np(sdf, x, y)
+
+    return sdf, siz, uniform_in(sdf_fn, n, pseed)
+
+
+def star_batch_workload(n_meshes: int = 256, seed: int = 7, sdf_n: int = 512, n_min: float = 1e3,
+                        n_max: float = 1e5, nv_min: int = 50, nv_max: int = 300, precision: int = 1,
+                        workers: int = 0) -> BatchWorkload:
+    """Independent random star polygons (nv_min..nv_max vertices, radii
+    U[0.4, 1]), SDF on sdf_n^2, sizing 0.002 + 0.05|sdf| on the same nodes,
+    point counts log-uniform in [n_min, n_max], uniform seeding inside each
+    shape.  workers > 1 builds the meshes in that many spawned processes."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for k in range(n_meshes):
+        nv = int(rng.integers(nv_min, nv_max + 1))
+        n = int(round(float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))))
+        jobs.append((nv, n, int(rng.integers(0, 2**31 - 1)), int(rng.integers(0, 2**31 - 1)), sdf_n))
+    if workers > 1 and n_meshes > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            meshes = list(ex.map(_star_batch_member, jobs))
+    else:
+        meshes = [_star_batch_member(j) for j in jobs]
+    return BatchWorkload(f"stars{n_meshes}-hybrid-batch", meshes, 2, precision, 100)
+
+
 def _bilinear_np(g: Grid, x, y):
     """Plain bilinear lookup used only to draw seeds inside a gridded shape."""
     tx = (np.asarray(x) - g.x0) / ((g.x1 - g.x0) / (g.nx - 1))
