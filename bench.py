@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--method", type=int, default=2)
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-quality / FP32 / CPU legs")
     ap.add_argument("--n-opt", type=float, default=None, help="points per neighbour bucket (default 3.3)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="add the N sweep (annulus 1e4..1e7, square 1e6) and the 1e7-point star")
     return ap.parse_args()
 
 
@@ -170,6 +172,120 @@ def oracle_sample_rate(wl, target_s, max_cells=None):
     om.rebuild_sample(cells)
     dt = time.perf_counter() - t
     return cnt, dt
+
+
+def batched_leg(g, torch, stream, steps, flush):
+    """256 independent star meshes stepped as one batch (one launch per
+    stage, autotuned tiling) against the same meshes stepped one mesh handle
+    after another, plus the batch's wall time until every mesh terminates."""
+    import workloads as W
+
+    wl = W.star_batch_workload(workers=min(16, os.cpu_count() or 1), precision=1)
+    meshes = [(s, z, W.to_fp32_positions(p)) for s, z, p in wl.meshes]
+    npts = wl.total_points
+    t0 = time.perf_counter()
+    b = g.MeshBatch(meshes, stream=stream.cuda_stream, autotune=True, precision=1, method=2)
+    init_s = time.perf_counter() - t0
+    tun = b.tuning()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush_l2(flush)
+            evs[k][0].record(stream)
+            fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(c) for a, c in evs) / steps
+
+    ms_b = timed(lambda: b.step_async(1))
+    b.close()
+    singles = [g.Mesh(s, z, p, precision=1, method=2, stream=stream.cuda_stream) for s, z, p in meshes]
+
+    def step_all():
+        for m in singles:
+            m.step_async(1)
+
+    ms_s = timed(step_all)
+    for m in singles:
+        m.close()
+    q = g.MeshBatch(meshes, stream=stream.cuda_stream, autotune=False, precision=1, method=2)
+    q.set_tuning(tun["n_opt"], tun["lanes"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = q.step(2000)
+    torch.cuda.synchronize()
+    tq = time.perf_counter() - t0
+    q.close()
+    sizes = [len(m[2]) for m in meshes]
+    return {"workload": f"{len(meshes)} random star polygons (50-300 vertices), 512^2 FP32 SDF each, sizing "
+                        f"0.002+0.05|sdf|, points log-uniform in [1e3,1e5] (total {npts}), uniform seeding, "
+                        f"hybrid, FP32 positions",
+            "meshes": len(meshes), "points": npts, "min_points": min(sizes), "max_points": max(sizes),
+            "value": npts / (ms_b / 1e3) / 1e6, "unit": "Mpts/s", "ms_per_step": ms_b,
+            "one_mesh_at_a_time": {"value": npts / (ms_s / 1e3) / 1e6, "unit": "Mpts/s", "ms_per_step": ms_s},
+            "tuning": {"n_opt": tun["n_opt"], "lanes": tun["lanes"],
+                       "candidates_ms": [[c[0], c[1], c[2]] for c in tun["candidates"]],
+                       "init_seconds_with_autotune": init_s},
+            "time_to_quality": {"seconds": tq, "all_terminated": all(x["terminated"] for x in st),
+                                "max_iterations": max(x["iterations"] for x in st),
+                                "min_angle_deg_worst": min(x["min_angle_deg"] for x in st if x["n_tri"] > 0),
+                                "max_alpha_worst": max(x["max_alpha"] for x in st)}}
+
+
+def device_rate(g, torch, stream, flush, sdf, siz, pts, steps, **params):
+    """Device time of `steps` iterations of a fresh mesh (L2 flushed before
+    each), after 3 warm-up iterations; returns (Mpts/s, ms per step)."""
+    m = g.Mesh(sdf, siz, pts, stream=stream.cuda_stream, **params)
+    for _ in range(3):
+        m.step_async(1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush_l2(flush)
+        evs[k][0].record(stream)
+        m.step_async(1)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    m.close()
+    return len(pts) / (ms / 1e3) / 1e6, ms
+
+
+def sweep_leg(g, torch, stream, steps, flush):
+    """Throughput over problem sizes (the annulus at 1e4..1e7 points, FP64
+    hybrid; the uniform square at 1e6) and the 1e7-point star polygon (FP32
+    positions, hybrid) with its wall time to quality."""
+    import workloads as W
+
+    out = {"annulus_fp64_hybrid": []}
+    for n in (10_000, 100_000, 10_000_000):
+        wl = W.annulus_workload(n=n)
+        v, ms = device_rate(g, torch, stream, flush, wl.sdf, wl.sizing, wl.points, steps, method=2)
+        out["annulus_fp64_hybrid"].append({"points": n, "value": v, "unit": "Mpts/s", "ms_per_step": ms})
+    wl = W.square_workload(1_000_000)
+    v, ms = device_rate(g, torch, stream, flush, wl.sdf, wl.sizing, wl.points, steps, method=2)
+    out["square_fp64_hybrid"] = {"points": 1_000_000, "value": v, "unit": "Mpts/s", "ms_per_step": ms}
+    wl = W.star_workload(10_000_000, workers=min(16, os.cpu_count() or 1))
+    p32 = W.to_fp32_positions(wl.points)
+    v, ms = device_rate(g, torch, stream, flush, wl.sdf, wl.sizing, p32, steps, method=2, precision=1)
+    m = g.Mesh(wl.sdf, wl.sizing, p32, method=2, precision=1, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = m.step(2000)
+    torch.cuda.synchronize()
+    tq = time.perf_counter() - t0
+    m.close()
+    out["star500_fp32_hybrid_1e7"] = {
+        "workload": "star polygon, 500 vertices (radii U[0.4,1], seed 2), 4096^2 FP32 SDF, curvature-adaptive "
+                    "sizing in [2e-4,1e-2] on 1024^2, 1e7 points ~ 1/h^2, FP32 positions, hybrid",
+        "value": v, "unit": "Mpts/s", "ms_per_step": ms,
+        "time_to_quality": {"seconds": tq, "iterations": s["iterations"], "terminated": bool(s["terminated"]),
+                            "min_angle_deg": s["min_angle_deg"], "half_mean_alpha": s["half_mean_alpha"],
+                            "max_alpha": s["max_alpha"], "n_tri": s["n_tri"]}}
+    return out
 
 
 def run_reference(args, wl):
@@ -333,6 +449,9 @@ def main():
             extras["fp32_positions"] = {"value": n * args.steps / (ms32 / 1e3) / 1e6, "unit": "Mpts/s",
                                         "ms_per_step": ms32 / args.steps}
             fm.close()
+        extras["batched"] = batched_leg(g, torch, stream, args.steps, flush)
+        if args.sweep:
+            extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
         cnt, dt = oracle_sample_rate(wl, 10.0)
         extras["cpu_baseline"] = {"value": cnt / dt / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
                                   "sample": f"{cnt} random cells of the workload: cell clipping, owned triangles "
@@ -349,7 +468,7 @@ def main():
                            "l2": "flushed before every timed step (256 MB write)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 11 * args.steps,
+                "gpu_launches": 12 * args.steps,
                 "last_step": {"method": st["method"], "switched": st["switched"], "n_tri": st["n_tri"],
                               "half_mean_alpha": st["half_mean_alpha"]}}
         line.update(extras)

@@ -76,6 +76,8 @@ def _load():
         for name in ("om_rebuild", "om_step"):
             getattr(lib, name).argtypes = [C.c_void_p]
         lib.om_rebuild_sample.argtypes = [C.c_void_p, i64p, C.c_int64, C.c_int]
+        lib.om_sample_triangles.restype = C.c_int64
+        lib.om_sample_triangles.argtypes = [C.c_void_p, i64p, C.c_int64, ip, C.c_int64]
         for name in ("om_num_points", "om_num_triangles", "om_num_edges"):
             getattr(lib, name).restype = C.c_int64
             getattr(lib, name).argtypes = [C.c_void_p]
@@ -195,6 +197,16 @@ class OracleMesh:
     def rebuild_sample(self, cells):
         cells = np.ascontiguousarray(cells, dtype=np.int64)
         self._lib.om_rebuild_sample(self._h, cells.ctypes.data_as(C.POINTER(C.c_int64)), len(cells), 0)
+
+    def sample_triangles(self, cells) -> np.ndarray:
+        """Valid triangles owned (smallest index) by the given cells."""
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        cp = cells.ctypes.data_as(C.POINTER(C.c_int64))
+        n = self._lib.om_sample_triangles(self._h, cp, len(cells), None, 0)
+        t = np.zeros((n, 3), dtype=np.int32)
+        if n:
+            self._lib.om_sample_triangles(self._h, cp, len(cells), t.ctypes.data_as(C.POINTER(C.c_int32)), n)
+        return t
 
     def stats(self) -> dict:
         s = _Stats()

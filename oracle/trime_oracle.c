@@ -1337,14 +1337,19 @@ int om_step(om_mesh* m) {
 /* Per-cell work of one iteration on a subset of cells, for timing: the
  * cell (Sec. 2.1), its owned triangles with Tests 1-3 (Sec. 4.1) and, with
  * with_centroid, its CVD centroid (Sec. 4.2).  Returns the triangles kept. */
-int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid) {
+/* Procedure I restricted to the given cells: each cell's clip, the valid
+ * triangles it owns (smallest index first, counter-clockwise) and, with
+ * with_centroid, its CVD centroid.  Owned triangles are written to tri (up to
+ * cap of them) when tri is not NULL; returns how many there are. */
+static int64_t sample_cells(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid, int32_t* tri,
+                            int64_t cap) {
     ogrid_t G;
     ogrid_build(m, &G);
     hp_t E[CELL_CAP];
     int32_t lab[CELL_CAP];
     double poly[2 * CELL_CAP];
     int64_t errs = 0;
-    int kept = 0;
+    int64_t kept = 0;
     for (int64_t q = 0; q < ncells; q++) {
         int64_t i = cells[q];
         int ne = cell_compute(m, &G, i, E, &errs);
@@ -1356,6 +1361,11 @@ int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with
             circumcenter_fixed(m->x[i], m->y[i], m->x[j], m->y[j], m->x[k], m->y[k], &ox, &oy, &R);
             if (!(reg_contains(m, i, ox, oy) && reg_contains(m, j, ox, oy) && reg_contains(m, k, ox, oy))) continue;
             if (m->P.validity && !triangle_valid(m, i, j, k)) continue;
+            if (tri && kept < cap) {
+                tri[3 * kept] = (int32_t)i;
+                tri[3 * kept + 1] = j;
+                tri[3 * kept + 2] = k;
+            }
             kept++;
         }
         if (with_centroid) {
@@ -1370,6 +1380,14 @@ int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with
     }
     ogrid_free(&G);
     return kept;
+}
+
+int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid) {
+    return (int)sample_cells(m, cells, ncells, with_centroid, NULL, 0);
+}
+
+int64_t om_sample_triangles(om_mesh* m, const int64_t* cells, int64_t ncells, int32_t* tri, int64_t cap) {
+    return sample_cells(m, cells, ncells, 0, tri, cap);
 }
 
 /* ------------------------------------------------------------------------ */

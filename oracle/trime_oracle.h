@@ -78,6 +78,12 @@ int om_rebuild(om_mesh* m);
 int om_step(om_mesh* m);
 /* Same as om_step but only for the cells listed (timing sample; no move). */
 int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid);
+/* The valid triangles owned by the given cells (Procedure I restricted to
+ * them; a triangle is owned by its smallest-index vertex), as index triples
+ * (smallest first, counter-clockwise) into tri (capacity cap triples).
+ * Returns the number of such triangles (may exceed cap; then only cap are
+ * written). */
+int64_t om_sample_triangles(om_mesh* m, const int64_t* cells, int64_t ncells, int32_t* tri, int64_t cap);
 
 int64_t om_num_points(const om_mesh* m);
 int64_t om_num_triangles(const om_mesh* m);

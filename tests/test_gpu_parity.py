@@ -251,3 +251,28 @@ def test_full_size_annulus_triangles(precision):
     wl = W.annulus_workload(n=1_000_000, method=2, precision=precision)
     gm, om = make_pair((wl.sdf, wl.sizing, wl.points), precision=precision, method=2)
     _tri_equal(gm, om)
+
+
+def test_full_size_star_1e7_sampled():
+    # the 1e7-point star polygon (500 vertices, 4096^2 SDF, FP32 positions):
+    # every triangle owned by 20000 random cells, as the oracle computes them
+    import os
+
+    import oracle
+    import paper_2309_13824_gb300 as g
+
+    wl = W.star_workload(10_000_000, workers=min(16, os.cpu_count() or 1))
+    p = W.to_fp32_positions(wl.points)
+    gm = g.Mesh(wl.sdf, wl.sizing, p, precision=1, method=2)
+    st = gm.rebuild()
+    assert st["ring_overflow"] == 0 and st["exact_overflow"] == 0
+    tg = gm.triangles()
+    assert st["n_tri"] == len(tg)
+    om = oracle.OracleMesh(wl.sdf, wl.sizing, p, method=2)
+    cells = np.random.default_rng(0).choice(len(p), 20000, replace=False)
+    to = sorted_tris(om.sample_triangles(cells))
+    sel = sorted_tris(tg[np.isin(tg[:, 0], cells)])
+    assert len(sel) == len(to) > 0
+    assert np.array_equal(sel, to)
+    s = gm.step(2)
+    assert s["ring_overflow"] == 0 and s["exact_overflow"] == 0 and s["n_tri"] > 0

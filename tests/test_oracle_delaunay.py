@@ -178,3 +178,21 @@ def test_duplicate_points_resolved(oracle_mod):
     # the duplicate with the smaller id has an empty cell (SoS: larger id owns it)
     assert 1 not in tri
     assert len(m.ring(1)) == 0 and len(m.ring(3)) > 0
+
+
+def test_sample_triangles_are_the_owned_subset():
+    # Procedure I on a subset of cells yields exactly the full rebuild's
+    # triangles whose smallest vertex is in the subset
+    import oracle
+    import workloads as W
+
+    wl = W.disk_workload(n=3000, seed=3)
+    om = oracle.OracleMesh(wl.sdf, wl.sizing, wl.points)
+    om.rebuild()
+    full = om.triangles()
+    cells = np.random.default_rng(1).choice(3000, 400, replace=False)
+    sub = om.sample_triangles(cells)
+    want = full[np.isin(full[:, 0], cells)]
+    key = lambda t: sorted(map(tuple, t.tolist()))
+    assert len(sub) == len(want) > 0
+    assert key(sub) == key(want)

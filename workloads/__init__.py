@@ -104,26 +104,41 @@ def _star_radius(verts_ccw, theta):
     return s
 
 
-def polygon_sdf_grid(verts_cw, n: int, box=BOX) -> Grid:
-    """Signed distance to a star polygon: nearest-segment distance, sign from
-    the radial inside test (the polygon is star-shaped around the origin)."""
+_SEG_TREES = {}
+
+
+def _segment_samples(verts_cw, h):
+    """kd-tree of points spaced h/4 along every segment, and their segment."""
     from scipy.spatial import cKDTree
 
-    X, Y = _node_grid(n, box)
+    key = (verts_cw.tobytes(), float(h))
+    if key not in _SEG_TREES:
+        a = verts_cw
+        b = np.roll(verts_cw, -1, axis=0)
+        seg_len = np.hypot(*(b - a).T)
+        k_per = np.maximum(2, np.ceil(seg_len / (h / 4)).astype(int))
+        samples, owner = [], []
+        for s in range(len(a)):
+            t = np.linspace(0, 1, k_per[s], endpoint=False)
+            samples.append(a[s] + t[:, None] * (b[s] - a[s]))
+            owner.append(np.full(k_per[s], s))
+        samples = np.concatenate(samples)
+        _SEG_TREES.clear()
+        _SEG_TREES[key] = (cKDTree(samples), np.concatenate(owner))
+    return _SEG_TREES[key]
+
+
+def _polygon_sdf_rows(args):
+    verts_cw, n, box, j0, j1 = args
+    x0, y0, x1, y1 = box
+    xs = x0 + np.arange(n) * ((x1 - x0) / (n - 1))
+    ys = y0 + np.arange(j0, j1) * ((y1 - y0) / (n - 1))
+    X, Y = np.meshgrid(xs, ys)
     P = np.stack([X.ravel(), Y.ravel()], 1)
     a = verts_cw
     b = np.roll(verts_cw, -1, axis=0)
-    h = (box[2] - box[0]) / (n - 1)
-    seg_len = np.hypot(*(b - a).T)
-    k_per = np.maximum(2, np.ceil(seg_len / (h / 4)).astype(int))
-    samples, owner = [], []
-    for s in range(len(a)):
-        t = np.linspace(0, 1, k_per[s], endpoint=False)
-        samples.append(a[s] + t[:, None] * (b[s] - a[s]))
-        owner.append(np.full(k_per[s], s))
-    samples = np.concatenate(samples)
-    owner = np.concatenate(owner)
-    tree = cKDTree(samples)
+    h = (x1 - x0) / (n - 1)
+    tree, owner = _segment_samples(verts_cw, h)
     best = np.full(len(P), np.inf)
     _, idx = tree.query(P, k=1)
     nseg = len(a)
@@ -137,8 +152,24 @@ def polygon_sdf_grid(verts_cw, n: int, box=BOX) -> Grid:
     ccw = verts_cw[::-1]
     rr = _star_radius(ccw, np.arctan2(P[:, 1], P[:, 0]))
     inside = np.hypot(P[:, 0], P[:, 1]) < rr
-    sdf = np.where(inside, -best, best).reshape(X.shape)
-    return Grid(np.ascontiguousarray(sdf, dtype=np.float32), *box)
+    return np.where(inside, -best, best).reshape(X.shape).astype(np.float32)
+
+
+def polygon_sdf_grid(verts_cw, n: int, box=BOX, workers: int = 0) -> Grid:
+    """Signed distance to a star polygon: nearest-segment distance, sign from
+    the radial inside test (the polygon is star-shaped around the origin).
+    Rows are computed in blocks, in `workers` spawned processes if > 1."""
+    step = max(1, (1 << 18) // n)
+    jobs = [(verts_cw, n, box, j, min(n, j + step)) for j in range(0, n, step)]
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            rows = list(ex.map(_polygon_sdf_rows, jobs))
+    else:
+        rows = [_polygon_sdf_rows(j) for j in jobs]
+    return Grid(np.ascontiguousarray(np.concatenate(rows, 0), dtype=np.float32), *box)
 
 
 # ---------------------------------------------------------------- point seeding
@@ -219,31 +250,116 @@ def square_workload(n: int, seed: int = 4, sdf_n: int = 256) -> Workload:
     return Workload(f"square-n{n}", sdf, siz, pts, 2, 0, 100)
 
 
-def star_workload(n: int, nv: int = 500, seed: int = 2, sdf_n: int = 1024, siz_n: int = 256,
-                  precision: int = 1) -> Workload:
-    """Random star polygon; sizing clamp(0.1*dist_to_boundary + 0.01*r_local, 2e-4, 1e-2)."""
-    verts = star_polygon(nv, 0.4, 1.0, seed)
-    sdf = polygon_sdf_grid(verts, sdf_n)
-    coarse = polygon_sdf_grid(verts, siz_n)
-    # local thickness proxy: each vertex's distance to the nearest non-incident vertex
+def _seg_dist(P, A, B):
+    """Distance from points P (m, 2) to segments A-B (broadcast)."""
+    e = B - A
+    t = np.clip(((P - A) * e).sum(-1) / (e * e).sum(-1), 0.0, 1.0)
+    return np.hypot(*np.moveaxis(P - (A + t[..., None] * e), -1, 0))
+
+
+def star_lfs(verts_cw):
+    """Local thickness at each vertex: distance to the nearest segment not
+    incident to it."""
+    nv = len(verts_cw)
+    a = verts_cw
+    b = np.roll(verts_cw, -1, axis=0)
+    d = _seg_dist(verts_cw[:, None, :], a[None, :, :], b[None, :, :])  # (vertex, segment)
+    idx = np.arange(nv)
+    d[idx, idx] = np.inf            # segment (v, v+1)
+    d[idx, (idx - 1) % nv] = np.inf  # segment (v-1, v)
+    return d.min(1)
+
+
+def star_sizing_grid(verts_cw, n: int, lo: float = 2e-4, hi: float = 1e-2, grad: float = 0.1,
+                     box=BOX) -> Grid:
+    """Curvature-adaptive sizing h(x) = clamp(min_s grad |x - v_s| + t(v_s), lo, hi)
+    over the polygon's vertices v_s, sampled on n^2 nodes, where the vertex
+    size t(v) is proportional to the local thickness lfs(v) and scaled so that
+    the narrowest vertex gets lo: the sizes span [lo, hi]."""
     from scipy.spatial import cKDTree
 
-    tree = cKDTree(verts)
-    dd, _ = tree.query(verts, k=3)
-    lfs = dd[:, 2]
-    Xs, Ys = coarse.nodes()
-    _, vi = tree.query(np.stack([Xs.ravel(), Ys.ravel()], 1), k=1)
-    h = np.clip(0.1 * np.abs(coarse.values.ravel()) + 0.25 * lfs[vi], 2e-4, 1e-2)
-    siz = Grid(np.ascontiguousarray(h.reshape(coarse.values.shape), dtype=np.float32),
-               coarse.x0, coarse.y0, coarse.x1, coarse.y1)
+    t = star_lfs(verts_cw)
+    t = t * (lo / t.min())
+    X, Y = _node_grid(n, box)
+    P = np.stack([X.ravel(), Y.ravel()], 1)
+    # min_s grad |x - v_s| + t_s over the k nearest vertices, exact wherever the
+    # k-th nearest cannot win (grad d_k + min t >= the minimum found); the
+    # remaining nodes are evaluated against every vertex
+    k = min(16, len(verts_cw))
+    d, idx = cKDTree(verts_cw).query(P, k=k)
+    d = d.reshape(len(P), k)
+    idx = idx.reshape(len(P), k)
+    h = (grad * d + t[idx]).min(1)
+    open_ = np.nonzero(grad * d[:, -1] + t.min() < h)[0]
+    for c in range(0, len(open_), 1 << 14):
+        q = P[open_[c:c + (1 << 14)]]
+        dd = np.hypot(q[:, None, 0] - verts_cw[None, :, 0], q[:, None, 1] - verts_cw[None, :, 1])
+        h[open_[c:c + (1 << 14)]] = (grad * dd + t[None, :]).min(1)
+    h = np.clip(h, lo, hi).reshape(X.shape)
+    return Grid(np.ascontiguousarray(h, dtype=np.float32), *box)
 
-    def sdf_fn(x, y):
-        return _bilinear_np(sdf, x, y)
 
-    def h_fn(x, y):
-        return _bilinear_np(siz, x, y)
+def _density_grid_chunk(args):
+    sdf, siz, n, seed_seq = args
+    rng = np.random.default_rng(seed_seq)
+    v = siz.values.astype(np.float64)
+    hmin = np.minimum(np.minimum(v[:-1, :-1], v[:-1, 1:]), np.minimum(v[1:, :-1], v[1:, 1:])).ravel()
+    cdf = np.cumsum(1.0 / hmin**2)
+    cdf /= cdf[-1]
+    dx = (siz.x1 - siz.x0) / (siz.nx - 1)
+    dy = (siz.y1 - siz.y0) / (siz.ny - 1)
+    ncx = siz.nx - 1
+    out = []
+    got = 0
+    while got < n:
+        m = max(1 << 16, 3 * (n - got))
+        c = np.minimum(np.searchsorted(cdf, rng.uniform(0, 1, m), side="right"), len(cdf) - 1)
+        ci, cj = c % ncx, c // ncx
+        x = siz.x0 + (ci + rng.uniform(0, 1, m)) * dx
+        y = siz.y0 + (cj + rng.uniform(0, 1, m)) * dy
+        keep = rng.uniform(0, 1, m) < (hmin[c] / _bilinear_np(siz, x, y)) ** 2
+        x, y = x[keep], y[keep]
+        inside = _bilinear_np(sdf, x, y) < 0
+        p = np.stack([x[inside], y[inside]], 1)
+        out.append(p)
+        got += len(p)
+    return np.concatenate(out)[:n]
 
-    pts = density_in(sdf_fn, h_fn, n, seed + 1, margin=0.0)
+
+def density_in_grid(sdf: Grid, siz: Grid, n: int, seed: int, workers: int = 0):
+    """n points inside {sdf < 0} with density proportional to 1/h^2 for the
+    bilinear sizing grid h: cells of the sizing grid are drawn with weight
+    area / hmin_cell^2 (hmin_cell = smallest corner value, a lower bound of h
+    in the cell), a point uniform in the cell is kept with probability
+    (hmin_cell / h(p))^2 and if sdf(p) < 0 (exact rejection sampling).  Points
+    come in blocks of 2^20 with their own seeds (numpy SeedSequence), so the
+    result does not depend on `workers`."""
+    block = 1 << 20
+    counts = [min(block, n - k) for k in range(0, n, block)]
+    seqs = np.random.SeedSequence(seed).spawn(len(counts))
+    jobs = [(sdf, siz, c, q) for c, q in zip(counts, seqs)]
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_density_grid_chunk, jobs))
+    else:
+        parts = [_density_grid_chunk(j) for j in jobs]
+    if not parts:
+        return np.zeros((0, 2))
+    return np.ascontiguousarray(np.concatenate(parts), dtype=np.float64)
+
+
+def star_workload(n: int, nv: int = 500, seed: int = 2, sdf_n: int = 4096, siz_n: int = 1024,
+                  precision: int = 1, workers: int = 0) -> Workload:
+    """Random star polygon (nv vertices at angles 2 pi k / nv, radii
+    U[0.4, 1]), exact segment SDF on sdf_n^2, curvature-adaptive sizing in
+    [2e-4, 1e-2] on siz_n^2 (star_sizing_grid), n points ~ 1/h^2 (seed + 1)."""
+    verts = star_polygon(nv, 0.4, 1.0, seed)
+    sdf = polygon_sdf_grid(verts, sdf_n, workers=workers)
+    siz = star_sizing_grid(verts, siz_n)
+    pts = density_in_grid(sdf, siz, n, seed + 1, workers=workers)
     return Workload(f"star{nv}-hybrid-n{n}", sdf, siz, pts, 2, precision, 100)
 
 
