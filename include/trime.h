@@ -223,6 +223,15 @@ int mesh_set_tuning(mesh_t* m, double n_opt, int32_t lanes);
 int mesh_exact_predicates(const double* pts, const int32_t* ids, int64_t nq, int32_t* out_orient,
                           int32_t* out_incircle);
 
+/* Verification hook of the tensor-core tile used by the learned model:
+ * D = A * B^T with A (M x K) and B (N x K) given as BF16 bit patterns
+ * (row-major HOST arrays of uint16) and D (M x N) a row-major HOST float32
+ * array, multiplied by tcgen05 MMAs on the device with FP32 accumulation in
+ * tensor memory.  M a positive multiple of 128; N and K multiples of 16 in
+ * [16, 256].  Synchronous.  TRIME_ETIMEOUT if a bounded device wait ran out.
+ * The paper has no counterpart (its method has no learned part). */
+int mesh_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int32_t M, int32_t N, int32_t K);
+
 /* ---------------------------------------------------------------- batches
  * Many independent meshes of uneven sizes stepped together: every stage of
  * an iteration is one kernel launch over all meshes (their points are

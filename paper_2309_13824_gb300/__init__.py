@@ -74,7 +74,7 @@ EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mes
            "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
            "mesh_batch_step", "mesh_batch_get_triangles", "mesh_batch_get_points", "mesh_batch_set_state",
            "mesh_batch_set_method_state", "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_batch_destroy",
-           "mesh_set_tuning", "mesh_batch_set_tuning"]
+           "mesh_set_tuning", "mesh_batch_set_tuning", "mesh_tc_gemm_bf16"]
 
 _lib = None
 
@@ -126,6 +126,7 @@ def lib():
     L.mesh_batch_profile_step.argtypes = [vp, C.c_int32, vp]
     L.mesh_batch_get_tuning.argtypes = [vp, P(mesh_tuning)]
     L.mesh_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
+    L.mesh_tc_gemm_bf16.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_int32]
     L.mesh_batch_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
     L.mesh_batch_destroy.argtypes = [vp]
     L.mesh_batch_destroy.restype = None
@@ -134,7 +135,8 @@ def lib():
                  "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc", "mesh_batch_init",
                  "mesh_batch_size", "mesh_batch_rebuild", "mesh_batch_step", "mesh_batch_get_triangles",
                  "mesh_batch_get_points", "mesh_batch_set_state", "mesh_batch_set_method_state",
-                 "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_set_tuning", "mesh_batch_set_tuning"):
+                 "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_set_tuning", "mesh_batch_set_tuning",
+                 "mesh_tc_gemm_bf16"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -194,6 +196,29 @@ def mesh_exact_predicates(pts, ids):
     _check(lib().mesh_exact_predicates(pts.ctypes.data_as(C.c_void_p), ids.ctypes.data_as(C.c_void_p), nq,
                                        o.ctypes.data_as(C.c_void_p), c.ctypes.data_as(C.c_void_p)))
     return o, c
+
+
+def bf16_bits(x) -> np.ndarray:
+    """float32 values rounded to the nearest BF16 (ties to even), as uint16 bits."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    r = ((u >> 16) & 1) + 0x7FFF
+    return ((u + r) >> 16).astype(np.uint16)
+
+
+def bf16_to_float(b) -> np.ndarray:
+    return (np.asarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def mesh_tc_gemm_bf16(A, B):
+    """D = A B^T on the tensor cores (A: M x K, B: N x K BF16 bit arrays)."""
+    A = np.ascontiguousarray(A, dtype=np.uint16)
+    B = np.ascontiguousarray(B, dtype=np.uint16)
+    M, K = A.shape
+    N = B.shape[0]
+    D = np.zeros((M, N), dtype=np.float32)
+    _check(lib().mesh_tc_gemm_bf16(A.ctypes.data_as(C.c_void_p), B.ctypes.data_as(C.c_void_p),
+                                   D.ctypes.data_as(C.c_void_p), M, N, K))
+    return D
 
 
 def _stats_dict(s: mesh_stats) -> dict:
