@@ -232,6 +232,78 @@ int mesh_exact_predicates(const double* pts, const int32_t* ids, int64_t nq, int
  * The paper has no counterpart (its method has no learned part). */
 int mesh_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int32_t M, int32_t N, int32_t K);
 
+/* ---------------------------------------------------------------- learned proposals
+ * A small network proposes, for every point, its displacement over the next
+ * iterations of the plain method; plain iterations remain the fallback and
+ * judge every proposal by the quality they measure (Sec. 3.6 Eqs. 11-12 and
+ * the minimum angle).  The paper's method has no learned part; this is an
+ * addition of this library.
+ *
+ * Network: 48 BF16 inputs (37 features, zero-padded), two hidden layers of
+ * 64 ReLU units, 2 outputs (the proposed displacement divided by h_i);
+ * BF16 weights and activations, FP32 accumulation, all products on the
+ * tensor cores.  Parameters: a flat FP32 vector of TRIME_MLP_PARAMS values,
+ * W1 (64 x 48, row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (2 x 64), b3 (2).
+ * Features of point i, in order: the offsets (x_j - x_i, y_j - y_i) / h_i of
+ * its 16 nearest other points (by squared distance, ties by smaller index,
+ * nearest first); ln(h_i / h_avg) (Sec. 3.7); the gradient of the sizing field
+ * at p_i; 1 if p_i is a boundary point (Sec. 4.3); 1 if the next move is CVD;
+ * each rounded to float32 and then to BF16 (nearest, ties to even). */
+#define TRIME_MLP_IN 48
+#define TRIME_MLP_PARAMS 7426
+typedef struct mlp_s mlp_t;
+
+/* Create a model on the current device: parameters from a HOST array of
+ * TRIME_MLP_PARAMS floats, or (params == NULL) a seeded He initialisation
+ * with zero biases.  Work is ordered on cuda_stream.  Errors: TRIME_EINVAL
+ * (non-finite parameter), TRIME_ENOMEM, TRIME_ECUDA. */
+int mlp_create(mlp_t** out, const float* params, uint64_t seed, void* cuda_stream);
+void mlp_destroy(mlp_t* m);
+/* Copy the FP32 parameters to / from a HOST array of TRIME_MLP_PARAMS floats;
+ * setting them also resets the optimiser state. */
+int mlp_get_params(mlp_t* m, float* params);
+int mlp_set_params(mlp_t* m, const float* params);
+/* Y (n x 2 float32) = network(X) for X (n x 48 BF16 bit patterns), both host
+ * or both device arrays (detected).  Synchronous. */
+int mlp_forward(mlp_t* m, const uint16_t* X, int64_t n, float* Y);
+/* Loss L = sum over the n samples and 2 outputs of (Y - T)^2 / (2n) and its
+ * gradient with respect to the parameters (HOST array of TRIME_MLP_PARAMS
+ * floats, same layout), computed by the device's forward and backward
+ * kernels.  X, T host or device.  Synchronous. */
+int mlp_loss_grad(mlp_t* m, const uint16_t* X, const float* T, int64_t n, double* loss, float* grad);
+/* Adam (beta 0.9 / 0.999, eps 1e-8, step lr) over `epochs` shuffled passes of
+ * mini-batches of `batch` (>= 128) samples of the DEVICE arrays X (n x 48
+ * BF16) and T (n x 2 float32); *last_loss (may be NULL) = mean batch loss of
+ * the last epoch.  Synchronous. */
+int mlp_train(mlp_t* m, const uint16_t* X, const float* T, int64_t n, int32_t epochs, int32_t batch, double lr,
+              uint64_t seed, double* last_loss);
+
+/* Features of every point of m at its current positions, in input order:
+ * X (n x 48 BF16 bits) and, if h is not NULL, h_i (n float32); host or
+ * device arrays.  Synchronous. */
+int mesh_features(mesh_t* m, uint16_t* X, float* h);
+
+/* Training pairs from m's own trajectory: the features now into X (DEVICE,
+ * n x 48 BF16) and, after running `horizon` plain iterations (which advance
+ * m), the displacement of every point divided by its h_i into T (DEVICE,
+ * n x 2 float32), input order.  Synchronous. */
+int mesh_collect_pairs(mesh_t* m, int32_t horizon, uint16_t* X, float* T);
+
+/* Move every point to p_i + h_i * network(features_i), the move clamped to
+ * jump * fac_pt * h_i and treated as in Sec. 4.3 (no rebuild, no quality
+ * check).  Synchronous. */
+int mesh_propose(mesh_t* m, mlp_t* net, double jump);
+
+/* mesh_step with a proposal before every `every`-th iteration (every >= 1):
+ * the state is saved, the proposal applied and one plain iteration run from
+ * it; the proposal is kept if that iteration's quality is at least as good as
+ * the last one before it (1/2-mean of alpha not larger, minimum angle not
+ * smaller by more than min_angle_tol degrees), otherwise the saved state is
+ * restored.  *accepted / *rejected (may be NULL) count the proposals.
+ * Statistics and termination as mesh_step (stats may not be NULL). */
+int mesh_step_learned(mesh_t* m, mlp_t* net, int32_t n_iters, int32_t every, double jump, double min_angle_tol,
+                      mesh_stats* stats, int32_t* accepted, int32_t* rejected);
+
 /* ---------------------------------------------------------------- batches
  * Many independent meshes of uneven sizes stepped together: every stage of
  * an iteration is one kernel launch over all meshes (their points are

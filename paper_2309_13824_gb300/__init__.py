@@ -74,7 +74,12 @@ EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mes
            "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
            "mesh_batch_step", "mesh_batch_get_triangles", "mesh_batch_get_points", "mesh_batch_set_state",
            "mesh_batch_set_method_state", "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_batch_destroy",
-           "mesh_set_tuning", "mesh_batch_set_tuning", "mesh_tc_gemm_bf16"]
+           "mesh_set_tuning", "mesh_batch_set_tuning", "mesh_tc_gemm_bf16", "mlp_create", "mlp_destroy",
+           "mlp_get_params", "mlp_set_params", "mlp_forward", "mlp_loss_grad", "mlp_train", "mesh_features",
+           "mesh_collect_pairs", "mesh_propose", "mesh_step_learned"]
+
+MLP_IN = 48
+MLP_PARAMS = 7426
 
 _lib = None
 
@@ -127,6 +132,19 @@ def lib():
     L.mesh_batch_get_tuning.argtypes = [vp, P(mesh_tuning)]
     L.mesh_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
     L.mesh_tc_gemm_bf16.argtypes = [vp, vp, vp, C.c_int32, C.c_int32, C.c_int32]
+    L.mlp_create.argtypes = [P(vp), vp, C.c_uint64, vp]
+    L.mlp_destroy.argtypes = [vp]
+    L.mlp_destroy.restype = None
+    L.mlp_get_params.argtypes = [vp, vp]
+    L.mlp_set_params.argtypes = [vp, vp]
+    L.mlp_forward.argtypes = [vp, vp, C.c_int64, vp]
+    L.mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int64, P(C.c_double), vp]
+    L.mlp_train.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_uint64, P(C.c_double)]
+    L.mesh_features.argtypes = [vp, vp, vp]
+    L.mesh_collect_pairs.argtypes = [vp, C.c_int32, vp, vp]
+    L.mesh_propose.argtypes = [vp, vp, C.c_double]
+    L.mesh_step_learned.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, P(mesh_stats),
+                                    P(C.c_int32), P(C.c_int32)]
     L.mesh_batch_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
     L.mesh_batch_destroy.argtypes = [vp]
     L.mesh_batch_destroy.restype = None
@@ -136,7 +154,9 @@ def lib():
                  "mesh_batch_size", "mesh_batch_rebuild", "mesh_batch_step", "mesh_batch_get_triangles",
                  "mesh_batch_get_points", "mesh_batch_set_state", "mesh_batch_set_method_state",
                  "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_set_tuning", "mesh_batch_set_tuning",
-                 "mesh_tc_gemm_bf16"):
+                 "mesh_tc_gemm_bf16", "mlp_create", "mlp_get_params", "mlp_set_params", "mlp_forward",
+                 "mlp_loss_grad", "mlp_train", "mesh_features", "mesh_collect_pairs", "mesh_propose",
+                 "mesh_step_learned"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -320,6 +340,31 @@ class Mesh:
     def set_tuning(self, n_opt: float, lanes: int = 16):
         _check(lib().mesh_set_tuning(self._h, n_opt, lanes))
 
+    # ---- learned proposals
+    def features(self):
+        """(n, 48) BF16 feature bits (uint16) and h_i (float32), input order."""
+        X = np.zeros((self.n, MLP_IN), dtype=np.uint16)
+        h = np.zeros(self.n, dtype=np.float32)
+        _check(lib().mesh_features(self._h, X.ctypes.data_as(C.c_void_p), h.ctypes.data_as(C.c_void_p)))
+        return X, h
+
+    def collect_pairs(self, horizon: int, X, T):
+        """Features now into X (device (n, 48) int16/uint16 tensor) and the
+        displacement / h_i after `horizon` plain iterations into T (device (n, 2) float32)."""
+        _check(lib().mesh_collect_pairs(self._h, horizon, _ptr(X), _ptr(T)))
+
+    def propose(self, net: "MLP", jump: float = 4.0):
+        _check(lib().mesh_propose(self._h, net._h, jump))
+
+    def step_learned(self, net: "MLP", n_iters: int, every: int = 10, jump: float = 4.0, min_angle_tol: float = 1.0):
+        s = mesh_stats()
+        acc, rej = C.c_int32(), C.c_int32()
+        _check(lib().mesh_step_learned(self._h, net._h, n_iters, every, jump, min_angle_tol, C.byref(s),
+                                       C.byref(acc), C.byref(rej)))
+        d = _stats_dict(s)
+        d["accepted"], d["rejected"] = acc.value, rej.value
+        return d
+
     def debug(self, what: int):
         width = [2, 2, 2, 1, 1, 1, 1][what]
         out = np.zeros(width * self.n)
@@ -442,3 +487,64 @@ class MeshBatch:
 
     def set_method_state(self, mesh: int, switched, prev_a=0.0, prev_b=0.0, prev_amax=0.0):
         _check(lib().mesh_batch_set_method_state(self._h, mesh, switched, prev_a, prev_b, prev_amax))
+
+
+class MLP:
+    """The learned displacement model (a handle to mlp_t)."""
+
+    def __init__(self, params=None, seed: int = 0, stream=None):
+        h = C.c_void_p()
+        p = None
+        if params is not None:
+            p = np.ascontiguousarray(params, dtype=np.float32).reshape(MLP_PARAMS)
+        st = C.c_void_p(0 if stream is None else int(stream))
+        _check(lib().mlp_create(C.byref(h), None if p is None else p.ctypes.data_as(C.c_void_p), seed, st))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(lib().mlp_get_params(self._h, p.ctypes.data_as(C.c_void_p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32).reshape(MLP_PARAMS)
+        _check(lib().mlp_set_params(self._h, p.ctypes.data_as(C.c_void_p)))
+
+    def forward(self, X):
+        """Y (n, 2) for BF16 feature bits X (n, 48): numpy arrays, or device tensors (then Y is a device tensor)."""
+        if hasattr(X, "data_ptr"):
+            import torch
+
+            Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+            _check(lib().mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(Y)))
+            return Y
+        X = np.ascontiguousarray(X, dtype=np.uint16).reshape(-1, MLP_IN)
+        Y = np.zeros((len(X), 2), dtype=np.float32)
+        _check(lib().mlp_forward(self._h, X.ctypes.data_as(C.c_void_p), len(X), Y.ctypes.data_as(C.c_void_p)))
+        return Y
+
+    def loss_grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.uint16).reshape(-1, MLP_IN)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1, 2)
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = C.c_double()
+        _check(lib().mlp_loss_grad(self._h, X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p), len(X),
+                                   C.byref(loss), g.ctypes.data_as(C.c_void_p)))
+        return loss.value, g
+
+    def train(self, X, T, epochs: int = 1, batch: int = 8192, lr: float = 1e-3, seed: int = 0) -> float:
+        """Adam on device tensors X (n, 48) uint16/int16 and T (n, 2) float32; returns the last epoch's loss."""
+        loss = C.c_double()
+        _check(lib().mlp_train(self._h, _ptr(X), _ptr(T), X.shape[0], epochs, batch, lr, seed, C.byref(loss)))
+        return loss.value

@@ -119,6 +119,41 @@ void launch_bucket_raw(const double* x, const double* y, int32_t n, double x0, d
                        int32_t nbx, int32_t nby, int32_t* bstart, int32_t* sorted_idx, int32_t* scratch,
                        cudaStream_t st);
 
+// ------------------------------------------------------------------ learned model
+constexpr int kMlpFeat = 37;   // features in use
+constexpr int kMlpIn = 48;     // padded input width (a multiple of 16)
+constexpr int kMlpHid = 64;
+constexpr int kMlpOut = 2;
+constexpr int kMlpOutPad = 16;
+// flat FP32 parameter vector: W1 (64 x 48), b1, W2 (64 x 64), b2, W3 (2 x 64), b3
+constexpr int kOW1 = 0, kOB1 = kOW1 + kMlpHid * kMlpIn, kOW2 = kOB1 + kMlpHid, kOB2 = kOW2 + kMlpHid * kMlpHid,
+              kOW3 = kOB2 + kMlpHid, kOB3 = kOW3 + kMlpOut * kMlpHid, kMlpParams = kOB3 + kMlpOut;
+
+struct MlpDev {
+    const float* p;        // FP32 parameters
+    const uint16_t* w1;    // BF16 copies: W1 (64 x 48), W2 (64 x 64), W3 (16 x 64, rows >= 2 zero)
+    const uint16_t* w2;
+    const uint16_t* w3;
+};
+
+// Y[i] (2 floats) for the rows X[idx ? idx[i] : i] (48 BF16 each), i < n
+void launch_mlp_forward(const MlpDev& w, const uint16_t* X, const int32_t* idx, int n, float* Y, int* err,
+                        cudaStream_t st);
+// grad += d/dp of sum (Y - T)^2 * scale / 2 over the n rows; loss += that sum
+void launch_mlp_grad(const MlpDev& w, const uint16_t* X, const float* T, const int32_t* idx, int n, float scale,
+                     float* grad, double* loss, int* err, cudaStream_t st);
+// features of every slot of a single mesh (slot order, or by point id with
+// by_id), h_i per row, and optionally the positions by id
+template <typename T>
+void launch_features(const IterArgs<T>& a, uint16_t* X, float* H, T* px, T* py, int by_id, float method_cvd,
+                     cudaStream_t st);
+// moves cur <- srt + h_i * Y (slot order), clamped to jump * fac_pt * h_i, treated as Sec. 4.3
+template <typename T>
+void launch_propose(const IterArgs<T>& a, const float* Y, float jump, cudaStream_t st);
+// T[id] = (cur position - (px, py)[id]) / H[id]
+template <typename T>
+void launch_targets(const IterArgs<T>& a, const T* px, const T* py, const float* H, float* Tout, cudaStream_t st);
+
 // records the calling thread's error message (mesh_last_error) and returns code
 int set_error(int code, const char* msg);
 

@@ -62,6 +62,8 @@ struct TuneCand {
     double ms;
 };
 
+struct LearnBufs;
+
 struct mesh_s {
     int prec = 0;
     bool batched = false;
@@ -100,10 +102,27 @@ struct mesh_s {
     float* pS = nullptr;
     void* xybuf = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    LearnBufs* learn = nullptr;
     std::vector<void*> allocs;
 };
 
 struct mesh_batch_s : mesh_s {};
+
+// learned proposals: scratch and the saved state of a judged proposal
+struct LearnBufs {
+    uint16_t* X = nullptr;  // [n][48] features
+    float* Y = nullptr;     // [n][2] proposals
+    float* H = nullptr;     // [n] h_i
+    void *px = nullptr, *py = nullptr;                      // positions by id
+    void *bx = nullptr, *by = nullptr, *bdp = nullptr;      // saved cur state
+    int32_t* bid = nullptr;
+    uint8_t* bcls = nullptr;
+};
+
+namespace trime {
+MlpDev mlp_view(const mlp_s* m);
+int* mlp_err(mlp_s* m);
+}  // namespace trime
 
 template <typename T>
 static T* dalloc(mesh_s* m, size_t count, int& rc) {
@@ -748,6 +767,7 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
 // ------------------------------------------------------------------ operations shared by both handles
 static void destroy(mesh_s* m) {
     if (m->st) cudaStreamSynchronize(m->st);
+    delete m->learn;
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     for (void* p : m->allocs) cudaFree(p);
     if (m->hctrl) cudaFreeHost(m->hctrl);
@@ -979,6 +999,128 @@ static int set_tuning(mesh_s* m, double nopt, int32_t lanes) {
     return sync_out(m);
 }
 
+// ------------------------------------------------------------------ learned proposals (single mesh)
+static int ensure_learn(mesh_s* m) {
+    if (m->learn) return 0;
+    size_t N = (size_t)std::max<int64_t>(m->nslots, 1), T = m->prec == 0 ? sizeof(double) : sizeof(float);
+    LearnBufs* L = new LearnBufs();
+    int rc = 0;
+    L->X = dalloc<uint16_t>(m, N * kMlpIn, rc);
+    L->Y = dalloc<float>(m, 2 * N, rc);
+    L->H = dalloc<float>(m, N, rc);
+    L->px = dalloc<char>(m, N * T, rc);
+    L->py = dalloc<char>(m, N * T, rc);
+    L->bx = dalloc<char>(m, N * T, rc);
+    L->by = dalloc<char>(m, N * T, rc);
+    L->bdp = dalloc<char>(m, N * T, rc);
+    L->bid = dalloc<int32_t>(m, N, rc);
+    L->bcls = dalloc<uint8_t>(m, N, rc);
+    if (rc) {
+        delete L;
+        return rc;
+    }
+    m->learn = L;
+    return 0;
+}
+
+// the move of the next iteration is CVD
+static float next_is_cvd(const mesh_s* m) {
+    const DevCtrl& c = m->hctrl[0];
+    return (c.method_param == 1 || (c.method_param == 2 && c.switched)) ? 1.0f : 0.0f;
+}
+
+// sort cur into srt at the current positions (a1) and compute the features
+template <typename T>
+static void enqueue_features(mesh_s* m, uint16_t* X, float* H, void* px, void* py, int by_id, float mflag) {
+    IterArgs<T> a = make_args<T>(m, 1);
+    launch_bucket<T>(a, m->st);
+    launch_features<T>(a, X, H, (T*)px, (T*)py, by_id, mflag, m->st);
+}
+
+static void features_any(mesh_s* m, uint16_t* X, float* H, void* px, void* py, int by_id, float mflag) {
+    if (m->prec == 0) enqueue_features<double>(m, X, H, px, py, by_id, mflag);
+    else enqueue_features<float>(m, X, H, px, py, by_id, mflag);
+}
+
+static int check_net_err(mesh_s* m, mlp_s* net) {
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, mlp_err(net), sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    if (h) {
+        cudaMemsetAsync(mlp_err(net), 0, sizeof(int), m->st);
+        return fail(TRIME_ETIMEOUT, "tensor-core wait ran out");
+    }
+    return 0;
+}
+
+// features, network and proposed move on m's stream (the network's parameters
+// are read from the model's memory; its own stream is not used)
+static int enqueue_propose(mesh_s* m, mlp_s* net, double jump) {
+    LearnBufs* L = m->learn;
+    features_any(m, L->X, nullptr, nullptr, nullptr, 0, next_is_cvd(m));
+    launch_mlp_forward(mlp_view(net), L->X, nullptr, (int)m->nslots, L->Y, mlp_err(net), m->st);
+    if (m->prec == 0) launch_propose<double>(make_args<double>(m, 1), L->Y, (float)jump, m->st);
+    else launch_propose<float>(make_args<float>(m, 1), L->Y, (float)jump, m->st);
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+static int copy_state(mesh_s* m, bool save) {
+    LearnBufs* L = m->learn;
+    size_t N = (size_t)m->nslots, T = m->prec == 0 ? sizeof(double) : sizeof(float);
+    auto cp = [&](void* cur, void* bak, size_t bytes) {
+        return cudaMemcpyAsync(save ? bak : cur, save ? cur : bak, bytes, cudaMemcpyDeviceToDevice, m->st);
+    };
+    CUDA_TRY(cp(m->cx, L->bx, N * T));
+    CUDA_TRY(cp(m->cy, L->by, N * T));
+    CUDA_TRY(cp(m->cdp, L->bdp, N * T));
+    CUDA_TRY(cp(m->cid, L->bid, N * sizeof(int32_t)));
+    CUDA_TRY(cp(m->ccls, L->bcls, N));
+    return 0;
+}
+
+static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every, double jump, double tol,
+                           mesh_stats* stats, int32_t* accepted, int32_t* rejected) {
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if ((rc = ensure_learn(m)) || (rc = reset_counters(m)) || (rc = read_ctrl(m))) return rc;
+    int start = m->hctrl[0].iterations, acc = 0, rej = 0;
+    for (int32_t k = 0; k < n_iters && !m->hctrl[0].terminated; k++) {
+        if (k > 0 && k % every == 0 && m->nslots > 0) {
+            if ((rc = read_ctrl(m))) return rc;
+            if (m->hctrl[0].terminated) break;
+            DevCtrl before = m->hctrl[0];
+            if ((rc = copy_state(m, true)) || (rc = enqueue_propose(m, net, jump))) return rc;
+            CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+            if ((rc = check_net_err(m, net)) || (rc = read_ctrl(m))) return rc;
+            const DevCtrl& after = m->hctrl[0];
+            bool ok = after.n_tri > 0 && after.half_a <= before.half_a && after.min_ang >= before.min_ang - tol;
+            if (ok) {
+                acc++;
+            } else {
+                rej++;
+                if ((rc = copy_state(m, false))) return rc;
+                DevCtrl c = before;
+                c.iterations = after.iterations;
+                c.cnt = after.cnt;
+                c.terminated = 0;
+                *m->hctrl = c;
+                CUDA_TRY(cudaMemcpyAsync(m->ctrl, m->hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
+                CUDA_TRY(cudaStreamSynchronize(m->st));
+            }
+            continue;
+        }
+        CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+        if ((k & 31) == 31 && (rc = read_ctrl(m))) return rc;
+    }
+    if ((rc = read_ctrl(m)) || (rc = sync_out(m))) return rc;
+    fill_stats(m, 0, m->hctrl[0].iterations - start, stats);
+    if (accepted) *accepted = acc;
+    if (rejected) *rejected = rej;
+    if (guard_tripped(m)) return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
+    return TRIME_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -1091,6 +1233,59 @@ int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms) {
 int mesh_set_tuning(mesh_t* m, double n_opt, int32_t lanes) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
     return set_tuning(m, n_opt, lanes);
+}
+
+int mesh_features(mesh_t* m, uint16_t* X, float* h) {
+    if (!m || !X) return fail(TRIME_EINVAL, "NULL argument");
+    if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    if (m->nslots == 0) return TRIME_OK;
+    int rc = sync_in(m);
+    if (rc || (rc = ensure_learn(m)) || (rc = read_ctrl(m))) return rc;
+    size_t N = (size_t)m->nslots;
+    bool dx = is_device_ptr(X), dh = h && is_device_ptr(h);
+    features_any(m, dx ? X : m->learn->X, h ? (dh ? h : m->learn->H) : nullptr, nullptr, nullptr, 1, next_is_cvd(m));
+    CUDA_TRY(cudaGetLastError());
+    if (!dx) CUDA_TRY(cudaMemcpyAsync(X, m->learn->X, N * kMlpIn * 2, cudaMemcpyDeviceToHost, m->st));
+    if (h && !dh) CUDA_TRY(cudaMemcpyAsync(h, m->learn->H, N * sizeof(float), cudaMemcpyDeviceToHost, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
+int mesh_collect_pairs(mesh_t* m, int32_t horizon, uint16_t* X, float* T) {
+    if (!m || !X || !T || horizon < 1) return fail(TRIME_EINVAL, "bad argument");
+    if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    if (!is_device_ptr(X) || !is_device_ptr(T)) return fail(TRIME_EINVAL, "X and T must be device arrays");
+    if (m->nslots == 0) return TRIME_OK;
+    int rc = sync_in(m);
+    if (rc || (rc = ensure_learn(m)) || (rc = read_ctrl(m))) return rc;
+    LearnBufs* L = m->learn;
+    features_any(m, X, L->H, L->px, L->py, 1, next_is_cvd(m));
+    for (int32_t k = 0; k < horizon; k++) CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+    if (m->prec == 0)
+        launch_targets<double>(make_args<double>(m, 1), (const double*)L->px, (const double*)L->py, L->H, T, m->st);
+    else
+        launch_targets<float>(make_args<float>(m, 1), (const float*)L->px, (const float*)L->py, L->H, T, m->st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
+int mesh_propose(mesh_t* m, mlp_t* net, double jump) {
+    if (!m || !net || !(jump > 0)) return fail(TRIME_EINVAL, "bad argument");
+    if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    if (m->nslots == 0) return TRIME_OK;
+    int rc = sync_in(m);
+    if (rc || (rc = ensure_learn(m)) || (rc = read_ctrl(m)) || (rc = enqueue_propose(m, net, jump))) return rc;
+    if ((rc = check_net_err(m, net))) return rc;
+    return sync_out(m);
+}
+
+int mesh_step_learned(mesh_t* m, mlp_t* net, int32_t n_iters, int32_t every, double jump, double min_angle_tol,
+                      mesh_stats* stats, int32_t* accepted, int32_t* rejected) {
+    if (!m || !net || !stats || n_iters < 0 || every < 1 || !(jump > 0) || !(min_angle_tol >= 0))
+        return fail(TRIME_EINVAL, "bad argument");
+    if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    return do_step_learned(m, net, n_iters, every, jump, min_angle_tol, stats, accepted, rejected);
 }
 
 // ------------------------------------------------------------------ batches

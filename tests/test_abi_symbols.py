@@ -11,7 +11,7 @@ HDR = os.path.join(os.path.dirname(HERE), "include", "trime.h")
 def declared_functions():
     src = open(HDR).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(mesh_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*((?:mesh|mlp)_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_library_exports_header_symbols():

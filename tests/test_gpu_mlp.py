@@ -30,3 +30,76 @@ def test_tensor_core_tile(M, N, K):
     exact = a @ b.T
     scale = np.abs(a) @ np.abs(b).T
     assert np.all(np.abs(D - exact) <= 2e-6 * scale + 1e-30), np.max(np.abs(D - exact) / scale)
+
+
+def _features_like(n, seed):
+    """Random inputs shaped like the features (37 used columns, zero padding)."""
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, 48))
+    X[:, :32] = rng.standard_normal((n, 32)) * 1.5
+    X[:, 32] = rng.uniform(-2, 2, n)
+    X[:, 33:35] = rng.standard_normal((n, 2)) * 0.05
+    X[:, 35] = rng.integers(0, 2, n)
+    X[:, 36] = rng.integers(0, 2, n)
+    return X
+
+
+def _device_params(seed):
+    from oracle import mlp as M
+
+    P = M.Params.random(seed)
+    p32 = P.flat().astype(np.float32)
+    return M.Params.from_flat(p32.astype(np.float64)), p32
+
+
+def test_forward_matches_oracle():
+    import paper_2309_13824_gb300 as g
+    from oracle import mlp as M
+
+    P, p32 = _device_params(5)
+    net = g.MLP(p32)
+    assert np.array_equal(net.params(), p32)
+    X = _features_like(1000, 1)
+    Y = net.forward(g.bf16_bits(X)).astype(np.float64)
+    Yo, (_, _, _, W3, _, _, _, H2) = M.forward(P, X, quantize=True)
+    # scale of each output: the magnitudes its last sum is made of
+    scale = np.abs(H2) @ np.abs(W3).T + np.abs(P.b3)
+    err = np.abs(Y - Yo) / scale
+    # FP32 sums vs exact ones, and rare one-ulp BF16 rounding flips of a hidden unit
+    assert np.quantile(err, 0.99) < 1e-5, np.quantile(err, 0.99)
+    assert err.max() < 2e-2, err.max()
+
+
+def test_gradients_match_oracle():
+    import paper_2309_13824_gb300 as g
+    from oracle import mlp as M
+
+    P, p32 = _device_params(7)
+    net = g.MLP(p32)
+    X = _features_like(700, 2)
+    T = np.random.default_rng(3).standard_normal((700, 2)) * 0.5
+    loss, grad = net.loss_grad(g.bf16_bits(X), T.astype(np.float32))
+    Lo, Go = M.loss_and_grads(P, X, T.astype(np.float32).astype(np.float64), quantize=True)
+    assert loss == pytest.approx(Lo, rel=1e-4)
+    go = Go.flat()
+    for name, a, b in (("W1", 0, 3072), ("b1", 3072, 3136), ("W2", 3136, 7232), ("b2", 7232, 7296),
+                       ("W3", 7296, 7424), ("b3", 7424, 7426)):
+        d = np.linalg.norm(grad[a:b] - go[a:b]) / np.linalg.norm(go[a:b])
+        assert d < 1e-2, (name, d)
+
+
+def test_training_reduces_loss():
+    import torch
+
+    import paper_2309_13824_gb300 as g
+
+    # a smooth target of the inputs: the network must fit it on the device
+    X = _features_like(20000, 4)
+    T = np.stack([np.tanh(X[:, 0] - 0.5 * X[:, 3]), 0.3 * X[:, 1] * X[:, 2]], 1) * 0.5
+    Xd = torch.from_numpy(g.bf16_bits(X).view(np.int16)).cuda()
+    Td = torch.from_numpy(T.astype(np.float32)).cuda()
+    net = g.MLP(seed=1)
+    l0, _ = net.loss_grad(g.bf16_bits(X), T.astype(np.float32))
+    l1 = net.train(Xd, Td, epochs=30, batch=1024, lr=2e-3)
+    l2, _ = net.loss_grad(g.bf16_bits(X), T.astype(np.float32))
+    assert l2 < 0.1 * l0, (l0, l1, l2)
