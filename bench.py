@@ -288,6 +288,47 @@ def sweep_leg(g, torch, stream, steps, flush):
     return out
 
 
+def learned_leg(g, stream):
+    """The learned displacement model: trained on the device on trajectories of
+    the disk (DistMesh, 1e4 points) and the benchmark annulus (hybrid, 1e6),
+    then the wall time of the hybrid method with and without its proposals to
+    the plain method's converged minimum angle minus 1 degree."""
+    import workloads as W
+    from paper_2309_13824_gb300 import learn
+
+    disk = W.disk_workload(n=10000)
+    ann = W.annulus_workload(n=1_000_000)
+    st = stream.cuda_stream
+    t0 = time.perf_counter()
+    net, loss, npairs = learn.train([(disk.sdf, disk.sizing, disk.points, 0, 0),
+                                     (ann.sdf, ann.sizing, ann.points, 2, 0)], stream=st)
+    out = {"training": {"pairs": npairs, "last_epoch_loss": loss, "seconds": time.perf_counter() - t0,
+                        "trajectories": "disk 1e4 DistMesh FP64 (seed 0) + annulus 1e6 hybrid FP64 (seed 1), "
+                                        "pairs every 11 iterations, horizon 10, 40+10 epochs Adam"},
+           "policy": {"every": 10, "jump": 10.0, "min_angle_tol": 1.0, "max_proposals": 5}}
+    star = W.star_workload(1_000_000, sdf_n=2048, siz_n=512, workers=min(16, os.cpu_count() or 1))
+    for name, wl, prec in (("annulus_1e6_fp64", ann, 0), ("star500_1e6_fp32", star, 1)):
+        pts = wl.points if prec == 0 else W.to_fp32_positions(wl.points)
+        tc, conv = learn.time_to_quality(wl.sdf, wl.sizing, pts, precision=prec, stream=st)
+        q = conv["min_angle_deg"] - 1.0
+        tp, sp = learn.time_to_quality(wl.sdf, wl.sizing, pts, precision=prec, target=q, stream=st)
+        tl, sl = learn.time_to_quality(wl.sdf, wl.sizing, pts, net=net, precision=prec, target=q, stream=st)
+
+        def rec(t, s):
+            return {"seconds": t, "iterations": s["iterations"], "target_reached": bool(s["target_reached"]),
+                    "min_angle_deg": s["min_angle_deg"], "half_mean_alpha": s["half_mean_alpha"],
+                    "max_alpha": s["max_alpha"], "mean_size_dev": s["mean_size_dev"]}
+
+        lr = rec(tl, sl)
+        lr.update({"proposals_kept": sl["accepted"], "proposals_undone": sl["rejected"]})
+        tlc, slc = learn.time_to_quality(wl.sdf, wl.sizing, pts, net=net, precision=prec, stream=st)
+        lc = rec(tlc, slc)
+        lc.update({"proposals_kept": slc["accepted"], "proposals_undone": slc["rejected"]})
+        out[name] = {"plain_converged": rec(tc, conv), "learned_converged": lc, "target_min_angle_deg": q,
+                     "plain_to_target": rec(tp, sp), "learned_to_target": lr}
+    return out
+
+
 def run_reference(args, wl):
     world, rank, local = dist_env()
     if rank != 0:
@@ -450,6 +491,7 @@ def main():
                                         "ms_per_step": ms32 / args.steps}
             fm.close()
         extras["batched"] = batched_leg(g, torch, stream, args.steps, flush)
+        extras["learned"] = learned_leg(g, stream)
         if args.sweep:
             extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
         cnt, dt = oracle_sample_rate(wl, 10.0)

@@ -94,7 +94,7 @@ typedef struct {
     int64_t quad_cap;          /* centroids that hit quad_max_level                       */
     int64_t dup_points;        /* points whose cell is empty (exact duplicate, SoS)       */
     int32_t small_moves;       /* every inner point moved less than fac_end*h_i           */
-    int32_t reserved1;
+    int32_t target_reached;    /* stopped at the quality target (mesh_set_quality_target) */
     /* Voronoi work of the last call, counted only with mesh_params.debug = 1: */
     int64_t vor_candidates;    /* candidate points loaded within the security radius      */
     int64_t vor_picks;         /* candidates applied to a cell                            */
@@ -203,6 +203,15 @@ int mesh_bucket_points_noalloc(const double* x, const double* y, int64_t n, doub
  * iteration.  Semantics otherwise as mesh_step.  Synchronises. */
 int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms);
 
+/* Stop the iterations as soon as the minimum angle of a rebuild reaches
+ * min_angle_deg (checked on the device after every rebuild).  While a target
+ * is set it replaces the quality termination test of Sec. 4 (the relative
+ * changes of the 1/2-means); the small-movement test stays.  0 removes the
+ * target.  Setting a target the mesh has not reached clears a previous
+ * termination.  Used to measure the wall time to a given quality.
+ * Synchronises. */
+int mesh_set_quality_target(mesh_t* m, double min_angle_deg);
+
 /* Tiling of the iteration: size the bucket grid for n_opt points per bucket
  * (> 0; the default is mesh_params.N_opt) and clip each Voronoi cell with
  * `lanes` = 16 (two cells per warp, cells needing more than 16 edges redone
@@ -239,7 +248,7 @@ int mesh_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int32_t M,
  * the minimum angle).  The paper's method has no learned part; this is an
  * addition of this library.
  *
- * Network: 48 BF16 inputs (37 features, zero-padded), two hidden layers of
+ * Network: 48 BF16 inputs (39 features, zero-padded), two hidden layers of
  * 64 ReLU units, 2 outputs (the proposed displacement divided by h_i);
  * BF16 weights and activations, FP32 accumulation, all products on the
  * tensor cores.  Parameters: a flat FP32 vector of TRIME_MLP_PARAMS values,
@@ -248,7 +257,10 @@ int mesh_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int32_t M,
  * its 16 nearest other points (by squared distance, ties by smaller index,
  * nearest first); ln(h_i / h_avg) (Sec. 3.7); the gradient of the sizing field
  * at p_i; 1 if p_i is a boundary point (Sec. 4.3); 1 if the next move is CVD;
- * each rounded to float32 and then to BF16 (nearest, ties to even). */
+ * the point's last move divided by h_i (zero when unknown: the positions
+ * before the last iteration are recorded by mesh_step_learned and
+ * mesh_collect_pairs, not by mesh_step); each rounded to float32 and then to
+ * BF16 (nearest, ties to even). */
 #define TRIME_MLP_IN 48
 #define TRIME_MLP_PARAMS 7426
 typedef struct mlp_s mlp_t;
@@ -283,10 +295,11 @@ int mlp_train(mlp_t* m, const uint16_t* X, const float* T, int64_t n, int32_t ep
  * device arrays.  Synchronous. */
 int mesh_features(mesh_t* m, uint16_t* X, float* h);
 
-/* Training pairs from m's own trajectory: the features now into X (DEVICE,
- * n x 48 BF16) and, after running `horizon` plain iterations (which advance
- * m), the displacement of every point divided by its h_i into T (DEVICE,
- * n x 2 float32), input order.  Synchronous. */
+/* Training pairs from m's own trajectory: one plain iteration, then the
+ * features (with that iteration's move) into X (DEVICE, n x 48 BF16) and,
+ * after `horizon` more plain iterations, the displacement of every point over
+ * them divided by its h_i into T (DEVICE, n x 2 float32), input order.
+ * Advances m by horizon + 1 iterations.  Synchronous. */
 int mesh_collect_pairs(mesh_t* m, int32_t horizon, uint16_t* X, float* T);
 
 /* Move every point to p_i + h_i * network(features_i), the move clamped to
@@ -299,10 +312,12 @@ int mesh_propose(mesh_t* m, mlp_t* net, double jump);
  * it; the proposal is kept if that iteration's quality is at least as good as
  * the last one before it (1/2-mean of alpha not larger, minimum angle not
  * smaller by more than min_angle_tol degrees), otherwise the saved state is
- * restored.  *accepted / *rejected (may be NULL) count the proposals.
- * Statistics and termination as mesh_step (stats may not be NULL). */
+ * restored.  At most max_proposals proposals are made (<= 0: no limit);
+ * the iterations after the last one are plain.  *accepted / *rejected (may be
+ * NULL) count the proposals.  Statistics and termination as mesh_step (stats
+ * may not be NULL). */
 int mesh_step_learned(mesh_t* m, mlp_t* net, int32_t n_iters, int32_t every, double jump, double min_angle_tol,
-                      mesh_stats* stats, int32_t* accepted, int32_t* rejected);
+                      int32_t max_proposals, mesh_stats* stats, int32_t* accepted, int32_t* rejected);
 
 /* ---------------------------------------------------------------- batches
  * Many independent meshes of uneven sizes stepped together: every stage of
@@ -365,6 +380,9 @@ int mesh_batch_set_method_state(mesh_batch_t* b, int32_t mesh, int32_t switched,
 
 /* mesh_profile_step for the whole batch. */
 int mesh_batch_profile_step(mesh_batch_t* b, int32_t n_iters, double* stage_ms);
+
+/* mesh_set_quality_target for one mesh of the batch, or all of them (mesh = -1). */
+int mesh_batch_set_quality_target(mesh_batch_t* b, int32_t mesh, double min_angle_deg);
 
 /* mesh_set_tuning for the whole batch (e.g. to reuse an earlier autotuning
  * result without timing again). */

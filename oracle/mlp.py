@@ -4,13 +4,14 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU legs use this module.
 The paper's method has no learned part; this is the plain definition the GPU
 kernels are checked against:
 
-* features of a point i (37 values, zero-padded to 48): the offsets of its 16
+* features of a point i (39 values, zero-padded to 48): the offsets of its 16
   nearest other points (by squared FP64 distance, ties by smaller index,
   nearest first) divided by h_i, the geometry-cell size of its cell (Sec. 3.7);
   ln(h_i / h_avg); the gradient of the sizing field mu at p_i (derivative of
   the bilinear interpolant, Sec. 3.3 grid); 1 if the point is a boundary point;
-  1 if the current move is CVD.  Each feature is rounded to float32 and then to
-  BF16 (round to nearest, ties to even);
+  1 if the current move is CVD; its last move divided by h_i (zero when not
+  known).  Each feature is rounded to float32 and then to BF16 (round to
+  nearest, ties to even);
 * the network: Z1 = X W1^T + b1, H1 = relu(Z1), Z2 = H1 W2^T + b2,
   H2 = relu(Z2), Y = H2 W3^T + b3 (64 hidden units, 2 outputs: the proposed
   displacement divided by h_i);
@@ -28,7 +29,7 @@ from __future__ import annotations
 
 import numpy as np
 
-N_FEAT = 37
+N_FEAT = 39
 K_IN = 48
 HID = 64
 N_OUT = 2
@@ -82,8 +83,9 @@ def sizing_gradient(grid, x: float, y: float):
     return gx, gy
 
 
-def features(points, h, havg, sizing, is_boundary, method_cvd: int) -> np.ndarray:
-    """(n, 48) features (unrounded FP64; the network reads bf16_round of them)."""
+def features(points, h, havg, sizing, is_boundary, method_cvd: int, previous=None) -> np.ndarray:
+    """(n, 48) features (unrounded FP64; the network reads bf16_round of them);
+    `previous` are the positions before the last iteration (or None)."""
     p = np.asarray(points, dtype=np.float64)
     n = len(p)
     nb = knn(p)
@@ -101,6 +103,9 @@ def features(points, h, havg, sizing, is_boundary, method_cvd: int) -> np.ndarra
         X[i, 34] = np.float32(gy)
         X[i, 35] = 1.0 if is_boundary[i] else 0.0
         X[i, 36] = float(method_cvd)
+        if previous is not None:
+            X[i, 37] = np.float32((p[i, 0] - previous[i, 0]) / h[i])
+            X[i, 38] = np.float32((p[i, 1] - previous[i, 1]) / h[i])
     return X
 
 

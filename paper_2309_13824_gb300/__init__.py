@@ -57,7 +57,7 @@ class mesh_stats(C.Structure):
                 ("fac_mu", C.c_double), ("exact_calls", C.c_int64), ("clip_inconsistent", C.c_int64),
                 ("ring_overflow", C.c_int64), ("exact_overflow", C.c_int64), ("newton_fail", C.c_int64),
                 ("trace_cap", C.c_int64), ("quad_cap", C.c_int64), ("dup_points", C.c_int64),
-                ("small_moves", C.c_int32), ("reserved1", C.c_int32), ("vor_candidates", C.c_int64),
+                ("small_moves", C.c_int32), ("target_reached", C.c_int32), ("vor_candidates", C.c_int64),
                 ("vor_picks", C.c_int64), ("vor_cuts", C.c_int64), ("vor_rings", C.c_int64), ("vor_wide", C.c_int64)]
 
 
@@ -76,7 +76,8 @@ EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mes
            "mesh_batch_set_method_state", "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_batch_destroy",
            "mesh_set_tuning", "mesh_batch_set_tuning", "mesh_tc_gemm_bf16", "mlp_create", "mlp_destroy",
            "mlp_get_params", "mlp_set_params", "mlp_forward", "mlp_loss_grad", "mlp_train", "mesh_features",
-           "mesh_collect_pairs", "mesh_propose", "mesh_step_learned"]
+           "mesh_collect_pairs", "mesh_propose", "mesh_step_learned", "mesh_set_quality_target",
+           "mesh_batch_set_quality_target"]
 
 MLP_IN = 48
 MLP_PARAMS = 7426
@@ -141,10 +142,12 @@ def lib():
     L.mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int64, P(C.c_double), vp]
     L.mlp_train.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_uint64, P(C.c_double)]
     L.mesh_features.argtypes = [vp, vp, vp]
+    L.mesh_set_quality_target.argtypes = [vp, C.c_double]
+    L.mesh_batch_set_quality_target.argtypes = [vp, C.c_int32, C.c_double]
     L.mesh_collect_pairs.argtypes = [vp, C.c_int32, vp, vp]
     L.mesh_propose.argtypes = [vp, vp, C.c_double]
-    L.mesh_step_learned.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, P(mesh_stats),
-                                    P(C.c_int32), P(C.c_int32)]
+    L.mesh_step_learned.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32,
+                                    P(mesh_stats), P(C.c_int32), P(C.c_int32)]
     L.mesh_batch_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
     L.mesh_batch_destroy.argtypes = [vp]
     L.mesh_batch_destroy.restype = None
@@ -156,7 +159,7 @@ def lib():
                  "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_set_tuning", "mesh_batch_set_tuning",
                  "mesh_tc_gemm_bf16", "mlp_create", "mlp_get_params", "mlp_set_params", "mlp_forward",
                  "mlp_loss_grad", "mlp_train", "mesh_features", "mesh_collect_pairs", "mesh_propose",
-                 "mesh_step_learned"):
+                 "mesh_step_learned", "mesh_set_quality_target", "mesh_batch_set_quality_target"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -340,6 +343,9 @@ class Mesh:
     def set_tuning(self, n_opt: float, lanes: int = 16):
         _check(lib().mesh_set_tuning(self._h, n_opt, lanes))
 
+    def set_quality_target(self, min_angle_deg: float):
+        _check(lib().mesh_set_quality_target(self._h, min_angle_deg))
+
     # ---- learned proposals
     def features(self):
         """(n, 48) BF16 feature bits (uint16) and h_i (float32), input order."""
@@ -349,18 +355,20 @@ class Mesh:
         return X, h
 
     def collect_pairs(self, horizon: int, X, T):
-        """Features now into X (device (n, 48) int16/uint16 tensor) and the
-        displacement / h_i after `horizon` plain iterations into T (device (n, 2) float32)."""
+        """One plain iteration, then the features into X (device (n, 48)
+        int16/uint16 tensor) and the displacement / h_i over `horizon` more
+        plain iterations into T (device (n, 2) float32)."""
         _check(lib().mesh_collect_pairs(self._h, horizon, _ptr(X), _ptr(T)))
 
     def propose(self, net: "MLP", jump: float = 4.0):
         _check(lib().mesh_propose(self._h, net._h, jump))
 
-    def step_learned(self, net: "MLP", n_iters: int, every: int = 10, jump: float = 4.0, min_angle_tol: float = 1.0):
+    def step_learned(self, net: "MLP", n_iters: int, every: int = 10, jump: float = 10.0, min_angle_tol: float = 1.0,
+                     max_proposals: int = 5):
         s = mesh_stats()
         acc, rej = C.c_int32(), C.c_int32()
-        _check(lib().mesh_step_learned(self._h, net._h, n_iters, every, jump, min_angle_tol, C.byref(s),
-                                       C.byref(acc), C.byref(rej)))
+        _check(lib().mesh_step_learned(self._h, net._h, n_iters, every, jump, min_angle_tol, max_proposals,
+                                       C.byref(s), C.byref(acc), C.byref(rej)))
         d = _stats_dict(s)
         d["accepted"], d["rejected"] = acc.value, rej.value
         return d
@@ -448,6 +456,9 @@ class MeshBatch:
 
     def set_tuning(self, n_opt: float, lanes: int = 16):
         _check(lib().mesh_batch_set_tuning(self._h, n_opt, lanes))
+
+    def set_quality_target(self, min_angle_deg: float, mesh: int = -1):
+        _check(lib().mesh_batch_set_quality_target(self._h, mesh, min_angle_deg))
 
     def tuning(self) -> dict:
         t = mesh_tuning()

@@ -64,6 +64,9 @@ struct DevCtrl {
     int32_t pad0;
     double prev_a, prev_b, prev_amax;
     double fac_mu;
+    double target_min_ang;  // > 0: stop once the minimum angle reaches it
+    int32_t target_reached;
+    int32_t pad1;
     double n_tri, n_edges, half_a, half_b, max_a, max_b, min_ang, size_dev;
     DevCounters cnt;
 };

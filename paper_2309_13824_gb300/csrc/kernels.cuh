@@ -120,7 +120,7 @@ void launch_bucket_raw(const double* x, const double* y, int32_t n, double x0, d
                        cudaStream_t st);
 
 // ------------------------------------------------------------------ learned model
-constexpr int kMlpFeat = 37;   // features in use
+constexpr int kMlpFeat = 39;   // features in use
 constexpr int kMlpIn = 48;     // padded input width (a multiple of 16)
 constexpr int kMlpHid = 64;
 constexpr int kMlpOut = 2;
@@ -143,10 +143,14 @@ void launch_mlp_forward(const MlpDev& w, const uint16_t* X, const int32_t* idx, 
 void launch_mlp_grad(const MlpDev& w, const uint16_t* X, const float* T, const int32_t* idx, int n, float scale,
                      float* grad, double* loss, int* err, cudaStream_t st);
 // features of every slot of a single mesh (slot order, or by point id with
-// by_id), h_i per row, and optionally the positions by id
+// by_id), h_i per row, optionally the positions by id; the last move is the
+// position minus (qx, qy)[id] (zero without them)
 template <typename T>
-void launch_features(const IterArgs<T>& a, uint16_t* X, float* H, T* px, T* py, int by_id, float method_cvd,
-                     cudaStream_t st);
+void launch_features(const IterArgs<T>& a, uint16_t* X, float* H, T* px, T* py, const T* qx, const T* qy, int by_id,
+                     float method_cvd, cudaStream_t st);
+// (qx, qy)[id] = the current positions (cur)
+template <typename T>
+void launch_snapshot(const IterArgs<T>& a, T* qx, T* qy, cudaStream_t st);
 // moves cur <- srt + h_i * Y (slot order), clamped to jump * fac_pt * h_i, treated as Sec. 4.3
 template <typename T>
 void launch_propose(const IterArgs<T>& a, const float* Y, float jump, cudaStream_t st);

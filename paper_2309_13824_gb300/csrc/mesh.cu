@@ -114,6 +114,8 @@ struct LearnBufs {
     float* Y = nullptr;     // [n][2] proposals
     float* H = nullptr;     // [n] h_i
     void *px = nullptr, *py = nullptr;                      // positions by id
+    void *qx = nullptr, *qy = nullptr;                      // positions by id before the last iteration
+    bool have_q = false;
     void *bx = nullptr, *by = nullptr, *bdp = nullptr;      // saved cur state
     int32_t* bid = nullptr;
     uint8_t* bcls = nullptr;
@@ -442,6 +444,7 @@ static void fill_stats(const mesh_s* m, int k, int iters, mesh_stats* s) {
     s->quad_cap = (int64_t)c.cnt.quad_cap;
     s->dup_points = (int64_t)c.cnt.dup_points;
     s->small_moves = c.small_moves;
+    s->target_reached = c.target_reached;
     s->vor_candidates = (int64_t)c.cnt.vor_candidates;
     s->vor_picks = (int64_t)c.cnt.vor_picks;
     s->vor_cuts = (int64_t)c.cnt.vor_cuts;
@@ -792,6 +795,7 @@ static int do_rebuild(mesh_s* m, mesh_stats* stats) {
 
 static int do_step(mesh_s* m, int32_t n_iters, mesh_stats* stats) {
     if (n_iters < 0) return fail(TRIME_EINVAL, "n_iters < 0");
+    if (m->learn && n_iters > 0) m->learn->have_q = false;  // the features' last move is no longer known
     int rc = sync_in(m);
     if (rc) return rc;
     if ((rc = reset_counters(m))) return rc;
@@ -1010,6 +1014,8 @@ static int ensure_learn(mesh_s* m) {
     L->H = dalloc<float>(m, N, rc);
     L->px = dalloc<char>(m, N * T, rc);
     L->py = dalloc<char>(m, N * T, rc);
+    L->qx = dalloc<char>(m, N * T, rc);
+    L->qy = dalloc<char>(m, N * T, rc);
     L->bx = dalloc<char>(m, N * T, rc);
     L->by = dalloc<char>(m, N * T, rc);
     L->bdp = dalloc<char>(m, N * T, rc);
@@ -1029,12 +1035,23 @@ static float next_is_cvd(const mesh_s* m) {
     return (c.method_param == 1 || (c.method_param == 2 && c.switched)) ? 1.0f : 0.0f;
 }
 
-// sort cur into srt at the current positions (a1) and compute the features
+// sort cur into srt at the current positions (a1) and compute the features;
+// the last move is measured from the snapshot taken before the last iteration
 template <typename T>
 static void enqueue_features(mesh_s* m, uint16_t* X, float* H, void* px, void* py, int by_id, float mflag) {
     IterArgs<T> a = make_args<T>(m, 1);
+    LearnBufs* L = m->learn;
     launch_bucket<T>(a, m->st);
-    launch_features<T>(a, X, H, (T*)px, (T*)py, by_id, mflag, m->st);
+    launch_features<T>(a, X, H, (T*)px, (T*)py, L->have_q ? (const T*)L->qx : nullptr,
+                       L->have_q ? (const T*)L->qy : nullptr, by_id, mflag, m->st);
+}
+
+// remember the positions before the next iteration (the features' last move)
+static void snapshot(mesh_s* m) {
+    LearnBufs* L = m->learn;
+    if (m->prec == 0) launch_snapshot<double>(make_args<double>(m, 1), (double*)L->qx, (double*)L->qy, m->st);
+    else launch_snapshot<float>(make_args<float>(m, 1), (float*)L->qx, (float*)L->qy, m->st);
+    L->have_q = true;
 }
 
 static void features_any(mesh_s* m, uint16_t* X, float* H, void* px, void* py, int by_id, float mflag) {
@@ -1080,17 +1097,18 @@ static int copy_state(mesh_s* m, bool save) {
 }
 
 static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every, double jump, double tol,
-                           mesh_stats* stats, int32_t* accepted, int32_t* rejected) {
+                           int32_t max_props, mesh_stats* stats, int32_t* accepted, int32_t* rejected) {
     int rc = sync_in(m);
     if (rc) return rc;
     if ((rc = ensure_learn(m)) || (rc = reset_counters(m)) || (rc = read_ctrl(m))) return rc;
     int start = m->hctrl[0].iterations, acc = 0, rej = 0;
     for (int32_t k = 0; k < n_iters && !m->hctrl[0].terminated; k++) {
-        if (k > 0 && k % every == 0 && m->nslots > 0) {
+        if (k > 0 && k % every == 0 && m->nslots > 0 && (max_props <= 0 || acc + rej < max_props)) {
             if ((rc = read_ctrl(m))) return rc;
             if (m->hctrl[0].terminated) break;
             DevCtrl before = m->hctrl[0];
             if ((rc = copy_state(m, true)) || (rc = enqueue_propose(m, net, jump))) return rc;
+            snapshot(m);
             CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
             if ((rc = check_net_err(m, net)) || (rc = read_ctrl(m))) return rc;
             const DevCtrl& after = m->hctrl[0];
@@ -1100,6 +1118,7 @@ static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every
             } else {
                 rej++;
                 if ((rc = copy_state(m, false))) return rc;
+                m->learn->have_q = false;  // the last move is unknown after the restore
                 DevCtrl c = before;
                 c.iterations = after.iterations;
                 c.cnt = after.cnt;
@@ -1110,6 +1129,7 @@ static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every
             }
             continue;
         }
+        snapshot(m);
         CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
         if ((k & 31) == 31 && (rc = read_ctrl(m))) return rc;
     }
@@ -1230,6 +1250,26 @@ int mesh_profile_step(mesh_t* m, int32_t n_iters, double* stage_ms) {
     return profile(m, n_iters, stage_ms);
 }
 
+static int set_target(mesh_s* m, int k, double min_angle) {
+    int rc = sync_in(m);
+    if (rc || (rc = read_ctrl(m))) return rc;
+    size_t lo = k < 0 ? 0 : (size_t)k, hi = k < 0 ? m->parts.size() : (size_t)k + 1;
+    for (size_t q = lo; q < hi; q++) {
+        DevCtrl& c = m->hctrl[q];
+        c.target_min_ang = min_angle;
+        c.target_reached = 0;
+        if (c.terminated && min_angle > 0 && !(c.min_ang >= min_angle)) c.terminated = 0;
+        CUDA_TRY(cudaMemcpyAsync(m->ctrl + q, &c, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
+int mesh_set_quality_target(mesh_t* m, double min_angle_deg) {
+    if (!m || !(min_angle_deg >= 0) || min_angle_deg > 60) return fail(TRIME_EINVAL, "bad argument");
+    return set_target(m, 0, min_angle_deg);
+}
+
 int mesh_set_tuning(mesh_t* m, double n_opt, int32_t lanes) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
     return set_tuning(m, n_opt, lanes);
@@ -1259,6 +1299,9 @@ int mesh_collect_pairs(mesh_t* m, int32_t horizon, uint16_t* X, float* T) {
     int rc = sync_in(m);
     if (rc || (rc = ensure_learn(m)) || (rc = read_ctrl(m))) return rc;
     LearnBufs* L = m->learn;
+    snapshot(m);
+    CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+    if ((rc = read_ctrl(m))) return rc;
     features_any(m, X, L->H, L->px, L->py, 1, next_is_cvd(m));
     for (int32_t k = 0; k < horizon; k++) CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
     if (m->prec == 0)
@@ -1281,11 +1324,11 @@ int mesh_propose(mesh_t* m, mlp_t* net, double jump) {
 }
 
 int mesh_step_learned(mesh_t* m, mlp_t* net, int32_t n_iters, int32_t every, double jump, double min_angle_tol,
-                      mesh_stats* stats, int32_t* accepted, int32_t* rejected) {
+                      int32_t max_proposals, mesh_stats* stats, int32_t* accepted, int32_t* rejected) {
     if (!m || !net || !stats || n_iters < 0 || every < 1 || !(jump > 0) || !(min_angle_tol >= 0))
         return fail(TRIME_EINVAL, "bad argument");
     if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
-    return do_step_learned(m, net, n_iters, every, jump, min_angle_tol, stats, accepted, rejected);
+    return do_step_learned(m, net, n_iters, every, jump, min_angle_tol, max_proposals, stats, accepted, rejected);
 }
 
 // ------------------------------------------------------------------ batches
@@ -1364,6 +1407,12 @@ int mesh_batch_set_method_state(mesh_batch_t* b, int32_t mesh, int32_t switched,
 int mesh_batch_profile_step(mesh_batch_t* b, int32_t n_iters, double* stage_ms) {
     if (!b || !stage_ms || n_iters < 0) return fail(TRIME_EINVAL, "bad argument");
     return profile(b, n_iters, stage_ms);
+}
+
+int mesh_batch_set_quality_target(mesh_batch_t* b, int32_t mesh, double min_angle_deg) {
+    if (!b || !(min_angle_deg >= 0) || min_angle_deg > 60) return fail(TRIME_EINVAL, "bad argument");
+    if (mesh < -1 || mesh >= (int32_t)b->parts.size()) return fail(TRIME_EINVAL, "mesh index out of range");
+    return set_target(b, mesh, min_angle_deg);
 }
 
 int mesh_batch_set_tuning(mesh_batch_t* b, double n_opt, int32_t lanes) {

@@ -6,6 +6,8 @@
 // offsets of its 16 nearest points / h_i, ln(h_i / h_avg), the sizing
 // gradient, the boundary flag and the move in use.  The paper's method has no
 // learned part; plain iterations stay the fallback and judge the proposals.
+// Two more features carry the point's last move / h_i, so the model can
+// extrapolate the trajectory it is on.
 //
 // Every product runs on the tensor cores: one CTA of 128 threads takes 128
 // samples, stages each operand in shared memory in the K-major core-matrix
@@ -490,7 +492,8 @@ __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_us
 // no unscanned bucket can hold a nearer point, then the 48 features.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_features(const __grid_constant__ IterArgs<T> a, uint16_t* X, float* H,
-                                                       T* px, T* py, int by_id, float mflag) {
+                                                       T* px, T* py, const T* qx, const T* qy, int by_id,
+                                                       float mflag) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.n) return;
     const MeshView& V = a.V;
@@ -561,6 +564,8 @@ __global__ void __launch_bounds__(kThreads) k_features(const __grid_constant__ I
     f[34] = bf16_bits((float)gy);
     f[35] = a.srt.cls[s] == PT_BOUNDARY ? kBf16One : 0;
     f[36] = bf16_bits(mflag);
+    f[37] = qx ? bf16_bits((float)fdiv(fsub(xd, (double)qx[id]), h)) : 0;
+    f[38] = qy ? bf16_bits((float)fdiv(fsub(yd, (double)qy[id]), h)) : 0;
     for (int k = kMlpFeat; k < kMlpIn; k++) f[k] = 0;
     uint4* dst = reinterpret_cast<uint4*>(X + row * kMlpIn);
     const uint4* src = reinterpret_cast<const uint4*>(f);
@@ -574,15 +579,32 @@ __global__ void __launch_bounds__(kThreads) k_features(const __grid_constant__ I
 }
 
 template <typename T>
-void launch_features(const IterArgs<T>& a, uint16_t* X, float* H, T* px, T* py, int by_id, float method_cvd,
-                     cudaStream_t st) {
+void launch_features(const IterArgs<T>& a, uint16_t* X, float* H, T* px, T* py, const T* qx, const T* qy, int by_id,
+                     float method_cvd, cudaStream_t st) {
     int g = (a.n + kThreads - 1) / kThreads;
-    if (g > 0) k_features<T><<<g, kThreads, 0, st>>>(a, X, H, px, py, by_id, method_cvd);
+    if (g > 0) k_features<T><<<g, kThreads, 0, st>>>(a, X, H, px, py, qx, qy, by_id, method_cvd);
 }
-template void launch_features<double>(const IterArgs<double>&, uint16_t*, float*, double*, double*, int, float,
-                                      cudaStream_t);
-template void launch_features<float>(const IterArgs<float>&, uint16_t*, float*, float*, float*, int, float,
-                                     cudaStream_t);
+template void launch_features<double>(const IterArgs<double>&, uint16_t*, float*, double*, double*, const double*,
+                                      const double*, int, float, cudaStream_t);
+template void launch_features<float>(const IterArgs<float>&, uint16_t*, float*, float*, float*, const float*,
+                                     const float*, int, float, cudaStream_t);
+
+template <typename T>
+__global__ void k_snapshot(const __grid_constant__ IterArgs<T> a, T* qx, T* qy) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    int id = a.cur.id[s];
+    qx[id] = a.cur.x[s];
+    qy[id] = a.cur.y[s];
+}
+
+template <typename T>
+void launch_snapshot(const IterArgs<T>& a, T* qx, T* qy, cudaStream_t st) {
+    int g = (a.n + kThreads - 1) / kThreads;
+    if (g > 0) k_snapshot<T><<<g, kThreads, 0, st>>>(a, qx, qy);
+}
+template void launch_snapshot<double>(const IterArgs<double>&, double*, double*, cudaStream_t);
+template void launch_snapshot<float>(const IterArgs<float>&, float*, float*, cudaStream_t);
 
 // the proposed move p + h_i Y of every slot, clamped and treated (Sec. 4.3);
 // the recorded previous move is capped at one plain step (fac_pt h_i)

@@ -378,6 +378,12 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_pre(const __grid_constan
         method = ctrl->method_param;
         term = qend;
     }
+    if (ctrl->target_min_ang > 0.0) {
+        // a quality target replaces the quality termination test: iterate
+        // until the minimum angle reaches it
+        term = n > 0 && ctrl->min_ang >= ctrl->target_min_ang;
+        if (term) ctrl->target_reached = 1;
+    }
     ctrl->prev_a = qa;
     ctrl->prev_b = qb;
     ctrl->prev_amax = qm;

@@ -33,7 +33,7 @@ def test_tensor_core_tile(M, N, K):
 
 
 def _features_like(n, seed):
-    """Random inputs shaped like the features (37 used columns, zero padding)."""
+    """Random inputs shaped like the features (39 used columns, zero padding)."""
     rng = np.random.default_rng(seed)
     X = np.zeros((n, 48))
     X[:, :32] = rng.standard_normal((n, 32)) * 1.5
@@ -41,6 +41,7 @@ def _features_like(n, seed):
     X[:, 33:35] = rng.standard_normal((n, 2)) * 0.05
     X[:, 35] = rng.integers(0, 2, n)
     X[:, 36] = rng.integers(0, 2, n)
+    X[:, 37:39] = rng.standard_normal((n, 2)) * 0.2
     return X
 
 
@@ -103,3 +104,56 @@ def test_training_reduces_loss():
     l1 = net.train(Xd, Td, epochs=30, batch=1024, lr=2e-3)
     l2, _ = net.loss_grad(g.bf16_bits(X), T.astype(np.float32))
     assert l2 < 0.1 * l0, (l0, l1, l2)
+
+
+@pytest.mark.parametrize("which", ["disk", "annulus"])
+def test_features_match_oracle(which):
+    import oracle
+    import paper_2309_13824_gb300 as g
+    from gpu_helpers import annulus_small, disk_small, h_of_points
+    from oracle import mlp as M
+
+    oracle.build()
+    sdf, siz, pts = disk_small(n=3001, seed=3) if which == "disk" else annulus_small(n=2500, seed=5)
+    method = 0 if which == "disk" else 1
+    gm = g.Mesh(sdf, siz, pts, method=method)
+    Xg, hg = gm.features()
+    om = oracle.OracleMesh(sdf, siz, pts, method=method)
+    h = h_of_points(om, pts)
+    _, _, _, havg = om.geometry()
+    Xo = g.bf16_bits(M.features(pts, h, havg, siz, om.classes() == 1, method))
+    assert np.allclose(hg, h, rtol=1e-7)
+    same = Xg == Xo
+    assert same[:, :32].mean() > 0.9999 and same[:, 33:].all(), (same[:, :32].mean(), same[:, 33:].mean())
+    assert same[:, 32].mean() > 0.999
+    # any difference is one BF16 ulp (a division or logarithm rounded differently)
+    d = np.abs(Xg.astype(np.int32) - Xo.astype(np.int32))
+    assert d.max() <= 1
+
+
+def test_learned_proposals_gain():
+    # trained on the method's own trajectories (a disk with DistMesh, an
+    # annulus with the hybrid), applied to annuli drawn with other seeds: the
+    # time to the plain method's converged minimum angle minus 1 degree
+    import workloads as W
+    from paper_2309_13824_gb300 import learn
+
+    disk = W.disk_workload(n=10000)
+    ann = W.annulus_workload(n=200000, seed=11)
+    net, loss, npairs = learn.train([(disk.sdf, disk.sizing, disk.points, 0, 0),
+                                     (ann.sdf, ann.sizing, ann.points, 2, 0)], epochs=30, fine_epochs=5)
+    assert npairs > 10**6 and loss < 0.01
+    its_plain = its_learned = 0
+    for seed in (21, 22, 23):
+        wl = W.annulus_workload(n=200000, seed=seed)
+        _, conv = learn.time_to_quality(wl.sdf, wl.sizing, wl.points)
+        q = conv["min_angle_deg"] - 1.0
+        _, sp = learn.time_to_quality(wl.sdf, wl.sizing, wl.points, target=q)
+        _, sl = learn.time_to_quality(wl.sdf, wl.sizing, wl.points, net=net, target=q)
+        assert sp["target_reached"] and sl["target_reached"], (seed, sp, sl)
+        assert sl["accepted"] > 0
+        its_plain += sp["iterations"]
+        its_learned += sl["iterations"]
+        print(f"seed {seed}: plain {sp['iterations']} iterations, learned {sl['iterations']} "
+              f"({sl['accepted']} proposals kept, {sl['rejected']} undone)")
+    assert its_learned < its_plain, (its_learned, its_plain)

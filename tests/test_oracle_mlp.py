@@ -111,6 +111,10 @@ def test_feature_invariances():
     assert ok.sum() > 100
     assert np.array_equal(offr[ok, :, 0], -off[ok, :, 1]) and np.array_equal(offr[ok, :, 1], off[ok, :, 0])
     assert np.all(Fr[:, 36] == 1) and np.all(F[:, 32] == 0) and np.all(F[:, 33:35] == 0)
+    assert np.all(F[:, 37:] == 0)
+    # the last move, relative to h
+    Fm = M.features(p, h, 0.05, siz, bnd, 0, previous=p - np.array([0.0125, -0.025]))
+    assert np.all(Fm[:, 37] == np.float32(0.25)) and np.all(Fm[:, 38] == np.float32(-0.5))
 
 
 def test_sizing_gradient_of_a_linear_field():
