@@ -281,6 +281,7 @@ template <typename T, bool B>
 __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterArgs<T> a) {
     const MeshView& V = mesh_of<B>(a, blockIdx.x * kThreads);
     if (!a.force && V.ctrl->terminated) return;
+    const bool cvd_now = V.ctrl->method_param == 1 || (V.ctrl->method_param == 2 && V.ctrl->switched);
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double acc[9] = {0, 0, 0, 0, 0, 180.0, 0, 0, 0};
     if (s < a.n && (!B || s - V.soff < V.n)) {
@@ -350,19 +351,29 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
             acc[3] = q3;
             acc[4] = q4;
             acc[5] = q5;
-            // valid edges (Eq. 3 sums), counted by the smaller id
+            // valid edges (Eq. 3 sums), counted by the smaller id; they set the
+            // DistMesh rest lengths, so they stay in T precision unless this
+            // iteration's move is CVD (then fac_mu only feeds a statistic)
             for (int t = 0; t < ne; t++) {
                 int j = lab[t];
                 if (j < 0) continue;
                 int tp = t == 0 ? ne - 1 : t - 1;
                 if (!((vm >> t) & 1u) && !((vm >> tp) & 1u)) continue;
                 if (!(idi < a.srt.id[j])) continue;
+                acc[6] += 1.0;
+                if (cvd_now) {
+                    float4 pj4 = a.pf[j];
+                    float ex = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y), ey = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
+                    float muf = bilin<float>(V.siz, pi4.x + 0.5f * ex, pi4.z + 0.5f * ey);
+                    acc[7] += (double)(ex * ex + ey * ey);
+                    acc[8] += (double)(muf * muf);
+                    continue;
+                }
                 T xj = a.srt.x[j], yj = a.srt.y[j];
                 T dx = xj - xi, dy = yj - yi;
                 T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
-                acc[6] += 1.0;
                 acc[7] += (double)(dx * dx + dy * dy);
-                acc[8] += (double)(mu * mu);  // Eq. 3 sums stay in T precision
+                acc[8] += (double)(mu * mu);
             }
         }
         a.vmask[s] = vm;

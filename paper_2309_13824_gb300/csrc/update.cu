@@ -230,27 +230,41 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
         T fac_mu = (T)V.ctrl->fac_mu;
         T Fx = 0, Fy = 0, fs = 0;
         // DistMesh forces on the valid edges (Eqs. 2-3); also the size deviation
+        // (a float statistic; in CVD iterations it is all this loop computes)
+        const float4 pi4 = a.pf[s];
         for (int t = 0; t < ne; t++) {
             int j = lab[t];
             if (j < 0) continue;
             int tp = t == 0 ? ne - 1 : t - 1;
             if (!((vm >> t) & 1u) && !((vm >> tp) & 1u)) continue;
+            bool owner = idi < a.srt.id[j];
+            if (method != 0) {
+                if (owner) {
+                    float4 pj4 = a.pf[j];
+                    float ex = ff_diff(pi4.x, pi4.y, pj4.x, pj4.y), ey = ff_diff(pi4.z, pi4.w, pj4.z, pj4.w);
+                    float muf = bilin<float>(V.siz, pj4.x + 0.5f * ex, pj4.z + 0.5f * ey);
+                    dev += (double)fabsf(sqrtf(ex * ex + ey * ey) / ((float)fac_mu * muf) - 1.0f);
+                    nedge += 1.0;
+                }
+                continue;
+            }
             T xj = a.srt.x[j], yj = a.srt.y[j];
             T dx = xi - xj, dy = yi - yj;
-            T l = sqrt(dx * dx + dy * dy);
+            T l2 = dx * dx + dy * dy;
+            T r = rsqrt(l2);  // 1 / l: one reciprocal square root instead of a root and a division
+            T l = l2 * r;
             T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
-            if (idi < a.srt.id[j]) {
+            if (owner) {
                 dev += (double)fabsf((float)l / ((float)fac_mu * (float)mu) - 1.0f);
                 nedge += 1.0;
             }
-            if (method != 0) continue;
             T l0 = (T)P.fac_F * fac_mu * mu;
             if (l < l0) {
-                T f = (T)P.k_spring * (l0 - l);
-                T fl = f / l;
+                T k = (T)P.k_spring;
+                T fl = k * (l0 * r - (T)1);  // f / l with f = k (l0 - l)
                 Fx += fl * dx;
                 Fy += fl * dy;
-                fs += f;
+                fs += k * (l0 - l);
             }
         }
         T pnx, pny, cx = xi, cy = yi;

@@ -101,24 +101,22 @@ __device__ __forceinline__ void lane_vertex(Lane& L, int ne, const Grp<G>& g, fl
     if (active && g.gl < ne) make_vertex(L, nx2, ny2, s2, lab2, RB);
 }
 
-template <typename T>
+// what the rare exact path needs besides the launch arguments
 struct CellCtx {
-    const T* x;
-    const T* y;
-    const int32_t* id;
     DevCtrl* ctrl;
-    double pix, piy;
-    int idi;
+    int si;  // the cell's slot
 };
 
 // exact decision for vertex (j, k) of cell i against candidate l: FP64 filter,
 // then expansion arithmetic with symbolic perturbation
 template <typename T>
-__device__ __noinline__ bool exact_cut(const CellCtx<T>& c, int sj, int sk, int sl) {
-    double pi[2] = {c.pix, c.piy};
-    double pj[2] = {(double)c.x[sj], (double)c.y[sj]};
-    double pk[2] = {(double)c.x[sk], (double)c.y[sk]};
-    double pl[2] = {(double)c.x[sl], (double)c.y[sl]};
+__device__ __noinline__ bool exact_cut(const IterArgs<T>& a, const CellCtx& c, int sj, int sk, int sl) {
+    const T* X = a.srt.x;
+    const T* Y = a.srt.y;
+    double pi[2] = {(double)X[c.si], (double)Y[c.si]};
+    double pj[2] = {(double)X[sj], (double)Y[sj]};
+    double pk[2] = {(double)X[sk], (double)Y[sk]};
+    double pl[2] = {(double)X[sl], (double)Y[sl]};
     double ax = pj[0] - pi[0], ay = pj[1] - pi[1];
     double bx = pk[0] - pi[0], by = pk[1] - pi[1];
     double cx = pl[0] - pi[0], cy = pl[1] - pi[1];
@@ -129,7 +127,8 @@ __device__ __noinline__ bool exact_cut(const CellCtx<T>& c, int sj, int sk, int 
     if (P > 1e-280 && fabs(lam) > 64.0 * 1.1102230246251565e-16 * P) return lam < 0.0;  // lam = -det4
     atomicAdd(&c.ctrl->cnt.exact_calls, 1ull);
     int o = orient_exact(pi, pj, pk);
-    int d = incircle_sos(pi, c.idi, pj, c.id[sj], pk, c.id[sk], pl, c.id[sl]);
+    const int32_t* id = a.srt.id;
+    int d = incircle_sos(pi, id[c.si], pj, id[sj], pk, id[sk], pl, id[sl]);
     if (o == kExactFail || d == kExactFail) {
         atomicAdd(&c.ctrl->cnt.exact_overflow, 1ull);
         return false;
@@ -139,10 +138,11 @@ __device__ __noinline__ bool exact_cut(const CellCtx<T>& c, int sj, int sk, int 
 
 // Clip the group's polygon by n.u <= s (label lab) when `active`; bisector:
 // a neighbour's bisector (n = d, s = |d|^2/2).  Executed by every lane of the
-// warp.  Returns 0 ok / no-op, 1 empty cell, 2 more than G edges.
+// warp.  Returns 0 ok / no-op, 1 empty cell, 2 more than G edges; any_cut
+// tells whether some cell of the warp changed.
 template <typename T, int G>
 __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, bool bisector, bool active, float RB,
-                       const Grp<G>& g, const CellCtx<T>& ctx) {
+                       const Grp<G>& g, const IterArgs<T>& a, const CellCtx& ctx, bool& any_cut) {
     bool cut = false;
     if (active && g.gl < ne) {
         if (bisector && L.bb) {
@@ -152,7 +152,7 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
             float bound = 32.0f * kEps * P;
             if (P > 1e-30f && lam < -bound) cut = true;
             else if (P > 1e-30f && lam > bound) cut = false;
-            else cut = exact_cut<T>(ctx, L.lab, L.nlab, lab);
+            else cut = exact_cut<T>(a, ctx, L.lab, L.nlab, lab);
         } else {
             cut = nx * L.vx + ny * L.vy > s;
         }
@@ -165,7 +165,8 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
         status = 1;
         doit = false;
     }
-    if (!warp_any(doit)) return status;  // nothing to cut anywhere in the warp
+    any_cut = warp_any(doit);
+    if (!any_cut) return status;  // nothing to cut anywhere in the warp
     int prevl = g.gl == 0 ? ne - 1 : g.gl - 1;
     bool pcut = (m >> (prevl & 31)) & 1u;
     unsigned starts = g.ballot(g.gl < ne && cut && !pcut);
@@ -174,7 +175,8 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
     int sidx = starts ? __ffs(starts) - 1 : 0;
     unsigned after = sidx >= 31 ? 0u : (ends >> (sidx + 1)) << (sidx + 1);
     int eidx = after ? __ffs(after) - 1 : (ends ? __ffs(ends) - 1 : 0);
-    int k = ne > 0 ? (sidx - eidx + ne) % ne + 1 : 1;  // kept edges E_e .. E_s
+    int k = sidx - eidx + 1;  // kept edges E_e .. E_s
+    if (k <= 0) k += ne;
     int nn = k + 1;
     if (doit && nn > G) {
         status = 2;
@@ -182,7 +184,9 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
     }
     // rotate the edges so E_e lands in lane 0, append the new edge in lane k,
     // then every lane recomputes its vertex (SIMT: as cheap as two lanes)
-    int src = doit ? (eidx + g.gl) % ne : g.gl;
+    int src = eidx + g.gl;  // (eidx + gl) mod ne for the lanes that keep an edge
+    if (src >= ne) src -= ne;
+    if (!doit) src = g.gl;
     float rnx = g.shfl(L.nx, src), rny = g.shfl(L.ny, src), rs = g.shfl(L.s, src);
     int rlab = g.shfl(L.lab, src);
     if (doit) {
@@ -219,14 +223,9 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
         live = false;
     }
     const float4 pi4 = a.pf[s];
-    CellCtx<T> ctx;
-    ctx.x = a.srt.x;
-    ctx.y = a.srt.y;
-    ctx.id = a.srt.id;
+    CellCtx ctx;
     ctx.ctrl = V.ctrl;
-    ctx.pix = (double)a.srt.x[s];
-    ctx.piy = (double)a.srt.y[s];
-    ctx.idi = a.srt.id[s];
+    ctx.si = s;
     // generator relative to the box corner, and the box size (float; the box
     // planes only need to bound Reg_i with the S/16 margin)
     const float xf = (pi4.x - P.bx0f) + pi4.y, yf = (pi4.z - P.by0f) + pi4.w;
@@ -269,7 +268,8 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
             float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
             float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
             float sb = b == 0 ? xf + mb : b == 1 ? (Wf - xf) + mb : b == 2 ? yf + mb : (Hf - yf) + mb;
-            int st = clip_by<T, G>(L, ne, nx, ny, sb, box_label(b), false, live && status == 0, RB, g, ctx);
+            bool any_cut;
+            int st = clip_by<T, G>(L, ne, nx, ny, sb, box_label(b), false, live && status == 0, RB, g, a, ctx, any_cut);
             if (st) status = st;
         }
     }
@@ -280,36 +280,29 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     const float bmargin = (float)(1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy)) + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
     bool done = !live || status != 0;
     int nst = 0;
-    // apply the staged candidates nearest first (warp-uniform loop)
+    // apply the staged candidates nearest first (warp-uniform loop).  The
+    // nearest entry is found by a minimum over keys made of the squared
+    // distance's bits with the entry index in the lowest 7 (the order of
+    // nearly equal distances does not matter for the result); each lane
+    // marks the entries it owns (gl, gl + G, ...) once taken.
     auto flush = [&]() {
+        unsigned used = 0;
         while (true) {
-            float best = INF;
-            int bi = -1;
-            float lim = 4.0f * Rmax * Rmax * 1.0001f;
-            for (int q = g.gl; q < nst; q += G) {
-                float d2 = stage[q].z;
-                if (d2 < lim && d2 < best) {
-                    best = d2;
-                    bi = q;
-                }
-            }
+            unsigned key = 0xFFFFFFFFu;
+            int kq = 0;
+            for (int q = g.gl; q < nst; q += G, kq++)
+                if (!((used >> kq) & 1u)) key = min(key, (__float_as_uint(stage[q].z) & ~0x7Fu) | (unsigned)q);
 #pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) {
-                float ob = __shfl_xor_sync(kFull, best, o);
-                int oi = __shfl_xor_sync(kFull, bi, o);
-                if (ob < best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            bool has = !done && bi >= 0;
+            for (int o = G / 2; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(kFull, key, o));
+            float lim = 4.0f * Rmax * Rmax * 1.0001f;
+            int bi = (int)(key & 0x7Fu);
+            bool has = !done && key != 0xFFFFFFFFu && __uint_as_float(key & ~0x7Fu) < lim;
             if (!warp_any(has)) break;
             float4 c = has ? stage[bi] : make_float4(0.f, 0.f, 1.f, 0.f);
-            __syncwarp();
-            if (has && g.gl == 0) stage[bi].z = INF;
-            __syncwarp();
+            if (has && (bi & (G - 1)) == g.gl) used |= 1u << (bi / G);
             int ne0 = ne;
-            int st = clip_by<T, G>(L, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, has, RB, g, ctx);
+            bool any_cut;
+            int st = clip_by<T, G>(L, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, has, RB, g, a, ctx, any_cut);
             if (P.debug && has && g.gl == 0) {
                 atomicAdd(&V.ctrl->cnt.vor_picks, 1ull);
                 if (ne != ne0 || st) atomicAdd(&V.ctrl->cnt.vor_cuts, 1ull);
@@ -319,7 +312,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                 done = true;
                 nst = 0;
             }
-            Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
+            if (any_cut) Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
         }
         nst = 0;
         __syncwarp();
@@ -385,8 +378,8 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                     dy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
                     d2 = dx * dx + dy * dy;
                     if (sizeof(T) == 8 && d2 < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
-                        dx = (float)((double)a.srt.x[cs] - ctx.pix);
-                        dy = (float)((double)a.srt.y[cs] - ctx.piy);
+                        dx = (float)((double)a.srt.x[cs] - (double)a.srt.x[s]);
+                        dy = (float)((double)a.srt.y[cs] - (double)a.srt.y[s]);
                         d2 = dx * dx + dy * dy;
                     }
                 }
@@ -443,7 +436,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
 // main pass: G lanes per cell, 32 / G cells per warp.  In a batch the cells
 // of a warp lie in one chunk, hence in one mesh.
 template <typename T, int G, bool B>
-__global__ void __launch_bounds__(kVoroThreads, 6) k_voronoi(const __grid_constant__ IterArgs<T> a) {
+__global__ void __launch_bounds__(kVoroThreads, 8) k_voronoi(const __grid_constant__ IterArgs<T> a) {
     if (!B && !a.force && a.V.ctrl->terminated) return;
     __shared__ float4 stage_all[kVoroThreads / G][kStageCap];
     Grp<G> g;
