@@ -154,24 +154,61 @@ def replica_value(points_per_rank, steps, local_seconds, dist=None, device="cpu"
     return points_per_rank * world * steps / t / 1e6, t
 
 
-def oracle_sample_rate(wl, target_s, max_cells=None):
-    """Oracle (single thread) per-cell iteration work on a random sample."""
+def oracle_sample_rate(wl, target_s, max_cells=None, threads=1, om=None):
+    """Oracle per-cell iteration work (cell clipping, owned triangles with
+    Tests 1-3, CVD centroid) on a random sample of cells sized to take about
+    target_s seconds; threads > 1 spreads the cells over OpenMP threads.
+    Returns (cells, seconds, oracle mesh)."""
     import oracle
 
     oracle.build()
-    om = oracle.OracleMesh(wl.sdf, wl.sizing, wl.points, method=wl.method)
+    if om is None:
+        om = oracle.OracleMesh(wl.sdf, wl.sizing, wl.points, method=wl.method)
     n = len(wl.points)
     rng = np.random.default_rng(123)
-    probe = rng.choice(n, min(n, 4000), replace=False)
+
+    def work(cells):
+        if threads > 1:
+            om.rebuild_sample_mt(cells, True, threads)
+        else:
+            om.rebuild_sample(cells, True)
+
+    probe = rng.choice(n, min(n, 4000 * threads), replace=False)
     t = time.perf_counter()
-    om.rebuild_sample(probe)
+    work(probe)
     per = (time.perf_counter() - t) / len(probe)
     cnt = int(min(n if max_cells is None else max_cells, max(len(probe), target_s / per)))
     cells = rng.choice(n, cnt, replace=False)
     t = time.perf_counter()
-    om.rebuild_sample(cells)
-    dt = time.perf_counter() - t
-    return cnt, dt
+    work(cells)
+    return cnt, time.perf_counter() - t, om
+
+
+def run_reference(args, wl):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    cells_per_step = 30000 * threads
+    om = None
+    for _ in range(args.warmup):
+        _, _, om = oracle_sample_rate(wl, 0.0, max_cells=2000, threads=threads, om=om)
+    times = []
+    cnt_total = 0
+    for _ in range(args.steps):
+        cnt, dt, om = oracle_sample_rate(wl, 1e9, max_cells=cells_per_step, threads=threads, om=om)
+        times.append(dt)
+        cnt_total += cnt
+    v = cnt_total / sum(times) / 1e6
+    sample = (f"{cells_per_step} random cells of the 1e6-point workload per step: cell clipping, owned triangles "
+              f"with Tests 1-3 and CVD centroid (FP64 oracle, OpenMP over {threads} threads)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "points": len(wl.points)},
+            "cpu_baseline": {"value": v, "unit": "Mpts/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 def batched_leg(g, torch, stream, steps, flush):
@@ -329,31 +366,6 @@ def learned_leg(g, stream):
     return out
 
 
-def run_reference(args, wl):
-    world, rank, local = dist_env()
-    if rank != 0:
-        return
-    cells_per_step = 30000
-    for _ in range(args.warmup):
-        oracle_sample_rate(wl, 0.0, max_cells=2000)
-    times = []
-    cnt_total = 0
-    for _ in range(args.steps):
-        cnt, dt = oracle_sample_rate(wl, 1e9, max_cells=cells_per_step)
-        times.append(dt)
-        cnt_total += cnt
-    v = cnt_total / sum(times) / 1e6
-    sample = (f"{cells_per_step} random cells of the 1e6-point workload per step: cell clipping, owned triangles "
-              f"with Tests 1-3 and CVD centroid (single thread, FP64 oracle)")
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpts/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "points": len(wl.points)},
-            "cpu_baseline": {"value": v, "unit": "Mpts/s", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": v, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -494,11 +506,15 @@ def main():
         extras["learned"] = learned_leg(g, stream)
         if args.sweep:
             extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
-        cnt, dt = oracle_sample_rate(wl, 10.0)
-        extras["cpu_baseline"] = {"value": cnt / dt / 1e6, "unit": "Mpts/s", "cores": 1, "kind": "oracle",
+        threads = os.cpu_count() or 1
+        cnt, dt, om = oracle_sample_rate(wl, 10.0, threads=threads)
+        cnt1, dt1, _ = oracle_sample_rate(wl, 5.0, threads=1, om=om)
+        extras["cpu_baseline"] = {"value": cnt / dt / 1e6, "unit": "Mpts/s", "cores": threads, "kind": "oracle",
                                   "sample": f"{cnt} random cells of the workload: cell clipping, owned triangles "
-                                            f"with Tests 1-3, CVD centroid; single-thread FP64 oracle "
-                                            f"({dt:.1f} s)"}
+                                            f"with Tests 1-3, CVD centroid; FP64 oracle on {threads} OpenMP "
+                                            f"threads ({dt:.1f} s)",
+                                  "value_1_thread": cnt1 / dt1 / 1e6,
+                                  "sample_1_thread": f"{cnt1} random cells, one thread ({dt1:.1f} s)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world, "steps": args.steps,

@@ -31,7 +31,7 @@ def build(force: bool = False) -> Path:
     _OUT.parent.mkdir(exist_ok=True)
     if force or not _OUT.exists() or _OUT.stat().st_mtime < max(_SRC.stat().st_mtime, _HDR.stat().st_mtime):
         tmp = _OUT.with_suffix(f".{os.getpid()}.tmp")
-        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        cmd = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
                "-o", str(tmp), str(_SRC), "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _OUT)
@@ -76,6 +76,8 @@ def _load():
         for name in ("om_rebuild", "om_step"):
             getattr(lib, name).argtypes = [C.c_void_p]
         lib.om_rebuild_sample.argtypes = [C.c_void_p, i64p, C.c_int64, C.c_int]
+        lib.om_rebuild_sample_mt.restype = C.c_int64
+        lib.om_rebuild_sample_mt.argtypes = [C.c_void_p, i64p, C.c_int64, C.c_int, C.c_int]
         lib.om_sample_triangles.restype = C.c_int64
         lib.om_sample_triangles.argtypes = [C.c_void_p, i64p, C.c_int64, ip, C.c_int64]
         for name in ("om_num_points", "om_num_triangles", "om_num_edges"):
@@ -194,9 +196,20 @@ class OracleMesh:
         self._lib.om_step(self._h)
         return self.stats()
 
-    def rebuild_sample(self, cells):
+    def rebuild_sample(self, cells, with_centroid: bool = True):
+        """Procedure I on the given cells (and their CVD centroids), single thread."""
         cells = np.ascontiguousarray(cells, dtype=np.int64)
-        self._lib.om_rebuild_sample(self._h, cells.ctypes.data_as(C.POINTER(C.c_int64)), len(cells), 0)
+        self._lib.om_rebuild_sample(self._h, cells.ctypes.data_as(C.POINTER(C.c_int64)), len(cells),
+                                    int(with_centroid))
+
+    def rebuild_sample_mt(self, cells, with_centroid: bool = True, threads: int = 0) -> int:
+        """rebuild_sample's work on `threads` OpenMP threads (0: all cores); timing only."""
+        import os
+
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        nt = threads or (os.cpu_count() or 1)
+        return self._lib.om_rebuild_sample_mt(self._h, cells.ctypes.data_as(C.POINTER(C.c_int64)), len(cells),
+                                              int(with_centroid), nt)
 
     def sample_triangles(self, cells) -> np.ndarray:
         """Valid triangles owned (smallest index) by the given cells."""

@@ -1386,6 +1386,45 @@ int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with
     return (int)sample_cells(m, cells, ncells, with_centroid, NULL, 0);
 }
 
+/* The same work spread over nthreads OpenMP threads (cells are independent);
+ * only for timing the oracle on all host cores.  Returns the number of owned
+ * valid triangles. */
+int64_t om_rebuild_sample_mt(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid, int nthreads) {
+    ogrid_t G;
+    ogrid_build(m, &G);
+    int64_t kept = 0;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 256) reduction(+ : kept)
+    for (int64_t q = 0; q < ncells; q++) {
+        hp_t E[CELL_CAP];
+        int32_t lab[CELL_CAP];
+        double poly[2 * CELL_CAP];
+        int64_t errs = 0;
+        int64_t i = cells[q];
+        int ne = cell_compute(m, &G, i, E, &errs);
+        for (int t = 0; t < ne; t++) lab[t] = E[t].lab;
+        for (int t = 0; t < ne; t++) {
+            int32_t j = lab[t], k = lab[(t + 1) % ne];
+            if (j < 0 || k < 0 || !(i < j && i < k)) continue;
+            double ox, oy, R;
+            circumcenter_fixed(m->x[i], m->y[i], m->x[j], m->y[j], m->x[k], m->y[k], &ox, &oy, &R);
+            if (!(reg_contains(m, i, ox, oy) && reg_contains(m, j, ox, oy) && reg_contains(m, k, ox, oy))) continue;
+            if (m->P.validity && !triangle_valid(m, i, j, k)) continue;
+            kept++;
+        }
+        if (with_centroid) {
+            int n = cell_polygon_labels(m, i, lab, ne, poly, CELL_CAP);
+            double gen[2] = {m->x[i], m->y[i]}, c[2];
+            double h = h_at(m, m->x[i], m->y[i]);
+            int32_t lv;
+            if (n >= 3)
+                centroid_adaptive(&m->siz, gen, poly, n, fmax(m->dprev[i] / h, m->P.fac_end), m->P.quad_max_level,
+                                  c, &lv, NULL);
+        }
+    }
+    ogrid_free(&G);
+    return kept;
+}
+
 int64_t om_sample_triangles(om_mesh* m, const int64_t* cells, int64_t ncells, int32_t* tri, int64_t cap) {
     return sample_cells(m, cells, ncells, 0, tri, cap);
 }

@@ -85,6 +85,10 @@ int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with
  * written). */
 int64_t om_sample_triangles(om_mesh* m, const int64_t* cells, int64_t ncells, int32_t* tri, int64_t cap);
 
+/* om_rebuild_sample's work spread over nthreads OpenMP threads (timing only);
+ * returns the number of owned valid triangles of the cells. */
+int64_t om_rebuild_sample_mt(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid, int nthreads);
+
 int64_t om_num_points(const om_mesh* m);
 int64_t om_num_triangles(const om_mesh* m);
 void om_get_triangles(const om_mesh* m, int32_t* tri);          /* 3*n_tri, sorted */
