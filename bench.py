@@ -435,11 +435,12 @@ def main():
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA issue, TFLOP/s
     achieved = VORONOI_FLOP_PER_CELL * n / t_vor / 1e12
+    pipe = g.mesh_measure_pipe_peaks()
     src = os.path.join(ROOT, "paper_2309_13824_gb300", "csrc", "voronoi.cuh")
     roofline = {"bound": "alu", "kernel": "k_voronoi", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": committed_traffic(src),
                 "peak_note": f"{sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and clocks)",
-                "stage_ms": stage_ms}
+                "stage_ms": stage_ms, "measured_pipe_peaks": pipe}
 
     # ---- end to end through the C ABI: H2D of the step's positions from
     # pinned host memory, one iteration, D2H of the moved positions

@@ -319,6 +319,14 @@ int mesh_propose(mesh_t* m, mlp_t* net, double jump);
 int mesh_step_learned(mesh_t* m, mlp_t* net, int32_t n_iters, int32_t every, double jump, double min_angle_tol,
                       int32_t max_proposals, mesh_stats* stats, int32_t* accepted, int32_t* rejected);
 
+/* Measured issue peaks of the FP32 and FP64 pipes of the current device
+ * (TFLOP/s; 8 independent fused multiply-add chains per thread, 8 blocks of
+ * 256 threads per SM), with the SM count and the nominal SM clock (kHz) the
+ * device reports: the roofline denominators of the arithmetic-bound kernels.
+ * sm_count and sm_clock_khz may be NULL.  Synchronous; about 0.1 s.  The paper
+ * has no counterpart. */
+int mesh_measure_pipe_peaks(double* fp32_tflops, double* fp64_tflops, int32_t* sm_count, int32_t* sm_clock_khz);
+
 /* ---------------------------------------------------------------- batches
  * Many independent meshes of uneven sizes stepped together: every stage of
  * an iteration is one kernel launch over all meshes (their points are

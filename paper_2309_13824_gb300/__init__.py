@@ -77,7 +77,7 @@ EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mes
            "mesh_set_tuning", "mesh_batch_set_tuning", "mesh_tc_gemm_bf16", "mlp_create", "mlp_destroy",
            "mlp_get_params", "mlp_set_params", "mlp_forward", "mlp_loss_grad", "mlp_train", "mesh_features",
            "mesh_collect_pairs", "mesh_propose", "mesh_step_learned", "mesh_set_quality_target",
-           "mesh_batch_set_quality_target"]
+           "mesh_batch_set_quality_target", "mesh_measure_pipe_peaks"]
 
 MLP_IN = 48
 MLP_PARAMS = 7426
@@ -143,6 +143,7 @@ def lib():
     L.mlp_train.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_uint64, P(C.c_double)]
     L.mesh_features.argtypes = [vp, vp, vp]
     L.mesh_set_quality_target.argtypes = [vp, C.c_double]
+    L.mesh_measure_pipe_peaks.argtypes = [P(C.c_double), P(C.c_double), P(C.c_int32), P(C.c_int32)]
     L.mesh_batch_set_quality_target.argtypes = [vp, C.c_int32, C.c_double]
     L.mesh_collect_pairs.argtypes = [vp, C.c_int32, vp, vp]
     L.mesh_propose.argtypes = [vp, vp, C.c_double]
@@ -159,7 +160,8 @@ def lib():
                  "mesh_batch_profile_step", "mesh_batch_get_tuning", "mesh_set_tuning", "mesh_batch_set_tuning",
                  "mesh_tc_gemm_bf16", "mlp_create", "mlp_get_params", "mlp_set_params", "mlp_forward",
                  "mlp_loss_grad", "mlp_train", "mesh_features", "mesh_collect_pairs", "mesh_propose",
-                 "mesh_step_learned", "mesh_set_quality_target", "mesh_batch_set_quality_target"):
+                 "mesh_step_learned", "mesh_set_quality_target", "mesh_batch_set_quality_target",
+                 "mesh_measure_pipe_peaks"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -242,6 +244,14 @@ def mesh_tc_gemm_bf16(A, B):
     _check(lib().mesh_tc_gemm_bf16(A.ctypes.data_as(C.c_void_p), B.ctypes.data_as(C.c_void_p),
                                    D.ctypes.data_as(C.c_void_p), M, N, K))
     return D
+
+
+def mesh_measure_pipe_peaks() -> dict:
+    """Measured FP32 / FP64 fused-multiply-add throughput of the current device."""
+    f32, f64 = C.c_double(), C.c_double()
+    sm, clk = C.c_int32(), C.c_int32()
+    _check(lib().mesh_measure_pipe_peaks(C.byref(f32), C.byref(f64), C.byref(sm), C.byref(clk)))
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value, "sm_count": sm.value, "sm_clock_mhz": clk.value / 1e3}
 
 
 def _stats_dict(s: mesh_stats) -> dict:
