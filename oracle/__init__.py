@@ -50,7 +50,7 @@ class _Params(C.Structure):
                 ("fac_pt", C.c_double), ("fac_geps", C.c_double), ("fac_voro_bound", C.c_double),
                 ("fac_end", C.c_double), ("T_circ", C.c_double), ("T_switch", C.c_double),
                 ("T_end_q", C.c_double), ("T_end_amax", C.c_double), ("N_opt", C.c_double),
-                ("eta", C.c_double), ("damping", C.c_double)]
+                ("eta", C.c_double), ("damping", C.c_double), ("fac_retria", C.c_double)]
 
 
 class _Stats(C.Structure):
@@ -59,7 +59,7 @@ class _Stats(C.Structure):
                 ("min_angle_deg", C.c_double), ("mean_size_dev", C.c_double), ("fac_mu", C.c_double),
                 ("newton_fail", C.c_int64), ("trace_cap", C.c_int64), ("quad_cap", C.c_int64),
                 ("clip_errors", C.c_int64), ("method_used", C.c_int32), ("terminated", C.c_int32),
-                ("switched", C.c_int32), ("small_moves", C.c_int32)]
+                ("switched", C.c_int32), ("small_moves", C.c_int32), ("triangulated", C.c_int32)]
 
 
 def _load():

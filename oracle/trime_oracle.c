@@ -366,6 +366,8 @@ struct om_mesh {
     double *pnew, *force, *fsum, *cen, *area;
     int32_t* qlevel;
     om_stats st;
+    int retri;                 /* the next step re-triangulates (Algorithm 1) */
+    double *tx, *ty;           /* positions at the last triangulation */
     int switched, have_prev;
     double prev_a, prev_b, prev_amax;
     int64_t clip_errors;
@@ -393,6 +395,7 @@ void om_default_params(om_params* p) {
     p->N_opt = 3.3;           /* App. B */
     p->eta = 0.5;             /* App. B */
     p->damping = 1.0;         /* App. B: alpha-hat */
+    p->fac_retria = 0.1;      /* App. B: fac_mvmt^retria (DistMesh only) */
 }
 
 static int point_cell(const om_mesh* m, double x, double y, int* gi, int* gj) {
@@ -511,8 +514,11 @@ om_mesh* om_create(const om_grid* sdf, const om_grid* sizing, const double* xy, 
     m->area = (double*)calloc(nn, sizeof(double));
     m->qlevel = (int32_t*)calloc(nn, sizeof(int32_t));
     m->ring_off = (int64_t*)calloc(nn + 1, sizeof(int64_t));
+    m->tx = (double*)calloc(nn, sizeof(double));
+    m->ty = (double*)calloc(nn, sizeof(double));
+    m->retri = 1;
     if (!m->x || !m->y || !m->cls || !m->dprev || !m->pnew || !m->force || !m->fsum || !m->cen || !m->area ||
-        !m->qlevel || !m->ring_off) { set_err("out of memory"); om_destroy(m); return NULL; }
+        !m->qlevel || !m->ring_off || !m->tx || !m->ty) { set_err("out of memory"); om_destroy(m); return NULL; }
     for (int64_t i = 0; i < n; i++) {
         double x = xy[2 * i], y = xy[2 * i + 1];
         if (!isfinite(x) || !isfinite(y) || x < m->sdf.x0 || x > m->sdf.x1 || y < m->sdf.y0 || y > m->sdf.y1) {
@@ -540,6 +546,7 @@ void om_destroy(om_mesh* m) {
     free(m->gcls); free(m->gh); free(m->ggeps);
     free(m->ring_off); free(m->ring); free(m->tri); free(m->edge);
     free(m->pnew); free(m->force); free(m->fsum); free(m->cen); free(m->area); free(m->qlevel);
+    free(m->tx); free(m->ty);
     free(m);
 }
 
@@ -1285,10 +1292,27 @@ int om_project_point(om_mesh* m, const double* p_old, int old_class, const doubl
 /* ------------------------------------------------------------------------ */
 /* one meshing iteration                                                    */
 /* ------------------------------------------------------------------------ */
-int om_step(om_mesh* m) {
+/* Eq. 3 scaling factor over the stored valid edges at the current positions
+ * (a DistMesh step that keeps the last triangulation, Algorithm 1) */
+static void fac_mu_current(om_mesh* m) {
+    double sl2 = 0, smu2 = 0;
+    for (int64_t e = 0; e < m->nedge; e++) {
+        int32_t i = m->edge[2 * e], j = m->edge[2 * e + 1];
+        double dx = m->x[j] - m->x[i], dy = m->y[j] - m->y[i];
+        double mu = bilin(&m->siz, (m->x[i] + m->x[j]) * 0.5, (m->y[i] + m->y[j]) * 0.5);
+        sl2 += dx * dx + dy * dy;
+        smu2 += mu * mu;
+    }
+    m->st.fac_mu = m->nedge > 0 ? sqrt(sl2 / smu2) : 1.0;
+}
+
+/* Procedure I, quality (Eqs. 11-12), the hybrid switch and the termination
+ * tests (Sec. 4), then the raw move; returns 1 if a termination test held
+ * (no move then). */
+static int triangulate_and_move(om_mesh* m) {
     om_rebuild(m);
-    m->st.newton_fail = m->st.trace_cap = m->st.quad_cap = 0;
-    m->st.small_moves = 0;
+    m->st.triangulated = 1;
+    for (int64_t i = 0; i < m->N; i++) { m->tx[i] = m->x[i]; m->ty[i] = m->y[i]; }
     double qa = m->st.half_mean_alpha, qb = m->st.half_mean_beta, qm = m->st.max_alpha;
     double ra = 1, rb = 1, rm = 1;
     if (m->have_prev) {
@@ -1317,7 +1341,27 @@ int om_step(om_mesh* m) {
         return 1;
     }
     if (method == 0) distmesh_move(m); else cvd_move(m);
-    int small = 1;
+    return 0;
+}
+
+/* Algorithm 1 (DistMesh): re-triangulate only when some point moved more
+ * than fac_retria h_i (h at its cell when triangulated) since the last
+ * triangulation; otherwise the springs act along the last triangulation's
+ * valid edges at the current positions (fac_mu from Eq. 3 at those
+ * positions), and neither quality nor the termination tests are evaluated. */
+int om_step(om_mesh* m) {
+    m->st.newton_fail = m->st.trace_cap = m->st.quad_cap = 0;
+    m->st.small_moves = 0;
+    if (m->P.method == 0 && m->P.fac_retria > 0 && !m->retri) {
+        fac_mu_current(m);
+        m->st.method_used = 0;
+        m->st.triangulated = 0;
+        m->st.terminated = 0;
+        distmesh_move(m);
+    } else if (triangulate_and_move(m)) {
+        return 1;
+    }
+    int small = 1, far = 0;
     for (int64_t i = 0; i < m->N; i++) {
         double po[2] = {m->x[i], m->y[i]}, pf[2];
         int32_t nc;
@@ -1325,12 +1369,15 @@ int om_step(om_mesh* m) {
         treat_point(m, po, oc, m->pnew + 2 * i, pf, &nc, &m->st.newton_fail, &m->st.trace_cap);
         double mv = hypot(pf[0] - po[0], pf[1] - po[1]);
         if (oc == PT_INNER && !(mv < m->P.fac_end * h_at(m, po[0], po[1]))) small = 0;
+        if (m->P.fac_retria > 0 && hypot(pf[0] - m->tx[i], pf[1] - m->ty[i]) > m->P.fac_retria * h_at(m, m->tx[i], m->ty[i]))
+            far = 1;
         m->dprev[i] = mv;
         m->x[i] = pf[0];
         m->y[i] = pf[1];
         m->cls[i] = (uint8_t)nc;
     }
     m->st.small_moves = small;
+    m->retri = m->P.method != 0 || !(m->P.fac_retria > 0) || far;
     return 0;
 }
 
@@ -1442,6 +1489,7 @@ void om_get_points(const om_mesh* m, double* xy) {
 }
 void om_set_points(om_mesh* m, const double* xy) {
     for (int64_t i = 0; i < m->N; i++) { m->x[i] = xy[2 * i]; m->y[i] = xy[2 * i + 1]; }
+    m->retri = 1;
 }
 void om_get_class(const om_mesh* m, uint8_t* c) { memcpy(c, m->cls, (size_t)m->N); }
 void om_set_class(om_mesh* m, const uint8_t* c) { memcpy(m->cls, c, (size_t)m->N); }

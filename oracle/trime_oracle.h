@@ -44,6 +44,7 @@ typedef struct {
     double fac_pt, fac_geps, fac_voro_bound, fac_end;
     double T_circ, T_switch, T_end_q, T_end_amax;
     double N_opt, eta, damping;
+    double fac_retria;         /* DistMesh re-triangulation threshold factor (Algorithm 1, App. B: 0.1); 0: every iteration */
 } om_params;
 
 typedef struct {
@@ -59,6 +60,7 @@ typedef struct {
     int32_t terminated;        /* termination test held (Sec. 4)         */
     int32_t switched;          /* hybrid has switched to CVD             */
     int32_t small_moves;       /* all inner moves < fac_end h_i          */
+    int32_t triangulated;      /* the step re-triangulated (Algorithm 1)  */
 } om_stats;
 
 typedef struct om_mesh om_mesh;
