@@ -69,6 +69,9 @@ typedef struct {
     double N_opt;            /* 3.3   points per bucket of the neighbour grid (Sec. 3.2)   */
     double eta;              /* 0.5   selected-boundary band factor (Sec. 3.5)             */
     double damping;          /* 1.0   Newton damping alpha-hat                             */
+    double fac_retria;       /* 0.1   DistMesh (method 0) re-triangulates only after some point
+                                      moved more than fac_retria*h_i since the last triangulation
+                                      (Algorithm 1); 0: every iteration                     */
 } mesh_params;
 
 /* Statistics of the last iteration run by mesh_step (or of mesh_rebuild). */
@@ -101,6 +104,7 @@ typedef struct {
     int64_t vor_cuts;          /* applications that changed a cell                        */
     int64_t vor_rings;         /* bucket rings scanned (summed over cells)                */
     int64_t vor_wide;          /* cells redone with 32 lanes                              */
+    int64_t triangulations;    /* iterations of the call that re-triangulated             */
 } mesh_stats;
 
 typedef struct mesh_s mesh_t;

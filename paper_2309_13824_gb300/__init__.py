@@ -46,7 +46,7 @@ class mesh_params(C.Structure):
                 ("k_spring", C.c_double), ("dt", C.c_double), ("fac_pt", C.c_double), ("fac_geps", C.c_double),
                 ("fac_voro_bound", C.c_double), ("fac_end", C.c_double), ("T_circ", C.c_double),
                 ("T_switch", C.c_double), ("T_end_q", C.c_double), ("T_end_amax", C.c_double),
-                ("N_opt", C.c_double), ("eta", C.c_double), ("damping", C.c_double)]
+                ("N_opt", C.c_double), ("eta", C.c_double), ("damping", C.c_double), ("fac_retria", C.c_double)]
 
 
 class mesh_stats(C.Structure):
@@ -58,7 +58,8 @@ class mesh_stats(C.Structure):
                 ("ring_overflow", C.c_int64), ("exact_overflow", C.c_int64), ("newton_fail", C.c_int64),
                 ("trace_cap", C.c_int64), ("quad_cap", C.c_int64), ("dup_points", C.c_int64),
                 ("small_moves", C.c_int32), ("target_reached", C.c_int32), ("vor_candidates", C.c_int64),
-                ("vor_picks", C.c_int64), ("vor_cuts", C.c_int64), ("vor_rings", C.c_int64), ("vor_wide", C.c_int64)]
+                ("vor_picks", C.c_int64), ("vor_cuts", C.c_int64), ("vor_rings", C.c_int64), ("vor_wide", C.c_int64),
+                ("triangulations", C.c_int64)]
 
 
 class mesh_tuning(C.Structure):

@@ -13,15 +13,16 @@
 
 namespace trime {
 
-// One thread per point.  In a batch, a mesh whose iterations have ended keeps
-// its sorted order: its slots all count into its pad bucket, so the offsets of
-// the meshes after it stay put; the padding slots of a live mesh count there too.
+// One thread per point.  In a batch, a mesh whose iterations have ended, or
+// that keeps its last triangulation this iteration, keeps its sorted order:
+// its slots all count into its pad bucket, so the offsets of the meshes after
+// it stay put; the padding slots of a live mesh count there too.
 template <typename T, bool B>
 __global__ void __launch_bounds__(kThreads) k_count(const __grid_constant__ IterArgs<T> a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const MeshView& V = mesh_of<B>(a, i);
-    bool term = !a.force && V.ctrl->terminated;
+    bool term = skip_rebuild(V.ctrl, a.force);
     if constexpr (B) {
         int loc = i - V.soff;
         if (term) {
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const __grid_constant__ It
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const MeshView& V = mesh_of<B>(a, i);
-    if (!a.force && V.ctrl->terminated) return;
+    if (skip_rebuild(V.ctrl, a.force)) return;
     if (B && i - V.soff >= V.n) return;
     int k = a.key[i];
     int d = a.bstart[k] + a.rank[i];
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_dups(const __grid_constant__ IterA
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     int sv = s < a.n ? s : a.n - 1;
     const MeshView& V = mesh_of<B>(a, sv);
-    if (!a.force && V.ctrl->terminated) return;
+    if (skip_rebuild(V.ctrl, a.force)) return;
     unsigned dup = 0;
     if (s < a.n && (!B || s - V.soff < V.n)) {
         int k = a.skey[s];

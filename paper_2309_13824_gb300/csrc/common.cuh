@@ -35,6 +35,7 @@ struct DevCounters {
     unsigned long long newton_fail, trace_cap, quad_cap, dup_points;
     // Voronoi work, counted only with debug recording on
     unsigned long long vor_candidates, vor_picks, vor_cuts, vor_rings, vor_wide;
+    unsigned long long triangulations;  // iterations that re-triangulated
 };
 
 // Per-block partial sums written by the emit kernel (a3/a4/a8 and Eq. 3 sums).
@@ -66,6 +67,8 @@ struct DevCtrl {
     double fac_mu;
     double target_min_ang;  // > 0: stop once the minimum angle reaches it
     int32_t target_reached;
+    int32_t retri;          // this iteration re-triangulates (DistMesh, Algorithm 1)
+    int32_t moved_far;      // some point moved more than fac_retria h_i since the triangulation
     int32_t pad1;
     double n_tri, n_edges, half_a, half_b, max_a, max_b, min_ang, size_dev;
     DevCounters cnt;
@@ -75,6 +78,7 @@ struct DevParams {
     int32_t bounded, validity, newton_max, trace_max, quad_max_level, debug;
     double fac_F, k_spring, dt, fac_pt, fac_geps, fac_voro_bound, fac_end, T_circ;
     double T_switch, T_end_q, T_end_amax, damping;
+    double fac_retria;  // DistMesh re-triangulation threshold factor (0: every iteration)
     double havg;
     // SDF box (domain box)
     double bx0, by0, bx1, by1;

@@ -280,7 +280,7 @@ __device__ __forceinline__ double warp_min_d(double v) {
 template <typename T, bool B>
 __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterArgs<T> a) {
     const MeshView& V = mesh_of<B>(a, blockIdx.x * kThreads);
-    if (!a.force && V.ctrl->terminated) return;
+    if (skip_rebuild(V.ctrl, a.force)) return;
     const bool cvd_now = V.ctrl->method_param == 1 || (V.ctrl->method_param == 2 && V.ctrl->switched);
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double acc[9] = {0, 0, 0, 0, 0, 180.0, 0, 0, 0};
@@ -402,6 +402,63 @@ void launch_emit(const IterArgs<T>& a, int nblocks, cudaStream_t st) {
     else k_emit<T, false><<<nblocks, kThreads, 0, st>>>(a);
 }
 template void launch_emit<double>(const IterArgs<double>&, int, cudaStream_t);
+
+// A DistMesh iteration that keeps the last triangulation (Algorithm 1): the
+// state this iteration moves is the current one (cur, slot order), and the
+// Eq. 3 sums run over the kept valid edges at the current positions; the
+// quality entries of the partials stay neutral.  One block per chunk.
+template <typename T, bool B>
+__global__ void __launch_bounds__(kThreads) k_dm_keep(const __grid_constant__ IterArgs<T> a) {
+    const MeshView& V = mesh_of<B>(a, blockIdx.x * kThreads);
+    if (V.ctrl->terminated || V.ctrl->retri) return;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[3] = {0, 0, 0};
+    if (s < a.n && (!B || s - V.soff < V.n)) {
+        T xi = a.cur.x[s], yi = a.cur.y[s];
+        a.wrk.x[s] = xi;
+        a.wrk.y[s] = yi;
+        a.wrk.cls[s] = a.cur.cls[s];
+        a.wrk.dprev[s] = a.cur.dprev[s];
+        int ne = a.ring_n[s];
+        uint32_t vm = a.vmask[s];
+        int idi = a.srt.id[s];
+        for (int t = 0; t < ne; t++) {
+            int j = a.ring[(size_t)s * kRingCap + t];
+            if (j < 0) continue;
+            int tp = t == 0 ? ne - 1 : t - 1;
+            if (!((vm >> t) & 1u) && !((vm >> tp) & 1u)) continue;
+            if (!(idi < a.srt.id[j])) continue;
+            T xj = a.cur.x[j], yj = a.cur.y[j];
+            T dx = xj - xi, dy = yj - yi;
+            T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
+            acc[0] += 1.0;
+            acc[1] += (double)(dx * dx + dy * dy);
+            acc[2] += (double)(mu * mu);
+        }
+    }
+    __shared__ double sh[kThreads / 32][3];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = 0; q < 3; q++) {
+        double v = warp_sum_d(acc[q]);
+        if (lane == 0) sh[w][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        int q = threadIdx.x;
+        double v = q == 5 ? 180.0 : 0.0;
+        if (q >= 6 && q < 9)
+            for (int k = 0; k < kThreads / 32; k++) v += sh[k][q - 6];
+        reinterpret_cast<double*>(&a.ep[blockIdx.x])[q] = v;
+    }
+}
+
+template <typename T>
+void launch_dm_keep(const IterArgs<T>& a, int nblocks, cudaStream_t st) {
+    if (a.Vs) k_dm_keep<T, true><<<nblocks, kThreads, 0, st>>>(a);
+    else k_dm_keep<T, false><<<nblocks, kThreads, 0, st>>>(a);
+}
+template void launch_dm_keep<double>(const IterArgs<double>&, int, cudaStream_t);
+template void launch_dm_keep<float>(const IterArgs<float>&, int, cudaStream_t);
 template void launch_emit<float>(const IterArgs<float>&, int, cudaStream_t);
 
 // ------------------------------------------------------------------ triangle output

@@ -58,6 +58,7 @@ struct IterArgs {
     const int32_t* cmesh;   // [n / kChunk] mesh of each chunk
     int32_t* ovf_n;    // cells queued for the 32-lane Voronoi pass
     State<T> cur, srt;
+    State<T> wrk;      // the positions a DistMesh iteration without re-triangulation moves (slot order)
     int32_t* cell;     // [n] geometry cell of each sorted slot (fixed formula)
     int32_t* key;      // [n] bucket of each cur point
     int32_t* rank;     // [n] rank inside its bucket
@@ -77,6 +78,12 @@ struct IterArgs {
     float4* pf;        // [n] sorted positions as float pairs (xhi, xlo, yhi, ylo)
     float* pS;         // [n] octagon span S = fac_voro_bound * h of each sorted slot
 };
+
+// the rebuild kernels of an iteration run unless the mesh has terminated or
+// keeps its last triangulation (a forced rebuild always runs)
+__device__ __forceinline__ bool skip_rebuild(const DevCtrl* c, int force) {
+    return !force && (c->terminated || !c->retri);
+}
 
 // the mesh owning a slot: the launch's own view, or the batch table entry of
 // the slot's chunk
@@ -98,6 +105,9 @@ inline void launch_voronoi(const IterArgs<T>& a, int lanes, cudaStream_t st) {
 }
 // a3/a4 + quality partials (a8) + Eq. 3 sums
 template <typename T> void launch_emit(const IterArgs<T>& a, int nblocks, cudaStream_t st);
+// a DistMesh iteration that keeps the last triangulation (Algorithm 1): the
+// current positions into wrk and the Eq. 3 sums over the kept valid edges
+template <typename T> void launch_dm_keep(const IterArgs<T>& a, int nblocks, cudaStream_t st);
 // a8 finalisation + hybrid / termination logic
 template <typename T> void launch_stats_pre(const IterArgs<T>& a, int decide, cudaStream_t st);
 // a5/a6/a7

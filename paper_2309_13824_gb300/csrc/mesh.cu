@@ -78,6 +78,9 @@ struct mesh_s {
     cudaStream_t user = nullptr, st = nullptr;
     cudaEvent_t ev = nullptr;
     void *cx = nullptr, *cy = nullptr, *cdp = nullptr, *sx = nullptr, *sy = nullptr, *sdp = nullptr;
+    void *wx = nullptr, *wy = nullptr, *wdp = nullptr;  // DistMesh iterations that keep the triangulation
+    uint8_t* wcls = nullptr;
+    bool tri_stale = false;  // the sorted order no longer matches the triangulation
     int32_t *cid = nullptr, *sid = nullptr;
     uint8_t *ccls = nullptr, *scls = nullptr;
     int32_t *cell = nullptr, *key = nullptr, *rank = nullptr, *skey = nullptr;
@@ -347,6 +350,7 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.ovf_n = m->ovf_n;
     a.cur = {(T*)m->cx, (T*)m->cy, m->cid, m->ccls, (T*)m->cdp};
     a.srt = {(T*)m->sx, (T*)m->sy, m->sid, m->scls, (T*)m->sdp};
+    a.wrk = {(T*)m->wx, (T*)m->wy, m->sid, m->wcls, (T*)m->wdp};
     a.cell = m->cell;
     a.key = m->key;
     a.rank = m->rank;
@@ -379,8 +383,12 @@ static void enqueue_rebuild(mesh_s* m, int force, int decide) {
 
 template <typename T>
 static void enqueue_iteration(mesh_s* m) {
-    enqueue_rebuild<T>(m, 0, 1);
     IterArgs<T> a = make_args<T>(m, 0);
+    launch_bucket<T>(a, m->st);
+    launch_voronoi<T>(a, m->lanes, m->st);
+    launch_emit<T>(a, m->nblk, m->st);
+    launch_dm_keep<T>(a, m->nblk, m->st);  // runs instead of the three above when the triangulation is kept
+    launch_stats_pre<T>(a, 1, m->st);
     launch_update<T>(a, m->nblk, m->st);
     launch_stats_post<T>(a, m->st);
 }
@@ -450,6 +458,7 @@ static void fill_stats(const mesh_s* m, int k, int iters, mesh_stats* s) {
     s->vor_cuts = (int64_t)c.cnt.vor_cuts;
     s->vor_rings = (int64_t)c.cnt.vor_rings;
     s->vor_wide = (int64_t)c.cnt.vor_wide;
+    s->triangulations = (int64_t)c.cnt.triangulations;
 }
 
 static bool guard_tripped(const mesh_s* m) {
@@ -463,6 +472,20 @@ static bool guard_tripped(const mesh_s* m) {
 __global__ void k_reset_counters(DevCtrl* ctrl, int n) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) ctrl[k].cnt = DevCounters{};
+}
+
+// the next iteration of part k (all parts for k < 0) re-triangulates: the
+// sorted order or the positions changed outside an iteration
+__global__ void k_force_retri(DevCtrl* ctrl, int lo, int hi) {
+    int k = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < hi) ctrl[k].retri = 1;
+}
+
+static int force_retri(mesh_s* m, int k) {
+    int lo = k < 0 ? 0 : k, hi = k < 0 ? (int)m->parts.size() : k + 1;
+    k_force_retri<<<(hi - lo + 127) / 128, 128, 0, m->st>>>(m->ctrl, lo, hi);
+    CUDA_TRY(cudaGetLastError());
+    return 0;
 }
 
 static int reset_counters(mesh_s* m) {
@@ -528,6 +551,7 @@ static void fill_devparams(DevParams& d, const mesh_params& P, const HostGeometr
     d.T_end_q = P.T_end_q;
     d.T_end_amax = P.T_end_amax;
     d.damping = P.damping;
+    d.fac_retria = P.fac_retria;
     d.havg = G.havg;
     d.bx0 = sdf->x0;
     d.by0 = sdf->y0;
@@ -599,6 +623,7 @@ static int upload_part(mesh_s* m, int k, const mesh_grid2d* sdf, const mesh_grid
     std::memset(&c0, 0, sizeof c0);
     c0.method_param = m->P.method;
     c0.last_method = -1;
+    c0.retri = 1;
     ok = ok && H2D(m->ctrl + k, &c0, sizeof c0);
     // the host vectors above must outlive the copies
     if (!ok || cudaStreamSynchronize(m->st) != cudaSuccess) return fail(TRIME_ECUDA, "initial upload failed");
@@ -712,6 +737,10 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->sx = dalloc<char>(m, N * T, rc);
     m->sy = dalloc<char>(m, N * T, rc);
     m->sdp = dalloc<char>(m, N * T, rc);
+    m->wx = dalloc<char>(m, N * T, rc);
+    m->wy = dalloc<char>(m, N * T, rc);
+    m->wdp = dalloc<char>(m, N * T, rc);
+    m->wcls = dalloc<uint8_t>(m, N, rc);
     m->cid = dalloc<int32_t>(m, N, rc);
     m->sid = dalloc<int32_t>(m, N, rc);
     m->ccls = dalloc<uint8_t>(m, N, rc);
@@ -784,6 +813,8 @@ static int do_rebuild(mesh_s* m, mesh_stats* stats) {
     if (rc) return rc;
     if ((rc = reset_counters(m))) return rc;
     enqueue(m, false, 1);
+    if ((rc = force_retri(m, -1))) return rc;  // cur keeps the previous sorted order
+    m->tri_stale = false;
     CUDA_TRY(cudaGetLastError());
     if ((rc = read_ctrl(m))) return rc;
     if ((rc = sync_out(m))) return rc;
@@ -804,6 +835,7 @@ static int do_step(mesh_s* m, int32_t n_iters, mesh_stats* stats) {
     std::vector<int> start(np);
     for (size_t k = 0; k < np; k++) start[k] = m->hctrl[k].iterations;
     if (!all_terminated(m)) {
+        if (n_iters > 0) m->tri_stale = false;  // the first iteration re-triangulates
         for (int32_t k = 0; k < n_iters; k++) {
             CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
             if ((k & 31) == 31 || (stats && k == n_iters - 1)) {
@@ -833,6 +865,11 @@ static int get_triangles(mesh_s* m, int k, int32_t* tri, int64_t cap, int64_t* n
     const Part& p = m->parts[k];
     int rc = sync_in(m);
     if (rc) return rc;
+    if (m->tri_stale) {
+        enqueue(m, false, 1);
+        if ((rc = force_retri(m, -1))) return rc;
+        m->tri_stale = false;
+    }
     int32_t total = 0;
     if (p.n > 0) {
         if (m->prec == 0) launch_tri_count<double>(make_args<double>(m, 1), p.soff, (int32_t)p.n, m->tcnt, m->st);
@@ -905,6 +942,7 @@ static int set_state(mesh_s* m, int k, const void* xy, const uint8_t* cls, const
         launch_set_state<float>(make_args<float>(m, 1), p.soff, (int32_t)N, xy ? (const float*)sxy : nullptr,
                                 cls ? scls : nullptr, dprev ? sdp : nullptr, m->st);
     CUDA_TRY(cudaGetLastError());
+    if ((rc = force_retri(m, k))) return rc;
     CUDA_TRY(cudaStreamSynchronize(m->st));
     return sync_out(m);
 }
@@ -921,6 +959,7 @@ static int set_method_state(mesh_s* m, int k, int32_t switched, double pa, doubl
     c.prev_amax = pm;
     c.terminated = 0;
     c.small_moves = 0;
+    c.retri = 1;
     CUDA_TRY(cudaMemcpyAsync(m->ctrl + k, &c, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
     CUDA_TRY(cudaStreamSynchronize(m->st));
     return sync_out(m);
@@ -935,6 +974,7 @@ static int profile_stages(mesh_s* m, cudaEvent_t* ev) {
     launch_voronoi<T>(a, m->lanes, m->st);
     CUDA_TRY(cudaEventRecord(ev[2], m->st));
     launch_emit<T>(a, m->nblk, m->st);
+    launch_dm_keep<T>(a, m->nblk, m->st);
     CUDA_TRY(cudaEventRecord(ev[3], m->st));
     launch_stats_pre<T>(a, 1, m->st);
     CUDA_TRY(cudaEventRecord(ev[4], m->st));
@@ -1057,6 +1097,8 @@ static void snapshot(mesh_s* m) {
 static void features_any(mesh_s* m, uint16_t* X, float* H, void* px, void* py, int by_id, float mflag) {
     if (m->prec == 0) enqueue_features<double>(m, X, H, px, py, by_id, mflag);
     else enqueue_features<float>(m, X, H, px, py, by_id, mflag);
+    force_retri(m, -1);  // the sort above no longer matches the triangulation
+    m->tri_stale = true;
 }
 
 static int check_net_err(mesh_s* m, mlp_s* net) {
@@ -1102,6 +1144,7 @@ static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every
     if (rc) return rc;
     if ((rc = ensure_learn(m)) || (rc = reset_counters(m)) || (rc = read_ctrl(m))) return rc;
     int start = m->hctrl[0].iterations, acc = 0, rej = 0;
+    if (n_iters > 0 && !m->hctrl[0].terminated) m->tri_stale = false;
     for (int32_t k = 0; k < n_iters && !m->hctrl[0].terminated; k++) {
         if (k > 0 && k % every == 0 && m->nslots > 0 && (max_props <= 0 || acc + rej < max_props)) {
             if ((rc = read_ctrl(m))) return rc;
@@ -1117,7 +1160,7 @@ static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every
                 acc++;
             } else {
                 rej++;
-                if ((rc = copy_state(m, false))) return rc;
+                if ((rc = copy_state(m, false)) || (rc = force_retri(m, 0))) return rc;
                 m->learn->have_q = false;  // the last move is unknown after the restore
                 DevCtrl c = before;
                 c.iterations = after.iterations;
@@ -1168,6 +1211,7 @@ void mesh_default_params(mesh_params* p) {
     p->N_opt = 3.3;
     p->eta = 0.5;
     p->damping = 1.0;
+    p->fac_retria = 0.1;
 }
 
 const char* mesh_last_error(void) { return g_err.c_str(); }

@@ -206,15 +206,22 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
     const MeshView& V = mesh_of<B>(a, blockIdx.x * kThreads);
     if (V.ctrl->terminated) return;
     const DevParams& P = V.P;
+    // a DistMesh iteration that keeps the last triangulation moves the current
+    // state (copied to wrk); otherwise the state sorted at the triangulation
+    const bool keep = !V.ctrl->retri;
+    const T* IX = keep ? a.wrk.x : a.srt.x;
+    const T* IY = keep ? a.wrk.y : a.srt.y;
+    const bool track = P.fac_retria > 0.0 && V.ctrl->method_param == 0;
+    unsigned moved = 0;
     int method = V.ctrl->method_now;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     double dev = 0, nedge = 0, notsmall = 0;
     unsigned long long nfail = 0, tcap = 0, qcap = 0;
     if (s < a.n && (!B || s - V.soff < V.n)) {
-        T xi = a.srt.x[s], yi = a.srt.y[s];
+        T xi = IX[s], yi = IY[s];
         int idi = a.srt.id[s];
-        int ocls = a.srt.cls[s];
-        T dprev = a.srt.dprev[s];
+        int ocls = keep ? a.wrk.cls[s] : a.srt.cls[s];
+        T dprev = keep ? a.wrk.dprev[s] : a.srt.dprev[s];
         T h = (T)V.gh[a.cell[s]];
         int ne = a.ring_n[s];
         uint32_t vm = a.vmask[s];
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
                 }
                 continue;
             }
-            T xj = a.srt.x[j], yj = a.srt.y[j];
+            T xj = IX[j], yj = IY[j];
             T dx = xi - xj, dy = yi - yj;
             T l2 = dx * dx + dy * dy;
             T r = rsqrt(l2);  // 1 / l: one reciprocal square root instead of a root and a division
@@ -283,6 +290,11 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
         T fx, fy;
         int ncls;
         treat_move<T>(V, xi, yi, ocls, pnx, pny, (T)P.fac_pt * h, fx, fy, ncls, tcap, nfail);
+        if (track) {
+            // Algorithm 1: distance from the position at the last triangulation
+            T ex = fx - a.srt.x[s], ey = fy - a.srt.y[s];
+            if (sqrt(ex * ex + ey * ey) > (T)P.fac_retria * h) moved = 1;
+        }
         T mvx = fx - xi, mvy = fy - yi;
         T mv = sqrt(mvx * mvx + mvy * mvy);
         if (ocls == PT_INNER && !(mv < (T)P.fac_end * h)) notsmall = 1.0;
@@ -305,6 +317,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
             a.dbg[9 * n + id] = (double)qlv;
         }
     }
+    if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) V.ctrl->moved_far = 1;
     unsigned m = __ballot_sync(0xffffffffu, nfail != 0);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&V.ctrl->cnt.newton_fail, (unsigned long long)__popc(m));
     m = __ballot_sync(0xffffffffu, tcap != 0);
@@ -364,6 +377,16 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_pre(const __grid_constan
     double qa = n > 0 ? (sh[0][1] / n) * (sh[0][1] / n) : 0.0;
     double qb = n > 0 ? (sh[0][2] / n) * (sh[0][2] / n) : 0.0;
     double qm = sh[0][3];
+    if (!a.force && !ctrl->retri) {
+        // the iteration keeps the last triangulation: only fac_mu (Eq. 3, at
+        // the current positions) changes; no quality, no decision
+        ctrl->fac_mu = sh[0][6] > 0 ? sqrt(sh[0][7] / sh[0][8]) : 1.0;
+        ctrl->method_now = 0;
+        ctrl->last_method = 0;
+        ctrl->iterations += 1;
+        return;
+    }
+    if (decide) ctrl->cnt.triangulations += 1;
     ctrl->n_tri = n;
     ctrl->half_a = qa;
     ctrl->half_b = qb;
@@ -433,6 +456,9 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_post(const __grid_consta
     int small = sh[0][2] == 0.0;
     ctrl->small_moves = small;
     if (small) ctrl->terminated = 1;  // Sec. 4: every inner move below fac_end * h_i
+    // Algorithm 1: DistMesh re-triangulates after a large movement only
+    ctrl->retri = ctrl->method_param != 0 || !(V.P.fac_retria > 0.0) || ctrl->moved_far;
+    ctrl->moved_far = 0;
 }
 
 template <typename T>

@@ -437,7 +437,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
 // of a warp lie in one chunk, hence in one mesh.
 template <typename T, int G, bool B>
 __global__ void __launch_bounds__(kVoroThreads, 8) k_voronoi(const __grid_constant__ IterArgs<T> a) {
-    if (!B && !a.force && a.V.ctrl->terminated) return;
+    if (!B && skip_rebuild(a.V.ctrl, a.force)) return;
     __shared__ float4 stage_all[kVoroThreads / G][kStageCap];
     Grp<G> g;
     int lane = threadIdx.x & 31;
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kVoroThreads, 8) k_voronoi(const __grid_consta
     float4* stage = stage_all[threadIdx.x / G];
     for (int w = blockIdx.x * (kVoroThreads / 32) + wib; w * cpw < a.n; w += nwarps) {
         const MeshView& V = mesh_of<B>(a, w * cpw);
-        if (B && !a.force && V.ctrl->terminated) continue;
+        if (B && skip_rebuild(V.ctrl, a.force)) continue;
         int s = w * cpw + lane / G;
         bool ok = s < a.n && (!B || s - V.soff < V.n);
         voronoi_cell<T, G>(a, V, ok ? s : -1, g, stage);
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kVoroThreads, 8) k_voronoi(const __grid_consta
 // 32-lane pass over the cells the 16-lane pass could not hold
 template <typename T, bool B>
 __global__ void __launch_bounds__(kVoroThreads) k_voronoi_wide(const __grid_constant__ IterArgs<T> a) {
-    if (!B && !a.force && a.V.ctrl->terminated) return;
+    if (!B && skip_rebuild(a.V.ctrl, a.force)) return;
     __shared__ float4 stage_all[kVoroThreads / 32][kStageCap];
     Grp<32> g;
     g.gl = threadIdx.x & 31;

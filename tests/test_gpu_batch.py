@@ -154,11 +154,11 @@ def test_batch_set_state_resumes_one_mesh():
     import paper_2309_13824_gb300 as g
 
     meshes = _mixed_meshes()
-    b = g.MeshBatch(meshes, method=0, autotune=False)
+    b = g.MeshBatch(meshes, method=0, autotune=False, fac_retria=0.0)
     b.step(3)
     k = 1
     s, z, p = meshes[k]
-    om = oracle.OracleMesh(s, z, p, method=0)
+    om = oracle.OracleMesh(s, z, p, method=0, fac_retria=0.0)
     om.step()
     om.step()
     b.set_state(k, om.points(), om.classes(), om.dprev())
@@ -192,3 +192,27 @@ def test_batch_full_size_stars():
         assert np.array_equal(tg, to), int(k)
     b.step(3)
     assert all(s["n_tri"] > 0 for s in b.step(1))
+
+
+def test_batch_distmesh_keeps_triangulations_per_mesh():
+    # each mesh of a batch decides its own re-triangulations (Algorithm 1)
+    import paper_2309_13824_gb300 as g
+
+    # smooth shapes: the star's spike tips make unsynchronised trajectories
+    # diverge exponentially (a projection near a corner amplifies rounding)
+    mixed = _mixed_meshes()
+    meshes = [mixed[0], mixed[1], mixed[5]]
+    b = g.MeshBatch(meshes, method=0, autotune=False)
+    oms = [oracle.OracleMesh(s, z, p, method=0) for s, z, p in meshes]
+    kept = 0
+    for step in range(40):
+        st = b.step(1)
+        for k, om in enumerate(oms):
+            if st[k]["iterations"] == 0:
+                continue  # this mesh has terminated
+            so = om.step()
+            assert st[k]["triangulations"] == so["triangulated"], (step, k)
+            kept += 1 - so["triangulated"]
+            err = np.linalg.norm(b.points(k) - om.points(), axis=1) / h_of_points(om, om.points())
+            assert err.max() < 1e-6, (step, k, err.max())  # compounding step rounding
+    assert kept > 0
