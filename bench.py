@@ -325,6 +325,30 @@ def sweep_leg(g, torch, stream, steps, flush):
     return out
 
 
+def distmesh_leg(g, torch, stream):
+    """The DistMesh method (config 1's disk at 1e4 points and the annulus at
+    1e6) to termination, re-triangulating every iteration and only after large
+    movements (Algorithm 1, fac_retria = 0.1)."""
+    import workloads as W
+
+    out = {}
+    for name, wl in (("disk_1e4", W.disk_workload(n=10000)), ("annulus_1e6", W.annulus_workload(n=1_000_000))):
+        rec = {}
+        for fac in (0.0, 0.1):
+            m = g.Mesh(wl.sdf, wl.sizing, wl.points, method=0, fac_retria=fac, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = m.step(2000)
+            torch.cuda.synchronize()
+            rec[f"fac_retria_{fac}"] = {"seconds": time.perf_counter() - t0, "iterations": s["iterations"],
+                                        "triangulations": s["triangulations"], "terminated": bool(s["terminated"]),
+                                        "min_angle_deg": s["min_angle_deg"], "half_mean_alpha": s["half_mean_alpha"],
+                                        "max_alpha": s["max_alpha"]}
+            m.close()
+        out[name] = rec
+    return out
+
+
 def learned_leg(g, stream):
     """The learned displacement model: trained on the device on trajectories of
     the disk (DistMesh, 1e4 points) and the benchmark annulus (hybrid, 1e6),
@@ -505,6 +529,7 @@ def main():
             fm.close()
         extras["batched"] = batched_leg(g, torch, stream, args.steps, flush)
         extras["learned"] = learned_leg(g, stream)
+        extras["distmesh"] = distmesh_leg(g, torch, stream)
         if args.sweep:
             extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
         threads = os.cpu_count() or 1

@@ -436,7 +436,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
 // main pass: G lanes per cell, 32 / G cells per warp.  In a batch the cells
 // of a warp lie in one chunk, hence in one mesh.
 template <typename T, int G, bool B>
-__global__ void __launch_bounds__(kVoroThreads, 8) k_voronoi(const __grid_constant__ IterArgs<T> a) {
+__global__ void __launch_bounds__(kVoroThreads, 7) k_voronoi(const __grid_constant__ IterArgs<T> a) {
     if (!B && skip_rebuild(a.V.ctrl, a.force)) return;
     __shared__ float4 stage_all[kVoroThreads / G][kStageCap];
     Grp<G> g;
