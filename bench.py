@@ -366,25 +366,36 @@ def learned_leg(g, stream):
     out = {"training": {"pairs": npairs, "last_epoch_loss": loss, "seconds": time.perf_counter() - t0,
                         "trajectories": "disk 1e4 DistMesh FP64 (seed 0) + annulus 1e6 hybrid FP64 (seed 1), "
                                         "pairs every 11 iterations, horizon 10, 40+10 epochs Adam"},
-           "policy": {"every": 10, "jump": 10.0, "min_angle_tol": 1.0, "max_proposals": 5}}
+           "policy": {"every": 5, "jump": 5.0, "min_angle_tol": 1.0, "max_proposals": 8,
+                      "judge": "proposal branch kept only if it beats the plain iteration from the same state"}}
     star = W.star_workload(1_000_000, sdf_n=2048, siz_n=512, workers=min(16, os.cpu_count() or 1))
     for name, wl, prec in (("annulus_1e6_fp64", ann, 0), ("star500_1e6_fp32", star, 1)):
         pts = wl.points if prec == 0 else W.to_fp32_positions(wl.points)
         tc, conv = learn.time_to_quality(wl.sdf, wl.sizing, pts, precision=prec, stream=st)
         q = conv["min_angle_deg"] - 1.0
         tp, sp = learn.time_to_quality(wl.sdf, wl.sizing, pts, precision=prec, target=q, stream=st)
-        tl, sl = learn.time_to_quality(wl.sdf, wl.sizing, pts, net=net, precision=prec, target=q, stream=st)
+        def guarded(**kw):
+            try:
+                return learn.time_to_quality(wl.sdf, wl.sizing, pts, net=net, precision=prec, stream=st, **kw)
+            except g.MeshError as e:  # reported, not fatal to the benchmark
+                return None, {"error": str(e)}
+
+        tl, sl = guarded(target=q)
 
         def rec(t, s):
+            if t is None:
+                return dict(s)
             return {"seconds": t, "iterations": s["iterations"], "target_reached": bool(s["target_reached"]),
                     "min_angle_deg": s["min_angle_deg"], "half_mean_alpha": s["half_mean_alpha"],
                     "max_alpha": s["max_alpha"], "mean_size_dev": s["mean_size_dev"]}
 
         lr = rec(tl, sl)
-        lr.update({"proposals_kept": sl["accepted"], "proposals_undone": sl["rejected"]})
-        tlc, slc = learn.time_to_quality(wl.sdf, wl.sizing, pts, net=net, precision=prec, stream=st)
+        if tl is not None:
+            lr.update({"proposals_kept": sl["accepted"], "proposals_undone": sl["rejected"]})
+        tlc, slc = guarded()
         lc = rec(tlc, slc)
-        lc.update({"proposals_kept": slc["accepted"], "proposals_undone": slc["rejected"]})
+        if tlc is not None:
+            lc.update({"proposals_kept": slc["accepted"], "proposals_undone": slc["rejected"]})
         out[name] = {"plain_converged": rec(tc, conv), "learned_converged": lc, "target_min_angle_deg": q,
                      "plain_to_target": rec(tp, sp), "learned_to_target": lr}
     return out

@@ -312,11 +312,11 @@ int mesh_collect_pairs(mesh_t* m, int32_t horizon, uint16_t* X, float* T);
 int mesh_propose(mesh_t* m, mlp_t* net, double jump);
 
 /* mesh_step with a proposal before every `every`-th iteration (every >= 1):
- * the state is saved, the proposal applied and one plain iteration run from
- * it; the proposal is kept if that iteration's quality is at least as good as
- * the last one before it (1/2-mean of alpha not larger, minimum angle not
- * smaller by more than min_angle_tol degrees), otherwise the saved state is
- * restored.  At most max_proposals proposals are made (<= 0: no limit);
+ * from the same state, one plain iteration and the proposal followed by one
+ * plain iteration both run; the proposal branch is kept if its quality beats
+ * the plain branch's (1/2-mean of alpha smaller, minimum angle not smaller by
+ * more than min_angle_tol degrees, no capacity guard tripped), otherwise the
+ * plain branch's state is restored.  Both branches count as iterations.  At most max_proposals proposals are made (<= 0: no limit);
  * the iterations after the last one are plain.  *accepted / *rejected (may be
  * NULL) count the proposals.  Statistics and termination as mesh_step (stats
  * may not be NULL). */

@@ -119,9 +119,10 @@ struct LearnBufs {
     void *px = nullptr, *py = nullptr;                      // positions by id
     void *qx = nullptr, *qy = nullptr;                      // positions by id before the last iteration
     bool have_q = false;
-    void *bx = nullptr, *by = nullptr, *bdp = nullptr;      // saved cur state
-    int32_t* bid = nullptr;
-    uint8_t* bcls = nullptr;
+    // two saved cur states: the start of a proposal and the plain branch
+    void *bx[2] = {nullptr, nullptr}, *by[2] = {nullptr, nullptr}, *bdp[2] = {nullptr, nullptr};
+    int32_t* bid[2] = {nullptr, nullptr};
+    uint8_t* bcls[2] = {nullptr, nullptr};
 };
 
 namespace trime {
@@ -462,11 +463,15 @@ static void fill_stats(const mesh_s* m, int k, int iters, mesh_stats* s) {
 }
 
 static bool guard_tripped(const mesh_s* m) {
+    unsigned long long ro = 0, eo = 0;
     for (size_t k = 0; k < m->parts.size(); k++) {
-        const DevCounters& c = m->hctrl[k].cnt;
-        if (c.ring_overflow || c.exact_overflow) return true;
+        ro += m->hctrl[k].cnt.ring_overflow;
+        eo += m->hctrl[k].cnt.exact_overflow;
     }
-    return false;
+    if (!ro && !eo) return false;
+    fail(TRIME_EDEVICE, "capacity guard tripped: " + std::to_string(ro) + " cells with more than 32 edges, " +
+                            std::to_string(eo) + " exact-arithmetic capacity or underflow guards");
+    return true;
 }
 
 __global__ void k_reset_counters(DevCtrl* ctrl, int n) {
@@ -820,7 +825,7 @@ static int do_rebuild(mesh_s* m, mesh_stats* stats) {
     if ((rc = sync_out(m))) return rc;
     if (stats)
         for (size_t k = 0; k < m->parts.size(); k++) fill_stats(m, (int)k, 0, &stats[k]);
-    if (guard_tripped(m)) return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
+    if (guard_tripped(m)) return TRIME_EDEVICE;
     return TRIME_OK;
 }
 
@@ -848,7 +853,7 @@ static int do_step(mesh_s* m, int32_t n_iters, mesh_stats* stats) {
     if ((rc = read_ctrl(m))) return rc;
     if ((rc = sync_out(m))) return rc;
     for (size_t k = 0; k < np; k++) fill_stats(m, (int)k, m->hctrl[k].iterations - start[k], &stats[k]);
-    if (guard_tripped(m)) return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
+    if (guard_tripped(m)) return TRIME_EDEVICE;
     return TRIME_OK;
 }
 
@@ -1056,11 +1061,13 @@ static int ensure_learn(mesh_s* m) {
     L->py = dalloc<char>(m, N * T, rc);
     L->qx = dalloc<char>(m, N * T, rc);
     L->qy = dalloc<char>(m, N * T, rc);
-    L->bx = dalloc<char>(m, N * T, rc);
-    L->by = dalloc<char>(m, N * T, rc);
-    L->bdp = dalloc<char>(m, N * T, rc);
-    L->bid = dalloc<int32_t>(m, N, rc);
-    L->bcls = dalloc<uint8_t>(m, N, rc);
+    for (int b = 0; b < 2; b++) {
+        L->bx[b] = dalloc<char>(m, N * T, rc);
+        L->by[b] = dalloc<char>(m, N * T, rc);
+        L->bdp[b] = dalloc<char>(m, N * T, rc);
+        L->bid[b] = dalloc<int32_t>(m, N, rc);
+        L->bcls[b] = dalloc<uint8_t>(m, N, rc);
+    }
     if (rc) {
         delete L;
         return rc;
@@ -1124,17 +1131,24 @@ static int enqueue_propose(mesh_s* m, mlp_s* net, double jump) {
     return 0;
 }
 
-static int copy_state(mesh_s* m, bool save) {
+static int copy_state(mesh_s* m, bool save, int b) {
     LearnBufs* L = m->learn;
     size_t N = (size_t)m->nslots, T = m->prec == 0 ? sizeof(double) : sizeof(float);
     auto cp = [&](void* cur, void* bak, size_t bytes) {
         return cudaMemcpyAsync(save ? bak : cur, save ? cur : bak, bytes, cudaMemcpyDeviceToDevice, m->st);
     };
-    CUDA_TRY(cp(m->cx, L->bx, N * T));
-    CUDA_TRY(cp(m->cy, L->by, N * T));
-    CUDA_TRY(cp(m->cdp, L->bdp, N * T));
-    CUDA_TRY(cp(m->cid, L->bid, N * sizeof(int32_t)));
-    CUDA_TRY(cp(m->ccls, L->bcls, N));
+    CUDA_TRY(cp(m->cx, L->bx[b], N * T));
+    CUDA_TRY(cp(m->cy, L->by[b], N * T));
+    CUDA_TRY(cp(m->cdp, L->bdp[b], N * T));
+    CUDA_TRY(cp(m->cid, L->bid[b], N * sizeof(int32_t)));
+    CUDA_TRY(cp(m->ccls, L->bcls[b], N));
+    return 0;
+}
+
+static int write_ctrl0(mesh_s* m, const DevCtrl& c) {
+    *m->hctrl = c;
+    CUDA_TRY(cudaMemcpyAsync(m->ctrl, m->hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
     return 0;
 }
 
@@ -1147,28 +1161,46 @@ static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every
     if (n_iters > 0 && !m->hctrl[0].terminated) m->tri_stale = false;
     for (int32_t k = 0; k < n_iters && !m->hctrl[0].terminated; k++) {
         if (k > 0 && k % every == 0 && m->nslots > 0 && (max_props <= 0 || acc + rej < max_props)) {
+            // two branches from the same state: one plain iteration, and the
+            // proposal followed by one plain iteration; the better one stays
             if ((rc = read_ctrl(m))) return rc;
             if (m->hctrl[0].terminated) break;
             DevCtrl before = m->hctrl[0];
-            if ((rc = copy_state(m, true)) || (rc = enqueue_propose(m, net, jump))) return rc;
+            // plain branch (the last-move snapshot stays that of the saved state)
+            if ((rc = copy_state(m, true, 0))) return rc;
+            CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+            if ((rc = read_ctrl(m))) return rc;
+            DevCtrl plain = m->hctrl[0];
+            // proposal branch from the saved state
+            if ((rc = copy_state(m, true, 1)) || (rc = copy_state(m, false, 0)) || (rc = force_retri(m, 0))) return rc;
+            DevCtrl c0 = before;
+            c0.iterations = plain.iterations;
+            c0.cnt = plain.cnt;
+            c0.retri = 1;
+            if ((rc = write_ctrl0(m, c0)) || (rc = enqueue_propose(m, net, jump))) return rc;
             snapshot(m);
             CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
             if ((rc = check_net_err(m, net)) || (rc = read_ctrl(m))) return rc;
             const DevCtrl& after = m->hctrl[0];
-            bool ok = after.n_tri > 0 && after.half_a <= before.half_a && after.min_ang >= before.min_ang - tol;
+            // a proposal whose judged iteration tripped a capacity guard loses too
+            bool guard = after.cnt.ring_overflow > plain.cnt.ring_overflow ||
+                         after.cnt.exact_overflow > plain.cnt.exact_overflow;
+            bool ok = !guard && after.n_tri > 0 && after.half_a < plain.half_a &&
+                      after.min_ang >= plain.min_ang - tol;
             if (ok) {
                 acc++;
             } else {
                 rej++;
-                if ((rc = copy_state(m, false)) || (rc = force_retri(m, 0))) return rc;
+                if ((rc = copy_state(m, false, 1)) || (rc = force_retri(m, 0))) return rc;
                 m->learn->have_q = false;  // the last move is unknown after the restore
-                DevCtrl c = before;
+                DevCtrl c = plain;
                 c.iterations = after.iterations;
                 c.cnt = after.cnt;
-                c.terminated = 0;
-                *m->hctrl = c;
-                CUDA_TRY(cudaMemcpyAsync(m->ctrl, m->hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
-                CUDA_TRY(cudaStreamSynchronize(m->st));
+                c.cnt.ring_overflow = plain.cnt.ring_overflow;  // belonged to the discarded branch
+                c.cnt.exact_overflow = plain.cnt.exact_overflow;
+                c.cnt.clip_inconsistent = plain.cnt.clip_inconsistent;
+                c.retri = 1;
+                if ((rc = write_ctrl0(m, c))) return rc;
             }
             continue;
         }
@@ -1180,7 +1212,7 @@ static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every
     fill_stats(m, 0, m->hctrl[0].iterations - start, stats);
     if (accepted) *accepted = acc;
     if (rejected) *rejected = rej;
-    if (guard_tripped(m)) return fail(TRIME_EDEVICE, "capacity guard tripped (ring or exact-arithmetic overflow)");
+    if (guard_tripped(m)) return TRIME_EDEVICE;
     return TRIME_OK;
 }
 
