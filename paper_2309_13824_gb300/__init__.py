@@ -374,7 +374,7 @@ class Mesh:
     def propose(self, net: "MLP", jump: float = 4.0):
         _check(lib().mesh_propose(self._h, net._h, jump))
 
-    def step_learned(self, net: "MLP", n_iters: int, every: int = 5, jump: float = 5.0, min_angle_tol: float = 1.0,
+    def step_learned(self, net: "MLP", n_iters: int, every: int = 5, jump: float = 5.0, min_angle_tol: float = 0.5,
                      max_proposals: int = 8):
         s = mesh_stats()
         acc, rej = C.c_int32(), C.c_int32()
