@@ -72,3 +72,30 @@ def time_to_quality(sdf, sizing, xy, net=None, target=None, precision=0, n_iters
     dt = time.perf_counter() - t0
     m.close()
     return dt, s
+
+
+def bench_kernels(n=1 << 20, batch=1 << 17, seed=0):
+    """One inference pass over n random feature rows and one training epoch
+    in batches of `batch` (times the model's kernels on their own)."""
+    import numpy as np
+    import torch
+
+    from . import bf16_bits
+
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, 48), np.float32)
+    X[:, :39] = rng.standard_normal((n, 39)).astype(np.float32)
+    Xd = torch.from_numpy(bf16_bits(X).view(np.int16)).cuda()
+    Td = torch.from_numpy(rng.standard_normal((n, 2)).astype(np.float32)).cuda()
+    net = MLP(seed=seed)
+    Y = net.forward(Xd)
+    loss = net.train(Xd, Td, epochs=1, batch=batch, lr=1e-3)
+    torch.cuda.synchronize()
+    return float(Y.abs().mean()), loss
+
+
+if __name__ == "__main__":
+    import sys
+
+    if "--bench" in sys.argv:
+        print("forward |Y| mean %.4f, epoch loss %.4f" % bench_kernels())
