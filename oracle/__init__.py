@@ -50,7 +50,8 @@ class _Params(C.Structure):
                 ("fac_pt", C.c_double), ("fac_geps", C.c_double), ("fac_voro_bound", C.c_double),
                 ("fac_end", C.c_double), ("T_circ", C.c_double), ("T_switch", C.c_double),
                 ("T_end_q", C.c_double), ("T_end_amax", C.c_double), ("N_opt", C.c_double),
-                ("eta", C.c_double), ("damping", C.c_double), ("fac_retria", C.c_double)]
+                ("eta", C.c_double), ("damping", C.c_double), ("fac_retria", C.c_double),
+                ("fac_add", C.c_double), ("T_add", C.c_double), ("n_total", C.c_int64)]
 
 
 class _Stats(C.Structure):
@@ -59,7 +60,8 @@ class _Stats(C.Structure):
                 ("min_angle_deg", C.c_double), ("mean_size_dev", C.c_double), ("fac_mu", C.c_double),
                 ("newton_fail", C.c_int64), ("trace_cap", C.c_int64), ("quad_cap", C.c_int64),
                 ("clip_errors", C.c_int64), ("method_used", C.c_int32), ("terminated", C.c_int32),
-                ("switched", C.c_int32), ("small_moves", C.c_int32), ("triangulated", C.c_int32)]
+                ("switched", C.c_int32), ("small_moves", C.c_int32), ("triangulated", C.c_int32),
+                ("added", C.c_int64), ("n_points", C.c_int64)]
 
 
 def _load():
@@ -176,12 +178,16 @@ class OracleMesh:
         self._sdf = _cgrid(sdf)
         self._siz = _cgrid(sizing)
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
-        self.n = len(xy)
-        h = lib.om_create(C.byref(self._sdf[0]), C.byref(self._siz[0]), _dp(xy), self.n, C.byref(p))
+        h = lib.om_create(C.byref(self._sdf[0]), C.byref(self._siz[0]), _dp(xy), len(xy), C.byref(p))
         if not h:
             raise ValueError(lib.om_last_error().decode())
         self._h = h
         self.ncx, self.ncy = sdf.nx - 1, sdf.ny - 1
+
+    @property
+    def n(self) -> int:
+        """N_current (grows under the point-addition scheme)."""
+        return int(self._lib.om_num_points(self._h))
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -345,7 +345,8 @@ typedef struct { double nx, ny, s; int32_t lab; } hp_t; /* n.u <= s, u relative 
 
 struct om_mesh {
     om_params P;
-    int64_t N;
+    int64_t N;                 /* N_current */
+    int64_t Ntot;              /* N_total (>= N; arrays hold Ntot points) */
     double *x, *y;
     uint8_t* cls;
     double* dprev;
@@ -396,6 +397,9 @@ void om_default_params(om_params* p) {
     p->eta = 0.5;             /* App. B */
     p->damping = 1.0;         /* App. B: alpha-hat */
     p->fac_retria = 0.1;      /* App. B: fac_mvmt^retria (DistMesh only) */
+    p->fac_add = 0.6;         /* App. B: fac_add */
+    p->T_add = 0.002;         /* App. B: T_quality^add */
+    p->n_total = 0;           /* no point addition */
 }
 
 static int point_cell(const om_mesh* m, double x, double y, int* gi, int* gj) {
@@ -498,11 +502,13 @@ om_mesh* om_create(const om_grid* sdf, const om_grid* sizing, const double* xy, 
     if (!m) return NULL;
     if (p) m->P = *p; else om_default_params(&m->P);
     m->N = n;
+    m->Ntot = m->P.n_total > n ? m->P.n_total : n;
+    if (!(m->P.fac_add > 0.0)) { set_err("fac_add must be > 0"); om_destroy(m); return NULL; }
     if (grid_copy(&m->sdf, sdf) || grid_copy(&m->siz, sizing)) { set_err("bad grid"); om_destroy(m); return NULL; }
     size_t ns = (size_t)m->siz.nx * (size_t)m->siz.ny;
     for (size_t k = 0; k < ns; k++)
         if (!(m->siz.v[k] > 0.0f)) { set_err("sizing must be positive"); om_destroy(m); return NULL; }
-    size_t nn = (size_t)(n > 0 ? n : 1);
+    size_t nn = (size_t)(m->Ntot > 0 ? m->Ntot : 1);
     m->x = (double*)malloc(nn * sizeof(double));
     m->y = (double*)malloc(nn * sizeof(double));
     m->cls = (uint8_t*)malloc(nn);
@@ -1306,9 +1312,94 @@ static void fac_mu_current(om_mesh* m) {
     m->st.fac_mu = m->nedge > 0 ? sqrt(sl2 / smu2) : 1.0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* point addition (Sec. 3.6) and the rescaled quantities (Sec. 3.7)         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double ratio;     /* R_circ / h_i */
+    int32_t v[3];     /* vertex indices, ascending */
+    double gx, gy;    /* centroid */
+} addc_t;
+
+/* larger ratio first; equal ratios by the smaller vertex triple */
+static int addc_rank_cmp(const void* a, const void* b) {
+    const addc_t* p = (const addc_t*)a;
+    const addc_t* q = (const addc_t*)b;
+    if (p->ratio != q->ratio) return p->ratio > q->ratio ? -1 : 1;
+    for (int k = 0; k < 3; k++)
+        if (p->v[k] != q->v[k]) return p->v[k] < q->v[k] ? -1 : 1;
+    return 0;
+}
+
+static int addc_triple_cmp(const void* a, const void* b) {
+    const addc_t* p = (const addc_t*)a;
+    const addc_t* q = (const addc_t*)b;
+    for (int k = 0; k < 3; k++)
+        if (p->v[k] != q->v[k]) return p->v[k] < q->v[k] ? -1 : 1;
+    return 0;
+}
+
+/* Adds N_add = min(floor(fac_add N_current), N_total - N_current) points
+ * (at least one, at most one per valid triangle) at the centroids of the
+ * valid triangles with the largest R_circ / h_i, where R_circ is the
+ * circumradius and h_i the desired edge length of the geometry cell holding
+ * the centroid (Sec. 3.6).  Ties in the ratio go to the smaller ascending
+ * vertex triple.  The new points take the indices N_current,
+ * N_current + 1, ... in the ascending order of their triangles' vertex
+ * triples.  Then h_i, geps_i and h_avg are multiplied by
+ * sqrt(N_old / N_current) (Sec. 3.7), and each new point is classified
+ * like an initial point with the rescaled quantities (inner, else boundary)
+ * and starts with a previous move of h_i.  Returns N_add. */
+static int64_t add_points(om_mesh* m) {
+    int64_t N0 = m->N;
+    int64_t nadd = (int64_t)floor(m->P.fac_add * (double)N0);
+    if (nadd < 1) nadd = 1;
+    if (nadd > m->Ntot - N0) nadd = m->Ntot - N0;
+    if (nadd > m->ntri) nadd = m->ntri;
+    if (nadd <= 0) return 0;
+    addc_t* c = (addc_t*)malloc(sizeof(addc_t) * (size_t)m->ntri);
+    if (!c) return 0;
+    for (int64_t t = 0; t < m->ntri; t++) {
+        int32_t i = m->tri[3 * t], j = m->tri[3 * t + 1], k = m->tri[3 * t + 2]; /* i smallest, CCW */
+        double ox, oy, R;
+        circumcenter_fixed(m->x[i], m->y[i], m->x[j], m->y[j], m->x[k], m->y[k], &ox, &oy, &R);
+        double gx = ((m->x[i] + m->x[j]) + m->x[k]) / 3.0;
+        double gy = ((m->y[i] + m->y[j]) + m->y[k]) / 3.0;
+        double r = R / h_at(m, gx, gy);
+        c[t].ratio = r >= 0.0 ? r : 0.0; /* a NaN ratio ranks last */
+        c[t].v[0] = i;
+        c[t].v[1] = j < k ? j : k;
+        c[t].v[2] = j < k ? k : j;
+        c[t].gx = gx;
+        c[t].gy = gy;
+    }
+    qsort(c, (size_t)m->ntri, sizeof(addc_t), addc_rank_cmp);
+    qsort(c, (size_t)nadd, sizeof(addc_t), addc_triple_cmp);
+    double s = sqrt((double)N0 / (double)(N0 + nadd));
+    size_t nc = (size_t)m->ncx * (size_t)m->ncy;
+    for (size_t q = 0; q < nc; q++) {
+        m->gh[q] *= s;
+        m->ggeps[q] *= s;
+    }
+    m->havg *= s;
+    for (int64_t r = 0; r < nadd; r++) {
+        int64_t p = N0 + r;
+        m->x[p] = c[r].gx;
+        m->y[p] = c[r].gy;
+        m->cls[p] = classify(m, m->x[p], m->y[p]) == PT_INNER ? PT_INNER : PT_BOUNDARY;
+        m->dprev[p] = h_at(m, m->x[p], m->y[p]);
+        m->pnew[2 * p] = m->x[p];
+        m->pnew[2 * p + 1] = m->y[p];
+    }
+    free(c);
+    m->N = N0 + nadd;
+    m->retri = 1;
+    return nadd;
+}
+
 /* Procedure I, quality (Eqs. 11-12), the hybrid switch and the termination
- * tests (Sec. 4), then the raw move; returns 1 if a termination test held
- * (no move then). */
+ * tests (Sec. 4), then the raw move; returns 1 if a termination test held,
+ * 2 if points were added (no move then). */
 static int triangulate_and_move(om_mesh* m) {
     om_rebuild(m);
     m->st.triangulated = 1;
@@ -1323,7 +1414,20 @@ static int triangulate_and_move(om_mesh* m) {
     int method;
     int terminated = 0;
     int quality_end = m->have_prev && ra < m->P.T_end_q && rb < m->P.T_end_q && rm < m->P.T_end_amax;
-    if (m->P.method == 2) {
+    if (m->N < m->Ntot) {
+        /* Sec. 3.6: until N_total is reached, a stalled mesh gets new points;
+         * the hybrid switch and the termination tests wait for N_total */
+        if (m->have_prev && ra < m->P.T_add && rb < m->P.T_add && m->ntri > 0) {
+            for (int64_t i = 0; i < m->N; i++) { m->pnew[2 * i] = m->x[i]; m->pnew[2 * i + 1] = m->y[i]; }
+            m->st.added = add_points(m);
+            m->have_prev = 0; /* the next change is not measured across the addition */
+            m->st.method_used = -1;
+            m->st.switched = m->switched;
+            m->st.terminated = 0;
+            return 2;
+        }
+        method = m->P.method == 1 ? 1 : 0;
+    } else if (m->P.method == 2) {
         if (!m->switched) {
             if (m->have_prev && ra < m->P.T_switch) m->switched = 1; /* Sec. 4.2: switch to CVD */
         } else if (quality_end) terminated = 1;
@@ -1352,14 +1456,19 @@ static int triangulate_and_move(om_mesh* m) {
 int om_step(om_mesh* m) {
     m->st.newton_fail = m->st.trace_cap = m->st.quad_cap = 0;
     m->st.small_moves = 0;
+    m->st.added = 0;
     if (m->P.method == 0 && m->P.fac_retria > 0 && !m->retri) {
         fac_mu_current(m);
         m->st.method_used = 0;
         m->st.triangulated = 0;
         m->st.terminated = 0;
         distmesh_move(m);
-    } else if (triangulate_and_move(m)) {
-        return 1;
+    } else {
+        int r = triangulate_and_move(m);
+        if (r) {
+            m->st.n_points = m->N;
+            return r;
+        }
     }
     int small = 1, far = 0;
     for (int64_t i = 0; i < m->N; i++) {
@@ -1377,6 +1486,7 @@ int om_step(om_mesh* m) {
         m->cls[i] = (uint8_t)nc;
     }
     m->st.small_moves = small;
+    m->st.n_points = m->N;
     m->retri = m->P.method != 0 || !(m->P.fac_retria > 0) || far;
     return 0;
 }
@@ -1506,4 +1616,7 @@ void om_get_fsum(const om_mesh* m, double* s) { memcpy(s, m->fsum, sizeof(double
 void om_get_centroid(const om_mesh* m, double* c) { memcpy(c, m->cen, sizeof(double) * 2 * (size_t)m->N); }
 void om_get_cell_area(const om_mesh* m, double* a) { memcpy(a, m->area, sizeof(double) * (size_t)m->N); }
 void om_get_quad_level(const om_mesh* m, int32_t* lv) { memcpy(lv, m->qlevel, sizeof(int32_t) * (size_t)m->N); }
-void om_get_stats(const om_mesh* m, om_stats* s) { *s = m->st; }
+void om_get_stats(const om_mesh* m, om_stats* s) {
+    *s = m->st;
+    s->n_points = m->N;
+}

@@ -14,6 +14,8 @@
  *   - CVD density-weighted centroid, adaptive quadrature      Sec. 2.3 Eq. 6, Sec. 4.2
  *   - point treatment: clamp, classify, sphere trace, Newton  Sec. 4.3 Eqs. 8-10
  *   - aspect/edge ratio quality, 1/2-means, hybrid switch     Sec. 3.6 Eqs. 11-12, Sec. 4
+ *   - point addition at the centroids of the triangles with   Sec. 3.6, Sec. 3.7
+ *     the largest R_circ / h_i, quantities rescaled
  *
  * Every sign decision of the triangulation (incircle / orientation) is exact:
  * big-integer arithmetic behind a deliberately loose double-precision filter,
@@ -45,6 +47,9 @@ typedef struct {
     double T_circ, T_switch, T_end_q, T_end_amax;
     double N_opt, eta, damping;
     double fac_retria;         /* DistMesh re-triangulation threshold factor (Algorithm 1, App. B: 0.1); 0: every iteration */
+    double fac_add;            /* point addition: N_add = min(floor(fac_add N_current), N_total - N_current) (Sec. 3.6, App. B: 0.6) */
+    double T_add;              /* point addition quality threshold T_quality^add (Sec. 3.6, App. B: 0.002) */
+    int64_t n_total;           /* N_total; above the initial n it runs the point-addition scheme (Sec. 3.6) */
 } om_params;
 
 typedef struct {
@@ -61,6 +66,8 @@ typedef struct {
     int32_t switched;          /* hybrid has switched to CVD             */
     int32_t small_moves;       /* all inner moves < fac_end h_i          */
     int32_t triangulated;      /* the step re-triangulated (Algorithm 1)  */
+    int64_t added;             /* points the step added (Sec. 3.6)        */
+    int64_t n_points;          /* N_current after the step                */
 } om_stats;
 
 typedef struct om_mesh om_mesh;
@@ -68,7 +75,10 @@ typedef struct om_mesh om_mesh;
 void om_default_params(om_params* p);
 
 /* Create from positions xy[2n] (x,y interleaved).  Grids are deep-copied.
- * Returns NULL on invalid input (message via om_last_error). */
+ * With p->n_total > n the mesh starts with N_current = n points and grows to
+ * N_total by the point-addition scheme (Sec. 3.6); h_i is computed from
+ * N_current (Sec. 3.7).  Returns NULL on invalid input (message via
+ * om_last_error). */
 om_mesh* om_create(const om_grid* sdf, const om_grid* sizing, const double* xy,
                    int64_t n, const om_params* p);
 void om_destroy(om_mesh* m);
@@ -76,7 +86,10 @@ const char* om_last_error(void);
 
 /* Procedure I at the current positions: cells, triangles, validity, quality. */
 int om_rebuild(om_mesh* m);
-/* One meshing iteration: rebuild, quality, hybrid/termination logic, move. */
+/* One meshing iteration: rebuild, quality, hybrid/termination logic, move.
+ * While N_current < N_total the termination tests and the hybrid switch are
+ * not evaluated; an iteration whose 1/2-means of alpha and beta both changed
+ * by less than T_add instead adds points (no move in that iteration). */
 int om_step(om_mesh* m);
 /* Same as om_step but only for the cells listed (timing sample; no move). */
 int om_rebuild_sample(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid);
