@@ -186,3 +186,11 @@ def test_no_addition_without_n_total():
     for _ in range(5):
         s = m.step()
         assert s["added"] == 0 and s["n_points"] == 200
+
+
+def test_no_change_measured_across_an_addition():
+    """The quality change is not measured across an addition: with T_add above
+    any change, additions come every second iteration, never back to back."""
+    w, m = _setup_about_to_add(n_total=5000)
+    got = [m.step()["added"] > 0 for _ in range(5)]
+    assert got == [True, False, True, False, True]
