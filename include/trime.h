@@ -72,6 +72,13 @@ typedef struct {
     double fac_retria;       /* 0.1   DistMesh (method 0) re-triangulates only after some point
                                       moved more than fac_retria*h_i since the last triangulation
                                       (Algorithm 1); 0: every iteration                     */
+    double fac_add;          /* 0.6   point addition: N_add = min(floor(fac_add*N_current),
+                                      N_total - N_current), at least 1 (Sec. 3.6)          */
+    double T_add;            /* 0.002 add points once the 1/2-means of alpha and beta both
+                                      change by less than this (Sec. 3.6)                  */
+    int64_t n_total;         /* 0     N_total: above mesh_init's n, the mesh starts with n
+                                      points and grows to n_total by the point-addition
+                                      scheme (Sec. 3.6); single meshes only                */
 } mesh_params;
 
 /* Statistics of the last iteration run by mesh_step (or of mesh_rebuild). */
@@ -105,6 +112,8 @@ typedef struct {
     int64_t vor_rings;         /* bucket rings scanned (summed over cells)                */
     int64_t vor_wide;          /* cells redone with 32 lanes                              */
     int64_t triangulations;    /* iterations of the call that re-triangulated             */
+    int64_t added;             /* points added by the call (Sec. 3.6)                     */
+    int64_t n_points;          /* N_current after the call                                */
 } mesh_stats;
 
 typedef struct mesh_s mesh_t;
@@ -119,8 +128,9 @@ void mesh_default_params(mesh_params* p);
  *  n >= 0.  p may be NULL for the defaults.  cuda_stream: a cudaStream_t
  *  (NULL = legacy default stream) on which all later work is ordered.
  * Precomputes the geometry grid on the SDF grid's cells (Sec. 3.2 classes,
- * Sec. 3.7 h_i and geps_i), allocates all device buffers and captures one
- * iteration into a CUDA graph.  Errors: TRIME_EINVAL, TRIME_ENOMEM, TRIME_ECUDA. */
+ * Sec. 3.7 h_i and geps_i, h_i from N_current = n), allocates all device
+ * buffers (for max(n, p->n_total) points) and captures one iteration into a
+ * CUDA graph.  Errors: TRIME_EINVAL, TRIME_ENOMEM, TRIME_ECUDA. */
 int mesh_init(mesh_t** out, const mesh_grid2d* sdf, const mesh_grid2d* sizing, const void* xy, int64_t n,
               const mesh_params* p, void* cuda_stream);
 
@@ -134,8 +144,23 @@ int mesh_rebuild(mesh_t* m, mesh_stats* stats);
  * Sec. 4 holds (checked on the host every 32 iterations; later iterations are
  * device-side no-ops).  With stats != NULL synchronises at the end, fills
  * *stats and returns TRIME_EDEVICE if a capacity guard tripped; with
- * stats == NULL the call is asynchronous on the caller's stream. */
+ * stats == NULL the call is asynchronous on the caller's stream.
+ * While N_current < N_total (point addition, Sec. 3.6) the hybrid switch and
+ * the termination tests are not evaluated; an iteration whose 1/2-means of
+ * alpha and beta both changed by less than T_add since the previous one
+ * (never measured across an addition) does not move: it pauses the graph
+ * and the host adds N_add points at the centroids of the valid triangles
+ * with the largest R_circ/h_i (h_i at the centroid; ties to the smaller
+ * ascending vertex-index triple), numbered N_current, N_current+1, ... in the
+ * ascending order of those triples, multiplies h_i, geps_i and h_avg by
+ * sqrt(N_old/N_current) (Sec. 3.7), classifies the new points like initial
+ * points and re-captures the iteration for the new size.  Such calls check
+ * for a pause every 8 iterations and synchronise even with stats == NULL;
+ * n_iters counts executed iterations (an addition is one). */
 int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats);
+
+/* N_current and N_total of a mesh (host-side state; no synchronisation). */
+int mesh_get_count(mesh_t* m, int64_t* n_current, int64_t* n_total);
 
 /* Valid triangles of the last rebuild as int32 (a, b, c) point indices, a the
  * smallest index, counter-clockwise; order unspecified.  tri may be host or
@@ -152,6 +177,12 @@ int mesh_get_points(mesh_t* m, void* xy, int64_t cap, int64_t* n_out);
  * pointers, any may be NULL to keep the current value.  Used to resume a
  * mesh or to start two implementations from identical states. */
 int mesh_set_state(mesh_t* m, const void* xy, const uint8_t* cls, const double* dprev);
+
+/* The per-point state mesh_set_state replaces, in input order, into HOST
+ * arrays of N_current entries (any may be NULL): positions in the mesh's
+ * precision, classes (0 inner / 1 boundary), previous move distances as
+ * float64.  Synchronous. */
+int mesh_get_state(mesh_t* m, void* xy, uint8_t* cls, double* dprev);
 
 /* Hybrid state: switched flag and the previous iteration's quality. */
 int mesh_set_method_state(mesh_t* m, int32_t switched, double prev_half_alpha, double prev_half_beta,
@@ -319,7 +350,8 @@ int mesh_propose(mesh_t* m, mlp_t* net, double jump);
  * plain branch's state is restored.  Both branches count as iterations.  At most max_proposals proposals are made (<= 0: no limit);
  * the iterations after the last one are plain.  *accepted / *rejected (may be
  * NULL) count the proposals.  Statistics and termination as mesh_step (stats
- * may not be NULL). */
+ * may not be NULL).  TRIME_EINVAL while N_current < N_total (point
+ * addition); mesh_features, mesh_collect_pairs and mesh_propose likewise. */
 int mesh_step_learned(mesh_t* m, mlp_t* net, int32_t n_iters, int32_t every, double jump, double min_angle_tol,
                       int32_t max_proposals, mesh_stats* stats, int32_t* accepted, int32_t* rejected);
 
@@ -365,7 +397,8 @@ typedef struct {
  *  (points per bucket in {2/3, 1, 3/2} x p->N_opt) x (16 or 32 Voronoi lanes
  *  per cell) on these inputs and keep the fastest (the triangles do not
  *  depend on the choice); autotune == 0 uses p->N_opt and 16 lanes.  Errors as
- *  mesh_init; a message names the offending mesh. */
+ *  mesh_init; a message names the offending mesh.  Point addition is not
+ *  available in a batch (p->n_total above a mesh's n: TRIME_EINVAL). */
 int mesh_batch_init(mesh_batch_t** out, int32_t n_meshes, const mesh_grid2d* sdfs, const mesh_grid2d* sizings,
                     const void* const* xys, const int64_t* ns, const mesh_params* p, int32_t autotune,
                     void* cuda_stream);

@@ -1366,7 +1366,7 @@ static int64_t add_points(om_mesh* m) {
         double gx = ((m->x[i] + m->x[j]) + m->x[k]) / 3.0;
         double gy = ((m->y[i] + m->y[j]) + m->y[k]) / 3.0;
         double r = R / h_at(m, gx, gy);
-        c[t].ratio = r >= 0.0 ? r : 0.0; /* a NaN ratio ranks last */
+        c[t].ratio = r > 0.0 ? r : 0.0; /* a NaN ratio ranks last */
         c[t].v[0] = i;
         c[t].v[1] = j < k ? j : k;
         c[t].v[2] = j < k ? k : j;

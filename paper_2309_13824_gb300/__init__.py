@@ -46,7 +46,8 @@ class mesh_params(C.Structure):
                 ("k_spring", C.c_double), ("dt", C.c_double), ("fac_pt", C.c_double), ("fac_geps", C.c_double),
                 ("fac_voro_bound", C.c_double), ("fac_end", C.c_double), ("T_circ", C.c_double),
                 ("T_switch", C.c_double), ("T_end_q", C.c_double), ("T_end_amax", C.c_double),
-                ("N_opt", C.c_double), ("eta", C.c_double), ("damping", C.c_double), ("fac_retria", C.c_double)]
+                ("N_opt", C.c_double), ("eta", C.c_double), ("damping", C.c_double), ("fac_retria", C.c_double),
+                ("fac_add", C.c_double), ("T_add", C.c_double), ("n_total", C.c_int64)]
 
 
 class mesh_stats(C.Structure):
@@ -59,7 +60,7 @@ class mesh_stats(C.Structure):
                 ("trace_cap", C.c_int64), ("quad_cap", C.c_int64), ("dup_points", C.c_int64),
                 ("small_moves", C.c_int32), ("target_reached", C.c_int32), ("vor_candidates", C.c_int64),
                 ("vor_picks", C.c_int64), ("vor_cuts", C.c_int64), ("vor_rings", C.c_int64), ("vor_wide", C.c_int64),
-                ("triangulations", C.c_int64)]
+                ("triangulations", C.c_int64), ("added", C.c_int64), ("n_points", C.c_int64)]
 
 
 class mesh_tuning(C.Structure):
@@ -69,7 +70,7 @@ class mesh_tuning(C.Structure):
 
 
 # every symbol include/trime.h declares
-EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles",
+EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
            "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step",
            "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
@@ -153,7 +154,9 @@ def lib():
     L.mesh_batch_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
     L.mesh_batch_destroy.argtypes = [vp]
     L.mesh_batch_destroy.restype = None
-    for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_triangles", "mesh_get_points",
+    L.mesh_get_count.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
+    L.mesh_get_state.argtypes = [vp, vp, vp, vp]
+    for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_get_triangles", "mesh_get_points",
                  "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
                  "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc", "mesh_batch_init",
                  "mesh_batch_size", "mesh_batch_rebuild", "mesh_batch_step", "mesh_batch_get_triangles",
@@ -269,15 +272,27 @@ class Mesh:
         self.precision = p.precision
         self.dtype = np.float64 if p.precision == 0 else np.float32
         xy = np.ascontiguousarray(np.asarray(xy, dtype=self.dtype).reshape(-1, 2))
-        self.n = len(xy)
         gs, ks = _grid(sdf)
         gz, kz = _grid(sizing)
         h = C.c_void_p()
         st = C.c_void_p(0 if stream is None else int(stream))
-        rc = L.mesh_init(C.byref(h), C.byref(gs), C.byref(gz), xy.ctypes.data_as(C.c_void_p), self.n,
+        rc = L.mesh_init(C.byref(h), C.byref(gs), C.byref(gz), xy.ctypes.data_as(C.c_void_p), len(xy),
                          C.byref(p), st)
         _check(rc)
         self._h = h
+
+    @property
+    def n(self) -> int:
+        """N_current: the number of points (grows under point addition)."""
+        c = C.c_int64()
+        _check(lib().mesh_get_count(self._h, C.byref(c), None))
+        return c.value
+
+    @property
+    def n_total(self) -> int:
+        c = C.c_int64()
+        _check(lib().mesh_get_count(self._h, None, C.byref(c)))
+        return c.value
 
     def close(self):
         if getattr(self, "_h", None):
@@ -350,6 +365,16 @@ class Mesh:
 
     def set_method_state(self, switched, prev_a=0.0, prev_b=0.0, prev_amax=0.0):
         _check(lib().mesh_set_method_state(self._h, switched, prev_a, prev_b, prev_amax))
+
+    def state(self):
+        """(positions, classes, previous move distances) in input order."""
+        n = self.n
+        xy = np.zeros((n, 2), dtype=self.dtype)
+        cls = np.zeros(n, dtype=np.uint8)
+        dp = np.zeros(n)
+        _check(lib().mesh_get_state(self._h, xy.ctypes.data_as(C.c_void_p), cls.ctypes.data_as(C.c_void_p),
+                                    dp.ctypes.data_as(C.c_void_p)))
+        return xy, cls, dp
 
     def set_tuning(self, n_opt: float, lanes: int = 16):
         _check(lib().mesh_set_tuning(self._h, n_opt, lanes))

@@ -263,6 +263,32 @@ template void launch_set_state<double>(const IterArgs<double>&, int32_t, int32_t
 template void launch_set_state<float>(const IterArgs<float>&, int32_t, int32_t, const float*, const uint8_t*,
                                       const double*, cudaStream_t);
 
+template <typename T>
+__global__ void k_get_state(const __grid_constant__ IterArgs<T> a, int32_t s0, int32_t ns, T* xy, uint8_t* cls,
+                            double* dprev) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    s += s0;
+    size_t id = (size_t)(a.cur.id[s] - s0);
+    if (xy) {
+        xy[2 * id] = a.cur.x[s];
+        xy[2 * id + 1] = a.cur.y[s];
+    }
+    if (cls) cls[id] = a.cur.cls[s];
+    if (dprev) dprev[id] = (double)a.cur.dprev[s];
+}
+
+template <typename T>
+void launch_get_state(const IterArgs<T>& a, int32_t s0, int32_t ns, T* xy, uint8_t* cls, double* dprev,
+                      cudaStream_t st) {
+    int g = (ns + kThreads - 1) / kThreads;
+    if (g > 0) k_get_state<T><<<g, kThreads, 0, st>>>(a, s0, ns, xy, cls, dprev);
+}
+template void launch_get_state<double>(const IterArgs<double>&, int32_t, int32_t, double*, uint8_t*, double*,
+                                       cudaStream_t);
+template void launch_get_state<float>(const IterArgs<float>&, int32_t, int32_t, float*, uint8_t*, double*,
+                                      cudaStream_t);
+
 // ------------------------------------------------------------------ standalone a1
 __global__ void k_count_raw(const double* x, const double* y, int32_t n, double x0, double y0, double ibsx,
                             double ibsy, int32_t nbx, int32_t nby, int32_t* key, int32_t* rank, int32_t* cnt) {

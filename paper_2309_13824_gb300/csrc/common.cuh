@@ -76,9 +76,12 @@ struct DevCtrl {
 
 struct DevParams {
     int32_t bounded, validity, newton_max, trace_max, quad_max_level, debug;
+    int32_t adding;     // N_current < N_total: point addition (Sec. 3.6) replaces the switch and termination tests
+    int32_t pad_p;
     double fac_F, k_spring, dt, fac_pt, fac_geps, fac_voro_bound, fac_end, T_circ;
     double T_switch, T_end_q, T_end_amax, damping;
     double fac_retria;  // DistMesh re-triangulation threshold factor (0: every iteration)
+    double T_add;       // point-addition quality threshold (Sec. 3.6)
     double havg;
     // SDF box (domain box)
     double bx0, by0, bx1, by1;
@@ -98,6 +101,22 @@ __device__ __forceinline__ double fadd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ double fsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double fmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// circumcentre (ox, oy) and circumradius R of triangle (a, b, c), fixed
+// formula (the vertex order is part of it: callers pass the canonical order,
+// smallest id first, counter-clockwise)
+__device__ __forceinline__ void circumcentre_fixed(double ax, double ay, double bx, double by, double cx, double cy,
+                                                   double& ox, double& oy, double& R) {
+    double bx_ = fsub(bx, ax), by_ = fsub(by, ay), cx_ = fsub(cx, ax), cy_ = fsub(cy, ay);
+    double B = fadd(fmul(bx_, bx_), fmul(by_, by_));
+    double C = fadd(fmul(cx_, cx_), fmul(cy_, cy_));
+    double D = fmul(2.0, fsub(fmul(bx_, cy_), fmul(by_, cx_)));
+    double ux = fdiv(fsub(fmul(cy_, B), fmul(by_, C)), D);
+    double uy = fdiv(fsub(fmul(bx_, C), fmul(cx_, B)), D);
+    ox = fadd(ax, ux);
+    oy = fadd(ay, uy);
+    R = __dsqrt_rn(fadd(fmul(ux, ux), fmul(uy, uy)));
+}
 
 // cell of the grid holding (x, y) and local coordinates, clamped to the grid
 __device__ __forceinline__ void grid_locate(const DevGrid& g, double x, double y, int& i, int& j, double& fx,

@@ -17,19 +17,6 @@ namespace trime {
 
 constexpr float kEpsF = 5.9604645e-8f;  // 2^-24
 
-__device__ __forceinline__ void circumcentre_fixed(double ax, double ay, double bx, double by, double cx, double cy,
-                                                   double& ox, double& oy, double& R) {
-    double bx_ = fsub(bx, ax), by_ = fsub(by, ay), cx_ = fsub(cx, ax), cy_ = fsub(cy, ay);
-    double B = fadd(fmul(bx_, bx_), fmul(by_, by_));
-    double C = fadd(fmul(cx_, cx_), fmul(cy_, cy_));
-    double D = fmul(2.0, fsub(fmul(bx_, cy_), fmul(by_, cx_)));
-    double ux = fdiv(fsub(fmul(cy_, B), fmul(by_, C)), D);
-    double uy = fdiv(fsub(fmul(bx_, C), fmul(cx_, B)), D);
-    ox = fadd(ax, ux);
-    oy = fadd(ay, uy);
-    R = __dsqrt_rn(fadd(fmul(ux, ux), fmul(uy, uy)));
-}
-
 // c in Reg_v = Oct_v (span S_v) cap domain box, fixed formula
 __device__ __forceinline__ bool reg_contains_fixed(const DevParams& P, double px, double py, double h, double cx,
                                                    double cy) {

@@ -11,6 +11,8 @@
 //   ring_n[N] u8, cellR[N]  edge count, conservative max vertex distance
 //   vmask[N] u32            bit t: triangle (slot, ring[t], ring[t+1]) valid
 #pragma once
+#include <string>
+
 #include "common.cuh"
 
 namespace trime {
@@ -113,6 +115,16 @@ template <typename T> void launch_stats_pre(const IterArgs<T>& a, int decide, cu
 // a5/a6/a7
 template <typename T> void launch_update(const IterArgs<T>& a, int nblocks, cudaStream_t st);
 template <typename T> void launch_stats_post(const IterArgs<T>& a, cudaStream_t st);
+// point addition (Sec. 3.6, 3.7) on a paused single mesh of n0 points whose
+// ntri valid triangles have owner offsets toff: keys (kAddKeyBytes per
+// triangle), selection of nadd, per-owner counts and offsets by id (cnt_id,
+// off_id: n0 + 1 each), geometry rescaling and the new points at slots
+// [n0, n0 + nadd) of cur; hist is 256 device ints, hhist 256 pinned host ints
+constexpr size_t kAddKeyBytes = 24;
+template <typename T>
+int add_select(const IterArgs<T>& a, int32_t n0, int32_t ntri, int64_t nadd, const int32_t* toff, void* keys,
+               int32_t* hist, int32_t* hhist, int32_t* cnt_id, int32_t* off_id, int32_t* scan_tmp, double* gh,
+               double* ggeps, int32_t nc, double scale, cudaStream_t st, std::string& err);
 // output helpers on the slots [s0, s0 + ns) of one mesh whose ids start at s0
 template <typename T> void launch_tri_count(const IterArgs<T>& a, int32_t s0, int32_t ns, int32_t* cnt,
                                             cudaStream_t st);
@@ -122,6 +134,8 @@ template <typename T> void launch_unpermute(const IterArgs<T>& a, int32_t s0, in
                                             cudaStream_t st);
 template <typename T> void launch_set_state(const IterArgs<T>& a, int32_t s0, int32_t ns, const T* xy,
                                             const uint8_t* cls, const double* dprev, cudaStream_t st);
+template <typename T> void launch_get_state(const IterArgs<T>& a, int32_t s0, int32_t ns, T* xy, uint8_t* cls,
+                                            double* dprev, cudaStream_t st);
 void launch_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out,
                        cudaStream_t st);
 // standalone a1 on raw arrays (mesh_bucket_points)

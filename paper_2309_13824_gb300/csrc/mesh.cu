@@ -106,6 +106,12 @@ struct mesh_s {
     void* xybuf = nullptr;
     cudaGraphExec_t gexec = nullptr;
     LearnBufs* learn = nullptr;
+    // point addition (single mesh): capacity N_total and the selection scratch
+    int64_t ncap = 0;
+    int64_t added_call = 0;      // points added during the current mesh_step
+    void* akeys = nullptr;       // [2 ncap + 16] selection keys
+    int32_t *ahist = nullptr, *hhist = nullptr;  // 256 device / pinned host
+    int32_t *acnt = nullptr, *aoff = nullptr;    // [ncap + 1] per-owner counts and offsets by id
     std::vector<void*> allocs;
 };
 
@@ -460,6 +466,8 @@ static void fill_stats(const mesh_s* m, int k, int iters, mesh_stats* s) {
     s->vor_rings = (int64_t)c.cnt.vor_rings;
     s->vor_wide = (int64_t)c.cnt.vor_wide;
     s->triangulations = (int64_t)c.cnt.triangulations;
+    s->added = m->batched ? 0 : m->added_call;
+    s->n_points = m->parts[k].n;
 }
 
 static bool guard_tripped(const mesh_s* m) {
@@ -507,6 +515,8 @@ static int check_params(const mesh_params& P) {
     if (P.quad_max_level < 1 || P.quad_max_level > 9) return fail(TRIME_EINVAL, "quad_max_level must be 1..9");
     if (P.newton_max < 0 || P.trace_max < 1) return fail(TRIME_EINVAL, "bad newton_max / trace_max");
     if (!(P.N_opt > 0) || !(P.fac_voro_bound > 0) || !(P.dt >= 0)) return fail(TRIME_EINVAL, "bad parameter value");
+    if (!(P.fac_add > 0) || !(P.T_add >= 0) || P.n_total < 0 || P.n_total > (int64_t)(1 << 30))
+        return fail(TRIME_EINVAL, "bad point-addition parameter (fac_add > 0, T_add >= 0, 0 <= n_total <= 2^30)");
     return 0;
 }
 
@@ -557,6 +567,7 @@ static void fill_devparams(DevParams& d, const mesh_params& P, const HostGeometr
     d.T_end_amax = P.T_end_amax;
     d.damping = P.damping;
     d.fac_retria = P.fac_retria;
+    d.T_add = P.T_add;
     d.havg = G.havg;
     d.bx0 = sdf->x0;
     d.by0 = sdf->y0;
@@ -702,6 +713,8 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     for (int k = 0; k < nparts; k++) {
         std::string who = m->batched ? "mesh " + std::to_string(k) + ": " : "";
         if ((rc = check_part(&sdfs[k], &sizings[k], xys ? xys[k] : nullptr, ns[k], P.precision, who))) return rc;
+        if (m->batched && P.n_total > ns[k])
+            return fail(TRIME_EINVAL, who + "point addition (n_total above n) is not available in a batch");
         if ((rc = host_geometry(sdfs[k], sizings[k], ns[k], P, G[k]))) return fail(rc, who + g_err);
         Part& p = m->parts[k];
         p.n = ns[k];
@@ -718,12 +731,30 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->nslots = slots;
     m->nblk = m->batched ? (int)(slots / kChunk) : (int)std::max<int64_t>(1, (slots + kThreads - 1) / kThreads);
     if (!m->batched) m->parts[0].c1 = m->nblk;
+    // a single mesh holds up to N_total points (Sec. 3.6): device arrays, the
+    // bucket grid and the block partials are sized for that many
+    m->ncap = m->batched ? slots : std::max<int64_t>(slots, P.n_total);
+    if (m->ncap > (int64_t)1 << 30) return fail(TRIME_EINVAL, "too many points");
+    for (Part& p : m->parts) p.dp.adding = !m->batched && p.n < m->ncap;
+    int nblk_cap = m->batched ? m->nblk : (int)std::max<int64_t>(1, (m->ncap + kThreads - 1) / kThreads);
     std::vector<double> nopts = {P.N_opt};
     if (tune) nopts = {P.N_opt * (2.0 / 3.0), P.N_opt, P.N_opt * 1.5};
     int nbmax = 0;
-    for (double no : nopts) {
-        if ((rc = layout_buckets(m, no))) return rc;
-        nbmax = std::max(nbmax, m->nbtot);
+    for (int at_cap = 0; at_cap < 2; at_cap++) {
+        Part& p0 = m->parts[0];
+        int64_t n_now = p0.n;
+        double rho_now = p0.rho_eff;
+        if (at_cap && !m->batched && m->ncap > n_now) {
+            // the expected point density grows with N_current (h_i ~ N^-1/2)
+            if (n_now > 0) p0.rho_eff = rho_now * ((double)m->ncap / (double)n_now) * (1.0 + 1e-9);
+            p0.n = m->ncap;
+        }
+        for (double no : nopts) {
+            if ((rc = layout_buckets(m, no))) return rc;
+            nbmax = std::max(nbmax, m->nbtot);
+        }
+        p0.n = n_now;
+        p0.rho_eff = rho_now;
     }
 
     if (cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -731,10 +762,11 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
         return fail(TRIME_ECUDA, "stream/event creation failed");
     if (cudaMallocHost(&m->hctrl, sizeof(DevCtrl) * nparts) != cudaSuccess) return fail(TRIME_ENOMEM, "pinned alloc");
 
-    size_t N = (size_t)slots;
+    size_t N = (size_t)m->ncap;
     size_t T = P.precision == 0 ? sizeof(double) : sizeof(float);
     size_t nmax = 0;
     for (const Part& p : m->parts) nmax = std::max(nmax, (size_t)p.n);
+    if (!m->batched) nmax = N;
     rc = 0;
     m->cx = dalloc<char>(m, N * T, rc);
     m->cy = dalloc<char>(m, N * T, rc);
@@ -764,8 +796,8 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->ring_n = dalloc<uint8_t>(m, N, rc);
     m->cellR = dalloc<float>(m, N, rc);
     m->vmask = dalloc<uint32_t>(m, N, rc);
-    m->ep = dalloc<EmitPartial>(m, (size_t)m->nblk, rc);
-    m->up = dalloc<UpdatePartial>(m, (size_t)m->nblk, rc);
+    m->ep = dalloc<EmitPartial>(m, (size_t)nblk_cap, rc);
+    m->up = dalloc<UpdatePartial>(m, (size_t)nblk_cap, rc);
     m->ctrl = dalloc<DevCtrl>(m, (size_t)nparts, rc);
     m->ovf_n = dalloc<int32_t>(m, 1, rc);
     m->dbg = P.debug ? dalloc<double>(m, 10 * N, rc) : nullptr;
@@ -779,6 +811,14 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     if (m->batched) {
         m->dviews = dalloc<MeshView>(m, (size_t)nparts, rc);
         m->cmesh = dalloc<int32_t>(m, N / kChunk, rc);
+    }
+    if (!m->batched && m->ncap > slots) {
+        m->akeys = dalloc<char>(m, (2 * N + 16) * kAddKeyBytes, rc);
+        m->ahist = dalloc<int32_t>(m, 256, rc);
+        m->acnt = dalloc<int32_t>(m, N + 1, rc);
+        m->aoff = dalloc<int32_t>(m, N + 1, rc);
+        if (!rc && cudaMallocHost(&m->hhist, 256 * sizeof(int32_t)) != cudaSuccess)
+            rc = fail(TRIME_ENOMEM, "pinned alloc");
     }
     if (rc) return rc;
     // padding slots hold zeros; no kernel reads them as points
@@ -808,6 +848,7 @@ static void destroy(mesh_s* m) {
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     for (void* p : m->allocs) cudaFree(p);
     if (m->hctrl) cudaFreeHost(m->hctrl);
+    if (m->hhist) cudaFreeHost(m->hhist);
     if (m->ev) cudaEventDestroy(m->ev);
     if (m->st) cudaStreamDestroy(m->st);
 }
@@ -829,6 +870,65 @@ static int do_rebuild(mesh_s* m, mesh_stats* stats) {
     return TRIME_OK;
 }
 
+// Sec. 3.6 point addition on a single mesh whose graph paused for it
+// (ctrl->terminated == 2): selection, numbering and the new points on the
+// device (addition.cu), the Sec. 3.7 rescaling of h_i, geps_i, h_avg and the
+// bucket density, then the layout and the captured iteration for the new
+// size.  The paused iteration's triangulation is read in place.
+static int add_points(mesh_s* m) {
+    Part& p = m->parts[0];
+    const int64_t n0 = p.n;
+    int64_t nadd = (int64_t)std::floor(m->P.fac_add * (double)n0);
+    nadd = std::min<int64_t>(std::max<int64_t>(nadd, 1), m->ncap - n0);
+    if (nadd <= 0 || !m->akeys) return fail(TRIME_EDEVICE, "point addition requested without room for points");
+    int32_t ntri = 0;
+    if (m->prec == 0) launch_tri_count<double>(make_args<double>(m, 1), 0, (int32_t)n0, m->tcnt, m->st);
+    else launch_tri_count<float>(make_args<float>(m, 1), 0, (int32_t)n0, m->tcnt, m->st);
+    launch_scan(m->tcnt, m->toff, (int32_t)n0, m->scan_tmp, m->st);
+    CUDA_TRY(cudaMemcpyAsync(&ntri, m->toff + n0, sizeof(int32_t), cudaMemcpyDeviceToHost, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    if ((size_t)ntri > 2 * (size_t)m->ncap + 16) return fail(TRIME_EDEVICE, "triangle count exceeds 2n+16");
+    nadd = std::min<int64_t>(nadd, ntri);
+    if (nadd <= 0) return fail(TRIME_EDEVICE, "point addition requested on a mesh without triangles");
+    const int64_t n1 = n0 + nadd;
+    const double scale = std::sqrt((double)n0 / (double)n1);
+    int32_t nc = (int32_t)((size_t)(p.sdf.nx - 1) * (size_t)(p.sdf.ny - 1));
+    std::string err;
+    int r = m->prec == 0 ? add_select<double>(make_args<double>(m, 1), (int32_t)n0, ntri, nadd, m->toff, m->akeys,
+                                              m->ahist, m->hhist, m->acnt, m->aoff, m->scan_tmp, p.gh, p.ggeps, nc,
+                                              scale, m->st, err)
+                         : add_select<float>(make_args<float>(m, 1), (int32_t)n0, ntri, nadd, m->toff, m->akeys,
+                                             m->ahist, m->hhist, m->acnt, m->aoff, m->scan_tmp, p.gh, p.ggeps, nc,
+                                             scale, m->st, err);
+    if (r) return fail(r == -1 ? TRIME_ECUDA : TRIME_EDEVICE, err);
+    // Sec. 3.7: the quantities scale with sqrt(N_old / N_current); the
+    // expected point density (bucket sizing) with N_current / N_old
+    p.dp.havg *= scale;
+    p.rho_eff *= (double)n1 / (double)n0;
+    p.n = n1;
+    p.dp.adding = n1 < m->ncap;
+    m->nslots = n1;
+    m->nblk = (int)std::max<int64_t>(1, (n1 + kThreads - 1) / kThreads);
+    p.c1 = m->nblk;
+    int rc = layout_buckets(m, m->nopt);
+    if (rc) return rc;
+    if (m->nbtot > m->nbcap) return fail(TRIME_EDEVICE, "bucket grid outgrew its allocation");
+    // the paused iteration counted; the next one re-triangulates and measures
+    // no quality change across the addition
+    DevCtrl& c = m->hctrl[0];
+    c.terminated = 0;
+    c.have_prev = 0;
+    c.retri = 1;
+    c.moved_far = 0;
+    CUDA_TRY(cudaMemcpyAsync(m->ctrl, &c, sizeof(DevCtrl), cudaMemcpyHostToDevice, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    m->tri_stale = true;
+    m->added_call += nadd;
+    return capture_graph(m);
+}
+
+static bool growing(const mesh_s* m) { return !m->batched && m->parts[0].n < m->ncap; }
+
 static int do_step(mesh_s* m, int32_t n_iters, mesh_stats* stats) {
     if (n_iters < 0) return fail(TRIME_EINVAL, "n_iters < 0");
     if (m->learn && n_iters > 0) m->learn->have_q = false;  // the features' last move is no longer known
@@ -836,10 +936,26 @@ static int do_step(mesh_s* m, int32_t n_iters, mesh_stats* stats) {
     if (rc) return rc;
     if ((rc = reset_counters(m))) return rc;
     if ((rc = read_ctrl(m))) return rc;
+    m->added_call = 0;
+    // a pause left by an asynchronous call
+    if (!m->batched && m->hctrl[0].terminated == 2 && (rc = add_points(m))) return rc;
     size_t np = m->parts.size();
     std::vector<int> start(np);
     for (size_t k = 0; k < np; k++) start[k] = m->hctrl[k].iterations;
-    if (!all_terminated(m)) {
+    if (growing(m)) {
+        // point addition: check for a pause every 8 iterations and count the
+        // executed iterations (those after a pause were device-side no-ops)
+        int done = 0;
+        while (done < n_iters) {
+            int chunk = std::min(8, n_iters - done);
+            m->tri_stale = false;  // the next iteration re-triangulates
+            for (int k = 0; k < chunk; k++) CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+            if ((rc = read_ctrl(m))) return rc;
+            if (m->hctrl[0].terminated == 2 && (rc = add_points(m))) return rc;
+            done = m->hctrl[0].iterations - start[0];
+            if (m->hctrl[0].terminated) break;
+        }
+    } else if (!all_terminated(m)) {
         if (n_iters > 0) m->tri_stale = false;  // the first iteration re-triangulates
         for (int32_t k = 0; k < n_iters; k++) {
             CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
@@ -952,6 +1068,30 @@ static int set_state(mesh_s* m, int k, const void* xy, const uint8_t* cls, const
     return sync_out(m);
 }
 
+static int get_state(mesh_s* m, int k, void* xy, uint8_t* cls, double* dprev) {
+    const Part& p = m->parts[k];
+    if (p.n == 0) return TRIME_OK;
+    size_t N = (size_t)p.n, T = m->prec == 0 ? sizeof(double) : sizeof(float);
+    int rc = sync_in(m);
+    if (rc) return rc;
+    // staging as in set_state: xy in xybuf, cls in tcnt, dprev in tbuf
+    char* sxy = (char*)m->xybuf;
+    uint8_t* scls = (uint8_t*)m->tcnt;
+    double* sdp = (double*)m->tbuf;
+    if (m->prec == 0)
+        launch_get_state<double>(make_args<double>(m, 1), p.soff, (int32_t)N, xy ? (double*)sxy : nullptr,
+                                 cls ? scls : nullptr, dprev ? sdp : nullptr, m->st);
+    else
+        launch_get_state<float>(make_args<float>(m, 1), p.soff, (int32_t)N, xy ? (float*)sxy : nullptr,
+                                cls ? scls : nullptr, dprev ? sdp : nullptr, m->st);
+    CUDA_TRY(cudaGetLastError());
+    if (xy) CUDA_TRY(cudaMemcpyAsync(xy, sxy, 2 * N * T, cudaMemcpyDeviceToHost, m->st));
+    if (cls) CUDA_TRY(cudaMemcpyAsync(cls, scls, N, cudaMemcpyDeviceToHost, m->st));
+    if (dprev) CUDA_TRY(cudaMemcpyAsync(dprev, sdp, N * sizeof(double), cudaMemcpyDeviceToHost, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return sync_out(m);
+}
+
 static int set_method_state(mesh_s* m, int k, int32_t switched, double pa, double pb, double pm) {
     int rc = sync_in(m);
     if (rc) return rc;
@@ -1036,7 +1176,7 @@ static int set_tuning(mesh_s* m, double nopt, int32_t lanes) {
         drop_alloc(m, m->bcount);
         drop_alloc(m, m->bstart);
         drop_alloc(m, m->scan_tmp);
-        size_t scan_n = std::max<size_t>((size_t)m->nbtot + 1, (size_t)m->nslots + 1);
+        size_t scan_n = std::max<size_t>((size_t)m->nbtot + 1, (size_t)std::max(m->nslots, m->ncap) + 1);
         m->bcount = dalloc<int32_t>(m, (size_t)m->nbtot, rc);
         m->bstart = dalloc<int32_t>(m, (size_t)m->nbtot + 1, rc);
         m->scan_tmp = dalloc<int32_t>(m, scan_n / 4096 + 2, rc);
@@ -1244,6 +1384,9 @@ void mesh_default_params(mesh_params* p) {
     p->eta = 0.5;
     p->damping = 1.0;
     p->fac_retria = 0.1;
+    p->fac_add = 0.6;
+    p->T_add = 0.002;
+    p->n_total = 0;
 }
 
 const char* mesh_last_error(void) { return g_err.c_str(); }
@@ -1281,6 +1424,18 @@ int mesh_rebuild(mesh_t* m, mesh_stats* stats) {
 int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
     return do_step(m, n_iters, stats);
+}
+
+int mesh_get_state(mesh_t* m, void* xy, uint8_t* cls, double* dprev) {
+    if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
+    return get_state(m, 0, xy, cls, dprev);
+}
+
+int mesh_get_count(mesh_t* m, int64_t* n_current, int64_t* n_total) {
+    if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
+    if (n_current) *n_current = m->parts[0].n;
+    if (n_total) *n_total = m->ncap;
+    return TRIME_OK;
 }
 
 int mesh_get_triangles(mesh_t* m, int32_t* tri, int64_t cap, int64_t* n_out) {
@@ -1354,6 +1509,7 @@ int mesh_set_tuning(mesh_t* m, double n_opt, int32_t lanes) {
 int mesh_features(mesh_t* m, uint16_t* X, float* h) {
     if (!m || !X) return fail(TRIME_EINVAL, "NULL argument");
     if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    if (growing(m)) return fail(TRIME_EINVAL, "learned proposals need N_current = N_total (point addition unfinished)");
     if (m->nslots == 0) return TRIME_OK;
     int rc = sync_in(m);
     if (rc || (rc = ensure_learn(m)) || (rc = read_ctrl(m))) return rc;
@@ -1370,6 +1526,7 @@ int mesh_features(mesh_t* m, uint16_t* X, float* h) {
 int mesh_collect_pairs(mesh_t* m, int32_t horizon, uint16_t* X, float* T) {
     if (!m || !X || !T || horizon < 1) return fail(TRIME_EINVAL, "bad argument");
     if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    if (growing(m)) return fail(TRIME_EINVAL, "learned proposals need N_current = N_total (point addition unfinished)");
     if (!is_device_ptr(X) || !is_device_ptr(T)) return fail(TRIME_EINVAL, "X and T must be device arrays");
     if (m->nslots == 0) return TRIME_OK;
     int rc = sync_in(m);
@@ -1392,6 +1549,7 @@ int mesh_collect_pairs(mesh_t* m, int32_t horizon, uint16_t* X, float* T) {
 int mesh_propose(mesh_t* m, mlp_t* net, double jump) {
     if (!m || !net || !(jump > 0)) return fail(TRIME_EINVAL, "bad argument");
     if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    if (growing(m)) return fail(TRIME_EINVAL, "learned proposals need N_current = N_total (point addition unfinished)");
     if (m->nslots == 0) return TRIME_OK;
     int rc = sync_in(m);
     if (rc || (rc = ensure_learn(m)) || (rc = read_ctrl(m)) || (rc = enqueue_propose(m, net, jump))) return rc;
@@ -1404,6 +1562,7 @@ int mesh_step_learned(mesh_t* m, mlp_t* net, int32_t n_iters, int32_t every, dou
     if (!m || !net || !stats || n_iters < 0 || every < 1 || !(jump > 0) || !(min_angle_tol >= 0))
         return fail(TRIME_EINVAL, "bad argument");
     if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    if (growing(m)) return fail(TRIME_EINVAL, "learned proposals need N_current = N_total (point addition unfinished)");
     return do_step_learned(m, net, n_iters, every, jump, min_angle_tol, max_proposals, stats, accepted, rejected);
 }
 

@@ -404,7 +404,18 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_pre(const __grid_constan
     }
     bool qend = ctrl->have_prev && ra < P.T_end_q && rb < P.T_end_q && rm < P.T_end_amax;
     int method, term = 0;
-    if (ctrl->method_param == 2) {
+    if (P.adding) {
+        // Sec. 3.6: until N_total is reached a stalled mesh gets new points
+        // (the host adds them while the graph is paused: terminated = 2);
+        // the hybrid switch and the termination tests wait for N_total
+        if (ctrl->have_prev && ra < P.T_add && rb < P.T_add && n > 0) {
+            ctrl->have_prev = 0;  // the next change is not measured across the addition
+            ctrl->iterations += 1;
+            ctrl->terminated = 2;
+            return;
+        }
+        method = ctrl->method_param == 1 ? 1 : 0;
+    } else if (ctrl->method_param == 2) {
         if (!ctrl->switched) {
             if (ctrl->have_prev && ra < P.T_switch) ctrl->switched = 1;  // Sec. 4.2
         } else if (qend) {
@@ -415,7 +426,7 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_pre(const __grid_constan
         method = ctrl->method_param;
         term = qend;
     }
-    if (ctrl->target_min_ang > 0.0) {
+    if (ctrl->target_min_ang > 0.0 && !P.adding) {
         // a quality target replaces the quality termination test: iterate
         // until the minimum angle reaches it
         term = n > 0 && ctrl->min_ang >= ctrl->target_min_ang;
@@ -455,7 +466,7 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_post(const __grid_consta
     ctrl->size_dev = sh[0][1] > 0 ? sh[0][0] / sh[0][1] : 0.0;
     int small = sh[0][2] == 0.0;
     ctrl->small_moves = small;
-    if (small) ctrl->terminated = 1;  // Sec. 4: every inner move below fac_end * h_i
+    if (small && !V.P.adding) ctrl->terminated = 1;  // Sec. 4: every inner move below fac_end * h_i
     // Algorithm 1: DistMesh re-triangulates after a large movement only
     ctrl->retri = ctrl->method_param != 0 || !(V.P.fac_retria > 0.0) || ctrl->moved_far;
     ctrl->moved_far = 0;

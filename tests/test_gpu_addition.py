@@ -1,0 +1,158 @@
+"""GPU parity of the point-addition scheme (Sec. 3.6, rescaling Sec. 3.7)
+against the oracle: one addition from identical states (bit-exact in FP64),
+the growth of a mesh to N_total, and the selection at full size checked
+against the definition written out in numpy."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import TOL_FP32, annulus_small, make_pair, sorted_tris
+
+pytestmark = pytest.mark.gpu
+
+
+def _sync(gm, om):
+    gm.set_state(om.points(), om.classes(), om.dprev())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_one_addition_matches_oracle(precision):
+    gm, om = make_pair(annulus_small(n=6007, seed=21), precision=precision, method=2, n_total=20000, T_add=1e9)
+    gm.step(1)
+    om.step()
+    if precision == 0:
+        _sync(gm, om)
+    else:
+        om.set_points(gm.points().astype(np.float64))
+        gm.set_state(None, om.classes(), om.dprev())
+    n0 = om.n
+    sg, so = gm.step(1), om.step()
+    assert so["added"] == int(np.floor(0.6 * n0)) and sg["added"] == so["added"]
+    assert sg["n_points"] == so["n_points"] == gm.n == om.n == n0 + so["added"]
+    assert sg["iterations"] == 1 and not sg["terminated"]
+    xg, cg, dg = gm.state()
+    xo, co, do = om.points(), om.classes(), om.dprev()
+    # the old points did not move
+    assert np.array_equal(xg[:n0].astype(np.float64), xo[:n0])
+    if precision == 0:
+        assert np.array_equal(xg, xo)  # same triangles, keys, order and centroids
+        assert np.array_equal(cg, co)
+        assert np.array_equal(dg, do)  # h_i rescaled identically
+    else:
+        err = np.abs(xg[n0:].astype(np.float64) - xo[n0:]).max(1) / np.maximum(np.abs(xo[n0:]).max(1), 1e-3)
+        assert err.max() < TOL_FP32
+        assert (cg[n0:] != co[n0:]).mean() < 1e-3
+        assert np.allclose(dg[n0:], do[n0:], rtol=1e-6)
+    # the next iteration triangulates all points, like the oracle
+    if precision == 0:
+        _sync(gm, om)
+        sg, so = gm.step(1), om.step()
+        assert sg["n_tri"] == so["n_tri"] and so["triangulated"] == 1
+        # both hold the triangulation of the iteration that just ran
+        assert np.array_equal(sorted_tris(gm.triangles()), sorted_tris(om.triangles()))
+
+
+def test_growth_to_n_total():
+    """20000 -> 32000 (+12000) -> 50000 (+min(19200, 18000)); the hybrid
+    switches and terminates only with all points present."""
+    wl = W.annulus_workload(n=20000, seed=22, sdf_n=512, siz_n=256)
+    import paper_2309_13824_gb300 as g
+
+    gm = g.Mesh(wl.sdf, wl.sizing, wl.points, method=2, n_total=50000)
+    assert gm.n == 20000 and gm.n_total == 50000
+    seq, switched_at = [], None
+    for it in range(1500):
+        s = gm.step(1)
+        if s["added"]:
+            seq.append((s["added"], s["n_points"]))
+            assert s["iterations"] == 1
+        if s["switched"] and switched_at is None:
+            switched_at = it
+            assert s["n_points"] == 50000
+        if s["n_points"] < 50000:
+            assert not s["switched"] and not s["terminated"]
+        if s["terminated"]:
+            break
+    assert seq == [(12000, 32000), (18000, 50000)]
+    assert s["terminated"] and gm.n == 50000
+    assert s["min_angle_deg"] > 10.0 and s["max_alpha"] < 10.0
+    p = gm.points()
+    assert len(p) == 50000 and np.isfinite(p).all()
+    t = gm.triangles()
+    assert len(np.unique(t)) > 0.99 * 50000
+
+
+def test_many_iterations_per_call():
+    """One call of many iterations pauses, adds and resumes inside the call:
+    the same additions as one iteration per call."""
+    wl = W.annulus_workload(n=5000, seed=23, sdf_n=512, siz_n=256)
+    import paper_2309_13824_gb300 as g
+
+    a = g.Mesh(wl.sdf, wl.sizing, wl.points, method=2, n_total=12000)
+    b = g.Mesh(wl.sdf, wl.sizing, wl.points, method=2, n_total=12000)
+    sa = a.step(400)
+    added, iters = 0, 0
+    for _ in range(400):
+        s = b.step(1)
+        added += s["added"]
+        iters += s["iterations"]
+        if s["terminated"]:
+            break
+    assert sa["added"] == added == 7000 and a.n == b.n == 12000
+    assert 0 < sa["iterations"] <= 400 and iters > 0
+
+
+def test_full_size_selection_against_definition():
+    """Annulus with 10^6 initial points, N_total 1.6 x 10^6, addition forced
+    at the second iteration: the 6 x 10^5 new points are exactly the
+    centroids of the valid triangles with the largest circumradius / h_i
+    (textbook circumradius, h_i of the centroid's cell), numbered in the
+    ascending order of their vertex triples."""
+    from scipy.spatial import cKDTree
+
+    import paper_2309_13824_gb300 as g
+
+    wl = W.annulus_workload(n=1_000_000, seed=1, sdf_n=1024, siz_n=512)
+    gm = g.Mesh(wl.sdf, wl.sizing, wl.points, method=2, n_total=1_600_000, T_add=1e9)
+    gm.step(1)
+    gm.rebuild()  # the triangulation the adding iteration will compute
+    tri = gm.triangles().astype(np.int64)
+    p0 = gm.points()
+    n0 = len(p0)
+    s = gm.step(1)
+    assert s["added"] == 600_000 and gm.n == 1_600_000
+    new = gm.points()[n0:]
+    om = oracle.OracleMesh(wl.sdf, wl.sizing, wl.points[:n0], method=2)
+    _, h, _, _ = om.geometry()
+    a, b, c = p0[tri[:, 0]], p0[tri[:, 1]], p0[tri[:, 2]]
+    la = np.linalg.norm(b - c, axis=1)
+    lb = np.linalg.norm(c - a, axis=1)
+    lc = np.linalg.norm(a - b, axis=1)
+    area = 0.5 * np.abs((b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0]))
+    R = la * lb * lc / (4 * area)
+    gc = (a + b + c) / 3.0
+    sdf = wl.sdf
+    dx = (sdf.x1 - sdf.x0) / (sdf.nx - 1)
+    dy = (sdf.y1 - sdf.y0) / (sdf.ny - 1)
+    gi = np.clip(np.floor((gc[:, 0] - sdf.x0) / dx), 0, sdf.nx - 2).astype(int)
+    gj = np.clip(np.floor((gc[:, 1] - sdf.y0) / dy), 0, sdf.ny - 2).astype(int)
+    ratio = R / h[gj, gi]
+    d, k = cKDTree(gc).query(new)
+    assert np.all(d <= 1e-13)
+    sel = np.zeros(len(tri), bool)
+    sel[k] = True
+    assert sel.sum() == 600_000
+    lo_sel, hi_uns = ratio[sel].min(), ratio[~sel].max()
+    assert lo_sel >= hi_uns * (1 - 1e-9), (lo_sel, hi_uns)
+    trip = np.sort(tri[k], axis=1)
+    order = np.lexsort((trip[:, 2], trip[:, 1], trip[:, 0]))
+    assert np.array_equal(order, np.arange(len(order)))
+
+
+def test_batch_rejects_point_addition():
+    import paper_2309_13824_gb300 as g
+
+    wl = W.disk_workload(n=1000, seed=3)
+    with pytest.raises(g.MeshError):
+        g.MeshBatch([(wl.sdf, wl.sizing, wl.points)], autotune=False, n_total=5000)
