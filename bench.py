@@ -349,6 +349,69 @@ def distmesh_leg(g, torch, stream):
     return out
 
 
+_STAR = {}
+
+
+def star_1e6():
+    """The star polygon with 10^6 points (2048^2 SDF, 512^2 sizing), built once."""
+    import workloads as W
+
+    if "w" not in _STAR:
+        _STAR["w"] = W.star_workload(1_000_000, sdf_n=2048, siz_n=512, workers=min(16, os.cpu_count() or 1))
+    return _STAR["w"]
+
+
+def addition_leg(g, torch, stream):
+    """Point addition (Sec. 3.6) against initialising all points, the paper's
+    comparison on its complicated shape: the star with N_total = 10^6, hybrid,
+    FP32 positions, from fac_init N_total = 2 x 10^5 seeds (the first points of
+    the same density sample) or all 10^6, until termination.  Also the device
+    time of one addition at that size (10^6 -> 1.6 x 10^6 points)."""
+    import workloads as W
+
+    star = star_1e6()
+    p32 = W.to_fp32_positions(star.points)
+    out = {}
+    for name, pts, kw in (("point_addition", p32[:200_000], {"n_total": 1_000_000}), ("init_all", p32, {})):
+        m = g.Mesh(star.sdf, star.sizing, pts, method=2, precision=1, stream=stream.cuda_stream, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        added = iters = 0
+        seq = []
+        for _ in range(40):
+            s = m.step(100)
+            iters += s["iterations"]
+            if s["added"]:
+                added += s["added"]
+                seq.append(s["n_points"])
+            if s["terminated"] or s["iterations"] == 0:
+                break
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "iterations": iters, "terminated": bool(s["terminated"]),
+                     "n_points": s["n_points"], "points_added": added, "n_after_each_addition": seq,
+                     "min_angle_deg": s["min_angle_deg"], "max_alpha": s["max_alpha"],
+                     "half_mean_alpha": s["half_mean_alpha"], "n_tri": s["n_tri"]}
+        m.close()
+    # one addition on its own: forced at the second iteration (T_add above any change)
+    m = g.Mesh(star.sdf, star.sizing, p32, method=2, precision=1, n_total=1_600_000, T_add=1e9,
+               stream=stream.cuda_stream)
+    m.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = m.step(1)
+    torch.cuda.synchronize()
+    t_add = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    m.step(1)
+    torch.cuda.synchronize()
+    out["one_addition"] = {"points_before": 1_000_000, "points_added": s["added"],
+                           "seconds_addition_call": t_add, "seconds_next_iteration": time.perf_counter() - t0,
+                           "note": "host clock around synchronous calls; the addition call includes its "
+                                   "triangulating iteration, the selection and the graph re-capture"}
+    m.close()
+    return out
+
+
 def learned_leg(g, stream):
     """The learned displacement model: trained on the device on trajectories of
     the disk (DistMesh, 1e4 points) and the benchmark annulus (hybrid, 1e6),
@@ -403,7 +466,7 @@ def learned_leg(g, stream):
             wins += tl < tp
     out["annulus_1e6_fp64"] = {"seeds": seeds, "plain_to_target_seconds_total": tot_p,
                                "learned_to_target_seconds_total": tot_l, "learned_faster_on": wins}
-    star = W.star_workload(1_000_000, sdf_n=2048, siz_n=512, workers=min(16, os.cpu_count() or 1))
+    star = star_1e6()
     p32 = W.to_fp32_positions(star.points)
     out["star500_1e6_fp32"] = {"plain_converged": rec(*guarded(star, p32, 1)),
                                "learned_converged": rec(*guarded(star, p32, 1, net=net))}
@@ -549,6 +612,7 @@ def main():
         extras["batched"] = batched_leg(g, torch, stream, args.steps, flush)
         extras["learned"] = learned_leg(g, stream)
         extras["distmesh"] = distmesh_leg(g, torch, stream)
+        extras["point_addition"] = addition_leg(g, torch, stream)
         if args.sweep:
             extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
         threads = os.cpu_count() or 1

@@ -74,6 +74,26 @@ __device__ __forceinline__ void make_vertex(Lane& L, float nx2, float ny2, float
                  r * (fabsf(L.nx * ny2) + fabsf(L.ny * nx2));
     float err = 64.0f * kEps * perm * fabsf(iD);
     bool ok = (D != 0.0f) && (r + err < RB);  // false for NaN as well
+    if (!ok) {
+        // nearly parallel edges (a bisector almost along a bounding line):
+        // the float vertex is too uncertain, so solve again in double, where
+        // every product of two float inputs is exact and the vertex carries
+        // a few ulps of error.  Its float rounding then decides the later
+        // float cut tests like any other vertex.
+        double Dd = (double)L.nx * (double)ny2 - (double)L.ny * (double)nx2;
+        if (Dd != 0.0) {
+            double uxd = ((double)L.s * (double)ny2 - (double)s2 * (double)L.ny) / Dd;
+            double uyd = ((double)s2 * (double)L.nx - (double)L.s * (double)nx2) / Dd;
+            double rd = sqrt(uxd * uxd + uyd * uyd);
+            if (rd < (double)RB) {
+                ux = (float)uxd;
+                uy = (float)uyd;
+                err = (float)rd * (8.0f * kEps) + 1e-30f;
+                r = (float)rd;
+                ok = r + err < RB;
+            }
+        }
+    }
     L.vR = ok ? r + err : RB;
     L.vx = ok ? ux : 0.0f;
     L.vy = ok ? uy : 0.0f;

@@ -24,8 +24,10 @@ def test_one_addition_matches_oracle(precision):
     if precision == 0:
         _sync(gm, om)
     else:
-        om.set_points(gm.points().astype(np.float64))
-        gm.set_state(None, om.classes(), om.dprev())
+        # both continue from the oracle's state rounded to float positions
+        p32 = W.to_fp32_positions(om.points())
+        om.set_points(p32.astype(np.float64))
+        gm.set_state(p32, om.classes(), om.dprev())
     n0 = om.n
     sg, so = gm.step(1), om.step()
     assert so["added"] == int(np.floor(0.6 * n0)) and sg["added"] == so["added"]
@@ -148,6 +150,30 @@ def test_full_size_selection_against_definition():
     trip = np.sort(tri[k], axis=1)
     order = np.lexsort((trip[:, 2], trip[:, 1], trip[:, 0]))
     assert np.array_equal(order, np.arange(len(order)))
+
+
+def test_star_growth_keeps_cells_consistent():
+    """The complicated shape grown from 2 x 10^5 to 10^6 points (hybrid, FP32
+    positions) until termination.  Boundary points projected onto the
+    polygon's straight edges are collinear, and bisectors then nearly
+    coincide with edges of the bounding octagon (the vertex between them is
+    ill-conditioned in float and is solved again in double): no clip may be
+    inconsistent and no capacity guard may trip (a trip raises)."""
+    import os
+
+    import paper_2309_13824_gb300 as g
+
+    star = W.star_workload(1_000_000, sdf_n=2048, siz_n=512, workers=min(16, os.cpu_count() or 1))
+    p32 = W.to_fp32_positions(star.points)
+    m = g.Mesh(star.sdf, star.sizing, p32[:200_000], method=2, precision=1, n_total=1_000_000)
+    inconsistent = 0
+    for _ in range(40):
+        s = m.step(50)
+        inconsistent += s["clip_inconsistent"]
+        if s["terminated"]:
+            break
+    assert m.n == 1_000_000 and s["terminated"]
+    assert inconsistent == 0
 
 
 def test_batch_rejects_point_addition():
