@@ -378,17 +378,18 @@ def addition_leg(g, torch, stream):
         t0 = time.perf_counter()
         added = iters = 0
         seq = []
-        for _ in range(40):
-            s = m.step(100)
+        for _ in range(200):
+            s = m.step(20)
             iters += s["iterations"]
             if s["added"]:
                 added += s["added"]
-                seq.append(s["n_points"])
+                seq.append([iters, s["n_points"]])
             if s["terminated"] or s["iterations"] == 0:
                 break
         torch.cuda.synchronize()
         out[name] = {"seconds": time.perf_counter() - t0, "iterations": iters, "terminated": bool(s["terminated"]),
-                     "n_points": s["n_points"], "points_added": added, "n_after_each_addition": seq,
+                     "n_points": s["n_points"], "points_added": added,
+                     "iterations_and_n_after_calls_that_added": seq,
                      "min_angle_deg": s["min_angle_deg"], "max_alpha": s["max_alpha"],
                      "half_mean_alpha": s["half_mean_alpha"], "n_tri": s["n_tri"]}
         m.close()
@@ -635,7 +636,7 @@ def main():
                            "l2": "flushed before every timed step (256 MB write)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 13 * args.steps,
+                "gpu_launches": 14 * args.steps,
                 "last_step": {"method": st["method"], "switched": st["switched"], "n_tri": st["n_tri"],
                               "half_mean_alpha": st["half_mean_alpha"]}}
         line.update(extras)

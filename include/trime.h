@@ -97,7 +97,7 @@ typedef struct {
     double fac_mu;             /* Eq. 3 scaling factor                                    */
     int64_t exact_calls;       /* predicate evaluations that needed exact arithmetic      */
     int64_t clip_inconsistent; /* clips whose cut set was not one run (0 expected)        */
-    int64_t ring_overflow;     /* cells with more than 32 edges (results dropped)         */
+    int64_t ring_overflow;     /* cells with more than 64 edges (results dropped)         */
     int64_t exact_overflow;    /* exact-arithmetic capacity or underflow guard tripped    */
     int64_t newton_fail;       /* projections that kept p_old (Sec. 4.3)                  */
     int64_t trace_cap;         /* sphere traces that hit trace_max                        */

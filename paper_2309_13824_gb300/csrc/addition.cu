@@ -68,10 +68,10 @@ __device__ __forceinline__ bool prefix_le(const AddKey& k, const AddPrefix& q) {
 template <typename T, typename F>
 __device__ __forceinline__ void for_owned(const IterArgs<T>& a, int s, F&& f) {
     int ne = a.ring_n[s];
-    uint32_t vm = a.vmask[s];
+    uint64_t vm = a.vmask[s];
     int idi = a.srt.id[s];
     for (int t = 0; t < ne; t++) {
-        if (!((vm >> t) & 1u)) continue;
+        if (!((vm >> t) & 1ull)) continue;
         int j = a.ring[(size_t)s * kRingCap + t], k = a.ring[(size_t)s * kRingCap + (t + 1 == ne ? 0 : t + 1)];
         if (idi < a.srt.id[j] && idi < a.srt.id[k]) f(j, k);
     }

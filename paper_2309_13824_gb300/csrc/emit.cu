@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
         T xi = a.srt.x[s], yi = a.srt.y[s];
         int idi = a.srt.id[s];
         int ci = a.cell[s];
-        uint32_t vm = 0;
+        uint64_t vm = 0;
         if (ne >= 2) {
             CellC cc;
             const float4 pi4 = a.pf[s];
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
                 Nbr nxt = t + 1 < ne ? load_nbr(a, lab[t + 1], pi4, xi, yi) : first;
                 if (cur.slot >= 0 && nxt.slot >= 0 && emitted(a, V, cc, idi, ci, xi, yi, cur, nxt) &&
                     valid_tri(a, V, cc, idi, ci, xi, yi, cur, nxt)) {
-                    vm |= 1u << t;
+                    vm |= 1ull << t;
                     if (idi < cur.id && idi < nxt.id) {
                         // quality of the triangle (Eq. 11), float from the relative coordinates
                         float bx = cur.dx, by = cur.dy, cx = nxt.dx, cy = nxt.dy;
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
                 int j = lab[t];
                 if (j < 0) continue;
                 int tp = t == 0 ? ne - 1 : t - 1;
-                if (!((vm >> t) & 1u) && !((vm >> tp) & 1u)) continue;
+                if (!((vm >> t) & 1ull) && !((vm >> tp) & 1ull)) continue;
                 if (!(idi < a.srt.id[j])) continue;
                 acc[6] += 1.0;
                 if (cvd_now) {
@@ -407,13 +407,13 @@ __global__ void __launch_bounds__(kThreads) k_dm_keep(const __grid_constant__ It
         a.wrk.cls[s] = a.cur.cls[s];
         a.wrk.dprev[s] = a.cur.dprev[s];
         int ne = a.ring_n[s];
-        uint32_t vm = a.vmask[s];
+        uint64_t vm = a.vmask[s];
         int idi = a.srt.id[s];
         for (int t = 0; t < ne; t++) {
             int j = a.ring[(size_t)s * kRingCap + t];
             if (j < 0) continue;
             int tp = t == 0 ? ne - 1 : t - 1;
-            if (!((vm >> t) & 1u) && !((vm >> tp) & 1u)) continue;
+            if (!((vm >> t) & 1ull) && !((vm >> tp) & 1ull)) continue;
             if (!(idi < a.srt.id[j])) continue;
             T xj = a.cur.x[j], yj = a.cur.y[j];
             T dx = xj - xi, dy = yj - yi;
@@ -456,11 +456,11 @@ __global__ void k_tri_count(const __grid_constant__ IterArgs<T> a, int32_t s0, i
     if (r >= ns) return;
     int s = s0 + r;
     int ne = a.ring_n[s];
-    uint32_t vm = a.vmask[s];
+    uint64_t vm = a.vmask[s];
     int idi = a.srt.id[s];
     int c = 0;
     for (int t = 0; t < ne; t++) {
-        if (!((vm >> t) & 1u)) continue;
+        if (!((vm >> t) & 1ull)) continue;
         int j = a.ring[(size_t)s * kRingCap + t], k = a.ring[(size_t)s * kRingCap + (t + 1 == ne ? 0 : t + 1)];
         if (idi < a.srt.id[j] && idi < a.srt.id[k]) c++;
     }
@@ -474,11 +474,11 @@ __global__ void k_tri_write(const __grid_constant__ IterArgs<T> a, int32_t s0, i
     if (r >= ns) return;
     int s = s0 + r;
     int ne = a.ring_n[s];
-    uint32_t vm = a.vmask[s];
+    uint64_t vm = a.vmask[s];
     int idi = a.srt.id[s];
     int o = off[r];
     for (int t = 0; t < ne; t++) {
-        if (!((vm >> t) & 1u)) continue;
+        if (!((vm >> t) & 1ull)) continue;
         int j = a.ring[(size_t)s * kRingCap + t], k = a.ring[(size_t)s * kRingCap + (t + 1 == ne ? 0 : t + 1)];
         int idj = a.srt.id[j], idk = a.srt.id[k];
         if (idi < idj && idi < idk) {

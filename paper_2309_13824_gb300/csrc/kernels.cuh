@@ -6,10 +6,10 @@
 //                           every later kernel of the iteration indexes by
 //                           sorted slot, so neighbours are near in memory
 //   srt.cell / srt.key      geometry cell and bucket of each sorted slot
-//   ring[N][32] int32       cell edge labels, CCW: neighbour slot (>= 0) or a
-//                           bounding line (< 0); one 128-byte row per cell
+//   ring[N][64] int32       cell edge labels, CCW: neighbour slot (>= 0) or a
+//                           bounding line (< 0); one 256-byte row per cell
 //   ring_n[N] u8, cellR[N]  edge count, conservative max vertex distance
-//   vmask[N] u32            bit t: triangle (slot, ring[t], ring[t+1]) valid
+//   vmask[N] u64            bit t: triangle (slot, ring[t], ring[t+1]) valid
 #pragma once
 #include <string>
 
@@ -58,7 +58,7 @@ struct IterArgs {
     MeshView V;        // the mesh of single-mesh launches
     const MeshView* Vs;     // [nmesh] per-mesh views of batched launches
     const int32_t* cmesh;   // [n / kChunk] mesh of each chunk
-    int32_t* ovf_n;    // cells queued for the 32-lane Voronoi pass
+    int32_t* ovf_n;    // [2] cells queued for the 32-lane and for the serial Voronoi pass
     State<T> cur, srt;
     State<T> wrk;      // the positions a DistMesh iteration without re-triangulation moves (slot order)
     int32_t* cell;     // [n] geometry cell of each sorted slot (fixed formula)
@@ -72,11 +72,12 @@ struct IterArgs {
     int32_t* ring;
     uint8_t* ring_n;
     float* cellR;
-    uint32_t* vmask;
+    uint64_t* vmask;
     EmitPartial* ep;   // [n / kThreads] one per block of the emit kernel
     UpdatePartial* up;
     double* dbg;       // [8][n] by original id, written when P.debug
     int32_t* ovf_list; // [n] cells whose 16-lane clipping ran out of lanes
+    int32_t* ovf2_list; // [n] cells whose 32-lane clipping ran out of lanes (serial pass)
     float4* pf;        // [n] sorted positions as float pairs (xhi, xlo, yhi, ylo)
     float* pS;         // [n] octagon span S = fac_voro_bound * h of each sorted slot
 };

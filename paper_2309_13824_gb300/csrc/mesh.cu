@@ -89,7 +89,7 @@ struct mesh_s {
     int32_t* ring = nullptr;
     uint8_t* ring_n = nullptr;
     float* cellR = nullptr;
-    uint32_t* vmask = nullptr;
+    uint64_t* vmask = nullptr;
     EmitPartial* ep = nullptr;
     UpdatePartial* up = nullptr;
     int nblk = 1;
@@ -374,6 +374,7 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.up = m->up;
     a.dbg = m->dbg;
     a.ovf_list = m->ovf_list;
+    a.ovf2_list = m->ovf_list + std::max<int64_t>(m->ncap, m->nslots);
     a.pf = m->pf;
     a.pS = m->pS;
     return a;
@@ -477,7 +478,7 @@ static bool guard_tripped(const mesh_s* m) {
         eo += m->hctrl[k].cnt.exact_overflow;
     }
     if (!ro && !eo) return false;
-    fail(TRIME_EDEVICE, "capacity guard tripped: " + std::to_string(ro) + " cells with more than 32 edges, " +
+    fail(TRIME_EDEVICE, "capacity guard tripped: " + std::to_string(ro) + " cells with more than 64 edges, " +
                             std::to_string(eo) + " exact-arithmetic capacity or underflow guards");
     return true;
 }
@@ -795,17 +796,17 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->ring = dalloc<int32_t>(m, N * kRingCap, rc);
     m->ring_n = dalloc<uint8_t>(m, N, rc);
     m->cellR = dalloc<float>(m, N, rc);
-    m->vmask = dalloc<uint32_t>(m, N, rc);
+    m->vmask = dalloc<uint64_t>(m, N, rc);
     m->ep = dalloc<EmitPartial>(m, (size_t)nblk_cap, rc);
     m->up = dalloc<UpdatePartial>(m, (size_t)nblk_cap, rc);
     m->ctrl = dalloc<DevCtrl>(m, (size_t)nparts, rc);
-    m->ovf_n = dalloc<int32_t>(m, 1, rc);
+    m->ovf_n = dalloc<int32_t>(m, 2, rc);
     m->dbg = P.debug ? dalloc<double>(m, 10 * N, rc) : nullptr;
     m->tcnt = dalloc<int32_t>(m, N + 1, rc);
     m->toff = dalloc<int32_t>(m, N + 1, rc);
     m->tbuf = dalloc<int32_t>(m, 3 * (2 * nmax + 16), rc);
     m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
-    m->ovf_list = dalloc<int32_t>(m, N, rc);
+    m->ovf_list = dalloc<int32_t>(m, 2 * N, rc);
     m->pf = dalloc<float4>(m, N, rc);
     m->pS = dalloc<float>(m, N, rc);
     if (m->batched) {

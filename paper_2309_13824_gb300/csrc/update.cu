@@ -13,7 +13,7 @@
 
 namespace trime {
 
-constexpr int kPolyCap = 48;
+constexpr int kPolyCap = kRingCap + 16;  // ring edges plus the octagon and box clips
 
 // ------------------------------------------------------------------ CVD centroid
 template <typename T>
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
         T dprev = keep ? a.wrk.dprev[s] : a.srt.dprev[s];
         T h = (T)V.gh[a.cell[s]];
         int ne = a.ring_n[s];
-        uint32_t vm = a.vmask[s];
+        uint64_t vm = a.vmask[s];
         int lab[kRingCap];
         const int4* row = reinterpret_cast<const int4*>(a.ring + (size_t)s * kRingCap);
         for (int q = 0; q < (ne + 3) / 4; q++) {
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
             int j = lab[t];
             if (j < 0) continue;
             int tp = t == 0 ? ne - 1 : t - 1;
-            if (!((vm >> t) & 1u) && !((vm >> tp) & 1u)) continue;
+            if (!((vm >> t) & 1ull) && !((vm >> tp) & 1ull)) continue;
             bool owner = idi < a.srt.id[j];
             if (method != 0) {
                 if (owner) {

@@ -7,7 +7,8 @@
 // relative to the generator) and the vertex V_t = E_t cap E_{t+1}.  The main
 // pass uses G = 16 (two cells per warp; final cells have 6-8 edges); a cell
 // that would need more than 16 edges is queued and redone with G = 32 by the
-// same code.  Candidates come from the bucket grid ring by ring, one per lane,
+// same code, and one that needs more than 32 by a serial pass (one thread per
+// cell, up to 64 edges).  Candidates come from the bucket grid ring by ring, one per lane,
 // are filtered by the security radius (a point farther than twice the largest
 // vertex distance cannot cut), staged in shared memory and applied nearest
 // first across the staged set.  A clip classifies every vertex in parallel,
@@ -429,17 +430,22 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
         }
     }
     if (!live) return;
-    if (status == 2 && G < 32) {
-        // out of lanes: queue the cell for the 32-lane pass
+    if (status == 2) {
+        // out of lanes: queue the cell for the 32-lane pass, or from there
+        // for the serial pass
         if (g.gl == 0) {
-            int q = atomicAdd(a.ovf_n, 1);
-            a.ovf_list[q] = s;
+            if (G < 32) {
+                int q = atomicAdd(a.ovf_n, 1);
+                a.ovf_list[q] = s;
+            } else {
+                int q = atomicAdd(a.ovf_n + 1, 1);
+                a.ovf2_list[q] = s;
+            }
             if (P.debug) atomicAdd(&V.ctrl->cnt.vor_wide, 1ull);
         }
         return;
     }
     if (status != 0) {
-        if (status == 2 && g.gl == 0) atomicAdd(&V.ctrl->cnt.ring_overflow, 1ull);
         if (g.gl == 0) {
             a.ring_n[s] = 0;
             a.cellR[s] = 0.0f;
@@ -493,21 +499,261 @@ __global__ void __launch_bounds__(kVoroThreads) k_voronoi_wide(const __grid_cons
     }
 }
 
+// ------------------------------------------------------------------ serial pass
+// A cell with more than 32 edges (a sparse region bordering a dense one, e.g.
+// a coarse boundary cell facing other parts of the shape across a narrow gap)
+// is built by one thread with the same vertices, cut decisions, single-run
+// rule and candidate order (bucket ring by bucket ring, nearest first within
+// a staged set) as the warp passes; its polygon (up to kRingCap edges) and
+// staged candidates live in shared memory.
+constexpr int kSerialThreads = 16;
+constexpr int kSerialStage = 96;
+
+// edge as (nx, ny, s, label bits)
+__device__ __forceinline__ Lane edge_vertex(const float4& e, const float4& f, float RB) {
+    Lane L;
+    L.nx = e.x;
+    L.ny = e.y;
+    L.s = e.z;
+    L.lab = __float_as_int(e.w);
+    L.bb = false;
+    L.M = L.Qx = L.Qy = L.PM = L.PQx = L.PQy = 0.0f;
+    make_vertex(L, f.x, f.y, f.z, __float_as_int(f.w), RB);
+    return L;
+}
+
+// clip_by for one thread: 0 ok / no-op, 1 empty cell, 2 more than kRingCap edges
+template <typename T>
+__device__ int clip_serial(float4* E, int& ne, float nx, float ny, float s, int lab, bool bisector, float RB,
+                           const IterArgs<T>& a, const CellCtx& ctx) {
+    unsigned long long m = 0;
+    for (int t = 0; t < ne; t++) {
+        Lane L = edge_vertex(E[t], E[t + 1 == ne ? 0 : t + 1], RB);
+        bool cut;
+        if (bisector && L.bb) {
+            float cl = 2.0f * s;
+            float lam = fmaf(nx, L.Qx, fmaf(ny, L.Qy, cl * L.M));
+            float P = fabsf(nx) * L.PQx + fabsf(ny) * L.PQy + cl * L.PM;
+            float bound = 32.0f * kEps * P;
+            if (P > 1e-30f && lam < -bound) cut = true;
+            else if (P > 1e-30f && lam > bound) cut = false;
+            else cut = exact_cut<T>(a, ctx, L.lab, L.nlab, lab);
+        } else {
+            cut = nx * L.vx + ny * L.vy > s;
+        }
+        if (cut) m |= 1ull << t;
+    }
+    if (!m) return 0;
+    unsigned long long full = ne >= 64 ? ~0ull : ((1ull << ne) - 1ull);
+    if ((m & full) == full) return 1;
+    int starts = 0, sidx = -1;
+    for (int t = 0; t < ne; t++) {
+        int p = t == 0 ? ne - 1 : t - 1;
+        if (((m >> t) & 1ull) && !((m >> p) & 1ull)) {
+            starts++;
+            if (sidx < 0) sidx = t;
+        }
+    }
+    if (starts != 1) atomicAdd(&ctx.ctrl->cnt.clip_inconsistent, 1ull);
+    int eidx = sidx;
+    while ((m >> eidx) & 1ull) eidx = eidx + 1 == ne ? 0 : eidx + 1;
+    int k = sidx - eidx + 1;  // kept edges E_e .. E_s
+    if (k <= 0) k += ne;
+    if (k + 1 > kRingCap) return 2;
+    // rotate E_e to position 0 in place (three reversals), then append
+    auto rev = [&](int i, int j) {
+        for (; i < j; i++, j--) {
+            float4 x = E[i];
+            E[i] = E[j];
+            E[j] = x;
+        }
+    };
+    if (eidx > 0) {
+        rev(0, eidx - 1);
+        rev(eidx, ne - 1);
+        rev(0, ne - 1);
+    }
+    E[k] = make_float4(nx, ny, s, __int_as_float(lab));
+    ne = k + 1;
+    return 0;
+}
+
+template <typename T>
+__device__ float serial_rmax(const float4* E, int ne, float RB) {
+    float r = 0.0f;
+    for (int t = 0; t < ne; t++) r = fmaxf(r, edge_vertex(E[t], E[t + 1 == ne ? 0 : t + 1], RB).vR);
+    return r;
+}
+
+template <typename T>
+__device__ void voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int s, float4* E, float4* C) {
+    const DevParams& P = V.P;
+    const float INF = __int_as_float(0x7f800000);
+    const float4 pi4 = a.pf[s];
+    CellCtx ctx;
+    ctx.ctrl = V.ctrl;
+    ctx.si = s;
+    const float xf = (pi4.x - P.bx0f) + pi4.y, yf = (pi4.z - P.by0f) + pi4.w;
+    const float Wf = (float)(P.bx1 - P.bx0), Hf = (float)(P.by1 - P.by0);
+    float RB, mb;
+    int ne;
+    if (P.bounded) {
+        float S = a.pS[s];
+        float SB = S * (17.0f / 16.0f);
+        RB = SB * 1.0824459f * 1.0001f;
+        mb = S * (1.0f / 16.0f);
+        const float c8[8] = {1.f, 0.70710678f, 0.f, -0.70710678f, -1.f, -0.70710678f, 0.f, 0.70710678f};
+        for (int t = 0; t < 8; t++) E[t] = make_float4(c8[t], c8[(t + 6) & 7], SB, __int_as_float(oct_label(t)));
+        ne = 8;
+    } else {
+        mb = 0.125f * (Wf > Hf ? Wf : Hf);
+        RB = (sqrtf(Wf * Wf + Hf * Hf) + 4.0f * mb) * 1.0001f;
+        ne = 4;
+        for (int b = 0; b < 4; b++) {
+            int bs = b == 0 ? 2 : (b == 1 ? 1 : (b == 2 ? 3 : 0));
+            float nx = bs == 0 ? -1.f : (bs == 1 ? 1.f : 0.f);
+            float ny = bs == 2 ? -1.f : (bs == 3 ? 1.f : 0.f);
+            float sb = bs == 0 ? xf + mb : bs == 1 ? (Wf - xf) + mb : bs == 2 ? yf + mb : (Hf - yf) + mb;
+            E[b] = make_float4(nx, ny, sb, __int_as_float(box_label(bs)));
+        }
+    }
+    int status = 0;
+    if (P.bounded) {
+        for (int b = 0; b < 4 && status == 0; b++) {
+            float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
+            float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
+            float sb = b == 0 ? xf + mb : b == 1 ? (Wf - xf) + mb : b == 2 ? yf + mb : (Hf - yf) + mb;
+            status = clip_serial<T>(E, ne, nx, ny, sb, box_label(b), false, RB, a, ctx);
+        }
+    }
+    float Rmax = status == 0 ? serial_rmax<T>(E, ne, RB) : 0.0f;
+    int bxi, byi;
+    bucket_of(P, pi4.x, pi4.z, bxi, byi);
+    const float bsx = (float)P.bsx, bsy = (float)P.bsy;
+    const float bmargin = (float)(1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy)) + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
+    bool done = status != 0;
+    int nst = 0;
+    // apply the staged candidates nearest first
+    auto flush = [&]() {
+        unsigned long long used0 = 0, used1 = 0;
+        while (!done) {
+            float best = INF;
+            int bi = -1;
+            for (int q = 0; q < nst; q++) {
+                bool u = q < 64 ? (used0 >> q) & 1ull : (used1 >> (q - 64)) & 1ull;
+                if (!u && C[q].z < best) {
+                    best = C[q].z;
+                    bi = q;
+                }
+            }
+            if (bi < 0 || !(best < 4.0f * Rmax * Rmax * 1.0001f)) break;
+            if (bi < 64) used0 |= 1ull << bi;
+            else used1 |= 1ull << (bi - 64);
+            float4 c = C[bi];
+            int ne0 = ne;
+            int st = clip_serial<T>(E, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, RB, a, ctx);
+            if (P.debug) {
+                atomicAdd(&V.ctrl->cnt.vor_picks, 1ull);
+                if (ne != ne0 || st) atomicAdd(&V.ctrl->cnt.vor_cuts, 1ull);
+            }
+            if (st) {
+                status = st;
+                done = true;
+            } else if (ne != ne0) {
+                Rmax = serial_rmax<T>(E, ne, RB);
+            }
+        }
+        nst = 0;
+    };
+    for (int r = 1; !done; r++) {
+        int nr = r == 1 ? 5 : 4 * r;
+        for (int k = 0; k < nr && !done; k++) {
+            int row, c0, c1;
+            if (r == 1) {
+                row = k < 3 ? byi : (k == 3 ? byi - 1 : byi + 1);
+                c0 = k == 0 ? bxi : (k == 1 ? bxi - 1 : (k == 2 ? bxi + 1 : bxi - 1));
+                c1 = k == 0 ? bxi : (k == 1 ? bxi - 1 : (k == 2 ? bxi + 1 : bxi + 1));
+                if (k == 1 && c0 < 0) c0 = 1, c1 = 0;
+                if (k == 2 && c1 >= P.nbx) c0 = 1, c1 = 0;
+            } else if (k < 2) {
+                row = k == 0 ? byi - r : byi + r;
+                c0 = bxi - r;
+                c1 = bxi + r;
+            } else {
+                int kk = k - 2;
+                row = byi - r + 1 + (kk >> 1);
+                c0 = c1 = (kk & 1) ? bxi + r : bxi - r;
+            }
+            c0 = c0 < 0 ? 0 : c0;
+            c1 = c1 >= P.nbx ? P.nbx - 1 : c1;
+            if (row < 0 || row >= P.nby || c0 > c1) continue;
+            int lo = a.bstart[V.boff + row * P.nbx + c0], hi = a.bstart[V.boff + row * P.nbx + c1 + 1];
+            for (int cs = lo; cs < hi && !done; cs++) {
+                if (cs == s || a.dom[cs]) continue;
+                float4 pj4 = a.pf[cs];
+                float dx = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y);
+                float dy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
+                float d2 = dx * dx + dy * dy;
+                if (sizeof(T) == 8 && d2 < 9.094947e-13f) {
+                    dx = (float)((double)a.srt.x[cs] - (double)a.srt.x[s]);
+                    dy = (float)((double)a.srt.y[cs] - (double)a.srt.y[s]);
+                    d2 = dx * dx + dy * dy;
+                }
+                if (!(d2 < 4.0f * Rmax * Rmax * 1.0001f)) continue;
+                if (nst == kSerialStage) flush();
+                C[nst++] = make_float4(dx, dy, d2, __int_as_float(cs));
+            }
+        }
+        flush();
+        if (!done) {
+            float dmin = INF;
+            if (bxi - r > 0) dmin = fminf(dmin, xf - (float)(bxi - r) * bsx);
+            if (bxi + r < P.nbx - 1) dmin = fminf(dmin, (float)(bxi + r + 1) * bsx - xf);
+            if (byi - r > 0) dmin = fminf(dmin, yf - (float)(byi - r) * bsy);
+            if (byi + r < P.nby - 1) dmin = fminf(dmin, (float)(byi + r + 1) * bsy - yf);
+            bool all = bxi - r <= 0 && bxi + r >= P.nbx - 1 && byi - r <= 0 && byi + r >= P.nby - 1;
+            if (all || 2.0f * Rmax * 1.0001f < dmin - bmargin) done = true;
+        }
+    }
+    if (status != 0) {
+        if (status == 2) atomicAdd(&V.ctrl->cnt.ring_overflow, 1ull);
+        a.ring_n[s] = 0;
+        a.cellR[s] = 0.0f;
+        return;
+    }
+    for (int t = 0; t < ne; t++) a.ring[(size_t)s * kRingCap + t] = __float_as_int(E[t].w);
+    a.ring_n[s] = (uint8_t)ne;
+    a.cellR[s] = Rmax;
+}
+
+template <typename T, bool B>
+__global__ void __launch_bounds__(kSerialThreads) k_voronoi_serial(const __grid_constant__ IterArgs<T> a) {
+    if (!B && skip_rebuild(a.V.ctrl, a.force)) return;
+    __shared__ float4 edges[kSerialThreads][kRingCap + 1];
+    __shared__ float4 stage[kSerialThreads][kSerialStage];
+    int n = a.ovf_n[1];
+    for (int i = blockIdx.x * kSerialThreads + threadIdx.x; i < n; i += gridDim.x * kSerialThreads) {
+        int s = a.ovf2_list[i];
+        voronoi_cell_serial<T>(a, mesh_of<B>(a, s), s, edges[threadIdx.x], stage[threadIdx.x]);
+    }
+}
+
 // lanes = 16: two cells per warp plus the 32-lane pass; lanes = 32: one cell
 // per warp
 template <typename T, bool B>
 void launch_voronoi_impl(const IterArgs<T>& a, int lanes, cudaStream_t st) {
-    cudaMemsetAsync(a.ovf_n, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(a.ovf_n, 0, 2 * sizeof(int32_t), st);
     if (lanes == 32) {
         int cpb = kVoroThreads / 32;
         int g = (a.n + cpb - 1) / cpb;
         k_voronoi<T, 32, B><<<g < 1 ? 1 : g, kVoroThreads, 0, st>>>(a);
-        return;
+    } else {
+        int cpb = kVoroThreads / 16;  // cells per block
+        int g = (a.n + cpb - 1) / cpb;
+        k_voronoi<T, 16, B><<<g < 1 ? 1 : g, kVoroThreads, 0, st>>>(a);
+        k_voronoi_wide<T, B><<<152 * 2, kVoroThreads, 0, st>>>(a);
     }
-    int cpb = kVoroThreads / 16;  // cells per block
-    int g = (a.n + cpb - 1) / cpb;
-    k_voronoi<T, 16, B><<<g < 1 ? 1 : g, kVoroThreads, 0, st>>>(a);
-    k_voronoi_wide<T, B><<<152 * 2, kVoroThreads, 0, st>>>(a);
+    k_voronoi_serial<T, B><<<152, kSerialThreads, 0, st>>>(a);
 }
 
 }  // namespace trime

@@ -300,3 +300,31 @@ def test_distmesh_keeps_triangulation_like_the_oracle():
         # 1e-6 h is far below the 0.1 h the re-triangulation decision reads
         assert err.max() < 1e-6, (k, err.max())
     assert 1 < tri_g < steps, (tri_g, steps)
+
+
+def _ringed_point(k, seed=5):
+    """One point ringed by k jittered neighbours (its cell has k edges), plus a
+    few far points: SDF of the square [-1, 1]^2, uniform sizing."""
+    rng = np.random.default_rng(seed)
+    sdf = W.grid_from_fn(lambda x, y: np.maximum(np.abs(x), np.abs(y)) - 1.0, 65)
+    siz = W.constant_grid(1.0)
+    th = 2 * np.pi * (np.arange(k) + 0.2 * rng.uniform(-1, 1, k)) / k
+    rad = 0.12 * (1 + 0.01 * rng.uniform(-1, 1, k))
+    ring = np.stack([0.1 + rad * np.cos(th), -0.05 + rad * np.sin(th)], 1)
+    far = np.array([[0.8, 0.8], [-0.8, 0.7], [-0.7, -0.8], [0.75, -0.7]])
+    return sdf, siz, np.concatenate([[[0.1, -0.05]], ring, far])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cells_with_more_than_32_edges(precision):
+    """A cell with 40 edges goes through the serial pass and gives the
+    oracle's triangles; one with 70 (over the 64-edge ring) is reported by
+    the capacity guard."""
+    gm, om = make_pair(_ringed_point(40), precision=precision, method=1)
+    st, tg = _tri_equal(gm, om)
+    assert len(om.ring(0)) == 40 and st["ring_overflow"] == 0 and st["clip_inconsistent"] == 0
+    assert np.count_nonzero(tg == 0) >= 38  # the triangles around the ringed point
+    gm2, _ = make_pair(_ringed_point(70), precision=precision, method=1)
+    with pytest.raises(Exception) as e:
+        gm2.rebuild()
+    assert "more than 64 edges" in str(e.value)
