@@ -164,9 +164,12 @@ struct MlpDev {
 // Y[i] (2 floats) for the rows X[idx ? idx[i] : i] (48 BF16 each), i < n
 void launch_mlp_forward(const MlpDev& w, const uint16_t* X, const int32_t* idx, int n, float* Y, int* err,
                         cudaStream_t st);
-// grad += d/dp of sum (Y - T)^2 * scale / 2 over the n rows; loss += that sum
-void launch_mlp_grad(const MlpDev& w, const uint16_t* X, const float* T, const int32_t* idx, int n, float scale,
-                     float* grad, double* loss, int* err, cudaStream_t st);
+// d/dp of sum (Y - T)^2 * scale / 2 over the n rows, as per-CTA partial sums
+// in gpart[c][kMlpParams] for c < the returned count (at most kGradParts);
+// loss += that sum
+constexpr int kGradParts = 152;
+int launch_mlp_grad(const MlpDev& w, const uint16_t* X, const float* T, const int32_t* idx, int n, float scale,
+                    float* gpart, double* loss, int* err, cudaStream_t st);
 // features of every slot of a single mesh (slot order, or by point id with
 // by_id), h_i per row, optionally the positions by id; the last move is the
 // position minus (qx, qy)[id] (zero without them)

@@ -249,7 +249,7 @@ __device__ __forceinline__ void mmas(uint32_t d, const void* A, const void* B, i
 
 __global__ void __launch_bounds__(kRows, 1) k_mlp_grad(const MlpDev w, const uint16_t* __restrict__ X,
                                                        const float* __restrict__ T, const int32_t* __restrict__ idx,
-                                                       int n, float scale, float* __restrict__ grad, double* loss,
+                                                       int n, float scale, float* __restrict__ gpart, double* loss,
                                                        int* err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sW1 = smem;
@@ -399,26 +399,31 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_grad(const MlpDev w, const uin
         if (!(ok = wait_all(&bar, phase))) break;
         first = false;
     }
+    // this CTA's gradient sums into its own slot (lane r = row r of the
+    // transposed gradients); the slots are added in a fixed order afterwards,
+    // so training is deterministic
+    float* G = gpart + (size_t)blockIdx.x * kMlpParams;
     if (ok && !first) {
-        // this CTA's gradient sums into global memory (lane r = row r of the transposed gradients)
         float a[kMlpHid];
 #pragma unroll
         for (int c = 0; c < 4; c++) tc::tmem_ld16(tbase + lane + cA1 + 16 * c, a + 16 * c);
         if (tid < kMlpIn)
-            for (int u = 0; u < kMlpHid; u++) atomicAdd(&grad[kOW1 + u * kMlpIn + tid], a[u]);
+            for (int u = 0; u < kMlpHid; u++) G[kOW1 + u * kMlpIn + tid] = a[u];
         else if (tid == kMlpIn)
-            for (int u = 0; u < kMlpHid; u++) atomicAdd(&grad[kOB1 + u], a[u]);
+            for (int u = 0; u < kMlpHid; u++) G[kOB1 + u] = a[u];
 #pragma unroll
         for (int c = 0; c < 4; c++) tc::tmem_ld16(tbase + lane + cA2 + 16 * c, a + 16 * c);
         if (tid < kMlpHid)
-            for (int u = 0; u < kMlpHid; u++) atomicAdd(&grad[kOW2 + u * kMlpHid + tid], a[u]);
+            for (int u = 0; u < kMlpHid; u++) G[kOW2 + u * kMlpHid + tid] = a[u];
         else if (tid == kMlpHid)
-            for (int u = 0; u < kMlpHid; u++) atomicAdd(&grad[kOB2 + u], a[u]);
+            for (int u = 0; u < kMlpHid; u++) G[kOB2 + u] = a[u];
         tc::tmem_ld16(tbase + lane + cA3, a);
         if (tid < kMlpHid)
-            for (int o = 0; o < kMlpOut; o++) atomicAdd(&grad[kOW3 + o * kMlpHid + tid], a[o]);
+            for (int o = 0; o < kMlpOut; o++) G[kOW3 + o * kMlpHid + tid] = a[o];
         else if (tid == kMlpHid)
-            for (int o = 0; o < kMlpOut; o++) atomicAdd(&grad[kOB3 + o], a[o]);
+            for (int o = 0; o < kMlpOut; o++) G[kOB3 + o] = a[o];
+    } else {
+        for (int k = tid; k < kMlpParams; k += kRows) G[k] = 0.f;
     }
     // loss of this CTA's samples
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
@@ -434,22 +439,33 @@ __global__ void __launch_bounds__(kRows, 1) k_mlp_grad(const MlpDev w, const uin
     if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
-void launch_mlp_grad(const MlpDev& w, const uint16_t* X, const float* T, const int32_t* idx, int n, float scale,
-                     float* grad, double* loss, int* err, cudaStream_t st) {
-    if (n <= 0) return;
+int launch_mlp_grad(const MlpDev& w, const uint16_t* X, const float* T, const int32_t* idx, int n, float scale,
+                    float* gpart, double* loss, int* err, cudaStream_t st) {
+    if (n <= 0) return 0;
     int ntiles = (n + kRows - 1) / kRows;
-    int grid = std::min(ntiles, 152);
+    int grid = std::min(ntiles, kGradParts);
     cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem);
-    k_mlp_grad<<<grid, kRows, kGradSmem, st>>>(w, X, T, idx, n, scale, grad, loss, err);
+    k_mlp_grad<<<grid, kRows, kGradSmem, st>>>(w, X, T, idx, n, scale, gpart, loss, err);
+    return grid;
 }
 
-// Adam on the FP32 parameters; refreshes the BF16 copies and clears the gradient
-__global__ void k_mlp_adam(float* p, float* grad, float* m, float* v, uint16_t* w1, uint16_t* w2, uint16_t* w3,
-                           float lr, float b1, float b2, float eps, float c1, float c2) {
+// the gradient: the per-CTA slots added in slot order
+__global__ void k_mlp_reduce(const float* gpart, int nparts, float* grad) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= kMlpParams) return;
-    float g = grad[k];
-    grad[k] = 0.f;
+    float g = 0.f;
+    for (int c = 0; c < nparts; c++) g += gpart[(size_t)c * kMlpParams + k];
+    grad[k] = g;
+}
+
+// Adam on the FP32 parameters (gradient: the per-CTA slots added in slot
+// order); refreshes the BF16 copies
+__global__ void k_mlp_adam(float* p, const float* gpart, int nparts, float* m, float* v, uint16_t* w1, uint16_t* w2,
+                           uint16_t* w3, float lr, float b1, float b2, float eps, float c1, float c2) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kMlpParams) return;
+    float g = 0.f;
+    for (int c = 0; c < nparts; c++) g += gpart[(size_t)c * kMlpParams + k];
     float mk = b1 * m[k] + (1.f - b1) * g;
     float vk = b2 * v[k] + (1.f - b2) * g * g;
     m[k] = mk;
@@ -712,6 +728,7 @@ extern "C" int mesh_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D,
 // ------------------------------------------------------------------ model handle
 struct mlp_s {
     float *p = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    float* gpart = nullptr;  // [kGradParts][kMlpParams] per-CTA gradient slots
     uint16_t *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;
     double* loss = nullptr;
     int* err = nullptr;
@@ -794,7 +811,7 @@ extern "C" {
 void mlp_destroy(mlp_t* m) {
     if (!m) return;
     if (m->st) cudaStreamSynchronize(m->st);
-    for (void* q : {(void*)m->p, (void*)m->grad, (void*)m->m, (void*)m->v, (void*)m->w1, (void*)m->w2, (void*)m->w3,
+    for (void* q : {(void*)m->p, (void*)m->grad, (void*)m->gpart, (void*)m->m, (void*)m->v, (void*)m->w1, (void*)m->w2, (void*)m->w3,
                     (void*)m->loss, (void*)m->err, (void*)m->perm, m->stage})
         cudaFree(q);
     if (m->ev) cudaEventDestroy(m->ev);
@@ -825,6 +842,7 @@ int mlp_create(mlp_t** out, const float* params, uint64_t seed, void* cuda_strea
               cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaMalloc(&m->p, sizeof(float) * kMlpParams) == cudaSuccess &&
               cudaMalloc(&m->grad, sizeof(float) * kMlpParams) == cudaSuccess &&
+              cudaMalloc(&m->gpart, sizeof(float) * kMlpParams * kGradParts) == cudaSuccess &&
               cudaMalloc(&m->m, sizeof(float) * kMlpParams) == cudaSuccess &&
               cudaMalloc(&m->v, sizeof(float) * kMlpParams) == cudaSuccess &&
               cudaMalloc(&m->w1, 2 * kMlpHid * kMlpIn) == cudaSuccess &&
@@ -910,13 +928,13 @@ int mlp_loss_grad(mlp_t* m, const uint16_t* X, const float* T, int64_t n, double
         MLP_TRY(cudaMemcpyAsync(tt, T, bt, cudaMemcpyHostToDevice, m->st));
         ts = tt;
     }
-    MLP_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, m->st));
     MLP_TRY(cudaMemsetAsync(m->loss, 0, sizeof(double), m->st));
-    launch_mlp_grad(mlp_view(m), xs, ts, nullptr, (int)n, 1.0f / (float)n, m->grad, m->loss, m->err, m->st);
+    int parts = launch_mlp_grad(mlp_view(m), xs, ts, nullptr, (int)n, 1.0f / (float)n, m->gpart, m->loss, m->err,
+                                m->st);
+    k_mlp_reduce<<<(kMlpParams + 255) / 256, 256, 0, m->st>>>(m->gpart, parts, m->grad);
     MLP_TRY(cudaGetLastError());
     MLP_TRY(cudaMemcpyAsync(grad, m->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, m->st));
     MLP_TRY(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st));
-    MLP_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kMlpParams, m->st));
     if ((rc = mlp_check_err(m))) return rc;
     return mlp_sync_out(m);
 }
@@ -949,12 +967,13 @@ int mlp_train(mlp_t* m, const uint16_t* X, const float* T, int64_t n, int32_t ep
         int64_t nb = 0;
         for (int64_t b0 = 0; b0 < n; b0 += batch) {
             int cnt = (int)std::min<int64_t>(batch, n - b0);
-            launch_mlp_grad(mlp_view(m), X, T, m->perm + b0, cnt, 1.0f / (float)cnt, m->grad, m->loss, m->err, m->st);
+            int parts = launch_mlp_grad(mlp_view(m), X, T, m->perm + b0, cnt, 1.0f / (float)cnt, m->gpart, m->loss,
+                                        m->err, m->st);
             m->t++;
             float c1 = (float)(1.0 - std::pow((double)b1, (double)m->t));
             float c2 = (float)(1.0 - std::pow((double)b2, (double)m->t));
-            k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, m->st>>>(m->p, m->grad, m->m, m->v, m->w1, m->w2, m->w3,
-                                                                     (float)lr, b1, b2, eps, c1, c2);
+            k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, m->st>>>(m->p, m->gpart, parts, m->m, m->v, m->w1, m->w2,
+                                                                     m->w3, (float)lr, b1, b2, eps, c1, c2);
             nb++;
         }
         MLP_TRY(cudaGetLastError());
