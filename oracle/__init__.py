@@ -106,6 +106,7 @@ def _load():
         lib.om_bilinear.argtypes = [P(_Grid), C.c_double, C.c_double]
         lib.om_polygon_centroid.argtypes = [P(_Grid), dp, dp, C.c_int, C.c_double, C.c_int, dp, ip]
         lib.om_project_point.argtypes = [C.c_void_p, dp, C.c_int, dp, dp, ip]
+        lib.om_segment_sdf.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, dp]
         _lib = lib
     return _lib
 
@@ -159,6 +160,19 @@ def polygon_centroid(sizing, gen, poly, eps_c, max_level=8):
     _load().om_polygon_centroid(C.byref(cg), _dp(_pt(gen)), _dp(poly), len(poly), eps_c, max_level, _dp(c),
                                 C.byref(lv))
     return c, lv.value
+
+
+def segment_sdf(verts_cw, px, py) -> np.ndarray:
+    """Sec. 3.1 SDF of the clockwise loop verts_cw (n, 2) at the points
+    (px, py), FP64, brute force (see om_segment_sdf)."""
+    lib = _load()
+    v = np.ascontiguousarray(verts_cw, dtype=np.float64).reshape(-1, 2)
+    px = np.ascontiguousarray(px, dtype=np.float64).ravel()
+    py = np.ascontiguousarray(py, dtype=np.float64).ravel()
+    out = np.empty(len(px))
+    if lib.om_segment_sdf(_dp(v), len(v), _dp(px), _dp(py), len(px), _dp(out)) != 0:
+        raise ValueError(lib.om_last_error().decode())
+    return out
 
 
 class OracleMesh:

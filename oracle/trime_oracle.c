@@ -1620,3 +1620,53 @@ void om_get_stats(const om_mesh* m, om_stats* s) {
     *s = m->st;
     s->n_points = m->N;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1: SDF from clockwise line segments (brute force)                 */
+/* ------------------------------------------------------------------------ */
+static void seg_normal(const double* xy, int64_t nv, int64_t k, double* nx, double* ny) {
+    int64_t k1 = k + 1 == nv ? 0 : k + 1;
+    double dx = xy[2 * k1] - xy[2 * k], dy = xy[2 * k1 + 1] - xy[2 * k + 1];
+    double L = sqrt(dx * dx + dy * dy);
+    *nx = dy / L; /* right of the direction: inward for a clockwise loop */
+    *ny = -dx / L;
+}
+
+int om_segment_sdf(const double* xy, int64_t nv, const double* px, const double* py, int64_t np, double* out) {
+    if (nv < 3 || !xy || (np > 0 && (!px || !py || !out))) { set_err("bad segment input"); return -1; }
+    for (int64_t q = 0; q < np; q++) {
+        double x = px[q], y = py[q];
+        double best = INFINITY, bt = 0.0;
+        int64_t bk = -1;
+        for (int64_t k = 0; k < nv; k++) {
+            int64_t k1 = k + 1 == nv ? 0 : k + 1;
+            double ax = xy[2 * k], ay = xy[2 * k + 1];
+            double ex = xy[2 * k1] - ax, ey = xy[2 * k1 + 1] - ay;
+            double wx = x - ax, wy = y - ay;
+            double t = (wx * ex + wy * ey) / (ex * ex + ey * ey);
+            if (!(t > 0.0)) t = 0.0;
+            if (t > 1.0) t = 1.0;
+            double cx = ax + t * ex, cy = ay + t * ey;
+            double dx = x - cx, dy = y - cy;
+            double d = sqrt(dx * dx + dy * dy);
+            if (d < best) { best = d; bk = k; bt = t; }
+        }
+        int64_t k1 = bk + 1 == nv ? 0 : bk + 1;
+        double ax = xy[2 * bk], ay = xy[2 * bk + 1];
+        double ex = xy[2 * k1] - ax, ey = xy[2 * k1 + 1] - ay;
+        double cx = ax + bt * ex, cy = ay + bt * ey;
+        double nx, ny;
+        seg_normal(xy, nv, bk, &nx, &ny);
+        if (bt == 0.0 || bt == 1.0) {
+            /* an end point: the sum of the incident segments' unit normals */
+            int64_t other = bt == 0.0 ? (bk == 0 ? nv - 1 : bk - 1) : k1;
+            double mx, my;
+            seg_normal(xy, nv, other, &mx, &my);
+            nx += mx;
+            ny += my;
+        }
+        double s = (x - cx) * nx + (y - cy) * ny;
+        out[q] = s > 0.0 ? -best : best;
+    }
+    return 0;
+}

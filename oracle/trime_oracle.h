@@ -16,6 +16,7 @@
  *   - aspect/edge ratio quality, 1/2-means, hybrid switch     Sec. 3.6 Eqs. 11-12, Sec. 4
  *   - point addition at the centroids of the triangles with   Sec. 3.6, Sec. 3.7
  *     the largest R_circ / h_i, quantities rescaled
+ *   - signed distance from clockwise line segments            Sec. 3.1
  *
  * Every sign decision of the triangulation (incircle / orientation) is exact:
  * big-integer arithmetic behind a deliberately loose double-precision filter,
@@ -140,6 +141,16 @@ int om_incircle(const double* a, const double* b, const double* c, const double*
 int om_incircle_sos(const double* a, int64_t ia, const double* b, int64_t ib,
                     const double* c, int64_t ic, const double* d, int64_t id);
 double om_bilinear(const om_grid* g, double x, double y);
+
+/* Sec. 3.1 signed distance from a closed loop of line segments given
+ * clockwise (vertex k to k+1, the last back to the first; nv >= 3), at np
+ * points (px, py): the distance to the closest segment (FP64, the smaller
+ * segment index on ties; closest point p* = a + t (b - a), t the clamped
+ * projection), negative where (p - p*) . n > 0 with n the segment's inward
+ * unit normal (right of its direction), or at an end point the sum of the
+ * two incident segments' unit normals; positive elsewhere.  Brute force over
+ * all segments.  Returns 0, or -1 on bad input. */
+int om_segment_sdf(const double* xy, int64_t nv, const double* px, const double* py, int64_t np, double* out);
 
 /* Standalone pieces for pins. */
 int om_polygon_centroid(const om_grid* sizing, const double* gen, const double* poly, int nv,
