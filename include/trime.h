@@ -211,6 +211,24 @@ int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, d
                        double y1, int32_t nbx, int32_t nby, int32_t* bucket_start, int32_t* sorted_idx,
                        int32_t* scratch, void* cuda_stream);
 
+/* Sec. 3.1: signed distance field of a closed loop of nv >= 3 line segments
+ * given clockwise (HOST array xy of nv (x, y) float64 pairs; segment k runs
+ * from vertex k to vertex k+1, the last back to vertex 0), sampled at the
+ * nodes (x0 + i (x1-x0)/(nx-1), y0 + j (y1-y0)/(ny-1)) into out (nx*ny
+ * float32, row-major out[j*nx + i], host or device memory), ready to pass as
+ * a mesh_grid2d.  The value is the distance to the closest segment (FP64, the
+ * smaller segment index on ties; closest point p* = a + t (b - a), t the
+ * clamped projection), negative where (p - p*) . n > 0 with n the segment's
+ * inward unit normal (right of its direction), or at an end point the sum of
+ * the two incident segments' unit normals; rounded to float32.  The segments
+ * are listed in a grid of cells about the mean segment length and searched
+ * outwards as in Sec. 3.1, once per cell (the nodes of a cell then test only
+ * its candidates).  Synchronous on cuda_stream; allocates and frees its
+ * scratch.  Errors: TRIME_EINVAL (fewer than 3 vertices, a non-finite or
+ * repeated vertex, a bad box or grid), TRIME_ECUDA. */
+int mesh_segment_sdf_grid(const double* xy, int64_t nv, double x0, double y0, double x1, double y1, int32_t nx,
+                          int32_t ny, float* out, void* cuda_stream);
+
 /* mesh_bucket_points for callers that cannot allocate device memory: the
  * same counting sort (same arguments and outputs, all DEVICE pointers), but
  * its scratch is a fixed 16 MiB array inside the library instead of a

@@ -70,7 +70,7 @@ class mesh_tuning(C.Structure):
 
 
 # every symbol include/trime.h declares
-EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_get_triangles",
+EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
            "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step",
            "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
@@ -156,7 +156,10 @@ def lib():
     L.mesh_batch_destroy.restype = None
     L.mesh_get_count.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
     L.mesh_get_state.argtypes = [vp, vp, vp, vp]
-    for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_get_triangles", "mesh_get_points",
+    L.mesh_segment_sdf_grid.argtypes = [P(C.c_double), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_int32, C.c_int32, vp, vp]
+    for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state",
+                 "mesh_segment_sdf_grid", "mesh_get_triangles", "mesh_get_points",
                  "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
                  "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc", "mesh_batch_init",
                  "mesh_batch_size", "mesh_batch_rebuild", "mesh_batch_step", "mesh_batch_get_triangles",
@@ -256,6 +259,20 @@ def mesh_measure_pipe_peaks() -> dict:
     sm, clk = C.c_int32(), C.c_int32()
     _check(lib().mesh_measure_pipe_peaks(C.byref(f32), C.byref(f64), C.byref(sm), C.byref(clk)))
     return {"fp32_tflops": f32.value, "fp64_tflops": f64.value, "sm_count": sm.value, "sm_clock_mhz": clk.value / 1e3}
+
+
+def segment_sdf_grid(verts_cw, n: int, box=(-1.1, -1.1, 1.1, 1.1), ny: int = None, out=None, stream=None):
+    """Sec. 3.1 SDF of the clockwise loop verts_cw (k, 2) on an n x ny node
+    grid over box (x0, y0, x1, y1) (mesh_segment_sdf_grid): a float32 numpy
+    array (ny, n), or written into `out` (host array or device tensor)."""
+    v = np.ascontiguousarray(verts_cw, dtype=np.float64).reshape(-1, 2)
+    ny = n if ny is None else ny
+    x0, y0, x1, y1 = box
+    res = out if out is not None else np.empty((ny, n), dtype=np.float32)
+    st = C.c_void_p(0 if stream is None else int(stream))
+    _check(lib().mesh_segment_sdf_grid(v.ctypes.data_as(C.POINTER(C.c_double)), len(v), x0, y0, x1, y1, n, ny,
+                                       _ptr(res), st))
+    return res
 
 
 def _stats_dict(s: mesh_stats) -> dict:

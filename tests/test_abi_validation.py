@@ -80,3 +80,20 @@ def test_invalid_batch_arguments(g):
     assert g.lib().mesh_batch_step(None, 1, None) == g.TRIME_EINVAL
     assert g.lib().mesh_batch_get_triangles(None, 0, None, 0, None) == g.TRIME_EINVAL
     assert g.lib().mesh_batch_size(None) == 0
+
+
+def test_segment_sdf_invalid_arguments(g):
+    out = np.zeros((8, 8), np.float32)
+    tri = np.array([[0.0, 0.0], [0.0, 1.0], [1.0, 0.0]])
+
+    def call(v, box=(-1, -1, 1, 1), n=8):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        return g.lib().mesh_segment_sdf_grid(v.ctypes.data_as(C.POINTER(C.c_double)), len(v), *box, n, n,
+                                             out.ctypes.data_as(C.c_void_p), None)
+
+    assert call(tri[:2]) == g.TRIME_EINVAL
+    assert call(np.array([[0.0, 0.0], [0.0, 0.0], [1.0, 0.0]])) == g.TRIME_EINVAL
+    assert "zero-length" in g.mesh_last_error()
+    assert call(np.array([[0.0, np.inf], [0.0, 1.0], [1.0, 0.0]])) == g.TRIME_EINVAL
+    assert call(tri, box=(1, -1, -1, 1)) == g.TRIME_EINVAL
+    assert call(tri, n=1) == g.TRIME_EINVAL
