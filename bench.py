@@ -325,6 +325,44 @@ def sweep_leg(g, torch, stream, steps, flush):
     return out
 
 
+def segment_sdf_leg(g, torch, stream):
+    """The SDF of the benchmark star (500 clockwise segments) on its 4096^2
+    grid, built on the device (mesh_segment_sdf_grid, into device memory;
+    device time by CUDA events, best of 3) against the host builder of the
+    workloads (a sampled nearest-segment search in numpy, all cores) and the
+    oracle's brute force on a sample of nodes (one core)."""
+    import workloads as W
+
+    v = W.star_polygon(500, 0.4, 1.0, 2)
+    n = 4096
+    out = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    g.segment_sdf_grid(v, n, out=out, stream=stream.cuda_stream)  # warm-up
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.segment_sdf_grid(v, n, out=out, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    t0 = time.perf_counter()
+    W.polygon_sdf_grid(v, n, workers=min(16, os.cpu_count() or 1))
+    host_s = time.perf_counter() - t0
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(0)
+    px, py = rng.uniform(-1.1, 1.1, 20000), rng.uniform(-1.1, 1.1, 20000)
+    t0 = time.perf_counter()
+    oracle.segment_sdf(v, px, py)
+    rate_or = 20000 / (time.perf_counter() - t0)
+    return {"nodes": n * n, "segments": len(v), "device_ms": best, "device_mnodes_per_s": n * n / best / 1e3,
+            "host_builder_seconds": host_s, "host_builder_workers": min(16, os.cpu_count() or 1),
+            "oracle_mnodes_per_s_1_core": rate_or / 1e6,
+            "note": "device time includes its scratch allocation and the cell candidate search"}
+
+
 def distmesh_leg(g, torch, stream):
     """The DistMesh method (config 1's disk at 1e4 points and the annulus at
     1e6) to termination, re-triangulating every iteration and only after large
@@ -614,6 +652,7 @@ def main():
         extras["learned"] = learned_leg(g, stream)
         extras["distmesh"] = distmesh_leg(g, torch, stream)
         extras["point_addition"] = addition_leg(g, torch, stream)
+        extras["segment_sdf"] = segment_sdf_leg(g, torch, stream)
         if args.sweep:
             extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
         threads = os.cpu_count() or 1
