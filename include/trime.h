@@ -229,6 +229,17 @@ int mesh_bucket_points(const double* x, const double* y, int64_t n, double x0, d
 int mesh_segment_sdf_grid(const double* xy, int64_t nv, double x0, double y0, double x1, double y1, int32_t nx,
                           int32_t ny, float* out, void* cuda_stream);
 
+/* Sec. 3.3 Eq. 7: the element sizing field mu(x) = min over the ns boundary
+ * samples s (HOST array sxy of (x, y) float64 pairs) of K |s - x| + lfs(s)
+ * (HOST array of ns local feature sizes, >= 0), K >= 0 the gradation, at the
+ * nodes (x0 + i (x1-x0)/(nx-1), y0 + j (y1-y0)/(ny-1)) into out (nx*ny
+ * float32, row-major, host or device memory), ready to pass as the sizing
+ * mesh_grid2d.  Exact minimum in FP64 (the samples in a bucket grid, each
+ * node searching outwards until no unvisited sample can do better), rounded
+ * to float32.  Synchronous on cuda_stream.  Errors: TRIME_EINVAL, TRIME_ECUDA. */
+int mesh_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K, double x0, double y0, double x1,
+                      double y1, int32_t nx, int32_t ny, float* out, void* cuda_stream);
+
 /* mesh_bucket_points for callers that cannot allocate device memory: the
  * same counting sort (same arguments and outputs, all DEVICE pointers), but
  * its scratch is a fixed 16 MiB array inside the library instead of a

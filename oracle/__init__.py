@@ -107,6 +107,7 @@ def _load():
         lib.om_polygon_centroid.argtypes = [P(_Grid), dp, dp, C.c_int, C.c_double, C.c_int, dp, ip]
         lib.om_project_point.argtypes = [C.c_void_p, dp, C.c_int, dp, dp, ip]
         lib.om_segment_sdf.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, dp]
+        lib.om_sizing_field.argtypes = [dp, dp, C.c_int64, C.c_double, dp, dp, C.c_int64, dp]
         _lib = lib
     return _lib
 
@@ -171,6 +172,20 @@ def segment_sdf(verts_cw, px, py) -> np.ndarray:
     py = np.ascontiguousarray(py, dtype=np.float64).ravel()
     out = np.empty(len(px))
     if lib.om_segment_sdf(_dp(v), len(v), _dp(px), _dp(py), len(px), _dp(out)) != 0:
+        raise ValueError(lib.om_last_error().decode())
+    return out
+
+
+def sizing_field(samples, lfs, K, px, py) -> np.ndarray:
+    """Eq. 7: min over the samples of K |s - x| + lfs(s) at the points
+    (px, py), FP64, brute force (om_sizing_field)."""
+    lib = _load()
+    s = np.ascontiguousarray(samples, dtype=np.float64).reshape(-1, 2)
+    lf = np.ascontiguousarray(lfs, dtype=np.float64).ravel()
+    px = np.ascontiguousarray(px, dtype=np.float64).ravel()
+    py = np.ascontiguousarray(py, dtype=np.float64).ravel()
+    out = np.empty(len(px))
+    if lib.om_sizing_field(_dp(s), _dp(lf), len(s), float(K), _dp(px), _dp(py), len(px), _dp(out)) != 0:
         raise ValueError(lib.om_last_error().decode())
     return out
 

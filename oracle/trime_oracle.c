@@ -1670,3 +1670,24 @@ int om_segment_sdf(const double* xy, int64_t nv, const double* px, const double*
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.3 Eq. 7: sizing field from boundary samples (brute force)         */
+/* ------------------------------------------------------------------------ */
+int om_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K, const double* px, const double* py,
+                    int64_t np, double* out) {
+    if (ns < 1 || !sxy || !lfs || !(K >= 0.0) || (np > 0 && (!px || !py || !out))) {
+        set_err("bad sizing input");
+        return -1;
+    }
+    for (int64_t q = 0; q < np; q++) {
+        double best = INFINITY;
+        for (int64_t k = 0; k < ns; k++) {
+            double dx = px[q] - sxy[2 * k], dy = py[q] - sxy[2 * k + 1];
+            double v = K * sqrt(dx * dx + dy * dy) + lfs[k];
+            if (v < best) best = v;
+        }
+        out[q] = best;
+    }
+    return 0;
+}

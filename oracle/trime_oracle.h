@@ -17,6 +17,7 @@
  *   - point addition at the centroids of the triangles with   Sec. 3.6, Sec. 3.7
  *     the largest R_circ / h_i, quantities rescaled
  *   - signed distance from clockwise line segments            Sec. 3.1
+ *   - element sizing field from boundary samples and lfs      Sec. 3.3 Eq. 7
  *
  * Every sign decision of the triangulation (incircle / orientation) is exact:
  * big-integer arithmetic behind a deliberately loose double-precision filter,
@@ -151,6 +152,13 @@ double om_bilinear(const om_grid* g, double x, double y);
  * two incident segments' unit normals; positive elsewhere.  Brute force over
  * all segments.  Returns 0, or -1 on bad input. */
 int om_segment_sdf(const double* xy, int64_t nv, const double* px, const double* py, int64_t np, double* out);
+
+/* Eq. 7 element sizing field mu(x) = min over the boundary samples s of
+ * K |s - x| + lfs(s) (Sec. 3.3), at np points; brute force over the ns
+ * samples sxy (x, y pairs) with local feature sizes lfs.  Returns 0, or -1
+ * on bad input. */
+int om_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K, const double* px, const double* py,
+                    int64_t np, double* out);
 
 /* Standalone pieces for pins. */
 int om_polygon_centroid(const om_grid* sizing, const double* gen, const double* poly, int nv,

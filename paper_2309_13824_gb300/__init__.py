@@ -70,7 +70,7 @@ class mesh_tuning(C.Structure):
 
 
 # every symbol include/trime.h declares
-EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_get_triangles",
+EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
            "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step",
            "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
@@ -158,8 +158,10 @@ def lib():
     L.mesh_get_state.argtypes = [vp, vp, vp, vp]
     L.mesh_segment_sdf_grid.argtypes = [P(C.c_double), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                         C.c_int32, C.c_int32, vp, vp]
+    L.mesh_sizing_field.argtypes = [P(C.c_double), P(C.c_double), C.c_int64, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.c_double, C.c_int32, C.c_int32, vp, vp]
     for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state",
-                 "mesh_segment_sdf_grid", "mesh_get_triangles", "mesh_get_points",
+                 "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_get_triangles", "mesh_get_points",
                  "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
                  "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc", "mesh_batch_init",
                  "mesh_batch_size", "mesh_batch_rebuild", "mesh_batch_step", "mesh_batch_get_triangles",
@@ -272,6 +274,22 @@ def segment_sdf_grid(verts_cw, n: int, box=(-1.1, -1.1, 1.1, 1.1), ny: int = Non
     st = C.c_void_p(0 if stream is None else int(stream))
     _check(lib().mesh_segment_sdf_grid(v.ctypes.data_as(C.POINTER(C.c_double)), len(v), x0, y0, x1, y1, n, ny,
                                        _ptr(res), st))
+    return res
+
+
+def sizing_field(samples, lfs, K: float, n: int, box=(-1.1, -1.1, 1.1, 1.1), ny: int = None, out=None,
+                 stream=None):
+    """Eq. 7 sizing field of boundary samples (k, 2) with local feature sizes
+    lfs (k,) and gradation K on an n x ny node grid over box
+    (mesh_sizing_field): a float32 numpy array (ny, n), or written into `out`."""
+    s = np.ascontiguousarray(samples, dtype=np.float64).reshape(-1, 2)
+    lf = np.ascontiguousarray(lfs, dtype=np.float64).ravel()
+    ny = n if ny is None else ny
+    x0, y0, x1, y1 = box
+    res = out if out is not None else np.empty((ny, n), dtype=np.float32)
+    st = C.c_void_p(0 if stream is None else int(stream))
+    _check(lib().mesh_sizing_field(s.ctypes.data_as(C.POINTER(C.c_double)), lf.ctypes.data_as(C.POINTER(C.c_double)),
+                                   len(s), float(K), x0, y0, x1, y1, n, ny, _ptr(res), st))
     return res
 
 
