@@ -108,6 +108,11 @@ def _load():
         lib.om_project_point.argtypes = [C.c_void_p, dp, C.c_int, dp, dp, ip]
         lib.om_segment_sdf.argtypes = [dp, C.c_int64, dp, dp, C.c_int64, dp]
         lib.om_sizing_field.argtypes = [dp, dp, C.c_int64, C.c_double, dp, dp, C.c_int64, dp]
+        lib.om_boundary_samples.restype = C.c_int64
+        lib.om_boundary_samples.argtypes = [dp, C.c_int64, C.c_double, C.c_double, dp, C.c_int64]
+        lib.om_medial_points.argtypes = [C.c_void_p, dp, u8p]
+        lib.om_lfs.restype = C.c_int64
+        lib.om_lfs.argtypes = [dp, C.c_int64, dp, C.c_int64, C.c_double, C.c_int32, dp]
         _lib = lib
     return _lib
 
@@ -188,6 +193,67 @@ def sizing_field(samples, lfs, K, px, py) -> np.ndarray:
     if lib.om_sizing_field(_dp(s), _dp(lf), len(s), float(K), _dp(px), _dp(py), len(px), _dp(out)) != 0:
         raise ValueError(lib.om_last_error().decode())
     return out
+
+
+def boundary_samples(verts_cw, ds, geps_hat) -> np.ndarray:
+    """App. A boundary samples of a clockwise segment loop, trimmed (om_boundary_samples)."""
+    lib = _load()
+    v = np.ascontiguousarray(verts_cw, dtype=np.float64).reshape(-1, 2)
+    n = lib.om_boundary_samples(_dp(v), len(v), float(ds), float(geps_hat), None, 0)
+    if n < 0:
+        raise ValueError(lib.om_last_error().decode())
+    out = np.empty((n, 2))
+    lib.om_boundary_samples(_dp(v), len(v), float(ds), float(geps_hat), _dp(out), n)
+    return out
+
+
+def lfs(samples, medial, r_nei, n_thres=3):
+    """Trimmed medial points and the local feature size of every sample (om_lfs):
+    (lfs (ns,), number of medial points kept)."""
+    lib = _load()
+    s = np.ascontiguousarray(samples, dtype=np.float64).reshape(-1, 2)
+    m = np.ascontiguousarray(medial, dtype=np.float64).reshape(-1, 2)
+    out = np.empty(len(s))
+    kept = lib.om_lfs(_dp(s), len(s), _dp(m), len(m), float(r_nei), int(n_thres), _dp(out))
+    if kept < 0:
+        raise ValueError(lib.om_last_error().decode())
+    return out, int(kept)
+
+
+def medial_list(v, flags) -> np.ndarray:
+    """The medial points in sample order, v1 then v2 of each sample."""
+    pts = []
+    for i in range(len(flags)):
+        if flags[i] & 1:
+            pts.append(v[i, :2])
+        if flags[i] & 2:
+            pts.append(v[i, 2:])
+    return np.array(pts).reshape(-1, 2)
+
+
+def auto_sizing(verts_cw, K, n, box=(-1.1, -1.1, 1.1, 1.1), fac_s=0.5, fac_geps=0.01, fac_nei=2.0, n_thres=3):
+    """The automatic sizing pipeline (App. A, Sec. 3.3, Eq. 7) on an n x n node
+    grid over box: boundary samples, their Delaunay triangles (unbounded cells,
+    no validity tests) on the oracle's own SDF grid, medial points, lfs, and
+    the sizing field at the nodes (FP64)."""
+    x0, y0, x1, y1 = box
+    dx, dy = (x1 - x0) / (n - 1), (y1 - y0) / (n - 1)
+    g = min(dx, dy)
+    ds, geps_hat = fac_s * g, fac_geps * g
+    S = boundary_samples(verts_cw, ds, geps_hat)
+    xs = x0 + np.arange(n) * dx
+    ys = y0 + np.arange(n) * dy
+    X, Y = np.meshgrid(xs, ys)
+    sdf = segment_sdf(verts_cw, X.ravel(), Y.ravel()).reshape(n, n).astype(np.float32)
+    from workloads import Grid, constant_grid
+
+    om = OracleMesh(Grid(sdf, x0, y0, x1, y1), constant_grid(1.0, 2, box), S, bounded=0, validity=0)
+    om.rebuild()
+    v, flags = om.medial_points()
+    M = medial_list(v, flags)
+    lf, kept = lfs(S, M, fac_nei * n_thres * ds, n_thres)
+    mu = sizing_field(S, lf, K, X.ravel(), Y.ravel()).reshape(n, n)
+    return {"samples": S, "medial": M, "kept": kept, "lfs": lf, "sizing": mu, "sdf": sdf, "ds": ds}
 
 
 class OracleMesh:
@@ -330,6 +396,14 @@ class OracleMesh:
 
     def set_method_state(self, switched, prev_a=0.0, prev_b=0.0, prev_amax=0.0):
         self._lib.om_set_method_state(self._h, switched, prev_a, prev_b, prev_amax)
+
+    def medial_points(self):
+        """(v (n, 4): v1 and v2 of every point, flags (n,) bit 0 / 1: v1 / v2 exist)
+        from the triangles of the last rebuild (om_medial_points)."""
+        v = np.zeros((self.n, 4))
+        f = np.zeros(self.n, dtype=np.uint8)
+        self._lib.om_medial_points(self._h, _dp(v), f.ctypes.data_as(C.POINTER(C.c_uint8)))
+        return v, f
 
     def ring(self, i):
         buf = np.zeros(512, dtype=np.int32)

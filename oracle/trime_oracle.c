@@ -1691,3 +1691,168 @@ int om_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K, 
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* App. A: boundary samples; Sec. 3.3: medial axis and lfs                   */
+/* ------------------------------------------------------------------------ */
+static double seg_sdf1(const double* xy, int64_t nv, double x, double y) {
+    double v;
+    om_segment_sdf(xy, nv, &x, &y, 1, &v);
+    return v;
+}
+
+int64_t om_boundary_samples(const double* xy, int64_t nv, double ds, double geps_hat, double* out, int64_t cap) {
+    if (nv < 3 || !(ds > 0.0) || !(geps_hat >= 0.0)) { set_err("bad sample input"); return -1; }
+    int64_t n = 0, ncap = nv;
+    for (int64_t k = 0; k < nv; k++) {
+        int64_t k1 = k + 1 == nv ? 0 : k + 1;
+        double L = sqrt((xy[2 * k1] - xy[2 * k]) * (xy[2 * k1] - xy[2 * k]) +
+                        (xy[2 * k1 + 1] - xy[2 * k + 1]) * (xy[2 * k1 + 1] - xy[2 * k + 1]));
+        if (L > ds) ncap += (int64_t)floor(L / ds);
+    }
+    double* px = (double*)malloc(sizeof(double) * (size_t)ncap);
+    double* py = (double*)malloc(sizeof(double) * (size_t)ncap);
+    uint8_t* alive = (uint8_t*)malloc((size_t)ncap);
+    uint8_t* done = (uint8_t*)malloc((size_t)ncap);
+    if (!px || !py || !alive || !done) { free(px); free(py); free(alive); free(done); set_err("oom"); return -1; }
+    for (int64_t k = 0; k < nv; k++) {
+        int64_t k1 = k + 1 == nv ? 0 : k + 1;
+        double ax = xy[2 * k], ay = xy[2 * k + 1], ex = xy[2 * k1] - ax, ey = xy[2 * k1 + 1] - ay;
+        double L = sqrt(ex * ex + ey * ey);
+        px[n] = ax; py[n] = ay; n++;
+        if (L > ds) {
+            int64_t m = (int64_t)floor(L / ds) + 1; /* intervals, each shorter than ds */
+            for (int64_t q = 1; q < m; q++) {
+                double t = (double)q / (double)m;
+                px[n] = ax + t * ex; py[n] = ay + t * ey; n++;
+            }
+        }
+    }
+    for (int64_t i = 0; i < n; i++) { alive[i] = 1; done[i] = 0; }
+    int any = 1;
+    while (any) {
+        any = 0;
+        for (int64_t i = 0; i < n; i++) {
+            if (!alive[i] || done[i]) continue;
+            /* closest valid other point: by (distance, index) */
+            double last_d = -1.0;
+            int64_t last_j = -1, found = -1;
+            double fd = 0.0, mx = 0.0, my = 0.0;
+            for (;;) {
+                double bd = INFINITY;
+                int64_t bj = -1;
+                for (int64_t j = 0; j < n; j++) {
+                    if (j == i || !alive[j]) continue;
+                    double dx = px[j] - px[i], dy = py[j] - py[i];
+                    double d = sqrt(dx * dx + dy * dy);
+                    /* next in (d, j) order after (last_d, last_j) */
+                    if (d < last_d || (d == last_d && j <= last_j)) continue;
+                    if (d < bd || (d == bd && j < bj)) { bd = d; bj = j; }
+                }
+                if (bj < 0) break;
+                double cx = (px[i] + px[bj]) * 0.5, cy = (py[i] + py[bj]) * 0.5;
+                if (fabs(seg_sdf1(xy, nv, cx, cy)) <= geps_hat) { found = bj; fd = bd; mx = cx; my = cy; break; }
+                last_d = bd; last_j = bj;
+            }
+            if (found < 0 || !(fd < ds)) { done[i] = 1; continue; }
+            alive[found] = 0;
+            px[i] = mx; py[i] = my;
+            any = 1;
+        }
+    }
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; i++)
+        if (alive[i]) {
+            if (c < cap && out) { out[2 * c] = px[i]; out[2 * c + 1] = py[i]; }
+            c++;
+        }
+    free(px); free(py); free(alive); free(done);
+    return c;
+}
+
+static int triple_less(const int32_t* a, const int32_t* b) {
+    int32_t x[3] = {a[0], a[1], a[2]}, y[3] = {b[0], b[1], b[2]};
+    /* sort each ascending */
+    for (int r = 0; r < 2; r++)
+        for (int q = 0; q < 2 - r; q++) {
+            if (x[q] > x[q + 1]) { int32_t t = x[q]; x[q] = x[q + 1]; x[q + 1] = t; }
+            if (y[q] > y[q + 1]) { int32_t t = y[q]; y[q] = y[q + 1]; y[q + 1] = t; }
+        }
+    for (int q = 0; q < 3; q++)
+        if (x[q] != y[q]) return x[q] < y[q];
+    return 0;
+}
+
+void om_medial_points(const om_mesh* m, double* v, uint8_t* flags) {
+    int64_t N = m->N;
+    double* best1 = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    int64_t* t1 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    double* cc = (double*)malloc(sizeof(double) * 2 * (size_t)(m->ntri > 0 ? m->ntri : 1));
+    for (int64_t i = 0; i < N; i++) { best1[i] = -1.0; t1[i] = -1; flags[i] = 0; }
+    for (int64_t t = 0; t < m->ntri; t++) {
+        const int32_t* T = m->tri + 3 * t;
+        double ox, oy, R;
+        circumcenter_fixed(m->x[T[0]], m->y[T[0]], m->x[T[1]], m->y[T[1]], m->x[T[2]], m->y[T[2]], &ox, &oy, &R);
+        cc[2 * t] = ox; cc[2 * t + 1] = oy;
+        for (int q = 0; q < 3; q++) {
+            int32_t p = T[q];
+            double dx = ox - m->x[p], dy = oy - m->y[p];
+            double d = sqrt(dx * dx + dy * dy);
+            if (d > best1[p] || (d == best1[p] && t1[p] >= 0 && triple_less(T, m->tri + 3 * t1[p]))) {
+                best1[p] = d; t1[p] = t;
+            }
+        }
+    }
+    for (int64_t i = 0; i < N; i++)
+        if (t1[i] >= 0) { v[4 * i] = cc[2 * t1[i]]; v[4 * i + 1] = cc[2 * t1[i] + 1]; flags[i] |= 1; }
+    double* best2 = best1;
+    int64_t* t2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    for (int64_t i = 0; i < N; i++) { best2[i] = -1.0; t2[i] = -1; }
+    for (int64_t t = 0; t < m->ntri; t++) {
+        const int32_t* T = m->tri + 3 * t;
+        double ox = cc[2 * t], oy = cc[2 * t + 1];
+        for (int q = 0; q < 3; q++) {
+            int32_t p = T[q];
+            if (!(flags[p] & 1)) continue;
+            double ux = v[4 * p] - m->x[p], uy = v[4 * p + 1] - m->y[p];
+            double dx = ox - m->x[p], dy = oy - m->y[p];
+            if (!(dx * ux + dy * uy <= 0.0)) continue;
+            double d = sqrt(dx * dx + dy * dy);
+            if (d > best2[p] || (d == best2[p] && t2[p] >= 0 && triple_less(T, m->tri + 3 * t2[p]))) {
+                best2[p] = d; t2[p] = t;
+            }
+        }
+    }
+    for (int64_t i = 0; i < N; i++)
+        if (t2[i] >= 0) { v[4 * i + 2] = cc[2 * t2[i]]; v[4 * i + 3] = cc[2 * t2[i] + 1]; flags[i] |= 2; }
+    free(best1); free(t1); free(t2); free(cc);
+}
+
+int64_t om_lfs(const double* sxy, int64_t ns, const double* mxy, int64_t nm, double r_nei, int32_t n_thres,
+               double* lfs) {
+    if (ns < 1 || nm < 1) { set_err("no samples or no medial points"); return -1; }
+    uint8_t* keep = (uint8_t*)malloc((size_t)nm);
+    int64_t kept = 0;
+    for (int64_t a = 0; a < nm; a++) {
+        int64_t c = 0;
+        for (int64_t b = 0; b < nm; b++) {
+            if (b == a) continue;
+            double dx = mxy[2 * b] - mxy[2 * a], dy = mxy[2 * b + 1] - mxy[2 * a + 1];
+            if (sqrt(dx * dx + dy * dy) <= r_nei) c++;
+        }
+        keep[a] = c >= n_thres;
+        kept += keep[a];
+    }
+    for (int64_t i = 0; i < ns; i++) {
+        double best = INFINITY;
+        for (int64_t a = 0; a < nm; a++) {
+            if (kept > 0 && !keep[a]) continue;
+            double dx = mxy[2 * a] - sxy[2 * i], dy = mxy[2 * a + 1] - sxy[2 * i + 1];
+            double d = sqrt(dx * dx + dy * dy);
+            if (d < best) best = d;
+        }
+        lfs[i] = best;
+    }
+    free(keep);
+    return kept;
+}

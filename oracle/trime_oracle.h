@@ -18,6 +18,7 @@
  *     the largest R_circ / h_i, quantities rescaled
  *   - signed distance from clockwise line segments            Sec. 3.1
  *   - element sizing field from boundary samples and lfs      Sec. 3.3 Eq. 7
+ *   - boundary samples, medial axis, local feature size       App. A, Sec. 3.3
  *
  * Every sign decision of the triangulation (incircle / orientation) is exact:
  * big-integer arithmetic behind a deliberately loose double-precision filter,
@@ -159,6 +160,30 @@ int om_segment_sdf(const double* xy, int64_t nv, const double* px, const double*
  * on bad input. */
 int om_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K, const double* px, const double* py,
                     int64_t np, double* out);
+
+/* App. A: boundary samples of a clockwise segment loop: every vertex and,
+ * on each segment longer than ds, floor(L/ds) evenly spaced interior points
+ * (spacing below ds), in segment order; then the serial trimming: in index
+ * order, each unfinished point finds its closest other point whose midpoint
+ * m with it has |sdf(m)| <= geps_hat (Sec. 3.1 segment SDF; ties by index);
+ * if that point is closer than ds it is deleted and the current point moves
+ * to m, otherwise the current point is finished; passes repeat until every
+ * point is finished.  Writes up to cap (x, y) pairs; returns the count or -1. */
+int64_t om_boundary_samples(const double* xy, int64_t nv, double ds, double geps_hat, double* out, int64_t cap);
+
+/* Sec. 3.3: medial-axis points of the points of m (boundary samples), read
+ * off the Delaunay triangles of the last om_rebuild (Voronoi vertices =
+ * circumcentres, fixed formula on the canonical order): v1 the circumcentre
+ * of an incident triangle farthest from the point, v2 the farthest one with
+ * (c - p) . (v1 - p) <= 0; ties to the smaller vertex-index triple.  v gets
+ * 4 doubles per point (v1, v2), flags bit 0 = v1 exists, bit 1 = v2 exists. */
+void om_medial_points(const om_mesh* m, double* v, uint8_t* flags);
+
+/* Sec. 3.3: the medial points (nm (x, y) pairs) with at least n_thres others
+ * within r_nei are kept (all of them if none would be); lfs of each sample =
+ * its distance to the closest kept point.  Returns the number kept or -1. */
+int64_t om_lfs(const double* sxy, int64_t ns, const double* mxy, int64_t nm, double r_nei, int32_t n_thres,
+               double* lfs);
 
 /* Standalone pieces for pins. */
 int om_polygon_centroid(const om_grid* sizing, const double* gen, const double* poly, int nv,
