@@ -240,6 +240,41 @@ int mesh_segment_sdf_grid(const double* xy, int64_t nv, double x0, double y0, do
 int mesh_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K, double x0, double y0, double x1,
                       double y1, int32_t nx, int32_t ny, float* out, void* cuda_stream);
 
+/* Sec. 3.3: medial-axis approximating points of the points of m (read as
+ * boundary samples), from the triangles of its last triangulation (rebuilt
+ * first if the points changed since): the Voronoi vertices of a cell are the
+ * circumcentres of its triangles (create m with bounded = 0 and validity = 0
+ * for the plain Delaunay triangles inside the SDF grid's box).  Per point,
+ * in input order, v (HOST, 4 doubles) gets v1, the circumcentre farthest from
+ * the point, and v2, the farthest one with (c - p) . (v1 - p) <= 0 (ties to
+ * the smaller ascending vertex-index triple); flags (HOST, 1 byte) bit 0 /
+ * bit 1 tell whether v1 / v2 exist.  Synchronous. */
+int mesh_medial_points(mesh_t* m, double* v, uint8_t* flags);
+
+/* The automatic sizing field of App. A and Sec. 3.3 for a clockwise loop of
+ * nv >= 3 segments (HOST xy), on the node grid (x0 + i (x1-x0)/(nx-1),
+ * y0 + j (y1-y0)/(ny-1)) whose cells serve as the geometry grid (dx, dy):
+ *  1. boundary samples: every vertex, and floor(L/ds) evenly spaced points on
+ *     each segment longer than ds = fac_s min(dx, dy) (fac_s 0.5), trimmed
+ *     serially in index order (each unfinished point finds its closest other
+ *     point whose midpoint with it has |sdf| <= fac_geps min(dx, dy), fac_geps
+ *     0.01; if closer than ds that point is deleted and the current point
+ *     moves to the midpoint, else the current point is finished; passes
+ *     repeat until all are finished);
+ *  2. their Delaunay triangles on the device (a mesh with bounded = 0 and
+ *     validity = 0 on the segment SDF grid of mesh_segment_sdf_grid) and the
+ *     medial points of mesh_medial_points (v1 then v2 of each sample);
+ *  3. the medial points with at least n_thres = 3 others within
+ *     r_nei = fac_nei n_thres ds (fac_nei 2) are kept (all if none would be);
+ *     lfs of a sample is its distance to the closest kept one;
+ *  4. mu on the grid by mesh_sizing_field with gradation K.
+ * sdf_out (may be NULL) and sizing_out receive nx*ny float32 values (host or
+ * device memory); counts (may be NULL) gets {samples, medial points, kept}.
+ * Synchronous on cuda_stream.  Errors as the functions it uses. */
+int mesh_auto_sizing(const double* xy, int64_t nv, double K, double x0, double y0, double x1, double y1,
+                     int32_t nx, int32_t ny, float* sdf_out, float* sizing_out, int64_t* counts,
+                     void* cuda_stream);
+
 /* mesh_bucket_points for callers that cannot allocate device memory: the
  * same counting sort (same arguments and outputs, all DEVICE pointers), but
  * its scratch is a fixed 16 MiB array inside the library instead of a

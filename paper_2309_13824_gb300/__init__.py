@@ -70,7 +70,7 @@ class mesh_tuning(C.Structure):
 
 
 # every symbol include/trime.h declares
-EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_get_triangles",
+EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
            "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step",
            "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
@@ -160,8 +160,11 @@ def lib():
                                         C.c_int32, C.c_int32, vp, vp]
     L.mesh_sizing_field.argtypes = [P(C.c_double), P(C.c_double), C.c_int64, C.c_double, C.c_double, C.c_double,
                                     C.c_double, C.c_double, C.c_int32, C.c_int32, vp, vp]
+    L.mesh_medial_points.argtypes = [vp, P(C.c_double), P(C.c_uint8)]
+    L.mesh_auto_sizing.argtypes = [P(C.c_double), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_int32, C.c_int32, vp, vp, P(C.c_int64), vp]
     for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state",
-                 "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_get_triangles", "mesh_get_points",
+                 "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing", "mesh_get_triangles", "mesh_get_points",
                  "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
                  "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc", "mesh_batch_init",
                  "mesh_batch_size", "mesh_batch_rebuild", "mesh_batch_step", "mesh_batch_get_triangles",
@@ -293,6 +296,22 @@ def sizing_field(samples, lfs, K: float, n: int, box=(-1.1, -1.1, 1.1, 1.1), ny:
     return res
 
 
+def auto_sizing(verts_cw, K: float, n: int, box=(-1.1, -1.1, 1.1, 1.1), ny: int = None, stream=None):
+    """The automatic sizing pipeline (App. A, Sec. 3.3, Eq. 7; mesh_auto_sizing)
+    for a clockwise polygon on an n x ny node grid: (SDF grid, sizing grid) as
+    float32 numpy arrays (ny, n) and the counts {samples, medial, kept}."""
+    v = np.ascontiguousarray(verts_cw, dtype=np.float64).reshape(-1, 2)
+    ny = n if ny is None else ny
+    x0, y0, x1, y1 = box
+    sdf = np.empty((ny, n), dtype=np.float32)
+    mu = np.empty((ny, n), dtype=np.float32)
+    cnt = (C.c_int64 * 3)()
+    st = C.c_void_p(0 if stream is None else int(stream))
+    _check(lib().mesh_auto_sizing(v.ctypes.data_as(C.POINTER(C.c_double)), len(v), float(K), x0, y0, x1, y1, n, ny,
+                                  _ptr(sdf), _ptr(mu), cnt, st))
+    return sdf, mu, {"samples": cnt[0], "medial": cnt[1], "kept": cnt[2]}
+
+
 def _stats_dict(s: mesh_stats) -> dict:
     return {name: getattr(s, name) for name, _ in mesh_stats._fields_}
 
@@ -413,6 +432,15 @@ class Mesh:
 
     def set_tuning(self, n_opt: float, lanes: int = 16):
         _check(lib().mesh_set_tuning(self._h, n_opt, lanes))
+
+    def medial_points(self):
+        """(v (n, 4): v1 and v2 of every point, flags (n,) bit 0 / 1: present), Sec. 3.3."""
+        n = self.n
+        v = np.zeros((n, 4))
+        f = np.zeros(n, dtype=np.uint8)
+        _check(lib().mesh_medial_points(self._h, v.ctypes.data_as(C.POINTER(C.c_double)),
+                                        f.ctypes.data_as(C.POINTER(C.c_uint8))))
+        return v, f
 
     def set_quality_target(self, min_angle_deg: float):
         _check(lib().mesh_set_quality_target(self._h, min_angle_deg))

@@ -490,6 +490,88 @@ __global__ void k_tri_write(const __grid_constant__ IterArgs<T> a, int32_t s0, i
     }
 }
 
+// ------------------------------------------------------------------ medial points
+// (Sec. 3.3) of every point of a single mesh, from the emitted triangles: the
+// Voronoi vertices of a cell are the circumcentres of its triangles (fixed
+// formula on the canonical order).  v1: the one farthest from the point; v2:
+// the farthest with (c - p) . (v1 - p) <= 0; ties to the smaller ascending
+// vertex-id triple.  Written by id: v[4 id ..] = (v1, v2), flags bit 0 / 1.
+__device__ __forceinline__ bool triple_before(int a0, int a1, int a2, int b0, int b1, int b2) {
+    // both triples ascending
+    if (a0 != b0) return a0 < b0;
+    if (a1 != b1) return a1 < b1;
+    return a2 < b2;
+}
+
+__device__ __forceinline__ void sort3(int& a, int& b, int& c) {
+    if (a > b) { int t = a; a = b; b = t; }
+    if (b > c) { int t = b; b = c; c = t; }
+    if (a > b) { int t = a; a = b; b = t; }
+}
+
+template <typename T>
+__global__ void k_medial(const __grid_constant__ IterArgs<T> a, int32_t ns, double* v, uint8_t* flags) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    int ne = a.ring_n[s];
+    uint64_t vm = a.vmask[s];
+    int idi = a.srt.id[s];
+    double px = (double)a.srt.x[s], py = (double)a.srt.y[s];
+    double best[2] = {-1.0, -1.0}, cx[2] = {0, 0}, cy[2] = {0, 0};
+    int tb[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1 && best[0] < 0.0) break;
+        double ux = fsub(cx[0], px), uy = fsub(cy[0], py);
+        for (int t = 0; t < ne; t++) {
+            if (!((vm >> t) & 1ull)) continue;
+            int j = a.ring[(size_t)s * kRingCap + t], k = a.ring[(size_t)s * kRingCap + (t + 1 == ne ? 0 : t + 1)];
+            int idj = a.srt.id[j], idk = a.srt.id[k];
+            // canonical order: smallest id first, counter-clockwise
+            int o0 = s, o1 = j, o2 = k;
+            if (idj < idi && idj < idk) { o0 = j; o1 = k; o2 = s; }
+            else if (idk < idi && idk < idj) { o0 = k; o1 = s; o2 = j; }
+            double ox, oy, R;
+            circumcentre_fixed((double)a.srt.x[o0], (double)a.srt.y[o0], (double)a.srt.x[o1], (double)a.srt.y[o1],
+                               (double)a.srt.x[o2], (double)a.srt.y[o2], ox, oy, R);
+            double dx = fsub(ox, px), dy = fsub(oy, py);
+            if (pass == 1 && !(fadd(fmul(dx, ux), fmul(dy, uy)) <= 0.0)) continue;
+            double d = __dsqrt_rn(fadd(fmul(dx, dx), fmul(dy, dy)));
+            int q0 = idi, q1 = idj, q2 = idk;
+            sort3(q0, q1, q2);
+            if (d > best[pass] ||
+                (d == best[pass] && triple_before(q0, q1, q2, tb[pass][0], tb[pass][1], tb[pass][2]))) {
+                best[pass] = d;
+                cx[pass] = ox;
+                cy[pass] = oy;
+                tb[pass][0] = q0;
+                tb[pass][1] = q1;
+                tb[pass][2] = q2;
+            }
+        }
+    }
+    uint8_t f = 0;
+    double* o = v + 4 * (size_t)idi;
+    if (best[0] >= 0.0) {
+        o[0] = cx[0];
+        o[1] = cy[0];
+        f |= 1;
+    }
+    if (best[1] >= 0.0) {
+        o[2] = cx[1];
+        o[3] = cy[1];
+        f |= 2;
+    }
+    flags[idi] = f;
+}
+
+template <typename T>
+void launch_medial(const IterArgs<T>& a, int32_t ns, double* v, uint8_t* flags, cudaStream_t st) {
+    int g = (ns + kThreads - 1) / kThreads;
+    if (g > 0) k_medial<T><<<g, kThreads, 0, st>>>(a, ns, v, flags);
+}
+template void launch_medial<double>(const IterArgs<double>&, int32_t, double*, uint8_t*, cudaStream_t);
+template void launch_medial<float>(const IterArgs<float>&, int32_t, double*, uint8_t*, cudaStream_t);
+
 template <typename T>
 void launch_tri_count(const IterArgs<T>& a, int32_t s0, int32_t ns, int32_t* cnt, cudaStream_t st) {
     int g = (ns + kThreads - 1) / kThreads;

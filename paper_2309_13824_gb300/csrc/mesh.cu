@@ -1432,6 +1432,37 @@ int mesh_get_state(mesh_t* m, void* xy, uint8_t* cls, double* dprev) {
     return get_state(m, 0, xy, cls, dprev);
 }
 
+int mesh_medial_points(mesh_t* m, double* v, uint8_t* flags) {
+    if (!m || !v || !flags) return fail(TRIME_EINVAL, "NULL argument");
+    const Part& p = m->parts[0];
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if (m->tri_stale) {
+        enqueue(m, false, 1);
+        if ((rc = force_retri(m, -1))) return rc;
+        m->tri_stale = false;
+    }
+    if (p.n == 0) return sync_out(m);
+    size_t n = (size_t)p.n;
+    double* dv = nullptr;
+    uint8_t* df = nullptr;
+    CUDA_TRY(cudaMalloc(&dv, sizeof(double) * 4 * n));
+    if (cudaMalloc(&df, n) != cudaSuccess) {
+        cudaFree(dv);
+        return fail(TRIME_ENOMEM, "cudaMalloc failed");
+    }
+    if (m->prec == 0) launch_medial<double>(make_args<double>(m, 1), (int32_t)p.n, dv, df, m->st);
+    else launch_medial<float>(make_args<float>(m, 1), (int32_t)p.n, dv, df, m->st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, dv, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, m->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flags, df, n, cudaMemcpyDeviceToHost, m->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    cudaFree(dv);
+    cudaFree(df);
+    if (e != cudaSuccess) return fail(TRIME_ECUDA, std::string("medial points: ") + cudaGetErrorString(e));
+    return sync_out(m);
+}
+
 int mesh_get_count(mesh_t* m, int64_t* n_current, int64_t* n_total) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
     if (n_current) *n_current = m->parts[0].n;
