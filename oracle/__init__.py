@@ -111,6 +111,10 @@ def _load():
         lib.om_boundary_samples.restype = C.c_int64
         lib.om_boundary_samples.argtypes = [dp, C.c_int64, C.c_double, C.c_double, dp, C.c_int64]
         lib.om_medial_points.argtypes = [C.c_void_p, dp, u8p]
+        lib.om_init_points.restype = C.c_int64
+        lib.om_init_points.argtypes = [P(_Grid), P(_Grid), C.c_int64, C.c_uint64, P(_Params), dp, C.c_int64]
+        lib.om_splitmix64.restype = C.c_uint64
+        lib.om_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         lib.om_lfs.restype = C.c_int64
         lib.om_lfs.argtypes = [dp, C.c_int64, dp, C.c_int64, C.c_double, C.c_int32, dp]
         _lib = lib
@@ -205,6 +209,26 @@ def boundary_samples(verts_cw, ds, geps_hat) -> np.ndarray:
     out = np.empty((n, 2))
     lib.om_boundary_samples(_dp(v), len(v), float(ds), float(geps_hat), _dp(out), n)
     return out
+
+
+def init_points(sdf, sizing, n_init, seed=0, **params) -> np.ndarray:
+    """Sec. 3.5 initial points (om_init_points), (n, 2) float64."""
+    lib = _load()
+    p = _Params()
+    lib.om_default_params(C.byref(p))
+    for k, v in params.items():
+        setattr(p, k, v)
+    gs, gz = _cgrid(sdf), _cgrid(sizing)
+    n = lib.om_init_points(C.byref(gs[0]), C.byref(gz[0]), int(n_init), int(seed), C.byref(p), None, 0)
+    if n < 0:
+        raise ValueError(lib.om_last_error().decode())
+    out = np.empty((n, 2))
+    lib.om_init_points(C.byref(gs[0]), C.byref(gz[0]), int(n_init), int(seed), C.byref(p), _dp(out), n)
+    return out
+
+
+def splitmix64(seed, n) -> int:
+    return int(_load().om_splitmix64(seed, n))
 
 
 def lfs(samples, medial, r_nei, n_thres=3):

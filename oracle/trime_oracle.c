@@ -1856,3 +1856,87 @@ int64_t om_lfs(const double* sxy, int64_t ns, const double* mxy, int64_t nm, dou
     free(keep);
     return kept;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.5: point initialisation                                            */
+/* ------------------------------------------------------------------------ */
+uint64_t om_splitmix64(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int64_t om_init_points(const om_grid* sdf, const om_grid* sizing, int64_t n_init, uint64_t seed, const om_params* p,
+                       double* out, int64_t cap) {
+    if (n_init < 1) { set_err("n_init must be >= 1"); return -1; }
+    om_mesh* m = (om_mesh*)calloc(1, sizeof *m);
+    if (!m) return -1;
+    if (p) m->P = *p; else om_default_params(&m->P);
+    m->N = n_init;
+    if (grid_copy(&m->sdf, sdf) || grid_copy(&m->siz, sizing) || geometry_setup(m)) {
+        set_err("bad grids");
+        om_destroy(m);
+        return -1;
+    }
+    int ncx = m->ncx, ncy = m->ncy;
+    size_t nc = (size_t)ncx * (size_t)ncy;
+    double dx = m->sdf.dx, dy = m->sdf.dy;
+    double band = m->P.eta * fmin(dx, dy);
+    double* rho = (double*)malloc(nc * sizeof(double));
+    uint8_t* sel = (uint8_t*)malloc(nc);
+    double* carry = (double*)calloc(nc, sizeof(double));
+    int64_t* cnt = (int64_t*)calloc(nc, sizeof(int64_t));
+    double sum_rho = 0.0;
+    for (int gj = 0; gj < ncy; gj++)
+        for (int gi = 0; gi < ncx; gi++) {
+            size_t c = cidx(m, gi, gj);
+            const float* r0 = m->sdf.v + (size_t)gj * m->sdf.nx + gi;
+            const float* r1 = r0 + m->sdf.nx;
+            double sm = 0.25 * ((((double)r0[0] + (double)r0[1]) + (double)r1[0]) + (double)r1[1]);
+            double mu = bilin(&m->siz, m->sdf.x0 + ((double)gi + 0.5) * dx, m->sdf.y0 + ((double)gj + 0.5) * dy);
+            rho[c] = 1.0 / (mu * mu);
+            sel[c] = m->gcls[c] == CLS_INNER || (m->gcls[c] == CLS_BOUNDARY && sm <= band);
+            if (sel[c]) sum_rho += rho[c];
+        }
+    int64_t total = 0;
+    for (int gj = 0; gj < ncy; gj++)
+        for (int gi = 0; gi < ncx; gi++) {
+            size_t c = cidx(m, gi, gj);
+            if (!sel[c]) continue;
+            double val = (rho[c] / sum_rho) * (double)n_init + carry[c];
+            double k = floor(val + 0.5);
+            if (k < 0.0) k = 0.0;
+            double R = val - k;
+            int nb[4][2] = {{gi + 1, gj}, {gi - 1, gj + 1}, {gi, gj + 1}, {gi + 1, gj + 1}};
+            int mn = 0;
+            for (int q = 0; q < 4; q++)
+                if (nb[q][0] >= 0 && nb[q][0] < ncx && nb[q][1] < ncy && sel[cidx(m, nb[q][0], nb[q][1])]) mn++;
+            for (int q = 0; q < 4 && mn > 0; q++)
+                if (nb[q][0] >= 0 && nb[q][0] < ncx && nb[q][1] < ncy && sel[cidx(m, nb[q][0], nb[q][1])])
+                    carry[cidx(m, nb[q][0], nb[q][1])] += R / (double)mn;
+            cnt[c] = (int64_t)k;
+            total += cnt[c];
+        }
+    int64_t g = 0;
+    for (int gj = 0; gj < ncy; gj++)
+        for (int gi = 0; gi < ncx; gi++) {
+            size_t c = cidx(m, gi, gj);
+            for (int64_t k = 0; k < cnt[c]; k++, g++) {
+                double u = (double)(om_splitmix64(seed, (uint64_t)(2 * g)) >> 11) * 0x1.0p-53;
+                double w = (double)(om_splitmix64(seed, (uint64_t)(2 * g + 1)) >> 11) * 0x1.0p-53;
+                double cx0 = m->sdf.x0 + (double)gi * dx, cy0 = m->sdf.y0 + (double)gj * dy;
+                double pt[2] = {cx0 + u * dx, cy0 + w * dy};
+                if (m->gcls[c] == CLS_BOUNDARY && bilin(&m->sdf, pt[0], pt[1]) > m->ggeps[c]) {
+                    double q[2];
+                    newton_project(m, pt, q);
+                    pt[0] = q[0];
+                    pt[1] = q[1];
+                }
+                if (g < cap && out) { out[2 * g] = pt[0]; out[2 * g + 1] = pt[1]; }
+            }
+        }
+    free(rho); free(sel); free(carry); free(cnt);
+    om_destroy(m);
+    return total;
+}

@@ -19,6 +19,7 @@
  *   - signed distance from clockwise line segments            Sec. 3.1
  *   - element sizing field from boundary samples and lfs      Sec. 3.3 Eq. 7
  *   - boundary samples, medial axis, local feature size       App. A, Sec. 3.3
+ *   - point initialisation with Floyd-Steinberg dithering      Sec. 3.5
  *
  * Every sign decision of the triangulation (incircle / orientation) is exact:
  * big-integer arithmetic behind a deliberately loose double-precision filter,
@@ -184,6 +185,24 @@ void om_medial_points(const om_mesh* m, double* v, uint8_t* flags);
  * its distance to the closest kept point.  Returns the number kept or -1. */
 int64_t om_lfs(const double* sxy, int64_t ns, const double* mxy, int64_t nm, double r_nei, int32_t n_thres,
                double* lfs);
+
+/* Sec. 3.5 point initialisation: the inner and selected boundary cells of the
+ * geometry grid (the SDF grid's cells; a boundary cell is selected when the
+ * SDF at its midpoint is at most eta min(dx, dy)) expect n^E = rho_norm n_init
+ * points (rho = 1/mu^2 at the midpoint, normalised over the selected cells).
+ * In row-major order (rows j = 0, 1, ..., columns i = 0, 1, ... within a row)
+ * each selected cell takes round(n^E + carried residual) points (at least 0;
+ * halves round up) and passes the residual in equal parts to its selected
+ * neighbours not yet visited among (i+1, j), (i-1, j+1), (i, j+1), (i+1, j+1).
+ * The k-th point overall is uniform in its cell: x = (x0 + i dx) + u dx with
+ * u = (h(2k) >> 11) 2^-53, y likewise with h(2k+1), where h(n) is the
+ * SplitMix64 output of seed + (n+1) 0x9E3779B97F4A7C15.  A point of a
+ * selected boundary cell whose SDF exceeds that cell's geps is projected by
+ * the damped Newton step of Sec. 4.3 (h_i and geps_i from N = n_init).  Writes
+ * up to cap (x, y) pairs in that order; returns the count, or -1. */
+int64_t om_init_points(const om_grid* sdf, const om_grid* sizing, int64_t n_init, uint64_t seed, const om_params* p,
+                       double* out, int64_t cap);
+uint64_t om_splitmix64(uint64_t seed, uint64_t n);
 
 /* Standalone pieces for pins. */
 int om_polygon_centroid(const om_grid* sizing, const double* gen, const double* poly, int nv,
