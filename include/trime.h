@@ -240,6 +240,26 @@ int mesh_segment_sdf_grid(const double* xy, int64_t nv, double x0, double y0, do
 int mesh_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K, double x0, double y0, double x1,
                       double y1, int32_t nx, int32_t ny, float* out, void* cuda_stream);
 
+/* Sec. 3.5: initial points for a mesh of n_init points (h_i and geps_i as
+ * mesh_init would compute them for n_init points; p NULL = defaults, of
+ * which eta, fac_geps, newton_max and damping are used).  The inner cells of
+ * the SDF grid and the boundary cells whose midpoint SDF is at most
+ * eta min(dx, dy) expect n^E = rho_norm n_init points (rho = 1/mu^2 at the
+ * cell midpoint, normalised over those cells); in row-major order (rows
+ * j = 0, 1, ...; i = 0, 1, ... within a row) each takes round(n^E + carried
+ * residual) points (halves up, at least 0) and passes the residual in equal
+ * parts to its selected neighbours not yet visited among (i+1, j), (i-1, j+1),
+ * (i, j+1), (i+1, j+1) (Floyd-Steinberg).  The k-th point overall is uniform
+ * in its cell: x = (x0 + i dx) + u dx, u = (h(2k) >> 11) 2^-53, y likewise
+ * with h(2k+1), h(n) the SplitMix64 output of seed + (n+1) 0x9E3779B97F4A7C15;
+ * a point of a boundary cell whose SDF exceeds the cell's geps is projected
+ * by the damped Newton iteration of Sec. 4.3.  xy: HOST array of cap (x, y)
+ * float64 pairs; *n_out = the number of points (which differs from n_init by
+ * the residuals left at the last cells); TRIME_ECAPACITY if cap is smaller.
+ * Synchronous. */
+int mesh_init_points(const mesh_grid2d* sdf, const mesh_grid2d* sizing, int64_t n_init, uint64_t seed,
+                     const mesh_params* p, double* xy, int64_t cap, int64_t* n_out, void* cuda_stream);
+
 /* Sec. 3.3: medial-axis approximating points of the points of m (read as
  * boundary samples), from the triangles of its last triangulation (rebuilt
  * first if the points changed since): the Voronoi vertices of a cell are the

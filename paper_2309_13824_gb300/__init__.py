@@ -70,7 +70,7 @@ class mesh_tuning(C.Structure):
 
 
 # every symbol include/trime.h declares
-EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing", "mesh_get_triangles",
+EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing", "mesh_init_points", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
            "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step",
            "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
@@ -163,8 +163,11 @@ def lib():
     L.mesh_medial_points.argtypes = [vp, P(C.c_double), P(C.c_uint8)]
     L.mesh_auto_sizing.argtypes = [P(C.c_double), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int32, C.c_int32, vp, vp, P(C.c_int64), vp]
+    L.mesh_init_points.argtypes = [P(mesh_grid2d), P(mesh_grid2d), C.c_int64, C.c_uint64, P(mesh_params),
+                                   P(C.c_double), C.c_int64, P(C.c_int64), vp]
     for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state",
-                 "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing", "mesh_get_triangles", "mesh_get_points",
+                 "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing",
+                 "mesh_init_points", "mesh_get_triangles", "mesh_get_points",
                  "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_bucket_points",
                  "mesh_exact_predicates", "mesh_profile_step", "mesh_bucket_points_noalloc", "mesh_batch_init",
                  "mesh_batch_size", "mesh_batch_rebuild", "mesh_batch_step", "mesh_batch_get_triangles",
@@ -310,6 +313,22 @@ def auto_sizing(verts_cw, K: float, n: int, box=(-1.1, -1.1, 1.1, 1.1), ny: int 
     _check(lib().mesh_auto_sizing(v.ctypes.data_as(C.POINTER(C.c_double)), len(v), float(K), x0, y0, x1, y1, n, ny,
                                   _ptr(sdf), _ptr(mu), cnt, st))
     return sdf, mu, {"samples": cnt[0], "medial": cnt[1], "kept": cnt[2]}
+
+
+def init_points(sdf, sizing, n_init: int, seed: int = 0, stream=None, **params) -> np.ndarray:
+    """Sec. 3.5 initial points (mesh_init_points): (n, 2) float64."""
+    p = _params(params)
+    gs, ks = _grid(sdf)
+    gz, kz = _grid(sizing)
+    n = C.c_int64()
+    st = C.c_void_p(0 if stream is None else int(stream))
+    rc = lib().mesh_init_points(C.byref(gs), C.byref(gz), int(n_init), int(seed), C.byref(p), None, 0, C.byref(n), st)
+    if rc not in (TRIME_OK, TRIME_ECAPACITY):
+        _check(rc)
+    out = np.empty((n.value, 2))
+    _check(lib().mesh_init_points(C.byref(gs), C.byref(gz), int(n_init), int(seed), C.byref(p),
+                                  out.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n), st))
+    return out
 
 
 def _stats_dict(s: mesh_stats) -> dict:

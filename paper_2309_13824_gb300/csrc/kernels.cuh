@@ -126,6 +126,10 @@ template <typename T>
 int add_select(const IterArgs<T>& a, int32_t n0, int32_t ntri, int64_t nadd, const int32_t* toff, void* keys,
                int32_t* hist, int32_t* hhist, int32_t* cnt_id, int32_t* off_id, int32_t* scan_tmp, double* gh,
                double* ggeps, int32_t nc, double scale, cudaStream_t st, std::string& err);
+// Sec. 3.5 initial points: point q uniform in cell pcell[q] (SplitMix64
+// stream of `seed`), projected by damped Newton when outside a boundary cell
+void launch_init_points(const DevGrid& sdf, const uint8_t* gcls, const double* ggeps, const int32_t* pcell,
+                        int64_t n, uint64_t seed, double damping, int newton_max, double* out, cudaStream_t st);
 // medial points (Sec. 3.3) of the ns points of a single mesh from its last
 // triangulation, by id: v[4 id ..] = (v1, v2), flags bit 0 / 1 = present
 template <typename T> void launch_medial(const IterArgs<T>& a, int32_t ns, double* v, uint8_t* flags,

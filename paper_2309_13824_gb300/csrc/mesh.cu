@@ -177,8 +177,9 @@ static bool grid_ok(const mesh_grid2d* g) {
 }
 
 struct HostGeometry {
-    std::vector<uint8_t> cls, idist;
-    std::vector<double> h, geps;
+    std::vector<uint8_t> cls, idist, sel;
+    std::vector<double> h, geps, rho;
+    double sum_rho = 0;
     double havg = 0;
     double rho_eff = 0;  // point-weighted mean point density (points per unit area)
 };
@@ -196,8 +197,10 @@ static int host_geometry(const mesh_grid2d& sdf, const mesh_grid2d& siz, int64_t
     G.cls.resize(nc);
     G.h.resize(nc);
     G.geps.resize(nc);
-    std::vector<double> rho(nc);
-    std::vector<uint8_t> sel(nc);
+    std::vector<double>& rho = G.rho;
+    std::vector<uint8_t>& sel = G.sel;
+    rho.assign(nc, 0.0);
+    sel.assign(nc, 0);
     double sum_rho = 0.0;
     int64_t nsel = 0;
     for (int gj = 0; gj < ncy; gj++)
@@ -218,6 +221,7 @@ static int host_geometry(const mesh_grid2d& sdf, const mesh_grid2d& siz, int64_t
             }
         }
     if (nsel == 0) return fail(TRIME_EINVAL, "the SDF grid has no inner or selected boundary cells");
+    G.sum_rho = sum_rho;
     double sum_h = 0.0;
     for (int gj = 0; gj < ncy; gj++)
         for (int gi = 0; gi < ncx; gi++) {
@@ -1430,6 +1434,76 @@ int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats) {
 int mesh_get_state(mesh_t* m, void* xy, uint8_t* cls, double* dprev) {
     if (!m) return fail(TRIME_EINVAL, "mesh is NULL");
     return get_state(m, 0, xy, cls, dprev);
+}
+
+int mesh_init_points(const mesh_grid2d* sdf, const mesh_grid2d* sizing, int64_t n_init, uint64_t seed,
+                     const mesh_params* p, double* xy, int64_t cap, int64_t* n_out, void* cuda_stream) {
+    if (!sdf || !sizing || !n_out) return fail(TRIME_EINVAL, "NULL argument");
+    if (n_init < 1 || n_init > (int64_t)1 << 30) return fail(TRIME_EINVAL, "n_init must be 1 .. 2^30");
+    mesh_params P;
+    if (p) P = *p;
+    else mesh_default_params(&P);
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (!grid_ok(sdf) || !grid_ok(sizing)) return fail(TRIME_EINVAL, "invalid grid");
+    for (size_t k = 0; k < (size_t)sizing->nx * sizing->ny; k++)
+        if (!(sizing->v[k] > 0.0f)) return fail(TRIME_EINVAL, "sizing values must be positive");
+    HostGeometry G;
+    if ((rc = host_geometry(*sdf, *sizing, n_init, P, G))) return rc;
+    // Sec. 3.5: Floyd-Steinberg dithering of n^E = rho_norm n_init over the
+    // selected cells in row-major order, the residual passed in equal parts to
+    // the selected neighbours not yet visited
+    int ncx = sdf->nx - 1, ncy = sdf->ny - 1;
+    size_t nc = (size_t)ncx * ncy;
+    std::vector<double> carry(nc, 0.0);
+    std::vector<int32_t> pcell;
+    for (int gj = 0; gj < ncy; gj++)
+        for (int gi = 0; gi < ncx; gi++) {
+            size_t c = (size_t)gj * ncx + gi;
+            if (!G.sel[c]) continue;
+            double val = (G.rho[c] / G.sum_rho) * (double)n_init + carry[c];
+            double k = std::floor(val + 0.5);
+            if (k < 0.0) k = 0.0;
+            double R = val - k;
+            const int nb[4][2] = {{gi + 1, gj}, {gi - 1, gj + 1}, {gi, gj + 1}, {gi + 1, gj + 1}};
+            int mn = 0;
+            for (int q = 0; q < 4; q++)
+                if (nb[q][0] >= 0 && nb[q][0] < ncx && nb[q][1] < ncy && G.sel[(size_t)nb[q][1] * ncx + nb[q][0]]) mn++;
+            for (int q = 0; q < 4 && mn > 0; q++)
+                if (nb[q][0] >= 0 && nb[q][0] < ncx && nb[q][1] < ncy && G.sel[(size_t)nb[q][1] * ncx + nb[q][0]])
+                    carry[(size_t)nb[q][1] * ncx + nb[q][0]] += R / (double)mn;
+            if ((int64_t)pcell.size() + (int64_t)k > (int64_t)1 << 30) return fail(TRIME_EINVAL, "too many points");
+            pcell.insert(pcell.end(), (size_t)k, (int32_t)c);
+        }
+    int64_t n = (int64_t)pcell.size();
+    *n_out = n;
+    if (cap < n) return fail(TRIME_ECAPACITY, "point buffer too small");
+    if (n == 0) return TRIME_OK;
+    if (!xy) return fail(TRIME_EINVAL, "xy is NULL");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    size_t ns = (size_t)sdf->nx * sdf->ny;
+    float* dsdf = nullptr;
+    uint8_t* dcls = nullptr;
+    double *dgeps = nullptr, *dout = nullptr;
+    int32_t* dcell = nullptr;
+    bool ok = cudaMalloc(&dsdf, ns * sizeof(float)) == cudaSuccess && cudaMalloc(&dcls, nc) == cudaSuccess &&
+              cudaMalloc(&dgeps, nc * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&dout, 2 * (size_t)n * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&dcell, (size_t)n * sizeof(int32_t)) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(dsdf, sdf->v, ns * sizeof(float), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(dcls, G.cls.data(), nc, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(dgeps, G.geps.data(), nc * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(dcell, pcell.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    if (ok) {
+        launch_init_points(dev_grid(sdf, dsdf), dcls, dgeps, dcell, n, seed, P.damping, P.newton_max, dout, st);
+        ok = cudaGetLastError() == cudaSuccess &&
+             cudaMemcpyAsync(xy, dout, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+             cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    for (void* q : {(void*)dsdf, (void*)dcls, (void*)dgeps, (void*)dout, (void*)dcell})
+        if (q) cudaFree(q);
+    if (!ok) return fail(TRIME_ECUDA, "point initialisation on the device failed");
+    return TRIME_OK;
 }
 
 int mesh_medial_points(mesh_t* m, double* v, uint8_t* flags) {

@@ -97,3 +97,13 @@ def test_segment_sdf_invalid_arguments(g):
     assert call(np.array([[0.0, np.inf], [0.0, 1.0], [1.0, 0.0]])) == g.TRIME_EINVAL
     assert call(tri, box=(1, -1, -1, 1)) == g.TRIME_EINVAL
     assert call(tri, n=1) == g.TRIME_EINVAL
+
+
+def test_init_points_invalid_arguments(g):
+    sdf = W.grid_from_fn(W.disk_sdf_fn, 32)
+    gs, a = g._grid(sdf)
+    gz, b = g._grid(W.constant_grid(1.0))
+    n = C.c_int64()
+    assert g.lib().mesh_init_points(C.byref(gs), C.byref(gz), 0, 1, None, None, 0, C.byref(n), None) == g.TRIME_EINVAL
+    gneg, c = g._grid(W.constant_grid(-1.0))
+    assert g.lib().mesh_init_points(C.byref(gs), C.byref(gneg), 10, 1, None, None, 0, C.byref(n), None) == g.TRIME_EINVAL
