@@ -363,6 +363,41 @@ def segment_sdf_leg(g, torch, stream):
             "note": "device time includes its scratch allocation and the cell candidate search"}
 
 
+def polygon_leg(g, torch, stream):
+    """From a polygon to a mesh with the initialisation pipeline (survey rows
+    f3, f4): the benchmark star (500 clockwise segments) -> its SDF grid and
+    automatic sizing field on 1024^2 (App. A, Sec. 3.3, Eq. 7, K = 0.1) ->
+    10^6 dithered initial points (Sec. 3.5) -> hybrid meshing (FP32 positions)
+    until termination.  Host clock around synchronous calls."""
+    import workloads as W
+
+    v = W.star_polygon(500, 0.4, 1.0, 2)
+    n, box = 1024, (-1.1, -1.1, 1.1, 1.1)
+    t0 = time.perf_counter()
+    sdf, mu, counts = g.auto_sizing(v, 0.1, n, box)
+    t_auto = time.perf_counter() - t0
+    sg, zg = W.Grid(sdf, *box), W.Grid(mu, *box)
+    t0 = time.perf_counter()
+    pts = g.init_points(sg, zg, 1_000_000, seed=1)
+    t_init = time.perf_counter() - t0
+    out = {"auto_sizing_seconds": t_auto, "samples": counts["samples"], "medial_points": counts["medial"],
+           "medial_kept": counts["kept"], "sizing_min": float(mu.min()), "sizing_max": float(mu.max()),
+           "init_points_seconds": t_init, "points": len(pts)}
+    try:
+        m = g.Mesh(sg, zg, W.to_fp32_positions(pts), method=2, precision=1, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = m.step(2000)
+        torch.cuda.synchronize()
+        out.update({"meshing_seconds": time.perf_counter() - t0, "iterations": s["iterations"],
+                    "terminated": bool(s["terminated"]), "min_angle_deg": s["min_angle_deg"],
+                    "max_alpha": s["max_alpha"], "half_mean_alpha": s["half_mean_alpha"]})
+        m.close()
+    except g.MeshError as e:
+        out["meshing_error"] = str(e)
+    return out
+
+
 def distmesh_leg(g, torch, stream):
     """The DistMesh method (config 1's disk at 1e4 points and the annulus at
     1e6) to termination, re-triangulating every iteration and only after large
@@ -653,6 +688,7 @@ def main():
         extras["distmesh"] = distmesh_leg(g, torch, stream)
         extras["point_addition"] = addition_leg(g, torch, stream)
         extras["segment_sdf"] = segment_sdf_leg(g, torch, stream)
+        extras["from_polygon"] = polygon_leg(g, torch, stream)
         if args.sweep:
             extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
         threads = os.cpu_count() or 1
