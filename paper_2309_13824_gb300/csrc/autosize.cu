@@ -262,6 +262,9 @@ extern "C" int mesh_auto_sizing(const double* xy, int64_t nv, double K, double x
     std::vector<uint8_t> fl((size_t)ns);
     mesh_stats st;
     rc = mesh_rebuild(m, &st);
+    // cells with more edges than a ring row are a guard trip for the mesh but
+    // are rebuilt in full for the medial points
+    if (rc == TRIME_EDEVICE && st.exact_overflow == 0 && st.ring_overflow > 0) rc = TRIME_OK;
     if (!rc) rc = mesh_medial_points(m, v.data(), fl.data());
     mesh_destroy(m);
     if (rc) return rc;

@@ -564,6 +564,89 @@ __global__ void k_medial(const __grid_constant__ IterArgs<T> a, int32_t ns, doub
     flags[idi] = f;
 }
 
+// the medial points of the cells rebuilt by the big-cell pass (rings of up
+// to kBigRing edges); a triangle counts when the fixed formulas emit it and
+// find it valid, as the emit kernel decides for ordinary cells
+template <typename T>
+__global__ void k_medial_big(const __grid_constant__ IterArgs<T> a, int32_t n, const int32_t* rings,
+                             const int32_t* lens, double* v, uint8_t* flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const MeshView& V = a.V;
+    int s = a.ovf3_list[i];
+    const int32_t* ring = rings + (size_t)i * kBigRing;
+    int ne = lens[i];
+    int idi = a.srt.id[s];
+    double px = (double)a.srt.x[s], py = (double)a.srt.y[s];
+    double best[2] = {-1.0, -1.0}, cx[2] = {0, 0}, cy[2] = {0, 0};
+    int tb[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1 && best[0] < 0.0) break;
+        double ux = fsub(cx[0], px), uy = fsub(cy[0], py);
+        for (int t = 0; t < ne; t++) {
+            int j = ring[t], k = ring[t + 1 == ne ? 0 : t + 1];
+            if (j < 0 || k < 0) continue;
+            double xs[3] = {px, (double)a.srt.x[j], (double)a.srt.x[k]};
+            double ys[3] = {py, (double)a.srt.y[j], (double)a.srt.y[k]};
+            int ids[3] = {idi, a.srt.id[j], a.srt.id[k]};
+            int cells[3] = {a.cell[s], a.cell[j], a.cell[k]};
+            int r = 0;
+            if (ids[1] < ids[r]) r = 1;
+            if (ids[2] < ids[r]) r = 2;
+            int o1 = r == 2 ? 0 : r + 1, o2 = o1 == 2 ? 0 : o1 + 1;
+            double ox, oy, R;
+            circumcentre_fixed(xs[r], ys[r], xs[o1], ys[o1], xs[o2], ys[o2], ox, oy, R);
+            bool em = true;
+            for (int q = 0; q < 3 && em; q++) em = reg_contains_fixed(V.P, xs[q], ys[q], V.gh[cells[q]], ox, oy);
+            if (!em) continue;
+            if (V.P.validity) {
+                Tri tr;
+                tr.x[0] = xs[r]; tr.y[0] = ys[r];
+                tr.x[1] = xs[o1]; tr.y[1] = ys[o1];
+                tr.x[2] = xs[o2]; tr.y[2] = ys[o2];
+                if (!valid_fixed(V, tr)) continue;
+            }
+            double dx = fsub(ox, px), dy = fsub(oy, py);
+            if (pass == 1 && !(fadd(fmul(dx, ux), fmul(dy, uy)) <= 0.0)) continue;
+            double d = __dsqrt_rn(fadd(fmul(dx, dx), fmul(dy, dy)));
+            int q0 = ids[0], q1 = ids[1], q2 = ids[2];
+            sort3(q0, q1, q2);
+            if (d > best[pass] ||
+                (d == best[pass] && triple_before(q0, q1, q2, tb[pass][0], tb[pass][1], tb[pass][2]))) {
+                best[pass] = d;
+                cx[pass] = ox;
+                cy[pass] = oy;
+                tb[pass][0] = q0;
+                tb[pass][1] = q1;
+                tb[pass][2] = q2;
+            }
+        }
+    }
+    uint8_t f = 0;
+    double* o = v + 4 * (size_t)idi;
+    if (best[0] >= 0.0) {
+        o[0] = cx[0];
+        o[1] = cy[0];
+        f |= 1;
+    }
+    if (best[1] >= 0.0) {
+        o[2] = cx[1];
+        o[3] = cy[1];
+        f |= 2;
+    }
+    flags[idi] = f;
+}
+
+template <typename T>
+void launch_medial_big(const IterArgs<T>& a, int32_t n, const int32_t* rings, const int32_t* lens, double* v,
+                       uint8_t* flags, cudaStream_t st) {
+    if (n > 0) k_medial_big<T><<<(n + 63) / 64, 64, 0, st>>>(a, n, rings, lens, v, flags);
+}
+template void launch_medial_big<double>(const IterArgs<double>&, int32_t, const int32_t*, const int32_t*, double*,
+                                        uint8_t*, cudaStream_t);
+template void launch_medial_big<float>(const IterArgs<float>&, int32_t, const int32_t*, const int32_t*, double*,
+                                       uint8_t*, cudaStream_t);
+
 template <typename T>
 void launch_medial(const IterArgs<T>& a, int32_t ns, double* v, uint8_t* flags, cudaStream_t st) {
     int g = (ns + kThreads - 1) / kThreads;

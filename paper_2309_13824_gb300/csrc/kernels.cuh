@@ -58,7 +58,7 @@ struct IterArgs {
     MeshView V;        // the mesh of single-mesh launches
     const MeshView* Vs;     // [nmesh] per-mesh views of batched launches
     const int32_t* cmesh;   // [n / kChunk] mesh of each chunk
-    int32_t* ovf_n;    // [2] cells queued for the 32-lane and for the serial Voronoi pass
+    int32_t* ovf_n;    // [3] cells queued for the 32-lane, the serial and the big-cell Voronoi pass
     State<T> cur, srt;
     State<T> wrk;      // the positions a DistMesh iteration without re-triangulation moves (slot order)
     int32_t* cell;     // [n] geometry cell of each sorted slot (fixed formula)
@@ -78,6 +78,7 @@ struct IterArgs {
     double* dbg;       // [8][n] by original id, written when P.debug
     int32_t* ovf_list; // [n] cells whose 16-lane clipping ran out of lanes
     int32_t* ovf2_list; // [n] cells whose 32-lane clipping ran out of lanes (serial pass)
+    int32_t* ovf3_list; // [n] cells with more edges than a ring row (big-cell pass on request)
     float4* pf;        // [n] sorted positions as float pairs (xhi, xlo, yhi, ylo)
     float* pS;         // [n] octagon span S = fac_voro_bound * h of each sorted slot
 };
@@ -106,6 +107,18 @@ inline void launch_voronoi(const IterArgs<T>& a, int lanes, cudaStream_t st) {
     if (a.Vs) launch_voronoi_impl<T, true>(a, lanes, st);
     else launch_voronoi_impl<T, false>(a, lanes, st);
 }
+// the cells listed in ovf3_list (more than kRingCap edges) rebuilt into
+// rings of up to 1024 edges (single mesh): scratch (1024 + 97) float4 per
+// cell, rings 1024 int32 per cell, lens one per cell
+template <typename T>
+void launch_voronoi_big(const IterArgs<T>& a, int32_t n, float4* scratch, int32_t* rings, int32_t* lens,
+                        cudaStream_t st);
+constexpr int kBigRing = 1024;
+constexpr size_t kBigScratchF4 = (size_t)kBigRing + 1 + 96;
+// medial points of the big cells: emission decided by the fixed formulas
+template <typename T>
+void launch_medial_big(const IterArgs<T>& a, int32_t n, const int32_t* rings, const int32_t* lens, double* v,
+                       uint8_t* flags, cudaStream_t st);
 // a3/a4 + quality partials (a8) + Eq. 3 sums
 template <typename T> void launch_emit(const IterArgs<T>& a, int nblocks, cudaStream_t st);
 // a DistMesh iteration that keeps the last triangulation (Algorithm 1): the

@@ -379,6 +379,7 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.dbg = m->dbg;
     a.ovf_list = m->ovf_list;
     a.ovf2_list = m->ovf_list + std::max<int64_t>(m->ncap, m->nslots);
+    a.ovf3_list = m->batched ? nullptr : m->ovf_list + 2 * std::max<int64_t>(m->ncap, m->nslots);
     a.pf = m->pf;
     a.pS = m->pS;
     return a;
@@ -804,13 +805,13 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->ep = dalloc<EmitPartial>(m, (size_t)nblk_cap, rc);
     m->up = dalloc<UpdatePartial>(m, (size_t)nblk_cap, rc);
     m->ctrl = dalloc<DevCtrl>(m, (size_t)nparts, rc);
-    m->ovf_n = dalloc<int32_t>(m, 2, rc);
+    m->ovf_n = dalloc<int32_t>(m, 3, rc);
     m->dbg = P.debug ? dalloc<double>(m, 10 * N, rc) : nullptr;
     m->tcnt = dalloc<int32_t>(m, N + 1, rc);
     m->toff = dalloc<int32_t>(m, N + 1, rc);
     m->tbuf = dalloc<int32_t>(m, 3 * (2 * nmax + 16), rc);
     m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
-    m->ovf_list = dalloc<int32_t>(m, 2 * N, rc);
+    m->ovf_list = dalloc<int32_t>(m, 3 * N, rc);
     m->pf = dalloc<float4>(m, N, rc);
     m->pS = dalloc<float>(m, N, rc);
     if (m->batched) {
@@ -1527,12 +1528,37 @@ int mesh_medial_points(mesh_t* m, double* v, uint8_t* flags) {
     }
     if (m->prec == 0) launch_medial<double>(make_args<double>(m, 1), (int32_t)p.n, dv, df, m->st);
     else launch_medial<float>(make_args<float>(m, 1), (int32_t)p.n, dv, df, m->st);
-    cudaError_t e = cudaGetLastError();
+    // cells with more edges than a ring row: rebuilt by the big-cell pass
+    int32_t nbig = 0;
+    cudaError_t e = cudaMemcpyAsync(&nbig, m->ovf_n + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, m->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+    float4* scratch = nullptr;
+    int32_t *rings = nullptr, *lens = nullptr;
+    if (e == cudaSuccess && nbig > 0) {
+        nbig = std::min<int32_t>(nbig, (int32_t)p.n);
+        e = cudaMalloc(&scratch, sizeof(float4) * kBigScratchF4 * (size_t)nbig);
+        if (e == cudaSuccess) e = cudaMalloc(&rings, sizeof(int32_t) * kBigRing * (size_t)nbig);
+        if (e == cudaSuccess) e = cudaMalloc(&lens, sizeof(int32_t) * (size_t)nbig);
+        if (e == cudaSuccess) {
+            if (m->prec == 0) {
+                launch_voronoi_big<double>(make_args<double>(m, 1), nbig, scratch, rings, lens, m->st);
+                launch_medial_big<double>(make_args<double>(m, 1), nbig, rings, lens, dv, df, m->st);
+            } else {
+                launch_voronoi_big<float>(make_args<float>(m, 1), nbig, scratch, rings, lens, m->st);
+                launch_medial_big<float>(make_args<float>(m, 1), nbig, rings, lens, dv, df, m->st);
+            }
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(v, dv, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, m->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(flags, df, n, cudaMemcpyDeviceToHost, m->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
     cudaFree(dv);
     cudaFree(df);
+    if (scratch) cudaFree(scratch);
+    if (rings) cudaFree(rings);
+    if (lens) cudaFree(lens);
     if (e != cudaSuccess) return fail(TRIME_ECUDA, std::string("medial points: ") + cudaGetErrorString(e));
     return sync_out(m);
 }

@@ -522,11 +522,14 @@ __device__ __forceinline__ Lane edge_vertex(const float4& e, const float4& f, fl
     return L;
 }
 
-// clip_by for one thread: 0 ok / no-op, 1 empty cell, 2 more than kRingCap edges
-template <typename T>
+// clip_by for one thread: 0 ok / no-op, 1 empty cell, 2 more than CAP edges
+template <typename T, int CAP>
 __device__ int clip_serial(float4* E, int& ne, float nx, float ny, float s, int lab, bool bisector, float RB,
                            const IterArgs<T>& a, const CellCtx& ctx) {
-    unsigned long long m = 0;
+    // cut flags: one bit per vertex, in CAP / 64 words
+    unsigned long long mw[(CAP + 63) / 64];
+    for (int w = 0; w < (CAP + 63) / 64; w++) mw[w] = 0;
+    auto cutv = [&](int t) { return (mw[t >> 6] >> (t & 63)) & 1ull; };
     for (int t = 0; t < ne; t++) {
         Lane L = edge_vertex(E[t], E[t + 1 == ne ? 0 : t + 1], RB);
         bool cut;
@@ -541,25 +544,26 @@ __device__ int clip_serial(float4* E, int& ne, float nx, float ny, float s, int 
         } else {
             cut = nx * L.vx + ny * L.vy > s;
         }
-        if (cut) m |= 1ull << t;
+        if (cut) mw[t >> 6] |= 1ull << (t & 63);
     }
-    if (!m) return 0;
-    unsigned long long full = ne >= 64 ? ~0ull : ((1ull << ne) - 1ull);
-    if ((m & full) == full) return 1;
+    int ncut = 0;
+    for (int t = 0; t < ne; t++) ncut += (int)cutv(t);
+    if (ncut == 0) return 0;
+    if (ncut == ne) return 1;
     int starts = 0, sidx = -1;
     for (int t = 0; t < ne; t++) {
         int p = t == 0 ? ne - 1 : t - 1;
-        if (((m >> t) & 1ull) && !((m >> p) & 1ull)) {
+        if (cutv(t) && !cutv(p)) {
             starts++;
             if (sidx < 0) sidx = t;
         }
     }
     if (starts != 1) atomicAdd(&ctx.ctrl->cnt.clip_inconsistent, 1ull);
     int eidx = sidx;
-    while ((m >> eidx) & 1ull) eidx = eidx + 1 == ne ? 0 : eidx + 1;
+    while (cutv(eidx)) eidx = eidx + 1 == ne ? 0 : eidx + 1;
     int k = sidx - eidx + 1;  // kept edges E_e .. E_s
     if (k <= 0) k += ne;
-    if (k + 1 > kRingCap) return 2;
+    if (k + 1 > CAP) return 2;
     // rotate E_e to position 0 in place (three reversals), then append
     auto rev = [&](int i, int j) {
         for (; i < j; i++, j--) {
@@ -585,8 +589,11 @@ __device__ float serial_rmax(const float4* E, int ne, float RB) {
     return r;
 }
 
-template <typename T>
-__device__ void voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int s, float4* E, float4* C) {
+// builds cell s with at most CAP edges; the ring goes to out_ring / *out_len
+// (and cellR); returns the status (2: more than CAP edges)
+template <typename T, int CAP>
+__device__ int voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int s, float4* E, float4* C,
+                                   int32_t* out_ring, int32_t* out_len) {
     const DevParams& P = V.P;
     const float INF = __int_as_float(0x7f800000);
     const float4 pi4 = a.pf[s];
@@ -623,7 +630,7 @@ __device__ void voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int
             float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
             float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
             float sb = b == 0 ? xf + mb : b == 1 ? (Wf - xf) + mb : b == 2 ? yf + mb : (Hf - yf) + mb;
-            status = clip_serial<T>(E, ne, nx, ny, sb, box_label(b), false, RB, a, ctx);
+            status = clip_serial<T, CAP>(E, ne, nx, ny, sb, box_label(b), false, RB, a, ctx);
         }
     }
     float Rmax = status == 0 ? serial_rmax<T>(E, ne, RB) : 0.0f;
@@ -651,7 +658,7 @@ __device__ void voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int
             else used1 |= 1ull << (bi - 64);
             float4 c = C[bi];
             int ne0 = ne;
-            int st = clip_serial<T>(E, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, RB, a, ctx);
+            int st = clip_serial<T, CAP>(E, ne, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, RB, a, ctx);
             if (P.debug) {
                 atomicAdd(&V.ctrl->cnt.vor_picks, 1ull);
                 if (ne != ne0 || st) atomicAdd(&V.ctrl->cnt.vor_cuts, 1ull);
@@ -716,14 +723,14 @@ __device__ void voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int
         }
     }
     if (status != 0) {
-        if (status == 2) atomicAdd(&V.ctrl->cnt.ring_overflow, 1ull);
-        a.ring_n[s] = 0;
+        *out_len = 0;
         a.cellR[s] = 0.0f;
-        return;
+        return status;
     }
-    for (int t = 0; t < ne; t++) a.ring[(size_t)s * kRingCap + t] = __float_as_int(E[t].w);
-    a.ring_n[s] = (uint8_t)ne;
+    for (int t = 0; t < ne; t++) out_ring[t] = __float_as_int(E[t].w);
+    *out_len = ne;
     a.cellR[s] = Rmax;
+    return 0;
 }
 
 template <typename T, bool B>
@@ -734,15 +741,47 @@ __global__ void __launch_bounds__(kSerialThreads) k_voronoi_serial(const __grid_
     int n = a.ovf_n[1];
     for (int i = blockIdx.x * kSerialThreads + threadIdx.x; i < n; i += gridDim.x * kSerialThreads) {
         int s = a.ovf2_list[i];
-        voronoi_cell_serial<T>(a, mesh_of<B>(a, s), s, edges[threadIdx.x], stage[threadIdx.x]);
+        const MeshView& V = mesh_of<B>(a, s);
+        int32_t len;
+        int st = voronoi_cell_serial<T, kRingCap>(a, V, s, edges[threadIdx.x], stage[threadIdx.x],
+                                                   a.ring + (size_t)s * kRingCap, &len);
+        a.ring_n[s] = (uint8_t)len;
+        if (st == 2) {
+            // more edges than a ring row holds: a guard trip, and the cell is
+            // listed for the big-cell pass of the medial points
+            atomicAdd(&V.ctrl->cnt.ring_overflow, 1ull);
+            if (a.ovf3_list) a.ovf3_list[atomicAdd(a.ovf_n + 2, 1)] = s;
+        }
     }
+}
+
+// cells beyond kRingCap edges, rebuilt on request (single mesh): polygon and
+// staged candidates in global scratch, rings of up to kBigCap edges
+constexpr int kBigCap = kBigRing;
+constexpr size_t kBigScratch = kBigScratchF4;  // float4 per cell
+static_assert(kBigScratch == (size_t)kBigCap + 1 + kSerialStage, "scratch layout");
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_voronoi_big(const __grid_constant__ IterArgs<T> a, int32_t n,
+                                                    float4* scratch, int32_t* rings, int32_t* lens) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int s = a.ovf3_list[i];
+        float4* E = scratch + (size_t)i * kBigScratch;
+        voronoi_cell_serial<T, kBigCap>(a, a.V, s, E, E + kBigCap + 1, rings + (size_t)i * kBigCap, lens + i);
+    }
+}
+
+template <typename T>
+void launch_voronoi_big(const IterArgs<T>& a, int32_t n, float4* scratch, int32_t* rings, int32_t* lens,
+                        cudaStream_t st) {
+    if (n > 0) k_voronoi_big<T><<<(n + 31) / 32, 32, 0, st>>>(a, n, scratch, rings, lens);
 }
 
 // lanes = 16: two cells per warp plus the 32-lane pass; lanes = 32: one cell
 // per warp
 template <typename T, bool B>
 void launch_voronoi_impl(const IterArgs<T>& a, int lanes, cudaStream_t st) {
-    cudaMemsetAsync(a.ovf_n, 0, 2 * sizeof(int32_t), st);
+    cudaMemsetAsync(a.ovf_n, 0, 3 * sizeof(int32_t), st);
     if (lanes == 32) {
         int cpb = kVoroThreads / 32;
         int g = (a.n + cpb - 1) / cpb;

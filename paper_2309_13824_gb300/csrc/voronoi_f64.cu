@@ -4,6 +4,7 @@
 
 namespace trime {
 template void launch_voronoi_impl<double, false>(const IterArgs<double>&, int, cudaStream_t);
+template void launch_voronoi_big<double>(const IterArgs<double>&, int32_t, float4*, int32_t*, int32_t*, cudaStream_t);
 
 // device exact predicates on explicit queries (verification hook)
 __global__ void k_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out) {

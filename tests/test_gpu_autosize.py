@@ -56,3 +56,26 @@ def test_pipeline_matches(name):
     assert np.array_equal(sdf.view(np.uint32), ref["sdf"].view(np.uint32))
     want = ref["sizing"].astype(np.float32)
     assert np.array_equal(mu.view(np.uint32), want.view(np.uint32)), np.count_nonzero(mu != want)
+
+
+def test_medial_points_of_a_cell_beyond_64_edges():
+    """A point ringed by 70 others has a 70-edge cell: a capacity guard trip
+    for the mesh, rebuilt in full for its medial points."""
+    import ctypes as C
+
+    import paper_2309_13824_gb300 as g
+    from test_gpu_parity import _ringed_point
+
+    sdf, siz, pts = _ringed_point(70)
+    gm = g.Mesh(sdf, siz, pts, bounded=0, validity=0)
+    st = g.mesh_stats()
+    rc = g.lib().mesh_rebuild(gm._h, C.byref(st))
+    assert rc == g.TRIME_EDEVICE and st.ring_overflow == 1 and st.exact_overflow == 0
+    vg, fg = gm.medial_points()
+    om = oracle.OracleMesh(sdf, siz, pts, bounded=0, validity=0)
+    om.rebuild()
+    vo, fo = om.medial_points()
+    assert len(om.ring(0)) == 70 and fg[0] & 1
+    assert np.array_equal(fg, fo)
+    assert np.array_equal(vg[fg & 1 > 0, :2], vo[fo & 1 > 0, :2])
+    assert np.array_equal(vg[fg & 2 > 0, 2:], vo[fo & 2 > 0, 2:])
