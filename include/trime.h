@@ -253,7 +253,9 @@ int mesh_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K
  * in its cell: x = (x0 + i dx) + u dx, u = (h(2k) >> 11) 2^-53, y likewise
  * with h(2k+1), h(n) the SplitMix64 output of seed + (n+1) 0x9E3779B97F4A7C15;
  * a point of a boundary cell whose SDF exceeds the cell's geps is projected
- * by the damped Newton iteration of Sec. 4.3.  xy: HOST array of cap (x, y)
+ * by the damped Newton iteration of Sec. 4.3 and moved there when the result
+ * is a boundary point (Sec. 4.3 classes; else it stays where it was drawn).
+ * xy: HOST array of cap (x, y)
  * float64 pairs; *n_out = the number of points (which differs from n_init by
  * the residuals left at the last cells); TRIME_ECAPACITY if cap is smaller.
  * Synchronous. */

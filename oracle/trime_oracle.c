@@ -1928,10 +1928,14 @@ int64_t om_init_points(const om_grid* sdf, const om_grid* sizing, int64_t n_init
                 double cx0 = m->sdf.x0 + (double)gi * dx, cy0 = m->sdf.y0 + (double)gj * dy;
                 double pt[2] = {cx0 + u * dx, cy0 + w * dy};
                 if (m->gcls[c] == CLS_BOUNDARY && bilin(&m->sdf, pt[0], pt[1]) > m->ggeps[c]) {
+                    /* the projection counts only when it ends as a boundary
+                     * point (Sec. 4.3); otherwise the point stays where drawn */
                     double q[2];
                     newton_project(m, pt, q);
-                    pt[0] = q[0];
-                    pt[1] = q[1];
+                    if (classify(m, q[0], q[1]) == PT_BOUNDARY) {
+                        pt[0] = q[0];
+                        pt[1] = q[1];
+                    }
                 }
                 if (g < cap && out) { out[2 * g] = pt[0]; out[2 * g + 1] = pt[1]; }
             }

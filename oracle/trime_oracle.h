@@ -198,7 +198,9 @@ int64_t om_lfs(const double* sxy, int64_t ns, const double* mxy, int64_t nm, dou
  * u = (h(2k) >> 11) 2^-53, y likewise with h(2k+1), where h(n) is the
  * SplitMix64 output of seed + (n+1) 0x9E3779B97F4A7C15.  A point of a
  * selected boundary cell whose SDF exceeds that cell's geps is projected by
- * the damped Newton step of Sec. 4.3 (h_i and geps_i from N = n_init).  Writes
+ * the damped Newton step of Sec. 4.3 (h_i and geps_i from N = n_init); the
+ * projection counts when it ends as a boundary point (Sec. 4.3 classes),
+ * otherwise the point stays where it was drawn.  Writes
  * up to cap (x, y) pairs in that order; returns the count, or -1. */
 int64_t om_init_points(const om_grid* sdf, const om_grid* sizing, int64_t n_init, uint64_t seed, const om_params* p,
                        double* out, int64_t cap);

@@ -44,7 +44,9 @@ __global__ void k_init_points(const DevGrid sdf, const uint8_t* gcls, const doub
     double cx0 = fadd(sdf.x0, fmul((double)gi, sdf.dx)), cy0 = fadd(sdf.y0, fmul((double)gj, sdf.dy));
     double x = fadd(cx0, fmul(u, sdf.dx)), y = fadd(cy0, fmul(w, sdf.dy));
     if (gcls[c] == CELL_BOUNDARY && bilin_fixed(sdf, x, y) > ggeps[c]) {
-        // damped Newton projection (Eqs. 8-10), gradient at the iterate
+        // damped Newton projection (Eqs. 8-10), gradient at the iterate; it
+        // counts only when it ends as a boundary point (Sec. 4.3 classes)
+        double x0 = x, y0 = y;
         double pnx = x, pny = y;
         for (int k = 0; k < newton_max; k++) {
             double f, fx, fy, fxy;
@@ -63,6 +65,13 @@ __global__ void k_init_points(const DevGrid sdf, const uint8_t* gcls, const doub
             int ci, cj;
             point_cell_fixed(sdf, x, y, ci, cj);
             if (fabs(bilin_fixed(sdf, x, y)) <= ggeps[cj * ncx + ci]) break;
+        }
+        int ci, cj;
+        bool on = point_cell_fixed(sdf, x, y, ci, cj) && gcls[cj * ncx + ci] == CELL_BOUNDARY &&
+                  fabs(bilin_fixed(sdf, x, y)) <= ggeps[cj * ncx + ci];
+        if (!on) {
+            x = x0;
+            y = y0;
         }
     }
     out[2 * q] = x;

@@ -46,3 +46,19 @@ def test_points_seed_a_mesh():
     m = g.Mesh(ann.sdf, ann.sizing, p, method=2)
     s = m.step(500)
     assert s["terminated"] and s["min_angle_deg"] > 20
+
+
+def test_polygon_to_mesh_input():
+    """A spiky polygon all the way to a mesh: its automatic sizing (1024^2),
+    10^5 initial points from it, and a mesh created and stepped from them."""
+    import paper_2309_13824_gb300 as g
+
+    box = (-1.1, -1.1, 1.1, 1.1)
+    v = W.star_polygon(500, 0.4, 1.0, 2)
+    sdf, mu, counts = g.auto_sizing(v, 0.1, 1024, box)
+    sg, zg = W.Grid(sdf, *box), W.Grid(mu, *box)
+    p = g.init_points(sg, zg, 100_000, seed=2)
+    assert np.all(np.isfinite(p)) and np.all(np.abs(p) <= 1.1)
+    m = g.Mesh(sg, zg, W.to_fp32_positions(p), method=2, precision=1)
+    s = m.step(5, check=False)
+    assert s["n_tri"] > 100_000
