@@ -175,7 +175,10 @@ int mesh_get_points(mesh_t* m, void* xy, int64_t cap, int64_t* n_out);
 /* Replace the per-point state (positions in the mesh's precision, point
  * classes 0 inner / 1 boundary, previous move distances as float64); host
  * pointers, any may be NULL to keep the current value.  Used to resume a
- * mesh or to start two implementations from identical states. */
+ * mesh or to start two implementations from identical states.  Positions are
+ * checked on the device after the copy: a position that is not finite or lies
+ * outside the SDF grid box returns TRIME_EINVAL (the message names the first
+ * such point) and leaves the state unchanged. */
 int mesh_set_state(mesh_t* m, const void* xy, const uint8_t* cls, const double* dprev);
 
 /* The per-point state mesh_set_state replaces, in input order, into HOST

@@ -252,6 +252,27 @@ __global__ void k_set_state(const __grid_constant__ IterArgs<T> a, int32_t s0, i
     if (dprev) a.cur.dprev[s] = (T)dprev[id];
 }
 
+// first index (into xy, in points) of a coordinate pair that is not finite
+// or lies outside the box; bad[0] must start above n
+template <typename T>
+__global__ void k_check_points(const T* xy, int32_t n, double x0, double y0, double x1, double y1, int32_t* bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = (double)xy[2 * i], y = (double)xy[2 * i + 1];
+    if (!(x >= x0 && x <= x1 && y >= y0 && y <= y1)) atomicMin(bad, i);
+}
+
+template <typename T>
+void launch_check_points(const T* xy, int32_t n, double x0, double y0, double x1, double y1, int32_t* bad,
+                         cudaStream_t st) {
+    int g = (n + kThreads - 1) / kThreads;
+    if (g > 0) k_check_points<T><<<g, kThreads, 0, st>>>(xy, n, x0, y0, x1, y1, bad);
+}
+template void launch_check_points<double>(const double*, int32_t, double, double, double, double, int32_t*,
+                                          cudaStream_t);
+template void launch_check_points<float>(const float*, int32_t, double, double, double, double, int32_t*,
+                                         cudaStream_t);
+
 template <typename T>
 void launch_set_state(const IterArgs<T>& a, int32_t s0, int32_t ns, const T* xy, const uint8_t* cls,
                       const double* dprev, cudaStream_t st) {

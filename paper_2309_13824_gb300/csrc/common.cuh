@@ -27,6 +27,8 @@ struct DevGrid {
     double x0, y0, x1, y1, dx, dy;
     const float* v;
     double idx, idy;  // 1/dx, 1/dy for the non-decision lookups of the moves
+    // x0, y0, 1/dx, 1/dy as float pairs (hi + lo) for float-float lookups
+    float fx0h, fx0l, fy0h, fy0l, fidxh, fidxl, fidyh, fidyl;
 };
 
 // Counters the device accumulates (mesh_stats fields).

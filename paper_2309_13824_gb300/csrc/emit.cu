@@ -11,6 +11,7 @@
 // evaluation with a proven error bound decides first when it is far from the
 // threshold.  Cell i records the result as bit t of vmask[i]; the triangle
 // is counted once, by its smallest-id vertex.
+#include "ff.cuh"
 #include "kernels.cuh"
 
 namespace trime {
@@ -247,22 +248,6 @@ __device__ bool valid_tri(const IterArgs<T>& a, const MeshView& V, const CellC& 
     return valid_fixed(V, t);
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ double warp_min_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 // one block per chunk of kThreads slots (one mesh in a batch)
 template <typename T, bool B>
 __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterArgs<T> a) {
@@ -270,7 +255,11 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
     if (skip_rebuild(V.ctrl, a.force)) return;
     const bool cvd_now = V.ctrl->method_param == 1 || (V.ctrl->method_param == 2 && V.ctrl->switched);
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[9] = {0, 0, 0, 0, 0, 180.0, 0, 0, 0};
+    // per-thread sums: triangle count, sum sqrt(alpha), sum sqrt(beta), max
+    // alpha, max beta, min angle; valid-edge count and the Eq. 3 sums
+    int nt = 0, nedge = 0;
+    float q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f, q5 = 180.f;
+    ff s7{0.f, 0.f}, s8{0.f, 0.f};
     if (s < a.n && (!B || s - V.soff < V.n)) {
         int ne = a.ring_n[s];
         int lab[kRingCap];
@@ -299,7 +288,6 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
             cc.ty = (float)((yd - V.sdf.y0) * V.sdf.idy);
             cc.idx = (float)V.sdf.idx;
             cc.idy = (float)V.sdf.idy;
-            float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f, q5 = 180.f;
             Nbr first = load_nbr(a, lab[0], pi4, xi, yi);
             Nbr cur = first;
             for (int t = 0; t < ne; t++) {
@@ -322,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
                         float cs = (p * p + q * q - lmin * lmin) / (2.0f * p * q);
                         cs = fminf(1.0f, fmaxf(-1.0f, cs));
                         float beta = lmax / lmin;
-                        q0 += 1.0f;
+                        nt++;
                         q1 += sqrtf(alpha);
                         q2 += sqrtf(beta);
                         q3 = fmaxf(q3, alpha);
@@ -332,45 +320,67 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
                 }
                 cur = nxt;
             }
-            acc[0] = q0;
-            acc[1] = q1;
-            acc[2] = q2;
-            acc[3] = q3;
-            acc[4] = q4;
-            acc[5] = q5;
             // valid edges (Eq. 3 sums), counted by the smaller id; they set the
             // DistMesh rest lengths, so they stay in T precision unless this
-            // iteration's move is CVD (then fac_mu only feeds a statistic)
+            // iteration's move is CVD (then fac_mu only feeds a statistic).  In
+            // FP64 mode the squared lengths are summed in double and the sizing
+            // is evaluated and summed in float-float.
+            double s7d = 0.0;
+            const ff fxi{pi4.x, pi4.y}, fyi{pi4.z, pi4.w};
             for (int t = 0; t < ne; t++) {
                 int j = lab[t];
                 if (j < 0) continue;
                 int tp = t == 0 ? ne - 1 : t - 1;
                 if (!((vm >> t) & 1ull) && !((vm >> tp) & 1ull)) continue;
                 if (!(idi < a.srt.id[j])) continue;
-                acc[6] += 1.0;
+                nedge++;
+                float4 pj4 = a.pf[j];
                 if (cvd_now) {
-                    float4 pj4 = a.pf[j];
                     float ex = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y), ey = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
                     float muf = bilin<float>(V.siz, pi4.x + 0.5f * ex, pi4.z + 0.5f * ey);
-                    acc[7] += (double)(ex * ex + ey * ey);
-                    acc[8] += (double)(muf * muf);
+                    s7 = ff_add_f(s7, ex * ex + ey * ey);
+                    s8 = ff_add_f(s8, muf * muf);
                     continue;
                 }
                 T xj = a.srt.x[j], yj = a.srt.y[j];
                 T dx = xj - xi, dy = yj - yi;
-                T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
-                acc[7] += (double)(dx * dx + dy * dy);
-                acc[8] += (double)(mu * mu);
+                if (sizeof(T) == 8) {
+                    s7d += (double)(dx * dx + dy * dy);
+                    ff m = bilin_ff(V.siz, ff_scale2(ff_add(fxi, ff{pj4.x, pj4.y}), 0.5f),
+                                    ff_scale2(ff_add(fyi, ff{pj4.z, pj4.w}), 0.5f));
+                    s8 = ff_add(s8, ff_mul(m, m));
+                } else {
+                    T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
+                    s7 = ff_add_f(s7, (float)(dx * dx + dy * dy));
+                    s8 = ff_add_f(s8, (float)(mu * mu));
+                }
             }
+            if (sizeof(T) == 8 && s7d != 0.0) s7 = ff_add(s7, ff_from_d(s7d));
         }
         a.vmask[s] = vm;
     }
-    // block reduction into one partial
+    // block reduction into one partial: integers and float extrema within the
+    // warp, sums in float-float, then double across the warps
+    nt = __reduce_add_sync(0xffffffffu, nt);
+    nedge = __reduce_add_sync(0xffffffffu, nedge);
+    ff w1 = warp_sum_ff(ff{q1, 0.f}), w2 = warp_sum_ff(ff{q2, 0.f});
+    s7 = warp_sum_ff(s7);
+    s8 = warp_sum_ff(s8);
+    q3 = warp_max(q3);
+    q4 = warp_max(q4);
+    q5 = -warp_max(-q5);
     __shared__ double sh[kThreads / 32][9];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int q = 0; q < 9; q++) {
-        double v = (q == 3 || q == 4) ? warp_max_d(acc[q]) : (q == 5 ? warp_min_d(acc[q]) : warp_sum_d(acc[q]));
-        if (lane == 0) sh[w][q] = v;
+    if (lane == 0) {
+        sh[w][0] = (double)nt;
+        sh[w][1] = ff_to_d(w1);
+        sh[w][2] = ff_to_d(w2);
+        sh[w][3] = (double)q3;
+        sh[w][4] = (double)q4;
+        sh[w][5] = (double)q5;
+        sh[w][6] = (double)nedge;
+        sh[w][7] = ff_to_d(s7);
+        sh[w][8] = ff_to_d(s8);
     }
     __syncthreads();
     if (threadIdx.x < 9) {
@@ -399,7 +409,8 @@ __global__ void __launch_bounds__(kThreads) k_dm_keep(const __grid_constant__ It
     const MeshView& V = mesh_of<B>(a, blockIdx.x * kThreads);
     if (V.ctrl->terminated || V.ctrl->retri) return;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[3] = {0, 0, 0};
+    int nedge = 0;
+    ff s7{0.f, 0.f}, s8{0.f, 0.f};
     if (s < a.n && (!B || s - V.soff < V.n)) {
         T xi = a.cur.x[s], yi = a.cur.y[s];
         a.wrk.x[s] = xi;
@@ -409,6 +420,14 @@ __global__ void __launch_bounds__(kThreads) k_dm_keep(const __grid_constant__ It
         int ne = a.ring_n[s];
         uint64_t vm = a.vmask[s];
         int idi = a.srt.id[s];
+        // FP64 mode: squared lengths in double, the sizing in float-float
+        // (as in the emit kernel, from positions split into float pairs)
+        double s7d = 0.0;
+        ff fxi{0.f, 0.f}, fyi{0.f, 0.f};
+        if (sizeof(T) == 8) {
+            fxi = ff_from_d((double)xi);
+            fyi = ff_from_d((double)yi);
+        }
         for (int t = 0; t < ne; t++) {
             int j = a.ring[(size_t)s * kRingCap + t];
             if (j < 0) continue;
@@ -417,17 +436,29 @@ __global__ void __launch_bounds__(kThreads) k_dm_keep(const __grid_constant__ It
             if (!(idi < a.srt.id[j])) continue;
             T xj = a.cur.x[j], yj = a.cur.y[j];
             T dx = xj - xi, dy = yj - yi;
-            T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
-            acc[0] += 1.0;
-            acc[1] += (double)(dx * dx + dy * dy);
-            acc[2] += (double)(mu * mu);
+            nedge++;
+            if (sizeof(T) == 8) {
+                s7d += (double)(dx * dx + dy * dy);
+                ff m = bilin_ff(V.siz, ff_scale2(ff_add(fxi, ff_from_d((double)xj)), 0.5f),
+                                ff_scale2(ff_add(fyi, ff_from_d((double)yj)), 0.5f));
+                s8 = ff_add(s8, ff_mul(m, m));
+            } else {
+                T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
+                s7 = ff_add_f(s7, (float)(dx * dx + dy * dy));
+                s8 = ff_add_f(s8, (float)(mu * mu));
+            }
         }
+        if (sizeof(T) == 8 && s7d != 0.0) s7 = ff_add(s7, ff_from_d(s7d));
     }
+    nedge = __reduce_add_sync(0xffffffffu, nedge);
+    s7 = warp_sum_ff(s7);
+    s8 = warp_sum_ff(s8);
     __shared__ double sh[kThreads / 32][3];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int q = 0; q < 3; q++) {
-        double v = warp_sum_d(acc[q]);
-        if (lane == 0) sh[w][q] = v;
+    if (lane == 0) {
+        sh[w][0] = (double)nedge;
+        sh[w][1] = ff_to_d(s7);
+        sh[w][2] = ff_to_d(s8);
     }
     __syncthreads();
     if (threadIdx.x < 10) {

@@ -156,6 +156,8 @@ template <typename T> void launch_unpermute(const IterArgs<T>& a, int32_t s0, in
                                             cudaStream_t st);
 template <typename T> void launch_set_state(const IterArgs<T>& a, int32_t s0, int32_t ns, const T* xy,
                                             const uint8_t* cls, const double* dprev, cudaStream_t st);
+template <typename T> void launch_check_points(const T* xy, int32_t n, double x0, double y0, double x1, double y1,
+                                               int32_t* bad, cudaStream_t st);
 template <typename T> void launch_get_state(const IterArgs<T>& a, int32_t s0, int32_t ns, T* xy, uint8_t* cls,
                                             double* dprev, cudaStream_t st);
 void launch_predicates(const double* pts, const int32_t* ids, int32_t nq, int32_t* o_out, int32_t* c_out,

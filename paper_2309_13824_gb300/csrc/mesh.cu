@@ -112,6 +112,7 @@ struct mesh_s {
     void* akeys = nullptr;       // [2 ncap + 16] selection keys
     int32_t *ahist = nullptr, *hhist = nullptr;  // 256 device / pinned host
     int32_t *acnt = nullptr, *aoff = nullptr;    // [ncap + 1] per-owner counts and offsets by id
+    int32_t *chk = nullptr, *hchk = nullptr;     // state-check result: device / pinned host
     std::vector<void*> allocs;
 };
 
@@ -549,6 +550,14 @@ static DevGrid dev_grid(const mesh_grid2d* g, const float* dv) {
               (g->y1 - g->y0) / (double)(g->ny - 1), dv, 0.0, 0.0};
     d.idx = 1.0 / d.dx;
     d.idy = 1.0 / d.dy;
+    auto split = [](double v, float& h, float& l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+    };
+    split(d.x0, d.fx0h, d.fx0l);
+    split(d.y0, d.fy0h, d.fy0l);
+    split(d.idx, d.fidxh, d.fidxl);
+    split(d.idy, d.fidyh, d.fidyl);
     return d;
 }
 
@@ -806,6 +815,8 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->up = dalloc<UpdatePartial>(m, (size_t)nblk_cap, rc);
     m->ctrl = dalloc<DevCtrl>(m, (size_t)nparts, rc);
     m->ovf_n = dalloc<int32_t>(m, 3, rc);
+    m->chk = dalloc<int32_t>(m, 1, rc);
+    if (!rc && cudaMallocHost(&m->hchk, sizeof(int32_t)) != cudaSuccess) rc = fail(TRIME_ENOMEM, "pinned alloc");
     m->dbg = P.debug ? dalloc<double>(m, 10 * N, rc) : nullptr;
     m->tcnt = dalloc<int32_t>(m, N + 1, rc);
     m->toff = dalloc<int32_t>(m, N + 1, rc);
@@ -855,6 +866,7 @@ static void destroy(mesh_s* m) {
     for (void* p : m->allocs) cudaFree(p);
     if (m->hctrl) cudaFreeHost(m->hctrl);
     if (m->hhist) cudaFreeHost(m->hhist);
+    if (m->hchk) cudaFreeHost(m->hchk);
     if (m->ev) cudaEventDestroy(m->ev);
     if (m->st) cudaStreamDestroy(m->st);
 }
@@ -1047,19 +1059,31 @@ static int set_state(mesh_s* m, int k, const void* xy, const uint8_t* cls, const
     const Part& p = m->parts[k];
     if (p.n == 0) return TRIME_OK;
     size_t N = (size_t)p.n, T = m->prec == 0 ? sizeof(double) : sizeof(float);
-    if (xy)
-        for (size_t i = 0; i < 2 * N; i++) {
-            double v = m->prec == 0 ? ((const double*)xy)[i] : (double)((const float*)xy)[i];
-            double lo = (i & 1) ? p.dp.by0 : p.dp.bx0, hi = (i & 1) ? p.dp.by1 : p.dp.bx1;
-            if (!std::isfinite(v) || v < lo || v > hi) return fail(TRIME_EINVAL, "point outside the SDF grid box");
-        }
     int rc = sync_in(m);
     if (rc) return rc;
     // staging: xy in xybuf, cls in tcnt, dprev in tbuf (all large enough)
     char* sxy = (char*)m->xybuf;
     uint8_t* scls = (uint8_t*)m->tcnt;
     double* sdp = (double*)m->tbuf;
-    if (xy) CUDA_TRY(cudaMemcpyAsync(sxy, xy, 2 * N * T, cudaMemcpyHostToDevice, m->st));
+    if (xy) {
+        // the positions are checked on the device before anything is changed
+        CUDA_TRY(cudaMemcpyAsync(sxy, xy, 2 * N * T, cudaMemcpyHostToDevice, m->st));
+        CUDA_TRY(cudaMemsetAsync(m->chk, 0x7f, sizeof(int32_t), m->st));
+        if (m->prec == 0)
+            launch_check_points<double>((const double*)sxy, (int32_t)N, p.dp.bx0, p.dp.by0, p.dp.bx1, p.dp.by1,
+                                        m->chk, m->st);
+        else
+            launch_check_points<float>((const float*)sxy, (int32_t)N, p.dp.bx0, p.dp.by0, p.dp.bx1, p.dp.by1,
+                                       m->chk, m->st);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(m->hchk, m->chk, sizeof(int32_t), cudaMemcpyDeviceToHost, m->st));
+        CUDA_TRY(cudaStreamSynchronize(m->st));
+        if (*m->hchk < (int32_t)N) {
+            sync_out(m);
+            return fail(TRIME_EINVAL, "point " + std::to_string(*m->hchk) +
+                                          " is not finite or outside the SDF grid box");
+        }
+    }
     if (cls) CUDA_TRY(cudaMemcpyAsync(scls, cls, N, cudaMemcpyHostToDevice, m->st));
     if (dprev) CUDA_TRY(cudaMemcpyAsync(sdp, dprev, N * sizeof(double), cudaMemcpyHostToDevice, m->st));
     if (m->prec == 0)

@@ -8,6 +8,7 @@
 // grid and projects it back by sphere tracing or damped Newton (Sec. 4.3).
 // The statistics kernels finalise the quality 1/2-means (Eq. 12), fac_mu
 // (Eq. 3), the hybrid switch (Sec. 4.2) and the termination tests (Sec. 4).
+#include "ff.cuh"
 #include "kernels.cuh"
 #include "treat.cuh"
 
@@ -187,19 +188,6 @@ __device__ void cvd_centroid(const IterArgs<T>& a, const MeshView& V, int s, int
 }
 
 // ------------------------------------------------------------------ update
-__device__ __forceinline__ double blk_sum(double v, double* sh) {
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += sh[k];
-    return t;
-}
-
 // one block per chunk of kThreads slots (one mesh in a batch)
 template <typename T, bool B>
 __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ IterArgs<T> a) {
@@ -215,7 +203,8 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
     unsigned moved = 0;
     int method = V.ctrl->method_now;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double dev = 0, nedge = 0, notsmall = 0;
+    float devf = 0.f;  // size deviation summed over the owned valid edges
+    int nown = 0, notsmall = 0;
     unsigned long long nfail = 0, tcap = 0, qcap = 0;
     if (s < a.n && (!B || s - V.soff < V.n)) {
         T xi = IX[s], yi = IY[s];
@@ -239,6 +228,15 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
         // DistMesh forces on the valid edges (Eqs. 2-3); also the size deviation
         // (a float statistic; in CVD iterations it is all this loop computes)
         const float4 pi4 = a.pf[s];
+        // FP64 mode: the sizing at each edge midpoint in float-float, from the
+        // float-pair positions of the triangulation or split from the current
+        // ones (iterations that keep the triangulation)
+        ff fxi{pi4.x, pi4.y}, fyi{pi4.z, pi4.w};
+        if (sizeof(T) == 8 && keep) {
+            fxi = ff_from_d((double)xi);
+            fyi = ff_from_d((double)yi);
+        }
+        const T l0f = (T)P.fac_F * fac_mu;
         for (int t = 0; t < ne; t++) {
             int j = lab[t];
             if (j < 0) continue;
@@ -250,8 +248,8 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
                     float4 pj4 = a.pf[j];
                     float ex = ff_diff(pi4.x, pi4.y, pj4.x, pj4.y), ey = ff_diff(pi4.z, pi4.w, pj4.z, pj4.w);
                     float muf = bilin<float>(V.siz, pj4.x + 0.5f * ex, pj4.z + 0.5f * ey);
-                    dev += (double)fabsf(sqrtf(ex * ex + ey * ey) / ((float)fac_mu * muf) - 1.0f);
-                    nedge += 1.0;
+                    devf += fabsf(sqrtf(ex * ex + ey * ey) / ((float)fac_mu * muf) - 1.0f);
+                    nown++;
                 }
                 continue;
             }
@@ -260,12 +258,30 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
             T l2 = dx * dx + dy * dy;
             T r = rsqrt(l2);  // 1 / l: one reciprocal square root instead of a root and a division
             T l = l2 * r;
-            T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
-            if (owner) {
-                dev += (double)fabsf((float)l / ((float)fac_mu * (float)mu) - 1.0f);
-                nedge += 1.0;
+            T mu;
+            float muf;
+            if (sizeof(T) == 8) {
+                ff fxj, fyj;
+                if (keep) {
+                    fxj = ff_from_d((double)xj);
+                    fyj = ff_from_d((double)yj);
+                } else {
+                    float4 pj4 = a.pf[j];
+                    fxj = ff{pj4.x, pj4.y};
+                    fyj = ff{pj4.z, pj4.w};
+                }
+                ff m = bilin_ff(V.siz, ff_scale2(ff_add(fxi, fxj), 0.5f), ff_scale2(ff_add(fyi, fyj), 0.5f));
+                mu = (T)ff_to_d(m);
+                muf = m.h;
+            } else {
+                mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
+                muf = (float)mu;
             }
-            T l0 = (T)P.fac_F * fac_mu * mu;
+            if (owner) {
+                devf += fabsf((float)l / ((float)fac_mu * muf) - 1.0f);
+                nown++;
+            }
+            T l0 = l0f * mu;
             if (l < l0) {
                 T k = (T)P.k_spring;
                 T fl = k * (l0 * r - (T)1);  // f / l with f = k (l0 - l)
@@ -297,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
         }
         T mvx = fx - xi, mvy = fy - yi;
         T mv = sqrt(mvx * mvx + mvy * mvy);
-        if (ocls == PT_INNER && !(mv < (T)P.fac_end * h)) notsmall = 1.0;
+        if (ocls == PT_INNER && !(mv < (T)P.fac_end * h)) notsmall = 1;
         a.cur.x[s] = fx;
         a.cur.y[s] = fy;
         a.cur.id[s] = idi;
@@ -324,11 +340,25 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&V.ctrl->cnt.trace_cap, (unsigned long long)__popc(m));
     m = __ballot_sync(0xffffffffu, qcap != 0);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&V.ctrl->cnt.quad_cap, (unsigned long long)__popc(m));
-    __shared__ double sh[kThreads / 32];
-    double v0 = blk_sum(dev, sh);
-    double v1 = blk_sum(nedge, sh);
-    double v2 = blk_sum(notsmall, sh);
+    // block sums: the deviation in float-float and the counts as integers
+    // within each warp, in double across the warps
+    ff dv = warp_sum_ff(ff{devf, 0.f});
+    int ne_w = __reduce_add_sync(0xffffffffu, nown), ns_w = __reduce_or_sync(0xffffffffu, notsmall);
+    __shared__ double sh[3][kThreads / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][w] = ff_to_d(dv);
+        sh[1][w] = (double)ne_w;
+        sh[2][w] = (double)ns_w;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double v0 = 0, v1 = 0, v2 = 0;
+        for (int k = 0; k < kThreads / 32; k++) {
+            v0 += sh[0][k];
+            v1 += sh[1][k];
+            v2 += sh[2][k];
+        }
         a.up[blockIdx.x].size_dev = v0;
         a.up[blockIdx.x].n_edge = v1;
         a.up[blockIdx.x].not_small = v2;

@@ -169,6 +169,22 @@ def test_cvd_and_dm_after_several_steps():
         gm2.set_state(om2.points(), om2.classes(), om2.dprev())
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_state_rejects_bad_positions_and_keeps_the_state(precision):
+    import paper_2309_13824_gb300 as g
+
+    gm, om = make_pair(disk_small(n=3001, seed=5), precision=precision, method=0)
+    before = gm.points().copy()
+    for bad in (np.nan, np.inf, 5.0):
+        p = before.copy()
+        p[1234, 1] = bad
+        with pytest.raises(g.MeshError, match="point 1234 "):
+            gm.set_state(p)
+        assert np.array_equal(gm.points(), before)
+    gm.set_state(before)
+    assert np.array_equal(gm.points(), before)
+
+
 def test_hybrid_switch_and_quality_trajectory():
     gm, om = make_pair(disk_small(n=4001, seed=2), precision=0, method=2)
     for k in range(12):
