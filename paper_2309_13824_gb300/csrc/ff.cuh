@@ -53,6 +53,26 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     return fast_two_sum(p, e);
 }
 
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+    float p = __fmul_rn(a.h, b);
+    float e = fmaf(a.h, b, -p);
+    e = fmaf(a.l, b, e);
+    return fast_two_sum(p, e);
+}
+
+// a / b: a float quotient and one correction from the float-float remainder
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    float rb = __frcp_rn(b.h);
+    float q1 = __fmul_rn(a.h, rb);
+    ff r = ff_sub(a, ff_mul_f(b, q1));
+    float q2 = __fmul_rn(r.h, rb);
+    ff q = fast_two_sum(q1, q2);
+    r = ff_sub(a, ff_mul(b, q));
+    return ff_add_f(q, __fmul_rn(r.h, rb));
+}
+
+__device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+
 __device__ __forceinline__ ff ff_scale2(ff a, float p2) { return {__fmul_rn(a.h, p2), __fmul_rn(a.l, p2)}; }
 
 __device__ __forceinline__ ff ff_from_d(double d) {

@@ -105,6 +105,53 @@ __device__ void level_sum(const MeshView& V, T gx, T gy, T v1x, T v1y, T v2x, T 
     }
 }
 
+// The same tree in float-float (FP64 mode): vertices relative to the
+// generator, the generator as a float pair; the longest edge, the leaf areas,
+// centroids, sizing and weights all carry about 48 bits.
+__device__ void level_sum_ff(const MeshView& V, ff gx, ff gy, ff v1x, ff v1y, ff v2x, ff v2y, int depth, ff& W,
+                             ff& WX, ff& WY) {
+    const ff third{__int_as_float(0x3EAAAAAB), __int_as_float(0xB22AAAAB)};  // 1/3 to 2^-50
+    ff st[9][6];
+    int sd[9];
+    const ff z{0.f, 0.f};
+    st[0][0] = z; st[0][1] = z; st[0][2] = v1x; st[0][3] = v1y; st[0][4] = v2x; st[0][5] = v2y;
+    sd[0] = depth;
+    int sp = 1;
+    while (sp > 0) {
+        sp--;
+        ff q0x = st[sp][0], q0y = st[sp][1], q1x = st[sp][2], q1y = st[sp][3], q2x = st[sp][4], q2y = st[sp][5];
+        int d = sd[sp];
+        if (d == 0) {
+            ff A = ff_scale2(ff_sub(ff_mul(ff_sub(q1x, q0x), ff_sub(q2y, q0y)),
+                                    ff_mul(ff_sub(q1y, q0y), ff_sub(q2x, q0x))), 0.5f);
+            ff cx = ff_mul(ff_add(ff_add(q0x, q1x), q2x), third);
+            ff cy = ff_mul(ff_add(ff_add(q0y, q1y), q2y), third);
+            ff mu = bilin_ff(V.siz, ff_add(gx, cx), ff_add(gy, cy));
+            ff w = ff_div(A, ff_mul(mu, mu));
+            W = ff_add(W, w);
+            WX = ff_add(WX, ff_mul(w, cx));
+            WY = ff_add(WY, ff_mul(w, cy));
+            continue;
+        }
+        ff e0x = ff_sub(q1x, q0x), e0y = ff_sub(q1y, q0y);
+        ff e1x = ff_sub(q2x, q1x), e1y = ff_sub(q2y, q1y);
+        ff e2x = ff_sub(q0x, q2x), e2y = ff_sub(q0y, q2y);
+        ff L01 = ff_add(ff_mul(e0x, e0x), ff_mul(e0y, e0y));
+        ff L12 = ff_add(ff_mul(e1x, e1x), ff_mul(e1y, e1y));
+        ff L20 = ff_add(ff_mul(e2x, e2x), ff_mul(e2y, e2y));
+        ff ax = q0x, ay = q0y, bx = q1x, by = q1y, cx = q2x, cy = q2y, Lm = L01;
+        if (ff_gt(L12, Lm)) { ax = q1x; ay = q1y; bx = q2x; by = q2y; cx = q0x; cy = q0y; Lm = L12; }
+        if (ff_gt(L20, Lm)) { ax = q2x; ay = q2y; bx = q0x; by = q0y; cx = q1x; cy = q1y; }
+        ff mx = ff_scale2(ff_add(ax, bx), 0.5f), my = ff_scale2(ff_add(ay, by), 0.5f);
+        st[sp][0] = mx; st[sp][1] = my; st[sp][2] = bx; st[sp][3] = by; st[sp][4] = cx; st[sp][5] = cy;
+        sd[sp] = d - 1;
+        sp++;
+        st[sp][0] = ax; st[sp][1] = ay; st[sp][2] = mx; st[sp][3] = my; st[sp][4] = cx; st[sp][5] = cy;
+        sd[sp] = d - 1;
+        sp++;
+    }
+}
+
 template <typename T>
 __device__ void cvd_centroid(const IterArgs<T>& a, const MeshView& V, int s, int ne, const int* lab, T xi, T yi, T h,
                              T dprev, T& cx, T& cy, int& level, bool& capped) {
@@ -162,8 +209,41 @@ __device__ void cvd_centroid(const IterArgs<T>& a, const MeshView& V, int s, int
     }
     if (!(A > 0)) return;
     T E = sqrt(A) * fmax(dprev / h, (T)P.fac_end);
-    T px = 0, py = 0;
     int Lmax = P.quad_max_level;
+    if (sizeof(T) == 8) {
+        // FP64 mode: the quadrature in float-float (the vertices above stay FP64)
+        const float4 pi4 = a.pf[s];
+        const ff gx{pi4.x, pi4.y}, gy{pi4.z, pi4.w};
+        ff fvx[kPolyCap], fvy[kPolyCap];
+        for (int t = 0; t < m; t++) {
+            fvx[t] = ff_from_d((double)vx[t]);
+            fvy[t] = ff_from_d((double)vy[t]);
+        }
+        ff E2 = ff_from_d((double)(E * E));
+        ff fpx{0.f, 0.f}, fpy{0.f, 0.f};
+        for (int k = 1; k <= Lmax; k++) {
+            ff W{0.f, 0.f}, WX{0.f, 0.f}, WY{0.f, 0.f};
+            for (int t = 0; t < m; t++) {
+                int u = t + 1 == m ? 0 : t + 1;
+                level_sum_ff(V, gx, gy, fvx[t], fvy[t], fvx[u], fvy[u], k - 1, W, WX, WY);
+            }
+            if (!(W.h > 0.f)) return;
+            ff ccx = ff_div(WX, W), ccy = ff_div(WY, W);
+            ff dx = ff_sub(ccx, fpx), dy = ff_sub(ccy, fpy);
+            bool conv = ff_gt(E2, ff_add(ff_mul(dx, dx), ff_mul(dy, dy)));
+            if (conv || k == Lmax) {
+                cx = xi + (T)ff_to_d(ccx);
+                cy = yi + (T)ff_to_d(ccy);
+                level = k;
+                capped = !conv;
+                return;
+            }
+            fpx = ccx;
+            fpy = ccy;
+        }
+        return;
+    }
+    T px = 0, py = 0;
     for (int k = 1; k <= Lmax; k++) {
         T W = 0, WX = 0, WY = 0;
         for (int t = 0; t < m; t++) {
@@ -188,11 +268,14 @@ __device__ void cvd_centroid(const IterArgs<T>& a, const MeshView& V, int s, int
 }
 
 // ------------------------------------------------------------------ update
-// one block per chunk of kThreads slots (one mesh in a batch)
-template <typename T, bool B>
+// one block per chunk of kThreads slots (one mesh in a batch).  MV selects the
+// move the variant computes (0 DistMesh, 1 CVD); both variants are launched
+// and the one that does not match the mesh's move of this iteration returns at
+// once, so each is compiled (and register-allocated) for its own move.
+template <typename T, bool B, int MV>
 __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ IterArgs<T> a) {
     const MeshView& V = mesh_of<B>(a, blockIdx.x * kThreads);
-    if (V.ctrl->terminated) return;
+    if (V.ctrl->terminated || (V.ctrl->method_now != 0) != (MV != 0)) return;
     const DevParams& P = V.P;
     // a DistMesh iteration that keeps the last triangulation moves the current
     // state (copied to wrk); otherwise the state sorted at the triangulation
@@ -201,7 +284,6 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
     const T* IY = keep ? a.wrk.y : a.srt.y;
     const bool track = P.fac_retria > 0.0 && V.ctrl->method_param == 0;
     unsigned moved = 0;
-    int method = V.ctrl->method_now;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     float devf = 0.f;  // size deviation summed over the owned valid edges
     int nown = 0, notsmall = 0;
@@ -243,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
             int tp = t == 0 ? ne - 1 : t - 1;
             if (!((vm >> t) & 1ull) && !((vm >> tp) & 1ull)) continue;
             bool owner = idi < a.srt.id[j];
-            if (method != 0) {
+            if constexpr (MV != 0) {
                 if (owner) {
                     float4 pj4 = a.pf[j];
                     float ex = ff_diff(pi4.x, pi4.y, pj4.x, pj4.y), ey = ff_diff(pi4.z, pi4.w, pj4.z, pj4.w);
@@ -292,7 +374,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
         }
         T pnx, pny, cx = xi, cy = yi;
         int qlv = 0;
-        if (method == 0) {
+        if constexpr (MV == 0) {
             pnx = xi + (T)P.dt * Fx;  // forward Euler (Eq. 5)
             pny = yi + (T)P.dt * Fy;
         } else {
@@ -367,8 +449,13 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
 
 template <typename T>
 void launch_update(const IterArgs<T>& a, int nblocks, cudaStream_t st) {
-    if (a.Vs) k_update<T, true><<<nblocks, kThreads, 0, st>>>(a);
-    else k_update<T, false><<<nblocks, kThreads, 0, st>>>(a);
+    if (a.Vs) {
+        k_update<T, true, 0><<<nblocks, kThreads, 0, st>>>(a);
+        k_update<T, true, 1><<<nblocks, kThreads, 0, st>>>(a);
+    } else {
+        k_update<T, false, 0><<<nblocks, kThreads, 0, st>>>(a);
+        k_update<T, false, 1><<<nblocks, kThreads, 0, st>>>(a);
+    }
 }
 template void launch_update<double>(const IterArgs<double>&, int, cudaStream_t);
 template void launch_update<float>(const IterArgs<float>&, int, cudaStream_t);
