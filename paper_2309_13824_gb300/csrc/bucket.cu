@@ -168,8 +168,11 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const __grid_constant__ It
     a.cell[d] = gj * ncx + gi;
     // per-slot float data read by the cell kernels (computed once per point)
     float xh = (float)x, yh = (float)y;
-    float xl = (float)(xd - (double)xh), yl = (float)(yd - (double)yh);
+    double rx = xd - (double)xh, ry = yd - (double)yh;  // exact
+    float xl = (float)rx, yl = (float)ry;
     a.pf[d] = make_float4(xh, xl, yh, yl);
+    // the remainders below xlo, ylo have at most 5 significant bits: exact
+    a.pf3[d] = make_float2((float)(rx - (double)xl), (float)(ry - (double)yl));
     a.pS[d] = (float)(V.P.fac_voro_bound * V.gh[gj * ncx + gi]);
 }
 

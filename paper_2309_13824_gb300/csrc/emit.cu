@@ -323,10 +323,10 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
             // valid edges (Eq. 3 sums), counted by the smaller id; they set the
             // DistMesh rest lengths, so they stay in T precision unless this
             // iteration's move is CVD (then fac_mu only feeds a statistic).  In
-            // FP64 mode the squared lengths are summed in double and the sizing
-            // is evaluated and summed in float-float.
-            double s7d = 0.0;
+            // FP64 mode both sums run in float-float, the edge vectors exact
+            // from the three-float positions.
             const ff fxi{pi4.x, pi4.y}, fyi{pi4.z, pi4.w};
+            const float2 pi3 = sizeof(T) == 8 ? a.pf3[s] : make_float2(0.f, 0.f);
             for (int t = 0; t < ne; t++) {
                 int j = lab[t];
                 if (j < 0) continue;
@@ -342,20 +342,22 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ IterA
                     s8 = ff_add_f(s8, muf * muf);
                     continue;
                 }
-                T xj = a.srt.x[j], yj = a.srt.y[j];
-                T dx = xj - xi, dy = yj - yi;
                 if (sizeof(T) == 8) {
-                    s7d += (double)(dx * dx + dy * dy);
+                    float2 pj3 = a.pf3[j];
+                    ff ex = ff_diff3(pj4.x, pj4.y, pj3.x, pi4.x, pi4.y, pi3.x);
+                    ff ey = ff_diff3(pj4.z, pj4.w, pj3.y, pi4.z, pi4.w, pi3.y);
+                    s7 = ff_add(s7, ff_add(ff_mul(ex, ex), ff_mul(ey, ey)));
                     ff m = bilin_ff(V.siz, ff_scale2(ff_add(fxi, ff{pj4.x, pj4.y}), 0.5f),
                                     ff_scale2(ff_add(fyi, ff{pj4.z, pj4.w}), 0.5f));
                     s8 = ff_add(s8, ff_mul(m, m));
                 } else {
+                    T xj = a.srt.x[j], yj = a.srt.y[j];
+                    T dx = xj - xi, dy = yj - yi;
                     T mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
                     s7 = ff_add_f(s7, (float)(dx * dx + dy * dy));
                     s8 = ff_add_f(s8, (float)(mu * mu));
                 }
             }
-            if (sizeof(T) == 8 && s7d != 0.0) s7 = ff_add(s7, ff_from_d(s7d));
         }
         a.vmask[s] = vm;
     }

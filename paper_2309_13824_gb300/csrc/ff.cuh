@@ -81,6 +81,25 @@ __device__ __forceinline__ ff ff_from_d(double d) {
 }
 __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.h + (double)a.l; }
 
+// a - b for values held exactly as three floats (h + l + t); the result
+// rounded once to float-float
+__device__ __forceinline__ ff ff_diff3(float ah, float al, float at, float bh, float bl, float bt) {
+    ff s = two_sum(ah, -bh), t = two_sum(al, -bl);
+    return ff_add_f(ff_add(s, t), __fsub_rn(at, bt));
+}
+
+// 1 / sqrt(a), a > 0: float estimate and two Newton corrections in float-float
+__device__ __forceinline__ ff ff_rsqrt(ff a) {
+    float r0 = rsqrtf(a.h);
+    ff r{r0, 0.f};
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        ff e = ff_add_f(ff_neg(ff_mul(a, ff_mul(r, r))), 1.0f);  // 1 - a r^2, small
+        r = ff_add_f(r, __fmul_rn(__fmul_rn(0.5f, r.h), e.h));
+    }
+    return r;
+}
+
 __device__ __forceinline__ bool ff_lt0(ff a) { return a.h < 0.f || (a.h == 0.f && a.l < 0.f); }
 __device__ __forceinline__ bool ff_ge1(ff a) { return a.h > 1.f || (a.h == 1.f && a.l >= 0.f); }
 

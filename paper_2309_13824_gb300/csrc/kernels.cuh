@@ -80,6 +80,7 @@ struct IterArgs {
     int32_t* ovf2_list; // [n] cells whose 32-lane clipping ran out of lanes (serial pass)
     int32_t* ovf3_list; // [n] cells with more edges than a ring row (big-cell pass on request)
     float4* pf;        // [n] sorted positions as float pairs (xhi, xlo, yhi, ylo)
+    float2* pf3;       // [n] third parts: x = xhi + xlo + x3 exactly (FP64 positions)
     float* pS;         // [n] octagon span S = fac_voro_bound * h of each sorted slot
 };
 

@@ -102,6 +102,7 @@ struct mesh_s {
     int32_t *tcnt = nullptr, *toff = nullptr, *tbuf = nullptr;
     int32_t* ovf_list = nullptr;
     float4* pf = nullptr;
+    float2* pf3 = nullptr;
     float* pS = nullptr;
     void* xybuf = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -382,6 +383,7 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.ovf2_list = m->ovf_list + std::max<int64_t>(m->ncap, m->nslots);
     a.ovf3_list = m->batched ? nullptr : m->ovf_list + 2 * std::max<int64_t>(m->ncap, m->nslots);
     a.pf = m->pf;
+    a.pf3 = m->pf3;
     a.pS = m->pS;
     return a;
 }
@@ -824,6 +826,7 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
     m->ovf_list = dalloc<int32_t>(m, 3 * N, rc);
     m->pf = dalloc<float4>(m, N, rc);
+    m->pf3 = dalloc<float2>(m, N, rc);
     m->pS = dalloc<float>(m, N, rc);
     if (m->batched) {
         m->dviews = dalloc<MeshView>(m, (size_t)nparts, rc);

@@ -319,6 +319,13 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
             fyi = ff_from_d((double)yi);
         }
         const T l0f = (T)P.fac_F * fac_mu;
+        // FP64 mode with the triangulation's positions: the whole spring sum in
+        // float-float, from positions held exactly as three floats
+        const bool ffs = sizeof(T) == 8 && !keep;
+        const float2 pi3 = ffs ? a.pf3[s] : make_float2(0.f, 0.f);
+        const ff l0ff = ffs ? ff_from_d((double)l0f) : ff{0.f, 0.f};
+        const ff kff = ffs ? ff_from_d(P.k_spring) : ff{0.f, 0.f};
+        ff FxF{0.f, 0.f}, FyF{0.f, 0.f}, fsF{0.f, 0.f};
         for (int t = 0; t < ne; t++) {
             int j = lab[t];
             if (j < 0) continue;
@@ -332,6 +339,29 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
                     float muf = bilin<float>(V.siz, pj4.x + 0.5f * ex, pj4.z + 0.5f * ey);
                     devf += fabsf(sqrtf(ex * ex + ey * ey) / ((float)fac_mu * muf) - 1.0f);
                     nown++;
+                }
+                continue;
+            }
+            if (ffs) {
+                float4 pj4 = a.pf[j];
+                float2 pj3 = a.pf3[j];
+                ff dx = ff_diff3(pi4.x, pi4.y, pi3.x, pj4.x, pj4.y, pj3.x);
+                ff dy = ff_diff3(pi4.z, pi4.w, pi3.y, pj4.z, pj4.w, pj3.y);
+                ff l2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
+                ff r = ff_rsqrt(l2);
+                ff l = ff_mul(l2, r);
+                ff mu = bilin_ff(V.siz, ff_scale2(ff_add(fxi, ff{pj4.x, pj4.y}), 0.5f),
+                                 ff_scale2(ff_add(fyi, ff{pj4.z, pj4.w}), 0.5f));
+                if (owner) {
+                    devf += fabsf(l.h / ((float)fac_mu * mu.h) - 1.0f);
+                    nown++;
+                }
+                ff l0 = ff_mul(l0ff, mu);
+                if (ff_gt(l0, l)) {
+                    ff fl = ff_mul(kff, ff_add_f(ff_mul(l0, r), -1.0f));  // f / l with f = k (l0 - l)
+                    FxF = ff_add(FxF, ff_mul(fl, dx));
+                    FyF = ff_add(FyF, ff_mul(fl, dy));
+                    fsF = ff_add(fsF, ff_mul(kff, ff_sub(l0, l)));
                 }
                 continue;
             }
@@ -371,6 +401,11 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
                 Fy += fl * dy;
                 fs += k * (l0 - l);
             }
+        }
+        if (ffs) {
+            Fx = (T)ff_to_d(FxF);
+            Fy = (T)ff_to_d(FyF);
+            fs = (T)ff_to_d(fsF);
         }
         T pnx, pny, cx = xi, cy = yi;
         int qlv = 0;
