@@ -711,7 +711,7 @@ def main():
                            "l2": "flushed before every timed step (256 MB write)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 15 * args.steps,  # kernels in the iteration graph
+                "gpu_launches": 16 * args.steps,  # kernels in the iteration graph
                 "last_step": {"method": st["method"], "switched": st["switched"], "n_tri": st["n_tri"],
                               "half_mean_alpha": st["half_mean_alpha"]}}
         line.update(extras)

@@ -110,7 +110,7 @@ typedef struct {
     int64_t vor_picks;         /* candidates applied to a cell                            */
     int64_t vor_cuts;          /* applications that changed a cell                        */
     int64_t vor_rings;         /* bucket rings scanned (summed over cells)                */
-    int64_t vor_wide;          /* cells redone with 32 lanes                              */
+    int64_t vor_wide;          /* cells queued for a wider Voronoi pass                  */
     int64_t triangulations;    /* iterations of the call that re-triangulated             */
     int64_t added;             /* points added by the call (Sec. 3.6)                     */
     int64_t n_points;          /* N_current after the call                                */
@@ -338,9 +338,10 @@ int mesh_set_quality_target(mesh_t* m, double min_angle_deg);
 
 /* Tiling of the iteration: size the bucket grid for n_opt points per bucket
  * (> 0; the default is mesh_params.N_opt) and clip each Voronoi cell with
- * `lanes` = 16 (two cells per warp, cells needing more than 16 edges redone
- * with 32) or 32 lanes (one cell per warp).  The results do not depend on
- * either choice, only the speed does.  Re-captures the iteration graph;
+ * `lanes` = 8 (four cells per warp; cells needing more than 8 edges at some
+ * step redone with 16, and from there with 32 lanes), 16 (two cells per warp,
+ * then 32) or 32 lanes (one cell per warp); the default is 8.  The results do
+ * not depend on either choice, only the speed does.  Re-captures the iteration graph;
  * synchronises.  Errors: TRIME_EINVAL, TRIME_ENOMEM, TRIME_ECUDA. */
 int mesh_set_tuning(mesh_t* m, double n_opt, int32_t lanes);
 
@@ -469,13 +470,13 @@ typedef struct mesh_batch_s mesh_batch_t;
 /* What mesh_batch_init's autotuner chose and what it measured. */
 typedef struct {
     double n_opt;             /* points per bucket the bucket grids are sized for     */
-    int32_t lanes;            /* Voronoi lanes per cell: 16 (two cells per warp) or 32 */
+    int32_t lanes;            /* Voronoi lanes per cell of the first pass: 8, 16 or 32 */
     int32_t n_candidates;     /* candidates timed (0 without autotuning)              */
     int64_t n_slots;          /* device slots: the meshes' points plus padding        */
     int64_t n_buckets;        /* buckets of all meshes, one pad bucket per mesh added */
-    double cand_n_opt[8];
-    int32_t cand_lanes[8];
-    double cand_ms[8];        /* device time of one rebuild (a1..a4) per candidate    */
+    double cand_n_opt[12];
+    int32_t cand_lanes[12];
+    double cand_ms[12];       /* device time of one rebuild (a1..a4) per candidate    */
 } mesh_tuning;
 
 /* Create a batch of n_meshes (1 .. 2^20) meshes on the current device.
@@ -483,9 +484,9 @@ typedef struct {
  *  HOST point arrays (precision as p->precision); ns: n_meshes point counts
  *  (>= 0; total padded size <= 2^30).  One parameter set p (NULL: defaults)
  *  serves every mesh.  autotune != 0: time one rebuild per candidate of
- *  (points per bucket in {2/3, 1, 3/2} x p->N_opt) x (16 or 32 Voronoi lanes
- *  per cell) on these inputs and keep the fastest (the triangles do not
- *  depend on the choice); autotune == 0 uses p->N_opt and 16 lanes.  Errors as
+ *  (points per bucket in {2/3, 1, 3/2} x p->N_opt) x (8, 16 or 32 Voronoi
+ *  lanes per cell) on these inputs and keep the fastest (the triangles do not
+ *  depend on the choice); autotune == 0 uses p->N_opt and 8 lanes.  Errors as
  *  mesh_init; a message names the offending mesh.  Point addition is not
  *  available in a batch (p->n_total above a mesh's n: TRIME_EINVAL). */
 int mesh_batch_init(mesh_batch_t** out, int32_t n_meshes, const mesh_grid2d* sdfs, const mesh_grid2d* sizings,

@@ -65,8 +65,8 @@ class mesh_stats(C.Structure):
 
 class mesh_tuning(C.Structure):
     _fields_ = [("n_opt", C.c_double), ("lanes", C.c_int32), ("n_candidates", C.c_int32),
-                ("n_slots", C.c_int64), ("n_buckets", C.c_int64), ("cand_n_opt", C.c_double * 8),
-                ("cand_lanes", C.c_int32 * 8), ("cand_ms", C.c_double * 8)]
+                ("n_slots", C.c_int64), ("n_buckets", C.c_int64), ("cand_n_opt", C.c_double * 12),
+                ("cand_lanes", C.c_int32 * 12), ("cand_ms", C.c_double * 12)]
 
 
 # every symbol include/trime.h declares
@@ -449,7 +449,7 @@ class Mesh:
                                     dp.ctypes.data_as(C.c_void_p)))
         return xy, cls, dp
 
-    def set_tuning(self, n_opt: float, lanes: int = 16):
+    def set_tuning(self, n_opt: float, lanes: int = 8):
         _check(lib().mesh_set_tuning(self._h, n_opt, lanes))
 
     def medial_points(self):
@@ -572,7 +572,7 @@ class MeshBatch:
         _check(lib().mesh_batch_profile_step(self._h, n_iters, ms.ctypes.data_as(C.c_void_p)))
         return dict(zip(["bucket", "voronoi", "emit", "stats", "update", "post", "total"], ms))
 
-    def set_tuning(self, n_opt: float, lanes: int = 16):
+    def set_tuning(self, n_opt: float, lanes: int = 8):
         _check(lib().mesh_batch_set_tuning(self._h, n_opt, lanes))
 
     def set_quality_target(self, min_angle_deg: float, mesh: int = -1):

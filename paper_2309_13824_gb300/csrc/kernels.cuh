@@ -58,7 +58,7 @@ struct IterArgs {
     MeshView V;        // the mesh of single-mesh launches
     const MeshView* Vs;     // [nmesh] per-mesh views of batched launches
     const int32_t* cmesh;   // [n / kChunk] mesh of each chunk
-    int32_t* ovf_n;    // [3] cells queued for the 32-lane, the serial and the big-cell Voronoi pass
+    int32_t* ovf_n;    // [4] cells queued for the 32-lane, the serial, the big-cell and the 16-lane Voronoi pass
     State<T> cur, srt;
     State<T> wrk;      // the positions a DistMesh iteration without re-triangulation moves (slot order)
     int32_t* cell;     // [n] geometry cell of each sorted slot (fixed formula)
@@ -76,6 +76,7 @@ struct IterArgs {
     EmitPartial* ep;   // [n / kThreads] one per block of the emit kernel
     UpdatePartial* up;
     double* dbg;       // [8][n] by original id, written when P.debug
+    int32_t* ovf0_list; // [n] cells whose 8-lane clipping ran out of lanes
     int32_t* ovf_list; // [n] cells whose 16-lane clipping ran out of lanes
     int32_t* ovf2_list; // [n] cells whose 32-lane clipping ran out of lanes (serial pass)
     int32_t* ovf3_list; // [n] cells with more edges than a ring row (big-cell pass on request)

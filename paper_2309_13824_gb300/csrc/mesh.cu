@@ -72,7 +72,7 @@ struct mesh_s {
     std::vector<Part> parts;
     int nbtot = 0;               // buckets in use (pad buckets included)
     int nbcap = 0;               // buckets allocated
-    int lanes = 16;              // Voronoi lanes per cell
+    int lanes = 8;               // Voronoi lanes per cell of the first pass
     double nopt = 3.3;           // points per bucket the grids are sized for
     std::vector<TuneCand> tune;  // autotuning record
     cudaStream_t user = nullptr, st = nullptr;
@@ -382,6 +382,7 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.ovf_list = m->ovf_list;
     a.ovf2_list = m->ovf_list + std::max<int64_t>(m->ncap, m->nslots);
     a.ovf3_list = m->batched ? nullptr : m->ovf_list + 2 * std::max<int64_t>(m->ncap, m->nslots);
+    a.ovf0_list = m->ovf_list + 3 * std::max<int64_t>(m->ncap, m->nslots);
     a.pf = m->pf;
     a.pf3 = m->pf3;
     a.pS = m->pS;
@@ -686,7 +687,7 @@ static int autotune(mesh_s* m, const std::vector<double>& nopts) {
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    const int lanes_c[2] = {16, 32};
+    const int lanes_c[3] = {8, 16, 32};
     TuneCand best{m->nopt, m->lanes, 1e300};
     m->tune.clear();
     int rc = 0;
@@ -816,7 +817,7 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->ep = dalloc<EmitPartial>(m, (size_t)nblk_cap, rc);
     m->up = dalloc<UpdatePartial>(m, (size_t)nblk_cap, rc);
     m->ctrl = dalloc<DevCtrl>(m, (size_t)nparts, rc);
-    m->ovf_n = dalloc<int32_t>(m, 3, rc);
+    m->ovf_n = dalloc<int32_t>(m, 4, rc);
     m->chk = dalloc<int32_t>(m, 1, rc);
     if (!rc && cudaMallocHost(&m->hchk, sizeof(int32_t)) != cudaSuccess) rc = fail(TRIME_ENOMEM, "pinned alloc");
     m->dbg = P.debug ? dalloc<double>(m, 10 * N, rc) : nullptr;
@@ -824,7 +825,7 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->toff = dalloc<int32_t>(m, N + 1, rc);
     m->tbuf = dalloc<int32_t>(m, 3 * (2 * nmax + 16), rc);
     m->xybuf = dalloc<char>(m, 2 * N * std::max<size_t>(T, sizeof(double)), rc);
-    m->ovf_list = dalloc<int32_t>(m, 3 * N, rc);
+    m->ovf_list = dalloc<int32_t>(m, 4 * N, rc);
     m->pf = dalloc<float4>(m, N, rc);
     m->pf3 = dalloc<float2>(m, N, rc);
     m->pS = dalloc<float>(m, N, rc);
@@ -1200,7 +1201,8 @@ static void drop_alloc(mesh_s* m, void* p) {
 }
 
 static int set_tuning(mesh_s* m, double nopt, int32_t lanes) {
-    if (!(nopt > 0) || (lanes != 16 && lanes != 32)) return fail(TRIME_EINVAL, "n_opt must be > 0, lanes 16 or 32");
+    if (!(nopt > 0) || (lanes != 8 && lanes != 16 && lanes != 32))
+        return fail(TRIME_EINVAL, "n_opt must be > 0, lanes 8, 16 or 32");
     int rc = sync_in(m);
     if (rc) return rc;
     CUDA_TRY(cudaStreamSynchronize(m->st));
@@ -1821,7 +1823,7 @@ int mesh_batch_get_tuning(const mesh_batch_t* b, mesh_tuning* out) {
     out->lanes = b->lanes;
     out->n_slots = b->nslots;
     out->n_buckets = b->nbtot;
-    int nc = (int)std::min<size_t>(b->tune.size(), 8);
+    int nc = (int)std::min<size_t>(b->tune.size(), 12);
     out->n_candidates = nc;
     for (int k = 0; k < nc; k++) {
         out->cand_n_opt[k] = b->tune[k].nopt;

@@ -5,10 +5,10 @@
 // A group of G lanes clips one cell: the convex polygon lives in the group,
 // one edge per lane: lane t holds edge E_t as a half-plane n.u <= s (u
 // relative to the generator) and the vertex V_t = E_t cap E_{t+1}.  The main
-// pass uses G = 16 (two cells per warp; final cells have 6-8 edges); a cell
-// that would need more than 16 edges is queued and redone with G = 32 by the
-// same code, and one that needs more than 32 by a serial pass (one thread per
-// cell, up to 64 edges).  Candidates come from the bucket grid ring by ring, one per lane,
+// pass uses G = 8 (four cells per warp; final cells have 6-8 edges); a cell
+// that would need more than 8 edges at some step is queued and redone with
+// G = 16, then G = 32 by the same code, and one that needs more than 32 by a
+// serial pass (one thread per cell, up to 64 edges).  Candidates come from the bucket grid ring by ring, one per lane,
 // are filtered by the security radius (a point farther than twice the largest
 // vertex distance cannot cut), staged in shared memory and applied nearest
 // first across the staged set.  A clip classifies every vertex in parallel,
@@ -431,10 +431,13 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     }
     if (!live) return;
     if (status == 2) {
-        // out of lanes: queue the cell for the 32-lane pass, or from there
-        // for the serial pass
+        // out of lanes: queue the cell for the next wider pass (8 -> 16 -> 32
+        // lanes), or from the 32-lane pass for the serial pass
         if (g.gl == 0) {
-            if (G < 32) {
+            if (G == 8) {
+                int q = atomicAdd(a.ovf_n + 3, 1);
+                a.ovf0_list[q] = s;
+            } else if (G == 16) {
                 int q = atomicAdd(a.ovf_n, 1);
                 a.ovf_list[q] = s;
             } else {
@@ -482,20 +485,29 @@ __global__ void __launch_bounds__(kVoroThreads, 7) k_voronoi(const __grid_consta
     }
 }
 
-// 32-lane pass over the cells the 16-lane pass could not hold
-template <typename T, bool B>
+// wider pass over the cells a narrower one could not hold: G lanes per cell,
+// the cells taken from a queue (the 8-lane pass's for G = 16, the 16-lane
+// pass's for G = 32)
+template <typename T, int G, bool B>
 __global__ void __launch_bounds__(kVoroThreads) k_voronoi_wide(const __grid_constant__ IterArgs<T> a) {
     if (!B && skip_rebuild(a.V.ctrl, a.force)) return;
-    __shared__ float4 stage_all[kVoroThreads / 32][kStageCap];
-    Grp<32> g;
-    g.gl = threadIdx.x & 31;
-    g.goff = 0;
+    __shared__ float4 stage_all[kVoroThreads / G][kStageCap];
+    Grp<G> g;
+    int lane = threadIdx.x & 31;
+    g.gl = lane & (G - 1);
+    g.goff = lane & ~(G - 1);
+    constexpr int cpw = 32 / G;
+    const int32_t* list = G == 16 ? a.ovf0_list : a.ovf_list;
+    int n = G == 16 ? a.ovf_n[3] : a.ovf_n[0];
     int wib = threadIdx.x >> 5;
     int nw = gridDim.x * (kVoroThreads / 32);
-    int n = *a.ovf_n;
-    for (int i = blockIdx.x * (kVoroThreads / 32) + wib; i < n; i += nw) {
-        int s = a.ovf_list[i];
-        voronoi_cell<T, 32>(a, mesh_of<B>(a, s), s, g, stage_all[wib]);
+    float4* stage = stage_all[threadIdx.x / G];
+    for (int w = blockIdx.x * (kVoroThreads / 32) + wib; w * cpw < n; w += nw) {
+        int i = w * cpw + lane / G;
+        int s = i < n ? list[i] : -1;
+        // the cells of one warp may belong to different meshes of a batch:
+        // each group reads its own mesh's view
+        voronoi_cell<T, G>(a, mesh_of<B>(a, s < 0 ? list[w * cpw] : s), s, g, stage);
     }
 }
 
@@ -781,16 +793,19 @@ void launch_voronoi_big(const IterArgs<T>& a, int32_t n, float4* scratch, int32_
 // per warp
 template <typename T, bool B>
 void launch_voronoi_impl(const IterArgs<T>& a, int lanes, cudaStream_t st) {
-    cudaMemsetAsync(a.ovf_n, 0, 3 * sizeof(int32_t), st);
+    cudaMemsetAsync(a.ovf_n, 0, 4 * sizeof(int32_t), st);
+    int cpb = kVoroThreads / lanes;  // cells per block
+    int g = (a.n + cpb - 1) / cpb;
+    if (g < 1) g = 1;
     if (lanes == 32) {
-        int cpb = kVoroThreads / 32;
-        int g = (a.n + cpb - 1) / cpb;
-        k_voronoi<T, 32, B><<<g < 1 ? 1 : g, kVoroThreads, 0, st>>>(a);
+        k_voronoi<T, 32, B><<<g, kVoroThreads, 0, st>>>(a);
+    } else if (lanes == 16) {
+        k_voronoi<T, 16, B><<<g, kVoroThreads, 0, st>>>(a);
+        k_voronoi_wide<T, 32, B><<<152 * 2, kVoroThreads, 0, st>>>(a);
     } else {
-        int cpb = kVoroThreads / 16;  // cells per block
-        int g = (a.n + cpb - 1) / cpb;
-        k_voronoi<T, 16, B><<<g < 1 ? 1 : g, kVoroThreads, 0, st>>>(a);
-        k_voronoi_wide<T, B><<<152 * 2, kVoroThreads, 0, st>>>(a);
+        k_voronoi<T, 8, B><<<g, kVoroThreads, 0, st>>>(a);
+        k_voronoi_wide<T, 16, B><<<152 * 4, kVoroThreads, 0, st>>>(a);
+        k_voronoi_wide<T, 32, B><<<152 * 2, kVoroThreads, 0, st>>>(a);
     }
     k_voronoi_serial<T, B><<<152, kSerialThreads, 0, st>>>(a);
 }

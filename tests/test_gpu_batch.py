@@ -78,7 +78,7 @@ def test_batch_triangles_match_oracle(precision):
     oms = _oracles(meshes, method=2)
     _check_triangles(b, oms, b.rebuild())
     # other tilings give the same triangles
-    for n_opt, lanes in ((2.0, 32), (6.0, 16), (3.3, 32)):
+    for n_opt, lanes in ((2.0, 32), (6.0, 16), (3.3, 32), (4.0, 8)):
         b.set_tuning(n_opt, lanes)
         assert b.tuning()["lanes"] == lanes
         _check_triangles(b, oms, b.rebuild())
@@ -90,7 +90,7 @@ def test_batch_autotune_record():
     meshes = _mixed_meshes()
     b = g.MeshBatch(meshes, method=2, autotune=True)
     t = b.tuning()
-    assert len(t["candidates"]) == 6
+    assert len(t["candidates"]) == 9  # 3 bucket sizes x 8, 16, 32 lanes
     best = min(t["candidates"], key=lambda c: c[2])
     assert (t["n_opt"], t["lanes"]) == (best[0], best[1])
     assert t["n_slots"] == sum((len(m[2]) + 255) // 256 * 256 for m in meshes)
