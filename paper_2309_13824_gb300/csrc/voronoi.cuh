@@ -33,6 +33,11 @@ namespace trime {
 constexpr float kEps = 5.9604645e-8f;  // 2^-24
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kStageCap = 96;  // staged candidates per group (16 bytes each)
+// resident blocks per SM the clipping kernels are compiled for (registers:
+// 65536 / (kVoroThreads x this)); a build-time tuning knob
+#ifndef TRIME_VORO_MINB
+#define TRIME_VORO_MINB 6
+#endif
 
 template <int G>
 struct Grp {
@@ -392,9 +397,10 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                 int cs = olo + (q - oex);
                 bool valid = !done && q < total && cs != s;
                 float dx = 0.f, dy = 0.f, d2 = INF;
-                if (valid) valid = !a.dom[cs];
                 if (valid) {
+                    // both loads issued together; a flagged duplicate is dropped after
                     float4 pj4 = a.pf[cs];
+                    valid = !a.dom[cs];
                     dx = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y);
                     dy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
                     d2 = dx * dx + dy * dy;
@@ -465,7 +471,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
 // main pass: G lanes per cell, 32 / G cells per warp.  In a batch the cells
 // of a warp lie in one chunk, hence in one mesh.
 template <typename T, int G, bool B>
-__global__ void __launch_bounds__(kVoroThreads, 7) k_voronoi(const __grid_constant__ IterArgs<T> a) {
+__global__ void __launch_bounds__(kVoroThreads, TRIME_VORO_MINB) k_voronoi(const __grid_constant__ IterArgs<T> a) {
     if (!B && skip_rebuild(a.V.ctrl, a.force)) return;
     __shared__ float4 stage_all[kVoroThreads / G][kStageCap];
     Grp<G> g;
@@ -489,7 +495,7 @@ __global__ void __launch_bounds__(kVoroThreads, 7) k_voronoi(const __grid_consta
 // the cells taken from a queue (the 8-lane pass's for G = 16, the 16-lane
 // pass's for G = 32)
 template <typename T, int G, bool B>
-__global__ void __launch_bounds__(kVoroThreads) k_voronoi_wide(const __grid_constant__ IterArgs<T> a) {
+__global__ void __launch_bounds__(kVoroThreads, TRIME_VORO_MINB) k_voronoi_wide(const __grid_constant__ IterArgs<T> a) {
     if (!B && skip_rebuild(a.V.ctrl, a.force)) return;
     __shared__ float4 stage_all[kVoroThreads / G][kStageCap];
     Grp<G> g;
@@ -804,7 +810,7 @@ void launch_voronoi_impl(const IterArgs<T>& a, int lanes, cudaStream_t st) {
         k_voronoi_wide<T, 32, B><<<152 * 2, kVoroThreads, 0, st>>>(a);
     } else {
         k_voronoi<T, 8, B><<<g, kVoroThreads, 0, st>>>(a);
-        k_voronoi_wide<T, 16, B><<<152 * 4, kVoroThreads, 0, st>>>(a);
+        k_voronoi_wide<T, 16, B><<<152 * TRIME_VORO_MINB, kVoroThreads, 0, st>>>(a);
         k_voronoi_wide<T, 32, B><<<152 * 2, kVoroThreads, 0, st>>>(a);
     }
     k_voronoi_serial<T, B><<<152, kSerialThreads, 0, st>>>(a);
