@@ -73,9 +73,12 @@ struct Lane {
 __device__ __forceinline__ void make_vertex(Lane& L, float nx2, float ny2, float s2, int lab2, float RB) {
     float D = L.nx * ny2 - L.ny * nx2;
     float px = L.s * ny2 - s2 * L.ny, py = s2 * L.nx - L.s * nx2;
-    float iD = 1.0f / D;
+    // approximate reciprocal and root (a few ulps): the bound err below
+    // allows 64 ulps of the vertex and of r
+    float iD = __fdividef(1.0f, D);
     float ux = px * iD, uy = py * iD;
-    float r = sqrtf(ux * ux + uy * uy);
+    float q = ux * ux + uy * uy;
+    float r = q > 0.0f ? q * rsqrtf(q) : 0.0f;
     float perm = fabsf(L.s * ny2) + fabsf(s2 * L.ny) + fabsf(s2 * L.nx) + fabsf(L.s * nx2) +
                  r * (fabsf(L.nx * ny2) + fabsf(L.ny * nx2));
     float err = 64.0f * kEps * perm * fabsf(iD);
@@ -289,7 +292,11 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     }
     lane_vertex<G>(L, ne, g, RB, true);
     int status = 0;
-    if (P.bounded) {
+    // the domain box cuts the octagon only if one of its planes comes closer
+    // than the octagon's circumradius RB (every vertex lies within RB)
+    bool near_box = live && !(RB * 1.001f < xf + mb && RB * 1.001f < (Wf - xf) + mb &&
+                              RB * 1.001f < yf + mb && RB * 1.001f < (Hf - yf) + mb);
+    if (P.bounded && warp_any(near_box)) {
         for (int b = 0; b < 4; b++) {
             float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
             float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
