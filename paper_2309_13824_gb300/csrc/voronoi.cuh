@@ -376,6 +376,14 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                 }
                 c0 = c0 < 0 ? 0 : c0;
                 c1 = c1 >= P.nbx ? P.nbx - 1 : c1;
+                if (r > 1 && row >= 0 && row < P.nby && c0 <= c1) {
+                    // outer rings: a bucket range farther than 2 Rmax (with the
+                    // bucket-assignment margin) holds no point that can cut
+                    float ddx = fmaxf(fmaxf((float)c0 * bsx - xf, xf - (float)(c1 + 1) * bsx), 0.0f);
+                    float ddy = fmaxf(fmaxf((float)row * bsy - yf, yf - (float)(row + 1) * bsy), 0.0f);
+                    float lim = 2.0f * Rmax * 1.0001f + bmargin;
+                    if (ddx * ddx + ddy * ddy > lim * lim) c1 = c0 - 1;
+                }
                 if (row >= 0 && row < P.nby && c0 <= c1) {
                     lo = a.bstart[V.boff + row * P.nbx + c0];
                     hi = a.bstart[V.boff + row * P.nbx + c1 + 1];
