@@ -115,24 +115,27 @@ def measured_peaks():
         return {}
 
 
-def committed_traffic(kernel_src):
-    """DRAM bytes per launch of the Voronoi kernel from the committed ncu
-    summary, or None if the kernel source changed since it was captured."""
+def committed_profile(kernel_src):
+    """DRAM bytes and warp instructions per launch of the Voronoi kernel from
+    the committed ncu summary; both None if the kernel source changed since
+    it was captured."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "voronoi_annulus_1e6.md")
     try:
         txt = open(path).read()
     except OSError:
-        return None
+        return None, None
     digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    tr, hs = None, None
+    tr, wi, hs = None, None, None
     for line in txt.splitlines():
         if line.startswith("traffic_bytes_per_launch:"):
             tr = float(line.split(":")[1])
+        if line.startswith("warp_instructions_per_launch:"):
+            wi = float(line.split(":")[1])
         if line.startswith("voronoi_cuh_sha256_16:"):
             hs = line.split(":")[1].strip()
-    return tr if hs == digest else None
+    return (tr, wi) if hs == digest else (None, None)
 
 
 def flush_l2(buf):
@@ -617,10 +620,20 @@ def main():
     achieved = VORONOI_FLOP_PER_CELL * n / t_vor / 1e12
     pipe = g.mesh_measure_pipe_peaks()
     src = os.path.join(ROOT, "paper_2309_13824_gb300", "csrc", "voronoi.cuh")
+    traffic, winst = committed_profile(src)
     roofline = {"bound": "alu", "kernel": "k_voronoi", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": committed_traffic(src),
+                "frac": achieved / alu_peak, "traffic": traffic,
                 "peak_note": f"{sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and clocks)",
                 "stage_ms": stage_ms, "measured_pipe_peaks": pipe}
+    if winst:
+        # the kernel is bound by instruction issue, not by FP32 arithmetic:
+        # its ncu warp-instruction count against one instruction per
+        # scheduler per clock (4 per SM), over the live Voronoi stage time
+        ipk = sm_count * 4 * sm_mhz * 1e6
+        roofline["issue"] = {"warp_instructions_per_launch": winst, "achieved_per_s": winst / t_vor,
+                             "peak_per_s": ipk, "frac": winst / t_vor / ipk,
+                             "note": "instructions of k_voronoi from the committed ncu capture; time of the whole "
+                                     "Voronoi stage (the wider passes included)"}
 
     # ---- end to end through the C ABI: H2D of the step's positions from
     # pinned host memory, one iteration, D2H of the moved positions
