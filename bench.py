@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-quality / FP32 / CPU legs")
     ap.add_argument("--n-opt", type=float, default=None, help="points per neighbour bucket (default 3.3)")
     ap.add_argument("--sweep", action="store_true",
-                    help="add the N sweep (annulus 1e4..1e7, square 1e6) and the 1e7-point star")
+                    help="add the N sweep (annulus 1e4..1e7, square 1e6) and the 1e7-point star "
+                         "(also with --no-extras)")
     return ap.parse_args()
 
 
@@ -666,6 +667,8 @@ def main():
         em.close()
 
     extras = {}
+    if args.sweep and rank == 0:
+        extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
     if not args.no_extras and rank == 0:
         # wall time to quality: hybrid from the seeds until termination
         tq = g.Mesh(wl.sdf, wl.sizing, pts, method=2, precision=args.precision, stream=stream.cuda_stream, **kw)
@@ -702,8 +705,6 @@ def main():
         extras["point_addition"] = addition_leg(g, torch, stream)
         extras["segment_sdf"] = segment_sdf_leg(g, torch, stream)
         extras["from_polygon"] = polygon_leg(g, torch, stream)
-        if args.sweep:
-            extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
         threads = os.cpu_count() or 1
         cnt, dt, om = oracle_sample_rate(wl, 10.0, threads=threads)
         cnt1, dt1, _ = oracle_sample_rate(wl, 5.0, threads=1, om=om)
