@@ -117,6 +117,14 @@ def _load():
         lib.om_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         lib.om_lfs.restype = C.c_int64
         lib.om_lfs.argtypes = [dp, C.c_int64, dp, C.c_int64, C.c_double, C.c_int32, dp]
+        lib.om_adf_build.restype = C.c_void_p
+        lib.om_adf_build.argtypes = [dp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                     C.c_int32, ip, dp, C.c_int32, C.c_int32]
+        lib.om_adf_size.restype = C.c_int64
+        lib.om_adf_size.argtypes = [C.c_void_p]
+        lib.om_adf_export.argtypes = [C.c_void_p, dp, ip, ip, ip]
+        lib.om_adf_eval.argtypes = [C.c_void_p, dp, dp, C.c_int64, dp]
+        lib.om_adf_free.argtypes = [C.c_void_p]
         _lib = lib
     return _lib
 
@@ -183,6 +191,49 @@ def segment_sdf(verts_cw, px, py) -> np.ndarray:
     if lib.om_segment_sdf(_dp(v), len(v), _dp(px), _dp(py), len(px), _dp(out)) != 0:
         raise ValueError(lib.om_last_error().decode())
     return out
+
+
+class OracleADF:
+    """Sec. 3.7 adaptive distance field of the clockwise loop verts_cw: one
+    quadtree per listed cell (index j (nx - 1) + i of the node grid over box),
+    split while the bilinear error at the edge midpoints and the centre
+    exceeds tol[r] and the level is below max_depth (om_adf_build)."""
+
+    def __init__(self, verts_cw, box, nx, ny, cells, tol, max_depth=10):
+        lib = _load()
+        self._v = np.ascontiguousarray(verts_cw, dtype=np.float64).reshape(-1, 2)
+        c = np.ascontiguousarray(cells, dtype=np.int32).ravel()
+        t = np.ascontiguousarray(tol, dtype=np.float64).ravel()
+        x0, y0, x1, y1 = (float(b) for b in box)
+        self._h = lib.om_adf_build(_dp(self._v), len(self._v), x0, y0, x1, y1, int(nx), int(ny),
+                                   c.ctypes.data_as(C.POINTER(C.c_int32)), _dp(t), len(c), int(max_depth))
+        if not self._h:
+            raise ValueError(lib.om_last_error().decode())
+
+    def nodes(self):
+        """(v (n, 4), child (n,), root (n,), lev (n, 3)) in build order."""
+        lib = _load()
+        n = lib.om_adf_size(self._h)
+        v = np.zeros((n, 4))
+        child = np.zeros(n, np.int32)
+        root = np.zeros(n, np.int32)
+        lev = np.zeros((n, 3), np.int32)
+        ip = C.POINTER(C.c_int32)
+        lib.om_adf_export(self._h, _dp(v), child.ctypes.data_as(ip), root.ctypes.data_as(ip), lev.ctypes.data_as(ip))
+        return v, child, root, lev
+
+    def eval(self, px, py):
+        lib = _load()
+        px = np.ascontiguousarray(px, dtype=np.float64).ravel()
+        py = np.ascontiguousarray(py, dtype=np.float64).ravel()
+        out = np.empty(len(px))
+        lib.om_adf_eval(self._h, _dp(px), _dp(py), len(px), _dp(out))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _load().om_adf_free(self._h)
+            self._h = None
 
 
 def sizing_field(samples, lfs, K, px, py) -> np.ndarray:

@@ -1672,6 +1672,167 @@ int om_segment_sdf(const double* xy, int64_t nv, const double* px, const double*
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 3.7: adaptive distance field on boundary grid cells                 */
+/* ------------------------------------------------------------------------ */
+struct om_adf {
+    double x0, y0, dx, dy;
+    int32_t ncx, ncy, ncells;
+    int32_t* cells;
+    int32_t* cellroot; /* [ncx * ncy] tree of each cell or -1 */
+    int64_t n, cap;
+    double* v;
+    int32_t *child, *root, *lev;
+};
+
+static int adf_grow(om_adf* a, int64_t need) {
+    if (need <= a->cap) return 0;
+    int64_t cap = a->cap ? a->cap : 1024;
+    while (cap < need) cap *= 2;
+    double* v = (double*)realloc(a->v, sizeof(double) * 4 * (size_t)cap);
+    if (v) a->v = v;
+    int32_t* c = (int32_t*)realloc(a->child, sizeof(int32_t) * (size_t)cap);
+    if (c) a->child = c;
+    int32_t* r = (int32_t*)realloc(a->root, sizeof(int32_t) * (size_t)cap);
+    if (r) a->root = r;
+    int32_t* l = (int32_t*)realloc(a->lev, sizeof(int32_t) * 3 * (size_t)cap);
+    if (l) a->lev = l;
+    if (!v || !c || !r || !l) return -1;
+    a->cap = cap;
+    return 0;
+}
+
+/* coordinate of node corner index i at level L of a cell starting at c0 */
+static double adf_coord(double c0, double w, int32_t i, int32_t L) {
+    return c0 + (double)i * (w * (1.0 / (double)(1 << L)));
+}
+
+static int adf_push(om_adf* a, int32_t root, int32_t L, int32_t ix, int32_t iy, double v00, double v10, double v01,
+                    double v11) {
+    if (adf_grow(a, a->n + 1)) return -1;
+    int64_t k = a->n++;
+    a->v[4 * k] = v00;
+    a->v[4 * k + 1] = v10;
+    a->v[4 * k + 2] = v01;
+    a->v[4 * k + 3] = v11;
+    a->child[k] = -1;
+    a->root[k] = root;
+    a->lev[3 * k] = L;
+    a->lev[3 * k + 1] = ix;
+    a->lev[3 * k + 2] = iy;
+    return 0;
+}
+
+void om_adf_free(om_adf* a) {
+    if (!a) return;
+    free(a->cells); free(a->cellroot); free(a->v); free(a->child); free(a->root); free(a->lev);
+    free(a);
+}
+
+om_adf* om_adf_build(const double* xy, int64_t nv, double x0, double y0, double x1, double y1, int32_t nx, int32_t ny,
+                     const int32_t* cells, const double* tol, int32_t ncells, int32_t max_depth) {
+    if (!xy || nv < 3 || nx < 2 || ny < 2 || !(x1 > x0) || !(y1 > y0) || ncells < 0 || (ncells > 0 && (!cells || !tol)) ||
+        max_depth < 0 || max_depth > 14) {
+        set_err("bad ADF input");
+        return NULL;
+    }
+    om_adf* a = (om_adf*)calloc(1, sizeof(om_adf));
+    if (!a) { set_err("oom"); return NULL; }
+    a->x0 = x0;
+    a->y0 = y0;
+    a->dx = (x1 - x0) / (double)(nx - 1);
+    a->dy = (y1 - y0) / (double)(ny - 1);
+    a->ncx = nx - 1;
+    a->ncy = ny - 1;
+    a->ncells = ncells;
+    a->cells = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ncells > 0 ? ncells : 1));
+    a->cellroot = (int32_t*)malloc(sizeof(int32_t) * (size_t)a->ncx * (size_t)a->ncy);
+    if (!a->cells || !a->cellroot) { om_adf_free(a); set_err("oom"); return NULL; }
+    for (int64_t c = 0; c < (int64_t)a->ncx * a->ncy; c++) a->cellroot[c] = -1;
+    /* level 0: the cells themselves, corners from the exact SDF */
+    for (int32_t r = 0; r < ncells; r++) {
+        int32_t c = cells[r];
+        if (c < 0 || c >= a->ncx * a->ncy || a->cellroot[c] >= 0) { om_adf_free(a); set_err("bad ADF cell list"); return NULL; }
+        a->cells[r] = c;
+        a->cellroot[c] = r;
+        double cx0 = x0 + (double)(c % a->ncx) * a->dx, cy0 = y0 + (double)(c / a->ncx) * a->dy;
+        double xa = adf_coord(cx0, a->dx, 0, 0), xb = adf_coord(cx0, a->dx, 1, 0);
+        double ya = adf_coord(cy0, a->dy, 0, 0), yb = adf_coord(cy0, a->dy, 1, 0);
+        double px[4] = {xa, xb, xa, xb}, py[4] = {ya, ya, yb, yb}, s[4];
+        om_segment_sdf(xy, nv, px, py, 4, s);
+        if (adf_push(a, r, 0, 0, 0, s[0], s[1], s[2], s[3])) { om_adf_free(a); set_err("oom"); return NULL; }
+    }
+    /* level by level: test the level's nodes in order, append the children */
+    int64_t lo = 0, hi = a->n;
+    for (int32_t L = 0; L < max_depth && lo < hi; L++) {
+        for (int64_t k = lo; k < hi; k++) {
+            int32_t r = a->root[k], ix = a->lev[3 * k + 1], iy = a->lev[3 * k + 2];
+            int32_t c = a->cells[r];
+            double cx0 = x0 + (double)(c % a->ncx) * a->dx, cy0 = y0 + (double)(c / a->ncx) * a->dy;
+            double xa = adf_coord(cx0, a->dx, 2 * ix, L + 1), xm = adf_coord(cx0, a->dx, 2 * ix + 1, L + 1);
+            double xb = adf_coord(cx0, a->dx, 2 * ix + 2, L + 1);
+            double ya = adf_coord(cy0, a->dy, 2 * iy, L + 1), ym = adf_coord(cy0, a->dy, 2 * iy + 1, L + 1);
+            double yb = adf_coord(cy0, a->dy, 2 * iy + 2, L + 1);
+            /* exact SDF at the bottom, top, left, right midpoints and the centre */
+            double px[5] = {xm, xm, xa, xb, xm}, py[5] = {ya, yb, ym, ym, ym}, s[5];
+            om_segment_sdf(xy, nv, px, py, 5, s);
+            double v00 = a->v[4 * k], v10 = a->v[4 * k + 1], v01 = a->v[4 * k + 2], v11 = a->v[4 * k + 3];
+            double p[5] = {(v00 + v10) * 0.5, (v01 + v11) * 0.5, (v00 + v01) * 0.5, (v10 + v11) * 0.5,
+                           ((v00 + v10) + (v01 + v11)) * 0.25};
+            double err = 0.0;
+            for (int q = 0; q < 5; q++) err = fmax(err, fabs(p[q] - s[q]));
+            if (!(err > tol[r])) continue;
+            a->child[k] = (int32_t)a->n;
+            if (adf_push(a, r, L + 1, 2 * ix, 2 * iy, v00, s[0], s[2], s[4]) ||
+                adf_push(a, r, L + 1, 2 * ix + 1, 2 * iy, s[0], v10, s[4], s[3]) ||
+                adf_push(a, r, L + 1, 2 * ix, 2 * iy + 1, s[2], s[4], v01, s[1]) ||
+                adf_push(a, r, L + 1, 2 * ix + 1, 2 * iy + 1, s[4], s[3], s[1], v11)) {
+                om_adf_free(a);
+                set_err("oom");
+                return NULL;
+            }
+        }
+        lo = hi;
+        hi = a->n;
+    }
+    return a;
+}
+
+int64_t om_adf_size(const om_adf* a) { return a ? a->n : 0; }
+
+void om_adf_export(const om_adf* a, double* v, int32_t* child, int32_t* root, int32_t* lev) {
+    memcpy(v, a->v, sizeof(double) * 4 * (size_t)a->n);
+    memcpy(child, a->child, sizeof(int32_t) * (size_t)a->n);
+    memcpy(root, a->root, sizeof(int32_t) * (size_t)a->n);
+    memcpy(lev, a->lev, sizeof(int32_t) * 3 * (size_t)a->n);
+}
+
+void om_adf_eval(const om_adf* a, const double* px, const double* py, int64_t np, double* out) {
+    for (int64_t q = 0; q < np; q++) {
+        double x = px[q], y = py[q];
+        double fi = floor((x - a->x0) / a->dx), fj = floor((y - a->y0) / a->dy);
+        int32_t i = !(fi >= 0.0) ? 0 : (fi > (double)(a->ncx - 1) ? a->ncx - 1 : (int32_t)fi);
+        int32_t j = !(fj >= 0.0) ? 0 : (fj > (double)(a->ncy - 1) ? a->ncy - 1 : (int32_t)fj);
+        int32_t r = a->cellroot[j * a->ncx + i];
+        if (r < 0) { out[q] = NAN; continue; }
+        double cx0 = a->x0 + (double)i * a->dx, cy0 = a->y0 + (double)j * a->dy;
+        int64_t k = r;
+        while (a->child[k] >= 0) {
+            int32_t L = a->lev[3 * k], ix = a->lev[3 * k + 1], iy = a->lev[3 * k + 2];
+            double xm = adf_coord(cx0, a->dx, 2 * ix + 1, L + 1), ym = adf_coord(cy0, a->dy, 2 * iy + 1, L + 1);
+            k = a->child[k] + (y >= ym ? 2 : 0) + (x >= xm ? 1 : 0);
+        }
+        int32_t L = a->lev[3 * k], ix = a->lev[3 * k + 1], iy = a->lev[3 * k + 2];
+        double wx = a->dx * (1.0 / (double)(1 << L)), wy = a->dy * (1.0 / (double)(1 << L));
+        double fx = (x - adf_coord(cx0, a->dx, ix, L)) / wx, fy = (y - adf_coord(cy0, a->dy, iy, L)) / wy;
+        fx = fx < 0.0 ? 0.0 : (fx > 1.0 ? 1.0 : fx);
+        fy = fy < 0.0 ? 0.0 : (fy > 1.0 ? 1.0 : fy);
+        const double* v = a->v + 4 * k;
+        double va = v[0] + fx * (v[1] - v[0]), vb = v[2] + fx * (v[3] - v[2]);
+        out[q] = va + fy * (vb - va);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 3.3 Eq. 7: sizing field from boundary samples (brute force)         */
 /* ------------------------------------------------------------------------ */
 int om_sizing_field(const double* sxy, const double* lfs, int64_t ns, double K, const double* px, const double* py,

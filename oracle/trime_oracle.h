@@ -20,6 +20,7 @@
  *   - element sizing field from boundary samples and lfs      Sec. 3.3 Eq. 7
  *   - boundary samples, medial axis, local feature size       App. A, Sec. 3.3
  *   - point initialisation with Floyd-Steinberg dithering      Sec. 3.5
+ *   - adaptive distance field (quadtrees on boundary cells)    Sec. 3.7 (Fig. 17), App. B
  *
  * Every sign decision of the triangulation (incircle / orientation) is exact:
  * big-integer arithmetic behind a deliberately loose double-precision filter,
@@ -154,6 +155,30 @@ double om_bilinear(const om_grid* g, double x, double y);
  * two incident segments' unit normals; positive elsewhere.  Brute force over
  * all segments.  Returns 0, or -1 on bad input. */
 int om_segment_sdf(const double* xy, int64_t nv, const double* px, const double* py, int64_t np, double* out);
+
+/* Sec. 3.7: adaptive distance field.  One quadtree per listed grid cell
+ * cells[r] = j (nx - 1) + i of the node grid (x0, y0, x1, y1, nx, ny), built
+ * top-down: a node's four corners hold the exact segment SDF (om_segment_sdf);
+ * the bilinear values at its four edge midpoints and its centre are compared
+ * with the exact SDF there, and the node splits into four children when the
+ * largest error exceeds tol[r] and its level is below max_depth.  Nodes are
+ * numbered level by level, children in their parent's order, each parent's
+ * four children consecutive in the quadrant order (0,0), (1,0), (0,1),
+ * (1,1).  Coordinates: cell corner cx0 = x0 + i dx, node corner
+ * cx0 + ix (dx 2^-L), the midpoints at level L + 1.  Returns a handle, or
+ * NULL on bad input. */
+typedef struct om_adf om_adf;
+om_adf* om_adf_build(const double* xy, int64_t nv, double x0, double y0, double x1, double y1, int32_t nx, int32_t ny,
+                     const int32_t* cells, const double* tol, int32_t ncells, int32_t max_depth);
+int64_t om_adf_size(const om_adf* a);
+/* Node arrays: v[4n] corners (v00, v10, v01, v11), child[n] first child or
+ * -1, root[n] index into cells, lev[3n] (level, ix, iy). */
+void om_adf_export(const om_adf* a, double* v, int32_t* child, int32_t* root, int32_t* lev);
+/* ADF values at np points: the leaf of the point's cell tree holding it
+ * (a coordinate equal to a midpoint goes to the upper child), bilinear in the
+ * leaf; NaN where the point's cell has no tree. */
+void om_adf_eval(const om_adf* a, const double* px, const double* py, int64_t np, double* out);
+void om_adf_free(om_adf* a);
 
 /* Eq. 7 element sizing field mu(x) = min over the boundary samples s of
  * K |s - x| + lfs(s) (Sec. 3.3), at np points; brute force over the ns

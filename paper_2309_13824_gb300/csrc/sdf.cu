@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "seg.cuh"
 #include "trime.h"
 
 namespace trime {
@@ -34,28 +35,6 @@ struct SegGrid {
     int32_t gx, gy;
     double diag;
 };
-
-__device__ __forceinline__ void seg_dist(const double* xy, int32_t nv, int32_t k, double x, double y, double& d,
-                                         double& t) {
-    int32_t k1 = k + 1 == nv ? 0 : k + 1;
-    double ax = xy[2 * k], ay = xy[2 * k + 1];
-    double ex = fsub(xy[2 * k1], ax), ey = fsub(xy[2 * k1 + 1], ay);
-    double wx = fsub(x, ax), wy = fsub(y, ay);
-    t = fdiv(fadd(fmul(wx, ex), fmul(wy, ey)), fadd(fmul(ex, ex), fmul(ey, ey)));
-    if (!(t > 0.0)) t = 0.0;
-    if (t > 1.0) t = 1.0;
-    double cx = fadd(ax, fmul(t, ex)), cy = fadd(ay, fmul(t, ey));
-    double dx = fsub(x, cx), dy = fsub(y, cy);
-    d = __dsqrt_rn(fadd(fmul(dx, dx), fmul(dy, dy)));
-}
-
-__device__ __forceinline__ void seg_normal(const double* xy, int32_t nv, int32_t k, double& nx, double& ny) {
-    int32_t k1 = k + 1 == nv ? 0 : k + 1;
-    double dx = fsub(xy[2 * k1], xy[2 * k]), dy = fsub(xy[2 * k1 + 1], xy[2 * k + 1]);
-    double L = __dsqrt_rn(fadd(fmul(dx, dx), fmul(dy, dy)));
-    nx = fdiv(dy, L);
-    ny = fdiv(-dx, L);
-}
 
 __device__ __forceinline__ int cell_x(const SegGrid& G, double x) {
     double f = floor((x - G.x0) / G.cw);
@@ -192,21 +171,7 @@ __global__ void k_sdf_nodes(const double* xy, int32_t nv, SegGrid G, const int32
         out[q] = __int_as_float(0x7fc00000);
         return;
     }
-    int32_t k1 = bk + 1 == nv ? 0 : bk + 1;
-    double ax = xy[2 * bk], ay = xy[2 * bk + 1];
-    double ex = fsub(xy[2 * k1], ax), ey = fsub(xy[2 * k1 + 1], ay);
-    double cx = fadd(ax, fmul(bt, ex)), cy = fadd(ay, fmul(bt, ey));
-    double nxv, nyv;
-    seg_normal(xy, nv, bk, nxv, nyv);
-    if (bt == 0.0 || bt == 1.0) {
-        int other = bt == 0.0 ? (bk == 0 ? nv - 1 : bk - 1) : k1;
-        double mx, my;
-        seg_normal(xy, nv, other, mx, my);
-        nxv = fadd(nxv, mx);
-        nyv = fadd(nyv, my);
-    }
-    double s = fadd(fmul(fsub(x, cx), nxv), fmul(fsub(y, cy), nyv));
-    out[q] = __double2float_rn(s > 0.0 ? -best : best);
+    out[q] = __double2float_rn(seg_signed(xy, nv, bk, bt, best, x, y));
 }
 
 }  // namespace trime
