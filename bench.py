@@ -367,6 +367,47 @@ def segment_sdf_leg(g, torch, stream):
             "note": "device time includes its scratch allocation and the cell candidate search"}
 
 
+def adf_measure(g, torch, m, v, sg):
+    """The mesh's adaptive distance field (Sec. 3.7: its boundary cells,
+    E_tol = 0.1 geps_i, depth 10): build time, nodes, evaluation rate at 10^6
+    points of the boundary cells (device buffers, CUDA events) and its error
+    against the exact segment SDF at 10^5 of them, beside the error of the
+    float32 grid the mesh samples."""
+    import workloads as W
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a = g.ADF.for_mesh(m, v, sg, fac_etol=0.1, max_depth=10)
+    t_build = time.perf_counter() - t0
+    nodes, levels = a.size()
+    rng = np.random.default_rng(11)
+    nx = sg.values.shape[1]
+    d = (sg.x1 - sg.x0) / (nx - 1)
+    c = a.cells[rng.integers(0, len(a.cells), 1_000_000)]
+    p = np.stack([sg.x0 + (c % (nx - 1) + rng.random(len(c))) * d, sg.y0 + (c // (nx - 1) + rng.random(len(c))) * d],
+                 1)
+    pd = torch.from_numpy(p).cuda()
+    out = torch.empty(len(p), dtype=torch.float64, device="cuda")
+    a.eval(pd, out=out)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream()
+    e0.record(cur)
+    a.eval(pd, out=out, stream=cur.cuda_stream)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    k = 100_000
+    exact = g.segment_sdf_points(v, p[:k])
+    adf = out[:k].cpu().numpy()
+    grid = W._bilinear_np(sg, p[:k, 0], p[:k, 1])
+    res = {"build_seconds": t_build, "boundary_cells": int(len(a.cells)), "nodes": int(nodes), "levels": int(levels),
+           "tol_median": float(np.median(a.tol)), "eval_ms_1e6": ms, "eval_mpts_per_s": 1e3 / ms,
+           "max_error": float(np.abs(adf - exact).max()), "mean_error": float(np.abs(adf - exact).mean()),
+           "grid_max_error": float(np.abs(grid - exact).max()), "grid_mean_error": float(np.abs(grid - exact).mean())}
+    a.close()
+    return res
+
+
 def polygon_leg(g, torch, stream):
     """From a polygon to a mesh with the initialisation pipeline (survey rows
     f3, f4): the benchmark star (500 clockwise segments) -> its SDF grid and
@@ -396,6 +437,7 @@ def polygon_leg(g, torch, stream):
         out.update({"meshing_seconds": time.perf_counter() - t0, "iterations": s["iterations"],
                     "terminated": bool(s["terminated"]), "min_angle_deg": s["min_angle_deg"],
                     "max_alpha": s["max_alpha"], "half_mean_alpha": s["half_mean_alpha"]})
+        out["adf"] = adf_measure(g, torch, m, v, sg)
         m.close()
     except g.MeshError as e:
         out["meshing_error"] = str(e)

@@ -300,6 +300,60 @@ int mesh_auto_sizing(const double* xy, int64_t nv, double K, double x0, double y
                      int32_t nx, int32_t ny, float* sdf_out, float* sizing_out, int64_t* counts,
                      void* cuda_stream);
 
+/* Exact signed distance (Sec. 3.1, the loop xy of nv clockwise vertices as
+ * mesh_segment_sdf_grid, FP64, not rounded) at np points pts (x, y pairs),
+ * by a search over every segment; pts and out in host or device memory.
+ * Synchronous on cuda_stream.  Errors: TRIME_EINVAL, TRIME_ECUDA. */
+int mesh_segment_sdf_points(const double* xy, int64_t nv, const double* pts, int64_t np, double* out,
+                            void* cuda_stream);
+
+/* Adaptive distance field (Sec. 3.7 and Fig. 17; App. B T_depth = 10,
+ * fac_Etol = 0.1): one quadtree per listed cell of the node grid
+ * (x0, y0, x1, y1, nx, ny; cell j (nx-1) + i spans nodes (i, j)..(i+1, j+1)).
+ * A node's corners hold the exact signed distance to the clockwise loop xy
+ * (mesh_segment_sdf_points); the bilinear values at its four edge midpoints
+ * and its centre are compared with the exact distances there, and the node
+ * splits into four children when the largest difference exceeds tol[r] of
+ * its cell cells[r] and its level is below max_depth (0..14).  Node
+ * coordinates: cell corner (x0 + i dx, y0 + j dy), node corner cx0 + ix
+ * (dx 2^-L) at level L.  Nodes are numbered level by level, the four
+ * children of a parent consecutive in the quadrant order (0,0), (1,0),
+ * (0,1), (1,1) and in their parents' order.  cells (distinct) and tol
+ * (finite, >= 0) are host arrays of ncells; the tree lives in device memory
+ * until mesh_adf_destroy.  Synchronous on cuda_stream.  Errors: TRIME_EINVAL,
+ * TRIME_ECAPACITY (more than 2^30 nodes), TRIME_ECUDA. */
+typedef struct adf_s adf_t;
+int mesh_adf_build(const double* xy, int64_t nv, double x0, double y0, double x1, double y1, int32_t nx, int32_t ny,
+                   const int32_t* cells, const double* tol, int32_t ncells, int32_t max_depth, adf_t** out,
+                   void* cuda_stream);
+
+/* The boundary cells of m's geometry grid (Sec. 3.2 class 1), ascending, and
+ * the tolerances E_tol,i = fac_etol geps_i sqrt(N_current / N_total)
+ * (Sec. 3.7), into HOST arrays of cap entries; *n_out = the number of
+ * boundary cells (TRIME_ECAPACITY if cap is smaller).  With mesh_adf_build
+ * on m's SDF grid box and node counts this gives the paper's ADF of a mesh. */
+int mesh_adf_cells(mesh_t* m, double fac_etol, int32_t* cells, double* tol, int64_t cap, int64_t* n_out);
+
+/* Node and level counts of a. */
+int mesh_adf_size(const adf_t* a, int64_t* n_nodes, int32_t* n_levels);
+
+/* Node arrays into HOST buffers of cap nodes: v[4n] corners (v00, v10, v01,
+ * v11), child[n] first child or -1, root[n] index into the cell list,
+ * lev[3n] (level, ix, iy).  *n_out = the node count (TRIME_ECAPACITY if cap
+ * is smaller). */
+int mesh_adf_export(const adf_t* a, double* v, int32_t* child, int32_t* root, int32_t* lev, int64_t cap,
+                    int64_t* n_out);
+
+/* ADF values at np points pts (x, y pairs; host or device): the point's cell
+ * by floor((x - x0) / dx), the leaf of its tree holding the point (a
+ * coordinate equal to a midpoint goes to the upper child), bilinear in the
+ * leaf; NaN where the cell has no tree.  out: np doubles, host or device.
+ * Synchronous on cuda_stream. */
+int mesh_adf_eval(const adf_t* a, const double* pts, int64_t np, double* out, void* cuda_stream);
+
+/* Release the tree (NULL is ignored). */
+void mesh_adf_destroy(adf_t* a);
+
 /* mesh_bucket_points for callers that cannot allocate device memory: the
  * same counting sort (same arguments and outputs, all DEVICE pointers), but
  * its scratch is a fixed 16 MiB array inside the library instead of a

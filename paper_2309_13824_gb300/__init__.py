@@ -70,7 +70,8 @@ class mesh_tuning(C.Structure):
 
 
 # every symbol include/trime.h declares
-EXPORTS = ["mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing", "mesh_init_points", "mesh_get_triangles",
+EXPORTS = ["mesh_segment_sdf_points", "mesh_adf_build", "mesh_adf_cells", "mesh_adf_size", "mesh_adf_export",
+           "mesh_adf_eval", "mesh_adf_destroy", "mesh_default_params", "mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state", "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing", "mesh_init_points", "mesh_get_triangles",
            "mesh_get_points", "mesh_set_state", "mesh_set_method_state", "mesh_get_debug", "mesh_destroy",
            "mesh_last_error", "mesh_bucket_points", "mesh_exact_predicates", "mesh_profile_step",
            "mesh_bucket_points_noalloc", "mesh_batch_init", "mesh_batch_size", "mesh_batch_rebuild",
@@ -165,6 +166,16 @@ def lib():
                                    C.c_double, C.c_int32, C.c_int32, vp, vp, P(C.c_int64), vp]
     L.mesh_init_points.argtypes = [P(mesh_grid2d), P(mesh_grid2d), C.c_int64, C.c_uint64, P(mesh_params),
                                    P(C.c_double), C.c_int64, P(C.c_int64), vp]
+    L.mesh_segment_sdf_points.argtypes = [P(C.c_double), C.c_int64, vp, C.c_int64, vp, vp]
+    L.mesh_adf_build.argtypes = [P(C.c_double), C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                 C.c_int32, P(C.c_int32), P(C.c_double), C.c_int32, C.c_int32, P(vp), vp]
+    L.mesh_adf_cells.argtypes = [vp, C.c_double, P(C.c_int32), P(C.c_double), C.c_int64, P(C.c_int64)]
+    L.mesh_adf_size.argtypes = [vp, P(C.c_int64), P(C.c_int32)]
+    L.mesh_adf_export.argtypes = [vp, P(C.c_double), P(C.c_int32), P(C.c_int32), P(C.c_int32), C.c_int64,
+                                  P(C.c_int64)]
+    L.mesh_adf_eval.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.mesh_adf_destroy.argtypes = [vp]
+    L.mesh_adf_destroy.restype = None
     for name in ("mesh_init", "mesh_rebuild", "mesh_step", "mesh_get_count", "mesh_get_state",
                  "mesh_segment_sdf_grid", "mesh_sizing_field", "mesh_medial_points", "mesh_auto_sizing",
                  "mesh_init_points", "mesh_get_triangles", "mesh_get_points",
@@ -176,7 +187,8 @@ def lib():
                  "mesh_tc_gemm_bf16", "mlp_create", "mlp_get_params", "mlp_set_params", "mlp_forward",
                  "mlp_loss_grad", "mlp_train", "mesh_features", "mesh_collect_pairs", "mesh_propose",
                  "mesh_step_learned", "mesh_set_quality_target", "mesh_batch_set_quality_target",
-                 "mesh_measure_pipe_peaks"):
+                 "mesh_measure_pipe_peaks", "mesh_segment_sdf_points", "mesh_adf_build", "mesh_adf_cells",
+                 "mesh_adf_size", "mesh_adf_export", "mesh_adf_eval"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -297,6 +309,99 @@ def sizing_field(samples, lfs, K: float, n: int, box=(-1.1, -1.1, 1.1, 1.1), ny:
     _check(lib().mesh_sizing_field(s.ctypes.data_as(C.POINTER(C.c_double)), lf.ctypes.data_as(C.POINTER(C.c_double)),
                                    len(s), float(K), x0, y0, x1, y1, n, ny, _ptr(res), st))
     return res
+
+
+def segment_sdf_points(verts_cw, pts, out=None, stream=None):
+    """Exact FP64 signed distance of the clockwise loop verts_cw at the
+    points pts (n, 2) (mesh_segment_sdf_points): a numpy array, or written
+    into `out` (numpy or CUDA tensor of n float64)."""
+    v = np.ascontiguousarray(verts_cw, dtype=np.float64).reshape(-1, 2)
+    if not hasattr(pts, "data_ptr"):
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    n = pts.shape[0]
+    res = out if out is not None else np.empty(n)
+    st = C.c_void_p(0 if stream is None else int(stream))
+    _check(lib().mesh_segment_sdf_points(v.ctypes.data_as(C.POINTER(C.c_double)), len(v), _ptr(pts), n, _ptr(res),
+                                         st))
+    return res
+
+
+class ADF:
+    """Adaptive distance field of a clockwise polygon (Sec. 3.7; a handle to
+    adf_t): one quadtree per listed grid cell, refined until the bilinear
+    error at the edge midpoints and centre is within the cell's tolerance."""
+
+    def __init__(self, verts_cw, box, nx: int, ny: int, cells, tol, max_depth: int = 10, stream=None):
+        self._v = np.ascontiguousarray(verts_cw, dtype=np.float64).reshape(-1, 2)
+        c = np.ascontiguousarray(cells, dtype=np.int32).ravel()
+        t = np.ascontiguousarray(tol, dtype=np.float64).ravel()
+        self.box, self.nx, self.ny = tuple(float(b) for b in box), int(nx), int(ny)
+        self.cells = c.copy()
+        h = C.c_void_p()
+        st = C.c_void_p(0 if stream is None else int(stream))
+        x0, y0, x1, y1 = self.box
+        _check(lib().mesh_adf_build(self._v.ctypes.data_as(C.POINTER(C.c_double)), len(self._v), x0, y0, x1, y1,
+                                    self.nx, self.ny, c.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    t.ctypes.data_as(C.POINTER(C.c_double)), len(c), int(max_depth), C.byref(h), st))
+        self._h = h
+
+    @classmethod
+    def for_mesh(cls, mesh, verts_cw, sdf_grid, fac_etol: float = 0.1, max_depth: int = 10, stream=None):
+        """The paper's ADF of a mesh: its boundary cells and tolerances
+        (mesh_adf_cells) on its SDF grid `sdf_grid` (the Grid it was made with)."""
+        n = C.c_int64()
+        L = lib()
+        rc = L.mesh_adf_cells(mesh._h, float(fac_etol), None, None, 0, C.byref(n))
+        if rc not in (0, -4):
+            _check(rc)
+        cells = np.zeros(n.value, np.int32)
+        tol = np.zeros(n.value)
+        _check(L.mesh_adf_cells(mesh._h, float(fac_etol), cells.ctypes.data_as(C.POINTER(C.c_int32)),
+                                tol.ctypes.data_as(C.POINTER(C.c_double)), len(cells), C.byref(n)))
+        g = sdf_grid
+        obj = cls(verts_cw, (g.x0, g.y0, g.x1, g.y1), g.values.shape[1], g.values.shape[0], cells, tol, max_depth,
+                  stream)
+        obj.tol = tol
+        return obj
+
+    def size(self):
+        n, lv = C.c_int64(), C.c_int32()
+        _check(lib().mesh_adf_size(self._h, C.byref(n), C.byref(lv)))
+        return n.value, lv.value
+
+    def nodes(self):
+        """(v (n, 4), child (n,), root (n,), lev (n, 3)) in build order."""
+        n = self.size()[0]
+        v = np.zeros((n, 4))
+        child = np.zeros(n, np.int32)
+        root = np.zeros(n, np.int32)
+        lev = np.zeros((n, 3), np.int32)
+        got = C.c_int64()
+        ip = C.POINTER(C.c_int32)
+        _check(lib().mesh_adf_export(self._h, v.ctypes.data_as(C.POINTER(C.c_double)), child.ctypes.data_as(ip),
+                                     root.ctypes.data_as(ip), lev.ctypes.data_as(ip), n, C.byref(got)))
+        return v, child, root, lev
+
+    def eval(self, pts, out=None, stream=None):
+        """ADF values at pts (n, 2) (numpy or CUDA tensor); NaN outside the trees."""
+        if not hasattr(pts, "data_ptr"):
+            pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+        n = pts.shape[0]
+        res = out if out is not None else np.empty(n)
+        st = C.c_void_p(0 if stream is None else int(stream))
+        _check(lib().mesh_adf_eval(self._h, _ptr(pts), n, _ptr(res), st))
+        return res
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mesh_adf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def auto_sizing(verts_cw, K: float, n: int, box=(-1.1, -1.1, 1.1, 1.1), ny: int = None, stream=None):

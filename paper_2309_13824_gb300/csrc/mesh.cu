@@ -1599,6 +1599,36 @@ int mesh_get_count(mesh_t* m, int64_t* n_current, int64_t* n_total) {
     return TRIME_OK;
 }
 
+int mesh_adf_cells(mesh_t* m, double fac_etol, int32_t* cells, double* tol, int64_t cap, int64_t* n_out) {
+    if (!m || !n_out || (cap > 0 && (!cells || !tol))) return fail(TRIME_EINVAL, "NULL argument");
+    if (m->batched) return fail(TRIME_EINVAL, "single meshes only");
+    if (!(fac_etol >= 0.0) || !std::isfinite(fac_etol)) return fail(TRIME_EINVAL, "fac_etol must be finite, >= 0");
+    const Part& p = m->parts[0];
+    size_t nc = (size_t)(p.sdf.nx - 1) * (size_t)(p.sdf.ny - 1);
+    std::vector<uint8_t> cls(nc);
+    std::vector<double> geps(nc);
+    int rc = sync_in(m);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(cls.data(), p.gcls, nc, cudaMemcpyDeviceToHost, m->st));
+    CUDA_TRY(cudaMemcpyAsync(geps.data(), p.ggeps, nc * sizeof(double), cudaMemcpyDeviceToHost, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    if ((rc = sync_out(m))) return rc;
+    // Sec. 3.7: E_tol,i = fac_Etol geps_i fac_pt with fac_pt = sqrt(N_current / N_total)
+    double fac_pt = std::sqrt((double)p.n / (double)std::max<int64_t>(m->ncap, 1));
+    int64_t n = 0;
+    for (size_t c = 0; c < nc; c++) {
+        if (cls[c] != CELL_BOUNDARY) continue;
+        if (n < cap) {
+            cells[n] = (int32_t)c;
+            tol[n] = fac_etol * geps[c] * fac_pt;
+        }
+        n++;
+    }
+    *n_out = n;
+    if (n > cap) return fail(TRIME_ECAPACITY, "ADF cell buffers too small");
+    return TRIME_OK;
+}
+
 int mesh_get_triangles(mesh_t* m, int32_t* tri, int64_t cap, int64_t* n_out) {
     if (!m || !n_out) return fail(TRIME_EINVAL, "NULL argument");
     return get_triangles(m, 0, tri, cap, n_out);

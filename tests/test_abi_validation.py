@@ -107,3 +107,34 @@ def test_init_points_invalid_arguments(g):
     assert g.lib().mesh_init_points(C.byref(gs), C.byref(gz), 0, 1, None, None, 0, C.byref(n), None) == g.TRIME_EINVAL
     gneg, c = g._grid(W.constant_grid(-1.0))
     assert g.lib().mesh_init_points(C.byref(gs), C.byref(gneg), 10, 1, None, None, 0, C.byref(n), None) == g.TRIME_EINVAL
+
+
+def test_adf_invalid_arguments(g):
+    L = g.lib()
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int32)
+    sq = np.ascontiguousarray([[-0.5, -0.5], [-0.5, 0.5], [0.5, 0.5], [0.5, -0.5]], dtype=np.float64)
+    cells = np.array([0, 5, 9], np.int32)
+    tol = np.full(3, 1e-4)
+    h = C.c_void_p()
+
+    def build(v=sq, nv=4, box=(-1.0, -1.0, 1.0, 1.0), n=9, c=cells, t=tol, depth=10):
+        return L.mesh_adf_build(v.ctypes.data_as(dp), nv, *box, n, n, c.ctypes.data_as(ip), t.ctypes.data_as(dp),
+                                len(c), depth, C.byref(h), None)
+
+    assert build(nv=2) == g.TRIME_EINVAL
+    assert build(box=(1.0, -1.0, -1.0, 1.0)) == g.TRIME_EINVAL
+    assert build(depth=15) == g.TRIME_EINVAL and "max_depth" in g.mesh_last_error()
+    assert build(c=np.array([0, 5, 5], np.int32)) == g.TRIME_EINVAL and "distinct" in g.mesh_last_error()
+    assert build(c=np.array([0, 5, 64], np.int32)) == g.TRIME_EINVAL  # 8 x 8 cells
+    assert build(t=np.array([1e-4, -1.0, 1e-4])) == g.TRIME_EINVAL
+    bad = sq.copy()
+    bad[1, 0] = np.inf
+    assert build(v=bad) == g.TRIME_EINVAL and "finite" in g.mesh_last_error()
+    assert not h.value  # nothing was built
+    pts = np.zeros((4, 2))
+    out = np.zeros(4)
+    assert L.mesh_segment_sdf_points(sq.ctypes.data_as(dp), 2, pts.ctypes.data_as(C.c_void_p), 4,
+                                     out.ctypes.data_as(C.c_void_p), None) == g.TRIME_EINVAL
+    assert L.mesh_adf_eval(None, pts.ctypes.data_as(C.c_void_p), 4, out.ctypes.data_as(C.c_void_p),
+                           None) == g.TRIME_EINVAL
