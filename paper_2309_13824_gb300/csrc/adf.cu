@@ -45,18 +45,19 @@ __global__ void k_adf_cellroot(const int32_t* cells, int32_t ncells, int32_t* ce
     if (r < ncells) cellroot[cells[r]] = r;
 }
 
-__global__ void k_adf_roots(const double* xy, int32_t nv, AdfGrid G, const int32_t* cells, int32_t ncells, double* v,
-                            int32_t* child, int32_t* root, int32_t* lev) {
+__global__ void k_adf_roots(const double* xy, int32_t nv, SegGrid S, const int32_t* cstart, const int32_t* cand,
+                            AdfGrid G, const int32_t* cells, int32_t ncells, double* v, int32_t* child, int32_t* root,
+                            int32_t* lev) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ncells) return;
     double cx0, cy0;
     cell_origin(G, cells[r], cx0, cy0);
     double xa = adf_coord(cx0, G.dx, 0, 0), xb = adf_coord(cx0, G.dx, 1, 0);
     double ya = adf_coord(cy0, G.dy, 0, 0), yb = adf_coord(cy0, G.dy, 1, 0);
-    v[4 * r] = seg_sdf_point(xy, nv, xa, ya);
-    v[4 * r + 1] = seg_sdf_point(xy, nv, xb, ya);
-    v[4 * r + 2] = seg_sdf_point(xy, nv, xa, yb);
-    v[4 * r + 3] = seg_sdf_point(xy, nv, xb, yb);
+    v[4 * r] = seg_sdf_cand(xy, nv, S, cstart, cand, xa, ya);
+    v[4 * r + 1] = seg_sdf_cand(xy, nv, S, cstart, cand, xb, ya);
+    v[4 * r + 2] = seg_sdf_cand(xy, nv, S, cstart, cand, xa, yb);
+    v[4 * r + 3] = seg_sdf_cand(xy, nv, S, cstart, cand, xb, yb);
     child[r] = -1;
     root[r] = r;
     lev[3 * r] = lev[3 * r + 1] = lev[3 * r + 2] = 0;
@@ -64,9 +65,9 @@ __global__ void k_adf_roots(const double* xy, int32_t nv, AdfGrid G, const int32
 
 // nodes [lo, lo + count) of level L: exact distances at the bottom, top,
 // left, right midpoints and the centre; split flag
-__global__ void k_adf_test(const double* xy, int32_t nv, AdfGrid G, const int32_t* cells, const double* tol,
-                           const double* v, const int32_t* root, const int32_t* lev, int64_t lo, int32_t count,
-                           int32_t* flag, double* s5) {
+__global__ void k_adf_test(const double* xy, int32_t nv, SegGrid S, const int32_t* cstart, const int32_t* cand,
+                           AdfGrid G, const int32_t* cells, const double* tol, const double* v, const int32_t* root,
+                           const int32_t* lev, int64_t lo, int32_t count, int32_t* flag, double* s5) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
     int64_t n = lo + k;
@@ -78,11 +79,11 @@ __global__ void k_adf_test(const double* xy, int32_t nv, AdfGrid G, const int32_
     double ya = adf_coord(cy0, G.dy, 2 * iy, L + 1), ym = adf_coord(cy0, G.dy, 2 * iy + 1, L + 1);
     double yb = adf_coord(cy0, G.dy, 2 * iy + 2, L + 1);
     double s[5];
-    s[0] = seg_sdf_point(xy, nv, xm, ya);
-    s[1] = seg_sdf_point(xy, nv, xm, yb);
-    s[2] = seg_sdf_point(xy, nv, xa, ym);
-    s[3] = seg_sdf_point(xy, nv, xb, ym);
-    s[4] = seg_sdf_point(xy, nv, xm, ym);
+    s[0] = seg_sdf_cand(xy, nv, S, cstart, cand, xm, ya);
+    s[1] = seg_sdf_cand(xy, nv, S, cstart, cand, xm, yb);
+    s[2] = seg_sdf_cand(xy, nv, S, cstart, cand, xa, ym);
+    s[3] = seg_sdf_cand(xy, nv, S, cstart, cand, xb, ym);
+    s[4] = seg_sdf_cand(xy, nv, S, cstart, cand, xm, ym);
     double v00 = v[4 * n], v10 = v[4 * n + 1], v01 = v[4 * n + 2], v11 = v[4 * n + 3];
     double p[5] = {fmul(fadd(v00, v10), 0.5), fmul(fadd(v01, v11), 0.5), fmul(fadd(v00, v01), 0.5),
                    fmul(fadd(v10, v11), 0.5), fmul(fadd(fadd(v00, v10), fadd(v01, v11)), 0.25)};
@@ -270,6 +271,7 @@ extern "C" int mesh_adf_build(const double* xy, int64_t nv, double x0, double y0
     int rc = TRIME_OK;
     int32_t *flag = nullptr, *off = nullptr, *tmp = nullptr;
     double* s5 = nullptr;
+    SegIndex SI;
     int32_t fcap = 0;
     int64_t lo = 0, hi = ncells;
     ADF_TRY(cudaMalloc(&a->xy, sizeof(double) * 2 * (size_t)nv));
@@ -282,11 +284,13 @@ extern "C" int mesh_adf_build(const double* xy, int64_t nv, double x0, double y0
         ADF_TRY(cudaMemcpyAsync(a->tol, tol, sizeof(double) * (size_t)ncells, cudaMemcpyHostToDevice, st));
     }
     ADF_TRY(cudaMemsetAsync(a->cellroot, 0xff, sizeof(int32_t) * (size_t)ncell_all, st));
+    // exact distances from the candidate lists of a segment cell grid over the box
+    if ((rc = seg_index_build(xy, a->xy, nv, x0, y0, x1, y1, &SI, st))) goto done;
     if ((rc = adf_grow(a, std::max<int64_t>(4 * (int64_t)ncells, 1024), st))) goto done;
     if (ncells > 0) {
         k_adf_cellroot<<<(ncells + 255) / 256, 256, 0, st>>>(a->cells, ncells, a->cellroot);
-        k_adf_roots<<<(ncells + 127) / 128, 128, 0, st>>>(a->xy, a->nv, a->G, a->cells, ncells, a->v, a->child,
-                                                         a->root, a->lev);
+        k_adf_roots<<<(ncells + 127) / 128, 128, 0, st>>>(a->xy, a->nv, SI.G, SI.cstart, SI.cand, a->G, a->cells,
+                                                         ncells, a->v, a->child, a->root, a->lev);
         ADF_TRY(cudaGetLastError());
     }
     a->n = ncells;
@@ -304,8 +308,8 @@ extern "C" int mesh_adf_build(const double* xy, int64_t nv, double x0, double y0
             ADF_TRY(cudaMalloc(&tmp, sizeof(int32_t) * ((size_t)fcap / 4096 + 2)));
             ADF_TRY(cudaMalloc(&s5, sizeof(double) * 5 * (size_t)fcap));
         }
-        k_adf_test<<<(count + 127) / 128, 128, 0, st>>>(a->xy, a->nv, a->G, a->cells, a->tol, a->v, a->root, a->lev,
-                                                        lo, count, flag, s5);
+        k_adf_test<<<(count + 127) / 128, 128, 0, st>>>(a->xy, a->nv, SI.G, SI.cstart, SI.cand, a->G, a->cells,
+                                                        a->tol, a->v, a->root, a->lev, lo, count, flag, s5);
         launch_scan(flag, off, count, tmp, st);
         ADF_TRY(cudaGetLastError());
         int32_t nsplit = 0;
@@ -323,6 +327,8 @@ extern "C" int mesh_adf_build(const double* xy, int64_t nv, double x0, double y0
     }
     ADF_TRY(cudaStreamSynchronize(st));
 done:
+    cudaStreamSynchronize(st);
+    seg_index_free(&SI);
     for (void* p : {(void*)flag, (void*)off, (void*)tmp, (void*)s5})
         if (p) cudaFree(p);
     if (rc) {

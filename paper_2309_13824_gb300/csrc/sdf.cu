@@ -30,21 +30,6 @@
 
 namespace trime {
 
-struct SegGrid {
-    double x0, y0, cw, ch;  // cell grid origin and cell size
-    int32_t gx, gy;
-    double diag;
-};
-
-__device__ __forceinline__ int cell_x(const SegGrid& G, double x) {
-    double f = floor((x - G.x0) / G.cw);
-    return f < 0.0 ? 0 : (f > (double)(G.gx - 1) ? G.gx - 1 : (int)f);
-}
-__device__ __forceinline__ int cell_y(const SegGrid& G, double y) {
-    double f = floor((y - G.y0) / G.ch);
-    return f < 0.0 ? 0 : (f > (double)(G.gy - 1) ? G.gy - 1 : (int)f);
-}
-
 // segment k's bounding box in cells
 __device__ __forceinline__ void seg_cells(const double* xy, int32_t nv, int32_t k, const SegGrid& G, int& i0, int& i1,
                                           int& j0, int& j1) {
@@ -154,24 +139,7 @@ __global__ void k_sdf_nodes(const double* xy, int32_t nv, SegGrid G, const int32
     if (q >= (int64_t)nx * ny) return;
     int i = (int)(q % nx), j = (int)(q / nx);
     double x = fadd(gx0, fmul((double)i, gdx)), y = fadd(gy0, fmul((double)j, gdy));
-    int c = cell_y(G, y) * G.gx + cell_x(G, x);
-    double best = INFINITY, bt = 0.0;
-    int bk = 0x7fffffff;
-    for (int u = cstart[c]; u < cstart[c + 1]; u++) {
-        int k = cand[u];
-        double d, t;
-        seg_dist(xy, nv, k, x, y, d, t);
-        if (d < best || (d == best && k < bk)) {
-            best = d;
-            bk = k;
-            bt = t;
-        }
-    }
-    if (bk >= nv) {  // no candidate (cannot happen: the closest segment always is one)
-        out[q] = __int_as_float(0x7fc00000);
-        return;
-    }
-    out[q] = __double2float_rn(seg_signed(xy, nv, bk, bt, best, x, y));
+    out[q] = __double2float_rn(seg_sdf_cand(xy, nv, G, cstart, cand, x, y));
 }
 
 }  // namespace trime
@@ -187,23 +155,22 @@ using namespace trime;
         }                                                                                   \
     } while (0)
 
-extern "C" int mesh_segment_sdf_grid(const double* xy, int64_t nv, double x0, double y0, double x1, double y1,
-                                     int32_t nx, int32_t ny, float* out, void* cuda_stream) {
-    if (!xy || !out) return set_error(TRIME_EINVAL, "NULL pointer");
-    if (nv < 3 || nv > (int64_t)1 << 26) return set_error(TRIME_EINVAL, "need 3 .. 2^26 vertices");
-    if (nx < 2 || ny < 2 || (int64_t)nx * ny > ((int64_t)1 << 31) - 1)
-        return set_error(TRIME_EINVAL, "grid must have 2 .. 2^31 nodes, at least 2 per side");
-    if (!(x1 > x0) || !(y1 > y0) || !std::isfinite(x0) || !std::isfinite(x1) || !std::isfinite(y0) ||
-        !std::isfinite(y1))
-        return set_error(TRIME_EINVAL, "bad grid box");
+namespace trime {
+
+void seg_index_free(SegIndex* s) {
+    for (void* p : {(void*)s->cnt, (void*)s->start, (void*)s->cur, (void*)s->list, (void*)s->tmp, (void*)s->ncand,
+                    (void*)s->cstart, (void*)s->cand, (void*)s->rad})
+        if (p) cudaFree(p);
+    *s = SegIndex{};
+}
+
+int seg_index_build(const double* xy, const double* dxy, int64_t nv, double x0, double y0, double x1, double y1,
+                    SegIndex* out, cudaStream_t st) {
+    *out = SegIndex{};
     double perim = 0.0;
     for (int64_t k = 0; k < nv; k++) {
         int64_t k1 = k + 1 == nv ? 0 : k + 1;
-        if (!std::isfinite(xy[2 * k]) || !std::isfinite(xy[2 * k + 1]))
-            return set_error(TRIME_EINVAL, "vertices must be finite");
-        double L = std::hypot(xy[2 * k1] - xy[2 * k], xy[2 * k1 + 1] - xy[2 * k + 1]);
-        if (!(L > 0.0)) return set_error(TRIME_EINVAL, "zero-length segment");
-        perim += L;
+        perim += std::hypot(xy[2 * k1] - xy[2 * k], xy[2 * k1 + 1] - xy[2 * k + 1]);
     }
     // cells about the mean segment length (Sec. 3.1), at most 2^22 of them
     double lbar = perim / (double)nv, W = x1 - x0, H = y1 - y0;
@@ -227,41 +194,30 @@ extern "C" int mesh_segment_sdf_grid(const double* xy, int64_t nv, double x0, do
         entries += w * h;
     }
     if (entries > (int64_t)1 << 30) return set_error(TRIME_EINVAL, "segments cover too many cells");
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     int rc = TRIME_OK;
+    SegIndex& S = *out;
+    S.G = G;
     std::vector<int32_t> hc;
     int32_t ncell = G.gx * G.gy;
-    size_t nn = (size_t)nx * (size_t)ny;
-    double* dxy = nullptr;
-    int32_t *cnt = nullptr, *start = nullptr, *cur = nullptr, *list = nullptr, *tmp = nullptr;
-    int32_t *ncand = nullptr, *cstart = nullptr, *cand = nullptr;
-    double* rad = nullptr;
-    float* dout = nullptr;
     int32_t total = 0, ctotal = 0;
-    cudaPointerAttributes at;
-    bool dev_out = cudaPointerGetAttributes(&at, out) == cudaSuccess &&
-                   (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
-    cudaGetLastError();
-    SDF_TRY(cudaMalloc(&dxy, sizeof(double) * 2 * (size_t)nv));
-    SDF_TRY(cudaMalloc(&cnt, sizeof(int32_t) * ncell));
-    SDF_TRY(cudaMalloc(&start, sizeof(int32_t) * ((size_t)ncell + 1)));
-    SDF_TRY(cudaMalloc(&cur, sizeof(int32_t) * ncell));
-    SDF_TRY(cudaMalloc(&tmp, sizeof(int32_t) * ((size_t)ncell / 4096 + 2)));
-    SDF_TRY(cudaMalloc(&ncand, sizeof(int32_t) * ncell));
-    SDF_TRY(cudaMalloc(&cstart, sizeof(int32_t) * ((size_t)ncell + 1)));
-    SDF_TRY(cudaMalloc(&rad, sizeof(double) * ncell));
-    SDF_TRY(cudaMemcpyAsync(dxy, xy, sizeof(double) * 2 * (size_t)nv, cudaMemcpyHostToDevice, st));
-    SDF_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ncell, st));
-    SDF_TRY(cudaMemsetAsync(cur, 0, sizeof(int32_t) * ncell, st));
-    k_seg_count<<<(int)((nv + 255) / 256), 256, 0, st>>>(dxy, (int32_t)nv, G, cnt);
-    launch_scan(cnt, start, ncell, tmp, st);
-    SDF_TRY(cudaMemcpyAsync(&total, start + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SDF_TRY(cudaMalloc(&S.cnt, sizeof(int32_t) * ncell));
+    SDF_TRY(cudaMalloc(&S.start, sizeof(int32_t) * ((size_t)ncell + 1)));
+    SDF_TRY(cudaMalloc(&S.cur, sizeof(int32_t) * ncell));
+    SDF_TRY(cudaMalloc(&S.tmp, sizeof(int32_t) * ((size_t)ncell / 4096 + 2)));
+    SDF_TRY(cudaMalloc(&S.ncand, sizeof(int32_t) * ncell));
+    SDF_TRY(cudaMalloc(&S.cstart, sizeof(int32_t) * ((size_t)ncell + 1)));
+    SDF_TRY(cudaMalloc(&S.rad, sizeof(double) * ncell));
+    SDF_TRY(cudaMemsetAsync(S.cnt, 0, sizeof(int32_t) * ncell, st));
+    SDF_TRY(cudaMemsetAsync(S.cur, 0, sizeof(int32_t) * ncell, st));
+    k_seg_count<<<(int)((nv + 255) / 256), 256, 0, st>>>(dxy, (int32_t)nv, G, S.cnt);
+    launch_scan(S.cnt, S.start, ncell, S.tmp, st);
+    SDF_TRY(cudaMemcpyAsync(&total, S.start + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     SDF_TRY(cudaStreamSynchronize(st));
-    SDF_TRY(cudaMalloc(&list, sizeof(int32_t) * std::max<int32_t>(total, 1)));
-    k_seg_fill<<<(int)((nv + 255) / 256), 256, 0, st>>>(dxy, (int32_t)nv, G, start, cur, list);
-    k_cell_count<<<(ncell + 127) / 128, 128, 0, st>>>(dxy, (int32_t)nv, G, start, list, rad, ncand);
+    SDF_TRY(cudaMalloc(&S.list, sizeof(int32_t) * std::max<int32_t>(total, 1)));
+    k_seg_fill<<<(int)((nv + 255) / 256), 256, 0, st>>>(dxy, (int32_t)nv, G, S.start, S.cur, S.list);
+    k_cell_count<<<(ncell + 127) / 128, 128, 0, st>>>(dxy, (int32_t)nv, G, S.start, S.list, S.rad, S.ncand);
     hc.resize(ncell);
-    SDF_TRY(cudaMemcpyAsync(hc.data(), ncand, sizeof(int32_t) * ncell, cudaMemcpyDeviceToHost, st));
+    SDF_TRY(cudaMemcpyAsync(hc.data(), S.ncand, sizeof(int32_t) * ncell, cudaMemcpyDeviceToHost, st));
     SDF_TRY(cudaStreamSynchronize(st));
     {
         int64_t sum = 0;
@@ -271,23 +227,60 @@ extern "C" int mesh_segment_sdf_grid(const double* xy, int64_t nv, double x0, do
             goto done;
         }
     }
-    launch_scan(ncand, cstart, ncell, tmp, st);
-    SDF_TRY(cudaMemcpyAsync(&ctotal, cstart + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    launch_scan(S.ncand, S.cstart, ncell, S.tmp, st);
+    SDF_TRY(cudaMemcpyAsync(&ctotal, S.cstart + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     SDF_TRY(cudaStreamSynchronize(st));
-    SDF_TRY(cudaMalloc(&cand, sizeof(int32_t) * std::max<int32_t>(ctotal, 1)));
-    k_cell_fill<<<(ncell + 127) / 128, 128, 0, st>>>(dxy, (int32_t)nv, G, start, list, rad, cstart, cand);
+    SDF_TRY(cudaMalloc(&S.cand, sizeof(int32_t) * std::max<int32_t>(ctotal, 1)));
+    k_cell_fill<<<(ncell + 127) / 128, 128, 0, st>>>(dxy, (int32_t)nv, G, S.start, S.list, S.rad, S.cstart, S.cand);
+    SDF_TRY(cudaGetLastError());
+done:
+    if (rc) seg_index_free(out);
+    return rc;
+}
+
+}  // namespace trime
+
+extern "C" int mesh_segment_sdf_grid(const double* xy, int64_t nv, double x0, double y0, double x1, double y1,
+                                     int32_t nx, int32_t ny, float* out, void* cuda_stream) {
+    if (!xy || !out) return set_error(TRIME_EINVAL, "NULL pointer");
+    if (nv < 3 || nv > (int64_t)1 << 26) return set_error(TRIME_EINVAL, "need 3 .. 2^26 vertices");
+    if (nx < 2 || ny < 2 || (int64_t)nx * ny > ((int64_t)1 << 31) - 1)
+        return set_error(TRIME_EINVAL, "grid must have 2 .. 2^31 nodes, at least 2 per side");
+    if (!(x1 > x0) || !(y1 > y0) || !std::isfinite(x0) || !std::isfinite(x1) || !std::isfinite(y0) ||
+        !std::isfinite(y1))
+        return set_error(TRIME_EINVAL, "bad grid box");
+    for (int64_t k = 0; k < nv; k++) {
+        int64_t k1 = k + 1 == nv ? 0 : k + 1;
+        if (!std::isfinite(xy[2 * k]) || !std::isfinite(xy[2 * k + 1]))
+            return set_error(TRIME_EINVAL, "vertices must be finite");
+        double L = std::hypot(xy[2 * k1] - xy[2 * k], xy[2 * k1 + 1] - xy[2 * k + 1]);
+        if (!(L > 0.0)) return set_error(TRIME_EINVAL, "zero-length segment");
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc = TRIME_OK;
+    size_t nn = (size_t)nx * (size_t)ny;
+    double* dxy = nullptr;
+    float* dout = nullptr;
+    SegIndex S;
+    cudaPointerAttributes at;
+    bool dev_out = cudaPointerGetAttributes(&at, out) == cudaSuccess &&
+                   (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    SDF_TRY(cudaMalloc(&dxy, sizeof(double) * 2 * (size_t)nv));
+    SDF_TRY(cudaMemcpyAsync(dxy, xy, sizeof(double) * 2 * (size_t)nv, cudaMemcpyHostToDevice, st));
+    if ((rc = seg_index_build(xy, dxy, nv, x0, y0, x1, y1, &S, st))) goto done;
     if (dev_out) dout = out;
     else SDF_TRY(cudaMalloc(&dout, sizeof(float) * nn));
-    k_sdf_nodes<<<(int)((nn + 255) / 256), 256, 0, st>>>(dxy, (int32_t)nv, G, cstart, cand, x0, y0,
+    k_sdf_nodes<<<(int)((nn + 255) / 256), 256, 0, st>>>(dxy, (int32_t)nv, S.G, S.cstart, S.cand, x0, y0,
                                                          (x1 - x0) / (double)(nx - 1), (y1 - y0) / (double)(ny - 1),
                                                          nx, ny, dout);
     SDF_TRY(cudaGetLastError());
     if (!dev_out) SDF_TRY(cudaMemcpyAsync(out, dout, sizeof(float) * nn, cudaMemcpyDeviceToHost, st));
     SDF_TRY(cudaStreamSynchronize(st));
 done:
-    for (void* p : {(void*)dxy, (void*)cnt, (void*)start, (void*)cur, (void*)list, (void*)tmp, (void*)ncand,
-                    (void*)cstart, (void*)cand, (void*)rad})
-        if (p) cudaFree(p);
+    cudaStreamSynchronize(st);
+    seg_index_free(&S);
+    if (dxy) cudaFree(dxy);
     if (dout && !dev_out) cudaFree(dout);
     return rc;
 }
