@@ -810,8 +810,9 @@ void launch_voronoi_big(const IterArgs<T>& a, int32_t n, float4* scratch, int32_
     if (n > 0) k_voronoi_big<T><<<(n + 31) / 32, 32, 0, st>>>(a, n, scratch, rings, lens);
 }
 
-// lanes = 16: two cells per warp plus the 32-lane pass; lanes = 32: one cell
-// per warp
+// lanes = 8: four cells per warp, then the 16- and 32-lane passes for the
+// queued cells; lanes = 16: two cells per warp plus the 32-lane pass;
+// lanes = 32: one cell per warp.  The serial pass follows in every case.
 template <typename T, bool B>
 void launch_voronoi_impl(const IterArgs<T>& a, int lanes, cudaStream_t st) {
     cudaMemsetAsync(a.ovf_n, 0, 4 * sizeof(int32_t), st);
