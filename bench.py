@@ -29,8 +29,14 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpoints/s per meshing iteration at 1e6 pts; wall time to quality at 1e6 pts"
 WORKLOAD = ("annulus r in [0.3,1], 1024^2 FP32 SDF, sizing 0.002+0.05|sdf| on 512^2, "
             "1e6 points ~ 1/h^2 (seed 1), hybrid DistMesh->CVD")
-VORONOI_FLOP_PER_CELL = 2500.0  # algorithmic flops of one cell's clipping
+VORONOI_FLOP_PER_CELL = 2500.0  # algorithmic flops of one cell's clipping: ~30 distance tests, ~8 cuts, ~60 predicates
 L2_FLUSH_BYTES = 256 << 20
+# FP64 mode keeps every decision (emission, validity, predicates' filters,
+# point treatment) in FP64 and evaluates the moves' sums in float-float
+# (pairs of f32, ~48 bits); FP32 mode holds positions, forces and centroids in
+# f32 with the same FP64/exact decisions
+DTYPE = {0: "f64 decisions, float-float (2xf32) moves", 1: "f32 positions, f64/exact decisions"}
+PRECISION = {0: "fp64 decisions, float-float moves", 1: "fp32 positions, fp64/exact predicates"}
 
 
 def parse():
@@ -409,8 +415,8 @@ def adf_measure(g, torch, m, v, sg):
 
 
 def polygon_leg(g, torch, stream):
-    """From a polygon to a mesh with the initialisation pipeline (survey rows
-    f3, f4): the benchmark star (500 clockwise segments) -> its SDF grid and
+    """From a polygon to a mesh with the initialisation pipeline (segment SDF,
+    automatic sizing, dithered initial points): the benchmark star (500 clockwise segments) -> its SDF grid and
     automatic sizing field on 1024^2 (App. A, Sec. 3.3, Eq. 7, K = 0.1) ->
     10^6 dithered initial points (Sec. 3.5) -> hybrid meshing (FP32 positions)
     until termination.  Host clock around synchronous calls."""
@@ -645,6 +651,8 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
+    step_stats = {"median_ms": float(np.median(step_ms)), "min_ms": float(min(step_ms)),
+                  "max_ms": float(max(step_ms)), "mean_ms": float(np.mean(step_ms))}
     st = mesh.step(0)
     value, total_s = replica_value(n, args.steps, total_s, dist, device="cuda")
 
@@ -758,14 +766,14 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32",
-                "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+                "data": "synthetic", "step_ms": step_stats,
                 "config": {"workload": WORKLOAD, "points": n, "method": ["dm", "cvd", "hybrid"][args.method],
-                           "precision": ["fp64", "fp32"][args.precision],
+                           "precision": PRECISION[args.precision],
                            "l2": "flushed before every timed step (256 MB write)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 16 * args.steps,  # kernels in the iteration graph
+                "gpu_launches": 17 * args.steps,  # 16 kernels of the iteration graph + the counter reset
                 "last_step": {"method": st["method"], "switched": st["switched"], "n_tri": st["n_tri"],
                               "half_mean_alpha": st["half_mean_alpha"]}}
         line.update(extras)

@@ -140,11 +140,13 @@ int mesh_rebuild(mesh_t* m, mesh_stats* stats);
 
 /* Run up to n_iters meshing iterations (Algorithms 1-2; hybrid Sec. 4.2),
  * each one graph launch: rebuild, quality, hybrid/termination decision, move,
- * point treatment (Sec. 4.3).  Stops early once a termination criterion of
- * Sec. 4 holds (checked on the host every 32 iterations; later iterations are
- * device-side no-ops).  With stats != NULL synchronises at the end, fills
- * *stats and returns TRIME_EDEVICE if a capacity guard tripped; with
- * stats == NULL the call is asynchronous on the caller's stream.
+ * point treatment (Sec. 4.3).  Once a termination criterion of Sec. 4 holds
+ * the later iterations are device-side no-ops.  With stats != NULL the host
+ * also checks for termination every 32 iterations (and stops launching),
+ * synchronises at the end, fills *stats and returns TRIME_EDEVICE if a
+ * capacity guard tripped.  With stats == NULL (and no point addition pending,
+ * below) the call only enqueues the n_iters launches on the caller's stream
+ * and never waits for the device.
  * While N_current < N_total (point addition, Sec. 3.6) the hybrid switch and
  * the termination tests are not evaluated; an iteration whose 1/2-means of
  * alpha and beta both changed by less than T_add since the previous one

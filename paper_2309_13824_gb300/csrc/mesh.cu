@@ -957,8 +957,17 @@ static int do_step(mesh_s* m, int32_t n_iters, mesh_stats* stats) {
     int rc = sync_in(m);
     if (rc) return rc;
     if ((rc = reset_counters(m))) return rc;
-    if ((rc = read_ctrl(m))) return rc;
     m->added_call = 0;
+    if (!stats && !growing(m) && !m->tri_stale) {
+        // asynchronous: only enqueue.  A mesh that has terminated (on the
+        // device, possibly in an iteration still in flight) turns every later
+        // launch of the graph into empty kernels, so no host read is needed.
+        // (A stale sorted order needs the host to know whether an iteration
+        // will re-triangulate, so that case takes the synchronous path.)
+        for (int32_t k = 0; k < n_iters; k++) CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
+        return sync_out(m);
+    }
+    if ((rc = read_ctrl(m))) return rc;
     // a pause left by an asynchronous call
     if (!m->batched && m->hctrl[0].terminated == 2 && (rc = add_points(m))) return rc;
     size_t np = m->parts.size();
@@ -987,7 +996,7 @@ static int do_step(mesh_s* m, int32_t n_iters, mesh_stats* stats) {
             }
         }
     }
-    if (!stats) return sync_out(m);  // asynchronous: no read-back
+    if (!stats) return sync_out(m);  // a growing mesh without stats: no final read-back
     if ((rc = read_ctrl(m))) return rc;
     if ((rc = sync_out(m))) return rc;
     for (size_t k = 0; k < np; k++) fill_stats(m, (int)k, m->hctrl[k].iterations - start[k], &stats[k]);
