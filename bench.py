@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--points", type=int, default=1_000_000)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--method", type=int, default=2)
-    ap.add_argument("--no-extras", action="store_true", help="skip time-to-quality / FP32 / CPU legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the legs beyond the headline iteration")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--n-opt", type=float, default=None, help="points per neighbour bucket (default 3.3)")
     ap.add_argument("--sweep", action="store_true",
                     help="add the N sweep (annulus 1e4..1e7, square 1e6) and the 1e7-point star "
@@ -65,29 +66,70 @@ def dist_env():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons during the timed region."""
+    """nvidia-smi clocks and throttle reasons during the timed region: rows
+    every 20 ms carry nvidia-smi's own timestamp, and only the rows inside
+    the window marked by mark_start()/mark_stop() count (the rows nearest to
+    it when the window is shorter than the sampling period)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.f = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # the first rows are written before the timed region starts
         except Exception:
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def parse(rows, t0=None, t1=None):
+        """Median SM clock, max clock and active throttle reasons of the rows
+        (lists of fields) whose timestamp lies in [t0, t1]."""
+        import datetime
+
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        recs = []
+        for r in rows:
+            try:
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                recs.append((ts, float(r[2]), float(r[3]),
+                             [n for k, n in enumerate(names) if r[6 + k].strip().lower() == "active"]))
+            except (ValueError, IndexError):
+                continue
+        if t0 is not None and t1 is not None and recs:
+            inside = [x for x in recs if t0 <= x[0] <= t1]
+            if not inside:  # a window shorter than the period: the nearest row on each side
+                before = [x for x in recs if x[0] < t0]
+                after = [x for x in recs if x[0] > t1]
+                inside = before[-1:] + after[:1]
+            recs = inside
+        sm = [x[1] for x in recs]
+        reasons = sorted({n for x in recs for n in x[3]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(x[2] for x in recs) if recs else None,
+                "reasons": reasons, "samples": len(sm)}
 
     def stop(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(2 * self.PERIOD_MS / 1e3)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -97,19 +139,9 @@ class ClockSampler:
         self.f.seek(0)
         rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
         os.unlink(self.f.name)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-                for k, name in enumerate(names):
-                    if r[5 + k].strip().lower() == "active":
-                        reasons.add(name)
-            except (ValueError, IndexError):
-                continue
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = self.parse(rows, self.t0, self.t1)
+        out["period_ms"] = self.PERIOD_MS
+        return out
 
 
 # ------------------------------------------------------------------ helpers
@@ -194,28 +226,44 @@ def oracle_sample_rate(wl, target_s, max_cells=None, threads=1, om=None):
     return cnt, time.perf_counter() - t, om
 
 
+def oracle_iterations(wl, threads, steps, om=None):
+    """Full oracle meshing iterations (om_step: bucketing, every cell's clip,
+    emission with Tests 1-3, quality, hybrid switch, DistMesh forces or CVD
+    centroids, point treatment) of the whole workload, the per-cell loops on
+    `threads` OpenMP threads.  Returns (seconds per iteration list, oracle
+    mesh); the mesh carries on along its own trajectory."""
+    import oracle
+
+    oracle.build()
+    if om is None:
+        om = oracle.OracleMesh(wl.sdf, wl.sizing, wl.points, method=wl.method)
+    om.set_threads(threads)
+    times = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        om.step()
+        times.append(time.perf_counter() - t)
+    return times, om
+
+
 def run_reference(args, wl):
+    """The oracle as the reference arm: each step is one full FP64 meshing
+    iteration of the whole workload on all host cores."""
     world, rank, local = dist_env()
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    cells_per_step = 30000 * threads
-    om = None
-    for _ in range(args.warmup):
-        _, _, om = oracle_sample_rate(wl, 0.0, max_cells=2000, threads=threads, om=om)
-    times = []
-    cnt_total = 0
-    for _ in range(args.steps):
-        cnt, dt, om = oracle_sample_rate(wl, 1e9, max_cells=cells_per_step, threads=threads, om=om)
-        times.append(dt)
-        cnt_total += cnt
-    v = cnt_total / sum(times) / 1e6
-    sample = (f"{cells_per_step} random cells of the 1e6-point workload per step: cell clipping, owned triangles "
-              f"with Tests 1-3 and CVD centroid (FP64 oracle, OpenMP over {threads} threads)")
+    _, om = oracle_iterations(wl, threads, args.warmup)
+    times, om = oracle_iterations(wl, threads, args.steps, om)
+    n = len(wl.points)
+    v = n * args.steps / sum(times) / 1e6
+    sample = (f"full meshing iterations of the {n}-point workload (FP64 oracle om_step: cells, emission with "
+              f"Tests 1-3, quality, hybrid switch, move, point treatment), per-cell loops on {threads} OpenMP "
+              f"threads, iterations {args.warmup + 1}..{args.warmup + args.steps} of the trajectory")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpts/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "points": len(wl.points)},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "points": n},
             "cpu_baseline": {"value": v, "unit": "Mpts/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -640,12 +688,14 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark_start()
     for k in range(args.steps):
         flush_l2(flush)
         ev[k][0].record(stream)
         mesh.step_async(1)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    clocks.mark_stop()
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -753,15 +803,22 @@ def main():
         extras["point_addition"] = addition_leg(g, torch, stream)
         extras["segment_sdf"] = segment_sdf_leg(g, torch, stream)
         extras["from_polygon"] = polygon_leg(g, torch, stream)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # the oracle on the host cores beside the device numbers (N = 1 only)
         threads = os.cpu_count() or 1
-        cnt, dt, om = oracle_sample_rate(wl, 10.0, threads=threads)
-        cnt1, dt1, _ = oracle_sample_rate(wl, 5.0, threads=1, om=om)
-        extras["cpu_baseline"] = {"value": cnt / dt / 1e6, "unit": "Mpts/s", "cores": threads, "kind": "oracle",
-                                  "sample": f"{cnt} random cells of the workload: cell clipping, owned triangles "
-                                            f"with Tests 1-3, CVD centroid; FP64 oracle on {threads} OpenMP "
-                                            f"threads ({dt:.1f} s)",
-                                  "value_1_thread": cnt1 / dt1 / 1e6,
-                                  "sample_1_thread": f"{cnt1} random cells, one thread ({dt1:.1f} s)"}
+        n = len(wl.points)
+        tm, om = oracle_iterations(wl, threads, 3)
+        t1, _ = oracle_iterations(wl, 1, 1, om)
+        cnt, dt, _ = oracle_sample_rate(wl, 5.0, threads=threads)
+        extras["cpu_baseline"] = {
+            "value": n * len(tm) / sum(tm) / 1e6, "unit": "Mpts/s", "cores": threads, "kind": "oracle",
+            "sample": f"3 full meshing iterations (1-3) of the {n}-point workload: FP64 oracle om_step, per-cell "
+                      f"loops on {threads} OpenMP threads ({sum(tm):.1f} s)",
+            "value_1_thread": n / t1[0] / 1e6,
+            "sample_1_thread": f"iteration 4 of the same trajectory on one thread ({t1[0]:.1f} s)",
+            "per_cell_only": {"value": cnt / dt / 1e6, "unit": "Mpts/s",
+                              "sample": f"{cnt} random cells: clip, owned triangles with Tests 1-3, CVD centroid "
+                                        f"(no bucketing, sorting, quality, forces or treatment), {threads} threads"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world, "steps": args.steps,

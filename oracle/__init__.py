@@ -78,6 +78,7 @@ def _load():
         for name in ("om_rebuild", "om_step"):
             getattr(lib, name).argtypes = [C.c_void_p]
         lib.om_rebuild_sample.argtypes = [C.c_void_p, i64p, C.c_int64, C.c_int]
+        lib.om_set_threads.argtypes = [C.c_void_p, C.c_int]
         lib.om_rebuild_sample_mt.restype = C.c_int64
         lib.om_rebuild_sample_mt.argtypes = [C.c_void_p, i64p, C.c_int64, C.c_int, C.c_int]
         lib.om_sample_triangles.restype = C.c_int64
@@ -363,6 +364,11 @@ class OracleMesh:
         if getattr(self, "_h", None):
             self._lib.om_destroy(self._h)
             self._h = None
+
+    def set_threads(self, threads: int):
+        """OpenMP threads for the per-cell loops of rebuild()/step() (results
+        are those of one thread)."""
+        self._lib.om_set_threads(self._h, int(threads))
 
     def rebuild(self):
         self._lib.om_rebuild(self._h)

@@ -11,6 +11,7 @@
 #include "trime_oracle.h"
 
 #include <math.h>
+#include <omp.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -372,6 +373,7 @@ struct om_mesh {
     int switched, have_prev;
     double prev_a, prev_b, prev_amax;
     int64_t clip_errors;
+    int threads;               /* OpenMP threads of the per-cell loops (results do not depend on it) */
 };
 
 void om_default_params(om_params* p) {
@@ -523,6 +525,7 @@ om_mesh* om_create(const om_grid* sdf, const om_grid* sizing, const double* xy, 
     m->tx = (double*)calloc(nn, sizeof(double));
     m->ty = (double*)calloc(nn, sizeof(double));
     m->retri = 1;
+    m->threads = 1;
     if (!m->x || !m->y || !m->cls || !m->dprev || !m->pnew || !m->force || !m->fsum || !m->cen || !m->area ||
         !m->qlevel || !m->ring_off || !m->tx || !m->ty) { set_err("out of memory"); om_destroy(m); return NULL; }
     for (int64_t i = 0; i < n; i++) {
@@ -868,10 +871,60 @@ static int edge_cmp(const void* a, const void* b) {
     return 0;
 }
 
+/* Procedure I over all cells on m->threads threads: thread t clips the
+ * contiguous cells [N t / T, N (t+1) / T) into its own buffer, and the
+ * buffers are concatenated in cell order, so the rings are those of one
+ * thread */
+static void rebuild_all_cells_mt(om_mesh* m, const ogrid_t* G) {
+    int T = m->threads;
+    int32_t** buf = (int32_t**)calloc((size_t)T, sizeof(int32_t*));
+    int64_t* len = (int64_t*)calloc((size_t)T, sizeof(int64_t));
+    int64_t errs = 0;
+#pragma omp parallel num_threads(T) reduction(+ : errs)
+    {
+        int t = omp_get_thread_num();
+        int64_t lo = m->N * t / T, hi = m->N * (t + 1) / T, cap = 8 * (hi - lo) + 64, n = 0;
+        int32_t* b = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+        hp_t E[CELL_CAP];
+        for (int64_t i = lo; i < hi; i++) {
+            int ne = cell_compute(m, G, i, E, &errs);
+            if (n + ne > cap) {
+                cap = 2 * (n + ne);
+                b = (int32_t*)realloc(b, sizeof(int32_t) * (size_t)cap);
+            }
+            for (int k = 0; k < ne; k++) b[n + k] = E[k].lab;
+            n += ne;
+            m->ring_off[i + 1] = ne; /* counts; offsets below */
+        }
+        buf[t] = b;
+        len[t] = n;
+    }
+    int64_t total = 0;
+    for (int t = 0; t < T; t++) total += len[t];
+    free(m->ring);
+    m->ring_cap = total > 0 ? total : 1;
+    m->ring = (int32_t*)malloc(sizeof(int32_t) * (size_t)m->ring_cap);
+    m->ring_off[0] = 0;
+    for (int64_t i = 0; i < m->N; i++) m->ring_off[i + 1] += m->ring_off[i];
+    for (int t = 0; t < T; t++) {
+        int64_t lo = m->N * t / T;
+        memcpy(m->ring + m->ring_off[lo], buf[t], sizeof(int32_t) * (size_t)len[t]);
+        free(buf[t]);
+    }
+    free(buf);
+    free(len);
+    m->clip_errors = errs;
+}
+
 /* Procedure I */
 static int rebuild_cells(om_mesh* m, const int64_t* cells, int64_t ncells, int keep) {
     ogrid_t G;
     ogrid_build(m, &G);
+    if (keep && !cells && m->threads > 1) {
+        rebuild_all_cells_mt(m, &G);
+        ogrid_free(&G);
+        return 0;
+    }
     hp_t E[CELL_CAP];
     int64_t errs = 0;
     int64_t total = 0;
@@ -900,11 +953,10 @@ static int rebuild_cells(om_mesh* m, const int64_t* cells, int64_t ncells, int k
     return 0;
 }
 
-static int emit_triangles(om_mesh* m) {
-    int64_t cap = 2 * m->N + 16, nt = 0;
-    free(m->tri);
-    m->tri = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)cap);
-    for (int64_t i = 0; i < m->N; i++) {
+/* the valid triangles owned (smallest index) by cells [lo, hi), appended
+ * to *tri (capacity *cap, count *nt) */
+static void emit_range(const om_mesh* m, int64_t lo, int64_t hi, int32_t** tri, int64_t* cap, int64_t* nt) {
+    for (int64_t i = lo; i < hi; i++) {
         int64_t o = m->ring_off[i], ne = m->ring_off[i + 1] - o;
         for (int64_t t = 0; t < ne; t++) {
             int32_t j = m->ring[o + t], k = m->ring[o + (t + 1) % ne];
@@ -913,10 +965,44 @@ static int emit_triangles(om_mesh* m) {
             circumcenter_fixed(m->x[i], m->y[i], m->x[j], m->y[j], m->x[k], m->y[k], &ox, &oy, &R);
             if (!(reg_contains(m, i, ox, oy) && reg_contains(m, j, ox, oy) && reg_contains(m, k, ox, oy))) continue;
             if (m->P.validity && !triangle_valid(m, i, j, k)) continue;
-            if (nt == cap) { cap *= 2; m->tri = (int32_t*)realloc(m->tri, sizeof(int32_t) * 3 * (size_t)cap); }
-            m->tri[3 * nt] = (int32_t)i; m->tri[3 * nt + 1] = j; m->tri[3 * nt + 2] = k;
-            nt++;
+            if (*nt == *cap) { *cap *= 2; *tri = (int32_t*)realloc(*tri, sizeof(int32_t) * 3 * (size_t)*cap); }
+            (*tri)[3 * *nt] = (int32_t)i; (*tri)[3 * *nt + 1] = j; (*tri)[3 * *nt + 2] = k;
+            (*nt)++;
         }
+    }
+}
+
+static int emit_triangles(om_mesh* m) {
+    int64_t cap = 2 * m->N + 16, nt = 0;
+    free(m->tri);
+    m->tri = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)cap);
+    if (m->threads > 1) {
+        /* per-thread lists, concatenated; the sort below fixes the order */
+        int T = m->threads;
+        int32_t** buf = (int32_t**)calloc((size_t)T, sizeof(int32_t*));
+        int64_t* cnt = (int64_t*)calloc((size_t)T, sizeof(int64_t));
+#pragma omp parallel num_threads(T)
+        {
+            int t = omp_get_thread_num();
+            int64_t lo = m->N * t / T, hi = m->N * (t + 1) / T, c = 2 * (hi - lo) + 16, n = 0;
+            int32_t* b = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)c);
+            emit_range(m, lo, hi, &b, &c, &n);
+            buf[t] = b;
+            cnt[t] = n;
+        }
+        for (int t = 0; t < T; t++) {
+            if (nt + cnt[t] > cap) {
+                cap = 2 * (nt + cnt[t]);
+                m->tri = (int32_t*)realloc(m->tri, sizeof(int32_t) * 3 * (size_t)cap);
+            }
+            memcpy(m->tri + 3 * nt, buf[t], sizeof(int32_t) * 3 * (size_t)cnt[t]);
+            nt += cnt[t];
+            free(buf[t]);
+        }
+        free(buf);
+        free(cnt);
+    } else {
+        emit_range(m, 0, m->N, &m->tri, &cap, &nt);
     }
     qsort(m->tri, (size_t)nt, 3 * sizeof(int32_t), tri_cmp);
     m->ntri = nt;
@@ -1171,8 +1257,10 @@ int om_get_ring(const om_mesh* m, int64_t i, int32_t* labels, int cap) {
 }
 
 static void cvd_move(om_mesh* m) {
-    double poly[2 * CELL_CAP];
+    int64_t qcap = 0;
+#pragma omp parallel for num_threads(m->threads > 1 ? m->threads : 1) schedule(dynamic, 1024) reduction(+ : qcap)
     for (int64_t i = 0; i < m->N; i++) {
+        double poly[2 * CELL_CAP];
         int n = cell_polygon(m, i, poly, CELL_CAP);
         double gen[2] = {m->x[i], m->y[i]};
         double h = h_at(m, m->x[i], m->y[i]);
@@ -1181,12 +1269,13 @@ static void cvd_move(om_mesh* m) {
         double A = 0;
         int r = n >= 3 ? centroid_adaptive(&m->siz, gen, poly, n, eps_c, m->P.quad_max_level, &m->cen[2 * i], &lv, &A)
                        : (m->cen[2 * i] = gen[0], m->cen[2 * i + 1] = gen[1], 0);
-        if (r == 2) m->st.quad_cap++;
+        if (r == 2) qcap++;
         m->qlevel[i] = lv;
         m->area[i] = A;
         m->pnew[2 * i] = m->cen[2 * i];
         m->pnew[2 * i + 1] = m->cen[2 * i + 1];
     }
+    m->st.quad_cap += qcap;
 }
 
 int om_polygon_centroid(const om_grid* sizing, const double* gen, const double* poly, int nv, double eps_c,
@@ -1471,11 +1560,14 @@ int om_step(om_mesh* m) {
         }
     }
     int small = 1, far = 0;
+    int64_t nfail = 0, tcap = 0;
+#pragma omp parallel for num_threads(m->threads > 1 ? m->threads : 1) schedule(static) \
+    reduction(&& : small) reduction(|| : far) reduction(+ : nfail, tcap)
     for (int64_t i = 0; i < m->N; i++) {
         double po[2] = {m->x[i], m->y[i]}, pf[2];
         int32_t nc;
         int oc = m->cls[i];
-        treat_point(m, po, oc, m->pnew + 2 * i, pf, &nc, &m->st.newton_fail, &m->st.trace_cap);
+        treat_point(m, po, oc, m->pnew + 2 * i, pf, &nc, &nfail, &tcap);
         double mv = hypot(pf[0] - po[0], pf[1] - po[1]);
         if (oc == PT_INNER && !(mv < m->P.fac_end * h_at(m, po[0], po[1]))) small = 0;
         if (m->P.fac_retria > 0 && hypot(pf[0] - m->tx[i], pf[1] - m->ty[i]) > m->P.fac_retria * h_at(m, m->tx[i], m->ty[i]))
@@ -1485,6 +1577,8 @@ int om_step(om_mesh* m) {
         m->y[i] = pf[1];
         m->cls[i] = (uint8_t)nc;
     }
+    m->st.newton_fail += nfail;
+    m->st.trace_cap += tcap;
     m->st.small_moves = small;
     m->st.n_points = m->N;
     m->retri = m->P.method != 0 || !(m->P.fac_retria > 0) || far;
@@ -1590,6 +1684,7 @@ int64_t om_sample_triangles(om_mesh* m, const int64_t* cells, int64_t ncells, in
 /* accessors                                                                */
 /* ------------------------------------------------------------------------ */
 int64_t om_num_points(const om_mesh* m) { return m->N; }
+void om_set_threads(om_mesh* m, int threads) { m->threads = threads > 1 ? threads : 1; }
 int64_t om_num_triangles(const om_mesh* m) { return m->ntri; }
 void om_get_triangles(const om_mesh* m, int32_t* tri) { memcpy(tri, m->tri, sizeof(int32_t) * 3 * (size_t)m->ntri); }
 int64_t om_num_edges(const om_mesh* m) { return m->nedge; }

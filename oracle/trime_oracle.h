@@ -110,6 +110,10 @@ int64_t om_sample_triangles(om_mesh* m, const int64_t* cells, int64_t ncells, in
 int64_t om_rebuild_sample_mt(om_mesh* m, const int64_t* cells, int64_t ncells, int with_centroid, int nthreads);
 
 int64_t om_num_points(const om_mesh* m);
+/* OpenMP threads of the per-cell loops of om_rebuild / om_step (cells,
+ * emission, centroids, point treatment); 1 (the default) runs serially.
+ * Results do not depend on it. */
+void om_set_threads(om_mesh* m, int threads);
 int64_t om_num_triangles(const om_mesh* m);
 void om_get_triangles(const om_mesh* m, int32_t* tri);          /* 3*n_tri, sorted */
 int64_t om_num_edges(const om_mesh* m);

@@ -35,9 +35,9 @@ class _Proc:
 def test_clock_record_parsing():
     s = bench.ClockSampler(0)
     s.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-    s.f.write("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
-              "0, 2055, 2070, 1200.5, 0x4, Not Active, Not Active, Not Active, Active\n"
-              "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+    s.f.write("2026/12/04 12:00:00.000, 0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+              "2026/12/04 12:00:00.020, 0, 2055, 2070, 1200.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+              "2026/12/04 12:00:00.040, 0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
               "garbage line\n")
     s.proc = _Proc()
     rec = s.stop()
@@ -45,3 +45,19 @@ def test_clock_record_parsing():
     assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0
     assert rec["reasons"] == ["sw_power_cap"]
     assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_clock_rows_inside_the_timed_window():
+    import datetime
+
+    def row(t, mhz, cap="Not Active"):
+        ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return [ts, "0", str(mhz), "2070", "1000", "0x0", "Not Active", "Not Active", "Not Active", cap]
+
+    t = 1_800_000_000.0
+    rows = [row(t, 1500, "Active"), row(t + 0.02, 2070), row(t + 0.04, 2060), row(t + 0.06, 1400, "Active")]
+    rec = bench.ClockSampler.parse(rows, t + 0.01, t + 0.05)
+    assert rec["samples"] == 2 and rec["sm_mhz"] == 2065.0 and rec["reasons"] == []
+    # a window between two rows takes the nearest row on each side
+    rec = bench.ClockSampler.parse(rows, t + 0.041, t + 0.045)
+    assert rec["samples"] == 2 and rec["reasons"] == ["sw_power_cap"]
