@@ -1029,6 +1029,36 @@ static int emit_triangles(om_mesh* m) {
     return 0;
 }
 
+/* sum of v[0..n) by pairwise (cascade) summation in index order: the
+ * rounding of the result grows like log2(n) ulps rather than n */
+static double pairwise_sum(const double* v, int64_t n) {
+    if (n <= 8) {
+        double s = 0.0;
+        for (int64_t k = 0; k < n; k++) s += v[k];
+        return s;
+    }
+    int64_t h = n / 2;
+    return pairwise_sum(v, h) + pairwise_sum(v + h, n - h);
+}
+
+/* Eq. 3 over the valid edges at the current positions: fac_mu =
+ * sqrt(sum l^2 / sum mu(m)^2), both sums pairwise in edge order */
+static double eq3_fac_mu(const om_mesh* m) {
+    if (m->nedge <= 0) return 1.0;
+    double* t = (double*)malloc(sizeof(double) * 2 * (size_t)m->nedge);
+    double *tl = t, *tm = t + m->nedge;
+    for (int64_t e = 0; e < m->nedge; e++) {
+        int32_t i = m->edge[2 * e], j = m->edge[2 * e + 1];
+        double dx = m->x[j] - m->x[i], dy = m->y[j] - m->y[i];
+        double mu = bilin(&m->siz, (m->x[i] + m->x[j]) * 0.5, (m->y[i] + m->y[j]) * 0.5);
+        tl[e] = dx * dx + dy * dy;
+        tm[e] = mu * mu;
+    }
+    double f = sqrt(pairwise_sum(tl, m->nedge) / pairwise_sum(tm, m->nedge));
+    free(t);
+    return f;
+}
+
 /* Sec. 3.6 Eq. 11-12 and Sec. 2.2 Eq. 3 */
 static void quality(om_mesh* m) {
     double sa = 0, sb = 0, amax = 0, bmax = 0, minang = 180.0;
@@ -1063,15 +1093,7 @@ static void quality(om_mesh* m) {
     m->st.max_beta = bmax;
     m->st.min_angle_deg = n > 0 ? minang : 0.0;
     /* fac_mu over the valid edges (Eq. 3) */
-    double sl2 = 0, smu2 = 0;
-    for (int64_t e = 0; e < m->nedge; e++) {
-        int32_t i = m->edge[2 * e], j = m->edge[2 * e + 1];
-        double dx = m->x[j] - m->x[i], dy = m->y[j] - m->y[i];
-        double mu = bilin(&m->siz, (m->x[i] + m->x[j]) * 0.5, (m->y[i] + m->y[j]) * 0.5);
-        sl2 += dx * dx + dy * dy;
-        smu2 += mu * mu;
-    }
-    m->st.fac_mu = m->nedge > 0 ? sqrt(sl2 / smu2) : 1.0;
+    m->st.fac_mu = eq3_fac_mu(m);
     double dev = 0;
     for (int64_t e = 0; e < m->nedge; e++) {
         int32_t i = m->edge[2 * e], j = m->edge[2 * e + 1];
@@ -1389,17 +1411,7 @@ int om_project_point(om_mesh* m, const double* p_old, int old_class, const doubl
 /* ------------------------------------------------------------------------ */
 /* Eq. 3 scaling factor over the stored valid edges at the current positions
  * (a DistMesh step that keeps the last triangulation, Algorithm 1) */
-static void fac_mu_current(om_mesh* m) {
-    double sl2 = 0, smu2 = 0;
-    for (int64_t e = 0; e < m->nedge; e++) {
-        int32_t i = m->edge[2 * e], j = m->edge[2 * e + 1];
-        double dx = m->x[j] - m->x[i], dy = m->y[j] - m->y[i];
-        double mu = bilin(&m->siz, (m->x[i] + m->x[j]) * 0.5, (m->y[i] + m->y[j]) * 0.5);
-        sl2 += dx * dx + dy * dy;
-        smu2 += mu * mu;
-    }
-    m->st.fac_mu = m->nedge > 0 ? sqrt(sl2 / smu2) : 1.0;
-}
+static void fac_mu_current(om_mesh* m) { m->st.fac_mu = eq3_fac_mu(m); }
 
 /* ------------------------------------------------------------------------ */
 /* point addition (Sec. 3.6) and the rescaled quantities (Sec. 3.7)         */

@@ -154,6 +154,31 @@ def test_forces_sum_to_zero_and_fac_mu(oracle_mod):
     assert st["fac_mu"] == pytest.approx(1.0, rel=1e-12)
 
 
+@pytest.mark.parametrize("case", ["annulus_2e5", "disk_1e4"])
+def test_fac_mu_sums_correctly_rounded(oracle_mod, case):
+    """Eq. 3's sums: fac_mu equals sqrt of the ratio of correctly rounded
+    sums (math.fsum) of l^2 and mu(m)^2 within a few ulps (the oracle sums
+    pairwise).  A running sum drifts by 6e-15 over the annulus's 6e5 edges
+    and by ~1e-13 over the disk's 3e4 identical mu^2 terms (uniform sizing:
+    every rounding goes the same way); the comparison of forces near relaxed
+    springs amplifies that."""
+    if case == "disk_1e4":
+        wl = W.disk_workload(n=10037, seed=0)
+    else:
+        wl = W.annulus_workload(n=200_003, seed=3, sdf_n=512, siz_n=256)
+    om = oracle_mod.OracleMesh(wl.sdf, wl.sizing, wl.points, method=0)
+    om.set_threads(4)
+    st = om.rebuild()
+    e, p = om.edges(), om.points()
+    assert len(e) > (500_000 if case == "annulus_2e5" else 25_000)
+    d = p[e[:, 1]] - p[e[:, 0]]
+    l2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
+    m = 0.5 * (p[e[:, 0]] + p[e[:, 1]])
+    mu = W._bilinear_np(wl.sizing, m[:, 0], m[:, 1])
+    want = math.sqrt(math.fsum(l2) / math.fsum(mu * mu))
+    assert abs(st["fac_mu"] - want) <= 4e-16 * want, (st["fac_mu"] - want) / want
+
+
 def test_quality_closed_forms(oracle_mod):
     eq = np.array([[0.0, 0.0], [0.05, 0.0], [0.025, 0.05 * math.sqrt(3) / 2]])
     st = _dm_mesh(oracle_mod, eq).rebuild()
