@@ -386,8 +386,14 @@ __global__ void __launch_bounds__(kThreads) k_update(const __grid_constant__ Ite
                 mu = (T)ff_to_d(m);
                 muf = m.h;
             } else {
-                mu = bilin<T>(V.siz, (xi + xj) * (T)0.5, (yi + yj) * (T)0.5);
-                muf = (float)mu;
+                // FP32 mode: the midpoint (exact as a float pair) and the
+                // lookup's grid coordinate in float-float, so mu carries one
+                // rounding; a float midpoint and coordinate perturb mu by up to
+                // |grad mu| |m| 2^-22, several 1e-6 of the smallest sizes here
+                ff m = bilin_ff(V.siz, ff_scale2(two_sum((float)xi, (float)xj), 0.5f),
+                                ff_scale2(two_sum((float)yi, (float)yj), 0.5f));
+                mu = (T)m.h;
+                muf = m.h;
             }
             if (owner) {
                 devf += fabsf((float)l / ((float)fac_mu * muf) - 1.0f);

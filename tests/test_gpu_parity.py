@@ -4,11 +4,12 @@ Triangle sets must be identical (the emission and validity decisions are
 fixed FP64 formulas and the predicates are exact).  Forces, centroids and
 positions of one iteration from identical states must agree within 1e-12
 (FP64 mode) or 2e-6 (FP32 mode) of their natural scale: positions by h_i
+(FP64) or the coordinate magnitude (FP32), centroids by sqrt(cell area)
 (FP64) or the coordinate magnitude (FP32), forces by k times the summed
-length of the valid edges at the point (f = k (l0 - l) cancels near
-equilibrium, so it is computed from terms of that size), centroids by sqrt(cell area) (FP64) or the
-coordinate magnitude (FP32).  Threshold branches (clamp, classification,
-projection) may flip only in FP32 mode; flips are counted and bounded.
+length of the valid edges at the point everywhere, and by the summed spring
+magnitudes sum |f_e| in distribution (see _check_forces).  Threshold branches (clamp, projection, class, quadrature
+level) may flip only in FP32 mode: flips are counted and bounded, and the
+tolerance applies to every other point.
 """
 import numpy as np
 import pytest
@@ -101,18 +102,71 @@ def _edge_length_scale(om, p0):
     return om.params.k_spring * out
 
 
+def _check_forces(gm, om, p0, tol):
+    """F_i against the oracle.  Every point: |dF| <= tol k sum(l), the size
+    of the terms k (l0 - l) the force is formed from.  Against sum |f_e|, the
+    force's own magnitude: the median below tol and (FP64) the 90th
+    percentile below tol.  f = k (l0 - l) has the condition number
+    l / |l0 - l|: where a point's springs are all nearly relaxed any rounding
+    of l0 or l (even the summation order of the global sums in fac_mu) is
+    amplified, so no floating-point evaluation meets tol |f| at every point.
+    The per-point sum |f| itself must meet the same bars."""
+    Fg, Fo = gm.debug(1), om.force()
+    kl = _edge_length_scale(om, p0)
+    fs = om.fsum()
+    err = np.linalg.norm(Fg - Fo, axis=1)
+    assert np.all(err[kl == 0] == 0)
+    on = kl > 0
+    loaded = fs > 0
+    fsg = gm.debug(3)
+    for e in (err, np.abs(fsg - fs)):
+        assert (e[on] / kl[on]).max() < tol, (e[on] / kl[on]).max()
+        q50, q90 = np.quantile(e[loaded] / fs[loaded], [0.5, 0.9])
+        assert q50 < tol, q50
+        if tol < 1e-9:
+            assert q90 < tol, q90
+    return err
+
+
+def _branch_flips(gm, om, p0, h_old, method):
+    """Points whose threshold branches differ between the two sides, each
+    side's decision taken from its own values: the clamp |p_new - p| > 0.4 h,
+    whether the treatment moved the clamped point (projection), the class
+    after treatment and, for CVD, the quadrature level."""
+    fac_pt = om.params.fac_pt
+    out = np.zeros(len(p0), dtype=bool)
+    fin = {"g": gm.points().astype(np.float64), "o": om.points()}
+    raw = {"g": gm.debug(0), "o": om.pnew()}
+    clamp, proj = {}, {}
+    for k in ("g", "o"):
+        d = raw[k] - p0
+        ln = np.linalg.norm(d, axis=1)
+        T = fac_pt * h_old
+        clamp[k] = ln > T
+        sc = np.where(clamp[k], T / np.where(ln > 0, ln, 1), 1.0)
+        cl = p0 + d * sc[:, None]
+        proj[k] = np.linalg.norm(fin[k] - cl, axis=1) > 1e-3 * h_old
+    out |= clamp["g"] != clamp["o"]
+    out |= proj["g"] != proj["o"]
+    out |= gm.debug(4).astype(int) != om.classes()
+    if method == 1:
+        out |= gm.debug(6).astype(int) != om.quad_level()
+    return out
+
+
 def _compare_step(gm, om, precision, method):
     p0 = om.points()
+    h_old = h_of_points(om, p0)
     gm.step(1)
     om.step()
     tol = TOL_FP64 if precision == 0 else TOL_FP32
+    flips = _branch_flips(gm, om, p0, h_old, method)
+    if precision == 0:
+        assert flips.sum() == 0, np.flatnonzero(flips)[:10]
+    else:
+        assert flips.mean() < 1e-3, flips.sum()
     if method == 0:
-        Fg, Fo = gm.debug(1), om.force()
-        scale = _edge_length_scale(om, p0)
-        err = np.linalg.norm(Fg - Fo, axis=1)
-        assert np.all(err[scale == 0] == 0)
-        scale = np.where(scale > 0, scale, 1.0)
-        assert (err / scale).max() < tol, (err / scale).max()
+        _check_forces(gm, om, p0, tol)
     else:
         cg, co = gm.debug(2), om.centroid()
         if precision == 0:
@@ -120,11 +174,6 @@ def _compare_step(gm, om, precision, method):
         else:
             scale = np.maximum(np.abs(co).max(1), 1e-3)
         err = np.linalg.norm(cg - co, axis=1) / scale
-        lv_g, lv_o = gm.debug(6).astype(int), om.quad_level()
-        flips = lv_g != lv_o
-        if precision == 0:
-            assert flips.sum() == 0
-        assert flips.mean() < 1e-3
         assert err[~flips].max() < tol, err[~flips].max()
     pg, po = gm.points(), om.points()
     if precision == 0:
@@ -132,21 +181,21 @@ def _compare_step(gm, om, precision, method):
     else:
         scale = np.maximum(np.abs(po).max(1), 1e-3)
     err = np.linalg.norm(pg.astype(np.float64) - po, axis=1) / scale
-    bad = err > tol
-    if precision == 0:
-        assert bad.sum() == 0, (bad.sum(), err.max())
-    else:
-        assert bad.mean() < 1e-3, (bad.sum(), err.max())
-    cg_cls, co_cls = gm.debug(4).astype(int), om.classes()
-    mism = cg_cls != co_cls
-    if precision == 0:
-        assert mism.sum() == 0
+    assert err[~flips].max() < tol, (err[~flips].max(), int(np.argmax(np.where(flips, 0, err))))
     return err
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_distmesh_step(precision):
     gm, om = make_pair(disk_small(), precision=precision, method=0)
+    _compare_step(gm, om, precision, 0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_distmesh_step_annulus(precision):
+    # adaptive sizing: mu from 0.002 to 0.04, the lookup at the spring
+    # midpoints is where FP32 rounding would show
+    gm, om = make_pair(annulus_small(), precision=precision, method=0, fac_retria=0.0)
     _compare_step(gm, om, precision, 0)
 
 
@@ -267,6 +316,37 @@ def test_full_size_annulus_triangles(precision):
     wl = W.annulus_workload(n=1_000_000, method=2, precision=precision)
     gm, om = make_pair((wl.sdf, wl.sizing, wl.points), precision=precision, method=2)
     _tri_equal(gm, om)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_mid_trajectory(precision):
+    """The benchmark's 1e6-point annulus after 10 hybrid iterations on the
+    GPU (the phase of the trajectory the benchmark times), loaded into the
+    oracle: the triangles identical, then one DistMesh and one CVD step from
+    that exact state compared element by element (forces or centroids,
+    positions, classes)."""
+    import os
+
+    import oracle
+    import paper_2309_13824_gb300 as g
+
+    wl = W.annulus_workload(n=1_000_000, method=2, precision=precision)
+    pts = wl.points if precision == 0 else W.to_fp32_positions(wl.points)
+    run = g.Mesh(wl.sdf, wl.sizing, pts, precision=precision, method=2)
+    s = run.step(10)
+    assert s["iterations"] == 10 and not s["terminated"]
+    P, cls, dprev = run.state()
+    run.close()
+    for method in (0, 1):
+        gm = g.Mesh(wl.sdf, wl.sizing, P, precision=precision, method=method, debug=1, fac_retria=0.0)
+        gm.set_state(P, cls, dprev)
+        om = oracle.OracleMesh(wl.sdf, wl.sizing, P.astype(np.float64), method=method, fac_retria=0.0)
+        om.set_classes(cls)
+        om.set_dprev(dprev)
+        om.set_threads(os.cpu_count() or 1)
+        _tri_equal(gm, om)
+        _compare_step(gm, om, precision, method)
+        gm.close()
 
 
 def test_full_size_star_1e7_sampled():

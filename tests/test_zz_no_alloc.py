@@ -65,3 +65,42 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rc = L.mesh_bucket_points_noalloc(dummy, dummy, 3_000_000, *BOX, 100, 100, dummy, dummy, None)
     assert rc == g.TRIME_EINVAL
     assert "4194304" in g.mesh_last_error()
+
+
+@pytest.mark.parametrize("n,nbx,nby", [
+    # 2n + nb + nb/4096 + 1 == 4194304 exactly: key, rank, counts and the
+    # tile sums fill the whole scratch
+    (2_090_916, 1039, 12),
+    # a bucket grid near its own cap (4096 x 1024) with few points: the tile
+    # sums (1024 of them) sit at the end of the scratch
+    (500, 2048, 2047),
+    # no points: every bucket is empty
+    (0, 7, 5),
+])
+def test_noalloc_edge_sizes(n, nbx, nby):
+    torch = pytest.importorskip("torch")
+    import paper_2309_13824_gb300 as g
+
+    g.build()
+    assert 2 * n + nbx * nby + nbx * nby // 4096 + 1 <= 4194304
+    rng = np.random.default_rng(n + nbx)
+    pts = rng.uniform(-1.1, 1.1, (n, 2))
+    want = _run(g, torch, pts, nbx, nby, noalloc=False)
+    for _ in range(2):  # twice in a row through the shared scratch
+        got = _run(g, torch, pts, nbx, nby, noalloc=True)
+        _same(got, want)
+    assert np.array_equal(np.sort(got[1]), np.arange(n))
+    if n == 0:
+        assert not got[0].any()
+
+
+def test_noalloc_rejects_one_past_the_limit():
+    import paper_2309_13824_gb300 as g
+
+    g.build()
+    L = g.lib()
+    dummy = C.c_void_p(1)
+    # one point more than the case that fills the scratch exactly
+    assert L.mesh_bucket_points_noalloc(dummy, dummy, 2_090_917, *BOX, 1039, 12, dummy, dummy, None) == g.TRIME_EINVAL
+    # a bucket grid beyond 4096 x 1024
+    assert L.mesh_bucket_points_noalloc(dummy, dummy, 1, *BOX, 4097, 1024, dummy, dummy, None) == g.TRIME_EINVAL
