@@ -114,6 +114,9 @@ typedef struct {
     int64_t triangulations;    /* iterations of the call that re-triangulated             */
     int64_t added;             /* points added by the call (Sec. 3.6)                     */
     int64_t n_points;          /* N_current after the call                                */
+    /* more Voronoi work counters (mesh_params.debug = 1 only): */
+    int64_t vor_fp64;          /* cut decisions the float filter left to the FP64 filter  */
+    int64_t vor_resolve;       /* polygon vertices solved again in double                 */
 } mesh_stats;
 
 typedef struct mesh_s mesh_t;

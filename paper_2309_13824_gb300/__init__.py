@@ -60,7 +60,8 @@ class mesh_stats(C.Structure):
                 ("trace_cap", C.c_int64), ("quad_cap", C.c_int64), ("dup_points", C.c_int64),
                 ("small_moves", C.c_int32), ("target_reached", C.c_int32), ("vor_candidates", C.c_int64),
                 ("vor_picks", C.c_int64), ("vor_cuts", C.c_int64), ("vor_rings", C.c_int64), ("vor_wide", C.c_int64),
-                ("triangulations", C.c_int64), ("added", C.c_int64), ("n_points", C.c_int64)]
+                ("triangulations", C.c_int64), ("added", C.c_int64), ("n_points", C.c_int64),
+                ("vor_fp64", C.c_int64), ("vor_resolve", C.c_int64)]
 
 
 class mesh_tuning(C.Structure):

@@ -38,6 +38,7 @@ struct DevCounters {
     // Voronoi work, counted only with debug recording on
     unsigned long long vor_candidates, vor_picks, vor_cuts, vor_rings, vor_wide;
     unsigned long long triangulations;  // iterations that re-triangulated
+    unsigned long long vor_fp64, vor_resolve;  // FP64 cut filters, vertices re-solved in double (debug)
 };
 
 // Per-block partial sums written by the emit kernel (a3/a4/a8 and Eq. 3 sums).

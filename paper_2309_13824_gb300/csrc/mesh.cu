@@ -476,6 +476,8 @@ static void fill_stats(const mesh_s* m, int k, int iters, mesh_stats* s) {
     s->vor_rings = (int64_t)c.cnt.vor_rings;
     s->vor_wide = (int64_t)c.cnt.vor_wide;
     s->triangulations = (int64_t)c.cnt.triangulations;
+    s->vor_fp64 = (int64_t)c.cnt.vor_fp64;
+    s->vor_resolve = (int64_t)c.cnt.vor_resolve;
     s->added = m->batched ? 0 : m->added_call;
     s->n_points = m->parts[k].n;
 }

@@ -70,7 +70,8 @@ struct Lane {
     float PQx, PQy, PM;   // and their absolute-value permanents
 };
 
-__device__ __forceinline__ void make_vertex(Lane& L, float nx2, float ny2, float s2, int lab2, float RB) {
+// returns true when the vertex had to be solved again in double
+__device__ __forceinline__ bool make_vertex(Lane& L, float nx2, float ny2, float s2, int lab2, float RB) {
     float D = L.nx * ny2 - L.ny * nx2;
     float px = L.s * ny2 - s2 * L.ny, py = s2 * L.nx - L.s * nx2;
     // approximate reciprocal and root (a few ulps): the bound err below
@@ -83,6 +84,7 @@ __device__ __forceinline__ void make_vertex(Lane& L, float nx2, float ny2, float
                  r * (fabsf(L.nx * ny2) + fabsf(L.ny * nx2));
     float err = 64.0f * kEps * perm * fabsf(iD);
     bool ok = (D != 0.0f) && (r + err < RB);  // false for NaN as well
+    const bool resolved = !ok;
     if (!ok) {
         // nearly parallel edges (a bisector almost along a bounding line):
         // the float vertex is too uncertain, so solve again in double, where
@@ -118,28 +120,33 @@ __device__ __forceinline__ void make_vertex(Lane& L, float nx2, float ny2, float
         L.PQx = al * fabsf(by) + bl * fabsf(ay);
         L.PQy = al * fabsf(bx) + bl * fabsf(ax);
     }
+    return resolved;
 }
 
 // vertex of this lane with the next lane's edge (all lanes participate)
+// what the rare exact path needs besides the launch arguments
+struct CellCtx {
+    DevCtrl* ctrl;
+    int si;   // the cell's slot
+    int dbg;  // count the FP64 filters and re-solves
+};
+
 template <int G>
-__device__ __forceinline__ void lane_vertex(Lane& L, int ne, const Grp<G>& g, float RB, bool active) {
+__device__ __forceinline__ void lane_vertex(Lane& L, int ne, const Grp<G>& g, float RB, bool active,
+                                            const CellCtx& ctx) {
     int nxt = g.gl + 1 >= ne ? 0 : g.gl + 1;
     float nx2 = g.shfl(L.nx, nxt), ny2 = g.shfl(L.ny, nxt);
     float s2 = g.shfl(L.s, nxt);
     int lab2 = g.shfl(L.lab, nxt);
-    if (active && g.gl < ne) make_vertex(L, nx2, ny2, s2, lab2, RB);
+    if (active && g.gl < ne && make_vertex(L, nx2, ny2, s2, lab2, RB) && ctx.dbg)
+        atomicAdd(&ctx.ctrl->cnt.vor_resolve, 1ull);
 }
-
-// what the rare exact path needs besides the launch arguments
-struct CellCtx {
-    DevCtrl* ctrl;
-    int si;  // the cell's slot
-};
 
 // exact decision for vertex (j, k) of cell i against candidate l: FP64 filter,
 // then expansion arithmetic with symbolic perturbation
 template <typename T>
 __device__ __noinline__ bool exact_cut(const IterArgs<T>& a, const CellCtx& c, int sj, int sk, int sl) {
+    if (c.dbg) atomicAdd(&c.ctrl->cnt.vor_fp64, 1ull);
     const T* X = a.srt.x;
     const T* Y = a.srt.y;
     double pi[2] = {(double)X[c.si], (double)Y[c.si]};
@@ -232,7 +239,7 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
         }
         ne = nn;
     }
-    lane_vertex<G>(L, ne, g, RB, doit);
+    lane_vertex<G>(L, ne, g, RB, doit, ctx);
     return status;
 }
 
@@ -255,6 +262,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     CellCtx ctx;
     ctx.ctrl = V.ctrl;
     ctx.si = s;
+    ctx.dbg = P.debug;
     // generator relative to the box corner, and the box size (float; the box
     // planes only need to bound Reg_i with the S/16 margin)
     const float xf = (pi4.x - P.bx0f) + pi4.y, yf = (pi4.z - P.by0f) + pi4.w;
@@ -290,7 +298,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
         L.s = bs == 0 ? xf + mb : bs == 1 ? (Wf - xf) + mb : bs == 2 ? yf + mb : (Hf - yf) + mb;
         L.lab = box_label(bs);
     }
-    lane_vertex<G>(L, ne, g, RB, true);
+    lane_vertex<G>(L, ne, g, RB, true, ctx);
     int status = 0;
     // the domain box cuts the octagon only if one of its planes comes closer
     // than the octagon's circumradius RB (every vertex lies within RB)
@@ -633,6 +641,7 @@ __device__ int voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int 
     CellCtx ctx;
     ctx.ctrl = V.ctrl;
     ctx.si = s;
+    ctx.dbg = P.debug;
     const float xf = (pi4.x - P.bx0f) + pi4.y, yf = (pi4.z - P.by0f) + pi4.w;
     const float Wf = (float)(P.bx1 - P.bx0), Hf = (float)(P.by1 - P.by0);
     float RB, mb;

@@ -53,6 +53,28 @@ def test_triangles_annulus(precision):
     _tri_equal(gm, om)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rebuilds_after_steps_and_moves(precision):
+    """Triangles equal the oracle's for a second rebuild at the same
+    positions, a rebuild after three iterations, and a rebuild after every
+    point moved by up to half its h."""
+    gm, om = make_pair(annulus_small(), precision=precision, method=2)
+    _tri_equal(gm, om)
+    _tri_equal(gm, om)
+    gm.step(3)
+    P, cls, dprev = gm.state()
+    om.set_points(P.astype(np.float64))
+    _tri_equal(gm, om)
+    rng = np.random.default_rng(17)
+    h = h_of_points(om, P.astype(np.float64))
+    Q = P.astype(np.float64) + rng.uniform(-0.5, 0.5, P.shape) * h[:, None]
+    Q = np.clip(Q, -1.05, 1.05).astype(P.dtype)
+    gm.set_state(Q)
+    om.set_points(Q.astype(np.float64))
+    st, _ = _tri_equal(gm, om)
+    assert st["clip_inconsistent"] == 0
+
+
 def test_triangles_unbounded_and_no_validity():
     sdf = W.grid_from_fn(lambda x, y: W.disk_sdf_fn(x, y, r=1.0), 64)
     rng = np.random.default_rng(5)
@@ -151,7 +173,7 @@ def _branch_flips(gm, om, p0, h_old, method):
     out |= gm.debug(4).astype(int) != om.classes()
     if method == 1:
         out |= gm.debug(6).astype(int) != om.quad_level()
-    return out
+    return out, proj["g"] | proj["o"]
 
 
 def _compare_step(gm, om, precision, method):
@@ -160,7 +182,7 @@ def _compare_step(gm, om, precision, method):
     gm.step(1)
     om.step()
     tol = TOL_FP64 if precision == 0 else TOL_FP32
-    flips = _branch_flips(gm, om, p0, h_old, method)
+    flips, projected = _branch_flips(gm, om, p0, h_old, method)
     if precision == 0:
         assert flips.sum() == 0, np.flatnonzero(flips)[:10]
     else:
@@ -180,7 +202,19 @@ def _compare_step(gm, om, precision, method):
         scale = h_of_points(om, po)
     else:
         scale = np.maximum(np.abs(po).max(1), 1e-3)
-    err = np.linalg.norm(pg.astype(np.float64) - po, axis=1) / scale
+    dist = np.linalg.norm(pg.astype(np.float64) - po, axis=1)
+    err = dist / scale
+    if precision == 1:
+        # the sphere trace and the Newton projection stop at the first iterate
+        # with |sdf| <= geps_i (Sec. 4.3): from float and double inputs both
+        # results lie in that band but need not be the same iterate, so a
+        # projected point is bounded by the band, not by 2e-6
+        geps_g = om.geometry()[2]
+        pr = projected & ~flips
+        cells = [om.point_cell(float(x), float(y)) for x, y in po[pr]]
+        ge = np.array([geps_g[gj, gi] for _, gi, gj in cells])
+        assert np.all(dist[pr] <= 2.0 * ge + tol * scale[pr])
+        flips = flips | projected
     assert err[~flips].max() < tol, (err[~flips].max(), int(np.argmax(np.where(flips, 0, err))))
     return err
 
@@ -336,6 +370,10 @@ def test_full_size_mid_trajectory(precision):
     s = run.step(10)
     assert s["iterations"] == 10 and not s["terminated"]
     P, cls, dprev = run.state()
+    # the running mesh's own rebuild (its bucket order of iteration 10)
+    st = run.rebuild()
+    assert st["ring_overflow"] == 0 and st["exact_overflow"] == 0 and st["clip_inconsistent"] == 0
+    t_run = sorted_tris(run.triangles())
     run.close()
     for method in (0, 1):
         gm = g.Mesh(wl.sdf, wl.sizing, P, precision=precision, method=method, debug=1, fac_retria=0.0)
@@ -344,7 +382,9 @@ def test_full_size_mid_trajectory(precision):
         om.set_classes(cls)
         om.set_dprev(dprev)
         om.set_threads(os.cpu_count() or 1)
-        _tri_equal(gm, om)
+        _, tg = _tri_equal(gm, om)
+        if method == 0:
+            assert np.array_equal(t_run, tg)
         _compare_step(gm, om, precision, method)
         gm.close()
 
