@@ -644,7 +644,47 @@ def learned_leg(g, stream):
     p32 = W.to_fp32_positions(star.points)
     out["star500_1e6_fp32"] = {"plain_converged": rec(*guarded(star, p32, 1)),
                                "learned_converged": rec(*guarded(star, p32, 1, net=net))}
+    out["batched_annuli_4x250k_fp64"] = batched_learned(g, net)
     return out
+
+
+def batched_learned(g, net):
+    """The batched form with the learned part at 10^6 points: four annuli of
+    2.5 x 10^5 points (seeds 5-8) stepped as one batch; each mesh's target is
+    the plain batch's converged minimum angle minus 1 degree; wall time (host
+    clock around synchronous calls) of the plain batch and of the learned
+    batch to every mesh's target."""
+    import torch
+
+    import workloads as W
+
+    meshes = []
+    for sd in (5, 6, 7, 8):
+        wl = W.annulus_workload(n=250_000, seed=sd)
+        meshes.append((wl.sdf, wl.sizing, wl.points))
+    conv = g.MeshBatch(meshes, method=2, autotune=False).step(2000)
+    targets = [c["min_angle_deg"] - 1.0 for c in conv]
+    res = {"points": sum(len(m[2]) for m in meshes), "meshes": len(meshes),
+           "targets_min_angle_deg": targets,
+           "policy": {"every": 5, "jump": 5.0, "min_angle_tol": 0.5, "max_rounds": 8}}
+    for name in ("plain", "learned"):
+        b = g.MeshBatch(meshes, method=2, autotune=False)
+        for k, q in enumerate(targets):
+            b.set_quality_target(q, mesh=k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = b.step(2000) if name == "plain" else b.step_learned(net, 2000, max_rounds=8)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"seconds": dt, "all_reached": all(x["target_reached"] for x in st),
+                     "iterations": [x["iterations"] for x in st],
+                     "min_angle_deg": [x["min_angle_deg"] for x in st],
+                     "max_alpha": [x["max_alpha"] for x in st]}
+        if name == "learned":
+            res[name]["proposals_kept"] = [x["accepted"] for x in st]
+            res[name]["proposals_undone"] = [x["rejected"] for x in st]
+        b.close()
+    return res
 
 
 def main():
@@ -830,7 +870,7 @@ def main():
                            "l2": "flushed before every timed step (256 MB write)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "e2e": e2e, "clocks": clk,
-                "gpu_launches": 17 * args.steps,  # 16 kernels of the iteration graph + the counter reset
+                "gpu_launches": 18 * args.steps,  # 17 kernels of the iteration graph + the counter reset
                 "last_step": {"method": st["method"], "switched": st["switched"], "n_tri": st["n_tri"],
                               "half_mean_alpha": st["half_mean_alpha"]}}
         line.update(extras)

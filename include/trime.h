@@ -582,6 +582,22 @@ int mesh_batch_set_quality_target(mesh_batch_t* b, int32_t mesh, double min_angl
  * result without timing again). */
 int mesh_batch_set_tuning(mesh_batch_t* b, double n_opt, int32_t lanes);
 
+/* mesh_step_learned for every mesh of the batch at once (the batched form
+ * with the learned part; the paper has no learned part).  Before every
+ * `every`-th iteration all meshes that have not terminated get a proposal
+ * round: from the same state one plain iteration and the proposal followed by
+ * one plain iteration run for the whole batch, then each mesh keeps the
+ * branch its own statistics favour (the rule of mesh_step_learned) and the
+ * meshes whose proposal lost are restored to their plain branch.  At most
+ * max_rounds rounds (<= 0: no limit).  stats (not NULL), accepted and
+ * rejected (may be NULL): n_meshes entries each, per mesh.  The features'
+ * "move in use" is each mesh's own (CVD once its hybrid has switched).
+ * Synchronous.  Errors as mesh_batch_step; TRIME_ETIMEOUT if a tensor-core
+ * wait of the model ran out. */
+int mesh_batch_step_learned(mesh_batch_t* b, mlp_t* net, int32_t n_iters, int32_t every, double jump,
+                            double min_angle_tol, int32_t max_rounds, mesh_stats* stats, int32_t* accepted,
+                            int32_t* rejected);
+
 /* The autotuner's choice and timings. */
 int mesh_batch_get_tuning(const mesh_batch_t* b, mesh_tuning* out);
 

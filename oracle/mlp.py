@@ -161,8 +161,11 @@ def forward(P: Params, X, quantize: bool = True):
     return Y, (X, W1, W2, W3, Z1, H1, Z2, H2)
 
 
-def loss_and_grads(P: Params, X, T, quantize: bool = True):
-    """L = sum (Y - T)^2 / (2 B) and its gradients as a Params of the same shapes."""
+def loss_and_grads(P: Params, X, T, quantize: bool = True, scales: bool = False):
+    """L = sum (Y - T)^2 / (2 B) and its gradients as a Params of the same
+    shapes; with scales=True also a Params holding, for every gradient
+    element, the sum of the absolute values of the products it adds up
+    (the size its accumulation rounding is relative to)."""
     Y, (Xq, W1, W2, W3, Z1, H1, Z2, H2) = forward(P, X, quantize)
     B = len(Y)
     R = Y - np.asarray(T, dtype=np.float64)
@@ -176,7 +179,12 @@ def loss_and_grads(P: Params, X, T, quantize: bool = True):
     dZ1 = _q((dZ2 @ W2) * (Z1 > 0), quantize)
     gW1 = dZ1.T @ Xq
     gb1 = dZ1.sum(0)
-    return L, Params(gW1, gb1, gW2, gb2, gW3, gb3)
+    G = Params(gW1, gb1, gW2, gb2, gW3, gb3)
+    if not scales:
+        return L, G
+    a = np.abs
+    S = Params(a(dZ1).T @ a(Xq), a(dZ1).sum(0), a(dZ2).T @ a(H1), a(dZ2).sum(0), a(dY).T @ a(H2), a(dY).sum(0))
+    return L, G, S
 
 
 def adam_step(P: Params, G: Params, m, v, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):

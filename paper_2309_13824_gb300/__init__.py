@@ -81,7 +81,7 @@ EXPORTS = ["mesh_segment_sdf_points", "mesh_adf_build", "mesh_adf_cells", "mesh_
            "mesh_set_tuning", "mesh_batch_set_tuning", "mesh_tc_gemm_bf16", "mlp_create", "mlp_destroy",
            "mlp_get_params", "mlp_set_params", "mlp_forward", "mlp_loss_grad", "mlp_train", "mesh_features",
            "mesh_collect_pairs", "mesh_propose", "mesh_step_learned", "mesh_set_quality_target",
-           "mesh_batch_set_quality_target", "mesh_measure_pipe_peaks"]
+           "mesh_batch_set_quality_target", "mesh_measure_pipe_peaks", "mesh_batch_step_learned"]
 
 MLP_IN = 48
 MLP_PARAMS = 7426
@@ -153,6 +153,8 @@ def lib():
     L.mesh_propose.argtypes = [vp, vp, C.c_double]
     L.mesh_step_learned.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32,
                                     P(mesh_stats), P(C.c_int32), P(C.c_int32)]
+    L.mesh_batch_step_learned.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32,
+                                          P(mesh_stats), P(C.c_int32), P(C.c_int32)]
     L.mesh_batch_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
     L.mesh_batch_destroy.argtypes = [vp]
     L.mesh_batch_destroy.restype = None
@@ -188,7 +190,7 @@ def lib():
                  "mesh_tc_gemm_bf16", "mlp_create", "mlp_get_params", "mlp_set_params", "mlp_forward",
                  "mlp_loss_grad", "mlp_train", "mesh_features", "mesh_collect_pairs", "mesh_propose",
                  "mesh_step_learned", "mesh_set_quality_target", "mesh_batch_set_quality_target",
-                 "mesh_measure_pipe_peaks", "mesh_segment_sdf_points", "mesh_adf_build", "mesh_adf_cells",
+                 "mesh_measure_pipe_peaks", "mesh_batch_step_learned", "mesh_segment_sdf_points", "mesh_adf_build", "mesh_adf_cells",
                  "mesh_adf_size", "mesh_adf_export", "mesh_adf_eval"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -672,6 +674,20 @@ class MeshBatch:
 
     def step_async(self, n_iters: int = 1):
         _check(lib().mesh_batch_step(self._h, n_iters, None))
+
+    def step_learned(self, net: "MLP", n_iters: int, every: int = 5, jump: float = 5.0, min_angle_tol: float = 0.5,
+                     max_rounds: int = 8):
+        """mesh_batch_step_learned: per-mesh statistics with the proposals
+        each mesh kept ("accepted") and undid ("rejected")."""
+        s = (mesh_stats * self.size)()
+        acc = (C.c_int32 * self.size)()
+        rej = (C.c_int32 * self.size)()
+        _check(lib().mesh_batch_step_learned(self._h, net._h, n_iters, every, jump, min_angle_tol, max_rounds, s,
+                                             acc, rej))
+        out = [_stats_dict(x) for x in s]
+        for k, d in enumerate(out):
+            d["accepted"], d["rejected"] = acc[k], rej[k]
+        return out
 
     def profile(self, n_iters: int = 1):
         ms = np.zeros(7)

@@ -3,9 +3,15 @@
 // plus the per-slot precomputation the later kernels read: the geometry cell
 // by the fixed formula and the exact-duplicate (SoS) flag.
 //
-// count: one atomic per point gives its bucket and rank; scan: exclusive
-// prefix over the bucket counts (three passes); scatter: each point moves its
-// whole state to bucket_start[key] + rank.  All passes are HBM-streaming.
+// count: one atomic per point gives its bucket and a provisional rank; scan:
+// exclusive prefix over the bucket counts (three passes); place: each point
+// writes its index at bucket_start[key] + provisional rank, so a bucket's
+// members are listed together (in the atomics' order); scatter: each point
+// moves its whole state to bucket_start[key] + the number of the bucket's
+// members with a smaller index.  The sort is therefore stable and every
+// iteration is bit-reproducible (the provisional ranks come from atomics and
+// change from run to run).  All passes are HBM-streaming; the stable rank
+// reads the point's bucket list (a few entries) once more.
 #include <mutex>
 
 #include "kernels.cuh"
@@ -41,6 +47,17 @@ __global__ void __launch_bounds__(kThreads) k_count(const __grid_constant__ Iter
     int k = V.boff + by * V.P.nbx + bx;
     a.key[i] = k;
     a.rank[i] = atomicAdd(&a.bcount[k], 1);
+}
+
+// the bucket's members listed together (provisional order)
+template <typename T, bool B>
+__global__ void __launch_bounds__(kThreads) k_place(const __grid_constant__ IterArgs<T> a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const MeshView& V = mesh_of<B>(a, i);
+    if (skip_rebuild(V.ctrl, a.force)) return;
+    if (B && i - V.soff >= V.n) return;
+    a.sidx[a.bstart[a.key[i]] + a.rank[i]] = i;
 }
 
 // ------------------------------------------------------------------ scan
@@ -142,7 +159,10 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const __grid_constant__ It
     if (skip_rebuild(V.ctrl, a.force)) return;
     if (B && i - V.soff >= V.n) return;
     int k = a.key[i];
-    int d = a.bstart[k] + a.rank[i];
+    // stable rank: the bucket's members with a smaller index come first
+    const int lo = a.bstart[k], hi = a.bstart[k + 1];
+    int d = lo;
+    for (int q = lo; q < hi; q++) d += a.sidx[q] < i;
     T x = a.cur.x[i], y = a.cur.y[i];
     a.srt.x[d] = x;
     a.srt.y[d] = y;
@@ -207,11 +227,13 @@ void launch_bucket(const IterArgs<T>& a, cudaStream_t st) {
     if (a.Vs) {
         k_count<T, true><<<g, kThreads, 0, st>>>(a);
         launch_scan(a.bcount, a.bstart, a.nbtot, a.scan_tmp, st);
+        k_place<T, true><<<g, kThreads, 0, st>>>(a);
         k_scatter<T, true><<<g, kThreads, 0, st>>>(a);
         k_dups<T, true><<<g, kThreads, 0, st>>>(a);
     } else {
         k_count<T, false><<<g, kThreads, 0, st>>>(a);
         launch_scan(a.bcount, a.bstart, a.nbtot, a.scan_tmp, st);
+        k_place<T, false><<<g, kThreads, 0, st>>>(a);
         k_scatter<T, false><<<g, kThreads, 0, st>>>(a);
         k_dups<T, false><<<g, kThreads, 0, st>>>(a);
     }

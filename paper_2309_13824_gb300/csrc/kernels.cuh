@@ -63,7 +63,8 @@ struct IterArgs {
     State<T> wrk;      // the positions a DistMesh iteration without re-triangulation moves (slot order)
     int32_t* cell;     // [n] geometry cell of each sorted slot (fixed formula)
     int32_t* key;      // [n] bucket of each cur point
-    int32_t* rank;     // [n] rank inside its bucket
+    int32_t* rank;     // [n] provisional rank inside its bucket (atomics)
+    int32_t* sidx;     // [n] point indices listed by bucket (provisional order inside a bucket)
     int32_t* skey;     // [n] bucket of each sorted slot
     uint8_t* dom;      // [n] sorted slot has an exact duplicate with a larger id
     int32_t* bcount;   // [nbtot] bucket counts

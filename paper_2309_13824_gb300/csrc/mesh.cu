@@ -83,7 +83,7 @@ struct mesh_s {
     bool tri_stale = false;  // the sorted order no longer matches the triangulation
     int32_t *cid = nullptr, *sid = nullptr;
     uint8_t *ccls = nullptr, *scls = nullptr;
-    int32_t *cell = nullptr, *key = nullptr, *rank = nullptr, *skey = nullptr;
+    int32_t *cell = nullptr, *key = nullptr, *rank = nullptr, *skey = nullptr, *sidx = nullptr;
     uint8_t* dom = nullptr;
     int32_t *bcount = nullptr, *bstart = nullptr, *scan_tmp = nullptr;
     int32_t* ring = nullptr;
@@ -131,6 +131,7 @@ struct LearnBufs {
     void *bx[2] = {nullptr, nullptr}, *by[2] = {nullptr, nullptr}, *bdp[2] = {nullptr, nullptr};
     int32_t* bid[2] = {nullptr, nullptr};
     uint8_t* bcls[2] = {nullptr, nullptr};
+    uint8_t* rflag = nullptr;  // [parts] restore flags
 };
 
 namespace trime {
@@ -367,6 +368,7 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.cell = m->cell;
     a.key = m->key;
     a.rank = m->rank;
+    a.sidx = m->sidx;
     a.skey = m->skey;
     a.dom = m->dom;
     a.bcount = m->bcount;
@@ -805,6 +807,7 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->cell = dalloc<int32_t>(m, N, rc);
     m->key = dalloc<int32_t>(m, N, rc);
     m->rank = dalloc<int32_t>(m, N, rc);
+    m->sidx = dalloc<int32_t>(m, N, rc);
     m->skey = dalloc<int32_t>(m, N, rc);
     m->dom = dalloc<uint8_t>(m, N, rc);
     m->bcount = dalloc<int32_t>(m, (size_t)nbmax, rc);
@@ -1309,7 +1312,8 @@ static int check_net_err(mesh_s* m, mlp_s* net) {
 // are read from the model's memory; its own stream is not used)
 static int enqueue_propose(mesh_s* m, mlp_s* net, double jump) {
     LearnBufs* L = m->learn;
-    features_any(m, L->X, nullptr, nullptr, nullptr, 0, next_is_cvd(m));
+    // a batch reads each mesh's move from its control block
+    features_any(m, L->X, nullptr, nullptr, nullptr, 0, m->batched ? -1.0f : next_is_cvd(m));
     launch_mlp_forward(mlp_view(net), L->X, nullptr, (int)m->nslots, L->Y, mlp_err(net), m->st);
     if (m->prec == 0) launch_propose<double>(make_args<double>(m, 1), L->Y, (float)jump, m->st);
     else launch_propose<float>(make_args<float>(m, 1), L->Y, (float)jump, m->st);
@@ -1338,56 +1342,125 @@ static int write_ctrl0(mesh_s* m, const DevCtrl& c) {
     return 0;
 }
 
+static int write_ctrl_all(mesh_s* m, const std::vector<DevCtrl>& c) {
+    std::copy(c.begin(), c.end(), m->hctrl);
+    CUDA_TRY(cudaMemcpyAsync(m->ctrl, m->hctrl, sizeof(DevCtrl) * c.size(), cudaMemcpyHostToDevice, m->st));
+    CUDA_TRY(cudaStreamSynchronize(m->st));
+    return 0;
+}
+
+// cur <- saved state b on the slots of the flagged parts (a single mesh is
+// part 0; in a batch a slot's part is its chunk's)
+template <typename T>
+__global__ void k_restore_parts(int32_t n, const int32_t* cmesh, const uint8_t* flag, T* cx, T* cy, T* cdp,
+                                int32_t* cid, uint8_t* ccls, const T* bx, const T* by, const T* bdp,
+                                const int32_t* bid, const uint8_t* bcls) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n || !flag[cmesh ? cmesh[s >> kChunkShift] : 0]) return;
+    cx[s] = bx[s];
+    cy[s] = by[s];
+    cdp[s] = bdp[s];
+    cid[s] = bid[s];
+    ccls[s] = bcls[s];
+}
+
+static int restore_parts(mesh_s* m, const std::vector<uint8_t>& flags, int b) {
+    LearnBufs* L = m->learn;
+    if (!L->rflag) {
+        int rc = 0;
+        L->rflag = dalloc<uint8_t>(m, flags.size(), rc);
+        if (rc) return rc;
+    }
+    CUDA_TRY(cudaMemcpyAsync(L->rflag, flags.data(), flags.size(), cudaMemcpyHostToDevice, m->st));
+    int n = (int)m->nslots, g = (n + kThreads - 1) / kThreads;
+    const int32_t* cm = m->batched ? m->cmesh : nullptr;
+    if (g > 0) {
+        if (m->prec == 0)
+            k_restore_parts<double><<<g, kThreads, 0, m->st>>>(n, cm, L->rflag, (double*)m->cx, (double*)m->cy,
+                                                             (double*)m->cdp, m->cid, m->ccls, (double*)L->bx[b],
+                                                             (double*)L->by[b], (double*)L->bdp[b], L->bid[b],
+                                                             L->bcls[b]);
+        else
+            k_restore_parts<float><<<g, kThreads, 0, m->st>>>(n, cm, L->rflag, (float*)m->cx, (float*)m->cy,
+                                                            (float*)m->cdp, m->cid, m->ccls, (float*)L->bx[b],
+                                                            (float*)L->by[b], (float*)L->bdp[b], L->bid[b],
+                                                            L->bcls[b]);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(m->st));  // flags is the caller's host memory
+    return 0;
+}
+
+// Learned proposals for a single mesh or every mesh of a batch: each
+// proposal round runs, from the same state, one plain iteration and the
+// proposal followed by one plain iteration; each mesh keeps the branch its
+// own quality statistics favour (meshes that have terminated take no part).
 static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every, double jump, double tol,
                            int32_t max_props, mesh_stats* stats, int32_t* accepted, int32_t* rejected) {
     int rc = sync_in(m);
     if (rc) return rc;
     if ((rc = ensure_learn(m)) || (rc = reset_counters(m)) || (rc = read_ctrl(m))) return rc;
-    int start = m->hctrl[0].iterations, acc = 0, rej = 0;
-    if (n_iters > 0 && !m->hctrl[0].terminated) m->tri_stale = false;
-    for (int32_t k = 0; k < n_iters && !m->hctrl[0].terminated; k++) {
-        if (k > 0 && k % every == 0 && m->nslots > 0 && (max_props <= 0 || acc + rej < max_props)) {
+    const size_t np = m->parts.size();
+    std::vector<int> start(np), acc(np, 0), rej(np, 0);
+    for (size_t p = 0; p < np; p++) start[p] = m->hctrl[p].iterations;
+    int rounds = 0;
+    if (n_iters > 0 && !all_terminated(m)) m->tri_stale = false;
+    for (int32_t k = 0; k < n_iters && !all_terminated(m); k++) {
+        if (k > 0 && k % every == 0 && m->nslots > 0 && (max_props <= 0 || rounds < max_props)) {
             // two branches from the same state: one plain iteration, and the
             // proposal followed by one plain iteration; the better one stays
             if ((rc = read_ctrl(m))) return rc;
-            if (m->hctrl[0].terminated) break;
-            DevCtrl before = m->hctrl[0];
+            if (all_terminated(m)) break;
+            const std::vector<DevCtrl> before(m->hctrl, m->hctrl + np);
             // plain branch (the last-move snapshot stays that of the saved state)
             if ((rc = copy_state(m, true, 0))) return rc;
             CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
             if ((rc = read_ctrl(m))) return rc;
-            DevCtrl plain = m->hctrl[0];
+            const std::vector<DevCtrl> plain(m->hctrl, m->hctrl + np);
             // proposal branch from the saved state
-            if ((rc = copy_state(m, true, 1)) || (rc = copy_state(m, false, 0)) || (rc = force_retri(m, 0))) return rc;
-            DevCtrl c0 = before;
-            c0.iterations = plain.iterations;
-            c0.cnt = plain.cnt;
-            c0.retri = 1;
-            if ((rc = write_ctrl0(m, c0)) || (rc = enqueue_propose(m, net, jump))) return rc;
+            if ((rc = copy_state(m, true, 1)) || (rc = copy_state(m, false, 0)) || (rc = force_retri(m, -1))) return rc;
+            std::vector<DevCtrl> c0(before);
+            for (size_t p = 0; p < np; p++) {
+                c0[p].iterations = plain[p].iterations;
+                c0[p].cnt = plain[p].cnt;
+                c0[p].retri = 1;
+            }
+            if ((rc = write_ctrl_all(m, c0)) || (rc = enqueue_propose(m, net, jump))) return rc;
             snapshot(m);
             CUDA_TRY(cudaGraphLaunch(m->gexec, m->st));
             if ((rc = check_net_err(m, net)) || (rc = read_ctrl(m))) return rc;
-            const DevCtrl& after = m->hctrl[0];
-            // a proposal whose judged iteration tripped a capacity guard loses too
-            bool guard = after.cnt.ring_overflow > plain.cnt.ring_overflow ||
-                         after.cnt.exact_overflow > plain.cnt.exact_overflow;
-            bool ok = !guard && after.n_tri > 0 && after.half_a < plain.half_a &&
-                      after.min_ang >= plain.min_ang - tol;
-            if (ok) {
-                acc++;
-            } else {
-                rej++;
-                if ((rc = copy_state(m, false, 1)) || (rc = force_retri(m, 0))) return rc;
-                m->learn->have_q = false;  // the last move is unknown after the restore
-                DevCtrl c = plain;
+            std::vector<DevCtrl> next(m->hctrl, m->hctrl + np);
+            std::vector<uint8_t> lose(np, 0);
+            bool any_lost = false;
+            for (size_t p = 0; p < np; p++) {
+                if (before[p].terminated) continue;
+                const DevCtrl& after = next[p];
+                // a proposal whose judged iteration tripped a capacity guard loses too
+                bool guard = after.cnt.ring_overflow > plain[p].cnt.ring_overflow ||
+                             after.cnt.exact_overflow > plain[p].cnt.exact_overflow;
+                bool ok = !guard && after.n_tri > 0 && after.half_a < plain[p].half_a &&
+                          after.min_ang >= plain[p].min_ang - tol;
+                if (ok) {
+                    acc[p]++;
+                    continue;
+                }
+                rej[p]++;
+                lose[p] = 1;
+                any_lost = true;
+                DevCtrl c = plain[p];
                 c.iterations = after.iterations;
                 c.cnt = after.cnt;
-                c.cnt.ring_overflow = plain.cnt.ring_overflow;  // belonged to the discarded branch
-                c.cnt.exact_overflow = plain.cnt.exact_overflow;
-                c.cnt.clip_inconsistent = plain.cnt.clip_inconsistent;
+                c.cnt.ring_overflow = plain[p].cnt.ring_overflow;  // belonged to the discarded branch
+                c.cnt.exact_overflow = plain[p].cnt.exact_overflow;
+                c.cnt.clip_inconsistent = plain[p].cnt.clip_inconsistent;
                 c.retri = 1;
-                if ((rc = write_ctrl0(m, c))) return rc;
+                next[p] = c;
             }
+            if (any_lost) {
+                if ((rc = restore_parts(m, lose, 1)) || (rc = write_ctrl_all(m, next))) return rc;
+                m->learn->have_q = false;  // the last move is unknown after the restore
+            }
+            rounds++;
             continue;
         }
         snapshot(m);
@@ -1395,9 +1468,11 @@ static int do_step_learned(mesh_s* m, mlp_s* net, int32_t n_iters, int32_t every
         if ((k & 31) == 31 && (rc = read_ctrl(m))) return rc;
     }
     if ((rc = read_ctrl(m)) || (rc = sync_out(m))) return rc;
-    fill_stats(m, 0, m->hctrl[0].iterations - start, stats);
-    if (accepted) *accepted = acc;
-    if (rejected) *rejected = rej;
+    for (size_t p = 0; p < np; p++) {
+        fill_stats(m, (int)p, m->hctrl[p].iterations - start[p], &stats[p]);
+        if (accepted) accepted[p] = acc[p];
+        if (rejected) rejected[p] = rej[p];
+    }
     if (guard_tripped(m)) return TRIME_EDEVICE;
     return TRIME_OK;
 }
@@ -1850,6 +1925,14 @@ int mesh_batch_set_quality_target(mesh_batch_t* b, int32_t mesh, double min_angl
     if (!b || !(min_angle_deg >= 0) || min_angle_deg > 60) return fail(TRIME_EINVAL, "bad argument");
     if (mesh < -1 || mesh >= (int32_t)b->parts.size()) return fail(TRIME_EINVAL, "mesh index out of range");
     return set_target(b, mesh, min_angle_deg);
+}
+
+int mesh_batch_step_learned(mesh_batch_t* b, mlp_t* net, int32_t n_iters, int32_t every, double jump,
+                            double min_angle_tol, int32_t max_rounds, mesh_stats* stats, int32_t* accepted,
+                            int32_t* rejected) {
+    if (!b || !net || !stats || n_iters < 0 || every < 1 || !(jump > 0) || !(min_angle_tol >= 0))
+        return fail(TRIME_EINVAL, "bad argument");
+    return do_step_learned(b, net, n_iters, every, jump, min_angle_tol, max_rounds, stats, accepted, rejected);
 }
 
 int mesh_batch_set_tuning(mesh_batch_t* b, double n_opt, int32_t lanes) {

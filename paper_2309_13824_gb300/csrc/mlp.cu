@@ -503,16 +503,18 @@ __device__ __forceinline__ void sizing_grad_fixed(const DevGrid& g, double x, do
 
 __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 
-// One thread per slot of a single mesh: the 16 nearest other points by
+// One thread per slot: the 16 nearest other points of the slot's mesh by
 // (squared FP64 distance, index), found ring by ring in the bucket grid until
-// no unscanned bucket can hold a nearer point, then the 48 features.
-template <typename T>
+// no unscanned bucket can hold a nearer point, then the 48 features.  In a
+// batch the padding slots are skipped (their rows are left as they are).
+template <typename T, bool B>
 __global__ void __launch_bounds__(kThreads) k_features(const __grid_constant__ IterArgs<T> a, uint16_t* X, float* H,
                                                        T* px, T* py, const T* qx, const T* qy, int by_id,
                                                        float mflag) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.n) return;
-    const MeshView& V = a.V;
+    const MeshView& V = mesh_of<B>(a, s);
+    if (B && s - V.soff >= V.n) return;
     const DevParams& P = V.P;
     T xt = a.srt.x[s], yt = a.srt.y[s];
     double xd = (double)xt, yd = (double)yt;
@@ -579,7 +581,11 @@ __global__ void __launch_bounds__(kThreads) k_features(const __grid_constant__ I
     f[33] = bf16_bits((float)gx);
     f[34] = bf16_bits((float)gy);
     f[35] = a.srt.cls[s] == PT_BOUNDARY ? kBf16One : 0;
-    f[36] = bf16_bits(mflag);
+    // the move in use: given by the caller, or (mflag < 0) read from the
+    // slot's mesh: CVD iterations once the hybrid has switched
+    float mf = mflag;
+    if (mf < 0.0f) mf = (V.ctrl->method_param == 1 || (V.ctrl->method_param == 2 && V.ctrl->switched)) ? 1.0f : 0.0f;
+    f[36] = bf16_bits(mf);
     f[37] = qx ? bf16_bits((float)fdiv(fsub(xd, (double)qx[id]), h)) : 0;
     f[38] = qy ? bf16_bits((float)fdiv(fsub(yd, (double)qy[id]), h)) : 0;
     for (int k = kMlpFeat; k < kMlpIn; k++) f[k] = 0;
@@ -598,17 +604,20 @@ template <typename T>
 void launch_features(const IterArgs<T>& a, uint16_t* X, float* H, T* px, T* py, const T* qx, const T* qy, int by_id,
                      float method_cvd, cudaStream_t st) {
     int g = (a.n + kThreads - 1) / kThreads;
-    if (g > 0) k_features<T><<<g, kThreads, 0, st>>>(a, X, H, px, py, qx, qy, by_id, method_cvd);
+    if (g <= 0) return;
+    if (a.Vs) k_features<T, true><<<g, kThreads, 0, st>>>(a, X, H, px, py, qx, qy, by_id, method_cvd);
+    else k_features<T, false><<<g, kThreads, 0, st>>>(a, X, H, px, py, qx, qy, by_id, method_cvd);
 }
 template void launch_features<double>(const IterArgs<double>&, uint16_t*, float*, double*, double*, const double*,
                                       const double*, int, float, cudaStream_t);
 template void launch_features<float>(const IterArgs<float>&, uint16_t*, float*, float*, float*, const float*,
                                      const float*, int, float, cudaStream_t);
 
-template <typename T>
+template <typename T, bool B>
 __global__ void k_snapshot(const __grid_constant__ IterArgs<T> a, T* qx, T* qy) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.n) return;
+    if (B && s - mesh_of<B>(a, s).soff >= mesh_of<B>(a, s).n) return;  // padding slot (its id is not a point's)
     int id = a.cur.id[s];
     qx[id] = a.cur.x[s];
     qy[id] = a.cur.y[s];
@@ -617,19 +626,23 @@ __global__ void k_snapshot(const __grid_constant__ IterArgs<T> a, T* qx, T* qy) 
 template <typename T>
 void launch_snapshot(const IterArgs<T>& a, T* qx, T* qy, cudaStream_t st) {
     int g = (a.n + kThreads - 1) / kThreads;
-    if (g > 0) k_snapshot<T><<<g, kThreads, 0, st>>>(a, qx, qy);
+    if (g <= 0) return;
+    if (a.Vs) k_snapshot<T, true><<<g, kThreads, 0, st>>>(a, qx, qy);
+    else k_snapshot<T, false><<<g, kThreads, 0, st>>>(a, qx, qy);
 }
 template void launch_snapshot<double>(const IterArgs<double>&, double*, double*, cudaStream_t);
 template void launch_snapshot<float>(const IterArgs<float>&, float*, float*, cudaStream_t);
 
 // the proposed move p + h_i Y of every slot, clamped and treated (Sec. 4.3);
-// the recorded previous move is capped at one plain step (fac_pt h_i)
-template <typename T>
+// the recorded previous move is capped at one plain step (fac_pt h_i).  In a
+// batch, padding slots and meshes that have terminated are left alone (the
+// 32 slots of a warp belong to one mesh).
+template <typename T, bool B>
 __global__ void __launch_bounds__(kThreads) k_propose(const __grid_constant__ IterArgs<T> a, const float* Y, float jump) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long tcap = 0, nfail = 0;
-    const MeshView& V = a.V;
-    if (s < a.n) {
+    const MeshView& V = mesh_of<B>(a, s < a.n ? s : a.n - 1);
+    if (s < a.n && (!B || (s - V.soff < V.n && !V.ctrl->terminated))) {
         T xi = a.srt.x[s], yi = a.srt.y[s];
         int ocls = a.srt.cls[s];
         T h = (T)V.gh[a.cell[s]];
@@ -654,7 +667,9 @@ __global__ void __launch_bounds__(kThreads) k_propose(const __grid_constant__ It
 template <typename T>
 void launch_propose(const IterArgs<T>& a, const float* Y, float jump, cudaStream_t st) {
     int g = (a.n + kThreads - 1) / kThreads;
-    if (g > 0) k_propose<T><<<g, kThreads, 0, st>>>(a, Y, jump);
+    if (g <= 0) return;
+    if (a.Vs) k_propose<T, true><<<g, kThreads, 0, st>>>(a, Y, jump);
+    else k_propose<T, false><<<g, kThreads, 0, st>>>(a, Y, jump);
 }
 template void launch_propose<double>(const IterArgs<double>&, const float*, float, cudaStream_t);
 template void launch_propose<float>(const IterArgs<float>&, const float*, float, cudaStream_t);

@@ -79,14 +79,26 @@ def test_gradients_match_oracle():
     net = g.MLP(p32)
     X = _features_like(700, 2)
     T = np.random.default_rng(3).standard_normal((700, 2)) * 0.5
+    n = 700
     loss, grad = net.loss_grad(g.bf16_bits(X), T.astype(np.float32))
-    Lo, Go = M.loss_and_grads(P, X, T.astype(np.float32).astype(np.float64), quantize=True)
+    Lo, Go, So = M.loss_and_grads(P, X, T.astype(np.float32).astype(np.float64), quantize=True, scales=True)
     assert loss == pytest.approx(Lo, rel=1e-4)
-    go = Go.flat()
+    go, so = Go.flat(), So.flat()
+    # element by element: the device adds the same BF16 products as the
+    # oracle (which rounds every operand where the device does) in FP32, so
+    # an element differs by at most n 2^-24 of the sum of its products'
+    # magnitudes (worst-case FP32 accumulation of n terms) -- except where an
+    # intermediate (H1, H2, dY, dZ2, dZ1) lay so close to a BF16 rounding
+    # boundary or a ReLU kink that FP32 and FP64 sums round it differently;
+    # those flips move a term by one BF16 ulp (2^-8) and are rare
+    bound = n * 2.0 ** -24 * so
+    err = np.abs(grad.astype(np.float64) - go)
+    ok = err <= bound + 1e-30
+    assert ok.mean() > 0.99, ok.mean()
+    assert np.all(err <= bound + 2.0 ** -7 * so + 1e-30), np.max((err - bound) / so)
     for name, a, b in (("W1", 0, 3072), ("b1", 3072, 3136), ("W2", 3136, 7232), ("b2", 7232, 7296),
                        ("W3", 7296, 7424), ("b3", 7424, 7426)):
-        d = np.linalg.norm(grad[a:b] - go[a:b]) / np.linalg.norm(go[a:b])
-        assert d < 1e-2, (name, d)
+        assert ok[a:b].mean() > 0.97, (name, ok[a:b].mean())
 
 
 def test_training_reduces_loss():
@@ -131,23 +143,29 @@ def test_features_match_oracle(which):
     assert d.max() <= 1
 
 
-def test_learned_proposals_reach_the_target():
+def test_learned_proposals_reach_the_target_in_fewer_iterations():
     # trained on the method's own trajectories (a disk with DistMesh, an
     # annulus with the hybrid), applied to annuli drawn with other seeds: the
     # iterations to the plain method's converged minimum angle minus 1 degree.
-    # The gain of one training varies (the trajectories the pairs come from
-    # are not bit-reproducible): totals of 130, 162 and 220 against the plain
-    # 161 were seen with the same code.  The test asserts what every training
-    # must do -- reach the target on every seed, keep some proposals, never be
-    # far slower -- and the benchmark measures the gain over seeds.
+    # Every iteration is bit-reproducible (stable bucket sort, fixed-order
+    # sums), so the pairs and the network of a training seed are too: this
+    # network needs 135 iterations on the three annuli against the plain
+    # method's 161.  Each proposal is judged by running the plain iteration
+    # beside it, so at 2e5 points the wall times are about equal; the
+    # benchmark measures the wall-time gain at 1e6 points.
     import workloads as W
     from paper_2309_13824_gb300 import learn
 
     disk = W.disk_workload(n=10000)
     ann = W.annulus_workload(n=200000, seed=11)
-    net, loss, npairs = learn.train([(disk.sdf, disk.sizing, disk.points, 0, 0),
-                                     (ann.sdf, ann.sizing, ann.points, 2, 0)], epochs=30, fine_epochs=5)
+    trajectories = [(disk.sdf, disk.sizing, disk.points, 0, 0), (ann.sdf, ann.sizing, ann.points, 2, 0)]
+    net, loss, npairs = learn.train(trajectories, epochs=30, fine_epochs=5, seed=0)
     assert npairs > 10**6 and loss < 0.01
+    again, loss2, _ = learn.train(trajectories, epochs=30, fine_epochs=5, seed=0)
+    # reproducible training: identical parameters (the gradient sums are added
+    # in a fixed order; the reported loss total uses atomics, so only its
+    # last bits may differ)
+    assert np.array_equal(again.params(), net.params()) and loss2 == pytest.approx(loss, rel=1e-12)
     its_plain = its_learned = 0
     for seed in (21, 22, 23):
         wl = W.annulus_workload(n=200000, seed=seed)
@@ -161,4 +179,52 @@ def test_learned_proposals_reach_the_target():
         its_learned += sl["iterations"]
         print(f"seed {seed}: plain {sp['iterations']} iterations, learned {sl['iterations']} "
               f"({sl['accepted']} proposals kept, {sl['rejected']} undone)")
-    assert its_learned < 1.5 * its_plain, (its_learned, its_plain)
+    assert its_learned < 0.9 * its_plain, (its_learned, its_plain)
+
+
+def test_batched_learned_proposals():
+    # the batched form with the learned part: three annuli stepped as one
+    # batch, each judged on its own statistics, reach their own targets (the
+    # plain batch's converged minimum angle minus 1 degree, per mesh); every
+    # mesh's proposal count stays within the rounds, and a mesh that reached
+    # its target stops.  Whether a mesh gets there in fewer iterations than
+    # the plain batch varies from mesh to mesh (a kept proposal can leave a
+    # worst triangle that later iterations take long to repair), so the
+    # counts are reported, not asserted; the benchmark measures the batch's
+    # wall time at 1e6 points.
+    import paper_2309_13824_gb300 as g
+    import workloads as W
+    from paper_2309_13824_gb300 import learn
+
+    disk = W.disk_workload(n=10000)
+    ann = W.annulus_workload(n=200000, seed=11)
+    net, _, _ = learn.train([(disk.sdf, disk.sizing, disk.points, 0, 0),
+                             (ann.sdf, ann.sizing, ann.points, 2, 0)], epochs=30, fine_epochs=5, seed=0)
+    meshes = []
+    for sd in (31, 32, 33):
+        wl = W.annulus_workload(n=100000, seed=sd)
+        meshes.append((wl.sdf, wl.sizing, wl.points))
+    conv = g.MeshBatch(meshes, method=2, autotune=False).step(2000)
+    assert all(c["terminated"] for c in conv)
+    targets = [c["min_angle_deg"] - 1.0 for c in conv]
+
+    def batch_with_targets():
+        b = g.MeshBatch(meshes, method=2, autotune=False)
+        for k, q in enumerate(targets):
+            b.set_quality_target(q, mesh=k)
+        return b
+
+    plain = batch_with_targets().step(2000)
+    b = batch_with_targets()
+    learned = b.step_learned(net, 2000, max_rounds=8)
+    for k in range(3):
+        assert plain[k]["target_reached"] and learned[k]["target_reached"], (k, plain[k], learned[k])
+        assert learned[k]["min_angle_deg"] >= targets[k]
+        assert learned[k]["accepted"] + learned[k]["rejected"] <= 8
+        print(f"mesh {k}: plain {plain[k]['iterations']} iterations, learned {learned[k]['iterations']} "
+              f"({learned[k]['accepted']} kept, {learned[k]['rejected']} undone)")
+    assert sum(x["accepted"] for x in learned) > 0
+    # every mesh has terminated: further calls leave the positions as they are
+    before = [b.points(k).copy() for k in range(3)]
+    b.step_learned(net, 20)
+    assert all(np.array_equal(before[k], b.points(k)) for k in range(3))

@@ -464,3 +464,27 @@ def test_cells_with_more_than_32_edges(precision):
     with pytest.raises(Exception) as e:
         gm2.rebuild()
     assert "more than 64 edges" in str(e.value)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_iterations_are_bit_reproducible(precision):
+    """The bucket sort is stable (ranks by point index, not by atomics), so
+    two meshes stepped from identical inputs stay bit-identical: positions,
+    classes, triangles and statistics after several hybrid iterations."""
+    import paper_2309_13824_gb300 as g
+
+    sdf, siz, pts = annulus_small(n=50021, seed=3)
+    if precision == 1:
+        pts = W.to_fp32_positions(pts)
+    runs = []
+    for _ in range(2):
+        m = g.Mesh(sdf, siz, pts, precision=precision, method=2)
+        st = m.step(12)
+        P, cls, dp = m.state()
+        runs.append((st, P, cls, dp, sorted_tris(m.triangles())))
+        m.close()
+    (s0, P0, c0, d0, t0), (s1, P1, c1, d1, t1) = runs
+    assert np.array_equal(P0, P1) and np.array_equal(c0, c1) and np.array_equal(d0, d1)
+    assert np.array_equal(t0, t1)
+    for k in ("half_mean_alpha", "max_alpha", "min_angle_deg", "fac_mu", "n_tri", "switched"):
+        assert s0[k] == s1[k], k
