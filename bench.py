@@ -818,6 +818,12 @@ def main():
                                      "terminated": bool(s["terminated"]), "min_angle_deg": s["min_angle_deg"],
                                      "half_mean_alpha": s["half_mean_alpha"], "max_alpha": s["max_alpha"],
                                      "mean_size_dev": s["mean_size_dev"], "n_tri": s["n_tri"]}
+        # the paper's table of the mesh at termination (quality report of the last rebuild)
+        q = tq.quality()
+        extras["time_to_quality"]["quality_report"] = {
+            k: q[k] for k in ("median_alpha", "mean_alpha", "max_alpha", "std_alpha", "median_beta", "mean_beta",
+                              "max_beta", "std_beta", "frac_alpha_lt_1_2", "frac_alpha_lt_2", "min_angle_deg",
+                              "alpha_hist", "mean_size_dev", "p95_size_dev")}
         tq.close()
         # FP32-position mode on the same workload
         if args.precision == 0:

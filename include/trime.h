@@ -119,6 +119,33 @@ typedef struct {
     int64_t vor_resolve;       /* polygon vertices solved again in double                 */
 } mesh_stats;
 
+/* Quality report of a mesh's last rebuild (mesh_quality): the statistics
+ * the paper tabulates at termination (Sec. 5 tables: median, mean, maximum
+ * and standard deviation of the aspect ratio alpha = R_circ / (2 R_in) and
+ * the edge ratio beta = l_max / l_min of the valid triangles (Sec. 3.6 Eqs.
+ * 11-12), the shares with alpha < 1.2 and < 2), the minimum angle, a
+ * histogram of alpha, and the deviation of the valid edges' lengths from the
+ * sizing field, |l / (fac_mu mu(m)) - 1| with Eq. 3's fac_mu.  All in FP64
+ * at the positions that rebuild triangulated. */
+typedef struct mesh_quality_stats {
+    int64_t n_tri;             /* valid triangles                                        */
+    int64_t n_edges;           /* valid edges                                            */
+    double median_alpha;       /* lower median: rank floor((n - 1) / 2) of the sorted values */
+    double median_beta;
+    double mean_alpha, mean_beta;
+    double max_alpha, max_beta;
+    double std_alpha, std_beta;       /* population standard deviations               */
+    double frac_alpha_lt_1_2;  /* share of the triangles with alpha < 1.2                */
+    double frac_alpha_lt_2;    /* share with alpha < 2                                   */
+    double min_angle_deg;
+    int64_t alpha_hist[10];    /* triangles per alpha bin; bin k holds [e_k, e_{k+1}) with
+                                  e = 1, 1.05, 1.1, 1.2, 1.3, 1.5, 2, 3, 5, 10, +inf
+                                  (a value rounded below 1 counts in bin 0)            */
+    double fac_mu;             /* Eq. 3 factor of the rebuild                            */
+    double mean_size_dev;      /* mean of |l / (fac_mu mu(m)) - 1| over the valid edges  */
+    double p95_size_dev;       /* its 95th percentile (nearest rank: rank ceil(0.95 n))  */
+} mesh_quality_stats;
+
 typedef struct mesh_s mesh_t;
 
 /* Fill *p with the defaults listed above.  Never fails. */
@@ -166,6 +193,14 @@ int mesh_step(mesh_t* m, int32_t n_iters, mesh_stats* stats);
 
 /* N_current and N_total of a mesh (host-side state; no synchronisation). */
 int mesh_get_count(mesh_t* m, int64_t* n_current, int64_t* n_total);
+
+/* The quality report of the last rebuild (of mesh_rebuild, or of the last
+ * iteration of mesh_step that re-triangulated; after mesh_set_state or an
+ * addition a rebuild runs first), into *q.  The per-triangle and per-edge
+ * values are computed on the device; medians and the percentile are exact
+ * order statistics.  Synchronous.  Errors: TRIME_EINVAL, TRIME_ENOMEM,
+ * TRIME_ECUDA. */
+int mesh_quality(mesh_t* m, mesh_quality_stats* q);
 
 /* Valid triangles of the last rebuild as int32 (a, b, c) point indices, a the
  * smallest index, counter-clockwise; order unspecified.  tri may be host or
@@ -567,6 +602,9 @@ int mesh_batch_step(mesh_batch_t* b, int32_t n_iters, mesh_stats* stats);
  * mesh_set_method_state for mesh index `mesh` of the batch (0-based, point
  * indices local to that mesh). */
 int mesh_batch_get_triangles(mesh_batch_t* b, int32_t mesh, int32_t* tri, int64_t cap, int64_t* n_out);
+
+/* mesh_quality for one mesh of the batch. */
+int mesh_batch_quality(mesh_batch_t* b, int32_t mesh, mesh_quality_stats* q);
 int mesh_batch_get_points(mesh_batch_t* b, int32_t mesh, void* xy, int64_t cap, int64_t* n_out);
 int mesh_batch_set_state(mesh_batch_t* b, int32_t mesh, const void* xy, const uint8_t* cls, const double* dprev);
 int mesh_batch_set_method_state(mesh_batch_t* b, int32_t mesh, int32_t switched, double prev_half_alpha,

@@ -64,6 +64,15 @@ class _Stats(C.Structure):
                 ("added", C.c_int64), ("n_points", C.c_int64)]
 
 
+class _Quality(C.Structure):
+    _fields_ = [("n_tri", C.c_int64), ("n_edges", C.c_int64), ("median_alpha", C.c_double),
+                ("median_beta", C.c_double), ("mean_alpha", C.c_double), ("mean_beta", C.c_double),
+                ("max_alpha", C.c_double), ("max_beta", C.c_double), ("std_alpha", C.c_double),
+                ("std_beta", C.c_double), ("frac_alpha_lt_1_2", C.c_double), ("frac_alpha_lt_2", C.c_double),
+                ("min_angle_deg", C.c_double), ("alpha_hist", C.c_int64 * 10), ("fac_mu", C.c_double),
+                ("mean_size_dev", C.c_double), ("p95_size_dev", C.c_double)]
+
+
 def _load():
     global _lib
     if _lib is None:
@@ -79,6 +88,8 @@ def _load():
             getattr(lib, name).argtypes = [C.c_void_p]
         lib.om_rebuild_sample.argtypes = [C.c_void_p, i64p, C.c_int64, C.c_int]
         lib.om_set_threads.argtypes = [C.c_void_p, C.c_int]
+        lib.om_quality_report.argtypes = [C.c_void_p, C.POINTER(_Quality)]
+        lib.om_quality_report.restype = None
         lib.om_rebuild_sample_mt.restype = C.c_int64
         lib.om_rebuild_sample_mt.argtypes = [C.c_void_p, i64p, C.c_int64, C.c_int, C.c_int]
         lib.om_sample_triangles.restype = C.c_int64
@@ -407,6 +418,14 @@ class OracleMesh:
         s = _Stats()
         self._lib.om_get_stats(self._h, C.byref(s))
         return {name: getattr(s, name) for name, _ in _Stats._fields_}
+
+    def quality(self) -> dict:
+        """om_quality_report of the last rebuild (at the current positions)."""
+        q = _Quality()
+        self._lib.om_quality_report(self._h, C.byref(q))
+        d = {name: getattr(q, name) for name, _ in _Quality._fields_}
+        d["alpha_hist"] = list(q.alpha_hist)
+        return d
 
     def triangles(self) -> np.ndarray:
         n = self._lib.om_num_triangles(self._h)

@@ -1729,6 +1729,90 @@ void om_get_stats(const om_mesh* m, om_stats* s) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* quality report (Sec. 3.6 Eqs. 11-12; the statistics of the Sec. 5 tables) */
+/* ------------------------------------------------------------------------ */
+static int dbl_cmp(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void om_quality_report(const om_mesh* m, om_quality* q) {
+    static const double edge[10] = {1.0, 1.05, 1.1, 1.2, 1.3, 1.5, 2.0, 3.0, 5.0, 10.0};
+    memset(q, 0, sizeof *q);
+    int64_t n = m->ntri, ne = m->nedge;
+    q->n_tri = n;
+    q->n_edges = ne;
+    q->fac_mu = m->st.fac_mu;
+    double* al = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* be = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double minang = 180.0;
+    for (int64_t t = 0; t < n; t++) {
+        int32_t a = m->tri[3 * t], b = m->tri[3 * t + 1], c = m->tri[3 * t + 2];
+        double la = hypot(m->x[b] - m->x[c], m->y[b] - m->y[c]);
+        double lb = hypot(m->x[c] - m->x[a], m->y[c] - m->y[a]);
+        double lc = hypot(m->x[a] - m->x[b], m->y[a] - m->y[b]);
+        double o = (m->x[b] - m->x[a]) * (m->y[c] - m->y[a]) - (m->y[b] - m->y[a]) * (m->x[c] - m->x[a]);
+        double A = 0.5 * fabs(o);
+        al[t] = (la * lb * lc * (la + lb + lc)) / (16.0 * A * A);
+        double lmax = fmax(la, fmax(lb, lc)), lmin = fmin(la, fmin(lb, lc));
+        be[t] = lmax / lmin;
+        double p, r;
+        if (lmin == la) { p = lb; r = lc; } else if (lmin == lb) { p = la; r = lc; } else { p = la; r = lb; }
+        double cs = (p * p + r * r - lmin * lmin) / (2.0 * p * r);
+        if (cs > 1.0) cs = 1.0;
+        if (cs < -1.0) cs = -1.0;
+        double ang = acos(cs) * (180.0 / M_PI);
+        if (ang < minang) minang = ang;
+    }
+    if (n > 0) {
+        double sa = 0, sb = 0;
+        for (int64_t t = 0; t < n; t++) { sa += al[t]; sb += be[t]; }
+        q->mean_alpha = sa / (double)n;
+        q->mean_beta = sb / (double)n;
+        double va = 0, vb = 0;
+        int64_t lt12 = 0, lt2 = 0;
+        for (int64_t t = 0; t < n; t++) {
+            va += (al[t] - q->mean_alpha) * (al[t] - q->mean_alpha);
+            vb += (be[t] - q->mean_beta) * (be[t] - q->mean_beta);
+            if (al[t] < 1.2) lt12++;
+            if (al[t] < 2.0) lt2++;
+            int k = 0;
+            while (k < 9 && al[t] >= edge[k + 1]) k++;
+            q->alpha_hist[k]++;
+            if (al[t] > q->max_alpha) q->max_alpha = al[t];
+            if (be[t] > q->max_beta) q->max_beta = be[t];
+        }
+        q->std_alpha = sqrt(va / (double)n);
+        q->std_beta = sqrt(vb / (double)n);
+        q->frac_alpha_lt_1_2 = (double)lt12 / (double)n;
+        q->frac_alpha_lt_2 = (double)lt2 / (double)n;
+        q->min_angle_deg = minang;
+        qsort(al, (size_t)n, sizeof(double), dbl_cmp);
+        qsort(be, (size_t)n, sizeof(double), dbl_cmp);
+        q->median_alpha = al[(n - 1) / 2];
+        q->median_beta = be[(n - 1) / 2];
+    }
+    free(al);
+    free(be);
+    if (ne > 0) {
+        double* dv = (double*)malloc(sizeof(double) * (size_t)ne);
+        double sd = 0;
+        for (int64_t e = 0; e < ne; e++) {
+            int32_t i = m->edge[2 * e], j = m->edge[2 * e + 1];
+            double dx = m->x[j] - m->x[i], dy = m->y[j] - m->y[i];
+            double mu = bilin(&m->siz, (m->x[i] + m->x[j]) * 0.5, (m->y[i] + m->y[j]) * 0.5);
+            dv[e] = fabs(sqrt(dx * dx + dy * dy) / (q->fac_mu * mu) - 1.0);
+            sd += dv[e];
+        }
+        q->mean_size_dev = sd / (double)ne;
+        qsort(dv, (size_t)ne, sizeof(double), dbl_cmp);
+        int64_t r = (int64_t)ceil(0.95 * (double)ne) - 1;
+        q->p95_size_dev = dv[r < 0 ? 0 : r];
+        free(dv);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 3.1: SDF from clockwise line segments (brute force)                 */
 /* ------------------------------------------------------------------------ */
 static void seg_normal(const double* xy, int64_t nv, int64_t k, double* nx, double* ny) {

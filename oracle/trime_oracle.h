@@ -135,6 +135,24 @@ void om_get_cell_area(const om_mesh* m, double* a);
 void om_get_quad_level(const om_mesh* m, int32_t* lv);
 void om_get_stats(const om_mesh* m, om_stats* s);
 
+/* The mesh-quality statistics the paper tabulates at termination (Sec. 5:
+ * median, mean, maximum, standard deviation of alpha and beta, shares with
+ * alpha < 1.2 and < 2) of the valid triangles of the last rebuild, at the
+ * current positions (call after om_rebuild), plus the minimum angle, the
+ * alpha histogram (bin k: [e_k, e_{k+1}), e = 1, 1.05, 1.1, 1.2, 1.3, 1.5,
+ * 2, 3, 5, 10, inf; values below 1 in bin 0) and |l / (fac_mu mu(m)) - 1|
+ * over the valid edges by mean and 95th percentile.  Medians: the value of
+ * rank floor((n-1)/2) of the sorted values; the percentile: rank
+ * ceil(0.95 n) - 1 (nearest rank). */
+typedef struct {
+    int64_t n_tri, n_edges;
+    double median_alpha, median_beta, mean_alpha, mean_beta, max_alpha, max_beta, std_alpha, std_beta;
+    double frac_alpha_lt_1_2, frac_alpha_lt_2, min_angle_deg;
+    int64_t alpha_hist[10];
+    double fac_mu, mean_size_dev, p95_size_dev;
+} om_quality;
+void om_quality_report(const om_mesh* m, om_quality* q);
+
 /* Per-cell views for pins. */
 int om_get_ring(const om_mesh* m, int64_t i, int32_t* labels, int cap);
 int om_get_cell_polygon(const om_mesh* m, int64_t i, double* xy, int cap);

@@ -81,7 +81,8 @@ EXPORTS = ["mesh_segment_sdf_points", "mesh_adf_build", "mesh_adf_cells", "mesh_
            "mesh_set_tuning", "mesh_batch_set_tuning", "mesh_tc_gemm_bf16", "mlp_create", "mlp_destroy",
            "mlp_get_params", "mlp_set_params", "mlp_forward", "mlp_loss_grad", "mlp_train", "mesh_features",
            "mesh_collect_pairs", "mesh_propose", "mesh_step_learned", "mesh_set_quality_target",
-           "mesh_batch_set_quality_target", "mesh_measure_pipe_peaks", "mesh_batch_step_learned"]
+           "mesh_batch_set_quality_target", "mesh_measure_pipe_peaks", "mesh_batch_step_learned", "mesh_quality",
+           "mesh_batch_quality"]
 
 MLP_IN = 48
 MLP_PARAMS = 7426
@@ -156,6 +157,8 @@ def lib():
     L.mesh_batch_step_learned.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32,
                                           P(mesh_stats), P(C.c_int32), P(C.c_int32)]
     L.mesh_batch_set_tuning.argtypes = [vp, C.c_double, C.c_int32]
+    L.mesh_quality.argtypes = [vp, P(mesh_quality_stats)]
+    L.mesh_batch_quality.argtypes = [vp, C.c_int32, P(mesh_quality_stats)]
     L.mesh_batch_destroy.argtypes = [vp]
     L.mesh_batch_destroy.restype = None
     L.mesh_get_count.argtypes = [vp, P(C.c_int64), P(C.c_int64)]
@@ -190,7 +193,7 @@ def lib():
                  "mesh_tc_gemm_bf16", "mlp_create", "mlp_get_params", "mlp_set_params", "mlp_forward",
                  "mlp_loss_grad", "mlp_train", "mesh_features", "mesh_collect_pairs", "mesh_propose",
                  "mesh_step_learned", "mesh_set_quality_target", "mesh_batch_set_quality_target",
-                 "mesh_measure_pipe_peaks", "mesh_batch_step_learned", "mesh_segment_sdf_points", "mesh_adf_build", "mesh_adf_cells",
+                 "mesh_measure_pipe_peaks", "mesh_batch_step_learned", "mesh_quality", "mesh_batch_quality", "mesh_segment_sdf_points", "mesh_adf_build", "mesh_adf_cells",
                  "mesh_adf_size", "mesh_adf_export", "mesh_adf_eval"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -443,6 +446,24 @@ def _stats_dict(s: mesh_stats) -> dict:
     return {name: getattr(s, name) for name, _ in mesh_stats._fields_}
 
 
+class mesh_quality_stats(C.Structure):
+    _fields_ = [("n_tri", C.c_int64), ("n_edges", C.c_int64), ("median_alpha", C.c_double),
+                ("median_beta", C.c_double), ("mean_alpha", C.c_double), ("mean_beta", C.c_double),
+                ("max_alpha", C.c_double), ("max_beta", C.c_double), ("std_alpha", C.c_double),
+                ("std_beta", C.c_double), ("frac_alpha_lt_1_2", C.c_double), ("frac_alpha_lt_2", C.c_double),
+                ("min_angle_deg", C.c_double), ("alpha_hist", C.c_int64 * 10), ("fac_mu", C.c_double),
+                ("mean_size_dev", C.c_double), ("p95_size_dev", C.c_double)]
+
+
+ALPHA_BIN_EDGES = (1.0, 1.05, 1.1, 1.2, 1.3, 1.5, 2.0, 3.0, 5.0, 10.0)
+
+
+def _quality_dict(q: mesh_quality_stats) -> dict:
+    d = {name: getattr(q, name) for name, _ in mesh_quality_stats._fields_}
+    d["alpha_hist"] = list(q.alpha_hist)
+    return d
+
+
 class Mesh:
     """One mesh on the current CUDA device (a handle to mesh_t)."""
 
@@ -509,6 +530,12 @@ class Mesh:
         ms = np.zeros(7)
         _check(lib().mesh_profile_step(self._h, n_iters, ms.ctypes.data_as(C.c_void_p)))
         return dict(zip(["bucket", "voronoi", "emit", "stats", "update", "post", "total"], ms))
+
+    def quality(self) -> dict:
+        """mesh_quality: the quality report of the last rebuild."""
+        q = mesh_quality_stats()
+        _check(lib().mesh_quality(self._h, C.byref(q)))
+        return _quality_dict(q)
 
     def triangles(self, out=None):
         """Valid triangles (int32, smallest id first, CCW), order unspecified.
@@ -706,6 +733,11 @@ class MeshBatch:
         nc = t.n_candidates
         return {"n_opt": t.n_opt, "lanes": t.lanes, "n_slots": t.n_slots, "n_buckets": t.n_buckets,
                 "candidates": [(t.cand_n_opt[k], t.cand_lanes[k], t.cand_ms[k]) for k in range(nc)]}
+
+    def quality(self, mesh: int) -> dict:
+        q = mesh_quality_stats()
+        _check(lib().mesh_batch_quality(self._h, mesh, C.byref(q)))
+        return _quality_dict(q)
 
     def triangles(self, mesh: int):
         L = lib()

@@ -22,7 +22,8 @@ OUT_DIR = PKG / "_build"
 LIB = OUT_DIR / "libtrime_gb300.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["voronoi_f64.cu", "voronoi_f32.cu", "voronoi_f64b.cu", "voronoi_f32b.cu", "bucket.cu", "emit.cu",
-         "update.cu", "mesh.cu", "mlp.cu", "peaks.cu", "addition.cu", "sdf.cu", "sizing.cu", "autosize.cu", "init.cu", "adf.cu"]
+         "update.cu", "mesh.cu", "mlp.cu", "peaks.cu", "addition.cu", "sdf.cu", "sizing.cu", "autosize.cu", "init.cu", "adf.cu",
+         "quality.cu"]
 
 
 def _nvcc() -> str:

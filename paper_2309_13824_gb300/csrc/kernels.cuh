@@ -212,6 +212,25 @@ void launch_propose(const IterArgs<T>& a, const float* Y, float jump, cudaStream
 template <typename T>
 void launch_targets(const IterArgs<T>& a, const T* px, const T* py, const float* H, float* Tout, cudaStream_t st);
 
+// the quality report of the slots [s0, s0 + ns) of one mesh's last rebuild
+// (quality.cu): device scratch for counts, offsets, per-triangle and
+// per-edge values (cap_t triangles, cap_e edges), block partials and a
+// 256-bin histogram with its pinned host copy
+struct QPartial;
+}  // namespace trime
+struct mesh_quality_stats;  // include/trime.h
+namespace trime {
+struct QBufs {
+    int32_t *tcnt, *ecnt, *toff, *eoff, *scan_tmp;
+    double *alpha, *beta, *ang, *dev;
+    QPartial* part;
+    unsigned int* hist;
+    unsigned int* hhist;
+};
+template <typename T>
+int quality_report(const IterArgs<T>& a, int32_t s0, int32_t ns, double fac_mu, const QBufs& b, int64_t cap_t,
+                   int64_t cap_e, cudaStream_t st, ::mesh_quality_stats* q, std::string& err);
+
 // records the calling thread's error message (mesh_last_error) and returns code
 int set_error(int code, const char* msg);
 

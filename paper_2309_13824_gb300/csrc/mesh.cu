@@ -75,6 +75,7 @@ struct mesh_s {
     int lanes = 8;               // Voronoi lanes per cell of the first pass
     double nopt = 3.3;           // points per bucket the grids are sized for
     std::vector<TuneCand> tune;  // autotuning record
+    struct QualityScratch* qs = nullptr;
     cudaStream_t user = nullptr, st = nullptr;
     cudaEvent_t ev = nullptr;
     void *cx = nullptr, *cy = nullptr, *cdp = nullptr, *sx = nullptr, *sy = nullptr, *sdp = nullptr;
@@ -118,6 +119,12 @@ struct mesh_s {
 };
 
 struct mesh_batch_s : mesh_s {};
+
+// scratch of the quality report, allocated on its first use
+struct QualityScratch {
+    QBufs b{};
+    int64_t cap_t = 0, cap_e = 0;
+};
 
 // learned proposals: scratch and the saved state of a judged proposal
 struct LearnBufs {
@@ -871,6 +878,10 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
 static void destroy(mesh_s* m) {
     if (m->st) cudaStreamSynchronize(m->st);
     delete m->learn;
+    if (m->qs) {
+        if (m->qs->b.hhist) cudaFreeHost(m->qs->b.hhist);
+        delete m->qs;
+    }
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     for (void* p : m->allocs) cudaFree(p);
     if (m->hctrl) cudaFreeHost(m->hctrl);
@@ -1049,6 +1060,51 @@ static int get_triangles(mesh_s* m, int k, int32_t* tri, int64_t cap, int64_t* n
         CUDA_TRY(cudaStreamSynchronize(m->st));
     }
     CUDA_TRY(cudaGetLastError());
+    return sync_out(m);
+}
+
+static int quality(mesh_s* m, int k, mesh_quality_stats* q) {
+    const Part& p = m->parts[k];
+    int rc = sync_in(m);
+    if (rc) return rc;
+    if (m->tri_stale) {
+        enqueue(m, false, 1);
+        if ((rc = force_retri(m, -1))) return rc;
+        m->tri_stale = false;
+    }
+    if (!m->qs) {
+        QualityScratch* Q = new QualityScratch();
+        size_t N = (size_t)std::max<int64_t>(m->nslots, m->ncap) + 1;
+        Q->cap_t = 2 * (int64_t)N + 16;
+        Q->cap_e = 3 * (int64_t)N + 16;
+        Q->b.tcnt = dalloc<int32_t>(m, N, rc);
+        Q->b.ecnt = dalloc<int32_t>(m, N, rc);
+        Q->b.toff = dalloc<int32_t>(m, N, rc);
+        Q->b.eoff = dalloc<int32_t>(m, N, rc);
+        Q->b.scan_tmp = dalloc<int32_t>(m, N / 4096 + 2, rc);
+        Q->b.alpha = dalloc<double>(m, (size_t)Q->cap_t, rc);
+        Q->b.beta = dalloc<double>(m, (size_t)Q->cap_t, rc);
+        Q->b.ang = dalloc<double>(m, (size_t)Q->cap_t, rc);
+        Q->b.dev = dalloc<double>(m, (size_t)Q->cap_e, rc);
+        Q->b.part = reinterpret_cast<QPartial*>(dalloc<char>(m, 152 * 256, rc));
+        Q->b.hist = dalloc<unsigned int>(m, 256, rc);
+        if (!rc && cudaMallocHost(&Q->b.hhist, 256 * sizeof(unsigned int)) != cudaSuccess)
+            rc = fail(TRIME_ENOMEM, "pinned alloc");
+        if (rc) {
+            if (Q->b.hhist) cudaFreeHost(Q->b.hhist);
+            delete Q;
+            return rc;
+        }
+        m->qs = Q;
+    }
+    if ((rc = read_ctrl(m))) return rc;
+    std::string err;
+    const double fac_mu = m->hctrl[k].fac_mu;
+    int r = m->prec == 0 ? quality_report<double>(make_args<double>(m, 1), p.soff, (int32_t)p.n, fac_mu, m->qs->b,
+                                                  m->qs->cap_t, m->qs->cap_e, m->st, q, err)
+                         : quality_report<float>(make_args<float>(m, 1), p.soff, (int32_t)p.n, fac_mu, m->qs->b,
+                                                 m->qs->cap_t, m->qs->cap_e, m->st, q, err);
+    if (r) return fail(r == -1 ? TRIME_ECUDA : TRIME_EDEVICE, err);
     return sync_out(m);
 }
 
@@ -1715,6 +1771,11 @@ int mesh_adf_cells(mesh_t* m, double fac_etol, int32_t* cells, double* tol, int6
     return TRIME_OK;
 }
 
+int mesh_quality(mesh_t* m, mesh_quality_stats* q) {
+    if (!m || !q) return fail(TRIME_EINVAL, "NULL argument");
+    return quality(m, 0, q);
+}
+
 int mesh_get_triangles(mesh_t* m, int32_t* tri, int64_t cap, int64_t* n_out) {
     if (!m || !n_out) return fail(TRIME_EINVAL, "NULL argument");
     return get_triangles(m, 0, tri, cap, n_out);
@@ -1925,6 +1986,12 @@ int mesh_batch_set_quality_target(mesh_batch_t* b, int32_t mesh, double min_angl
     if (!b || !(min_angle_deg >= 0) || min_angle_deg > 60) return fail(TRIME_EINVAL, "bad argument");
     if (mesh < -1 || mesh >= (int32_t)b->parts.size()) return fail(TRIME_EINVAL, "mesh index out of range");
     return set_target(b, mesh, min_angle_deg);
+}
+
+int mesh_batch_quality(mesh_batch_t* b, int32_t mesh, mesh_quality_stats* q) {
+    if (!b || !q) return fail(TRIME_EINVAL, "NULL argument");
+    if (mesh < 0 || mesh >= (int32_t)b->parts.size()) return fail(TRIME_EINVAL, "mesh index out of range");
+    return quality(b, mesh, q);
 }
 
 int mesh_batch_step_learned(mesh_batch_t* b, mlp_t* net, int32_t n_iters, int32_t every, double jump,

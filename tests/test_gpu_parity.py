@@ -385,6 +385,13 @@ def test_full_size_mid_trajectory(precision):
         _, tg = _tri_equal(gm, om)
         if method == 0:
             assert np.array_equal(t_run, tg)
+            # the quality report of this rebuild (a8): device against oracle
+            qg, qo = gm.quality(), om.quality()
+            assert qg["n_tri"] == qo["n_tri"] and qg["n_edges"] == qo["n_edges"]
+            assert np.abs(np.array(qg["alpha_hist"]) - np.array(qo["alpha_hist"])).sum() <= 2
+            for k in ("median_alpha", "median_beta", "mean_alpha", "max_alpha"):
+                assert qg[k] == pytest.approx(qo[k], rel=1e-12), k
+            assert qg["p95_size_dev"] == pytest.approx(qo["p95_size_dev"], rel=1e-10 if precision == 0 else 2e-6)
         _compare_step(gm, om, precision, method)
         gm.close()
 
