@@ -8,7 +8,7 @@ sampling with density proportional to 1/h^2 (seed 1), hybrid method
 (bucketing, Voronoi cells, triangle emission and validity, quality, move,
 point treatment) over all points.
 
-    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-extras] [--no-sweep] [--no-cpu]
 
 Prints one JSON line (rank 0).  N > 1 runs N independent replicas, one per
 GPU (the meshes do not exchange data), and reports their aggregate.
@@ -51,9 +51,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the legs beyond the headline iteration")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--n-opt", type=float, default=None, help="points per neighbour bucket (default 3.3)")
-    ap.add_argument("--sweep", action="store_true",
-                    help="add the N sweep (annulus 1e4..1e7, square 1e6) and the 1e7-point star "
-                         "(also with --no-extras)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the N sweep (annulus 1e4..1e7, square 1e6) and the 1e7-point star")
     return ap.parse_args()
 
 
@@ -88,7 +87,13 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
-            time.sleep(0.5)  # the first rows are written before the timed region starts
+            # nvidia-smi's start-up (driver queries) must be over before the
+            # timed region: wait for its first rows (at most 10 s)
+            t_end = time.time() + 10.0
+            while time.time() < t_end and self.proc.poll() is None:
+                if os.path.getsize(self.f.name) > 0 and open(self.f.name).read().count("\n") >= 3:
+                    break
+                time.sleep(0.05)
         except Exception:
             self.proc = None
 
@@ -154,10 +159,10 @@ def measured_peaks():
         return {}
 
 
-def committed_profile(kernel_src):
+def committed_profile(kernel_src, points=1_000_000):
     """DRAM bytes and warp instructions per launch of the Voronoi kernel from
     the committed ncu summary; both None if the kernel source changed since
-    it was captured."""
+    it was captured or the workload has another size."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "voronoi_annulus_1e6.md")
@@ -174,7 +179,7 @@ def committed_profile(kernel_src):
             wi = float(line.split(":")[1])
         if line.startswith("voronoi_cuh_sha256_16:"):
             hs = line.split(":")[1].strip()
-    return (tr, wi) if hs == digest else (None, None)
+    return (tr, wi) if hs == digest and points == 1_000_000 else (None, None)
 
 
 def flush_l2(buf):
@@ -761,7 +766,7 @@ def main():
     achieved = VORONOI_FLOP_PER_CELL * n / t_vor / 1e12
     pipe = g.mesh_measure_pipe_peaks()
     src = os.path.join(ROOT, "paper_2309_13824_gb300", "csrc", "voronoi.cuh")
-    traffic, winst = committed_profile(src)
+    traffic, winst = committed_profile(src, n)
     roofline = {"bound": "alu", "kernel": "k_voronoi", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "peak_note": f"{sm_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and clocks)",
@@ -805,7 +810,7 @@ def main():
         em.close()
 
     extras = {}
-    if args.sweep and rank == 0:
+    if not args.no_sweep and not args.no_extras and rank == 0:
         extras["sweep"] = sweep_leg(g, torch, stream, args.steps, flush)
     if not args.no_extras and rank == 0:
         # wall time to quality: hybrid from the seeds until termination

@@ -18,6 +18,7 @@ def test_committed_profile_follows_the_source_hash(tmp_path, monkeypatch):
         f"voronoi_cuh_sha256_16: {digest}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.committed_profile(str(src)) == (1234.0, 5678.0)
+    assert bench.committed_profile(str(src), 200_000) == (None, None)  # captured on 1e6 points only
     src.write_text("__global__ void k() { /* changed */ }\n")
     assert bench.committed_profile(str(src)) == (None, None)
     (prof / "voronoi_annulus_1e6.md").unlink()
