@@ -194,6 +194,12 @@ __global__ void __launch_bounds__(kThreads) k_add_write(const __grid_constant__ 
         int gi, gj;
         point_cell_fixed(V.sdf, (double)px, (double)py, gi, gj);
         a.cur.dprev[nid] = (T)V.gh[gj * (V.sdf.nx - 1) + gi];  // a first move of h_i
+        // the triangle's corners are the new point's first clipping candidates
+        int32_t* row = a.ring + (size_t)nid * kRingCap;
+        row[0] = s;
+        row[1] = j;
+        row[2] = k;
+        a.ring_n[nid] = 3;
     });
 }
 

@@ -163,6 +163,20 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const __grid_constant__ It
     const int lo = a.bstart[k], hi = a.bstart[k + 1];
     int d = lo;
     for (int q = lo; q < hi; q++) d += a.sidx[q] < i;
+    a.perm[i] = d;
+    {
+        // the point's bisector neighbours at the last rebuild (old slots):
+        // the clipping pass starts from them
+        const int nr = a.ring_n[i];
+        const int32_t* row = a.ring + (size_t)i * kRingCap;
+        int32_t* wr = a.warm + (size_t)d * kWarm;
+        int c = 0;
+        for (int t = 0; t < nr && c < kWarm; t++) {
+            int l = row[t];
+            if (l >= 0) wr[c++] = l;
+        }
+        for (; c < kWarm; c++) wr[c] = -1;
+    }
     T x = a.cur.x[i], y = a.cur.y[i];
     a.srt.x[d] = x;
     a.srt.y[d] = y;
@@ -214,6 +228,19 @@ __global__ void __launch_bounds__(kThreads) k_dups(const __grid_constant__ IterA
         for (int q = a.bstart[k]; q < e; q++)
             if (q != s && a.srt.x[q] == x && a.srt.y[q] == y && a.srt.id[q] > id) dup = 1;
         a.dom[s] = (uint8_t)dup;
+        // previous neighbours to this rebuild's slots; a label outside the
+        // mesh's own slots is dropped
+        int4* w4 = reinterpret_cast<int4*>(a.warm + (size_t)s * kWarm);
+        const int lo = V.soff, hi = V.soff + V.n;
+#pragma unroll
+        for (int h = 0; h < kWarm / 4; h++) {
+            int4 w = w4[h];
+            w.x = w.x >= lo && w.x < hi ? a.perm[w.x] : -1;
+            w.y = w.y >= lo && w.y < hi ? a.perm[w.y] : -1;
+            w.z = w.z >= lo && w.z < hi ? a.perm[w.z] : -1;
+            w.w = w.w >= lo && w.w < hi ? a.perm[w.w] : -1;
+            w4[h] = w;
+        }
     }
     unsigned m = __ballot_sync(0xffffffffu, dup);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(&V.ctrl->cnt.dup_points, (unsigned long long)__popc(m));

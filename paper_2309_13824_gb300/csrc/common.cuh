@@ -13,6 +13,7 @@ namespace trime {
 
 constexpr int kWarp = 32;
 constexpr int kRingCap = 64;  // edges per cell: 16 or 32 in a warp's lanes, up to 64 in the serial pass
+constexpr int kWarm = 8;      // neighbours of the previous triangulation a cell starts from
 constexpr double kRT = 0.70710678118654752440;  // double nearest sqrt(2)/2
 
 enum : uint8_t { CELL_INNER = 0, CELL_BOUNDARY = 1, CELL_OUTER = 2 };

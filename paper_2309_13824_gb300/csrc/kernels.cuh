@@ -72,6 +72,9 @@ struct IterArgs {
     int32_t* scan_tmp;
     int32_t* ring;
     uint8_t* ring_n;
+    int32_t* warm;     // [n * kWarm] a slot's bisector neighbours at the last rebuild (-1 padded): old slots
+                       // after the scatter, this rebuild's slots after k_dups
+    int32_t* perm;     // [n] new slot of each old slot (written by the scatter)
     float* cellR;
     uint64_t* vmask;
     EmitPartial* ep;   // [n / kThreads] one per block of the emit kernel

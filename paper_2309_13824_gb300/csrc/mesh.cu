@@ -89,6 +89,7 @@ struct mesh_s {
     int32_t *bcount = nullptr, *bstart = nullptr, *scan_tmp = nullptr;
     int32_t* ring = nullptr;
     uint8_t* ring_n = nullptr;
+    int32_t *warm = nullptr, *perm = nullptr;
     float* cellR = nullptr;
     uint64_t* vmask = nullptr;
     EmitPartial* ep = nullptr;
@@ -383,6 +384,8 @@ static IterArgs<T> make_args(mesh_s* m, int force) {
     a.scan_tmp = m->scan_tmp;
     a.ring = m->ring;
     a.ring_n = m->ring_n;
+    a.warm = m->warm;
+    a.perm = m->perm;
     a.cellR = m->cellR;
     a.vmask = m->vmask;
     a.ep = m->ep;
@@ -824,6 +827,8 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     m->nbcap = nbmax;
     m->ring = dalloc<int32_t>(m, N * kRingCap, rc);
     m->ring_n = dalloc<uint8_t>(m, N, rc);
+    m->warm = dalloc<int32_t>(m, N * kWarm, rc);
+    m->perm = dalloc<int32_t>(m, N, rc);
     m->cellR = dalloc<float>(m, N, rc);
     m->vmask = dalloc<uint64_t>(m, N, rc);
     m->ep = dalloc<EmitPartial>(m, (size_t)nblk_cap, rc);
@@ -860,6 +865,7 @@ static int create(mesh_s* m, int nparts, const mesh_grid2d* sdfs, const mesh_gri
     CUDA_TRY(cudaMemsetAsync(m->cdp, 0, N * T, m->st));
     CUDA_TRY(cudaMemsetAsync(m->cid, 0, N * sizeof(int32_t), m->st));
     CUDA_TRY(cudaMemsetAsync(m->ccls, 0, N, m->st));
+    CUDA_TRY(cudaMemsetAsync(m->ring_n, 0, N, m->st));  // no previous triangulation
     for (int k = 0; k < nparts; k++)
         if ((rc = upload_part(m, k, &sdfs[k], &sizings[k], xys ? xys[k] : nullptr, G[k]))) return rc;
     if (m->batched) {

@@ -32,7 +32,7 @@ namespace trime {
 
 constexpr float kEps = 5.9604645e-8f;  // 2^-24
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kStageCap = 96;  // staged candidates per group (16 bytes each)
+constexpr int kStageCap = 64;  // staged candidates per group (16 bytes each; one bit each in a 64-bit mask)
 // resident blocks per SM the clipping kernels are compiled for (registers:
 // 65536 / (kVoroThreads x this)); a build-time tuning knob
 #ifndef TRIME_VORO_MINB
@@ -172,6 +172,25 @@ __device__ __noinline__ bool exact_cut(const IterArgs<T>& a, const CellCtx& c, i
     return d * o > 0;
 }
 
+// Does the half-plane n.u <= s (label lab; bisector: a neighbour's bisector,
+// n = d, s = |d|^2/2) cut this lane's vertex?  A vertex on the candidate's
+// own bisector (the candidate already is one of its two edges) is not cut.
+template <typename T>
+__device__ __forceinline__ bool cuts(const Lane& L, float nx, float ny, float s, int lab, bool bisector,
+                                     const IterArgs<T>& a, const CellCtx& ctx) {
+    if (bisector && (lab == L.lab || lab == L.nlab)) return false;
+    if (bisector && L.bb) {
+        float cl = 2.0f * s;
+        float lam = fmaf(nx, L.Qx, fmaf(ny, L.Qy, cl * L.M));
+        float P = fabsf(nx) * L.PQx + fabsf(ny) * L.PQy + cl * L.PM;
+        float bound = 32.0f * kEps * P;
+        if (P > 1e-30f && lam < -bound) return true;
+        if (P > 1e-30f && lam > bound) return false;
+        return exact_cut<T>(a, ctx, L.lab, L.nlab, lab);
+    }
+    return nx * L.vx + ny * L.vy > s;
+}
+
 // Clip the group's polygon by n.u <= s (label lab) when `active`; bisector:
 // a neighbour's bisector (n = d, s = |d|^2/2).  Executed by every lane of the
 // warp.  Returns 0 ok / no-op, 1 empty cell, 2 more than G edges; any_cut
@@ -179,20 +198,7 @@ __device__ __noinline__ bool exact_cut(const IterArgs<T>& a, const CellCtx& c, i
 template <typename T, int G>
 __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, bool bisector, bool active, float RB,
                        const Grp<G>& g, const IterArgs<T>& a, const CellCtx& ctx, bool& any_cut) {
-    bool cut = false;
-    if (active && g.gl < ne) {
-        if (bisector && L.bb) {
-            float cl = 2.0f * s;
-            float lam = fmaf(nx, L.Qx, fmaf(ny, L.Qy, cl * L.M));
-            float P = fabsf(nx) * L.PQx + fabsf(ny) * L.PQy + cl * L.PM;
-            float bound = 32.0f * kEps * P;
-            if (P > 1e-30f && lam < -bound) cut = true;
-            else if (P > 1e-30f && lam > bound) cut = false;
-            else cut = exact_cut<T>(a, ctx, L.lab, L.nlab, lab);
-        } else {
-            cut = nx * L.vx + ny * L.vy > s;
-        }
-    }
+    bool cut = active && g.gl < ne && cuts<T>(L, nx, ny, s, lab, bisector, a, ctx);
     unsigned m = g.ballot(cut);
     unsigned full = ne >= 32 ? kFull : ((1u << ne) - 1u);
     int status = 0;
@@ -243,6 +249,15 @@ __device__ int clip_by(Lane& L, int& ne, float nx, float ny, float s, int lab, b
     return status;
 }
 
+// monotone key of a direction's angle, in [0, 4): the quadrant (decided by
+// the signs) plus a fraction that grows with the angle inside it
+__device__ __forceinline__ float dir_key(float x, float y) {
+    if (y >= 0.0f && x > 0.0f) return __fdividef(y, x + y);
+    if (x <= 0.0f && y > 0.0f) return 1.0f + __fdividef(-x, y - x);
+    if (y <= 0.0f && x < 0.0f) return 2.0f + __fdividef(-y, -x - y);
+    return 3.0f + __fdividef(x, x - y);
+}
+
 // one cell per group; slot < 0 marks an idle group (it still takes part in
 // every collective operation of its warp)
 template <typename T, int G>
@@ -267,51 +282,133 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     // planes only need to bound Reg_i with the S/16 margin)
     const float xf = (pi4.x - P.bx0f) + pi4.y, yf = (pi4.z - P.by0f) + pi4.w;
     const float Wf = (float)(P.bx1 - P.bx0), Hf = (float)(P.by1 - P.by0);
-    float RB, mb;
+    float RB, mb, SB = 0.0f;
+    if (P.bounded) {
+        float S = a.pS[s];
+        SB = S * (17.0f / 16.0f);
+        RB = SB * 1.0824459f * 1.0001f;  // octagon circumradius SB / cos(pi/8)
+        mb = S * (1.0f / 16.0f);
+    } else {
+        mb = 0.125f * (Wf > Hf ? Wf : Hf);
+        RB = (sqrtf(Wf * Wf + Hf * Hf) + 4.0f * mb) * 1.0001f;
+    }
     Lane L;
+    L.nx = L.ny = L.s = 0.0f;
+    L.lab = -1;
     L.bb = false;
     L.vR = 0.0f;
     L.vx = L.vy = 0.0f;
     L.nlab = -1;
     L.M = L.Qx = L.Qy = L.PM = L.PQx = L.PQy = 0.0f;
-    int ne;
-    if (P.bounded) {
-        float S = a.pS[s];
-        float SB = S * (17.0f / 16.0f);
-        RB = SB * 1.0824459f * 1.0001f;  // octagon circumradius SB / cos(pi/8)
-        mb = S * (1.0f / 16.0f);
-        const float c8[8] = {1.f, 0.70710678f, 0.f, -0.70710678f, -1.f, -0.70710678f, 0.f, 0.70710678f};
-        int t = g.gl & 7;
-        L.nx = c8[t];
-        L.ny = c8[(t + 6) & 7];
-        L.s = SB;
-        L.lab = oct_label(t);
-        ne = 8;
-    } else {
-        mb = 0.125f * (Wf > Hf ? Wf : Hf);
-        RB = (sqrtf(Wf * Wf + Hf * Hf) + 4.0f * mb) * 1.0001f;
-        ne = 4;  // enlarged box, CCW: bottom, right, top, left
-        int b = g.gl & 3;
-        int bs = b == 0 ? 2 : (b == 1 ? 1 : (b == 2 ? 3 : 0));
-        L.nx = bs == 0 ? -1.f : (bs == 1 ? 1.f : 0.f);
-        L.ny = bs == 2 ? -1.f : (bs == 3 ? 1.f : 0.f);
-        L.s = bs == 0 ? xf + mb : bs == 1 ? (Wf - xf) + mb : bs == 2 ? yf + mb : (Hf - yf) + mb;
-        L.lab = box_label(bs);
-    }
-    lane_vertex<G>(L, ne, g, RB, true, ctx);
+    int ne = 0;
     int status = 0;
-    // the domain box cuts the octagon only if one of its planes comes closer
-    // than the octagon's circumradius RB (every vertex lies within RB)
-    bool near_box = live && !(RB * 1.001f < xf + mb && RB * 1.001f < (Wf - xf) + mb &&
-                              RB * 1.001f < yf + mb && RB * 1.001f < (Hf - yf) + mb);
-    if (P.bounded && warp_any(near_box)) {
-        for (int b = 0; b < 4; b++) {
-            float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
-            float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
-            float sb = b == 0 ? xf + mb : b == 1 ? (Wf - xf) + mb : b == 2 ? yf + mb : (Hf - yf) + mb;
-            bool any_cut;
-            int st = clip_by<T, G>(L, ne, nx, ny, sb, box_label(b), false, live && status == 0, RB, g, a, ctx, any_cut);
-            if (st) status = st;
+
+    // the cell's bisector neighbours at the last rebuild, one per lane, in
+    // their ring order (points move little between rebuilds)
+    int wcs = -1;
+    if (live && g.gl < kWarm) wcs = a.warm[(size_t)s * kWarm + g.gl];
+    bool wvalid = wcs >= 0 && wcs != s;
+    float wdx = 0.f, wdy = 0.f, wd2 = INF;
+    if (wvalid) {
+        float4 pj4 = a.pf[wcs];
+        wvalid = !a.dom[wcs];
+        wdx = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y);
+        wdy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
+        wd2 = wdx * wdx + wdy * wdy;
+        if (sizeof(T) == 8 && wd2 < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
+            wdx = (float)((double)a.srt.x[wcs] - (double)a.srt.x[s]);
+            wdy = (float)((double)a.srt.y[wcs] - (double)a.srt.y[s]);
+            wd2 = wdx * wdx + wdy * wdy;
+        }
+        wvalid = wvalid && wd2 > 0.0f;
+    }
+
+    // 1. Direct construction.  If the previous neighbours, in ring order,
+    // each turn left by less than pi (a float filter on the orientation of
+    // consecutive normals), wind once around the generator, and every edge
+    // keeps a positive length (the vertex of edges t, t+1 strictly inside
+    // edge t+2: the exact cut predicate), their bisectors bound a convex
+    // polygon that is exactly the intersection of their half-planes, built in
+    // one step.  Any other case starts from the octagon (2.).
+    const unsigned wm = g.ballot(wvalid);
+    const int nw = __popc(wm);
+    bool direct = live && P.bounded && nw >= 3 && (wm & (wm + 1u)) == 0u;  // a prefix of the lanes
+    if (warp_any(direct)) {
+        if (direct) {
+            L.nx = wdx;
+            L.ny = wdy;
+            L.s = 0.5f * wd2;
+            L.lab = wcs;
+            ne = nw;
+        }
+        const int n1 = g.gl + 1 >= ne ? 0 : g.gl + 1;
+        const int n2 = g.gl + 2 >= ne ? ((g.gl + 2 - ne) & (G - 1)) : g.gl + 2;
+        const float key = dir_key(L.nx, L.ny);
+        const float ax = g.shfl(L.nx, n1), ay = g.shfl(L.ny, n1), key1 = g.shfl(key, n1);
+        const float bx = g.shfl(L.nx, n2), by = g.shfl(L.ny, n2), bs = g.shfl(L.s, n2);
+        const int blab = g.shfl(L.lab, n2);
+        lane_vertex<G>(L, ne, g, RB, direct, ctx);
+        bool bad = false, desc = false;
+        if (direct && g.gl < ne) {
+            const float D = L.nx * ay - L.ny * ax;
+            const float PD = fabsf(L.nx * ay) + fabsf(L.ny * ax);
+            desc = key1 < key;
+            bad = !(D > 64.0f * kEps * PD) || !(L.vR < RB) || cuts<T>(L, bx, by, bs, blab, true, a, ctx);
+        }
+        const unsigned badm = g.ballot(bad), descm = g.ballot(desc);
+        direct = direct && badm == 0u && __popc(descm) == 1;
+    }
+    // 2. Sequential start: the octagon (or the enlarged box)
+    const bool seq = live && !direct;
+    if (warp_any(seq)) {
+        if (seq) {
+            if (P.bounded) {
+                const float c8[8] = {1.f, 0.70710678f, 0.f, -0.70710678f, -1.f, -0.70710678f, 0.f, 0.70710678f};
+                int t = g.gl & 7;
+                L.nx = c8[t];
+                L.ny = c8[(t + 6) & 7];
+                L.s = SB;
+                L.lab = oct_label(t);
+                ne = 8;
+            } else {
+                ne = 4;  // enlarged box, CCW: bottom, right, top, left
+                int b = g.gl & 3;
+                int bs = b == 0 ? 2 : (b == 1 ? 1 : (b == 2 ? 3 : 0));
+                L.nx = bs == 0 ? -1.f : (bs == 1 ? 1.f : 0.f);
+                L.ny = bs == 2 ? -1.f : (bs == 3 ? 1.f : 0.f);
+                L.s = bs == 0 ? xf + mb : bs == 1 ? (Wf - xf) + mb : bs == 2 ? yf + mb : (Hf - yf) + mb;
+                L.lab = box_label(bs);
+            }
+        }
+        lane_vertex<G>(L, ne, g, RB, seq, ctx);
+    }
+    if (P.bounded) {
+        // a directly built polygon reaching beyond the octagon's inradius is
+        // clipped by the octagon's planes
+        const bool reach = g.ballot(direct && g.gl < ne && L.vR > SB) != 0u;
+        if (warp_any(reach)) {
+            for (int k = 0; k < 8; k++) {
+                const float c8[8] = {1.f, 0.70710678f, 0.f, -0.70710678f, -1.f, -0.70710678f, 0.f, 0.70710678f};
+                bool any_cut;
+                int st = clip_by<T, G>(L, ne, c8[k], c8[(k + 6) & 7], SB, oct_label(k), false, reach && status == 0,
+                                       RB, g, a, ctx, any_cut);
+                if (st) status = st;
+            }
+        }
+        // the domain box cuts the polygon only if one of its planes comes
+        // closer than the octagon's circumradius RB (every vertex lies within RB)
+        bool near_box = live && !(RB * 1.001f < xf + mb && RB * 1.001f < (Wf - xf) + mb &&
+                                  RB * 1.001f < yf + mb && RB * 1.001f < (Hf - yf) + mb);
+        if (warp_any(near_box)) {
+            for (int b = 0; b < 4; b++) {
+                float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
+                float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
+                float sb = b == 0 ? xf + mb : b == 1 ? (Wf - xf) + mb : b == 2 ? yf + mb : (Hf - yf) + mb;
+                bool any_cut;
+                int st = clip_by<T, G>(L, ne, nx, ny, sb, box_label(b), false, live && status == 0, RB, g, a, ctx,
+                                       any_cut);
+                if (st) status = st;
+            }
         }
     }
     float Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
@@ -321,13 +418,12 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     const float bmargin = (float)(1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy)) + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
     bool done = !live || status != 0;
     int nst = 0;
-    // apply the staged candidates nearest first (warp-uniform loop).  The
-    // nearest entry is found by a minimum over keys made of the squared
-    // distance's bits with the entry index in the lowest 7 (the order of
-    // nearly equal distances does not matter for the result); each lane
-    // marks the entries it owns (gl, gl + G, ...) once taken.
+    unsigned used = 0;  // per lane: its staged entries (gl, gl + G, ...) already taken or dropped
+    // apply the staged entries that are not yet used, nearest first
+    // (warp-uniform loop).  The nearest entry is found by a minimum over keys
+    // made of the squared distance's bits with the entry index in the lowest
+    // 7 (the order of nearly equal distances does not matter for the result).
     auto flush = [&]() {
-        unsigned used = 0;
         while (true) {
             unsigned key = 0xFFFFFFFFu;
             int kq = 0;
@@ -356,8 +452,44 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
             if (any_cut) Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
         }
         nst = 0;
+        used = 0;
         __syncwarp();
     };
+    // test every staged entry against the polygon at once: an entry that
+    // cuts no vertex never will (the polygon only shrinks) and is dropped;
+    // the others are applied one by one (flush)
+    auto settle = [&]() {
+        unsigned long long cm = 0ull;
+        if (!done && g.gl < ne) {
+            for (int q = 0; q < nst; q++) {
+                const float4 c = stage[q];
+                if (cuts<T>(L, c.x, c.y, 0.5f * c.z, __float_as_int(c.w), true, a, ctx)) cm |= 1ull << q;
+            }
+        }
+        unsigned lo = (unsigned)cm, hi = (unsigned)(cm >> 32);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            lo |= __shfl_xor_sync(kFull, lo, o);
+            hi |= __shfl_xor_sync(kFull, hi, o);
+        }
+        cm = ((unsigned long long)hi << 32) | lo;
+        int kq = 0;
+        for (int q = g.gl; q < nst; q += G, kq++)
+            if (!((cm >> q) & 1ull)) used |= 1u << kq;
+        if (warp_any(cm != 0ull)) flush();
+        nst = 0;
+        used = 0;
+        __syncwarp();
+    };
+    // sequentially started cells apply their previous neighbours first
+    {
+        const bool keep = seq && !done && wvalid && wd2 < 4.0f * Rmax * Rmax * 1.0001f;
+        const unsigned km = g.ballot(keep);
+        if (keep) stage[__popc(km & ((1u << g.gl) - 1u))] = make_float4(wdx, wdy, wd2, __int_as_float(wcs));
+        nst = __popc(km);
+        __syncwarp();
+        if (warp_any(nst > 0)) flush();
+    }
     for (int r = 1; warp_any(!done); r++) {
         if (P.debug && !done && g.gl == 0) atomicAdd(&V.ctrl->cnt.vor_rings, 1ull);
         int nr = r == 1 ? 5 : 4 * r;
@@ -384,13 +516,19 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                 }
                 c0 = c0 < 0 ? 0 : c0;
                 c1 = c1 >= P.nbx ? P.nbx - 1 : c1;
-                if (r > 1 && row >= 0 && row < P.nby && c0 <= c1) {
-                    // outer rings: a bucket range farther than 2 Rmax (with the
-                    // bucket-assignment margin) holds no point that can cut
-                    float ddx = fmaxf(fmaxf((float)c0 * bsx - xf, xf - (float)(c1 + 1) * bsx), 0.0f);
-                    float ddy = fmaxf(fmaxf((float)row * bsy - yf, yf - (float)(row + 1) * bsy), 0.0f);
+                if (row >= 0 && row < P.nby && c0 <= c1) {
+                    // buckets farther than 2 Rmax (with the bucket-assignment
+                    // margin) hold no point that can cut: the row is dropped,
+                    // or its column range trimmed to the disk's chord
                     float lim = 2.0f * Rmax * 1.0001f + bmargin;
-                    if (ddx * ddx + ddy * ddy > lim * lim) c1 = c0 - 1;
+                    float ddy = fmaxf(fmaxf((float)row * bsy - yf, yf - (float)(row + 1) * bsy), 0.0f);
+                    if (ddy > lim) {
+                        c1 = c0 - 1;
+                    } else {
+                        float w = sqrtf(lim * lim - ddy * ddy) + bmargin;
+                        c0 = max(c0, (int)floorf((xf - w) / bsx));
+                        c1 = min(c1, (int)floorf((xf + w) / bsx));
+                    }
                 }
                 if (row >= 0 && row < P.nby && c0 <= c1) {
                     lo = a.bstart[V.boff + row * P.nbx + c0];
@@ -436,7 +574,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                 bool keep = valid && d2 < 4.0f * Rmax * Rmax * 1.0001f;
                 unsigned km = g.ballot(keep);
                 if (warp_any(nst + __popc(km) > kStageCap)) {
-                    flush();
+                    settle();
                     keep = keep && !done && d2 < 4.0f * Rmax * Rmax * 1.0001f;
                     km = g.ballot(keep);
                 }
@@ -446,7 +584,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                 __syncwarp();
             }
         }
-        flush();
+        settle();
         // nothing outside the (2r+1)^2 block can cut once it is beyond 2 Rmax
         if (!done) {
             float dmin = INF;
