@@ -117,6 +117,7 @@ typedef struct {
     /* more Voronoi work counters (mesh_params.debug = 1 only): */
     int64_t vor_fp64;          /* cut decisions the float filter left to the FP64 filter  */
     int64_t vor_resolve;       /* polygon vertices solved again in double                 */
+    int64_t vor_direct;        /* cells built in one step from their previous neighbours  */
 } mesh_stats;
 
 /* Quality report of a mesh's last rebuild (mesh_quality): the statistics

@@ -61,7 +61,7 @@ class mesh_stats(C.Structure):
                 ("small_moves", C.c_int32), ("target_reached", C.c_int32), ("vor_candidates", C.c_int64),
                 ("vor_picks", C.c_int64), ("vor_cuts", C.c_int64), ("vor_rings", C.c_int64), ("vor_wide", C.c_int64),
                 ("triangulations", C.c_int64), ("added", C.c_int64), ("n_points", C.c_int64),
-                ("vor_fp64", C.c_int64), ("vor_resolve", C.c_int64)]
+                ("vor_fp64", C.c_int64), ("vor_resolve", C.c_int64), ("vor_direct", C.c_int64)]
 
 
 class mesh_tuning(C.Structure):

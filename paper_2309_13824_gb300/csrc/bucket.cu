@@ -165,17 +165,14 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const __grid_constant__ It
     for (int q = lo; q < hi; q++) d += a.sidx[q] < i;
     a.perm[i] = d;
     {
-        // the point's bisector neighbours at the last rebuild (old slots):
-        // the clipping pass starts from them
+        // the point's cell edges at the last rebuild in ring order (old
+        // slots, or bounding-plane labels): the clipping pass starts from them
         const int nr = a.ring_n[i];
         const int32_t* row = a.ring + (size_t)i * kRingCap;
         int32_t* wr = a.warm + (size_t)d * kWarm;
         int c = 0;
-        for (int t = 0; t < nr && c < kWarm; t++) {
-            int l = row[t];
-            if (l >= 0) wr[c++] = l;
-        }
-        for (; c < kWarm; c++) wr[c] = -1;
+        for (; c < nr && c < kWarm; c++) wr[c] = row[c];
+        for (; c < kWarm; c++) wr[c] = kNoLabel;
     }
     T x = a.cur.x[i], y = a.cur.y[i];
     a.srt.x[d] = x;
@@ -228,17 +225,18 @@ __global__ void __launch_bounds__(kThreads) k_dups(const __grid_constant__ IterA
         for (int q = a.bstart[k]; q < e; q++)
             if (q != s && a.srt.x[q] == x && a.srt.y[q] == y && a.srt.id[q] > id) dup = 1;
         a.dom[s] = (uint8_t)dup;
-        // previous neighbours to this rebuild's slots; a label outside the
-        // mesh's own slots is dropped
+        // previous neighbours to this rebuild's slots (bounding-plane labels
+        // stay); a slot outside the mesh's own slots becomes an empty entry
         int4* w4 = reinterpret_cast<int4*>(a.warm + (size_t)s * kWarm);
         const int lo = V.soff, hi = V.soff + V.n;
+        auto map = [&](int l) { return l < 0 ? l : (l >= lo && l < hi ? a.perm[l] : kNoLabel); };
 #pragma unroll
         for (int h = 0; h < kWarm / 4; h++) {
             int4 w = w4[h];
-            w.x = w.x >= lo && w.x < hi ? a.perm[w.x] : -1;
-            w.y = w.y >= lo && w.y < hi ? a.perm[w.y] : -1;
-            w.z = w.z >= lo && w.z < hi ? a.perm[w.z] : -1;
-            w.w = w.w >= lo && w.w < hi ? a.perm[w.w] : -1;
+            w.x = map(w.x);
+            w.y = map(w.y);
+            w.z = map(w.z);
+            w.w = map(w.w);
             w4[h] = w;
         }
     }

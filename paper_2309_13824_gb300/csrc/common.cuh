@@ -22,6 +22,7 @@ enum : uint8_t { PT_INNER = 0, PT_BOUNDARY = 1, PT_OUTSIDE = 2 };
 // bounding-edge labels in a ring: bisectors carry the neighbour's sorted slot (>= 0)
 __host__ __device__ constexpr int32_t oct_label(int k) { return -1 - k; }   // -1..-8
 __host__ __device__ constexpr int32_t box_label(int b) { return -9 - b; }   // -9..-12 (L,R,B,T)
+constexpr int32_t kNoLabel = -1000;  // an empty entry of a previous-neighbour row
 
 struct DevGrid {
     int32_t nx, ny;
@@ -40,6 +41,7 @@ struct DevCounters {
     unsigned long long vor_candidates, vor_picks, vor_cuts, vor_rings, vor_wide;
     unsigned long long triangulations;  // iterations that re-triangulated
     unsigned long long vor_fp64, vor_resolve;  // FP64 cut filters, vertices re-solved in double (debug)
+    unsigned long long vor_direct;             // cells built from their previous neighbours (debug)
 };
 
 // Per-block partial sums written by the emit kernel (a3/a4/a8 and Eq. 3 sums).

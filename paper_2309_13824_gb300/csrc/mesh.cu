@@ -490,6 +490,7 @@ static void fill_stats(const mesh_s* m, int k, int iters, mesh_stats* s) {
     s->triangulations = (int64_t)c.cnt.triangulations;
     s->vor_fp64 = (int64_t)c.cnt.vor_fp64;
     s->vor_resolve = (int64_t)c.cnt.vor_resolve;
+    s->vor_direct = (int64_t)c.cnt.vor_direct;
     s->added = m->batched ? 0 : m->added_call;
     s->n_points = m->parts[k].n;
 }

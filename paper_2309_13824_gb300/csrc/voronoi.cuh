@@ -174,11 +174,11 @@ __device__ __noinline__ bool exact_cut(const IterArgs<T>& a, const CellCtx& c, i
 
 // Does the half-plane n.u <= s (label lab; bisector: a neighbour's bisector,
 // n = d, s = |d|^2/2) cut this lane's vertex?  A vertex on the candidate's
-// own bisector (the candidate already is one of its two edges) is not cut.
+// own line (the candidate already is one of its two edges) is not cut.
 template <typename T>
 __device__ __forceinline__ bool cuts(const Lane& L, float nx, float ny, float s, int lab, bool bisector,
                                      const IterArgs<T>& a, const CellCtx& ctx) {
-    if (bisector && (lab == L.lab || lab == L.nlab)) return false;
+    if (lab == L.lab || lab == L.nlab) return false;
     if (bisector && L.bb) {
         float cl = 2.0f * s;
         float lam = fmaf(nx, L.Qx, fmaf(ny, L.Qy, cl * L.M));
@@ -258,6 +258,28 @@ __device__ __forceinline__ float dir_key(float x, float y) {
     return 3.0f + __fdividef(x, x - y);
 }
 
+// the half-plane n.u <= s of a bounding-plane label, relative to the
+// generator: octagon plane k (label -1 - k) with normal (cos k pi/4,
+// sin k pi/4) at the span SB; domain-box plane b (label -9 - b: left, right,
+// bottom, top) enlarged by mb; (xf, yf) the generator relative to the box's
+// lower corner, W x H the box
+__device__ __forceinline__ void bounding_plane(int lab, float SB, float xf, float yf, float W, float H, float mb,
+                                               float& nx, float& ny, float& s) {
+    constexpr float h = 0.70710678f;
+    if (lab >= oct_label(7)) {
+        const int k = -1 - lab;
+        const int c = (k + 6) & 7;
+        nx = k == 0 ? 1.f : k == 4 ? -1.f : (k == 2 || k == 6) ? 0.f : (k == 1 || k == 7) ? h : -h;
+        ny = c == 0 ? 1.f : c == 4 ? -1.f : (c == 2 || c == 6) ? 0.f : (c == 1 || c == 7) ? h : -h;
+        s = SB;
+    } else {
+        const int b = -9 - lab;
+        nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
+        ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
+        s = b == 0 ? xf + mb : b == 1 ? (W - xf) + mb : b == 2 ? yf + mb : (H - yf) + mb;
+    }
+}
+
 // one cell per group; slot < 0 marks an idle group (it still takes part in
 // every collective operation of its warp)
 template <typename T, int G>
@@ -303,33 +325,42 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     int ne = 0;
     int status = 0;
 
-    // the cell's bisector neighbours at the last rebuild, one per lane, in
-    // their ring order (points move little between rebuilds)
-    int wcs = -1;
-    if (live && g.gl < kWarm) wcs = a.warm[(size_t)s * kWarm + g.gl];
-    bool wvalid = wcs >= 0 && wcs != s;
-    float wdx = 0.f, wdy = 0.f, wd2 = INF;
-    if (wvalid) {
-        float4 pj4 = a.pf[wcs];
-        wvalid = !a.dom[wcs];
+    // the cell's edges at the last rebuild, one per lane in ring order
+    // (points move little between rebuilds): a neighbour's slot, a
+    // bounding-plane label or an empty entry.  (wdx, wdy, ws): the edge's
+    // half-plane n.u <= s; wd2 = |d|^2 for a neighbour.
+    int wl = kNoLabel;
+    if (live && g.gl < kWarm) wl = a.warm[(size_t)s * kWarm + g.gl];
+    const bool wbis = wl >= 0 && wl != s;
+    bool wvalid = false;
+    float wdx = 0.f, wdy = 0.f, wd2 = INF, ws = 0.f;
+    if (wbis) {
+        float4 pj4 = a.pf[wl];
         wdx = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y);
         wdy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
         wd2 = wdx * wdx + wdy * wdy;
         if (sizeof(T) == 8 && wd2 < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
-            wdx = (float)((double)a.srt.x[wcs] - (double)a.srt.x[s]);
-            wdy = (float)((double)a.srt.y[wcs] - (double)a.srt.y[s]);
+            wdx = (float)((double)a.srt.x[wl] - (double)a.srt.x[s]);
+            wdy = (float)((double)a.srt.y[wl] - (double)a.srt.y[s]);
             wd2 = wdx * wdx + wdy * wdy;
         }
-        wvalid = wvalid && wd2 > 0.0f;
+        ws = 0.5f * wd2;
+        wvalid = !a.dom[wl] && wd2 > 0.0f;
+    } else if (P.bounded && wl < 0 && wl >= box_label(3)) {
+        bounding_plane(wl, SB, xf, yf, Wf, Hf, mb, wdx, wdy, ws);
+        wvalid = true;
     }
 
-    // 1. Direct construction.  If the previous neighbours, in ring order,
-    // each turn left by less than pi (a float filter on the orientation of
+    // 1. Direct construction.  If the previous edges, in ring order, each
+    // turn left by less than pi (a float filter on the orientation of
     // consecutive normals), wind once around the generator, and every edge
     // keeps a positive length (the vertex of edges t, t+1 strictly inside
-    // edge t+2: the exact cut predicate), their bisectors bound a convex
-    // polygon that is exactly the intersection of their half-planes, built in
-    // one step.  Any other case starts from the octagon (2.).
+    // edge t+2: the exact cut predicate for two bisectors), they bound a
+    // convex polygon that is exactly the intersection of their half-planes,
+    // built in one step.  An edge without a positive length (a neighbour
+    // lost by a flip) is dropped and the rest certified again; a dropped
+    // point is tested again with the bucket candidates below, like any other
+    // point.  Any other case starts from the octagon (2.).
     const unsigned wm = g.ballot(wvalid);
     const int nw = __popc(wm);
     bool direct = live && P.bounded && nw >= 3 && (wm & (wm + 1u)) == 0u;  // a prefix of the lanes
@@ -337,78 +368,130 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
         if (direct) {
             L.nx = wdx;
             L.ny = wdy;
-            L.s = 0.5f * wd2;
-            L.lab = wcs;
+            L.s = ws;
+            L.lab = wl;
             ne = nw;
         }
-        const int n1 = g.gl + 1 >= ne ? 0 : g.gl + 1;
-        const int n2 = g.gl + 2 >= ne ? ((g.gl + 2 - ne) & (G - 1)) : g.gl + 2;
-        const float key = dir_key(L.nx, L.ny);
-        const float ax = g.shfl(L.nx, n1), ay = g.shfl(L.ny, n1), key1 = g.shfl(key, n1);
-        const float bx = g.shfl(L.nx, n2), by = g.shfl(L.ny, n2), bs = g.shfl(L.s, n2);
-        const int blab = g.shfl(L.lab, n2);
-        lane_vertex<G>(L, ne, g, RB, direct, ctx);
-        bool bad = false, desc = false;
-        if (direct && g.gl < ne) {
-            const float D = L.nx * ay - L.ny * ax;
-            const float PD = fabsf(L.nx * ay) + fabsf(L.ny * ax);
-            desc = key1 < key;
-            bad = !(D > 64.0f * kEps * PD) || !(L.vR < RB) || cuts<T>(L, bx, by, bs, blab, true, a, ctx);
+        bool built = false;
+#pragma unroll 1
+        for (int round = 0; round < 3 && warp_any(direct && !built); round++) {
+            const bool act = direct && !built;
+            const int n1 = g.gl + 1 >= ne ? 0 : g.gl + 1;
+            const int n2 = g.gl + 2 >= ne ? ((g.gl + 2 - ne) & (G - 1)) : g.gl + 2;
+            const float key = dir_key(L.nx, L.ny);
+            const float ax = g.shfl(L.nx, n1), ay = g.shfl(L.ny, n1), key1 = g.shfl(key, n1);
+            const float bx = g.shfl(L.nx, n2), by = g.shfl(L.ny, n2), bs = g.shfl(L.s, n2);
+            const int blab = g.shfl(L.lab, n2);
+            lane_vertex<G>(L, ne, g, RB, act, ctx);
+            bool bad = false, desc = false, flat = false;
+            if (act && g.gl < ne) {
+                const float D = L.nx * ay - L.ny * ax;
+                const float PD = fabsf(L.nx * ay) + fabsf(L.ny * ax);
+                desc = key1 < key;
+                bad = !(D > 64.0f * kEps * PD) || !(L.vR < RB);
+                if (!bad && blab >= 0 && L.bb) {
+                    flat = cuts<T>(L, bx, by, bs, blab, true, a, ctx);  // edge t+1 has no length (exact)
+                } else if (!bad) {
+                    // a bounding plane takes part: a float decision that must
+                    // clear the vertex's error bound (vR - |V|) and the
+                    // rounding of the dot product; an uncertain case starts
+                    // from the octagon
+                    const float dot = bx * L.vx + by * L.vy;
+                    const float ev = fmaxf(L.vR - sqrtf(L.vx * L.vx + L.vy * L.vy), 0.0f);
+                    const float mg = sqrtf(bx * bx + by * by) * ev * 1.01f +
+                                     8.0f * kEps * (fabsf(bx * L.vx) + fabsf(by * L.vy) + fabsf(bs));
+                    if (dot > bs + mg) flat = true;
+                    else if (!(dot < bs - mg)) bad = true;
+                }
+            }
+            const unsigned badm = g.ballot(bad), descm = g.ballot(desc), flatm = g.ballot(flat);
+            if (act && (badm != 0u || __popc(descm) != 1)) direct = false;
+            else if (act && flatm == 0u) built = true;
+            // drop the flagged edges: lane r takes the r-th kept one
+            const bool drop = act && direct && !built;
+            const unsigned all = (1u << (ne & 31)) - 1u;
+            const unsigned rm = drop ? (((flatm << 1) | (flatm >> ((ne - 1) & 31))) & all) : 0u;
+            const unsigned keepm = all & ~rm;
+            const int nk = __popc(keepm);
+            if (drop && nk < 3) direct = false;
+            int src = g.gl;
+            if (drop && nk >= 3 && g.gl < nk) {
+                unsigned mm = keepm;
+                for (int q = 0; q < g.gl; q++) mm &= mm - 1u;
+                src = __ffs(mm) - 1;
+            }
+            const float cnx = g.shfl(L.nx, src), cny = g.shfl(L.ny, src), csv = g.shfl(L.s, src);
+            const int clab = g.shfl(L.lab, src);
+            if (drop && nk >= 3) {
+                L.nx = cnx;
+                L.ny = cny;
+                L.s = csv;
+                L.lab = clab;
+                ne = nk;
+            }
         }
-        const unsigned badm = g.ballot(bad), descm = g.ballot(desc);
-        direct = direct && badm == 0u && __popc(descm) == 1;
+        direct = direct && built;
     }
+    if (P.debug && direct && g.gl == 0) atomicAdd(&V.ctrl->cnt.vor_direct, 1ull);
     // 2. Sequential start: the octagon (or the enlarged box)
     const bool seq = live && !direct;
     if (warp_any(seq)) {
         if (seq) {
+            ne = P.bounded ? 8 : 4;
             if (P.bounded) {
-                const float c8[8] = {1.f, 0.70710678f, 0.f, -0.70710678f, -1.f, -0.70710678f, 0.f, 0.70710678f};
-                int t = g.gl & 7;
-                L.nx = c8[t];
-                L.ny = c8[(t + 6) & 7];
-                L.s = SB;
-                L.lab = oct_label(t);
-                ne = 8;
+                // octagon, CCW from the +x normal
+                bounding_plane(oct_label(g.gl & 7), SB, xf, yf, Wf, Hf, mb, L.nx, L.ny, L.s);
+                L.lab = oct_label(g.gl & 7);
             } else {
-                ne = 4;  // enlarged box, CCW: bottom, right, top, left
-                int b = g.gl & 3;
-                int bs = b == 0 ? 2 : (b == 1 ? 1 : (b == 2 ? 3 : 0));
-                L.nx = bs == 0 ? -1.f : (bs == 1 ? 1.f : 0.f);
-                L.ny = bs == 2 ? -1.f : (bs == 3 ? 1.f : 0.f);
-                L.s = bs == 0 ? xf + mb : bs == 1 ? (Wf - xf) + mb : bs == 2 ? yf + mb : (Hf - yf) + mb;
+                // enlarged box, CCW: bottom, right, top, left
+                const int b = g.gl & 3;
+                const int bs = b == 0 ? 2 : (b == 1 ? 1 : (b == 2 ? 3 : 0));
+                bounding_plane(box_label(bs), SB, xf, yf, Wf, Hf, mb, L.nx, L.ny, L.s);
                 L.lab = box_label(bs);
             }
         }
         lane_vertex<G>(L, ne, g, RB, seq, ctx);
     }
     if (P.bounded) {
-        // a directly built polygon reaching beyond the octagon's inradius is
-        // clipped by the octagon's planes
-        const bool reach = g.ballot(direct && g.gl < ne && L.vR > SB) != 0u;
-        if (warp_any(reach)) {
-            for (int k = 0; k < 8; k++) {
-                const float c8[8] = {1.f, 0.70710678f, 0.f, -0.70710678f, -1.f, -0.70710678f, 0.f, 0.70710678f};
-                bool any_cut;
-                int st = clip_by<T, G>(L, ne, c8[k], c8[(k + 6) & 7], SB, oct_label(k), false, reach && status == 0,
-                                       RB, g, a, ctx, any_cut);
-                if (st) status = st;
+        // the planes of the octagon (bit k) and of the domain box (bit 8 + b)
+        // that cut some vertex: a direct polygon reaching beyond the
+        // octagon's inradius, or any polygon when a box plane comes closer
+        // than the octagon's circumradius.  The polygon only shrinks, so a
+        // plane that cuts none of the vertices never will.
+        const bool near_box = live && !(RB * 1.001f < xf + mb && RB * 1.001f < (Wf - xf) + mb &&
+                                        RB * 1.001f < yf + mb && RB * 1.001f < (Hf - yf) + mb);
+        unsigned pm = 0u;
+        if (live && g.gl < ne) {
+            if (direct && L.vR > SB) {
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    float nx, ny, sp;
+                    bounding_plane(oct_label(k), SB, xf, yf, Wf, Hf, mb, nx, ny, sp);
+                    if (cuts<T>(L, nx, ny, sp, oct_label(k), false, a, ctx)) pm |= 1u << k;
+                }
+            }
+            if (near_box) {
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    float nx, ny, sp;
+                    bounding_plane(box_label(b), SB, xf, yf, Wf, Hf, mb, nx, ny, sp);
+                    if (cuts<T>(L, nx, ny, sp, box_label(b), false, a, ctx)) pm |= 1u << (8 + b);
+                }
             }
         }
-        // the domain box cuts the polygon only if one of its planes comes
-        // closer than the octagon's circumradius RB (every vertex lies within RB)
-        bool near_box = live && !(RB * 1.001f < xf + mb && RB * 1.001f < (Wf - xf) + mb &&
-                                  RB * 1.001f < yf + mb && RB * 1.001f < (Hf - yf) + mb);
-        if (warp_any(near_box)) {
-            for (int b = 0; b < 4; b++) {
-                float nx = b == 0 ? -1.f : (b == 1 ? 1.f : 0.f);
-                float ny = b == 2 ? -1.f : (b == 3 ? 1.f : 0.f);
-                float sb = b == 0 ? xf + mb : b == 1 ? (Wf - xf) + mb : b == 2 ? yf + mb : (Hf - yf) + mb;
-                bool any_cut;
-                int st = clip_by<T, G>(L, ne, nx, ny, sb, box_label(b), false, live && status == 0, RB, g, a, ctx,
-                                       any_cut);
-                if (st) status = st;
-            }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) pm |= __shfl_xor_sync(kFull, pm, o);
+        unsigned todo = __reduce_or_sync(kFull, pm);
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int lab = k < 8 ? oct_label(k) : box_label(k - 8);
+            float nx, ny, sp;
+            bounding_plane(lab, SB, xf, yf, Wf, Hf, mb, nx, ny, sp);
+            bool any_cut;
+            int st = clip_by<T, G>(L, ne, nx, ny, sp, lab, false, live && status == 0 && ((pm >> k) & 1u), RB, g, a,
+                                   ctx, any_cut);
+            if (st) status = st;
         }
     }
     float Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
@@ -483,9 +566,9 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     };
     // sequentially started cells apply their previous neighbours first
     {
-        const bool keep = seq && !done && wvalid && wd2 < 4.0f * Rmax * Rmax * 1.0001f;
+        const bool keep = seq && !done && wbis && wvalid && wd2 < 4.0f * Rmax * Rmax * 1.0001f;
         const unsigned km = g.ballot(keep);
-        if (keep) stage[__popc(km & ((1u << g.gl) - 1u))] = make_float4(wdx, wdy, wd2, __int_as_float(wcs));
+        if (keep) stage[__popc(km & ((1u << g.gl) - 1u))] = make_float4(wdx, wdy, wd2, __int_as_float(wl));
         nst = __popc(km);
         __syncwarp();
         if (warp_any(nst > 0)) flush();
@@ -544,43 +627,62 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
             }
             int total = g.shfl(incl, G - 1);
             int excl = incl - cnt;
-            for (int q0 = 0; warp_any(q0 < total); q0 += G) {
-                int q = q0 + g.gl;
-                int ow = 0;
+            // two candidates per lane and iteration (entries q0 + gl and
+            // q0 + G + gl), their loads issued together
+            for (int q0 = 0; warp_any(q0 < total); q0 += 2 * G) {
+                int cs[2];
+                bool valid[2];
 #pragma unroll
-                for (int step = G / 2; step > 0; step >>= 1) {
-                    int pr = ow + step;
-                    int ex = g.shfl(excl, pr);
-                    if (ex <= q) ow = pr;
-                }
-                int olo = g.shfl(lo, ow);
-                int oex = g.shfl(excl, ow);
-                int cs = olo + (q - oex);
-                bool valid = !done && q < total && cs != s;
-                float dx = 0.f, dy = 0.f, d2 = INF;
-                if (valid) {
-                    // both loads issued together; a flagged duplicate is dropped after
-                    float4 pj4 = a.pf[cs];
-                    valid = !a.dom[cs];
-                    dx = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y);
-                    dy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
-                    d2 = dx * dx + dy * dy;
-                    if (sizeof(T) == 8 && d2 < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
-                        dx = (float)((double)a.srt.x[cs] - (double)a.srt.x[s]);
-                        dy = (float)((double)a.srt.y[cs] - (double)a.srt.y[s]);
-                        d2 = dx * dx + dy * dy;
+                for (int h = 0; h < 2; h++) {
+                    const int q = q0 + h * G + g.gl;
+                    int ow = 0;
+#pragma unroll
+                    for (int step = G / 2; step > 0; step >>= 1) {
+                        int pr = ow + step;
+                        int ex = g.shfl(excl, pr);
+                        if (ex <= q) ow = pr;
                     }
+                    const int olo = g.shfl(lo, ow);
+                    const int oex = g.shfl(excl, ow);
+                    cs[h] = olo + (q - oex);
+                    valid[h] = !done && q < total && cs[h] != s;
                 }
-                bool keep = valid && d2 < 4.0f * Rmax * Rmax * 1.0001f;
-                unsigned km = g.ballot(keep);
-                if (warp_any(nst + __popc(km) > kStageCap)) {
+                float4 pj4[2];
+                bool dup[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    pj4[h] = valid[h] ? a.pf[cs[h]] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    dup[h] = valid[h] && a.dom[cs[h]];
+                }
+                float dx[2], dy[2], d2[2];
+                bool keep[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    dx[h] = ff_diff(pj4[h].x, pj4[h].y, pi4.x, pi4.y);
+                    dy[h] = ff_diff(pj4[h].z, pj4[h].w, pi4.z, pi4.w);
+                    d2[h] = dx[h] * dx[h] + dy[h] * dy[h];
+                    if (sizeof(T) == 8 && valid[h] && d2[h] < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
+                        dx[h] = (float)((double)a.srt.x[cs[h]] - (double)a.srt.x[s]);
+                        dy[h] = (float)((double)a.srt.y[cs[h]] - (double)a.srt.y[s]);
+                        d2[h] = dx[h] * dx[h] + dy[h] * dy[h];
+                    }
+                    keep[h] = valid[h] && !dup[h] && d2[h] < 4.0f * Rmax * Rmax * 1.0001f;
+                }
+                unsigned km0 = g.ballot(keep[0]), km1 = g.ballot(keep[1]);
+                if (warp_any(nst + __popc(km0) + __popc(km1) > kStageCap)) {
                     settle();
-                    keep = keep && !done && d2 < 4.0f * Rmax * Rmax * 1.0001f;
-                    km = g.ballot(keep);
+#pragma unroll
+                    for (int h = 0; h < 2; h++) keep[h] = keep[h] && !done && d2[h] < 4.0f * Rmax * Rmax * 1.0001f;
+                    km0 = g.ballot(keep[0]);
+                    km1 = g.ballot(keep[1]);
                 }
-                if (keep) stage[nst + __popc(km & ((1u << g.gl) - 1u))] = make_float4(dx, dy, d2, __int_as_float(cs));
-                if (P.debug && g.gl == 0 && km) atomicAdd(&V.ctrl->cnt.vor_candidates, (unsigned long long)__popc(km));
-                nst += __popc(km);
+                const unsigned lt = (1u << g.gl) - 1u;
+                if (keep[0]) stage[nst + __popc(km0 & lt)] = make_float4(dx[0], dy[0], d2[0], __int_as_float(cs[0]));
+                if (keep[1])
+                    stage[nst + __popc(km0) + __popc(km1 & lt)] = make_float4(dx[1], dy[1], d2[1], __int_as_float(cs[1]));
+                if (P.debug && g.gl == 0 && (km0 | km1))
+                    atomicAdd(&V.ctrl->cnt.vor_candidates, (unsigned long long)(__popc(km0) + __popc(km1)));
+                nst += __popc(km0) + __popc(km1);
                 __syncwarp();
             }
         }
