@@ -96,11 +96,23 @@ struct DevParams {
     double bsx, bsy;  // bucket sizes
     // float copies used by the bucket assignment (both kernels use these)
     float bx0f, by0f, ibsxf, ibsyf;
+    // float copies for the clipping kernels: box size, bucket sizes, and the
+    // bucket-assignment margin 1e-3 max(bsx, bsy)
+    float Wf, Hf, bsxf, bsyf, bmargf;
 };
 
 // a - b for positions stored as float pairs (hi, lo) with hi + lo = x to 2^-48 |x|;
 // relative error below 2^-22 once |a - b| >= 2^-20 (callers fall back to double below)
 __device__ __forceinline__ float ff_diff(float ah, float al, float bh, float bl) { return (ah - bh) + (al - bl); }
+
+// (X[j] - xi, Y[j] - yi) formed in double and rounded to float, for points
+// closer than ff_diff resolves (|d| < 2^-20): rare, so kept out of line (a
+// call that is predicated off issues nothing, while inline code would issue
+// its FP64 instructions, predicated off, for every point tested)
+template <typename T>
+static __device__ __noinline__ float2 close_diff(const T* X, const T* Y, int j, T xi, T yi) {
+    return make_float2((float)((double)X[j] - (double)xi), (float)((double)Y[j] - (double)yi));
+}
 
 // ---------------------------------------------------------------- fixed FP64 ops
 __device__ __forceinline__ double fadd(double a, double b) { return __dadd_rn(a, b); }

@@ -35,7 +35,7 @@ struct Tri {
 };
 
 // Tests 1-3 on the canonical order (a = smallest id, CCW)
-__device__ bool valid_fixed(const MeshView& V, const Tri& t) {
+static __device__ __noinline__ bool valid_fixed(const MeshView& V, const Tri& t) {
     const DevGrid& s = V.sdf;
     int ncx = s.nx - 1;
     double gx = fdiv(fadd(fadd(t.x[0], t.x[1]), t.x[2]), 3.0);
@@ -87,8 +87,9 @@ __device__ __forceinline__ Nbr load_nbr(const IterArgs<T>& a, int lab, float4 pi
         n.dx = ff_diff(pj4.x, pj4.y, pi4.x, pi4.y);
         n.dy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
         if (sizeof(T) == 8 && n.dx * n.dx + n.dy * n.dy < 9.094947e-13f) {  // |d| < 2^-20
-            n.dx = (float)(a.srt.x[lab] - xi);
-            n.dy = (float)(a.srt.y[lab] - yi);
+            const float2 e = close_diff<T>(a.srt.x, a.srt.y, lab, xi, yi);
+            n.dx = e.x;
+            n.dy = e.y;
         }
         n.S = a.pS[lab];
     } else {
@@ -99,6 +100,10 @@ __device__ __forceinline__ Nbr load_nbr(const IterArgs<T>& a, int lab, float4 pi
     }
     return n;
 }
+
+template <typename T>
+static __device__ __noinline__ bool emitted_fixed(const IterArgs<T>& a, const MeshView& V, int idi, int ci, T xi,
+                                                  T yi, int js, int jid, int jcell, int ks, int kid, int kcell);
 
 // emission decision for (i, j, k), CCW as seen from cell i
 template <typename T>
@@ -133,11 +138,20 @@ __device__ bool emitted(const IterArgs<T>& a, const MeshView& V, const CellC& cc
         }
         if (state != 2) return state == 1;
     }
-    // fixed FP64 formula on the canonical order
-    double xs[3] = {(double)xi, (double)a.srt.x[j.slot], (double)a.srt.x[k.slot]};
-    double ys[3] = {(double)yi, (double)a.srt.y[j.slot], (double)a.srt.y[k.slot]};
-    int ids[3] = {idi, j.id, k.id};
-    int cells[3] = {ci, j.cell, k.cell};
+    return emitted_fixed<T>(a, V, idi, ci, xi, yi, j.slot, j.id, j.cell, k.slot, k.id, k.cell);
+}
+
+// the fixed FP64 formula on the canonical order (the float filter above
+// leaves about 1e-4 decisions per cell to it: out of line, so that its FP64
+// instructions are not issued for every triangle)
+template <typename T>
+static __device__ __noinline__ bool emitted_fixed(const IterArgs<T>& a, const MeshView& V, int idi, int ci, T xi,
+                                                  T yi, int js, int jid, int jcell, int ks, int kid, int kcell) {
+    const DevParams& P = V.P;
+    double xs[3] = {(double)xi, (double)a.srt.x[js], (double)a.srt.x[ks]};
+    double ys[3] = {(double)yi, (double)a.srt.y[js], (double)a.srt.y[ks]};
+    int ids[3] = {idi, jid, kid};
+    int cells[3] = {ci, jcell, kcell};
     int r = 0;
     if (ids[1] < ids[r]) r = 1;
     if (ids[2] < ids[r]) r = 2;

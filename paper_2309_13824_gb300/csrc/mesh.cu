@@ -308,6 +308,11 @@ static void size_buckets(Part& p, double nopt) {
     d.by0f = (float)d.by0;
     d.ibsxf = (float)(1.0 / d.bsx);
     d.ibsyf = (float)(1.0 / d.bsy);
+    d.Wf = (float)(d.bx1 - d.bx0);
+    d.Hf = (float)(d.by1 - d.by0);
+    d.bsxf = (float)d.bsx;
+    d.bsyf = (float)d.bsy;
+    d.bmargf = (float)(1e-3 * (d.bsx > d.bsy ? d.bsx : d.bsy));
     p.nb = d.nbx * d.nby;
 }
 

@@ -70,6 +70,22 @@ struct Lane {
     float PQx, PQy, PM;   // and their absolute-value permanents
 };
 
+// The vertex of n1.u <= s1 and n2.u <= s2 solved in double, where every
+// product of two float inputs is exact and the vertex carries a few ulps of
+// error; its float rounding then decides the later float cut tests like any
+// other vertex.  Returns (ux, uy, |u|, error bound), or w = 0 when the lines
+// are parallel or the vertex lies beyond RB.
+static __device__ __noinline__ float4 resolve_vertex(float nx, float ny, float s, float nx2, float ny2, float s2,
+                                                     float RB) {
+    const double Dd = (double)nx * (double)ny2 - (double)ny * (double)nx2;
+    if (Dd == 0.0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const double uxd = ((double)s * (double)ny2 - (double)s2 * (double)ny) / Dd;
+    const double uyd = ((double)s2 * (double)nx - (double)s * (double)nx2) / Dd;
+    const double rd = sqrt(uxd * uxd + uyd * uyd);
+    if (!(rd < (double)RB)) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return make_float4((float)uxd, (float)uyd, (float)rd, (float)rd * (8.0f * kEps) + 1e-30f);
+}
+
 // returns true when the vertex had to be solved again in double
 __device__ __forceinline__ bool make_vertex(Lane& L, float nx2, float ny2, float s2, int lab2, float RB) {
     float D = L.nx * ny2 - L.ny * nx2;
@@ -87,22 +103,15 @@ __device__ __forceinline__ bool make_vertex(Lane& L, float nx2, float ny2, float
     const bool resolved = !ok;
     if (!ok) {
         // nearly parallel edges (a bisector almost along a bounding line):
-        // the float vertex is too uncertain, so solve again in double, where
-        // every product of two float inputs is exact and the vertex carries
-        // a few ulps of error.  Its float rounding then decides the later
-        // float cut tests like any other vertex.
-        double Dd = (double)L.nx * (double)ny2 - (double)L.ny * (double)nx2;
-        if (Dd != 0.0) {
-            double uxd = ((double)L.s * (double)ny2 - (double)s2 * (double)L.ny) / Dd;
-            double uyd = ((double)s2 * (double)L.nx - (double)L.s * (double)nx2) / Dd;
-            double rd = sqrt(uxd * uxd + uyd * uyd);
-            if (rd < (double)RB) {
-                ux = (float)uxd;
-                uy = (float)uyd;
-                err = (float)rd * (8.0f * kEps) + 1e-30f;
-                r = (float)rd;
-                ok = r + err < RB;
-            }
+        // the float vertex is too uncertain, so solve again in double (out of
+        // line: rare)
+        const float4 v = resolve_vertex(L.nx, L.ny, L.s, nx2, ny2, s2, RB);
+        if (v.w > 0.0f) {
+            ux = v.x;
+            uy = v.y;
+            r = v.z;
+            err = v.w;
+            ok = r + err < RB;
         }
     }
     L.vR = ok ? r + err : RB;
@@ -303,7 +312,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     // generator relative to the box corner, and the box size (float; the box
     // planes only need to bound Reg_i with the S/16 margin)
     const float xf = (pi4.x - P.bx0f) + pi4.y, yf = (pi4.z - P.by0f) + pi4.w;
-    const float Wf = (float)(P.bx1 - P.bx0), Hf = (float)(P.by1 - P.by0);
+    const float Wf = P.Wf, Hf = P.Hf;
     float RB, mb, SB = 0.0f;
     if (P.bounded) {
         float S = a.pS[s];
@@ -340,8 +349,9 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
         wdy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
         wd2 = wdx * wdx + wdy * wdy;
         if (sizeof(T) == 8 && wd2 < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
-            wdx = (float)((double)a.srt.x[wl] - (double)a.srt.x[s]);
-            wdy = (float)((double)a.srt.y[wl] - (double)a.srt.y[s]);
+            const float2 e = close_diff<T>(a.srt.x, a.srt.y, wl, a.srt.x[s], a.srt.y[s]);
+            wdx = e.x;
+            wdy = e.y;
             wd2 = wdx * wdx + wdy * wdy;
         }
         ws = 0.5f * wd2;
@@ -497,8 +507,8 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     float Rmax = g.max(g.gl < ne ? L.vR : 0.0f);
     int bxi, byi;
     bucket_of(P, pi4.x, pi4.z, bxi, byi);
-    const float bsx = (float)P.bsx, bsy = (float)P.bsy;
-    const float bmargin = (float)(1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy)) + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
+    const float bsx = P.bsxf, bsy = P.bsyf;
+    const float bmargin = P.bmargf + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
     bool done = !live || status != 0;
     int nst = 0;
     unsigned used = 0;  // per lane: its staged entries (gl, gl + G, ...) already taken or dropped
@@ -662,8 +672,9 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                     dy[h] = ff_diff(pj4[h].z, pj4[h].w, pi4.z, pi4.w);
                     d2[h] = dx[h] * dx[h] + dy[h] * dy[h];
                     if (sizeof(T) == 8 && valid[h] && d2[h] < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
-                        dx[h] = (float)((double)a.srt.x[cs[h]] - (double)a.srt.x[s]);
-                        dy[h] = (float)((double)a.srt.y[cs[h]] - (double)a.srt.y[s]);
+                        const float2 e = close_diff<T>(a.srt.x, a.srt.y, cs[h], a.srt.x[s], a.srt.y[s]);
+                        dx[h] = e.x;
+                        dy[h] = e.y;
                         d2[h] = dx[h] * dx[h] + dy[h] * dy[h];
                     }
                     keep[h] = valid[h] && !dup[h] && d2[h] < 4.0f * Rmax * Rmax * 1.0001f;
@@ -883,7 +894,7 @@ __device__ int voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int 
     ctx.si = s;
     ctx.dbg = P.debug;
     const float xf = (pi4.x - P.bx0f) + pi4.y, yf = (pi4.z - P.by0f) + pi4.w;
-    const float Wf = (float)(P.bx1 - P.bx0), Hf = (float)(P.by1 - P.by0);
+    const float Wf = P.Wf, Hf = P.Hf;
     float RB, mb;
     int ne;
     if (P.bounded) {
@@ -918,8 +929,8 @@ __device__ int voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int 
     float Rmax = status == 0 ? serial_rmax<T>(E, ne, RB) : 0.0f;
     int bxi, byi;
     bucket_of(P, pi4.x, pi4.z, bxi, byi);
-    const float bsx = (float)P.bsx, bsy = (float)P.bsy;
-    const float bmargin = (float)(1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy)) + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
+    const float bsx = P.bsxf, bsy = P.bsyf;
+    const float bmargin = P.bmargf + 4e-6f * (1.0f + fabsf(xf) + fabsf(yf));
     bool done = status != 0;
     int nst = 0;
     // apply the staged candidates nearest first
@@ -984,8 +995,9 @@ __device__ int voronoi_cell_serial(const IterArgs<T>& a, const MeshView& V, int 
                 float dy = ff_diff(pj4.z, pj4.w, pi4.z, pi4.w);
                 float d2 = dx * dx + dy * dy;
                 if (sizeof(T) == 8 && d2 < 9.094947e-13f) {
-                    dx = (float)((double)a.srt.x[cs] - (double)a.srt.x[s]);
-                    dy = (float)((double)a.srt.y[cs] - (double)a.srt.y[s]);
+                    const float2 e = close_diff<T>(a.srt.x, a.srt.y, cs, a.srt.x[s], a.srt.y[s]);
+                    dx = e.x;
+                    dy = e.y;
                     d2 = dx * dx + dy * dy;
                 }
                 if (!(d2 < 4.0f * Rmax * Rmax * 1.0001f)) continue;
