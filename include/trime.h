@@ -473,11 +473,12 @@ int mesh_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int32_t M,
  * BF16 weights and activations, FP32 accumulation, all products on the
  * tensor cores.  Parameters: a flat FP32 vector of TRIME_MLP_PARAMS values,
  * W1 (64 x 48, row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (2 x 64), b3 (2).
- * Features of point i, in order: the offsets (x_j - x_i, y_j - y_i) / h_i of
+ * Features of point i, in order: the offsets (x_j - x_i, y_j - y_i) r_i of
  * its 16 nearest other points (by squared distance, ties by smaller index,
- * nearest first); ln(h_i / h_avg) (Sec. 3.7); the gradient of the sizing field
- * at p_i; 1 if p_i is a boundary point (Sec. 4.3); 1 if the next move is CVD;
- * the point's last move divided by h_i (zero when unknown: the positions
+ * nearest first), r_i = 1 / h_i rounded once to FP64; ln(h_i / h_avg)
+ * (Sec. 3.7); the gradient of the sizing field at p_i; 1 if p_i is a boundary
+ * point (Sec. 4.3); 1 if the next move is CVD; the point's last move times
+ * r_i (zero when unknown: the positions
  * before the last iteration are recorded by mesh_step_learned and
  * mesh_collect_pairs, not by mesh_step); each rounded to float32 and then to
  * BF16 (nearest, ties to even). */

@@ -6,10 +6,11 @@ kernels are checked against:
 
 * features of a point i (39 values, zero-padded to 48): the offsets of its 16
   nearest other points (by squared FP64 distance, ties by smaller index,
-  nearest first) divided by h_i, the geometry-cell size of its cell (Sec. 3.7);
+  nearest first) scaled by r_i = 1 / h_i (rounded once to FP64), h_i the
+  geometry-cell size of its cell (Sec. 3.7);
   ln(h_i / h_avg); the gradient of the sizing field mu at p_i (derivative of
   the bilinear interpolant, Sec. 3.3 grid); 1 if the point is a boundary point;
-  1 if the current move is CVD; its last move divided by h_i (zero when not
+  1 if the current move is CVD; its last move scaled by r_i (zero when not
   known).  Each feature is rounded to float32 and then to BF16 (round to
   nearest, ties to even);
 * the network: Z1 = X W1^T + b1, H1 = relu(Z1), Z2 = H1 W2^T + b2,
@@ -91,12 +92,13 @@ def features(points, h, havg, sizing, is_boundary, method_cvd: int, previous=Non
     nb = knn(p)
     X = np.zeros((n, K_IN))
     for i in range(n):
+        r = 1.0 / float(h[i])
         for k in range(N_NEIGH):
             j = nb[i, k]
             if j < 0:
                 continue
-            X[i, 2 * k] = np.float32((p[j, 0] - p[i, 0]) / h[i])
-            X[i, 2 * k + 1] = np.float32((p[j, 1] - p[i, 1]) / h[i])
+            X[i, 2 * k] = np.float32((p[j, 0] - p[i, 0]) * r)
+            X[i, 2 * k + 1] = np.float32((p[j, 1] - p[i, 1]) * r)
         X[i, 32] = np.float32(np.log(h[i] / havg))
         gx, gy = sizing_gradient(sizing, p[i, 0], p[i, 1])
         X[i, 33] = np.float32(gx)
@@ -104,8 +106,8 @@ def features(points, h, havg, sizing, is_boundary, method_cvd: int, previous=Non
         X[i, 35] = 1.0 if is_boundary[i] else 0.0
         X[i, 36] = float(method_cvd)
         if previous is not None:
-            X[i, 37] = np.float32((p[i, 0] - previous[i, 0]) / h[i])
-            X[i, 38] = np.float32((p[i, 1] - previous[i, 1]) / h[i])
+            X[i, 37] = np.float32((p[i, 0] - previous[i, 0]) * r)
+            X[i, 38] = np.float32((p[i, 1] - previous[i, 1]) * r)
     return X
 
 

@@ -3,10 +3,10 @@
 // A 3-layer perceptron (48 BF16 inputs, two hidden layers of 64 ReLU units,
 // 2 outputs) proposes, for every point, its displacement over the next
 // iterations of the plain method divided by h_i, from local features: the
-// offsets of its 16 nearest points / h_i, ln(h_i / h_avg), the sizing
+// offsets of its 16 nearest points times 1 / h_i, ln(h_i / h_avg), the sizing
 // gradient, the boundary flag and the move in use.  The paper's method has no
 // learned part; plain iterations stay the fallback and judge the proposals.
-// Two more features carry the point's last move / h_i, so the model can
+// Two more features carry the point's last move times 1 / h_i, so the model can
 // extrapolate the trajectory it is on.
 //
 // Every product runs on the tensor cores: one CTA of 128 threads takes 128
@@ -520,37 +520,73 @@ __global__ void __launch_bounds__(kThreads) k_features(const __grid_constant__ I
     double xd = (double)xt, yd = (double)yt;
     int id = a.srt.id[s];
     double h = V.gh[a.cell[s]];
-    double bd[16];
+    // the 16 nearest so far: squared FP64 distances as their bit patterns
+    // (for non-negative doubles the unsigned order of the bits is the order
+    // of the values, so the insertion compares on the integer pipe), ids,
+    // slots
+    unsigned long long bd[16];
     int bid[16], bq[16];
     int cnt = 0;
+    // once 16 are held, a candidate whose float-pair squared distance f2
+    // certainly exceeds the 16th (f2 (1 - 2^-18) > bd[15], with bd[15]
+    // rounded up to float in b15) is skipped without the FP64 distance: the
+    // float-pair difference has a relative error below 2^-22 for |d| >=
+    // 2^-20, so f2 is within 2^-20 of d^2, and such a candidate would be
+    // rejected by the exact comparison anyway
+    float b15 = __int_as_float(0x7f800000);
+    const float4 pi4 = a.pf[s];
     int bxi, byi;
     bucket_of(P, xt, yt, bxi, byi);
     double margin = 1e-3 * (P.bsx > P.bsy ? P.bsx : P.bsy) + 4e-6 * (1.0 + fabs(xd) + fabs(yd));
+    // candidate q: the float pre-test, then the exact (FP64 distance, id)
+    // insertion into the 16 nearest
+    auto consider = [&](int q, const float4& pq) {
+        if (q == s) return;
+        if (cnt == 16) {
+            const float fx = ff_diff(pq.x, pq.y, pi4.x, pi4.y), fy = ff_diff(pq.z, pq.w, pi4.z, pi4.w);
+            const float f2 = fx * fx + fy * fy;
+            if (f2 >= 9.094947e-13f && f2 * (1.0f - 0x1p-18f) > b15) return;
+        }
+        double dx = fsub((double)a.srt.x[q], xd), dy = fsub((double)a.srt.y[q], yd);
+        const unsigned long long d2 = (unsigned long long)__double_as_longlong(fadd(fmul(dx, dx), fmul(dy, dy)));
+        int qi = a.srt.id[q];
+        if (cnt == 16 && !(d2 < bd[15] || (d2 == bd[15] && qi < bid[15]))) return;
+        int p = cnt < 16 ? cnt++ : 15;
+        while (p > 0 && (d2 < bd[p - 1] || (d2 == bd[p - 1] && qi < bid[p - 1]))) {
+            bd[p] = bd[p - 1];
+            bid[p] = bid[p - 1];
+            bq[p] = bq[p - 1];
+            p--;
+        }
+        bd[p] = d2;
+        bid[p] = qi;
+        bq[p] = q;
+        if (cnt == 16) b15 = __double2float_ru(__longlong_as_double((long long)bd[15]));
+    };
+    // the slots [lo, hi) four at a time, their positions loaded together
+    auto scan = [&](int lo, int hi) {
+        for (int q0 = lo; q0 < hi; q0 += 4) {
+            float4 pq[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) pq[u] = q0 + u < hi ? a.pf[q0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (q0 + u < hi) consider(q0 + u, pq[u]);
+        }
+    };
     for (int r = 0;; r++) {
+        // the ring's buckets: its top and bottom rows as one slot range each
+        // (the buckets of a row are consecutive in the sorted order), the
+        // two side buckets of the rows between
         for (int by = byi - r; by <= byi + r; by++) {
             if (by < 0 || by >= P.nby) continue;
-            bool full_row = r == 0 || by == byi - r || by == byi + r;
-            for (int bx = bxi - r; bx <= bxi + r; bx += full_row ? 1 : 2 * r) {
-                if (bx < 0 || bx >= P.nbx) continue;
-                int k = V.boff + by * P.nbx + bx;
-                int e = a.bstart[k + 1];
-                for (int q = a.bstart[k]; q < e; q++) {
-                    if (q == s) continue;
-                    double dx = fsub((double)a.srt.x[q], xd), dy = fsub((double)a.srt.y[q], yd);
-                    double d2 = fadd(fmul(dx, dx), fmul(dy, dy));
-                    int qi = a.srt.id[q];
-                    if (cnt == 16 && !(d2 < bd[15] || (d2 == bd[15] && qi < bid[15]))) continue;
-                    int p = cnt < 16 ? cnt++ : 15;
-                    while (p > 0 && (d2 < bd[p - 1] || (d2 == bd[p - 1] && qi < bid[p - 1]))) {
-                        bd[p] = bd[p - 1];
-                        bid[p] = bid[p - 1];
-                        bq[p] = bq[p - 1];
-                        p--;
-                    }
-                    bd[p] = d2;
-                    bid[p] = qi;
-                    bq[p] = q;
-                }
+            const int k0 = V.boff + by * P.nbx;
+            if (r == 0 || by == byi - r || by == byi + r) {
+                const int c0 = max(bxi - r, 0), c1 = min(bxi + r, P.nbx - 1);
+                scan(a.bstart[k0 + c0], a.bstart[k0 + c1 + 1]);
+            } else {
+                if (bxi - r >= 0) scan(a.bstart[k0 + bxi - r], a.bstart[k0 + bxi - r + 1]);
+                if (bxi + r < P.nbx) scan(a.bstart[k0 + bxi + r], a.bstart[k0 + bxi + r + 1]);
             }
         }
         if (bxi - r <= 0 && bxi + r >= P.nbx - 1 && byi - r <= 0 && byi + r >= P.nby - 1) break;
@@ -561,16 +597,19 @@ __global__ void __launch_bounds__(kThreads) k_features(const __grid_constant__ I
             if (byi - r > 0) dmin = fmin(dmin, yd - (P.by0 + (byi - r) * P.bsy));
             if (byi + r < P.nby - 1) dmin = fmin(dmin, (P.by0 + (byi + r + 1) * P.bsy) - yd);
             dmin -= margin;
-            if (dmin > 0.0 && bd[15] < dmin * dmin) break;
+            if (dmin > 0.0 && __longlong_as_double((long long)bd[15]) < dmin * dmin) break;
         }
     }
     size_t row = (size_t)(by_id ? id : s);
+    // offsets are scaled by r_i = 1 / h_i rounded once (one division per
+    // point instead of one per offset)
+    const double rh = fdiv(1.0, h);
     __align__(16) uint16_t f[kMlpIn];
     for (int k = 0; k < 16; k++) {
         if (k < cnt) {
             int j = bq[k];
-            f[2 * k] = bf16_bits((float)fdiv(fsub((double)a.srt.x[j], xd), h));
-            f[2 * k + 1] = bf16_bits((float)fdiv(fsub((double)a.srt.y[j], yd), h));
+            f[2 * k] = bf16_bits((float)fmul(fsub((double)a.srt.x[j], xd), rh));
+            f[2 * k + 1] = bf16_bits((float)fmul(fsub((double)a.srt.y[j], yd), rh));
         } else {
             f[2 * k] = f[2 * k + 1] = 0;
         }
@@ -586,8 +625,8 @@ __global__ void __launch_bounds__(kThreads) k_features(const __grid_constant__ I
     float mf = mflag;
     if (mf < 0.0f) mf = (V.ctrl->method_param == 1 || (V.ctrl->method_param == 2 && V.ctrl->switched)) ? 1.0f : 0.0f;
     f[36] = bf16_bits(mf);
-    f[37] = qx ? bf16_bits((float)fdiv(fsub(xd, (double)qx[id]), h)) : 0;
-    f[38] = qy ? bf16_bits((float)fdiv(fsub(yd, (double)qy[id]), h)) : 0;
+    f[37] = qx ? bf16_bits((float)fmul(fsub(xd, (double)qx[id]), rh)) : 0;
+    f[38] = qy ? bf16_bits((float)fmul(fsub(yd, (double)qy[id]), rh)) : 0;
     for (int k = kMlpFeat; k < kMlpIn; k++) f[k] = 0;
     uint4* dst = reinterpret_cast<uint4*>(X + row * kMlpIn);
     const uint4* src = reinterpret_cast<const uint4*>(f);
