@@ -583,132 +583,189 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
         __syncwarp();
         if (warp_any(nst > 0)) flush();
     }
-    for (int r = 1; warp_any(!done); r++) {
-        if (P.debug && !done && g.gl == 0) atomicAdd(&V.ctrl->cnt.vor_rings, 1ull);
-        int nr = r == 1 ? 5 : 4 * r;
-        for (int kb = 0; kb < nr; kb += G) {
-            int k = kb + g.gl;
-            int lo = 0, hi = 0;
-            if (!done && k < nr) {
-                int row, c0, c1;
-                if (r == 1) {
-                    // own bucket first, then its row neighbours, then the rows below / above
-                    row = k < 3 ? byi : (k == 3 ? byi - 1 : byi + 1);
-                    c0 = k == 0 ? bxi : (k == 1 ? bxi - 1 : (k == 2 ? bxi + 1 : bxi - 1));
-                    c1 = k == 0 ? bxi : (k == 1 ? bxi - 1 : (k == 2 ? bxi + 1 : bxi + 1));
-                    if (k == 1 && c0 < 0) c0 = 1, c1 = 0;       // no bucket left of the grid
-                    if (k == 2 && c1 >= P.nbx) c0 = 1, c1 = 0;  // no bucket right of the grid
-                } else if (k < 2) {
-                    row = k == 0 ? byi - r : byi + r;
-                    c0 = bxi - r;
-                    c1 = bxi + r;
-                } else {
-                    int kk = k - 2;
-                    row = byi - r + 1 + (kk >> 1);
-                    c0 = c1 = (kk & 1) ? bxi + r : bxi - r;
+    // the slot ranges [lo, hi) of the group's lanes: their points loaded two
+    // per lane and step, staged when within 2 Rmax
+    auto load = [&](int lo, int hi) {
+        int cnt = hi - lo;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            int y = __shfl_up_sync(kFull, incl, o, G);
+            if (g.gl >= o) incl += y;
+        }
+        int total = g.shfl(incl, G - 1);
+        int excl = incl - cnt;
+        // two candidates per lane and iteration (entries q0 + gl and
+        // q0 + G + gl), their loads issued together
+        for (int q0 = 0; warp_any(q0 < total); q0 += 2 * G) {
+            int cs[2];
+            bool valid[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int q = q0 + h * G + g.gl;
+                int ow = 0;
+#pragma unroll
+                for (int step = G / 2; step > 0; step >>= 1) {
+                    int pr = ow + step;
+                    int ex = g.shfl(excl, pr);
+                    if (ex <= q) ow = pr;
                 }
-                c0 = c0 < 0 ? 0 : c0;
-                c1 = c1 >= P.nbx ? P.nbx - 1 : c1;
-                if (row >= 0 && row < P.nby && c0 <= c1) {
-                    // buckets farther than 2 Rmax (with the bucket-assignment
-                    // margin) hold no point that can cut: the row is dropped,
-                    // or its column range trimmed to the disk's chord
-                    float lim = 2.0f * Rmax * 1.0001f + bmargin;
-                    float ddy = fmaxf(fmaxf((float)row * bsy - yf, yf - (float)(row + 1) * bsy), 0.0f);
-                    if (ddy > lim) {
-                        c1 = c0 - 1;
+                const int olo = g.shfl(lo, ow);
+                const int oex = g.shfl(excl, ow);
+                cs[h] = olo + (q - oex);
+                valid[h] = !done && q < total && cs[h] != s;
+            }
+            float4 pj4[2];
+            bool dup[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                pj4[h] = valid[h] ? a.pf[cs[h]] : make_float4(0.f, 0.f, 0.f, 0.f);
+                dup[h] = valid[h] && a.dom[cs[h]];
+            }
+            float dx[2], dy[2], d2[2];
+            bool keep[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                dx[h] = ff_diff(pj4[h].x, pj4[h].y, pi4.x, pi4.y);
+                dy[h] = ff_diff(pj4[h].z, pj4[h].w, pi4.z, pi4.w);
+                d2[h] = dx[h] * dx[h] + dy[h] * dy[h];
+                if (sizeof(T) == 8 && valid[h] && d2[h] < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
+                    const float2 e = close_diff<T>(a.srt.x, a.srt.y, cs[h], a.srt.x[s], a.srt.y[s]);
+                    dx[h] = e.x;
+                    dy[h] = e.y;
+                    d2[h] = dx[h] * dx[h] + dy[h] * dy[h];
+                }
+                keep[h] = valid[h] && !dup[h] && d2[h] < 4.0f * Rmax * Rmax * 1.0001f;
+            }
+            unsigned km0 = g.ballot(keep[0]), km1 = g.ballot(keep[1]);
+            if (warp_any(nst + __popc(km0) + __popc(km1) > kStageCap)) {
+                settle();
+#pragma unroll
+                for (int h = 0; h < 2; h++) keep[h] = keep[h] && !done && d2[h] < 4.0f * Rmax * Rmax * 1.0001f;
+                km0 = g.ballot(keep[0]);
+                km1 = g.ballot(keep[1]);
+            }
+            const unsigned lt = (1u << g.gl) - 1u;
+            if (keep[0]) stage[nst + __popc(km0 & lt)] = make_float4(dx[0], dy[0], d2[0], __int_as_float(cs[0]));
+            if (keep[1])
+                stage[nst + __popc(km0) + __popc(km1 & lt)] = make_float4(dx[1], dy[1], d2[1], __int_as_float(cs[1]));
+            if (P.debug && g.gl == 0 && (km0 | km1))
+                atomicAdd(&V.ctrl->cnt.vor_candidates, (unsigned long long)(__popc(km0) + __popc(km1)));
+            nst += __popc(km0) + __popc(km1);
+            __syncwarp();
+        }
+    };
+    // a bucket row's column range [c0, c1] trimmed to the chord of the disk
+    // of radius 2 Rmax (with the bucket-assignment margin); false when the
+    // row holds no point that can cut
+    auto trim = [&](int row, int& c0, int& c1) -> bool {
+        c0 = c0 < 0 ? 0 : c0;
+        c1 = c1 >= P.nbx ? P.nbx - 1 : c1;
+        if (row < 0 || row >= P.nby || c0 > c1) return false;
+        const float lim = 2.0f * Rmax * 1.0001f + bmargin;
+        const float ddy = fmaxf(fmaxf((float)row * bsy - yf, yf - (float)(row + 1) * bsy), 0.0f);
+        if (ddy > lim) return false;
+        const float w = sqrtf(lim * lim - ddy * ddy) + bmargin;
+        c0 = max(c0, (int)floorf((xf - w) / bsx));
+        c1 = min(c1, (int)floorf((xf + w) / bsx));
+        return c0 <= c1;
+    };
+    // (1) cells started from the octagon: bucket rings around their own
+    // bucket (the 3x3 block, then rings of width 1), each followed by the
+    // batched test, until nothing beyond the rings read can cut: their
+    // radius shrinks ring by ring
+    {
+        bool rdone = done || !seq;
+        for (int r = 1; warp_any(!rdone); r++) {
+            if (P.debug && !rdone && g.gl == 0) atomicAdd(&V.ctrl->cnt.vor_rings, 1ull);
+            const int nr = r == 1 ? 3 : 4 * r;
+            for (int kb = 0; kb < nr; kb += G) {
+                const int k = kb + g.gl;
+                int lo = 0, hi = 0;
+                if (!rdone && k < nr) {
+                    int row, c0, c1;
+                    if (r == 1) {
+                        row = byi - 1 + k;
+                        c0 = bxi - 1;
+                        c1 = bxi + 1;
+                    } else if (k < 2) {
+                        row = k == 0 ? byi - r : byi + r;
+                        c0 = bxi - r;
+                        c1 = bxi + r;
                     } else {
-                        float w = sqrtf(lim * lim - ddy * ddy) + bmargin;
-                        c0 = max(c0, (int)floorf((xf - w) / bsx));
-                        c1 = min(c1, (int)floorf((xf + w) / bsx));
+                        const int kk = k - 2;
+                        row = byi - r + 1 + (kk >> 1);
+                        c0 = c1 = (kk & 1) ? bxi + r : bxi - r;
+                    }
+                    if (trim(row, c0, c1)) {
+                        lo = a.bstart[V.boff + row * P.nbx + c0];
+                        hi = a.bstart[V.boff + row * P.nbx + c1 + 1];
                     }
                 }
-                if (row >= 0 && row < P.nby && c0 <= c1) {
+                load(lo, hi);
+            }
+            settle();
+            // nothing outside the (2r+1)^2 block can cut once it is beyond 2 Rmax
+            if (!rdone) {
+                float dmin = INF;
+                if (bxi - r > 0) dmin = fminf(dmin, xf - (float)(bxi - r) * bsx);
+                if (bxi + r < P.nbx - 1) dmin = fminf(dmin, (float)(bxi + r + 1) * bsx - xf);
+                if (byi - r > 0) dmin = fminf(dmin, yf - (float)(byi - r) * bsy);
+                if (byi + r < P.nby - 1) dmin = fminf(dmin, (float)(byi + r + 1) * bsy - yf);
+                const bool all = bxi - r <= 0 && bxi + r >= P.nbx - 1 && byi - r <= 0 && byi + r >= P.nby - 1;
+                if (done || all || 2.0f * Rmax * 1.0001f < dmin - bmargin) rdone = true;
+            }
+        }
+        if (seq) done = true;
+    }
+    // (2) directly built cells (their radius is close to final): every
+    // bucket row that the disk of radius 2 Rmax around the generator
+    // reaches, one row per lane from the generator's row outward,
+    // each trimmed to the disk's chord with the radius of the moment.  The
+    // radius only shrinks, so this one pass holds every point that can cut
+    // the cell.
+    {
+        if (P.debug && !done && g.gl == 0) atomicAdd(&V.ctrl->cnt.vor_rings, 1ull);
+        const float lim = 2.0f * Rmax * 1.0001f + bmargin;
+        int rlo = 0, rhi = -1;
+        if (!done) {
+            rlo = max(0, (int)floorf((yf - lim) / bsy));
+            rhi = min(P.nby - 1, (int)floorf((yf + lim) / bsy));
+        }
+        const int nrows = rhi - rlo + 1;
+        const int c = min(max(byi, rlo), max(rhi, rlo));  // the generator's row
+        const int na = c - rlo, nb = rhi - c, m = min(na, nb);
+        for (int kb = 0; warp_any(kb < nrows); kb += G) {
+            const int k = kb + g.gl;
+            int lo = 0, hi = 0;
+            if (!done && k < nrows) {
+                // c, c - 1, c + 1, c - 2, ..., then the longer side's rest
+                const int row = k == 0 ? c
+                                : k <= 2 * m ? ((k & 1) ? c - (k + 1) / 2 : c + k / 2)
+                                             : (na > nb ? c - (k - m) : c + (k - m));
+                int c0 = 0, c1 = P.nbx - 1;
+                if (trim(row, c0, c1)) {
                     lo = a.bstart[V.boff + row * P.nbx + c0];
                     hi = a.bstart[V.boff + row * P.nbx + c1 + 1];
                 }
             }
-            int cnt = hi - lo;
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) {
-                int y = __shfl_up_sync(kFull, incl, o, G);
-                if (g.gl >= o) incl += y;
-            }
-            int total = g.shfl(incl, G - 1);
-            int excl = incl - cnt;
-            // two candidates per lane and iteration (entries q0 + gl and
-            // q0 + G + gl), their loads issued together
-            for (int q0 = 0; warp_any(q0 < total); q0 += 2 * G) {
-                int cs[2];
-                bool valid[2];
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const int q = q0 + h * G + g.gl;
-                    int ow = 0;
-#pragma unroll
-                    for (int step = G / 2; step > 0; step >>= 1) {
-                        int pr = ow + step;
-                        int ex = g.shfl(excl, pr);
-                        if (ex <= q) ow = pr;
-                    }
-                    const int olo = g.shfl(lo, ow);
-                    const int oex = g.shfl(excl, ow);
-                    cs[h] = olo + (q - oex);
-                    valid[h] = !done && q < total && cs[h] != s;
-                }
-                float4 pj4[2];
-                bool dup[2];
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    pj4[h] = valid[h] ? a.pf[cs[h]] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    dup[h] = valid[h] && a.dom[cs[h]];
-                }
-                float dx[2], dy[2], d2[2];
-                bool keep[2];
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    dx[h] = ff_diff(pj4[h].x, pj4[h].y, pi4.x, pi4.y);
-                    dy[h] = ff_diff(pj4[h].z, pj4[h].w, pi4.z, pi4.w);
-                    d2[h] = dx[h] * dx[h] + dy[h] * dy[h];
-                    if (sizeof(T) == 8 && valid[h] && d2[h] < 9.094947e-13f) {  // |d| < 2^-20: exact double difference
-                        const float2 e = close_diff<T>(a.srt.x, a.srt.y, cs[h], a.srt.x[s], a.srt.y[s]);
-                        dx[h] = e.x;
-                        dy[h] = e.y;
-                        d2[h] = dx[h] * dx[h] + dy[h] * dy[h];
-                    }
-                    keep[h] = valid[h] && !dup[h] && d2[h] < 4.0f * Rmax * Rmax * 1.0001f;
-                }
-                unsigned km0 = g.ballot(keep[0]), km1 = g.ballot(keep[1]);
-                if (warp_any(nst + __popc(km0) + __popc(km1) > kStageCap)) {
-                    settle();
-#pragma unroll
-                    for (int h = 0; h < 2; h++) keep[h] = keep[h] && !done && d2[h] < 4.0f * Rmax * Rmax * 1.0001f;
-                    km0 = g.ballot(keep[0]);
-                    km1 = g.ballot(keep[1]);
-                }
-                const unsigned lt = (1u << g.gl) - 1u;
-                if (keep[0]) stage[nst + __popc(km0 & lt)] = make_float4(dx[0], dy[0], d2[0], __int_as_float(cs[0]));
-                if (keep[1])
-                    stage[nst + __popc(km0) + __popc(km1 & lt)] = make_float4(dx[1], dy[1], d2[1], __int_as_float(cs[1]));
-                if (P.debug && g.gl == 0 && (km0 | km1))
-                    atomicAdd(&V.ctrl->cnt.vor_candidates, (unsigned long long)(__popc(km0) + __popc(km1)));
-                nst += __popc(km0) + __popc(km1);
-                __syncwarp();
-            }
+            load(lo, hi);
         }
         settle();
-        // nothing outside the (2r+1)^2 block can cut once it is beyond 2 Rmax
-        if (!done) {
-            float dmin = INF;
-            if (bxi - r > 0) dmin = fminf(dmin, xf - (float)(bxi - r) * bsx);
-            if (bxi + r < P.nbx - 1) dmin = fminf(dmin, (float)(bxi + r + 1) * bsx - xf);
-            if (byi - r > 0) dmin = fminf(dmin, yf - (float)(byi - r) * bsy);
-            if (byi + r < P.nby - 1) dmin = fminf(dmin, (float)(byi + r + 1) * bsy - yf);
-            bool all = bxi - r <= 0 && bxi + r >= P.nbx - 1 && byi - r <= 0 && byi + r >= P.nby - 1;
-            if (all || 2.0f * Rmax * 1.0001f < dmin - bmargin) done = true;
-        }
+        done = true;
     }
+    // the ring is written from its smallest label on, so that it depends on
+    // the cell alone, not on the order of the clips (which cells shared a
+    // warp, or the previous rebuild's rotation); every lane of the warp
+    // takes part, before any group returns
+    const bool wr = live && status == 0;
+    int mn = wr && g.gl < ne ? L.lab : 0x7fffffff;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+    const unsigned at = g.ballot(wr && g.gl < ne && L.lab == mn);
+    int src = g.gl + (at ? __ffs(at) - 1 : 0);
+    if (src >= ne) src -= ne;
+    const int lab = g.shfl(L.lab, src & (G - 1));
     if (!live) return;
     if (status == 2) {
         // out of lanes: queue the cell for the next wider pass (8 -> 16 -> 32
@@ -735,7 +792,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
         }
         return;
     }
-    if (g.gl < ne) a.ring[(size_t)s * kRingCap + g.gl] = L.lab;
+    if (g.gl < ne) a.ring[(size_t)s * kRingCap + g.gl] = lab;
     if (g.gl == 0) {
         a.ring_n[s] = (uint8_t)ne;
         a.cellR[s] = Rmax;
