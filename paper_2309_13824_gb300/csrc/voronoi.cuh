@@ -290,8 +290,11 @@ __device__ __forceinline__ void bounding_plane(int lab, float SB, float xf, floa
 }
 
 // one cell per group; slot < 0 marks an idle group (it still takes part in
-// every collective operation of its warp)
-template <typename T, int G>
+// every collective operation of its warp).  DISK: directly built cells read
+// their security disk's bucket rows in one pass; without it (the batched
+// kernels, whose register budget the second reading loop would strain) every
+// cell reads bucket rings.
+template <typename T, int G, bool DISK>
 __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, const Grp<G>& g, float4* stage) {
     const DevParams& P = V.P;
     const float INF = __int_as_float(0x7f800000);
@@ -675,7 +678,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     // batched test, until nothing beyond the rings read can cut: their
     // radius shrinks ring by ring
     {
-        bool rdone = done || !seq;
+        bool rdone = done || (DISK && !seq);
         for (int r = 1; warp_any(!rdone); r++) {
             if (P.debug && !rdone && g.gl == 0) atomicAdd(&V.ctrl->cnt.vor_rings, 1ull);
             const int nr = r == 1 ? 3 : 4 * r;
@@ -716,7 +719,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
                 if (done || all || 2.0f * Rmax * 1.0001f < dmin - bmargin) rdone = true;
             }
         }
-        if (seq) done = true;
+        if (seq || !DISK) done = true;
     }
     // (2) directly built cells (their radius is close to final): every
     // bucket row that the disk of radius 2 Rmax around the generator
@@ -724,7 +727,7 @@ __device__ void voronoi_cell(const IterArgs<T>& a, const MeshView& V, int slot, 
     // each trimmed to the disk's chord with the radius of the moment.  The
     // radius only shrinks, so this one pass holds every point that can cut
     // the cell.
-    {
+    if constexpr (DISK) {
         if (P.debug && !done && g.gl == 0) atomicAdd(&V.ctrl->cnt.vor_rings, 1ull);
         const float lim = 2.0f * Rmax * 1.0001f + bmargin;
         int rlo = 0, rhi = -1;
@@ -818,7 +821,7 @@ __global__ void __launch_bounds__(kVoroThreads, TRIME_VORO_MINB) k_voronoi(const
         if (B && skip_rebuild(V.ctrl, a.force)) continue;
         int s = w * cpw + lane / G;
         bool ok = s < a.n && (!B || s - V.soff < V.n);
-        voronoi_cell<T, G>(a, V, ok ? s : -1, g, stage);
+        voronoi_cell<T, G, !B>(a, V, ok ? s : -1, g, stage);
     }
 }
 
@@ -844,7 +847,7 @@ __global__ void __launch_bounds__(kVoroThreads, TRIME_VORO_MINB) k_voronoi_wide(
         int s = i < n ? list[i] : -1;
         // the cells of one warp may belong to different meshes of a batch:
         // each group reads its own mesh's view
-        voronoi_cell<T, G>(a, mesh_of<B>(a, s < 0 ? list[w * cpw] : s), s, g, stage);
+        voronoi_cell<T, G, !B>(a, mesh_of<B>(a, s < 0 ? list[w * cpw] : s), s, g, stage);
     }
 }
 
