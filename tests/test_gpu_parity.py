@@ -75,6 +75,25 @@ def test_rebuilds_after_steps_and_moves(precision):
     assert st["clip_inconsistent"] == 0
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rebuild_after_positions_shuffled(precision):
+    """The clipping pass starts each cell from its neighbours at the last
+    rebuild, but those are only candidates: after every point was given
+    another point's position (each cell's previous neighbours are now
+    arbitrary points of the mesh) a rebuild still gives the oracle's
+    triangles without an inconsistent clip, and so does the next rebuild,
+    whose previous neighbours are exact again."""
+    gm, om = make_pair(annulus_small(), precision=precision, method=2)
+    gm.step(3)
+    P, cls, dprev = gm.state()
+    Q = P[np.random.default_rng(23).permutation(len(P))]
+    gm.set_state(Q)
+    om.set_points(Q.astype(np.float64))
+    for _ in range(2):
+        st, _ = _tri_equal(gm, om)
+        assert st["clip_inconsistent"] == 0
+
+
 def test_triangles_unbounded_and_no_validity():
     sdf = W.grid_from_fn(lambda x, y: W.disk_sdf_fn(x, y, r=1.0), 64)
     rng = np.random.default_rng(5)
