@@ -110,6 +110,13 @@ def test_triangles_degenerate_lattice():
     st, tg = _tri_equal(gm, om)
     assert st["exact_calls"] > 0
     assert len(tg) == 2 * 39 * 39
+    # bounded cells, rebuilt a second time: the second rebuild starts every
+    # cell from its previous neighbours, whose certificate (every edge of
+    # positive length) meets the cocircular vertices
+    gm, om = make_pair((sdf, W.constant_grid(1.0), pts))
+    for _ in range(2):
+        st, tg = _tri_equal(gm, om)
+        assert st["exact_calls"] > 0 and st["clip_inconsistent"] == 0
 
 
 def test_tiny_and_empty_inputs():
@@ -128,8 +135,9 @@ def test_duplicate_points():
     pts[10] = pts[20]
     pts[30] = pts[31] = pts[32]
     gm, om = make_pair((sdf, W.constant_grid(1.0), pts))
-    st, tg = _tri_equal(gm, om)
-    assert st["dup_points"] == 3
+    for _ in range(2):  # the second rebuild starts from the previous neighbours
+        st, tg = _tri_equal(gm, om)
+        assert st["dup_points"] == 3
 
 
 def _edge_length_scale(om, p0):
