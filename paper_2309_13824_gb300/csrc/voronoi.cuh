@@ -8,13 +8,23 @@
 // pass uses G = 8 (four cells per warp; final cells have 6-8 edges); a cell
 // that would need more than 8 edges at some step is queued and redone with
 // G = 16, then G = 32 by the same code, and one that needs more than 32 by a
-// serial pass (one thread per cell, up to 64 edges).  Candidates come from the bucket grid ring by ring, one per lane,
-// are filtered by the security radius (a point farther than twice the largest
-// vertex distance cannot cut), staged in shared memory and applied nearest
-// first across the staged set.  A clip classifies every vertex in parallel,
-// finds the single run of cut vertices with two ballots and rotates the edge
-// list with shuffles.  Every collective operation is executed by the whole
-// warp; a group with nothing to do runs it as a no-op.
+// serial pass (one thread per cell, up to 64 edges).
+//
+// The cell is the intersection of the half-planes of all other points, so
+// neither the candidates tried nor their order change it.  A cell starts from
+// its edges at the last rebuild: when they still bound a convex polygon that
+// winds once with every edge of positive length (checked with the exact
+// predicate below), that polygon is taken in one step; otherwise the cell
+// starts from the octagon and clips by those previous neighbours first.
+// Candidates then come from the bucket grid -- the rows of the disk of
+// radius 2 Rmax for a directly built cell, ring by ring otherwise -- filtered
+// by that security radius (a point farther than twice the largest vertex
+// distance cannot cut), staged in shared memory, tested against every vertex
+// at once, and only those that cut are applied, nearest first.  A clip
+// classifies every vertex in parallel, finds the single run of cut vertices
+// with two ballots and rotates the edge list with shuffles.  Every collective
+// operation is executed by the whole warp; a group with nothing to do runs it
+// as a no-op.
 //
 // Exactness: a vertex where two bisectors meet is the circumcentre of
 // (i, j, k); the candidate l cuts it iff det4(i,j,k,l) > 0 (l inside that
