@@ -46,7 +46,7 @@ constexpr int kStageCap = 64;  // staged candidates per group (16 bytes each; on
 // resident blocks per SM the clipping kernels are compiled for (registers:
 // 65536 / (kVoroThreads x this)); a build-time tuning knob
 #ifndef TRIME_VORO_MINB
-#define TRIME_VORO_MINB 6
+#define TRIME_VORO_MINB 5
 #endif
 
 template <int G>
